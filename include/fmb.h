@@ -1,0 +1,171 @@
+/*
+ * fmb.h -- C ABI of the GB300 (sm_103a) renderer for the simplified, two-parameter
+ * Fuzzy Metaballs model of "Flexible Techniques for Differentiable Rendering with
+ * 3D Gaussians" (Keselman & Hebert, WACV 2024).
+ *
+ * Model (paper Sec. 3.1-3.2, Sec. 5, Sec. 6):
+ *   Gaussian i: mean mu_i, precision Sigma_i^-1 = L_i L_i^T with L_i lower
+ *   triangular (the "inverse root precision" of Sec. 3.1), weight lambda_i > 0.
+ *   For the ray v (unit length, world frame) from the camera centre o of a pixel:
+ *     t_i     = (mu_i - o)^T Sigma_i^-1 v / (v^T Sigma_i^-1 v)   (max-likelihood
+ *               depth along the ray, next to Eq. 2)
+ *     d_i     = -1/2 (o + v t_i - mu_i)^T Sigma_i^-1 (o + v t_i - mu_i) + ln lambda_i  (Eq. 2)
+ *     delta_i = exp(d_i)                                            (Eq. 4)
+ *     w_i     = exp(beta1 d_i - (beta2 / eta) t_i)                  (Eq. 7)
+ *     depth   = sum_i w_i t_i / sum_i w_i                           (Eq. 3)
+ *     alpha   = 1 - exp(-sum_i delta_i)                             (Eq. 8)
+ *     normal  = R n_f, n_f = N/|N|, N = sum_i w_i n_i / sum_i w_i,
+ *               n_i = Sigma_i^-1 (o + v t_i - mu_i) / |...|         (Eq. 17 blended by Eq. 3)
+ *     flow_j  = pi(R_j p + t_j) - (x + 1/2, y + 1/2), p = o + v depth,
+ *               pi(X) = (fx X0/X2 + cx, fy X1/X2 + cy)              (Sec. 5)
+ *   The blend is sort-free: outputs do not depend on the order of the Gaussians.
+ *
+ * Conventions for every entry point:
+ *   - All array pointers are DEVICE pointers owned by the caller, fp32 (or int64
+ *     where stated), C-contiguous.  Pointers named h_* are HOST pointers, read
+ *     before the call returns.
+ *   - The library never allocates device memory.  Scratch memory is the caller's
+ *     `workspace` (size from fmb_workspace_bytes, base aligned to 256 bytes).
+ *   - Work is enqueued on `stream` and the call returns without synchronising.
+ *   - Invalid arguments are reported before anything is enqueued.  No C++ exception
+ *     crosses the ABI.  On a non-OK status, fmb_last_error() returns a message
+ *     (thread-local, valid until the next call on the same thread).
+ *   - Invalid data that is not checked on the host (lambda <= 0, a singular L, a
+ *     flow target point at or behind its camera plane, NaN inputs) gives NaN or Inf
+ *     in the affected outputs; it never makes a kernel read or write out of bounds.
+ *   - Pose: 12 floats, R (3x3 row-major) then t, world -> camera:
+ *     x_cam = R x_world + t; OpenCV axes (x right, y down, z forward).
+ *   - Pixel (x, y) of a view is ray (x + 1/2 - cx)/fx, (y + 1/2 - cy)/fy, 1,
+ *     normalised; pixels are stored row-major, p = y * W + x.
+ *   - Depth is the distance along the unit ray (not z-depth).
+ */
+#ifndef FMB_H
+#define FMB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (same type as cudaStream_t / CUstream); NULL = legacy default stream. */
+typedef struct CUstream_st* fmb_stream_t;
+
+typedef enum {
+  FMB_OK = 0,
+  FMB_ERR_INVALID_ARG = 1, /* a size, index, pointer or parameter failed host validation */
+  FMB_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed */
+  FMB_ERR_TIMEOUT = 3,     /* a bounded device-side wait gave up (see fmb_read_device_status) */
+  FMB_ERR_WORKSPACE = 4    /* workspace missing, too small or misaligned */
+} fmb_status;
+
+/* Renderer parameters.  beta1, beta2: Eq. 7 (Sec. 7 uses beta1 = 21.4, beta2 = 3.14);
+ * eta: the shape scale of Sec. 3.1 (> 0; 1 = no rescaling). */
+typedef struct {
+  float beta1;
+  float beta2;
+  float eta;
+  int variant;       /* 0 = two-parameter model of Sec. 3.2 (the only one implemented) */
+  int want_normals;  /* 1: compute the blended normal plane (Eq. 17) and its adjoint */
+  int n_flow;        /* flow slots per view, 0..2 (Sec. 5: forward i+1 and backward i-1) */
+  int deterministic; /* backward: 1 = fixed-order two-stage reduction, 0 = fp32 atomics */
+  int use_persistent;/* reserved for the persistent work-queue launch; must be 0 for now */
+  int fwd_rays_per_thread; /* tile hints; 0 = library default */
+  int fwd_threads;
+  int bwd_ray_tile;
+  int bwd_threads;
+} fmb_params;
+
+/* One camera view of one object.  Planes of the view start at pixel `pix_offset`
+ * of the batched output buffers (see fmb_render_forward). */
+typedef struct {
+  int W, H;               /* image size in pixels, >= 1 */
+  float fx, fy, cx, cy;   /* pinhole intrinsics; fx, fy > 0 (Sec. 5 uses fx = fy, centred) */
+  int object;             /* index of the object (Gaussian range) this view renders */
+  int pose;               /* index into poses: the camera's pose */
+  int flow_target[2];     /* pose indices of the flow targets of slots 0 and 1, or -1 */
+  long long pix_offset;   /* first pixel of this view in the batched planes */
+} fmb_view;
+
+/*
+ * Forward render of a batch of views (paper Eq. 2, 3, 4, 7, 8, 17 and Sec. 5 flow).
+ *
+ * Scene: n_objects objects; object k owns Gaussians [h_obj_offsets[k],
+ * h_obj_offsets[k+1]) (host int64 array of n_objects + 1 entries, starting at 0,
+ * non-decreasing, every object with >= 1 Gaussian).  means: [G][3]; chol: [G][6]
+ * packed (L00, L10, L11, L20, L21, L22); weights: [G] (lambda > 0), with
+ * G = h_obj_offsets[n_objects].  poses: [n_poses][12].
+ *
+ * Outputs (device, overwritten for every pixel of every view; P_v = W*H):
+ *   depth  [P_total]          depth[pix_offset + p]
+ *   alpha  [P_total]          alpha[pix_offset + p]
+ *   normal [3*P_total]        per view a [3][P_v] block at 3*pix_offset (camera
+ *                             frame, unit length); may be NULL if !want_normals
+ *   flow   [2*n_flow*P_total] per view a [n_flow][2][P_v] block at
+ *                             2*n_flow*pix_offset, in pixels (u then v); a slot
+ *                             whose flow_target is -1 is written as 0; NULL if
+ *                             n_flow == 0
+ *   saved  [3*P_total]        per view a [3][P_v] block at 3*pix_offset:
+ *                             0: log2 of sum_i 2^(e_i log2 e), e_i = beta1 d_i - (beta2/eta) t_i
+ *                             1: sum_i delta_i;  2: |N| (0 without normals)
+ *                             The backward pass needs it.
+ * Views may not overlap in the output planes (checked).
+ * workspace: >= fmb_workspace_bytes(...) bytes, 256-byte aligned; its contents
+ * are scratch and need not be preserved between calls.
+ */
+fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
+                              const float* means, const float* chol, const float* weights, int n_poses,
+                              const float* poses, int n_views, const fmb_view* h_views, float* depth,
+                              float* alpha, float* normal, float* flow, float* saved, void* workspace,
+                              size_t workspace_bytes, fmb_stream_t stream);
+
+/*
+ * Adjoint of fmb_render_forward (the derivative of the renderer defined above;
+ * the paper differentiates its JAX renderer automatically, Sec. 4).  It recomputes
+ * every ray-Gaussian term from the saved per-pixel log-normaliser instead of
+ * storing per-pair values.
+ *
+ * Inputs: the same scene, poses, views and params as the forward call; the
+ * forward's depth, normal (NULL if !want_normals) and saved planes; the upstream
+ * gradients g_depth, g_alpha, g_normal, g_flow in the layouts of the forward
+ * outputs (each may be NULL = zero).
+ * Outputs (overwritten, never accumulated): grad_means [G][3], grad_chol [G][6],
+ * grad_weights [G] (d/d lambda), grad_poses [n_poses][12] (d/dR as a free 3x3
+ * matrix, row-major, then d/dt; NULL = pose gradients not computed).
+ * deterministic = 1 gives bitwise-reproducible results (fixed-order two-stage
+ * reduction through the workspace); 0 uses fp32 atomics.
+ */
+fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
+                               const float* means, const float* chol, const float* weights, int n_poses,
+                               const float* poses, int n_views, const fmb_view* h_views, const float* depth,
+                               const float* normal, const float* saved, const float* g_depth,
+                               const float* g_alpha, const float* g_normal, const float* g_flow,
+                               float* grad_means, float* grad_chol, float* grad_weights, float* grad_poses,
+                               void* workspace, size_t workspace_bytes, fmb_stream_t stream);
+
+/* Workspace bytes needed by fmb_render_forward and fmb_render_backward for this
+ * batch (the larger of the two).  Returns 0 on invalid arguments (see
+ * fmb_last_error). */
+size_t fmb_workspace_bytes(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
+                           int n_views, const fmb_view* h_views);
+
+/* Copies the device status word of a workspace to *h_status and synchronises
+ * `stream`: 0 = no device-side error; nonzero = a bounded wait gave up (the
+ * outputs of that call are invalid).  The word is cleared by every render call. */
+fmb_status fmb_read_device_status(const void* workspace, int* h_status, fmb_stream_t stream);
+
+/* Message for the last non-OK status returned on this thread ("" if none). */
+const char* fmb_last_error(void);
+
+/* Library version string. */
+const char* fmb_version(void);
+
+/* Fills *p with the default parameters (beta1 21.4, beta2 3.14, eta 1, normals on,
+ * one flow slot, atomics, plain launch, default tiles). */
+void fmb_default_params(fmb_params* p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMB_H */

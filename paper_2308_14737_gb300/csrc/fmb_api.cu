@@ -1,0 +1,389 @@
+// fmb_api.cu -- the C ABI of include/fmb.h: host-side validation, launch planning
+// and the enqueueing of the prologue, forward, backward and reduction kernels.
+// No device memory is allocated here; scratch lives in the caller's workspace:
+//
+//   [0, 256)            status word (int) and padding
+//   [256, 256 + 64 R)   R per-(view, Gaussian) records, R = sum over views of K
+//   [.., ..)            backward partials (deterministic mode only)
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "fmb_internal.cuh"
+
+namespace fmb {
+int forward_rays_per_cta(int rpt);
+}
+
+namespace {
+
+thread_local std::string g_err;
+
+constexpr size_t kHeaderBytes = 256;
+constexpr int kDefaultRpt = 2;
+constexpr int kDefaultRayTile = 256;
+constexpr int kMaxGaussPerCta = 128;
+constexpr long long kMaxK = 1 << 22;
+
+fmb_status fail(fmb_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+struct BwdBlocking {
+  int n_gb, GB, S;
+};
+
+BwdBlocking bwd_blocking(int K, int T) {
+  const int gbmax = std::min(T, kMaxGaussPerCta);
+  BwdBlocking b;
+  b.n_gb = (K + gbmax - 1) / gbmax;
+  b.GB = (K + b.n_gb - 1) / b.n_gb;
+  b.S = std::max(1, T / b.GB);
+  return b;
+}
+
+// Threads per backward CTA: the candidate that wastes the fewest thread slots over
+// the batch, weighted by each view's pairs.
+int choose_bwd_threads(const fmb_view* views, int n_views, const long long* offs) {
+  const int cand[] = {128, 160, 192, 224, 256};
+  int best = 256;
+  double best_eff = -1.0;
+  for (int T : cand) {
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < n_views; ++i) {
+      const int K = static_cast<int>(offs[views[i].object + 1] - offs[views[i].object]);
+      const double pairs = static_cast<double>(views[i].W) * views[i].H * K;
+      BwdBlocking b = bwd_blocking(K, T);
+      const double eff = (static_cast<double>(b.GB) * b.S / T) * (static_cast<double>(K) / (b.n_gb * b.GB));
+      num += pairs * eff;
+      den += pairs;
+    }
+    const double eff = den > 0 ? num / den : 0.0;
+    if (eff > best_eff + 1e-9 || (std::fabs(eff - best_eff) <= 1e-9 && T > best)) {
+      best_eff = eff;
+      best = T;
+    }
+  }
+  return best;
+}
+
+struct Plan {
+  std::vector<fmb::Batch> fwd;  // forward launches (tiles of rays)
+  std::vector<fmb::Batch> bwd;  // backward launches (ray tiles x Gaussian blocks)
+  long long n_records = 0;
+  long long part_floats = 0;
+  long long n_gauss = 0;
+  int maxK = 0;
+  int rpt = kDefaultRpt;
+  int ray_tile = kDefaultRayTile;
+  int bwd_threads = 256;
+};
+
+fmb_status validate_scene(const fmb_params* p, int n_objects, const long long* offs, int n_views,
+                          const fmb_view* views) {
+  if (!p) return fail(FMB_ERR_INVALID_ARG, "params is NULL");
+  if (!std::isfinite(p->beta1) || !std::isfinite(p->beta2)) return fail(FMB_ERR_INVALID_ARG, "beta1/beta2 not finite");
+  if (!(p->eta > 0.0f) || !std::isfinite(p->eta)) return fail(FMB_ERR_INVALID_ARG, "eta must be > 0");
+  if (p->variant != 0) return fail(FMB_ERR_INVALID_ARG, "only variant 0 (two-parameter model) is implemented");
+  if (p->n_flow < 0 || p->n_flow > 2) return fail(FMB_ERR_INVALID_ARG, "n_flow must be 0, 1 or 2");
+  if (p->use_persistent != 0) return fail(FMB_ERR_INVALID_ARG, "use_persistent is not available yet");
+  if (p->fwd_rays_per_thread != 0 && p->fwd_rays_per_thread != 1 && p->fwd_rays_per_thread != 2 &&
+      p->fwd_rays_per_thread != 4)
+    return fail(FMB_ERR_INVALID_ARG, "fwd_rays_per_thread must be 0, 1, 2 or 4");
+  if (p->fwd_threads != 0 && p->fwd_threads != 128) return fail(FMB_ERR_INVALID_ARG, "fwd_threads must be 0 or 128");
+  if (p->bwd_ray_tile < 0 || p->bwd_ray_tile > 1024 || (p->bwd_ray_tile % 32) != 0)
+    return fail(FMB_ERR_INVALID_ARG, "bwd_ray_tile must be a multiple of 32 in [32, 1024] (0 = default)");
+  if (p->bwd_threads != 0 && (p->bwd_threads < 32 || p->bwd_threads > 256 || (p->bwd_threads % 32) != 0))
+    return fail(FMB_ERR_INVALID_ARG, "bwd_threads must be a multiple of 32 in [32, 256] (0 = default)");
+  if (n_objects < 1) return fail(FMB_ERR_INVALID_ARG, "n_objects must be >= 1");
+  if (!offs) return fail(FMB_ERR_INVALID_ARG, "h_obj_offsets is NULL");
+  if (offs[0] != 0) return fail(FMB_ERR_INVALID_ARG, "h_obj_offsets[0] must be 0");
+  for (int k = 0; k < n_objects; ++k) {
+    const long long K = offs[k + 1] - offs[k];
+    if (K < 1) return fail(FMB_ERR_INVALID_ARG, "object " + std::to_string(k) + " has no Gaussians");
+    if (K > kMaxK) return fail(FMB_ERR_INVALID_ARG, "object " + std::to_string(k) + " has too many Gaussians");
+  }
+  if (n_views < 1) return fail(FMB_ERR_INVALID_ARG, "n_views must be >= 1");
+  if (!views) return fail(FMB_ERR_INVALID_ARG, "h_views is NULL");
+  return FMB_OK;
+}
+
+fmb_status validate_views(int n_objects, int n_poses, int n_views, const fmb_view* views) {
+  std::vector<std::pair<long long, long long>> spans;
+  spans.reserve(n_views);
+  for (int i = 0; i < n_views; ++i) {
+    const fmb_view& v = views[i];
+    const std::string id = "view " + std::to_string(i) + ": ";
+    if (v.W < 1 || v.H < 1) return fail(FMB_ERR_INVALID_ARG, id + "W and H must be >= 1");
+    if (static_cast<long long>(v.W) * v.H > (1ll << 30)) return fail(FMB_ERR_INVALID_ARG, id + "image too large");
+    if (!(v.fx > 0.f) || !(v.fy > 0.f) || !std::isfinite(v.fx) || !std::isfinite(v.fy))
+      return fail(FMB_ERR_INVALID_ARG, id + "fx, fy must be > 0");
+    if (!std::isfinite(v.cx) || !std::isfinite(v.cy)) return fail(FMB_ERR_INVALID_ARG, id + "cx, cy not finite");
+    if (v.object < 0 || v.object >= n_objects) return fail(FMB_ERR_INVALID_ARG, id + "object out of range");
+    if (v.pose < 0 || v.pose >= n_poses) return fail(FMB_ERR_INVALID_ARG, id + "pose out of range");
+    for (int j = 0; j < 2; ++j)
+      if (v.flow_target[j] < -1 || v.flow_target[j] >= n_poses)
+        return fail(FMB_ERR_INVALID_ARG, id + "flow_target out of range");
+    if (v.pix_offset < 0) return fail(FMB_ERR_INVALID_ARG, id + "pix_offset < 0");
+    spans.emplace_back(v.pix_offset, v.pix_offset + static_cast<long long>(v.W) * v.H);
+  }
+  std::sort(spans.begin(), spans.end());
+  for (size_t i = 1; i < spans.size(); ++i)
+    if (spans[i].first < spans[i - 1].second) return fail(FMB_ERR_INVALID_ARG, "views overlap in the output planes");
+  return FMB_OK;
+}
+
+Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_views, const fmb_view* views) {
+  Plan pl;
+  pl.rpt = p->fwd_rays_per_thread > 0 ? p->fwd_rays_per_thread : kDefaultRpt;
+  pl.ray_tile = p->bwd_ray_tile > 0 ? p->bwd_ray_tile : kDefaultRayTile;
+  pl.bwd_threads = p->bwd_threads > 0 ? p->bwd_threads : choose_bwd_threads(views, n_views, offs);
+  pl.n_gauss = offs[n_objects];
+  const int rays_fwd = fmb::forward_rays_per_cta(pl.rpt);
+  const int n_flow = p->n_flow;
+  long long rec = 0, part = 0;
+  for (int base = 0; base < n_views; base += fmb::kMaxBatchViews) {
+    const int nb = std::min(fmb::kMaxBatchViews, n_views - base);
+    fmb::Batch bf;
+    std::memset(&bf, 0, sizeof(bf));
+    fmb::Batch bb = bf;
+    bf.n_views = bb.n_views = nb;
+    long long ctas_f = 0, ctas_b = 0;
+    for (int i = 0; i < nb; ++i) {
+      const fmb_view& v = views[base + i];
+      fmb::DevView d;
+      std::memset(&d, 0, sizeof(d));
+      d.W = v.W;
+      d.H = v.H;
+      d.fx = v.fx;
+      d.fy = v.fy;
+      d.cx = v.cx;
+      d.cy = v.cy;
+      d.pose = v.pose;
+      d.tgt0 = n_flow > 0 ? v.flow_target[0] : -1;
+      d.tgt1 = n_flow > 1 ? v.flow_target[1] : -1;
+      d.obj = v.object;
+      d.K = static_cast<int>(offs[v.object + 1] - offs[v.object]);
+      pl.maxK = std::max(pl.maxK, d.K);
+      d.gauss_off = offs[v.object];
+      d.rec_off = rec;
+      d.pix_off = v.pix_offset;
+      rec += d.K;
+      const long long P = static_cast<long long>(v.W) * v.H;
+      // forward
+      fmb::DevView df = d;
+      df.n_tiles = static_cast<int>((P + rays_fwd - 1) / rays_fwd);
+      df.n_gblocks = 1;
+      df.cta_begin = static_cast<int>(ctas_f);
+      ctas_f += df.n_tiles;
+      bf.v[i] = df;
+      // backward
+      fmb::DevView db = d;
+      BwdBlocking bk = bwd_blocking(d.K, pl.bwd_threads);
+      db.n_tiles = static_cast<int>((P + pl.ray_tile - 1) / pl.ray_tile);
+      db.n_gblocks = bk.n_gb;
+      db.GB = bk.GB;
+      db.S = bk.S;
+      db.slot_floats = 10 * bk.GB + 12 * (1 + n_flow);
+      db.part_off = part;
+      part += static_cast<long long>(db.n_tiles) * db.n_gblocks * db.slot_floats;
+      db.cta_begin = static_cast<int>(ctas_b);
+      ctas_b += static_cast<long long>(db.n_tiles) * db.n_gblocks;
+      bb.v[i] = db;
+    }
+    if (ctas_f > 0x7fffffffll || ctas_b > 0x7fffffffll) throw std::runtime_error("grid too large");
+    bf.total_ctas = static_cast<int>(ctas_f);
+    bb.total_ctas = static_cast<int>(ctas_b);
+    pl.fwd.push_back(bf);
+    pl.bwd.push_back(bb);
+  }
+  pl.n_records = rec;
+  pl.part_floats = part;
+  return pl;
+}
+
+size_t workspace_needed(const fmb_params* p, const Plan& pl) {
+  size_t bytes = kHeaderBytes + align256(static_cast<size_t>(pl.n_records) * 16 * fmb::kRecFloat4);
+  if (p->deterministic) bytes += align256(static_cast<size_t>(pl.part_floats) * sizeof(float));
+  return bytes;
+}
+
+fmb::Consts make_consts(const fmb_params* p) {
+  const double log2e = 1.4426950408889634;
+  fmb::Consts c;
+  c.K2 = static_cast<float>(-(static_cast<double>(p->beta2) / p->eta) * log2e);
+  c.K3 = static_cast<float>(-0.5 * log2e);
+  c.beta1 = p->beta1;
+  c.b2e = static_cast<float>(static_cast<double>(p->beta2) / p->eta);
+  return c;
+}
+
+fmb_status check_workspace(void* ws, size_t bytes, size_t need) {
+  if (!ws) return fail(FMB_ERR_WORKSPACE, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(FMB_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  if (bytes < need)
+    return fail(FMB_ERR_WORKSPACE, "workspace too small: need " + std::to_string(need) + " bytes, got " +
+                                       std::to_string(bytes));
+  return FMB_OK;
+}
+
+fmb_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(FMB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+extern "C" {
+
+void fmb_default_params(fmb_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->beta1 = 21.4f;
+  p->beta2 = 3.14f;
+  p->eta = 1.0f;
+  p->want_normals = 1;
+  p->n_flow = 1;
+}
+
+const char* fmb_last_error(void) { return g_err.c_str(); }
+
+const char* fmb_version(void) { return "fmb-gb300 0.1 (sm_103a)"; }
+
+size_t fmb_workspace_bytes(const fmb_params* params, int n_objects, const long long* h_obj_offsets, int n_views,
+                           const fmb_view* h_views) {
+  try {
+    if (validate_scene(params, n_objects, h_obj_offsets, n_views, h_views) != FMB_OK) return 0;
+    Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views);
+    return workspace_needed(params, pl);
+  } catch (const std::exception& e) {
+    fail(FMB_ERR_INVALID_ARG, e.what());
+    return 0;
+  } catch (...) {
+    fail(FMB_ERR_INVALID_ARG, "unknown error");
+    return 0;
+  }
+}
+
+fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
+                              const float* means, const float* chol, const float* weights, int n_poses,
+                              const float* poses, int n_views, const fmb_view* h_views, float* depth,
+                              float* alpha, float* normal, float* flow, float* saved, void* workspace,
+                              size_t workspace_bytes, fmb_stream_t stream) {
+  try {
+    g_err.clear();
+    fmb_status st = validate_scene(params, n_objects, h_obj_offsets, n_views, h_views);
+    if (st != FMB_OK) return st;
+    if (n_poses < 1 || !poses) return fail(FMB_ERR_INVALID_ARG, "poses missing");
+    if (!means || !chol || !weights) return fail(FMB_ERR_INVALID_ARG, "means, chol and weights are required");
+    if (!depth || !alpha || !saved) return fail(FMB_ERR_INVALID_ARG, "depth, alpha and saved are required");
+    if (params->want_normals && !normal) return fail(FMB_ERR_INVALID_ARG, "normal is NULL but want_normals is set");
+    if (params->n_flow > 0 && !flow) return fail(FMB_ERR_INVALID_ARG, "flow is NULL but n_flow > 0");
+    st = validate_views(n_objects, n_poses, n_views, h_views);
+    if (st != FMB_OK) return st;
+    Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views);
+    st = check_workspace(workspace, workspace_bytes, workspace_needed(params, pl));
+    if (st != FMB_OK) return st;
+
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int* status = static_cast<int*>(workspace);
+    float4* records = reinterpret_cast<float4*>(static_cast<char*>(workspace) + kHeaderBytes);
+    const fmb::Scene sc{means, chol, weights, poses};
+    const fmb::Consts c = make_consts(params);
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    for (const fmb::Batch& b : pl.fwd) {
+      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, s);
+      if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
+      e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, depth, alpha,
+                              normal, flow, saved, status, s);
+      if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+    }
+    return FMB_OK;
+  } catch (const std::exception& e) {
+    return fail(FMB_ERR_INVALID_ARG, e.what());
+  } catch (...) {
+    return fail(FMB_ERR_INVALID_ARG, "unknown error");
+  }
+}
+
+fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
+                               const float* means, const float* chol, const float* weights, int n_poses,
+                               const float* poses, int n_views, const fmb_view* h_views, const float* depth,
+                               const float* normal, const float* saved, const float* g_depth,
+                               const float* g_alpha, const float* g_normal, const float* g_flow,
+                               float* grad_means, float* grad_chol, float* grad_weights, float* grad_poses,
+                               void* workspace, size_t workspace_bytes, fmb_stream_t stream) {
+  try {
+    g_err.clear();
+    fmb_status st = validate_scene(params, n_objects, h_obj_offsets, n_views, h_views);
+    if (st != FMB_OK) return st;
+    if (n_poses < 1 || !poses) return fail(FMB_ERR_INVALID_ARG, "poses missing");
+    if (!means || !chol || !weights) return fail(FMB_ERR_INVALID_ARG, "means, chol and weights are required");
+    if (!depth || !saved) return fail(FMB_ERR_INVALID_ARG, "depth and saved (forward outputs) are required");
+    if (params->want_normals && g_normal && !normal)
+      return fail(FMB_ERR_INVALID_ARG, "normal (forward output) is required with g_normal");
+    if (!grad_means || !grad_chol || !grad_weights)
+      return fail(FMB_ERR_INVALID_ARG, "grad_means, grad_chol and grad_weights are required");
+    st = validate_views(n_objects, n_poses, n_views, h_views);
+    if (st != FMB_OK) return st;
+    Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views);
+    st = check_workspace(workspace, workspace_bytes, workspace_needed(params, pl));
+    if (st != FMB_OK) return st;
+
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int* status = static_cast<int*>(workspace);
+    char* base = static_cast<char*>(workspace);
+    float4* records = reinterpret_cast<float4*>(base + kHeaderBytes);
+    float* partials = nullptr;
+    if (params->deterministic)
+      partials = reinterpret_cast<float*>(base + kHeaderBytes + align256(static_cast<size_t>(pl.n_records) * 16 * fmb::kRecFloat4));
+    const fmb::Scene sc{means, chol, weights, poses};
+    const fmb::Consts c = make_consts(params);
+    const bool normals = params->want_normals != 0;
+    fmb::BwdIn in{depth, normals ? normal : nullptr, saved, g_depth, g_alpha, normals ? g_normal : nullptr,
+                  params->n_flow > 0 ? g_flow : nullptr};
+    fmb::BwdOut out{grad_means, grad_chol, grad_weights, grad_poses, partials};
+
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grad_means, 0, sizeof(float) * 3 * pl.n_gauss, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grad_chol, 0, sizeof(float) * 6 * pl.n_gauss, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grad_weights, 0, sizeof(float) * pl.n_gauss, s);
+    if (e == cudaSuccess && grad_poses) e = cudaMemsetAsync(grad_poses, 0, sizeof(float) * 12 * n_poses, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    for (const fmb::Batch& b : pl.bwd) {
+      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, s);
+      if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
+      e = fmb::launch_backward(b, sc, c, records, normals, params->n_flow, pl.ray_tile, pl.bwd_threads, in, out,
+                               status, s);
+      if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+      if (partials) {
+        e = fmb::launch_backward_reduce(b, params->n_flow, pl.n_gauss, n_poses, out, s);
+        if (e != cudaSuccess) return cuda_fail(e, "reduction launch");
+      }
+    }
+    return FMB_OK;
+  } catch (const std::exception& e) {
+    return fail(FMB_ERR_INVALID_ARG, e.what());
+  } catch (...) {
+    return fail(FMB_ERR_INVALID_ARG, "unknown error");
+  }
+}
+
+fmb_status fmb_read_device_status(const void* workspace, int* h_status, fmb_stream_t stream) {
+  if (!workspace || !h_status) return fail(FMB_ERR_INVALID_ARG, "workspace and h_status are required");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(h_status, workspace, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the status word");
+  return FMB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,469 @@
+// fmb_backward.cu -- adjoint of the forward render (the derivative of Eq. 2, 3, 4,
+// 7, 8, 17 and of the Sec. 5 flow) with respect to the means, the precision
+// factors L, the weights lambda and the camera poses.
+//
+// Layout of the work: a CTA takes one view, one tile of rays and one block of
+// Gaussians.  Phase 1 turns each ray's upstream gradients into a 64-byte record in
+// shared memory (the per-pixel part of the adjoint: flow, normal renormalisation,
+// alpha).  Phase 2 is Gaussian-parallel: each thread owns one Gaussian, recomputes
+// its pair terms for every ray of its subgroup from the saved log-normaliser (no
+// per-pair state was stored by the forward) and accumulates the Gaussian's
+// gradient sums in registers.  Phase 3 combines the subgroups, converts the sums
+// into gradients of mu, L, lambda and of the pose, and writes them once per CTA
+// (fp32 atomics, or per-CTA partials that a second kernel adds in a fixed order).
+//
+// Adjoint in the whitened form (a = L^T v, b = L^T (mu - o), t = a.b/a.a,
+// u = t a - b, q = u.u, g = L u, n = g/|g|, what = softmax of e):
+//   ebar  = what (Dbar (t - D) + Nbar . n)            (softmax of Eq. 3)
+//   dbar  = beta1 ebar + Abar e^{-sum delta} delta     (Eq. 7, Eq. 8)
+//   tbar  = Dbar what - (beta2/eta) ebar + (L^T gbar) . a
+//   gbar  = what/|g| (Nbar - (n . Nbar) n)             (Eq. 17 normalisation)
+//   ubar  = L^T gbar - dbar u
+//   y     = ubar - (tbar/a.a) a,  bbar = -y,  abar = t y - (tbar/a.a) u
+// and per Gaussian: Lbar = lower(sum gbar u^T + sum v abar^T + (mu - o) bbar^T),
+// mubar = L sum bbar, lambdabar = sum dbar / lambda.  The term -dbar u . a of tbar
+// is dropped: u . a = 0 exactly at the max-likelihood depth.
+#include "fmb_internal.cuh"
+
+namespace fmb {
+
+constexpr int kBwdMaxThreads = 256;
+constexpr int kAccFloats = 20;  // 19 accumulators (+1 pad) per thread in the reduction
+
+struct BwdAcc {
+  float Sd;               // sum dbar
+  float Y0, Y1, Y2;       // sum y   (= -sum bbar)
+  float G00, G10, G11, G20, G21, G22;  // sum gbar u^T (lower)
+  float M[9];             // sum v abar^T (row-major)
+};
+
+template <bool NORMALS>
+__device__ __forceinline__ void bwd_pair(BwdAcc& A, const GaussRec& gr, const float4& q0, const float4& q1,
+                                         const float4& q2, const float4& q3, const Consts& k) {
+  const float L00 = gr.L[0], L10 = gr.L[1], L11 = gr.L[2], L20 = gr.L[3], L21 = gr.L[4], L22 = gr.L[5];
+  const float v0 = q0.x, v1 = q0.y, v2 = q0.z, lse2 = q0.w;
+  const float Dbar = q1.x, KA = q1.y, C = q1.z;
+  const PairGeom G = pair_geom(gr.L, gr.b, gr.mh, gr.nbl, v0, v1, v2, q2.z, q2.w, q3.x);
+  const float a0 = G.a0, a1 = G.a1, a2 = G.a2, inv = G.inv, t = G.t;
+  const float u0 = G.u0, u1 = G.u1, u2 = G.u2;
+  const float x = fmaf(G.q, k.K3, gr.l2);  // log2(delta)
+  const float what = ex2_approx(fmaf(x, k.beta1, fmaf(t, k.K2, -lse2)));
+  const float delta = ex2_approx(x);
+  float ebar, ub0, ub1, ub2, tbar;
+  float gb0 = 0.f, gb1 = 0.f, gb2 = 0.f;
+  if (NORMALS) {
+    const float Nb0 = q1.w, Nb1 = q2.x, Nb2 = q2.y;
+    const float g0 = L00 * u0;
+    const float g1 = fmaf(L11, u1, L10 * u0);
+    const float g2 = fmaf(L22, u2, fmaf(L21, u1, L20 * u0));
+    const float gg = fmaxf(fmaf(g2, g2, fmaf(g1, g1, g0 * g0)), 1e-30f);
+    const float rs = rsqrt_approx(gg);
+    const float n0 = g0 * rs, n1 = g1 * rs, n2 = g2 * rs;
+    const float nN = fmaf(n2, Nb2, fmaf(n1, Nb1, n0 * Nb0));
+    ebar = what * (fmaf(Dbar, t, -C) + nN);
+    const float sc = what * rs;
+    const float sN = sc * nN;
+    gb0 = fmaf(-sN, n0, sc * Nb0);
+    gb1 = fmaf(-sN, n1, sc * Nb1);
+    gb2 = fmaf(-sN, n2, sc * Nb2);
+    ub0 = fmaf(L20, gb2, fmaf(L10, gb1, L00 * gb0));
+    ub1 = fmaf(L21, gb2, L11 * gb1);
+    ub2 = L22 * gb2;
+    tbar = fmaf(ub2, a2, fmaf(ub1, a1, fmaf(ub0, a0, fmaf(Dbar, what, -k.b2e * ebar))));
+  } else {
+    ebar = what * fmaf(Dbar, t, -C);
+    ub0 = ub1 = ub2 = 0.f;
+    tbar = fmaf(Dbar, what, -k.b2e * ebar);
+  }
+  const float dbar = fmaf(k.beta1, ebar, KA * delta);
+  ub0 = fmaf(-dbar, u0, ub0);
+  ub1 = fmaf(-dbar, u1, ub1);
+  ub2 = fmaf(-dbar, u2, ub2);
+  const float s2 = tbar * inv;
+  const float y0 = fmaf(-s2, a0, ub0);
+  const float y1 = fmaf(-s2, a1, ub1);
+  const float y2 = fmaf(-s2, a2, ub2);
+  const float ab0 = fmaf(t, y0, -s2 * u0);
+  const float ab1 = fmaf(t, y1, -s2 * u1);
+  const float ab2 = fmaf(t, y2, -s2 * u2);
+  A.Sd += dbar;
+  A.Y0 += y0;
+  A.Y1 += y1;
+  A.Y2 += y2;
+  if (NORMALS) {
+    A.G00 = fmaf(gb0, u0, A.G00);
+    A.G10 = fmaf(gb1, u0, A.G10);
+    A.G11 = fmaf(gb1, u1, A.G11);
+    A.G20 = fmaf(gb2, u0, A.G20);
+    A.G21 = fmaf(gb2, u1, A.G21);
+    A.G22 = fmaf(gb2, u2, A.G22);
+  }
+  A.M[0] = fmaf(v0, ab0, A.M[0]);
+  A.M[1] = fmaf(v0, ab1, A.M[1]);
+  A.M[2] = fmaf(v0, ab2, A.M[2]);
+  A.M[3] = fmaf(v1, ab0, A.M[3]);
+  A.M[4] = fmaf(v1, ab1, A.M[4]);
+  A.M[5] = fmaf(v1, ab2, A.M[5]);
+  A.M[6] = fmaf(v2, ab0, A.M[6]);
+  A.M[7] = fmaf(v2, ab1, A.M[7]);
+  A.M[8] = fmaf(v2, ab2, A.M[8]);
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+template <bool NORMALS, int NFLOW>
+__global__ void __launch_bounds__(kBwdMaxThreads) backward_kernel(const __grid_constant__ Batch batch, Scene s,
+                                                                  Consts k, const float4* __restrict__ records,
+                                                                  BwdIn in, BwdOut out, int ray_tile) {
+  extern __shared__ float4 bsm[];
+  __shared__ float pose_red[kBwdMaxThreads / 32][12 * (1 + 2)];
+  constexpr int NPV = 12 * (1 + NFLOW);  // pose values reduced per CTA
+
+  const int vi = find_view(batch, blockIdx.x);
+  const DevView& V = batch.v[vi];
+  const int local = blockIdx.x - V.cta_begin;
+  const int tile = local / V.n_gblocks;
+  const int gb = local - tile * V.n_gblocks;
+  const int P = V.W * V.H;
+  const int pix0 = tile * ray_tile;
+  const int nr = min(ray_tile, P - pix0);
+  const int tid = threadIdx.x;
+  const int T = blockDim.x;
+  const long long off = V.pix_off;
+  const bool want_pose = out.gposes != nullptr;
+  const bool ray_pose = want_pose && gb == 0;  // per-ray pose terms: once per tile
+
+  float R[9], tp[3];
+  load_pose(s.poses, V.pose, R, tp);
+  const float o0 = -fmaf(R[6], tp[2], fmaf(R[3], tp[1], R[0] * tp[0]));
+  const float o1 = -fmaf(R[7], tp[2], fmaf(R[4], tp[1], R[1] * tp[0]));
+  const float o2 = -fmaf(R[8], tp[2], fmaf(R[5], tp[1], R[2] * tp[0]));
+
+  float pose_acc[NPV];
+#pragma unroll
+  for (int i = 0; i < NPV; ++i) pose_acc[i] = 0.f;
+
+  // ---------------- phase 1: per-ray records
+  {
+    float Rj[NFLOW > 0 ? NFLOW : 1][9], tj[NFLOW > 0 ? NFLOW : 1][3];
+    bool has_t[NFLOW > 0 ? NFLOW : 1];
+#pragma unroll
+    for (int j = 0; j < NFLOW; ++j) {
+      const int tg = j == 0 ? V.tgt0 : V.tgt1;
+      has_t[j] = tg >= 0 && in.g_flow != nullptr;
+      if (has_t[j]) load_pose(s.poses, tg, Rj[j], tj[j]);
+    }
+    for (int r = tid; r < nr; r += T) {
+      const int p = pix0 + r;
+      float vc[3], v[3], vl[3], pxy[2];
+      pixel_ray_dd(V, R, p, vc, v, vl, pxy);
+      const float D = in.depth[off + p];
+      const float* sv = in.saved + 3 * off;
+      const float lse2 = sv[p];
+      const float Sd = sv[P + p];
+      const float gD = in.g_depth ? in.g_depth[off + p] : 0.f;
+      const float gA = in.g_alpha ? in.g_alpha[off + p] : 0.f;
+      float pb0 = 0.f, pb1 = 0.f, pb2 = 0.f;
+      if (NFLOW > 0) {
+        const float p0 = fmaf(v[0], D, o0), p1 = fmaf(v[1], D, o1), p2 = fmaf(v[2], D, o2);
+        const float* gf = in.g_flow + 2 * NFLOW * off;
+#pragma unroll
+        for (int j = 0; j < NFLOW; ++j) {
+          if (!has_t[j]) continue;
+          const float X0 = fmaf(Rj[j][2], p2, fmaf(Rj[j][1], p1, fmaf(Rj[j][0], p0, tj[j][0])));
+          const float X1 = fmaf(Rj[j][5], p2, fmaf(Rj[j][4], p1, fmaf(Rj[j][3], p0, tj[j][1])));
+          const float X2 = fmaf(Rj[j][8], p2, fmaf(Rj[j][7], p1, fmaf(Rj[j][6], p0, tj[j][2])));
+          const float iz = 1.0f / X2;
+          const float gu = gf[(2 * j) * P + p], gv = gf[(2 * j + 1) * P + p];
+          const float Xb0 = gu * V.fx * iz;
+          const float Xb1 = gv * V.fy * iz;
+          const float Xb2 = -(Xb0 * X0 + Xb1 * X1) * iz;
+          pb0 += fmaf(Rj[j][6], Xb2, fmaf(Rj[j][3], Xb1, Rj[j][0] * Xb0));
+          pb1 += fmaf(Rj[j][7], Xb2, fmaf(Rj[j][4], Xb1, Rj[j][1] * Xb0));
+          pb2 += fmaf(Rj[j][8], Xb2, fmaf(Rj[j][5], Xb1, Rj[j][2] * Xb0));
+          if (ray_pose) {
+            float* pa = pose_acc + 12 * (1 + j);
+            const float Xb[3] = {Xb0, Xb1, Xb2};
+            const float pp[3] = {p0, p1, p2};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) pa[3 * a + c] = fmaf(Xb[a], pp[c], pa[3 * a + c]);
+              pa[9 + a] += Xb[a];
+            }
+          }
+        }
+      }
+      const float Dbar = fmaf(v[2], pb2, fmaf(v[1], pb1, fmaf(v[0], pb0, gD)));
+      if (ray_pose && NFLOW > 0) {
+        // p = o + v D with o = -R^T t, v = R^T vc:  Rbar += (D vc - t) pbar^T, tbar -= R pbar
+        const float w[3] = {fmaf(D, vc[0], -tp[0]), fmaf(D, vc[1], -tp[1]), fmaf(D, vc[2], -tp[2])};
+        const float pb[3] = {pb0, pb1, pb2};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) pose_acc[3 * a + c] = fmaf(w[a], pb[c], pose_acc[3 * a + c]);
+          pose_acc[9 + a] -= fmaf(R[3 * a + 2], pb2, fmaf(R[3 * a + 1], pb1, R[3 * a] * pb0));
+        }
+      }
+      float Nb0 = 0.f, Nb1 = 0.f, Nb2 = 0.f;
+      if (NORMALS && in.g_normal != nullptr) {
+        const float* nr3 = in.normal + 3 * off;
+        const float* gn3 = in.g_normal + 3 * off;
+        const float nc[3] = {nr3[p], nr3[P + p], nr3[2 * P + p]};
+        const float gn[3] = {gn3[p], gn3[P + p], gn3[2 * P + p]};
+        const float Nn = sv[2 * P + p];
+        // world-frame blended normal and its upstream gradient (R^T applied)
+        float nf[3], nfb[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          nf[c] = fmaf(R[6 + c], nc[2], fmaf(R[3 + c], nc[1], R[c] * nc[0]));
+          nfb[c] = fmaf(R[6 + c], gn[2], fmaf(R[3 + c], gn[1], R[c] * gn[0]));
+        }
+        if (ray_pose) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) pose_acc[3 * a + c] = fmaf(gn[a], nf[c], pose_acc[3 * a + c]);
+        }
+        if (Nn > 0.f) {
+          const float iN = 1.0f / Nn;
+          const float sdot = fmaf(nf[2], nfb[2], fmaf(nf[1], nfb[1], nf[0] * nfb[0]));
+          Nb0 = fmaf(-sdot, nf[0], nfb[0]) * iN;
+          Nb1 = fmaf(-sdot, nf[1], nfb[1]) * iN;
+          Nb2 = fmaf(-sdot, nf[2], nfb[2]) * iN;
+        }
+      }
+      // Nbar is orthogonal to N, so the softmax centring term is Dbar * D alone.
+      const float C = Dbar * D;
+      const float KA = gA * expf(-Sd);
+      float4* rr = bsm + kRayRecFloat4 * r;
+      rr[0] = make_float4(v[0], v[1], v[2], lse2);
+      rr[1] = make_float4(Dbar, KA, C, Nb0);
+      rr[2] = make_float4(Nb1, Nb2, vl[0], vl[1]);
+      rr[3] = make_float4(vl[2], 0.f, 0.f, 0.f);
+    }
+  }
+  __syncthreads();
+
+  // ---------------- phase 2: Gaussian-parallel pair loop
+  const int GB = V.GB, S = V.S;
+  const int gl = tid % GB;
+  const int sg = tid / GB;
+  const int g = gb * GB + gl;
+  const bool active = (sg < S) && (g < V.K);
+  BwdAcc A;
+  A.Sd = A.Y0 = A.Y1 = A.Y2 = 0.f;
+  A.G00 = A.G10 = A.G11 = A.G20 = A.G21 = A.G22 = 0.f;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) A.M[i] = 0.f;
+  GaussRec gr{};
+  if (active) {
+    const float4* rec = records + kRecFloat4 * (V.rec_off + g);
+    gr = unpack_rec(rec[0], rec[1], rec[2], rec[3]);
+#pragma unroll 2
+    for (int r = sg; r < nr; r += S) {
+      const float4* rr = bsm + kRayRecFloat4 * r;
+      bwd_pair<NORMALS>(A, gr, rr[0], rr[1], rr[2], rr[3], k);
+    }
+  }
+  const float* Lr = gr.L;
+  __syncthreads();  // ray records are dead; the shared memory is reused below
+
+  // ---------------- phase 3: combine ray subgroups, finalise per Gaussian
+  float* red = reinterpret_cast<float*>(bsm);
+  if (sg < S) {
+    float* d = red + kAccFloats * tid;
+    d[0] = A.Sd; d[1] = A.Y0; d[2] = A.Y1; d[3] = A.Y2;
+    d[4] = A.G00; d[5] = A.G10; d[6] = A.G11; d[7] = A.G20; d[8] = A.G21; d[9] = A.G22;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[10 + i] = A.M[i];
+  }
+  __syncthreads();
+  float* slot = nullptr;
+  if (out.partials) {
+    slot = out.partials + V.part_off + static_cast<long long>(tile * V.n_gblocks + gb) * V.slot_floats;
+  }
+  if (sg == 0 && gl < GB) {
+    float acc[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) acc[i] = 0.f;
+    for (int s2 = 0; s2 < S; ++s2) {
+      const float* d = red + kAccFloats * (s2 * GB + gl);
+#pragma unroll
+      for (int i = 0; i < 19; ++i) acc[i] += d[i];
+    }
+    float gm[3] = {0, 0, 0}, gL[6] = {0, 0, 0, 0, 0, 0}, glam = 0.f;
+    if (g < V.K) {
+      const long long gg = V.gauss_off + g;
+      const float L00 = Lr[0], L10 = Lr[1], L11 = Lr[2], L20 = Lr[3], L21 = Lr[4], L22 = Lr[5];
+      const float Bb0 = -acc[1], Bb1 = -acc[2], Bb2 = -acc[3];
+      // mubar = L bbar_sum
+      gm[0] = L00 * Bb0;
+      gm[1] = fmaf(L11, Bb1, L10 * Bb0);
+      gm[2] = fmaf(L22, Bb2, fmaf(L21, Bb1, L20 * Bb0));
+      const float m0 = gr.mh[0], m1 = gr.mh[1], m2 = gr.mh[2];
+      const float* M = acc + 10;
+      gL[0] = acc[4] + M[0] + m0 * Bb0;  // (0,0)
+      gL[1] = acc[5] + M[3] + m1 * Bb0;  // (1,0)
+      gL[2] = acc[6] + M[4] + m1 * Bb1;  // (1,1)
+      gL[3] = acc[7] + M[6] + m2 * Bb0;  // (2,0)
+      gL[4] = acc[8] + M[7] + m2 * Bb1;  // (2,1)
+      gL[5] = acc[9] + M[8] + m2 * Bb2;  // (2,2)
+      glam = acc[0] / s.weights[gg];
+      if (want_pose) {
+        // Rbar += R (M L^T) + t mubar^T ; tbar += R mubar
+        float ML[9];
+        const float Lf[9] = {L00, 0.f, 0.f, L10, L11, 0.f, L20, L21, L22};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            ML[3 * a + c] = fmaf(M[3 * a + 2], Lf[3 * c + 2], fmaf(M[3 * a + 1], Lf[3 * c + 1], M[3 * a] * Lf[3 * c]));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            pose_acc[3 * a + c] += fmaf(R[3 * a + 2], ML[6 + c], fmaf(R[3 * a + 1], ML[3 + c], R[3 * a] * ML[c])) +
+                                   tp[a] * gm[c];
+          pose_acc[9 + a] += fmaf(R[3 * a + 2], gm[2], fmaf(R[3 * a + 1], gm[1], R[3 * a] * gm[0]));
+        }
+      }
+      if (slot == nullptr) {
+        atomicAdd(out.gmeans + 3 * gg + 0, gm[0]);
+        atomicAdd(out.gmeans + 3 * gg + 1, gm[1]);
+        atomicAdd(out.gmeans + 3 * gg + 2, gm[2]);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) atomicAdd(out.gchol + 6 * gg + i, gL[i]);
+        atomicAdd(out.gweights + gg, glam);
+      }
+    }
+    if (slot != nullptr) {
+      float* d = slot + 10 * gl;
+      d[0] = gm[0]; d[1] = gm[1]; d[2] = gm[2];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) d[3 + i] = gL[i];
+      d[9] = glam;
+    }
+  }
+
+  // ---------------- phase 4: pose gradient of this CTA
+  if (want_pose) {
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int i = 0; i < NPV; ++i) {
+      const float x = warp_sum(pose_acc[i]);
+      if (lane == 0) pose_red[warp][i] = x;
+    }
+    __syncthreads();
+    if (tid < NPV) {
+      float x = 0.f;
+      const int nw = (T + 31) / 32;
+      for (int w = 0; w < nw; ++w) x += pose_red[w][tid];
+      if (slot != nullptr) {
+        slot[10 * GB + tid] = x;
+      } else {
+        const int j = tid / 12 - 1;
+        const int pidx = j < 0 ? V.pose : (j == 0 ? V.tgt0 : V.tgt1);
+        if (pidx >= 0) atomicAdd(out.gposes + 12 * static_cast<long long>(pidx) + tid % 12, x);
+      }
+    }
+  }
+}
+
+template <bool NORMALS, int NFLOW>
+static cudaError_t launch_bwd_t(const Batch& b, const Scene& s, const Consts& c, const float4* records,
+                                int ray_tile, int threads, const BwdIn& in, const BwdOut& out, cudaStream_t st) {
+  const int smem = max(ray_tile * kRayRecFloat4 * static_cast<int>(sizeof(float4)),
+                       threads * kAccFloats * static_cast<int>(sizeof(float)));
+  auto kern = backward_kernel<NORMALS, NFLOW>;
+  // Dynamic plus static shared memory above the 48 KB default needs the opt-in.
+  if (smem + static_cast<int>(sizeof(float) * (kBwdMaxThreads / 32) * 36) > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<b.total_ctas, threads, smem, st>>>(b, s, c, records, in, out, ray_tile);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
+                            int n_flow, int ray_tile, int threads, const BwdIn& in, const BwdOut& out,
+                            int* status, cudaStream_t st) {
+  (void)status;
+  if (normals) {
+    if (n_flow == 0) return launch_bwd_t<true, 0>(b, s, c, records, ray_tile, threads, in, out, st);
+    if (n_flow == 1) return launch_bwd_t<true, 1>(b, s, c, records, ray_tile, threads, in, out, st);
+    return launch_bwd_t<true, 2>(b, s, c, records, ray_tile, threads, in, out, st);
+  }
+  if (n_flow == 0) return launch_bwd_t<false, 0>(b, s, c, records, ray_tile, threads, in, out, st);
+  if (n_flow == 1) return launch_bwd_t<false, 1>(b, s, c, records, ray_tile, threads, in, out, st);
+  return launch_bwd_t<false, 2>(b, s, c, records, ray_tile, threads, in, out, st);
+}
+
+// ------------------------------------------- deterministic second stage
+// One thread per (Gaussian, component): adds the partials of every (view, tile)
+// slot of this launch that covers the Gaussian, in view then tile order.
+__global__ void reduce_gauss_kernel(const __grid_constant__ Batch batch, const float* __restrict__ partials,
+                                    float* gmeans, float* gchol, float* gweights, long long n_gauss) {
+  const long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (idx >= n_gauss * 10) return;
+  const long long g = idx / 10;
+  const int comp = static_cast<int>(idx - g * 10);
+  float acc = 0.f;
+  bool hit = false;
+  for (int v = 0; v < batch.n_views; ++v) {
+    const DevView& V = batch.v[v];
+    if (g < V.gauss_off || g >= V.gauss_off + V.K) continue;
+    hit = true;
+    const int gi = static_cast<int>(g - V.gauss_off);
+    const int gbk = gi / V.GB, gl = gi - gbk * V.GB;
+    for (int t = 0; t < V.n_tiles; ++t)
+      acc += partials[V.part_off + static_cast<long long>(t * V.n_gblocks + gbk) * V.slot_floats + 10 * gl + comp];
+  }
+  if (!hit) return;
+  if (comp < 3)
+    gmeans[3 * g + comp] += acc;
+  else if (comp < 9)
+    gchol[6 * g + comp - 3] += acc;
+  else
+    gweights[g] += acc;
+}
+
+// One thread per (pose, component).
+__global__ void reduce_pose_kernel(const __grid_constant__ Batch batch, const float* __restrict__ partials,
+                                   float* gposes, int n_poses, int n_flow) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_poses * 12) return;
+  const int p = idx / 12, comp = idx % 12;
+  float acc = 0.f;
+  for (int v = 0; v < batch.n_views; ++v) {
+    const DevView& V = batch.v[v];
+    int part = -1;
+    for (int j = -1; j < n_flow; ++j) {
+      const int pidx = j < 0 ? V.pose : (j == 0 ? V.tgt0 : V.tgt1);
+      if (pidx != p) continue;
+      part = 12 * (j + 1) + comp;
+      const int nslots = V.n_tiles * V.n_gblocks;
+      for (int sl = 0; sl < nslots; ++sl)
+        acc += partials[V.part_off + static_cast<long long>(sl) * V.slot_floats + 10 * V.GB + part];
+    }
+  }
+  gposes[12 * static_cast<long long>(p) + comp] += acc;
+}
+
+cudaError_t launch_backward_reduce(const Batch& b, int n_flow, long long n_gauss, int n_poses, const BwdOut& out,
+                                   cudaStream_t st) {
+  const long long n = n_gauss * 10;
+  reduce_gauss_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(b, out.partials, out.gmeans,
+                                                                              out.gchol, out.gweights, n_gauss);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || out.gposes == nullptr) return e;
+  reduce_pose_kernel<<<(n_poses * 12 + 127) / 128, 128, 0, st>>>(b, out.partials, out.gposes, n_poses, n_flow);
+  return cudaGetLastError();
+}
+
+}  // namespace fmb

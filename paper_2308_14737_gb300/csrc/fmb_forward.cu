@@ -1,0 +1,291 @@
+// fmb_forward.cu -- prologue (per view x Gaussian records) and forward render
+// kernel of the two-parameter Fuzzy Metaballs renderer.
+//
+// Formulation (paper Eq. 2, 3, 4, 7, 8, 17; Sec. 5 flow), whitened per Gaussian:
+// with Sigma^-1 = L L^T, a = L^T v and b = L^T (mu - o), the max-likelihood depth is
+// t = a.b / a.a, the residual in the whitened frame is u = t a - b = L^T (o + v t - mu),
+// q = u.u, d = -q/2 + ln(lambda), delta = e^d, and the weight exponent of Eq. 7 is
+// e = beta1 d - (beta2/eta) t.  The local normal Sigma^-1 (o + v t - mu) of Eq. 17 is
+// g = L u.  Everything is evaluated in the log2 domain so that the exponentials
+// are single ex2 instructions.
+#include "fmb_internal.cuh"
+
+namespace fmb {
+
+constexpr int kFwdThreads = 128;
+constexpr int kChunk = 256;  // records per shared-memory stage (16 KB)
+
+// ------------------------------------------------------------------ prologue
+// One thread per (view, Gaussian): the record of unpack_rec.  The camera centre
+// o = -R^T t and m = mu - o are formed as exact float pairs (error-free
+// transformations), so that the per-pair residual can be evaluated to full fp32
+// accuracy relative to its own size.
+__global__ void __launch_bounds__(128) prologue_kernel(const __grid_constant__ Batch batch, Scene s, Consts k,
+                                                        float4* __restrict__ records) {
+  const DevView& V = batch.v[blockIdx.y];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V.K) return;
+  float R[9], t[3];
+  load_pose(s.poses, V.pose, R, t);
+  const long long g = V.gauss_off + i;
+  const float* L = s.chol + 6 * g;
+  const float L00 = L[0], L10 = L[1], L11 = L[2], L20 = L[3], L21 = L[4], L22 = L[5];
+  float mh[3], ml[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float oh, ol, sh, se;
+    camera_centre_dd(R, t, c, oh, ol);
+    two_sum(s.means[3 * g + c], -oh, sh, se);
+    two_sum(sh, __fsub_rn(se, ol), mh[c], ml[c]);
+  }
+  const float b0 = fmaf(L20, mh[2], fmaf(L10, mh[1], L00 * mh[0]));
+  const float b1 = fmaf(L21, mh[2], L11 * mh[1]);
+  const float b2 = L22 * mh[2];
+  const float nb0 = -fmaf(L20, ml[2], fmaf(L10, ml[1], L00 * ml[0]));
+  const float nb1 = -fmaf(L21, ml[2], L11 * ml[1]);
+  const float nb2 = -(L22 * ml[2]);
+  const float l2 = log2f(s.weights[g]);
+  float4* r = records + kRecFloat4 * (V.rec_off + i);
+  r[0] = make_float4(L00, L10, L11, L20);
+  r[1] = make_float4(L21, L22, b0, b1);
+  r[2] = make_float4(b2, mh[0], mh[1], mh[2]);
+  r[3] = make_float4(nb0, nb1, nb2, l2);
+  (void)k;
+}
+
+cudaError_t launch_prologue(const Batch& b, const Scene& s, const Consts& c, float4* records, int maxK,
+                            cudaStream_t st) {
+  dim3 grid((maxK + 127) / 128, b.n_views);
+  prologue_kernel<<<grid, 128, 0, st>>>(b, s, c, records);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- forward
+struct RayAcc {
+  float v0, v1, v2;     // world ray direction (high part)
+  float vl0, vl1, vl2;  // low part
+  float m;           // running shift of the log2 weights
+  float Sw, Swt, Sd;  // sum w, sum w t, sum delta
+  float N0, N1, N2;   // sum w n
+};
+
+template <bool NORMALS>
+__device__ __forceinline__ void fwd_pair(RayAcc& A, const GaussRec& g, const Consts& k) {
+  const PairGeom G = pair_geom(g.L, g.b, g.mh, g.nbl, A.v0, A.v1, A.v2, A.vl0, A.vl1, A.vl2);
+  const float x = fmaf(G.q, k.K3, g.l2);  // log2(delta)
+  A.Sd += ex2_approx(x);
+  const float e2 = fmaf(x, k.beta1, G.t * k.K2);
+  if (e2 > A.m + kLazyShift) {
+    const float s = ex2_approx(A.m - e2);
+    A.Sw *= s;
+    A.Swt *= s;
+    if (NORMALS) {
+      A.N0 *= s;
+      A.N1 *= s;
+      A.N2 *= s;
+    }
+    A.m = e2;
+  }
+  const float w = ex2_approx(e2 - A.m);
+  A.Sw += w;
+  A.Swt = fmaf(w, G.t, A.Swt);
+  if (NORMALS) {
+    const float L00 = g.L[0], L10 = g.L[1], L11 = g.L[2], L20 = g.L[3], L21 = g.L[4], L22 = g.L[5];
+    const float g0 = L00 * G.u0;
+    const float g1 = fmaf(L11, G.u1, L10 * G.u0);
+    const float g2 = fmaf(L22, G.u2, fmaf(L21, G.u1, L20 * G.u0));
+    const float gg = fmaxf(fmaf(g2, g2, fmaf(g1, g1, g0 * g0)), 1e-30f);
+    const float ws = w * rsqrt_approx(gg);
+    A.N0 = fmaf(ws, g0, A.N0);
+    A.N1 = fmaf(ws, g1, A.N1);
+    A.N2 = fmaf(ws, g2, A.N2);
+  }
+}
+
+struct FwdOut {
+  float* depth;
+  float* alpha;
+  float* normal;
+  float* flow;
+  float* saved;
+};
+
+template <bool NORMALS, int NFLOW, int RPT>
+__global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_constant__ Batch batch, Scene s,
+                                                              Consts k, const float4* __restrict__ records,
+                                                              FwdOut out, int* status) {
+  extern __shared__ float4 fwd_smem[];  // 2 stages x kChunk records
+  __shared__ __align__(8) uint64_t bars[2];
+
+  const int vi = find_view(batch, blockIdx.x);
+  const DevView& V = batch.v[vi];
+  const int tile = blockIdx.x - V.cta_begin;
+  const int P = V.W * V.H;
+  const int tid = threadIdx.x;
+  const int K = V.K;
+
+  float R[9], tp[3];
+  load_pose(s.poses, V.pose, R, tp);
+  const float o0 = -fmaf(R[6], tp[2], fmaf(R[3], tp[1], R[0] * tp[0]));
+  const float o1 = -fmaf(R[7], tp[2], fmaf(R[4], tp[1], R[1] * tp[0]));
+  const float o2 = -fmaf(R[8], tp[2], fmaf(R[5], tp[1], R[2] * tp[0]));
+
+  // Stage the first record chunks while the rays are set up.
+  const float4* src = records + kRecFloat4 * V.rec_off;
+  const int nchunks = (K + kChunk - 1) / kChunk;
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int c = 0; c < 2 && c < nchunks; ++c) {
+      const int n = min(kChunk, K - c * kChunk);
+      mbar_arrive_expect_tx(&bars[c], n * 16u * kRecFloat4);
+      bulk_g2s(fwd_smem + c * kChunk * kRecFloat4, src + c * kChunk * kRecFloat4, n * 16u * kRecFloat4, &bars[c]);
+    }
+  }
+
+  RayAcc A[RPT];
+  int pix[RPT];
+  float pxy[RPT][2];
+  float vc[RPT][3];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    int p = tile * (kFwdThreads * RPT) + r * kFwdThreads + tid;
+    pix[r] = p;
+    p = min(p, P - 1);  // rays past the end compute a valid pixel and store nothing
+    float v[3], vl[3];
+    pixel_ray_dd(V, R, p, vc[r], v, vl, pxy[r]);
+    A[r].v0 = v[0];
+    A[r].v1 = v[1];
+    A[r].v2 = v[2];
+    A[r].vl0 = vl[0];
+    A[r].vl1 = vl[1];
+    A[r].vl2 = vl[2];
+    A[r].m = -INFINITY;
+    A[r].Sw = A[r].Swt = A[r].Sd = 0.f;
+    A[r].N0 = A[r].N1 = A[r].N2 = 0.f;
+  }
+
+  bool failed = false;
+  for (int c = 0; c < nchunks; ++c) {
+    const int stage = c & 1;
+    const bool ok = mbar_wait_bounded(&bars[stage], (c >> 1) & 1, status);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    const int n = min(kChunk, K - c * kChunk);
+    const float4* rec = fwd_smem + stage * kChunk * kRecFloat4;
+#pragma unroll 2
+    for (int i = 0; i < n; ++i) {
+      const GaussRec g = unpack_rec(rec[kRecFloat4 * i + 0], rec[kRecFloat4 * i + 1], rec[kRecFloat4 * i + 2],
+                                    rec[kRecFloat4 * i + 3]);
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) fwd_pair<NORMALS>(A[r], g, k);
+    }
+    __syncthreads();  // every thread is done with this stage before it is refilled
+    if (tid == 0 && c + 2 < nchunks) {
+      const int n2 = min(kChunk, K - (c + 2) * kChunk);
+      mbar_arrive_expect_tx(&bars[stage], n2 * 16u * kRecFloat4);
+      bulk_g2s(fwd_smem + stage * kChunk * kRecFloat4, src + (c + 2) * kChunk * kRecFloat4, n2 * 16u * kRecFloat4,
+               &bars[stage]);
+    }
+  }
+  if (failed) return;
+
+  // Flow targets (uniform over the CTA).
+  float Rj[NFLOW > 0 ? NFLOW : 1][9], tj[NFLOW > 0 ? NFLOW : 1][3];
+  bool has_t[NFLOW > 0 ? NFLOW : 1];
+#pragma unroll
+  for (int j = 0; j < NFLOW; ++j) {
+    const int tg = j == 0 ? V.tgt0 : V.tgt1;
+    has_t[j] = tg >= 0;
+    if (has_t[j]) load_pose(s.poses, tg, Rj[j], tj[j]);
+  }
+
+  const long long off = V.pix_off;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    if (pix[r] >= P) continue;
+    const long long p = pix[r];
+    const float iSw = 1.0f / A[r].Sw;
+    const float D = A[r].Swt * iSw;
+    out.depth[off + p] = D;
+    out.alpha[off + p] = -expm1f(-A[r].Sd);
+    float* sv = out.saved + 3 * off;
+    sv[p] = A[r].m + log2f(A[r].Sw);
+    sv[P + p] = A[r].Sd;
+    if (NORMALS) {
+      const float N0 = A[r].N0 * iSw, N1 = A[r].N1 * iSw, N2 = A[r].N2 * iSw;
+      const float Nn = sqrtf(fmaf(N0, N0, fmaf(N1, N1, N2 * N2)));
+      const float iN = Nn > 0.f ? 1.0f / Nn : 0.f;
+      const float n0 = N0 * iN, n1 = N1 * iN, n2 = N2 * iN;
+      float* nrm = out.normal + 3 * off;
+      nrm[p] = fmaf(R[2], n2, fmaf(R[1], n1, R[0] * n0));
+      nrm[P + p] = fmaf(R[5], n2, fmaf(R[4], n1, R[3] * n0));
+      nrm[2 * P + p] = fmaf(R[8], n2, fmaf(R[7], n1, R[6] * n0));
+      sv[2 * P + p] = Nn;
+    } else {
+      sv[2 * P + p] = 0.f;
+    }
+    if (NFLOW > 0) {
+      const float p0 = fmaf(A[r].v0, D, o0), p1 = fmaf(A[r].v1, D, o1), p2 = fmaf(A[r].v2, D, o2);
+      float* fl = out.flow + 2 * NFLOW * off;
+#pragma unroll
+      for (int j = 0; j < NFLOW; ++j) {
+        float fu = 0.f, fv = 0.f;
+        if (has_t[j]) {
+          const float X0 = fmaf(Rj[j][2], p2, fmaf(Rj[j][1], p1, fmaf(Rj[j][0], p0, tj[j][0])));
+          const float X1 = fmaf(Rj[j][5], p2, fmaf(Rj[j][4], p1, fmaf(Rj[j][3], p0, tj[j][1])));
+          const float X2 = fmaf(Rj[j][8], p2, fmaf(Rj[j][7], p1, fmaf(Rj[j][6], p0, tj[j][2])));
+          const float iz = 1.0f / X2;
+          fu = fmaf(V.fx * X0, iz, V.cx) - pxy[r][0];
+          fv = fmaf(V.fy * X1, iz, V.cy) - pxy[r][1];
+        }
+        fl[(2 * j) * P + p] = fu;
+        fl[(2 * j + 1) * P + p] = fv;
+      }
+    }
+  }
+  (void)vc;
+}
+
+template <bool NORMALS, int NFLOW, int RPT>
+static cudaError_t launch_fwd_t(const Batch& b, const Scene& s, const Consts& c, const float4* records,
+                                const FwdOut& o, int* status, cudaStream_t st) {
+  auto kern = forward_kernel<NORMALS, NFLOW, RPT>;
+  const int smem = 2 * kChunk * kRecFloat4 * static_cast<int>(sizeof(float4));
+  kern<<<b.total_ctas, kFwdThreads, smem, st>>>(b, s, c, records, o, status);
+  return cudaGetLastError();
+}
+
+template <bool NORMALS, int NFLOW>
+static cudaError_t launch_fwd_r(int rpt, const Batch& b, const Scene& s, const Consts& c, const float4* records,
+                                const FwdOut& o, int* status, cudaStream_t st) {
+  switch (rpt) {
+    case 1: return launch_fwd_t<NORMALS, NFLOW, 1>(b, s, c, records, o, status, st);
+    case 2: return launch_fwd_t<NORMALS, NFLOW, 2>(b, s, c, records, o, status, st);
+    default: return launch_fwd_t<NORMALS, NFLOW, 4>(b, s, c, records, o, status, st);
+  }
+}
+
+cudaError_t launch_forward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
+                           int n_flow, int rpt, float* depth, float* alpha, float* normal, float* flow,
+                           float* saved, int* status, cudaStream_t st) {
+  FwdOut o{depth, alpha, normal, flow, saved};
+  if (normals) {
+    if (n_flow == 0) return launch_fwd_r<true, 0>(rpt, b, s, c, records, o, status, st);
+    if (n_flow == 1) return launch_fwd_r<true, 1>(rpt, b, s, c, records, o, status, st);
+    return launch_fwd_r<true, 2>(rpt, b, s, c, records, o, status, st);
+  }
+  if (n_flow == 0) return launch_fwd_r<false, 0>(rpt, b, s, c, records, o, status, st);
+  if (n_flow == 1) return launch_fwd_r<false, 1>(rpt, b, s, c, records, o, status, st);
+  return launch_fwd_r<false, 2>(rpt, b, s, c, records, o, status, st);
+}
+
+int forward_rays_per_cta(int rpt) { return kFwdThreads * rpt; }
+
+}  // namespace fmb

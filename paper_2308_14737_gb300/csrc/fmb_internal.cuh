@@ -1,0 +1,367 @@
+// fmb_internal.cuh -- device-side structures and PTX helpers shared by the CUDA
+// translation units of libfmb (forward, backward, C ABI).  Nothing here is part
+// of the public ABI (include/fmb.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fmb.h"
+
+namespace fmb {
+
+// Views per kernel launch: the view table travels in the kernel's parameter space
+// (a __grid_constant__ struct), so launches need no host->device copy and can be
+// captured in CUDA graphs.  Larger batches are split into several launches.
+constexpr int kMaxBatchViews = 64;
+
+// Per (view, Gaussian) record written by the prologue, 64 bytes (4 x float4):
+//   [L00 L10 L11 L20 | L21 L22 b0 b1 | b2 mh0 mh1 mh2 | nbl0 nbl1 nbl2 l2]
+// m = mu - o (the mean relative to the view's camera centre o) is kept as an
+// unevaluated float pair mh + ml (exact to about 2^-48 relative); b = L^T mh is the
+// whitened mean used for the max-likelihood depth, nbl = -L^T ml the low part of
+// the whitened mean, l2 = log2(lambda).
+constexpr int kRecFloat4 = 4;
+constexpr int kRecBytes = 16 * kRecFloat4;
+
+// Backward per-ray record in shared memory, 64 bytes (4 x float4):
+//   [v0 v1 v2 lse2 | Dbar KA C Nb0 | Nb1 Nb2 vl0 vl1 | vl2 0 0 0]
+// (v + vl is the ray direction as an unevaluated float pair.)
+constexpr int kRayRecFloat4 = 4;
+
+// Device status word values (first int of the workspace).
+constexpr int kDevOk = 0;
+constexpr int kDevTimeout = 1;
+
+// Lazy max-shift threshold of the forward's running log-sum-exp, in log2 units:
+// the shift m is raised only when a new exponent exceeds it by more than this, so
+// partial sums stay below K * 2^64 (far from fp32 overflow) and the shift changes
+// rarely.
+constexpr float kLazyShift = 64.0f;
+
+// Time limit of every device-side wait, in nanoseconds.
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+
+struct DevView {
+  int W, H;
+  float fx, fy, cx, cy;
+  int pose, tgt0, tgt1;
+  int K;           // Gaussians of the view's object
+  int obj;
+  int cta_begin;   // first CTA of this view within the launch
+  int n_tiles;     // ray tiles of this view
+  int n_gblocks;   // backward: Gaussian blocks
+  int GB, S;       // backward: Gaussians per block, ray subgroups per CTA
+  long long gauss_off;  // first Gaussian of the object in means/chol/weights
+  long long rec_off;    // first record (in records) of this view in the workspace
+  long long pix_off;    // first pixel of this view in the planes
+  long long part_off;   // backward deterministic mode: float offset of the view's first slot
+  int slot_floats;      // floats per (tile, gblock) slot in deterministic mode
+  int pad_;
+};
+
+struct Batch {
+  int n_views;
+  int total_ctas;
+  DevView v[kMaxBatchViews];
+};
+
+// Constants folded from the parameters (log2 domain).
+// With x = log2(delta) = K3 q + log2(lambda), the log2 weight of Eq. 7 is
+// e2 = beta1 x + K2 t.
+struct Consts {
+  float K2;   // -(beta2 / eta) * log2(e) : coefficient of t in the log2 weight
+  float K3;   // -0.5 * log2(e)           : coefficient of q in log2(delta)
+  float beta1;
+  float b2e;  // beta2 / eta
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// Makes mbarrier initialisation visible to the async (bulk-copy) proxy.
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// Bulk (non-tensor) copy global -> this CTA's shared memory, completion counted on
+// `bar`.  dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of `bar` to complete, for at most kWaitLimitNs.  On
+// timeout records kDevTimeout in *status and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_timer_ns();
+  for (;;) {
+    for (int i = 0; i < 256; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (global_timer_ns() - t0 > kWaitLimitNs) {
+      atomicExch(status, kDevTimeout);
+      return false;
+    }
+  }
+}
+
+// ------------------------------------------------ error-free transformations
+// (Knuth's TwoSum and the FMA-based TwoProduct; exact as long as the compiler
+// neither reassociates nor contracts them, which nvcc does not do to additions.)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = fmaf(a, b, -p);
+}
+// x = -(R^T t)_k as an unevaluated pair hi + lo (the camera centre o_k).
+__device__ __forceinline__ void camera_centre_dd(const float R[9], const float t[3], int k, float& hi, float& lo) {
+  float p0, e0, p1, e1, p2, e2, s1, f1, s2, f2;
+  two_prod(R[k], t[0], p0, e0);
+  two_prod(R[3 + k], t[1], p1, e1);
+  two_prod(R[6 + k], t[2], p2, e2);
+  two_sum(p0, p1, s1, f1);
+  two_sum(s1, p2, s2, f2);
+  const float l = __fadd_rn(__fadd_rn(__fadd_rn(e0, e1), __fadd_rn(e2, f1)), f2);
+  float h2, l2;
+  two_sum(s2, l, h2, l2);  // renormalise
+  hi = -h2;
+  lo = -l2;
+}
+
+// Geometry of one ray/Gaussian pair (Eq. 2 with the max-likelihood depth):
+//   a = L^T v, t = a.b / a.a, r = v t - m (world frame, with the ray v = v + vl and
+//   m = mh + ml as exact float pairs), u = L^T r projected once more orthogonal to a.
+// The residual is formed from the exact pairs, and the final projection
+// removes the component t's fp32 rounding leaves along a, so u is accurate
+// relative to |u| even when |u| << |b| (rays passing close to a distant
+// Gaussian's centre), where u = t a - b in plain fp32 would lose ~|b|/|u| ulps.
+struct PairGeom {
+  float a0, a1, a2, inv, t, u0, u1, u2, q;
+};
+__device__ __forceinline__ PairGeom pair_geom(const float L[6], const float b[3], const float mh[3],
+                                              const float nbl[3], float v0, float v1, float v2, float vl0,
+                                              float vl1, float vl2) {
+  PairGeom G;
+  const float L00 = L[0], L10 = L[1], L11 = L[2], L20 = L[3], L21 = L[4], L22 = L[5];
+  G.a0 = fmaf(L20, v2, fmaf(L10, v1, L00 * v0));
+  G.a1 = fmaf(L21, v2, L11 * v1);
+  G.a2 = L22 * v2;
+  const float aa = fmaf(G.a2, G.a2, fmaf(G.a1, G.a1, G.a0 * G.a0));
+  const float ab = fmaf(G.a2, b[2], fmaf(G.a1, b[1], G.a0 * b[0]));
+  G.inv = rcp_approx(aa);
+  G.t = ab * G.inv;
+  const float r0 = fmaf(vl0, G.t, fmaf(v0, G.t, -mh[0]));
+  const float r1 = fmaf(vl1, G.t, fmaf(v1, G.t, -mh[1]));
+  const float r2 = fmaf(vl2, G.t, fmaf(v2, G.t, -mh[2]));
+  float u0 = fmaf(L00, r0, fmaf(L10, r1, fmaf(L20, r2, nbl[0])));
+  float u1 = fmaf(L11, r1, fmaf(L21, r2, nbl[1]));
+  float u2 = fmaf(L22, r2, nbl[2]);
+  const float k = fmaf(u2, G.a2, fmaf(u1, G.a1, u0 * G.a0)) * G.inv;
+  G.u0 = fmaf(-k, G.a0, u0);
+  G.u1 = fmaf(-k, G.a1, u1);
+  G.u2 = fmaf(-k, G.a2, u2);
+  G.q = fmaf(G.u2, G.u2, fmaf(G.u1, G.u1, G.u0 * G.u0));
+  return G;
+}
+
+struct GaussRec {
+  float L[6], b[3], mh[3], nbl[3], l2;
+};
+__device__ __forceinline__ GaussRec unpack_rec(const float4& r0, const float4& r1, const float4& r2,
+                                               const float4& r3) {
+  GaussRec g;
+  g.L[0] = r0.x; g.L[1] = r0.y; g.L[2] = r0.z; g.L[3] = r0.w; g.L[4] = r1.x; g.L[5] = r1.y;
+  g.b[0] = r1.z; g.b[1] = r1.w; g.b[2] = r2.x;
+  g.mh[0] = r2.y; g.mh[1] = r2.z; g.mh[2] = r2.w;
+  g.nbl[0] = r3.x; g.nbl[1] = r3.y; g.nbl[2] = r3.z;
+  g.l2 = r3.w;
+  return g;
+}
+
+// Index of the view owning CTA `b` (views sorted by cta_begin).
+__device__ __forceinline__ int find_view(const Batch& batch, int b) {
+  int lo = 0, hi = batch.n_views - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (batch.v[mid].cta_begin <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// Pixel-centre ray of pixel p as an unevaluated float pair: camera-frame unit
+// direction vc (high part), world direction v + vl = R^T (c / |c|) with
+// c = ((x + 1/2 - cx)/fx, (y + 1/2 - cy)/fy, 1), accurate to a few units of 2^-48.
+// Uses error-free transformations and one Newton step for 1/|c| in pair
+// arithmetic.
+__device__ __forceinline__ void pixel_ray_dd(const DevView& V, const float* R, int p, float vc[3], float v[3],
+                                             float vl[3], float pxy[2]) {
+  const int y = p / V.W;
+  const int x = p - y * V.W;
+  pxy[0] = static_cast<float>(x) + 0.5f;
+  pxy[1] = static_cast<float>(y) + 0.5f;
+  float ch[2], cl[2];
+  const float f[2] = {V.fx, V.fy};
+  const float cc[2] = {V.cx, V.cy};
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    float dh, dl;
+    two_sum(pxy[k], -cc[k], dh, dl);
+    ch[k] = __fdiv_rn(dh, f[k]);
+    const float rem = fmaf(-ch[k], f[k], dh);  // exact remainder of the division
+    cl[k] = __fdiv_rn(__fadd_rn(rem, dl), f[k]);
+  }
+  // s = |c|^2 = c0^2 + c1^2 + 1 as sh + sl
+  float p0, e0, p1, e1, s1, f1, sh, f2;
+  two_prod(ch[0], ch[0], p0, e0);
+  two_prod(ch[1], ch[1], p1, e1);
+  two_sum(p0, p1, s1, f1);
+  two_sum(s1, 1.0f, sh, f2);
+  const float sl = __fadd_rn(__fadd_rn(__fadd_rn(e0, e1), __fadd_rn(f1, f2)),
+                             2.0f * fmaf(ch[0], cl[0], __fmul_rn(ch[1], cl[1])));
+  // rn = 1/sqrt(s): one Newton step from rsqrtf, residual 1 - s rn0^2 in pair arithmetic
+  const float rn0 = rsqrtf(sh);
+  float hh, hl, wh, wl;
+  two_prod(rn0, rn0, hh, hl);
+  two_prod(sh, hh, wh, wl);
+  const float resid = __fsub_rn(__fsub_rn(1.0f, wh), __fadd_rn(wl, fmaf(sh, hl, __fmul_rn(sl, hh))));
+  float rnh, rnl;
+  two_sum(rn0, __fmul_rn(0.5f * rn0, resid), rnh, rnl);
+  // vc = c * rn
+  float vch[3], vcl[3];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    two_prod(ch[k], rnh, vch[k], vcl[k]);
+    vcl[k] = __fadd_rn(vcl[k], fmaf(ch[k], rnl, __fmul_rn(cl[k], rnh)));
+  }
+  vch[2] = rnh;
+  vcl[2] = rnl;
+  // v = R^T vc
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    float q0, g0, q1, g1, q2, g2, t1, h1, t2, h2;
+    two_prod(R[j], vch[0], q0, g0);
+    two_prod(R[3 + j], vch[1], q1, g1);
+    two_prod(R[6 + j], vch[2], q2, g2);
+    two_sum(q0, q1, t1, h1);
+    two_sum(t1, q2, t2, h2);
+    float lo = __fadd_rn(__fadd_rn(__fadd_rn(g0, g1), __fadd_rn(g2, h1)), h2);
+    lo = fmaf(R[j], vcl[0], fmaf(R[3 + j], vcl[1], fmaf(R[6 + j], vcl[2], lo)));
+    two_sum(t2, lo, v[j], vl[j]);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) vc[k] = vch[k];
+}
+
+// Pixel-centre ray of pixel p: camera-frame unit direction vc and world direction
+// v = R^T vc (plain fp32).
+__device__ __forceinline__ void pixel_ray(const DevView& V, const float* R, int p, float vc[3], float v[3],
+                                          float pxy[2]) {
+  const int y = p / V.W;
+  const int x = p - y * V.W;
+  pxy[0] = static_cast<float>(x) + 0.5f;
+  pxy[1] = static_cast<float>(y) + 0.5f;
+  const float c0 = (pxy[0] - V.cx) / V.fx;
+  const float c1 = (pxy[1] - V.cy) / V.fy;
+  const float rn = rsqrtf(fmaf(c0, c0, fmaf(c1, c1, 1.0f)));
+  vc[0] = c0 * rn;
+  vc[1] = c1 * rn;
+  vc[2] = rn;
+  v[0] = fmaf(R[6], vc[2], fmaf(R[3], vc[1], R[0] * vc[0]));
+  v[1] = fmaf(R[7], vc[2], fmaf(R[4], vc[1], R[1] * vc[0]));
+  v[2] = fmaf(R[8], vc[2], fmaf(R[5], vc[1], R[2] * vc[0]));
+}
+
+__device__ __forceinline__ void load_pose(const float* poses, int idx, float R[9], float t[3]) {
+  const float* p = poses + 12 * static_cast<long long>(idx);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) R[k] = __ldg(p + k);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) t[k] = __ldg(p + 9 + k);
+}
+
+// ----------------------------------------------------------- launchers (host)
+struct Scene {
+  const float* means;
+  const float* chol;
+  const float* weights;
+  const float* poses;
+};
+
+cudaError_t launch_prologue(const Batch& b, const Scene& s, const Consts& c, float4* records, int maxK,
+                            cudaStream_t st);
+cudaError_t launch_forward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
+                           int n_flow, int rpt, float* depth, float* alpha, float* normal, float* flow,
+                           float* saved, int* status, cudaStream_t st);
+
+struct BwdOut {
+  float* gmeans;
+  float* gchol;
+  float* gweights;
+  float* gposes;  // may be null
+  float* partials;  // deterministic mode: workspace region, else null
+};
+struct BwdIn {
+  const float* depth;
+  const float* normal;
+  const float* saved;
+  const float* g_depth;
+  const float* g_alpha;
+  const float* g_normal;
+  const float* g_flow;
+};
+cudaError_t launch_backward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
+                            int n_flow, int ray_tile, int threads, const BwdIn& in, const BwdOut& out,
+                            int* status, cudaStream_t st);
+cudaError_t launch_backward_reduce(const Batch& b, int n_flow, long long n_gauss, int n_poses,
+                                   const BwdOut& out, cudaStream_t st);
+
+}  // namespace fmb

@@ -1,0 +1,263 @@
+"""Thin Python binding of libfmb (include/fmb.h).
+
+The functions ``fmb_render_forward``, ``fmb_render_backward``,
+``fmb_workspace_bytes`` and ``fmb_read_device_status`` marshal torch tensors (device
+memory) and numpy arrays (host metadata) into the C ABI and do nothing else: every
+step of the render runs in the library's CUDA kernels.  ``Renderer`` and
+``FmbRender`` (a ``torch.autograd.Function``) wrap them for PyTorch users.
+
+There is no fallback: if ``libfmb.so`` has not been built, or no CUDA device is
+present, the calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libfmb.so")
+
+FMB_OK = 0
+STATUS_NAMES = {0: "FMB_OK", 1: "FMB_ERR_INVALID_ARG", 2: "FMB_ERR_CUDA", 3: "FMB_ERR_TIMEOUT",
+                4: "FMB_ERR_WORKSPACE"}
+
+
+class FmbParams(ctypes.Structure):
+    _fields_ = [("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eta", ctypes.c_float),
+                ("variant", ctypes.c_int), ("want_normals", ctypes.c_int), ("n_flow", ctypes.c_int),
+                ("deterministic", ctypes.c_int), ("use_persistent", ctypes.c_int),
+                ("fwd_rays_per_thread", ctypes.c_int), ("fwd_threads", ctypes.c_int),
+                ("bwd_ray_tile", ctypes.c_int), ("bwd_threads", ctypes.c_int)]
+
+
+class FmbView(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_int), ("H", ctypes.c_int), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("object", ctypes.c_int), ("pose", ctypes.c_int),
+                ("flow_target", ctypes.c_int * 2), ("pix_offset", ctypes.c_longlong)]
+
+
+class FmbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libfmb.so (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libfmb.so not found at {path}: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(path)
+    vp, fp, i, sz = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    P = ctypes.POINTER(FmbParams)
+    V = ctypes.POINTER(FmbView)
+    LL = ctypes.POINTER(ctypes.c_longlong)
+    L.fmb_render_forward.argtypes = [P, i, LL, fp, fp, fp, i, fp, i, V, fp, fp, fp, fp, fp, vp, sz, vp]
+    L.fmb_render_forward.restype = ctypes.c_int
+    L.fmb_render_backward.argtypes = [P, i, LL, fp, fp, fp, i, fp, i, V, fp, fp, fp, fp, fp, fp, fp, fp, fp, fp,
+                                      fp, vp, sz, vp]
+    L.fmb_render_backward.restype = ctypes.c_int
+    L.fmb_workspace_bytes.argtypes = [P, i, LL, i, V]
+    L.fmb_workspace_bytes.restype = sz
+    L.fmb_read_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
+    L.fmb_read_device_status.restype = ctypes.c_int
+    L.fmb_last_error.argtypes = []
+    L.fmb_last_error.restype = ctypes.c_char_p
+    L.fmb_version.argtypes = []
+    L.fmb_version.restype = ctypes.c_char_p
+    L.fmb_default_params.argtypes = [P]
+    L.fmb_default_params.restype = None
+    _lib = L
+    return L
+
+
+def default_params(**overrides) -> FmbParams:
+    p = FmbParams()
+    load_library().fmb_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def make_views(views) -> ctypes.Array:
+    """ctypes array of FmbView from a list of dicts (W, H, fx, fy, cx, cy, object, pose,
+    flow_target, pix_offset)."""
+    arr = (FmbView * len(views))()
+    for k, v in enumerate(views):
+        a = arr[k]
+        a.W, a.H = int(v["W"]), int(v["H"])
+        a.fx, a.fy, a.cx, a.cy = float(v["fx"]), float(v["fy"]), float(v["cx"]), float(v["cy"])
+        a.object, a.pose = int(v["object"]), int(v["pose"])
+        ft = tuple(v.get("flow_target", (-1, -1)))
+        a.flow_target[0] = int(ft[0]) if len(ft) > 0 else -1
+        a.flow_target[1] = int(ft[1]) if len(ft) > 1 else -1
+        a.pix_offset = int(v["pix_offset"])
+    return arr
+
+
+def _offsets(obj_offsets):
+    o = np.ascontiguousarray(np.asarray(obj_offsets, dtype=np.int64))
+    return o, o.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if t.numel() and not t.is_cuda:
+            raise ValueError("device tensors expected")
+        if t.numel() and not t.is_contiguous():
+            raise ValueError("contiguous tensors expected")
+        if t.numel() and t.dtype != torch.float32 and t.dtype != torch.uint8:
+            raise ValueError(f"float32 tensors expected, got {t.dtype}")
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(int(t))
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _check(status):
+    if status != FMB_OK:
+        raise FmbError(status, load_library().fmb_last_error().decode())
+
+
+def fmb_workspace_bytes(params: FmbParams, obj_offsets, views) -> int:
+    L = load_library()
+    o, op = _offsets(obj_offsets)
+    va = views if isinstance(views, ctypes.Array) else make_views(views)
+    n = L.fmb_workspace_bytes(ctypes.byref(params), len(o) - 1, op, len(va), va)
+    if n == 0:
+        raise FmbError(1, L.fmb_last_error().decode())
+    return int(n)
+
+
+def fmb_render_forward(params, obj_offsets, means, chol, weights, poses, views, depth, alpha, normal, flow, saved,
+                       workspace, stream=None):
+    L = load_library()
+    o, op = _offsets(obj_offsets)
+    va = views if isinstance(views, ctypes.Array) else make_views(views)
+    _check(L.fmb_render_forward(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol), _ptr(weights),
+                                int(poses.shape[0]), _ptr(poses), len(va), va, _ptr(depth), _ptr(alpha),
+                                _ptr(normal), _ptr(flow), _ptr(saved), _ptr(workspace), workspace.numel(),
+                                _stream(stream)))
+
+
+def fmb_render_backward(params, obj_offsets, means, chol, weights, poses, views, depth, normal, saved, g_depth,
+                        g_alpha, g_normal, g_flow, grad_means, grad_chol, grad_weights, grad_poses, workspace,
+                        stream=None):
+    L = load_library()
+    o, op = _offsets(obj_offsets)
+    va = views if isinstance(views, ctypes.Array) else make_views(views)
+    _check(L.fmb_render_backward(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol), _ptr(weights),
+                                 int(poses.shape[0]), _ptr(poses), len(va), va, _ptr(depth), _ptr(normal),
+                                 _ptr(saved), _ptr(g_depth), _ptr(g_alpha), _ptr(g_normal), _ptr(g_flow),
+                                 _ptr(grad_means), _ptr(grad_chol), _ptr(grad_weights), _ptr(grad_poses),
+                                 _ptr(workspace), workspace.numel(), _stream(stream)))
+
+
+def fmb_read_device_status(workspace, stream=None) -> int:
+    L = load_library()
+    st = ctypes.c_int(0)
+    _check(L.fmb_read_device_status(_ptr(workspace), ctypes.byref(st), _stream(stream)))
+    return int(st.value)
+
+
+def alloc_workspace(nbytes: int, device="cuda") -> torch.Tensor:
+    """uint8 device buffer of at least nbytes, 256-byte aligned (torch's caching
+    allocator returns 512-byte aligned blocks)."""
+    ws = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+    if ws.data_ptr() % 256:
+        raise RuntimeError("workspace not 256-byte aligned")
+    return ws
+
+
+class Renderer:
+    """Fixed batch layout (objects, views, params) with preallocated planes and
+    workspace.  ``forward`` and ``backward`` enqueue the C ABI calls on the current
+    stream; the caller's tensors are read in place."""
+
+    def __init__(self, obj_offsets, views, n_poses, params: FmbParams | None = None, device="cuda"):
+        self.params = params if params is not None else default_params()
+        self.obj_offsets = np.ascontiguousarray(np.asarray(obj_offsets, dtype=np.int64))
+        self.views = [dict(v) for v in views]
+        self.c_views = make_views(self.views)
+        self.n_poses = int(n_poses)
+        self.P = int(sum(v["W"] * v["H"] for v in self.views))
+        self.device = device
+        self.ws = alloc_workspace(fmb_workspace_bytes(self.params, self.obj_offsets, self.c_views), device)
+        nf = self.params.n_flow
+        f32 = dict(dtype=torch.float32, device=device)
+        self.depth = torch.empty(self.P, **f32)
+        self.alpha = torch.empty(self.P, **f32)
+        self.normal = torch.empty(3 * self.P, **f32) if self.params.want_normals else None
+        self.flow = torch.empty(2 * nf * self.P, **f32) if nf > 0 else None
+        self.saved = torch.empty(3 * self.P, **f32)
+
+    def forward(self, means, chol, weights, poses, stream=None):
+        fmb_render_forward(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, self.depth,
+                           self.alpha, self.normal, self.flow, self.saved, self.ws, stream)
+        return dict(depth=self.depth, alpha=self.alpha, normal=self.normal, flow=self.flow, saved=self.saved)
+
+    def backward(self, means, chol, weights, poses, g_depth, g_alpha, g_normal, g_flow, want_pose=True,
+                 out=None, stream=None):
+        G = means.shape[0]
+        if out is None:
+            f32 = dict(dtype=torch.float32, device=means.device)
+            out = dict(means=torch.empty(G, 3, **f32), chol=torch.empty(G, 6, **f32), weights=torch.empty(G, **f32),
+                       poses=torch.empty(poses.shape[0], 12, **f32) if want_pose else None)
+        fmb_render_backward(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, self.depth,
+                            self.normal, self.saved, g_depth, g_alpha, g_normal, g_flow, out["means"], out["chol"],
+                            out["weights"], out["poses"], self.ws, stream)
+        return out
+
+
+class FmbRender(torch.autograd.Function):
+    """Differentiable render: (means, chol, weights, poses) -> (depth, alpha,
+    normal, flow) planes, with the library's adjoint as the backward."""
+
+    @staticmethod
+    def forward(ctx, renderer: Renderer, means, chol, weights, poses):
+        out = renderer.forward(means, chol, weights, poses)
+        ctx.renderer = renderer
+        ctx.save_for_backward(means, chol, weights, poses)
+        # outputs are copies so that the renderer's planes can be reused by the next call
+        res = [out["depth"].clone(), out["alpha"].clone(),
+               out["normal"].clone() if out["normal"] is not None else torch.zeros(0, device=means.device),
+               out["flow"].clone() if out["flow"] is not None else torch.zeros(0, device=means.device)]
+        ctx.saved_planes = (res[0], out["saved"].clone(), res[2] if out["normal"] is not None else None)
+        return tuple(res)
+
+    @staticmethod
+    def backward(ctx, g_depth, g_alpha, g_normal, g_flow):
+        r: Renderer = ctx.renderer
+        means, chol, weights, poses = ctx.saved_tensors
+        depth, saved, normal = ctx.saved_planes
+        r.depth.copy_(depth)
+        r.saved.copy_(saved)
+        if normal is not None:
+            r.normal.copy_(normal)
+        c = lambda g: None if g is None or g.numel() == 0 else g.contiguous()
+        out = r.backward(means, chol, weights, poses, c(g_depth), c(g_alpha), c(g_normal), c(g_flow),
+                         want_pose=poses.requires_grad)
+        return None, out["means"], out["chol"], out["weights"], out["poses"]
+
+
+def render(renderer: Renderer, means, chol, weights, poses):
+    """Differentiable render through ``FmbRender``."""
+    return FmbRender.apply(renderer, means, chol, weights, poses)

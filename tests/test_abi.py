@@ -1,0 +1,150 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+function include/fmb.h declares, its structs match the binding's layout, and host
+validation rejects bad arguments before anything touches a device."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2308_14737_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fmb():
+    from paper_2308_14737_gb300 import build
+
+    build.build()
+    from paper_2308_14737_gb300 import fmb as m
+
+    m.load_library()
+    return m
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "fmb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fmb_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_function(fmb):
+    names = header_functions()
+    assert "fmb_render_forward" in names and "fmb_render_backward" in names
+    lib = fmb.load_library()
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_struct_layouts(fmb):
+    assert ctypes.sizeof(fmb.FmbView) == 48
+    assert fmb.FmbView.pix_offset.offset == 40
+    assert ctypes.sizeof(fmb.FmbParams) == 48
+
+
+def test_default_params_and_version(fmb):
+    p = fmb.default_params()
+    assert abs(p.beta1 - 21.4) < 1e-6 and abs(p.beta2 - 3.14) < 1e-6 and p.eta == 1.0
+    assert p.want_normals == 1 and p.n_flow == 1 and p.deterministic == 0
+    assert b"sm_103a" in fmb.load_library().fmb_version()
+
+
+def test_workspace_bytes(fmb):
+    s = synth.config1(K=10, n_views=3, W=8, H=6)
+    p = fmb.default_params()
+    n = fmb.fmb_workspace_bytes(p, s.obj_offsets, s.views)
+    assert n >= 256 + 48 * 30 and n % 256 == 0
+    p.deterministic = 1
+    assert fmb.fmb_workspace_bytes(p, s.obj_offsets, s.views) > n
+
+
+class _Fake:
+    """Stand-in for a device buffer: only its address is used, and validation
+    fails before any address is dereferenced."""
+
+    def __init__(self, n=1 << 20):
+        self.buf = (ctypes.c_ubyte * 512)()
+        self.n = n
+
+    def numel(self):
+        return self.n
+
+    def data_ptr(self):
+        a = ctypes.addressof(self.buf)
+        return (a + 255) // 256 * 256
+
+
+def _call_fwd(fmb, params, offs, views, n_poses=1, **override):
+    L = fmb.load_library()
+    f = _Fake()
+    va = fmb.make_views(views)
+    o = np.asarray(offs, dtype=np.int64)
+    args = dict(means=f, chol=f, weights=f, poses=f, depth=f, alpha=f, normal=f, flow=f, saved=f, ws=f)
+    args.update(override)
+    P = lambda k: None if args[k] is None else ctypes.c_void_p(args[k].data_ptr())
+    ws = args["ws"]
+    return L.fmb_render_forward(ctypes.byref(params), len(o) - 1, o.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                P("means"), P("chol"), P("weights"), n_poses, P("poses"), len(va), va, P("depth"),
+                                P("alpha"), P("normal"), P("flow"), P("saved"),
+                                None if ws is None else ctypes.c_void_p(ws.data_ptr()), 0 if ws is None else ws.n,
+                                None), L.fmb_last_error().decode()
+
+
+def _view(**kw):
+    v = dict(W=4, H=3, fx=4.0, fy=4.0, cx=2.0, cy=1.5, object=0, pose=0, flow_target=(-1, -1), pix_offset=0)
+    v.update(kw)
+    return v
+
+
+@pytest.mark.parametrize("bad,msg", [
+    (dict(W=0), "W and H"),
+    (dict(fx=0.0), "fx, fy"),
+    (dict(object=1), "object out of range"),
+    (dict(pose=3), "pose out of range"),
+    (dict(flow_target=(5, -1)), "flow_target"),
+    (dict(pix_offset=-1), "pix_offset"),
+])
+def test_forward_rejects_bad_views(fmb, bad, msg):
+    st, err = _call_fwd(fmb, fmb.default_params(), [0, 5], [_view(**bad)])
+    assert st == 1 and msg in err
+
+
+def test_forward_rejects_bad_params(fmb):
+    for k, v, msg in [("eta", 0.0, "eta"), ("variant", 1, "variant"), ("n_flow", 3, "n_flow"),
+                      ("fwd_rays_per_thread", 3, "fwd_rays_per_thread"), ("bwd_threads", 100, "bwd_threads")]:
+        p = fmb.default_params()
+        setattr(p, k, v)
+        st, err = _call_fwd(fmb, p, [0, 5], [_view()])
+        assert st == 1 and msg in err, (k, err)
+
+
+def test_forward_rejects_bad_scene_and_buffers(fmb):
+    p = fmb.default_params()
+    assert _call_fwd(fmb, p, [0, 0], [_view()])[0] == 1  # empty object
+    assert _call_fwd(fmb, p, [1, 5], [_view()])[0] == 1  # offsets must start at 0
+    st, err = _call_fwd(fmb, p, [0, 5], [_view(), _view(pix_offset=6)])
+    assert st == 1 and "overlap" in err
+    st, err = _call_fwd(fmb, p, [0, 5], [_view()], normal=None)
+    assert st == 1 and "normal" in err
+    st, err = _call_fwd(fmb, p, [0, 5], [_view()], flow=None)
+    assert st == 1 and "flow" in err
+    st, err = _call_fwd(fmb, p, [0, 5], [_view()], ws=None)
+    assert st == 4
+    small = _Fake(n=16)
+    st, err = _call_fwd(fmb, p, [0, 5], [_view()], ws=small)
+    assert st == 4 and "too small" in err
+
+
+def test_backward_rejects_missing_outputs(fmb):
+    L = fmb.load_library()
+    f = _Fake()
+    p = fmb.default_params()
+    va = fmb.make_views([_view()])
+    o = np.asarray([0, 5], dtype=np.int64)
+    fp = ctypes.c_void_p(f.data_ptr())
+    st = L.fmb_render_backward(ctypes.byref(p), 1, o.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), fp, fp, fp,
+                               1, fp, 1, va, fp, fp, fp, fp, fp, fp, fp, None, fp, fp, None, fp, 1 << 20, None)
+    assert st == 1 and "grad_means" in L.fmb_last_error().decode()

@@ -1,0 +1,160 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  Small cases are compared on every pixel and every gradient
+entry; the full-size workloads run in the launch configuration the benchmark
+uses and are compared on sampled pixels (forward) and on the exact gradient of
+sampled pixels (backward: the upstream gradients vanish outside the sample, so
+the oracle needs only those pixels)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2308_14737_gb300 import fmb, synth
+
+from gpu_util import (compare_forward, compare_grads, gpu_backward, gpu_forward, masked_upstream,
+                      oracle_backward_sampled, oracle_forward_sampled, pixel_mask_from, sample_pixels)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_14737_gb300 import build
+
+    build.build()
+    oracle.build()
+    fmb.load_library()
+
+
+def _full_check(scene, n_flow, normals=True, deterministic=False, want_pose=True, seed=1, **pk):
+    params = fmb.default_params(n_flow=n_flow, want_normals=int(normals), deterministic=int(deterministic), **pk)
+    gpu, r, dev = gpu_forward(scene, params)
+    ref = oracle.render_scene(scene, n_flow=n_flow)
+    stats = compare_forward(scene, gpu, ref, n_flow, normals)
+    ups = masked_upstream(scene, ref["alpha"], n_flow, seed=seed)
+    if not normals:
+        ups["g_normal"] = np.zeros_like(ups["g_normal"])
+    g = gpu_backward(r, dev, ups, want_pose=want_pose)
+    refg = oracle.backward_scene(scene, ups["g_depth"], ups["g_alpha"], ups["g_normal"] if normals else None,
+                                 ups["g_flow"], n_flow=n_flow)
+    errs = compare_grads(g, refg, keys=("means", "chol", "weights") + (("poses",) if want_pose else ()))
+    return stats, errs, g
+
+
+def test_config0_single_view_64x64_K40():
+    s = synth.config0()
+    _full_check(s, n_flow=0)
+
+
+def test_orbit_small_with_flow_and_pose():
+    s = synth.config1(K=100, n_views=4, W=64, H=48)
+    _full_check(s, n_flow=1)
+
+
+def test_two_flow_slots_with_missing_targets():
+    s = synth.config3(n_views=3, K=37, W=40, H=30)
+    _full_check(s, n_flow=2)
+
+
+def test_normals_off():
+    s = synth.config1(K=30, n_views=2, W=33, H=17)
+    _full_check(s, n_flow=1, normals=False)
+
+
+@pytest.mark.parametrize("rpt", [1, 2, 4])
+def test_rays_per_thread_variants(rpt):
+    s = synth.config1(K=45, n_views=2, W=37, H=29)
+    _full_check(s, n_flow=1, fwd_rays_per_thread=rpt)
+
+
+def test_ragged_objects_and_edge_sizes():
+    """K in {1, 2, 31, 33, 300} (300 crosses the 256-record staging chunk), images
+    from 1x1 to 65x9, several objects and views in one launch."""
+    rng = np.random.default_rng(7)
+    objs, views, poses = [], [], []
+    sizes = [(1, 1), (3, 5), (33, 17), (65, 9), (16, 16)]
+    for o, K in enumerate([1, 2, 31, 33, 300]):
+        objs.append(synth.random_gaussians(rng, K, "cholesky"))
+        for W, H in sizes[o:o + 2]:
+            poses.append(synth.look_at_pose(synth.sphere_positions(rng, 1)[0]))
+            views.append(dict(W=W, H=H, fx=float(max(W, H)), fy=float(max(W, H)), cx=W / 2, cy=H / 2, object=o,
+                              pose=len(poses) - 1, flow_target=(len(poses) % 3, -1)))
+    s = synth.make_scene(objs, views, poses)
+    _full_check(s, n_flow=1)
+
+
+def test_deterministic_mode_is_bitwise_reproducible():
+    s = synth.config1(K=100, n_views=3, W=48, H=40)
+    _, _, g1 = _full_check(s, n_flow=1, deterministic=True)
+    _, _, g2 = _full_check(s, n_flow=1, deterministic=True)
+    for k in g1:
+        assert np.array_equal(g1[k], g2[k]), k
+    _, _, ga = _full_check(s, n_flow=1, deterministic=False)
+    for k in g1:
+        np.testing.assert_allclose(g1[k], ga[k], rtol=0, atol=1e-5 * np.abs(g1[k]).max())
+
+
+@pytest.mark.parametrize("ray_tile,threads", [(32, 64), (128, 128), (512, 256), (1024, 224)])
+def test_backward_tilings(ray_tile, threads):
+    s = synth.config1(K=70, n_views=2, W=50, H=31)
+    _full_check(s, n_flow=1, bwd_ray_tile=ray_tile, bwd_threads=threads)
+
+
+def test_gaussian_blocks_over_128():
+    """K = 300 splits into several Gaussian blocks per CTA; K = 129 leaves a block
+    with one Gaussian."""
+    for K in (129, 300):
+        s = synth.config1(K=K, n_views=2, W=24, H=20)
+        _full_check(s, n_flow=1, deterministic=(K == 300))
+
+
+def test_permutation_invariance():
+    s = synth.config1(K=60, n_views=2, W=40, H=30)
+    p = fmb.default_params(n_flow=1)
+    a, _, _ = gpu_forward(s, p)
+    perm = np.random.default_rng(3).permutation(60)
+    s2 = synth.make_scene([(s.means[perm], s.chol[perm], s.weights[perm])],
+                          [{k: v for k, v in vv.items() if k != "pix_offset"} for vv in s.views], s.poses)
+    b, _, _ = gpu_forward(s2, p)
+    mask = a["alpha"] >= 1e-2
+    assert np.all(np.abs(a["depth"] - b["depth"])[mask] <= 1e-4 + 1e-5 * np.abs(a["depth"][mask]))
+    assert np.all(np.abs(a["alpha"] - b["alpha"]) <= 1e-5)
+
+
+def _sampled_full_size(scene, n_flow, n_per_view, seed=0, deterministic=False):
+    params = fmb.default_params(n_flow=n_flow, deterministic=int(deterministic))
+    gpu, r, dev = gpu_forward(scene, params)
+    pix = sample_pixels(scene, n_per_view, seed)
+    ref = oracle_forward_sampled(scene, pix, n_flow)
+    stats = compare_forward(scene, gpu, None, n_flow, True, pixels_per_view=ref)
+    alpha_ref = np.zeros(scene.n_pixels)
+    for vi, v in enumerate(scene.views):
+        alpha_ref[v["pix_offset"] + ref[vi][0]] = ref[vi][1]["alpha"]
+    ups = masked_upstream(scene, alpha_ref, n_flow, seed=seed + 1, pixel_mask=pixel_mask_from(scene, pix))
+    g = gpu_backward(r, dev, ups)
+    refg = oracle_backward_sampled(scene, ups, pix, n_flow)
+    errs = compare_grads(g, refg)
+    return stats, errs
+
+
+def test_orbit_full_size_16x320x240_K100_sampled():
+    _sampled_full_size(synth.config1(), n_flow=1, n_per_view=400)
+
+
+def test_large_K4096_8x1024x768_sampled():
+    _sampled_full_size(synth.config4(), n_flow=1, n_per_view=48)
+
+
+def test_ragged_batch_64_objects_sampled():
+    _sampled_full_size(synth.config2(), n_flow=0, n_per_view=64, deterministic=True)
+
+
+def test_device_status_is_clear_and_outputs_finite():
+    s = synth.config1(K=20, n_views=2, W=16, H=12)
+    gpu, r, _ = gpu_forward(s, fmb.default_params())
+    for k in ("depth", "alpha", "normal", "flow", "saved"):
+        assert np.all(np.isfinite(gpu[k])), k
+    assert fmb.fmb_read_device_status(r.ws) == 0
