@@ -5,7 +5,8 @@
  *
  * Model (paper Sec. 3.1-3.2, Sec. 5, Sec. 6):
  *   Gaussian i: mean mu_i, precision Sigma_i^-1 = L_i L_i^T with L_i lower
- *   triangular (the "inverse root precision" of Sec. 3.1), weight lambda_i > 0.
+ *   triangular (Sec. 3.1 parameterises the shape by an inverse square root of the
+ *   precision), weight lambda_i > 0.
  *   For the ray v (unit length, world frame) from the camera centre o of a pixel:
  *     t_i     = (mu_i - o)^T Sigma_i^-1 v / (v^T Sigma_i^-1 v)   (max-likelihood
  *               depth along the ray, next to Eq. 2)
@@ -142,6 +143,29 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
                                const float* g_alpha, const float* g_normal, const float* g_flow,
                                float* grad_means, float* grad_chol, float* grad_weights, float* grad_poses,
                                void* workspace, size_t workspace_bytes, fmb_stream_t stream);
+
+/*
+ * fmb_render_forward without a workspace argument, for callers that cannot
+ * allocate device memory (a plugin whose host application owns all device memory
+ * and exposes no allocator, or a real-time path where cudaMalloc's implicit device
+ * synchronisation is not acceptable).  The paper has no counterpart: this is a
+ * deployment variant of the same forward render, with the same arguments,
+ * layouts and results minus `workspace`/`workspace_bytes`.
+ *
+ * Its scratch is one fixed 1 MiB array in the library (held on every device that
+ * loads the library until the process exits): a batch needs 256 + 64 x (sum over
+ * views of the view's Gaussian count) bytes, and a larger batch is rejected with
+ * FMB_ERR_WORKSPACE.  Nothing is allocated.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the array: calls whose GPU work overlaps
+ * (different streams or host threads) race on it.  Errors are reported as for
+ * fmb_render_forward; the device status word lives in the fixed array and has no
+ * reader.
+ */
+fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
+                                      const float* means, const float* chol, const float* weights, int n_poses,
+                                      const float* poses, int n_views, const fmb_view* h_views, float* depth,
+                                      float* alpha, float* normal, float* flow, float* saved, fmb_stream_t stream);
 
 /* Workspace bytes needed by fmb_render_forward and fmb_render_backward for this
  * batch (the larger of the two).  Returns 0 on invalid arguments (see

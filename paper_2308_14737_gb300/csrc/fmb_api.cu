@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <exception>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -387,3 +388,98 @@ fmb_status fmb_read_device_status(const void* workspace, int* h_status, fmb_stre
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------
+// Forward render without a caller-provided workspace.
+//
+// Some callers cannot allocate device memory: a plugin whose host application
+// owns all device memory and exposes no allocator, or code on a real-time path
+// where cudaMalloc's implicit device synchronisation is not acceptable.  For them
+// the forward pass's scratch (status word and per-(view, Gaussian) records) lives
+// in the fixed array below, which every device that loads this library holds
+// until the process exits.  No cudaMalloc, cudaFree or allocating library routine
+// is called.
+//
+// The array's name is only a host-side stand-in: the device address is obtained
+// once per device with cudaGetSymbolAddress, during that device's first call
+// (so the first call on a device should come before any stream capture).  All
+// calls share the array and it keeps the last call's contents; the status word is
+// cleared by every call and the records are rewritten, but calls whose work
+// overlaps on the GPU (different streams, or different host threads) race on it.
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(1) << 20;  // 1 MiB
+constexpr int kStaticMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_fmb_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void* g_static_ptr[kStaticMaxDevices] = {nullptr};
+
+fmb_status static_scratch_address(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kStaticMaxDevices) return fail(FMB_ERR_CUDA, "device index out of range for static scratch");
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_fmb_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch");
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return FMB_OK;
+}
+
+}  // namespace
+
+extern "C" fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n_objects,
+                                                 const long long* h_obj_offsets, const float* means,
+                                                 const float* chol, const float* weights, int n_poses,
+                                                 const float* poses, int n_views, const fmb_view* h_views,
+                                                 float* depth, float* alpha, float* normal, float* flow,
+                                                 float* saved, fmb_stream_t stream) {
+  try {
+    g_err.clear();
+    fmb_status st = validate_scene(params, n_objects, h_obj_offsets, n_views, h_views);
+    if (st != FMB_OK) return st;
+    if (n_poses < 1 || !poses) return fail(FMB_ERR_INVALID_ARG, "poses missing");
+    if (!means || !chol || !weights) return fail(FMB_ERR_INVALID_ARG, "means, chol and weights are required");
+    if (!depth || !alpha || !saved) return fail(FMB_ERR_INVALID_ARG, "depth, alpha and saved are required");
+    if (params->want_normals && !normal) return fail(FMB_ERR_INVALID_ARG, "normal is NULL but want_normals is set");
+    if (params->n_flow > 0 && !flow) return fail(FMB_ERR_INVALID_ARG, "flow is NULL but n_flow > 0");
+    st = validate_views(n_objects, n_poses, n_views, h_views);
+    if (st != FMB_OK) return st;
+    Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views);
+    const size_t need = kHeaderBytes + align256(static_cast<size_t>(pl.n_records) * 16 * fmb::kRecFloat4);
+    if (need > kStaticScratchBytes)
+      return fail(FMB_ERR_WORKSPACE, "batch needs " + std::to_string(need) + " bytes of scratch; the static scratch " +
+                                         "holds " + std::to_string(kStaticScratchBytes) +
+                                         " (64 bytes per view and Gaussian, plus 256)");
+    void* ws = nullptr;
+    st = static_scratch_address(&ws);
+    if (st != FMB_OK) return st;
+
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int* status = static_cast<int*>(ws);
+    float4* records = reinterpret_cast<float4*>(static_cast<char*>(ws) + kHeaderBytes);
+    const fmb::Scene sc{means, chol, weights, poses};
+    const fmb::Consts c = make_consts(params);
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    for (const fmb::Batch& b : pl.fwd) {
+      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, s);
+      if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
+      e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, depth, alpha,
+                              normal, flow, saved, status, s);
+      if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+    }
+    return FMB_OK;
+  } catch (const std::exception& e) {
+    return fail(FMB_ERR_INVALID_ARG, e.what());
+  } catch (...) {
+    return fail(FMB_ERR_INVALID_ARG, "unknown error");
+  }
+}

@@ -67,6 +67,8 @@ def load_library(path: str = LIB_PATH):
     L.fmb_render_backward.argtypes = [P, i, LL, fp, fp, fp, i, fp, i, V, fp, fp, fp, fp, fp, fp, fp, fp, fp, fp,
                                       fp, vp, sz, vp]
     L.fmb_render_backward.restype = ctypes.c_int
+    L.fmb_render_forward_noalloc.argtypes = [P, i, LL, fp, fp, fp, i, fp, i, V, fp, fp, fp, fp, fp, vp]
+    L.fmb_render_forward_noalloc.restype = ctypes.c_int
     L.fmb_workspace_bytes.argtypes = [P, i, LL, i, V]
     L.fmb_workspace_bytes.restype = sz
     L.fmb_read_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
@@ -156,6 +158,18 @@ def fmb_render_forward(params, obj_offsets, means, chol, weights, poses, views, 
                                 int(poses.shape[0]), _ptr(poses), len(va), va, _ptr(depth), _ptr(alpha),
                                 _ptr(normal), _ptr(flow), _ptr(saved), _ptr(workspace), workspace.numel(),
                                 _stream(stream)))
+
+
+def fmb_render_forward_noalloc(params, obj_offsets, means, chol, weights, poses, views, depth, alpha, normal, flow,
+                               saved, stream=None):
+    """fmb_render_forward with the library's fixed scratch instead of a workspace
+    (for callers that cannot allocate device memory)."""
+    L = load_library()
+    o, op = _offsets(obj_offsets)
+    va = views if isinstance(views, ctypes.Array) else make_views(views)
+    _check(L.fmb_render_forward_noalloc(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol),
+                                        _ptr(weights), int(poses.shape[0]), _ptr(poses), len(va), va, _ptr(depth),
+                                        _ptr(alpha), _ptr(normal), _ptr(flow), _ptr(saved), _stream(stream)))
 
 
 def fmb_render_backward(params, obj_offsets, means, chol, weights, poses, views, depth, normal, saved, g_depth,
