@@ -178,6 +178,15 @@ size_t fmb_workspace_bytes(const fmb_params* params, int n_objects, const long l
  * outputs of that call are invalid).  The word is cleared by every render call. */
 fmb_status fmb_read_device_status(const void* workspace, int* h_status, fmb_stream_t stream);
 
+/* ALU throughput probe (a measurement utility, not part of the paper's method):
+ * launches `blocks` CTAs of 256 threads that each run 8 independent chains of
+ * `iters` operations of one kind -- 0: FP32 FMA, 1: packed FP32x2 FMA (two FMAs per
+ * instruction), 2: ex2.approx, 3: rcp.approx, 4: rsqrt.approx -- and store one float
+ * per thread into `out` (device, >= blocks * 256 floats).  Time it with events on
+ * `stream` to get the GPU's FP32-pipe and SFU rates.  Returns FMB_ERR_INVALID_ARG
+ * on bad arguments, FMB_ERR_CUDA if the launch fails. */
+fmb_status fmb_probe_alu(int kind, int blocks, int iters, float* out, fmb_stream_t stream);
+
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char* fmb_last_error(void);
 

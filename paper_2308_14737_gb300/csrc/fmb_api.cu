@@ -26,8 +26,7 @@ namespace {
 thread_local std::string g_err;
 
 constexpr size_t kHeaderBytes = 256;
-constexpr int kDefaultRpt = 2;
-constexpr int kDefaultRayTile = 256;
+constexpr int kDefaultRpt = 4;
 constexpr int kMaxGaussPerCta = 128;
 constexpr long long kMaxK = 1 << 22;
 
@@ -54,8 +53,8 @@ BwdBlocking bwd_blocking(int K, int T) {
 // Threads per backward CTA: the candidate that wastes the fewest thread slots over
 // the batch, weighted by each view's pairs.
 int choose_bwd_threads(const fmb_view* views, int n_views, const long long* offs) {
-  const int cand[] = {128, 160, 192, 224, 256};
-  int best = 256;
+  const int cand[] = {128, 160, 192, 224};
+  int best = 224;
   double best_eff = -1.0;
   for (int T : cand) {
     double num = 0.0, den = 0.0;
@@ -84,8 +83,8 @@ struct Plan {
   long long n_gauss = 0;
   int maxK = 0;
   int rpt = kDefaultRpt;
-  int ray_tile = kDefaultRayTile;
-  int bwd_threads = 256;
+  int ray_tile = 448;
+  int bwd_threads = 224;
 };
 
 fmb_status validate_scene(const fmb_params* p, int n_objects, const long long* offs, int n_views,
@@ -102,8 +101,8 @@ fmb_status validate_scene(const fmb_params* p, int n_objects, const long long* o
   if (p->fwd_threads != 0 && p->fwd_threads != 128) return fail(FMB_ERR_INVALID_ARG, "fwd_threads must be 0 or 128");
   if (p->bwd_ray_tile < 0 || p->bwd_ray_tile > 1024 || (p->bwd_ray_tile % 32) != 0)
     return fail(FMB_ERR_INVALID_ARG, "bwd_ray_tile must be a multiple of 32 in [32, 1024] (0 = default)");
-  if (p->bwd_threads != 0 && (p->bwd_threads < 32 || p->bwd_threads > 256 || (p->bwd_threads % 32) != 0))
-    return fail(FMB_ERR_INVALID_ARG, "bwd_threads must be a multiple of 32 in [32, 256] (0 = default)");
+  if (p->bwd_threads != 0 && (p->bwd_threads < 32 || p->bwd_threads > 224 || (p->bwd_threads % 32) != 0))
+    return fail(FMB_ERR_INVALID_ARG, "bwd_threads must be a multiple of 32 in [32, 224] (0 = default)");
   if (n_objects < 1) return fail(FMB_ERR_INVALID_ARG, "n_objects must be >= 1");
   if (!offs) return fail(FMB_ERR_INVALID_ARG, "h_obj_offsets is NULL");
   if (offs[0] != 0) return fail(FMB_ERR_INVALID_ARG, "h_obj_offsets[0] must be 0");
@@ -145,8 +144,9 @@ fmb_status validate_views(int n_objects, int n_poses, int n_views, const fmb_vie
 Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_views, const fmb_view* views) {
   Plan pl;
   pl.rpt = p->fwd_rays_per_thread > 0 ? p->fwd_rays_per_thread : kDefaultRpt;
-  pl.ray_tile = p->bwd_ray_tile > 0 ? p->bwd_ray_tile : kDefaultRayTile;
   pl.bwd_threads = p->bwd_threads > 0 ? p->bwd_threads : choose_bwd_threads(views, n_views, offs);
+  // default ray tile: two rays per thread in the per-ray phase, so that phase is balanced
+  pl.ray_tile = p->bwd_ray_tile > 0 ? p->bwd_ray_tile : 2 * pl.bwd_threads;
   pl.n_gauss = offs[n_objects];
   const int rays_fwd = fmb::forward_rays_per_cta(pl.rpt);
   const int n_flow = p->n_flow;
@@ -298,13 +298,13 @@ fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const lon
     float4* records = reinterpret_cast<float4*>(static_cast<char*>(workspace) + kHeaderBytes);
     const fmb::Scene sc{means, chol, weights, poses};
     const fmb::Consts c = make_consts(params);
-    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    for (const fmb::Batch& b : pl.fwd) {
-      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, s);
+    cudaError_t e = cudaSuccess;
+    for (size_t bi = 0; bi < pl.fwd.size(); ++bi) {
+      const fmb::Batch& b = pl.fwd[bi];
+      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, bi == 0 ? status : nullptr, s);
       if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
-      e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, depth, alpha,
-                              normal, flow, saved, status, s);
+      e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, pl.maxK, depth,
+                              alpha, normal, flow, saved, status, s);
       if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     }
     return FMB_OK;
@@ -353,14 +353,21 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
                   params->n_flow > 0 ? g_flow : nullptr};
     fmb::BwdOut out{grad_means, grad_chol, grad_weights, grad_poses, partials};
 
-    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(grad_means, 0, sizeof(float) * 3 * pl.n_gauss, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(grad_chol, 0, sizeof(float) * 6 * pl.n_gauss, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(grad_weights, 0, sizeof(float) * pl.n_gauss, s);
-    if (e == cudaSuccess && grad_poses) e = cudaMemsetAsync(grad_poses, 0, sizeof(float) * 12 * n_poses, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    fmb::ZeroJob zj{};
+    zj.ptr[0] = reinterpret_cast<float*>(status);
+    zj.n[0] = 1;
+    zj.ptr[1] = grad_means;
+    zj.n[1] = 3 * pl.n_gauss;
+    zj.ptr[2] = grad_chol;
+    zj.n[2] = 6 * pl.n_gauss;
+    zj.ptr[3] = grad_weights;
+    zj.n[3] = pl.n_gauss;
+    zj.ptr[4] = grad_poses;
+    zj.n[4] = grad_poses ? 12ll * n_poses : 0;
+    cudaError_t e = fmb::launch_zero(zj, s);
+    if (e != cudaSuccess) return cuda_fail(e, "zeroing launch");
     for (const fmb::Batch& b : pl.bwd) {
-      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, s);
+      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, s);
       if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
       e = fmb::launch_backward(b, sc, c, records, normals, params->n_flow, pl.ray_tile, pl.bwd_threads, in, out,
                                status, s);
@@ -467,13 +474,13 @@ extern "C" fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n
     float4* records = reinterpret_cast<float4*>(static_cast<char*>(ws) + kHeaderBytes);
     const fmb::Scene sc{means, chol, weights, poses};
     const fmb::Consts c = make_consts(params);
-    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    for (const fmb::Batch& b : pl.fwd) {
-      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, s);
+    cudaError_t e = cudaSuccess;
+    for (size_t bi = 0; bi < pl.fwd.size(); ++bi) {
+      const fmb::Batch& b = pl.fwd[bi];
+      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, bi == 0 ? status : nullptr, s);
       if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
-      e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, depth, alpha,
-                              normal, flow, saved, status, s);
+      e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, pl.maxK, depth,
+                              alpha, normal, flow, saved, status, s);
       if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     }
     return FMB_OK;

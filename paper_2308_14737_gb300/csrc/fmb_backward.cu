@@ -27,7 +27,11 @@
 
 namespace fmb {
 
-constexpr int kBwdMaxThreads = 256;
+constexpr int kBwdMaxThreads = 224;
+#ifndef FMB_BWD_MIN_BLOCKS
+#define FMB_BWD_MIN_BLOCKS 3
+#endif
+constexpr int kBwdMinBlocks = FMB_BWD_MIN_BLOCKS;  // resident CTAs per SM the register budget targets
 constexpr int kAccFloats = 20;  // 19 accumulators (+1 pad) per thread in the reduction
 
 struct BwdAcc {
@@ -116,12 +120,13 @@ __device__ __forceinline__ float warp_sum(float x) {
 }
 
 template <bool NORMALS, int NFLOW>
-__global__ void __launch_bounds__(kBwdMaxThreads) backward_kernel(const __grid_constant__ Batch batch, Scene s,
-                                                                  Consts k, const float4* __restrict__ records,
-                                                                  BwdIn in, BwdOut out, int ray_tile) {
+__global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
+    backward_kernel(const __grid_constant__ Batch batch, Scene s, Consts k, const float4* __restrict__ records,
+                    BwdIn in, BwdOut out, int ray_tile) {
   extern __shared__ float4 bsm[];
-  __shared__ float pose_red[kBwdMaxThreads / 32][12 * (1 + 2)];
   constexpr int NPV = 12 * (1 + NFLOW);  // pose values reduced per CTA
+  __shared__ float pose_ray[kBwdMaxThreads / 32][NPV];  // per-warp sums of the per-ray pose terms
+  __shared__ float pose_gau[kBwdMaxThreads / 32][12];   // per-warp sums of the per-Gaussian pose terms
 
   const int vi = find_view(batch, blockIdx.x);
   const DevView& V = batch.v[vi];
@@ -133,22 +138,21 @@ __global__ void __launch_bounds__(kBwdMaxThreads) backward_kernel(const __grid_c
   const int nr = min(ray_tile, P - pix0);
   const int tid = threadIdx.x;
   const int T = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
   const long long off = V.pix_off;
   const bool want_pose = out.gposes != nullptr;
   const bool ray_pose = want_pose && gb == 0;  // per-ray pose terms: once per tile
 
-  float R[9], tp[3];
-  load_pose(s.poses, V.pose, R, tp);
-  const float o0 = -fmaf(R[6], tp[2], fmaf(R[3], tp[1], R[0] * tp[0]));
-  const float o1 = -fmaf(R[7], tp[2], fmaf(R[4], tp[1], R[1] * tp[0]));
-  const float o2 = -fmaf(R[8], tp[2], fmaf(R[5], tp[1], R[2] * tp[0]));
-
-  float pose_acc[NPV];
-#pragma unroll
-  for (int i = 0; i < NPV; ++i) pose_acc[i] = 0.f;
-
-  // ---------------- phase 1: per-ray records
+  // ---------------- phase 1: per-ray records (and the per-ray pose terms)
   {
+    float R[9], tp[3];
+    load_pose(s.poses, V.pose, R, tp);
+    const float o0 = -fmaf(R[6], tp[2], fmaf(R[3], tp[1], R[0] * tp[0]));
+    const float o1 = -fmaf(R[7], tp[2], fmaf(R[4], tp[1], R[1] * tp[0]));
+    const float o2 = -fmaf(R[8], tp[2], fmaf(R[5], tp[1], R[2] * tp[0]));
+    float pose_acc[NPV];
+#pragma unroll
+    for (int i = 0; i < NPV; ++i) pose_acc[i] = 0.f;
     float Rj[NFLOW > 0 ? NFLOW : 1][9], tj[NFLOW > 0 ? NFLOW : 1][3];
     bool has_t[NFLOW > 0 ? NFLOW : 1];
 #pragma unroll
@@ -247,6 +251,14 @@ __global__ void __launch_bounds__(kBwdMaxThreads) backward_kernel(const __grid_c
       rr[2] = make_float4(Nb1, Nb2, vl[0], vl[1]);
       rr[3] = make_float4(vl[2], 0.f, 0.f, 0.f);
     }
+    // Reduce the per-ray pose terms now, so that they hold no registers in the loop.
+    if (want_pose) {
+#pragma unroll
+      for (int i = 0; i < NPV; ++i) {
+        const float x = warp_sum(pose_acc[i]);
+        if (lane == 0) pose_ray[warp][i] = x;
+      }
+    }
   }
   __syncthreads();
 
@@ -271,7 +283,6 @@ __global__ void __launch_bounds__(kBwdMaxThreads) backward_kernel(const __grid_c
       bwd_pair<NORMALS>(A, gr, rr[0], rr[1], rr[2], rr[3], k);
     }
   }
-  const float* Lr = gr.L;
   __syncthreads();  // ray records are dead; the shared memory is reused below
 
   // ---------------- phase 3: combine ray subgroups, finalise per Gaussian
@@ -288,6 +299,9 @@ __global__ void __launch_bounds__(kBwdMaxThreads) backward_kernel(const __grid_c
   if (out.partials) {
     slot = out.partials + V.part_off + static_cast<long long>(tile * V.n_gblocks + gb) * V.slot_floats;
   }
+  float pose_g[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) pose_g[i] = 0.f;
   if (sg == 0 && gl < GB) {
     float acc[19];
 #pragma unroll
@@ -300,7 +314,7 @@ __global__ void __launch_bounds__(kBwdMaxThreads) backward_kernel(const __grid_c
     float gm[3] = {0, 0, 0}, gL[6] = {0, 0, 0, 0, 0, 0}, glam = 0.f;
     if (g < V.K) {
       const long long gg = V.gauss_off + g;
-      const float L00 = Lr[0], L10 = Lr[1], L11 = Lr[2], L20 = Lr[3], L21 = Lr[4], L22 = Lr[5];
+      const float L00 = gr.L[0], L10 = gr.L[1], L11 = gr.L[2], L20 = gr.L[3], L21 = gr.L[4], L22 = gr.L[5];
       const float Bb0 = -acc[1], Bb1 = -acc[2], Bb2 = -acc[3];
       // mubar = L bbar_sum
       gm[0] = L00 * Bb0;
@@ -317,6 +331,8 @@ __global__ void __launch_bounds__(kBwdMaxThreads) backward_kernel(const __grid_c
       glam = acc[0] / s.weights[gg];
       if (want_pose) {
         // Rbar += R (M L^T) + t mubar^T ; tbar += R mubar
+        float R[9], tp[3];
+        load_pose(s.poses, V.pose, R, tp);
         float ML[9];
         const float Lf[9] = {L00, 0.f, 0.f, L10, L11, 0.f, L20, L21, L22};
 #pragma unroll
@@ -328,9 +344,9 @@ __global__ void __launch_bounds__(kBwdMaxThreads) backward_kernel(const __grid_c
         for (int a = 0; a < 3; ++a) {
 #pragma unroll
           for (int c = 0; c < 3; ++c)
-            pose_acc[3 * a + c] += fmaf(R[3 * a + 2], ML[6 + c], fmaf(R[3 * a + 1], ML[3 + c], R[3 * a] * ML[c])) +
-                                   tp[a] * gm[c];
-          pose_acc[9 + a] += fmaf(R[3 * a + 2], gm[2], fmaf(R[3 * a + 1], gm[1], R[3 * a] * gm[0]));
+            pose_g[3 * a + c] = fmaf(R[3 * a + 2], ML[6 + c], fmaf(R[3 * a + 1], ML[3 + c], R[3 * a] * ML[c])) +
+                                tp[a] * gm[c];
+          pose_g[9 + a] = fmaf(R[3 * a + 2], gm[2], fmaf(R[3 * a + 1], gm[1], R[3 * a] * gm[0]));
         }
       }
       if (slot == nullptr) {
@@ -353,17 +369,16 @@ __global__ void __launch_bounds__(kBwdMaxThreads) backward_kernel(const __grid_c
 
   // ---------------- phase 4: pose gradient of this CTA
   if (want_pose) {
-    const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
-    for (int i = 0; i < NPV; ++i) {
-      const float x = warp_sum(pose_acc[i]);
-      if (lane == 0) pose_red[warp][i] = x;
+    for (int i = 0; i < 12; ++i) {
+      const float x = warp_sum(pose_g[i]);
+      if (lane == 0) pose_gau[warp][i] = x;
     }
     __syncthreads();
     if (tid < NPV) {
       float x = 0.f;
       const int nw = (T + 31) / 32;
-      for (int w = 0; w < nw; ++w) x += pose_red[w][tid];
+      for (int w = 0; w < nw; ++w) x += pose_ray[w][tid] + (tid < 12 ? pose_gau[w][tid] : 0.f);
       if (slot != nullptr) {
         slot[10 * GB + tid] = x;
       } else {
@@ -382,7 +397,7 @@ static cudaError_t launch_bwd_t(const Batch& b, const Scene& s, const Consts& c,
                        threads * kAccFloats * static_cast<int>(sizeof(float)));
   auto kern = backward_kernel<NORMALS, NFLOW>;
   // Dynamic plus static shared memory above the 48 KB default needs the opt-in.
-  if (smem + static_cast<int>(sizeof(float) * (kBwdMaxThreads / 32) * 36) > 48 * 1024) {
+  if (smem + static_cast<int>(sizeof(float) * (kBwdMaxThreads / 32) * 48) > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
@@ -402,6 +417,23 @@ cudaError_t launch_backward(const Batch& b, const Scene& s, const Consts& c, con
   if (n_flow == 0) return launch_bwd_t<false, 0>(b, s, c, records, ray_tile, threads, in, out, st);
   if (n_flow == 1) return launch_bwd_t<false, 1>(b, s, c, records, ray_tile, threads, in, out, st);
   return launch_bwd_t<false, 2>(b, s, c, records, ray_tile, threads, in, out, st);
+}
+
+// ------------------------------------------------- zeroing of the outputs
+// One launch clears the status word and every gradient output before the
+// backward kernels accumulate into them.
+__global__ void zero_kernel(ZeroJob job) {
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  for (int b = 0; b < ZeroJob::kMax; ++b) {
+    if (job.ptr[b] == nullptr) continue;
+    for (long long j = i; j < job.n[b]; j += stride) job.ptr[b][j] = 0.f;
+  }
+}
+
+cudaError_t launch_zero(const ZeroJob& job, cudaStream_t st) {
+  zero_kernel<<<2 * 152, 256, 0, st>>>(job);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------- deterministic second stage

@@ -21,9 +21,10 @@ constexpr int kChunk = 256;  // records per shared-memory stage (16 KB)
 // transformations), so that the per-pair residual can be evaluated to full fp32
 // accuracy relative to its own size.
 __global__ void __launch_bounds__(128) prologue_kernel(const __grid_constant__ Batch batch, Scene s, Consts k,
-                                                        float4* __restrict__ records) {
+                                                        float4* __restrict__ records, int* status_to_clear) {
   const DevView& V = batch.v[blockIdx.y];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (status_to_clear != nullptr && i == 0 && blockIdx.y == 0) *status_to_clear = kDevOk;
   if (i >= V.K) return;
   float R[9], t[3];
   load_pose(s.poses, V.pose, R, t);
@@ -54,9 +55,9 @@ __global__ void __launch_bounds__(128) prologue_kernel(const __grid_constant__ B
 }
 
 cudaError_t launch_prologue(const Batch& b, const Scene& s, const Consts& c, float4* records, int maxK,
-                            cudaStream_t st) {
+                            int* status_to_clear, cudaStream_t st) {
   dim3 grid((maxK + 127) / 128, b.n_views);
-  prologue_kernel<<<grid, 128, 0, st>>>(b, s, c, records);
+  prologue_kernel<<<grid, 128, 0, st>>>(b, s, c, records, status_to_clear);
   return cudaGetLastError();
 }
 
@@ -255,35 +256,36 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
 
 template <bool NORMALS, int NFLOW, int RPT>
 static cudaError_t launch_fwd_t(const Batch& b, const Scene& s, const Consts& c, const float4* records,
-                                const FwdOut& o, int* status, cudaStream_t st) {
+                                const FwdOut& o, int maxK, int* status, cudaStream_t st) {
   auto kern = forward_kernel<NORMALS, NFLOW, RPT>;
-  const int smem = 2 * kChunk * kRecFloat4 * static_cast<int>(sizeof(float4));
+  const int stages = maxK > kChunk ? 2 : 1;  // a second stage only when K spans several chunks
+  const int smem = stages * kChunk * kRecFloat4 * static_cast<int>(sizeof(float4));
   kern<<<b.total_ctas, kFwdThreads, smem, st>>>(b, s, c, records, o, status);
   return cudaGetLastError();
 }
 
 template <bool NORMALS, int NFLOW>
 static cudaError_t launch_fwd_r(int rpt, const Batch& b, const Scene& s, const Consts& c, const float4* records,
-                                const FwdOut& o, int* status, cudaStream_t st) {
+                                const FwdOut& o, int maxK, int* status, cudaStream_t st) {
   switch (rpt) {
-    case 1: return launch_fwd_t<NORMALS, NFLOW, 1>(b, s, c, records, o, status, st);
-    case 2: return launch_fwd_t<NORMALS, NFLOW, 2>(b, s, c, records, o, status, st);
-    default: return launch_fwd_t<NORMALS, NFLOW, 4>(b, s, c, records, o, status, st);
+    case 1: return launch_fwd_t<NORMALS, NFLOW, 1>(b, s, c, records, o, maxK, status, st);
+    case 2: return launch_fwd_t<NORMALS, NFLOW, 2>(b, s, c, records, o, maxK, status, st);
+    default: return launch_fwd_t<NORMALS, NFLOW, 4>(b, s, c, records, o, maxK, status, st);
   }
 }
 
 cudaError_t launch_forward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
-                           int n_flow, int rpt, float* depth, float* alpha, float* normal, float* flow,
+                           int n_flow, int rpt, int maxK, float* depth, float* alpha, float* normal, float* flow,
                            float* saved, int* status, cudaStream_t st) {
   FwdOut o{depth, alpha, normal, flow, saved};
   if (normals) {
-    if (n_flow == 0) return launch_fwd_r<true, 0>(rpt, b, s, c, records, o, status, st);
-    if (n_flow == 1) return launch_fwd_r<true, 1>(rpt, b, s, c, records, o, status, st);
-    return launch_fwd_r<true, 2>(rpt, b, s, c, records, o, status, st);
+    if (n_flow == 0) return launch_fwd_r<true, 0>(rpt, b, s, c, records, o, maxK, status, st);
+    if (n_flow == 1) return launch_fwd_r<true, 1>(rpt, b, s, c, records, o, maxK, status, st);
+    return launch_fwd_r<true, 2>(rpt, b, s, c, records, o, maxK, status, st);
   }
-  if (n_flow == 0) return launch_fwd_r<false, 0>(rpt, b, s, c, records, o, status, st);
-  if (n_flow == 1) return launch_fwd_r<false, 1>(rpt, b, s, c, records, o, status, st);
-  return launch_fwd_r<false, 2>(rpt, b, s, c, records, o, status, st);
+  if (n_flow == 0) return launch_fwd_r<false, 0>(rpt, b, s, c, records, o, maxK, status, st);
+  if (n_flow == 1) return launch_fwd_r<false, 1>(rpt, b, s, c, records, o, maxK, status, st);
+  return launch_fwd_r<false, 2>(rpt, b, s, c, records, o, maxK, status, st);
 }
 
 int forward_rays_per_cta(int rpt) { return kFwdThreads * rpt; }

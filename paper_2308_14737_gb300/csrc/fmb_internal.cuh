@@ -336,11 +336,19 @@ struct Scene {
   const float* poses;
 };
 
+// status_to_clear: if not null, the prologue also zeroes this status word.
 cudaError_t launch_prologue(const Batch& b, const Scene& s, const Consts& c, float4* records, int maxK,
-                            cudaStream_t st);
+                            int* status_to_clear, cudaStream_t st);
 cudaError_t launch_forward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
-                           int n_flow, int rpt, float* depth, float* alpha, float* normal, float* flow,
+                           int n_flow, int rpt, int maxK, float* depth, float* alpha, float* normal, float* flow,
                            float* saved, int* status, cudaStream_t st);
+
+struct ZeroJob {
+  static constexpr int kMax = 6;
+  float* ptr[kMax];
+  long long n[kMax];
+};
+cudaError_t launch_zero(const ZeroJob& job, cudaStream_t st);
 
 struct BwdOut {
   float* gmeans;
