@@ -26,8 +26,8 @@ namespace {
 thread_local std::string g_err;
 
 constexpr size_t kHeaderBytes = 256;
-constexpr int kDefaultRpt = 4;
-constexpr int kMaxGaussPerCta = 128;
+constexpr int kDefaultRpt = 2;
+constexpr int kMaxGaussPerCta = 256;
 constexpr long long kMaxK = 1 << 22;
 
 fmb_status fail(fmb_status s, const std::string& msg) {
@@ -41,20 +41,23 @@ struct BwdBlocking {
   int n_gb, GB, S;
 };
 
+// Backward blocking of K Gaussians for T threads: each thread owns two Gaussians
+// (one per packed lane), so a CTA covers GB <= min(2T, 256) Gaussians with
+// ceil(GB/2) threads per ray subgroup and S subgroups.
 BwdBlocking bwd_blocking(int K, int T) {
-  const int gbmax = std::min(T, kMaxGaussPerCta);
+  const int gbmax = std::min(2 * T, kMaxGaussPerCta);
   BwdBlocking b;
   b.n_gb = (K + gbmax - 1) / gbmax;
   b.GB = (K + b.n_gb - 1) / b.n_gb;
-  b.S = std::max(1, T / b.GB);
+  b.S = std::max(1, T / ((b.GB + 1) / 2));
   return b;
 }
 
 // Threads per backward CTA: the candidate that wastes the fewest thread slots over
 // the batch, weighted by each view's pairs.
 int choose_bwd_threads(const fmb_view* views, int n_views, const long long* offs) {
-  const int cand[] = {128, 160, 192, 224};
-  int best = 224;
+  const int cand[] = {128, 160};
+  int best = 160;
   double best_eff = -1.0;
   for (int T : cand) {
     double num = 0.0, den = 0.0;
@@ -62,7 +65,8 @@ int choose_bwd_threads(const fmb_view* views, int n_views, const long long* offs
       const int K = static_cast<int>(offs[views[i].object + 1] - offs[views[i].object]);
       const double pairs = static_cast<double>(views[i].W) * views[i].H * K;
       BwdBlocking b = bwd_blocking(K, T);
-      const double eff = (static_cast<double>(b.GB) * b.S / T) * (static_cast<double>(K) / (b.n_gb * b.GB));
+      const int gb2 = (b.GB + 1) / 2;
+      const double eff = (static_cast<double>(gb2) * b.S / T) * (static_cast<double>(K) / (b.n_gb * 2.0 * gb2));
       num += pairs * eff;
       den += pairs;
     }
@@ -83,8 +87,8 @@ struct Plan {
   long long n_gauss = 0;
   int maxK = 0;
   int rpt = kDefaultRpt;
-  int ray_tile = 448;
-  int bwd_threads = 224;
+  int ray_tile = 480;
+  int bwd_threads = 160;
 };
 
 fmb_status validate_scene(const fmb_params* p, int n_objects, const long long* offs, int n_views,
@@ -101,8 +105,8 @@ fmb_status validate_scene(const fmb_params* p, int n_objects, const long long* o
   if (p->fwd_threads != 0 && p->fwd_threads != 128) return fail(FMB_ERR_INVALID_ARG, "fwd_threads must be 0 or 128");
   if (p->bwd_ray_tile < 0 || p->bwd_ray_tile > 1024 || (p->bwd_ray_tile % 32) != 0)
     return fail(FMB_ERR_INVALID_ARG, "bwd_ray_tile must be a multiple of 32 in [32, 1024] (0 = default)");
-  if (p->bwd_threads != 0 && (p->bwd_threads < 32 || p->bwd_threads > 224 || (p->bwd_threads % 32) != 0))
-    return fail(FMB_ERR_INVALID_ARG, "bwd_threads must be a multiple of 32 in [32, 224] (0 = default)");
+  if (p->bwd_threads != 0 && (p->bwd_threads < 32 || p->bwd_threads > 160 || (p->bwd_threads % 32) != 0))
+    return fail(FMB_ERR_INVALID_ARG, "bwd_threads must be a multiple of 32 in [32, 160] (0 = default)");
   if (n_objects < 1) return fail(FMB_ERR_INVALID_ARG, "n_objects must be >= 1");
   if (!offs) return fail(FMB_ERR_INVALID_ARG, "h_obj_offsets is NULL");
   if (offs[0] != 0) return fail(FMB_ERR_INVALID_ARG, "h_obj_offsets[0] must be 0");
@@ -145,8 +149,9 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
   Plan pl;
   pl.rpt = p->fwd_rays_per_thread > 0 ? p->fwd_rays_per_thread : kDefaultRpt;
   pl.bwd_threads = p->bwd_threads > 0 ? p->bwd_threads : choose_bwd_threads(views, n_views, offs);
-  // default ray tile: two rays per thread in the per-ray phase, so that phase is balanced
-  pl.ray_tile = p->bwd_ray_tile > 0 ? p->bwd_ray_tile : 2 * pl.bwd_threads;
+  // default ray tile: three rays per thread in the per-ray phase (balanced, and long
+  // enough to amortise the per-CTA reductions)
+  pl.ray_tile = p->bwd_ray_tile > 0 ? p->bwd_ray_tile : 3 * pl.bwd_threads;
   pl.n_gauss = offs[n_objects];
   const int rays_fwd = fmb::forward_rays_per_cta(pl.rpt);
   const int n_flow = p->n_flow;

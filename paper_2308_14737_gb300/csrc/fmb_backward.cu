@@ -3,12 +3,13 @@
 // factors L, the weights lambda and the camera poses.
 //
 // Layout of the work: a CTA takes one view, one tile of rays and one block of
-// Gaussians.  Phase 1 turns each ray's upstream gradients into a 64-byte record in
-// shared memory (the per-pixel part of the adjoint: flow, normal renormalisation,
-// alpha).  Phase 2 is Gaussian-parallel: each thread owns one Gaussian, recomputes
-// its pair terms for every ray of its subgroup from the saved log-normaliser (no
-// per-pair state was stored by the forward) and accumulates the Gaussian's
-// gradient sums in registers.  Phase 3 combines the subgroups, converts the sums
+// Gaussians.  Phase 1 turns each ray's upstream gradients into a record in shared
+// memory (the per-pixel part of the adjoint: flow, normal renormalisation, alpha),
+// every value stored twice so that one 16-byte load yields two broadcast pairs.
+// Phase 2 is Gaussian-parallel: each thread owns two Gaussians, one per lane of
+// packed FP32x2 arithmetic, recomputes their pair terms for every ray of its
+// subgroup from the saved log-normaliser (no per-pair state was stored by the
+// forward) and accumulates both Gaussians' gradient sums in registers.  Phase 3 combines the subgroups, converts the sums
 // into gradients of mu, L, lambda and of the pose, and writes them once per CTA
 // (fp32 atomics, or per-CTA partials that a second kernel adds in a fixed order).
 //
@@ -23,94 +24,100 @@
 // and per Gaussian: Lbar = lower(sum gbar u^T + sum v abar^T + (mu - o) bbar^T),
 // mubar = L sum bbar, lambdabar = sum dbar / lambda.  The term -dbar u . a of tbar
 // is dropped: u . a = 0 exactly at the max-likelihood depth.
+#include "fmb_f32x2.cuh"
 #include "fmb_internal.cuh"
 
 namespace fmb {
 
-constexpr int kBwdMaxThreads = 224;
+constexpr int kBwdMaxThreads = 160;
 #ifndef FMB_BWD_MIN_BLOCKS
 #define FMB_BWD_MIN_BLOCKS 3
 #endif
 constexpr int kBwdMinBlocks = FMB_BWD_MIN_BLOCKS;  // resident CTAs per SM the register budget targets
-constexpr int kAccFloats = 20;  // 19 accumulators (+1 pad) per thread in the reduction
+constexpr int kAccFloats = 38;  // 19 packed accumulators per thread in the reduction
 
-struct BwdAcc {
-  float Sd;               // sum dbar
-  float Y0, Y1, Y2;       // sum y   (= -sum bbar)
-  float G00, G10, G11, G20, G21, G22;  // sum gbar u^T (lower)
-  float M[9];             // sum v abar^T (row-major)
+// Per-thread gradient sums of the thread's two Gaussians (one per lane).
+struct BwdAcc2 {
+  f2 nSd;                 // -sum dbar
+  f2 Y0, Y1, Y2;          // sum y   (= -sum bbar)
+  f2 G00, G10, G11, G20, G21, G22;  // sum gbar u^T (lower)
+  f2 M[9];                // sum v abar^T (row-major)
 };
 
+// Shared-memory record of one ray, 7 x 16 bytes, every value duplicated:
+//   [v0 v0 v1 v1 | v2 v2 -lse2 -lse2 | Dbar Dbar -KA -KA | -C -C Nb0 Nb0 |
+//    Nb1 Nb1 Nb2 Nb2 | vl0 vl0 vl1 vl1 | vl2 vl2 0 0]
+constexpr int kRayRec2 = 7;
+
 template <bool NORMALS>
-__device__ __forceinline__ void bwd_pair(BwdAcc& A, const GaussRec& gr, const float4& q0, const float4& q1,
-                                         const float4& q2, const float4& q3, const Consts& k) {
-  const float L00 = gr.L[0], L10 = gr.L[1], L11 = gr.L[2], L20 = gr.L[3], L21 = gr.L[4], L22 = gr.L[5];
-  const float v0 = q0.x, v1 = q0.y, v2 = q0.z, lse2 = q0.w;
-  const float Dbar = q1.x, KA = q1.y, C = q1.z;
-  const PairGeom G = pair_geom(gr.L, gr.b, gr.mh, gr.nbl, v0, v1, v2, q2.z, q2.w, q3.x);
-  const float a0 = G.a0, a1 = G.a1, a2 = G.a2, inv = G.inv, t = G.t;
-  const float u0 = G.u0, u1 = G.u1, u2 = G.u2;
-  const float x = fmaf(G.q, k.K3, gr.l2);  // log2(delta)
-  const float what = ex2_approx(fmaf(x, k.beta1, fmaf(t, k.K2, -lse2)));
-  const float delta = ex2_approx(x);
-  float ebar, ub0, ub1, ub2, tbar;
-  float gb0 = 0.f, gb1 = 0.f, gb2 = 0.f;
+__device__ __forceinline__ void bwd_pair2(BwdAcc2& A, const GaussRec2& gr, const ulonglong2* __restrict__ rr, f2 K2,
+                                          f2 K3, f2 B1, f2 nB1, f2 nB2E, f2 tiny) {
+  const ulonglong2 q0 = rr[0], q1 = rr[1], q2 = rr[2], q3 = rr[3], q4 = rr[4], q5 = rr[5], q6 = rr[6];
+  const f2 v0 = as_f2(q0.x), v1 = as_f2(q0.y), v2 = as_f2(q1.x), nlse = as_f2(q1.y);
+  const f2 Dbar = as_f2(q2.x), nKA = as_f2(q2.y), nC = as_f2(q3.x);
+  const PairGeom2 G = pair_geom2(gr, v0, v1, v2, as_f2(q5.x), as_f2(q5.y), as_f2(q6.x));
+  const f2 t = G.t;
+  const f2 x = fma2(G.q, K3, gr.l2);  // log2(delta)
+  const f2 what = ex2_2(fma2(x, B1, fma2(t, K2, nlse)));
+  const f2 delta = ex2_2(x);
+  f2 ebar, ub0, ub1, ub2, tbar, gb0, gb1, gb2;
   if (NORMALS) {
-    const float Nb0 = q1.w, Nb1 = q2.x, Nb2 = q2.y;
-    const float g0 = L00 * u0;
-    const float g1 = fmaf(L11, u1, L10 * u0);
-    const float g2 = fmaf(L22, u2, fmaf(L21, u1, L20 * u0));
-    const float gg = fmaxf(fmaf(g2, g2, fmaf(g1, g1, g0 * g0)), 1e-30f);
-    const float rs = rsqrt_approx(gg);
-    const float n0 = g0 * rs, n1 = g1 * rs, n2 = g2 * rs;
-    const float nN = fmaf(n2, Nb2, fmaf(n1, Nb1, n0 * Nb0));
-    ebar = what * (fmaf(Dbar, t, -C) + nN);
-    const float sc = what * rs;
-    const float sN = sc * nN;
-    gb0 = fmaf(-sN, n0, sc * Nb0);
-    gb1 = fmaf(-sN, n1, sc * Nb1);
-    gb2 = fmaf(-sN, n2, sc * Nb2);
-    ub0 = fmaf(L20, gb2, fmaf(L10, gb1, L00 * gb0));
-    ub1 = fmaf(L21, gb2, L11 * gb1);
-    ub2 = L22 * gb2;
-    tbar = fmaf(ub2, a2, fmaf(ub1, a1, fmaf(ub0, a0, fmaf(Dbar, what, -k.b2e * ebar))));
+    const f2 Nb0 = as_f2(q3.y), Nb1 = as_f2(q4.x), Nb2 = as_f2(q4.y);
+    const f2 g0 = mul2(gr.L[0], G.u0);
+    const f2 g1 = fma2(gr.L[2], G.u1, mul2(gr.L[1], G.u0));
+    const f2 g2 = fma2(gr.L[5], G.u2, fma2(gr.L[4], G.u1, mul2(gr.L[3], G.u0)));
+    const f2 gg = add2(fma2(g2, g2, fma2(g1, g1, mul2(g0, g0))), tiny);
+    const f2 rs = rsqrt_2(gg);
+    const f2 n0 = mul2(g0, rs), n1 = mul2(g1, rs), n2 = mul2(g2, rs);
+    const f2 nN = fma2(n2, Nb2, fma2(n1, Nb1, mul2(n0, Nb0)));
+    ebar = mul2(what, add2(fma2(Dbar, t, nC), nN));
+    const f2 sc = mul2(what, rs);
+    const f2 sN = mul2(sc, nN);
+    const f2 nsN = pk(-lo(sN), -hi(sN));
+    gb0 = fma2(nsN, n0, mul2(sc, Nb0));
+    gb1 = fma2(nsN, n1, mul2(sc, Nb1));
+    gb2 = fma2(nsN, n2, mul2(sc, Nb2));
+    ub0 = fma2(gr.L[3], gb2, fma2(gr.L[1], gb1, mul2(gr.L[0], gb0)));
+    ub1 = fma2(gr.L[4], gb2, mul2(gr.L[2], gb1));
+    ub2 = mul2(gr.L[5], gb2);
+    tbar = fma2(ub2, G.a2, fma2(ub1, G.a1, fma2(ub0, G.a0, fma2(Dbar, what, mul2(nB2E, ebar)))));
   } else {
-    ebar = what * fmaf(Dbar, t, -C);
-    ub0 = ub1 = ub2 = 0.f;
-    tbar = fmaf(Dbar, what, -k.b2e * ebar);
+    ebar = mul2(what, fma2(Dbar, t, nC));
+    ub0 = ub1 = ub2 = gb0 = gb1 = gb2 = dup(0.f);
+    tbar = fma2(Dbar, what, mul2(nB2E, ebar));
   }
-  const float dbar = fmaf(k.beta1, ebar, KA * delta);
-  ub0 = fmaf(-dbar, u0, ub0);
-  ub1 = fmaf(-dbar, u1, ub1);
-  ub2 = fmaf(-dbar, u2, ub2);
-  const float s2 = tbar * inv;
-  const float y0 = fmaf(-s2, a0, ub0);
-  const float y1 = fmaf(-s2, a1, ub1);
-  const float y2 = fmaf(-s2, a2, ub2);
-  const float ab0 = fmaf(t, y0, -s2 * u0);
-  const float ab1 = fmaf(t, y1, -s2 * u1);
-  const float ab2 = fmaf(t, y2, -s2 * u2);
-  A.Sd += dbar;
-  A.Y0 += y0;
-  A.Y1 += y1;
-  A.Y2 += y2;
+  const f2 ndbar = fma2(nB1, ebar, mul2(nKA, delta));  // -dbar
+  ub0 = fma2(ndbar, G.u0, ub0);
+  ub1 = fma2(ndbar, G.u1, ub1);
+  ub2 = fma2(ndbar, G.u2, ub2);
+  const f2 ns2 = mul2(tbar, G.ninv);  // -tbar / a.a
+  const f2 y0 = fma2(ns2, G.a0, ub0);
+  const f2 y1 = fma2(ns2, G.a1, ub1);
+  const f2 y2 = fma2(ns2, G.a2, ub2);
+  const f2 ab0 = fma2(t, y0, mul2(ns2, G.u0));
+  const f2 ab1 = fma2(t, y1, mul2(ns2, G.u1));
+  const f2 ab2 = fma2(t, y2, mul2(ns2, G.u2));
+  A.nSd = add2(A.nSd, ndbar);
+  A.Y0 = add2(A.Y0, y0);
+  A.Y1 = add2(A.Y1, y1);
+  A.Y2 = add2(A.Y2, y2);
   if (NORMALS) {
-    A.G00 = fmaf(gb0, u0, A.G00);
-    A.G10 = fmaf(gb1, u0, A.G10);
-    A.G11 = fmaf(gb1, u1, A.G11);
-    A.G20 = fmaf(gb2, u0, A.G20);
-    A.G21 = fmaf(gb2, u1, A.G21);
-    A.G22 = fmaf(gb2, u2, A.G22);
+    A.G00 = fma2(gb0, G.u0, A.G00);
+    A.G10 = fma2(gb1, G.u0, A.G10);
+    A.G11 = fma2(gb1, G.u1, A.G11);
+    A.G20 = fma2(gb2, G.u0, A.G20);
+    A.G21 = fma2(gb2, G.u1, A.G21);
+    A.G22 = fma2(gb2, G.u2, A.G22);
   }
-  A.M[0] = fmaf(v0, ab0, A.M[0]);
-  A.M[1] = fmaf(v0, ab1, A.M[1]);
-  A.M[2] = fmaf(v0, ab2, A.M[2]);
-  A.M[3] = fmaf(v1, ab0, A.M[3]);
-  A.M[4] = fmaf(v1, ab1, A.M[4]);
-  A.M[5] = fmaf(v1, ab2, A.M[5]);
-  A.M[6] = fmaf(v2, ab0, A.M[6]);
-  A.M[7] = fmaf(v2, ab1, A.M[7]);
-  A.M[8] = fmaf(v2, ab2, A.M[8]);
+  A.M[0] = fma2(v0, ab0, A.M[0]);
+  A.M[1] = fma2(v0, ab1, A.M[1]);
+  A.M[2] = fma2(v0, ab2, A.M[2]);
+  A.M[3] = fma2(v1, ab0, A.M[3]);
+  A.M[4] = fma2(v1, ab1, A.M[4]);
+  A.M[5] = fma2(v1, ab2, A.M[5]);
+  A.M[6] = fma2(v2, ab0, A.M[6]);
+  A.M[7] = fma2(v2, ab1, A.M[7]);
+  A.M[8] = fma2(v2, ab2, A.M[8]);
 }
 
 __device__ __forceinline__ float warp_sum(float x) {
@@ -245,11 +252,14 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
       // Nbar is orthogonal to N, so the softmax centring term is Dbar * D alone.
       const float C = Dbar * D;
       const float KA = gA * expf(-Sd);
-      float4* rr = bsm + kRayRecFloat4 * r;
-      rr[0] = make_float4(v[0], v[1], v[2], lse2);
-      rr[1] = make_float4(Dbar, KA, C, Nb0);
-      rr[2] = make_float4(Nb1, Nb2, vl[0], vl[1]);
-      rr[3] = make_float4(vl[2], 0.f, 0.f, 0.f);
+      float4* rr = bsm + kRayRec2 * r;
+      rr[0] = make_float4(v[0], v[0], v[1], v[1]);
+      rr[1] = make_float4(v[2], v[2], -lse2, -lse2);
+      rr[2] = make_float4(Dbar, Dbar, -KA, -KA);
+      rr[3] = make_float4(-C, -C, Nb0, Nb0);
+      rr[4] = make_float4(Nb1, Nb1, Nb2, Nb2);
+      rr[5] = make_float4(vl[0], vl[0], vl[1], vl[1]);
+      rr[6] = make_float4(vl[2], vl[2], 0.f, 0.f);
     }
     // Reduce the per-ray pose terms now, so that they hold no registers in the loop.
     if (want_pose) {
@@ -262,26 +272,35 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
   }
   __syncthreads();
 
-  // ---------------- phase 2: Gaussian-parallel pair loop
+  // ---------------- phase 2: Gaussian-parallel pair loop (two Gaussians per thread)
   const int GB = V.GB, S = V.S;
-  const int gl = tid % GB;
-  const int sg = tid / GB;
-  const int g = gb * GB + gl;
-  const bool active = (sg < S) && (g < V.K);
-  BwdAcc A;
-  A.Sd = A.Y0 = A.Y1 = A.Y2 = 0.f;
-  A.G00 = A.G10 = A.G11 = A.G20 = A.G21 = A.G22 = 0.f;
+  const int GB2 = (GB + 1) / 2;  // threads per ray subgroup
+  const int gl2 = tid % GB2;
+  const int sg = tid / GB2;
+  const int g0 = gb * GB + 2 * gl2;        // lane 0 Gaussian
+  const bool has1 = 2 * gl2 + 1 < GB && g0 + 1 < V.K;  // lane 1 holds a real Gaussian
+  const bool active = (sg < S) && (g0 < V.K);
+  BwdAcc2 A;
+  A.nSd = A.Y0 = A.Y1 = A.Y2 = dup(0.f);
+  A.G00 = A.G10 = A.G11 = A.G20 = A.G21 = A.G22 = dup(0.f);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) A.M[i] = 0.f;
-  GaussRec gr{};
+  for (int i = 0; i < 9; ++i) A.M[i] = dup(0.f);
+  GaussRec ga{}, gbr{};
   if (active) {
-    const float4* rec = records + kRecFloat4 * (V.rec_off + g);
-    gr = unpack_rec(rec[0], rec[1], rec[2], rec[3]);
-#pragma unroll 2
-    for (int r = sg; r < nr; r += S) {
-      const float4* rr = bsm + kRayRecFloat4 * r;
-      bwd_pair<NORMALS>(A, gr, rr[0], rr[1], rr[2], rr[3], k);
+    const float4* rec = records + kRecFloat4 * (V.rec_off + g0);
+    ga = unpack_rec(rec[0], rec[1], rec[2], rec[3]);
+    if (has1) {
+      const float4* rec1 = rec + kRecFloat4;
+      gbr = unpack_rec(rec1[0], rec1[1], rec1[2], rec1[3]);
+    } else {
+      gbr = ga;  // a copy keeps the unused lane finite; its sums are never written
     }
+    const GaussRec2 gr = pair_rec(ga, gbr);
+    const f2 K2v = dup(k.K2), K3v = dup(k.K3), B1v = dup(k.beta1), nB1v = dup(-k.beta1), nB2E = dup(-k.b2e);
+    const f2 tiny = dup(1e-30f);
+    const ulonglong2* rays = reinterpret_cast<const ulonglong2*>(bsm);
+#pragma unroll 2
+    for (int r = sg; r < nr; r += S) bwd_pair2<NORMALS>(A, gr, rays + kRayRec2 * r, K2v, K3v, B1v, nB1v, nB2E, tiny);
   }
   __syncthreads();  // ray records are dead; the shared memory is reused below
 
@@ -289,10 +308,13 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
   float* red = reinterpret_cast<float*>(bsm);
   if (sg < S) {
     float* d = red + kAccFloats * tid;
-    d[0] = A.Sd; d[1] = A.Y0; d[2] = A.Y1; d[3] = A.Y2;
-    d[4] = A.G00; d[5] = A.G10; d[6] = A.G11; d[7] = A.G20; d[8] = A.G21; d[9] = A.G22;
+    const f2 v[19] = {A.nSd, A.Y0, A.Y1, A.Y2, A.G00, A.G10, A.G11, A.G20, A.G21, A.G22,
+                      A.M[0], A.M[1], A.M[2], A.M[3], A.M[4], A.M[5], A.M[6], A.M[7], A.M[8]};
 #pragma unroll
-    for (int i = 0; i < 9; ++i) d[10 + i] = A.M[i];
+    for (int i = 0; i < 19; ++i) {
+      d[i] = lo(v[i]);
+      d[19 + i] = hi(v[i]);
+    }
   }
   __syncthreads();
   float* slot = nullptr;
@@ -302,68 +324,77 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
   float pose_g[12];
 #pragma unroll
   for (int i = 0; i < 12; ++i) pose_g[i] = 0.f;
-  if (sg == 0 && gl < GB) {
-    float acc[19];
+  if (sg == 0 && gl2 < GB2) {
+    float R[9], tp[3];
+    const bool want_R = want_pose;
+    if (want_R) load_pose(s.poses, V.pose, R, tp);
 #pragma unroll
-    for (int i = 0; i < 19; ++i) acc[i] = 0.f;
-    for (int s2 = 0; s2 < S; ++s2) {
-      const float* d = red + kAccFloats * (s2 * GB + gl);
+    for (int lane2 = 0; lane2 < 2; ++lane2) {
+      const int gi = 2 * gl2 + lane2;  // Gaussian index within the block
+      if (gi >= GB) break;
+      const int g = gb * GB + gi;
+      float acc[19];
 #pragma unroll
-      for (int i = 0; i < 19; ++i) acc[i] += d[i];
-    }
-    float gm[3] = {0, 0, 0}, gL[6] = {0, 0, 0, 0, 0, 0}, glam = 0.f;
-    if (g < V.K) {
-      const long long gg = V.gauss_off + g;
-      const float L00 = gr.L[0], L10 = gr.L[1], L11 = gr.L[2], L20 = gr.L[3], L21 = gr.L[4], L22 = gr.L[5];
-      const float Bb0 = -acc[1], Bb1 = -acc[2], Bb2 = -acc[3];
-      // mubar = L bbar_sum
-      gm[0] = L00 * Bb0;
-      gm[1] = fmaf(L11, Bb1, L10 * Bb0);
-      gm[2] = fmaf(L22, Bb2, fmaf(L21, Bb1, L20 * Bb0));
-      const float m0 = gr.mh[0], m1 = gr.mh[1], m2 = gr.mh[2];
-      const float* M = acc + 10;
-      gL[0] = acc[4] + M[0] + m0 * Bb0;  // (0,0)
-      gL[1] = acc[5] + M[3] + m1 * Bb0;  // (1,0)
-      gL[2] = acc[6] + M[4] + m1 * Bb1;  // (1,1)
-      gL[3] = acc[7] + M[6] + m2 * Bb0;  // (2,0)
-      gL[4] = acc[8] + M[7] + m2 * Bb1;  // (2,1)
-      gL[5] = acc[9] + M[8] + m2 * Bb2;  // (2,2)
-      glam = acc[0] / s.weights[gg];
-      if (want_pose) {
-        // Rbar += R (M L^T) + t mubar^T ; tbar += R mubar
-        float R[9], tp[3];
-        load_pose(s.poses, V.pose, R, tp);
-        float ML[9];
-        const float Lf[9] = {L00, 0.f, 0.f, L10, L11, 0.f, L20, L21, L22};
+      for (int i = 0; i < 19; ++i) acc[i] = 0.f;
+      for (int s2 = 0; s2 < S; ++s2) {
+        const float* d = red + kAccFloats * (s2 * GB2 + gl2) + 19 * lane2;
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < 19; ++i) acc[i] += d[i];
+      }
+      float gm[3] = {0, 0, 0}, gL[6] = {0, 0, 0, 0, 0, 0}, glam = 0.f;
+      if (g < V.K && active) {
+        const GaussRec& gr1 = lane2 == 0 ? ga : gbr;
+        const long long gg = V.gauss_off + g;
+        const float L00 = gr1.L[0], L10 = gr1.L[1], L11 = gr1.L[2], L20 = gr1.L[3], L21 = gr1.L[4], L22 = gr1.L[5];
+        const float Bb0 = -acc[1], Bb1 = -acc[2], Bb2 = -acc[3];
+        // mubar = L bbar_sum
+        gm[0] = L00 * Bb0;
+        gm[1] = fmaf(L11, Bb1, L10 * Bb0);
+        gm[2] = fmaf(L22, Bb2, fmaf(L21, Bb1, L20 * Bb0));
+        const float m0 = gr1.mh[0], m1 = gr1.mh[1], m2 = gr1.mh[2];
+        const float* M = acc + 10;
+        gL[0] = acc[4] + M[0] + m0 * Bb0;  // (0,0)
+        gL[1] = acc[5] + M[3] + m1 * Bb0;  // (1,0)
+        gL[2] = acc[6] + M[4] + m1 * Bb1;  // (1,1)
+        gL[3] = acc[7] + M[6] + m2 * Bb0;  // (2,0)
+        gL[4] = acc[8] + M[7] + m2 * Bb1;  // (2,1)
+        gL[5] = acc[9] + M[8] + m2 * Bb2;  // (2,2)
+        glam = -acc[0] / s.weights[gg];
+        if (want_R) {
+          // Rbar += R (M L^T) + t mubar^T ; tbar += R mubar
+          float ML[9];
+          const float Lf[9] = {L00, 0.f, 0.f, L10, L11, 0.f, L20, L21, L22};
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
-            ML[3 * a + c] = fmaf(M[3 * a + 2], Lf[3 * c + 2], fmaf(M[3 * a + 1], Lf[3 * c + 1], M[3 * a] * Lf[3 * c]));
+          for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
+            for (int c = 0; c < 3; ++c)
+              ML[3 * a + c] =
+                  fmaf(M[3 * a + 2], Lf[3 * c + 2], fmaf(M[3 * a + 1], Lf[3 * c + 1], M[3 * a] * Lf[3 * c]));
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
-            pose_g[3 * a + c] = fmaf(R[3 * a + 2], ML[6 + c], fmaf(R[3 * a + 1], ML[3 + c], R[3 * a] * ML[c])) +
-                                tp[a] * gm[c];
-          pose_g[9 + a] = fmaf(R[3 * a + 2], gm[2], fmaf(R[3 * a + 1], gm[1], R[3 * a] * gm[0]));
+          for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              pose_g[3 * a + c] += fmaf(R[3 * a + 2], ML[6 + c], fmaf(R[3 * a + 1], ML[3 + c], R[3 * a] * ML[c])) +
+                                   tp[a] * gm[c];
+            pose_g[9 + a] += fmaf(R[3 * a + 2], gm[2], fmaf(R[3 * a + 1], gm[1], R[3 * a] * gm[0]));
+          }
+        }
+        if (slot == nullptr) {
+          atomicAdd(out.gmeans + 3 * gg + 0, gm[0]);
+          atomicAdd(out.gmeans + 3 * gg + 1, gm[1]);
+          atomicAdd(out.gmeans + 3 * gg + 2, gm[2]);
+#pragma unroll
+          for (int i = 0; i < 6; ++i) atomicAdd(out.gchol + 6 * gg + i, gL[i]);
+          atomicAdd(out.gweights + gg, glam);
         }
       }
-      if (slot == nullptr) {
-        atomicAdd(out.gmeans + 3 * gg + 0, gm[0]);
-        atomicAdd(out.gmeans + 3 * gg + 1, gm[1]);
-        atomicAdd(out.gmeans + 3 * gg + 2, gm[2]);
+      if (slot != nullptr) {
+        float* d = slot + 10 * gi;
+        d[0] = gm[0]; d[1] = gm[1]; d[2] = gm[2];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) atomicAdd(out.gchol + 6 * gg + i, gL[i]);
-        atomicAdd(out.gweights + gg, glam);
+        for (int i = 0; i < 6; ++i) d[3 + i] = gL[i];
+        d[9] = glam;
       }
-    }
-    if (slot != nullptr) {
-      float* d = slot + 10 * gl;
-      d[0] = gm[0]; d[1] = gm[1]; d[2] = gm[2];
-#pragma unroll
-      for (int i = 0; i < 6; ++i) d[3 + i] = gL[i];
-      d[9] = glam;
     }
   }
 
@@ -393,7 +424,7 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
 template <bool NORMALS, int NFLOW>
 static cudaError_t launch_bwd_t(const Batch& b, const Scene& s, const Consts& c, const float4* records,
                                 int ray_tile, int threads, const BwdIn& in, const BwdOut& out, cudaStream_t st) {
-  const int smem = max(ray_tile * kRayRecFloat4 * static_cast<int>(sizeof(float4)),
+  const int smem = max(ray_tile * kRayRec2 * static_cast<int>(sizeof(float4)),
                        threads * kAccFloats * static_cast<int>(sizeof(float)));
   auto kern = backward_kernel<NORMALS, NFLOW>;
   // Dynamic plus static shared memory above the 48 KB default needs the opt-in.

@@ -8,6 +8,7 @@
 // e = beta1 d - (beta2/eta) t.  The local normal Sigma^-1 (o + v t - mu) of Eq. 17 is
 // g = L u.  Everything is evaluated in the log2 domain so that the exponentials
 // are single ex2 instructions.
+#include "fmb_f32x2.cuh"
 #include "fmb_internal.cuh"
 
 namespace fmb {
@@ -103,6 +104,57 @@ __device__ __forceinline__ void fwd_pair(RayAcc& A, const GaussRec& g, const Con
   }
 }
 
+// Two rays of one thread, packed lane-wise (lane 0 = even ray, lane 1 = odd ray).
+struct RayAcc2 {
+  f2 v0, v1, v2, vl0, vl1, vl2;
+  f2 m, Sw, Swt, Sd, N0, N1, N2;
+};
+
+template <bool NORMALS>
+__device__ __forceinline__ void fwd_pair2(RayAcc2& A, const GaussRec2& g, f2 K2, f2 K3, f2 beta1, f2 tiny) {
+  const PairGeom2 G = pair_geom2(g, A.v0, A.v1, A.v2, A.vl0, A.vl1, A.vl2);
+  const f2 x = fma2(G.q, K3, g.l2);  // log2(delta)
+  A.Sd = add2(A.Sd, ex2_2(x));
+  const f2 e2 = fma2(x, beta1, mul2(G.t, K2));
+  f2 d = sub2(e2, A.m);
+  if (fmaxf(lo(d), hi(d)) > kLazyShift) {  // rare: raise the shift of the lane(s) it no longer bounds
+    float dl = lo(d), dh = hi(d), sl = 1.f, sh = 1.f, ml = lo(A.m), mh = hi(A.m);
+    if (dl > kLazyShift) {
+      sl = ex2_approx(-dl);
+      ml = lo(e2);
+      dl = 0.f;
+    }
+    if (dh > kLazyShift) {
+      sh = ex2_approx(-dh);
+      mh = hi(e2);
+      dh = 0.f;
+    }
+    const f2 sc = pk(sl, sh);
+    A.Sw = mul2(A.Sw, sc);
+    A.Swt = mul2(A.Swt, sc);
+    if (NORMALS) {
+      A.N0 = mul2(A.N0, sc);
+      A.N1 = mul2(A.N1, sc);
+      A.N2 = mul2(A.N2, sc);
+    }
+    A.m = pk(ml, mh);
+    d = pk(dl, dh);
+  }
+  const f2 w = ex2_2(d);
+  A.Sw = add2(A.Sw, w);
+  A.Swt = fma2(w, G.t, A.Swt);
+  if (NORMALS) {
+    const f2 g0 = mul2(g.L[0], G.u0);
+    const f2 g1 = fma2(g.L[2], G.u1, mul2(g.L[1], G.u0));
+    const f2 g2 = fma2(g.L[5], G.u2, fma2(g.L[4], G.u1, mul2(g.L[3], G.u0)));
+    const f2 gg = add2(fma2(g2, g2, fma2(g1, g1, mul2(g0, g0))), tiny);
+    const f2 ws = mul2(w, rsqrt_2(gg));
+    A.N0 = fma2(ws, g0, A.N0);
+    A.N1 = fma2(ws, g1, A.N1);
+    A.N2 = fma2(ws, g2, A.N2);
+  }
+}
+
 struct FwdOut {
   float* depth;
   float* alpha;
@@ -148,7 +200,12 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
     }
   }
 
-  RayAcc A[RPT];
+  // RPT even: rays are processed as packed pairs (PACKED); RPT == 1: scalar.
+  constexpr bool PACKED = (RPT % 2) == 0;
+  constexpr int NA = PACKED ? 1 : RPT;
+  constexpr int NP = PACKED ? RPT / 2 : 1;
+  RayAcc A[NA];
+  RayAcc2 A2[NP];
   int pix[RPT];
   float pxy[RPT][2];
   float vc[RPT][3];
@@ -159,16 +216,32 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
     p = min(p, P - 1);  // rays past the end compute a valid pixel and store nothing
     float v[3], vl[3];
     pixel_ray_dd(V, R, p, vc[r], v, vl, pxy[r]);
-    A[r].v0 = v[0];
-    A[r].v1 = v[1];
-    A[r].v2 = v[2];
-    A[r].vl0 = vl[0];
-    A[r].vl1 = vl[1];
-    A[r].vl2 = vl[2];
-    A[r].m = -INFINITY;
-    A[r].Sw = A[r].Swt = A[r].Sd = 0.f;
-    A[r].N0 = A[r].N1 = A[r].N2 = 0.f;
+    if (!PACKED) {
+      RayAcc& a = A[PACKED ? 0 : r];
+      a.v0 = v[0];
+      a.v1 = v[1];
+      a.v2 = v[2];
+      a.vl0 = vl[0];
+      a.vl1 = vl[1];
+      a.vl2 = vl[2];
+      a.m = -INFINITY;
+      a.Sw = a.Swt = a.Sd = 0.f;
+      a.N0 = a.N1 = a.N2 = 0.f;
+    } else {
+      RayAcc2& a = A2[r / 2];
+      if ((r & 1) == 0) {
+        a.v0 = pk(v[0], 0.f); a.v1 = pk(v[1], 0.f); a.v2 = pk(v[2], 0.f);
+        a.vl0 = pk(vl[0], 0.f); a.vl1 = pk(vl[1], 0.f); a.vl2 = pk(vl[2], 0.f);
+      } else {
+        a.v0 = pk(lo(a.v0), v[0]); a.v1 = pk(lo(a.v1), v[1]); a.v2 = pk(lo(a.v2), v[2]);
+        a.vl0 = pk(lo(a.vl0), vl[0]); a.vl1 = pk(lo(a.vl1), vl[1]); a.vl2 = pk(lo(a.vl2), vl[2]);
+      }
+      a.m = dup(-INFINITY);
+      a.Sw = a.Swt = a.Sd = dup(0.f);
+      a.N0 = a.N1 = a.N2 = dup(0.f);
+    }
   }
+  const f2 K2v = dup(k.K2), K3v = dup(k.K3), B1v = dup(k.beta1), tiny = dup(1e-30f);
 
   bool failed = false;
   for (int c = 0; c < nchunks; ++c) {
@@ -184,8 +257,14 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
     for (int i = 0; i < n; ++i) {
       const GaussRec g = unpack_rec(rec[kRecFloat4 * i + 0], rec[kRecFloat4 * i + 1], rec[kRecFloat4 * i + 2],
                                     rec[kRecFloat4 * i + 3]);
+      if (PACKED) {
+        const GaussRec2 g2 = broadcast_rec(g);
 #pragma unroll
-      for (int r = 0; r < RPT; ++r) fwd_pair<NORMALS>(A[r], g, k);
+        for (int q = 0; q < NP; ++q) fwd_pair2<NORMALS>(A2[q], g2, K2v, K3v, B1v, tiny);
+      } else {
+#pragma unroll
+        for (int r = 0; r < NA; ++r) fwd_pair<NORMALS>(A[r], g, k);
+      }
     }
     __syncthreads();  // every thread is done with this stage before it is refilled
     if (tid == 0 && c + 2 < nchunks) {
@@ -212,15 +291,32 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
   for (int r = 0; r < RPT; ++r) {
     if (pix[r] >= P) continue;
     const long long p = pix[r];
-    const float iSw = 1.0f / A[r].Sw;
-    const float D = A[r].Swt * iSw;
+    RayAcc a;
+    if (PACKED) {
+      const RayAcc2& b = A2[r / 2];
+      const bool h = (r & 1) != 0;
+      a.v0 = h ? hi(b.v0) : lo(b.v0);
+      a.v1 = h ? hi(b.v1) : lo(b.v1);
+      a.v2 = h ? hi(b.v2) : lo(b.v2);
+      a.m = h ? hi(b.m) : lo(b.m);
+      a.Sw = h ? hi(b.Sw) : lo(b.Sw);
+      a.Swt = h ? hi(b.Swt) : lo(b.Swt);
+      a.Sd = h ? hi(b.Sd) : lo(b.Sd);
+      a.N0 = h ? hi(b.N0) : lo(b.N0);
+      a.N1 = h ? hi(b.N1) : lo(b.N1);
+      a.N2 = h ? hi(b.N2) : lo(b.N2);
+    } else {
+      a = A[PACKED ? 0 : r];
+    }
+    const float iSw = 1.0f / a.Sw;
+    const float D = a.Swt * iSw;
     out.depth[off + p] = D;
-    out.alpha[off + p] = -expm1f(-A[r].Sd);
+    out.alpha[off + p] = -expm1f(-a.Sd);
     float* sv = out.saved + 3 * off;
-    sv[p] = A[r].m + log2f(A[r].Sw);
-    sv[P + p] = A[r].Sd;
+    sv[p] = a.m + log2f(a.Sw);
+    sv[P + p] = a.Sd;
     if (NORMALS) {
-      const float N0 = A[r].N0 * iSw, N1 = A[r].N1 * iSw, N2 = A[r].N2 * iSw;
+      const float N0 = a.N0 * iSw, N1 = a.N1 * iSw, N2 = a.N2 * iSw;
       const float Nn = sqrtf(fmaf(N0, N0, fmaf(N1, N1, N2 * N2)));
       const float iN = Nn > 0.f ? 1.0f / Nn : 0.f;
       const float n0 = N0 * iN, n1 = N1 * iN, n2 = N2 * iN;
@@ -233,7 +329,7 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
       sv[2 * P + p] = 0.f;
     }
     if (NFLOW > 0) {
-      const float p0 = fmaf(A[r].v0, D, o0), p1 = fmaf(A[r].v1, D, o1), p2 = fmaf(A[r].v2, D, o2);
+      const float p0 = fmaf(a.v0, D, o0), p1 = fmaf(a.v1, D, o1), p2 = fmaf(a.v2, D, o2);
       float* fl = out.flow + 2 * NFLOW * off;
 #pragma unroll
       for (int j = 0; j < NFLOW; ++j) {

@@ -114,7 +114,7 @@ def test_forward_rejects_bad_views(fmb, bad, msg):
 
 def test_forward_rejects_bad_params(fmb):
     for k, v, msg in [("eta", 0.0, "eta"), ("variant", 1, "variant"), ("n_flow", 3, "n_flow"),
-                      ("fwd_rays_per_thread", 3, "fwd_rays_per_thread"), ("bwd_threads", 100, "bwd_threads")]:
+                      ("fwd_rays_per_thread", 3, "fwd_rays_per_thread"), ("bwd_threads", 100, "bwd_threads"), ("bwd_threads", 192, "bwd_threads")]:
         p = fmb.default_params()
         setattr(p, k, v)
         st, err = _call_fwd(fmb, p, [0, 5], [_view()])

@@ -97,7 +97,7 @@ def test_deterministic_mode_is_bitwise_reproducible():
         np.testing.assert_allclose(g1[k], ga[k], rtol=0, atol=1e-5 * np.abs(g1[k]).max())
 
 
-@pytest.mark.parametrize("ray_tile,threads", [(32, 64), (128, 128), (512, 192), (1024, 224), (448, 224)])
+@pytest.mark.parametrize("ray_tile,threads", [(32, 64), (128, 128), (512, 96), (1024, 160), (320, 160)])
 def test_backward_tilings(ray_tile, threads):
     s = synth.config1(K=70, n_views=2, W=50, H=31)
     _full_check(s, n_flow=1, bwd_ray_tile=ray_tile, bwd_threads=threads)
