@@ -70,7 +70,9 @@ typedef struct {
   int want_normals;  /* 1: compute the blended normal plane (Eq. 17) and its adjoint */
   int n_flow;        /* flow slots per view, 0..2 (Sec. 5: forward i+1 and backward i-1) */
   int deterministic; /* backward: 1 = fixed-order two-stage reduction, 0 = fp32 atomics */
-  int use_persistent;/* reserved for the persistent work-queue launch; must be 0 for now */
+  int use_persistent;/* 1: persistent launch (one grid of resident CTAs popping (view, tile)
+                        work items, most expensive first, from a counter in the workspace);
+                        0: one CTA per work item */
   int fwd_rays_per_thread; /* tile hints; 0 = library default */
   int fwd_threads;
   int bwd_ray_tile;

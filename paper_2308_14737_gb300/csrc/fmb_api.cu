@@ -2,7 +2,8 @@
 // and the enqueueing of the prologue, forward, backward and reduction kernels.
 // No device memory is allocated here; scratch lives in the caller's workspace:
 //
-//   [0, 256)            status word (int) and padding
+//   [0, 256)            status word (int) at 0, forward work counter at 64,
+//                       backward work counter at 128
 //   [256, 256 + 64 R)   R per-(view, Gaussian) records, R = sum over views of K
 //   [.., ..)            backward partials (deterministic mode only)
 #include <algorithm>
@@ -26,6 +27,8 @@ namespace {
 thread_local std::string g_err;
 
 constexpr size_t kHeaderBytes = 256;
+constexpr size_t kFwdCounterOffset = 64;
+constexpr size_t kBwdCounterOffset = 128;
 constexpr int kDefaultRpt = 2;
 constexpr int kMaxGaussPerCta = 256;
 constexpr long long kMaxK = 1 << 22;
@@ -98,7 +101,7 @@ fmb_status validate_scene(const fmb_params* p, int n_objects, const long long* o
   if (!(p->eta > 0.0f) || !std::isfinite(p->eta)) return fail(FMB_ERR_INVALID_ARG, "eta must be > 0");
   if (p->variant != 0) return fail(FMB_ERR_INVALID_ARG, "only variant 0 (two-parameter model) is implemented");
   if (p->n_flow < 0 || p->n_flow > 2) return fail(FMB_ERR_INVALID_ARG, "n_flow must be 0, 1 or 2");
-  if (p->use_persistent != 0) return fail(FMB_ERR_INVALID_ARG, "use_persistent is not available yet");
+  if (p->use_persistent != 0 && p->use_persistent != 1) return fail(FMB_ERR_INVALID_ARG, "use_persistent must be 0 or 1");
   if (p->fwd_rays_per_thread != 0 && p->fwd_rays_per_thread != 1 && p->fwd_rays_per_thread != 2 &&
       p->fwd_rays_per_thread != 4)
     return fail(FMB_ERR_INVALID_ARG, "fwd_rays_per_thread must be 0, 1, 2 or 4");
@@ -145,6 +148,21 @@ fmb_status validate_views(int n_objects, int n_poses, int n_views, const fmb_vie
   return FMB_OK;
 }
 
+template <class Cost, class Count>
+void order_items(fmb::Batch& b, Cost cost, Count count) {
+  std::vector<int> idx(b.n_views);
+  for (int i = 0; i < b.n_views; ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost(b.v[x]) > cost(b.v[y]); });
+  long long acc = 0;
+  for (int j = 0; j < b.n_views; ++j) {
+    b.order_view[j] = idx[j];
+    b.order_begin[j] = static_cast<int>(acc);
+    acc += count(b.v[idx[j]]);
+  }
+  b.order_begin[b.n_views] = static_cast<int>(acc);
+  b.n_items = static_cast<int>(acc);
+}
+
 Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_views, const fmb_view* views) {
   Plan pl;
   pl.rpt = p->fwd_rays_per_thread > 0 ? p->fwd_rays_per_thread : kDefaultRpt;
@@ -188,7 +206,6 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
       fmb::DevView df = d;
       df.n_tiles = static_cast<int>((P + rays_fwd - 1) / rays_fwd);
       df.n_gblocks = 1;
-      df.cta_begin = static_cast<int>(ctas_f);
       ctas_f += df.n_tiles;
       bf.v[i] = df;
       // backward
@@ -201,13 +218,16 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
       db.slot_floats = 10 * bk.GB + 12 * (1 + n_flow);
       db.part_off = part;
       part += static_cast<long long>(db.n_tiles) * db.n_gblocks * db.slot_floats;
-      db.cta_begin = static_cast<int>(ctas_b);
       ctas_b += static_cast<long long>(db.n_tiles) * db.n_gblocks;
       bb.v[i] = db;
     }
     if (ctas_f > 0x7fffffffll || ctas_b > 0x7fffffffll) throw std::runtime_error("grid too large");
-    bf.total_ctas = static_cast<int>(ctas_f);
-    bb.total_ctas = static_cast<int>(ctas_b);
+    // Work items view by view, the views ordered by decreasing cost per item
+    // (forward: K x rays per tile; backward: Gaussians per block x rays per tile).
+    order_items(bf, [&](const fmb::DevView& v) { return static_cast<double>(v.K); },
+                [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles); });
+    order_items(bb, [&](const fmb::DevView& v) { return static_cast<double>(v.GB); },
+                [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles) * v.n_gblocks; });
     pl.fwd.push_back(bf);
     pl.bwd.push_back(bb);
   }
@@ -304,12 +324,15 @@ fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const lon
     const fmb::Scene sc{means, chol, weights, poses};
     const fmb::Consts c = make_consts(params);
     cudaError_t e = cudaSuccess;
+    int* counter = params->use_persistent
+                       ? reinterpret_cast<int*>(reinterpret_cast<char*>(status) + kFwdCounterOffset)
+                       : nullptr;
     for (size_t bi = 0; bi < pl.fwd.size(); ++bi) {
       const fmb::Batch& b = pl.fwd[bi];
-      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, bi == 0 ? status : nullptr, s);
+      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, bi == 0 ? status : nullptr, counter, s);
       if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
       e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, pl.maxK, depth,
-                              alpha, normal, flow, saved, status, s);
+                              alpha, normal, flow, saved, status, counter, s);
       if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     }
     return FMB_OK;
@@ -371,11 +394,12 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
     zj.n[4] = grad_poses ? 12ll * n_poses : 0;
     cudaError_t e = fmb::launch_zero(zj, s);
     if (e != cudaSuccess) return cuda_fail(e, "zeroing launch");
+    int* counter = params->use_persistent ? reinterpret_cast<int*>(base + kBwdCounterOffset) : nullptr;
     for (const fmb::Batch& b : pl.bwd) {
-      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, s);
+      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, counter, s);
       if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
       e = fmb::launch_backward(b, sc, c, records, normals, params->n_flow, pl.ray_tile, pl.bwd_threads, in, out,
-                               status, s);
+                               counter, s);
       if (e != cudaSuccess) return cuda_fail(e, "backward launch");
       if (partials) {
         e = fmb::launch_backward_reduce(b, params->n_flow, pl.n_gauss, n_poses, out, s);
@@ -480,12 +504,15 @@ extern "C" fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n
     const fmb::Scene sc{means, chol, weights, poses};
     const fmb::Consts c = make_consts(params);
     cudaError_t e = cudaSuccess;
+    int* counter = params->use_persistent
+                       ? reinterpret_cast<int*>(reinterpret_cast<char*>(status) + kFwdCounterOffset)
+                       : nullptr;
     for (size_t bi = 0; bi < pl.fwd.size(); ++bi) {
       const fmb::Batch& b = pl.fwd[bi];
-      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, bi == 0 ? status : nullptr, s);
+      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, bi == 0 ? status : nullptr, counter, s);
       if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
       e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, pl.maxK, depth,
-                              alpha, normal, flow, saved, status, s);
+                              alpha, normal, flow, saved, status, counter, s);
       if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     }
     return FMB_OK;

@@ -24,6 +24,8 @@
 // and per Gaussian: Lbar = lower(sum gbar u^T + sum v abar^T + (mu - o) bbar^T),
 // mubar = L sum bbar, lambdabar = sum dbar / lambda.  The term -dbar u . a of tbar
 // is dropped: u . a = 0 exactly at the max-likelihood depth.
+#include <algorithm>
+
 #include "fmb_f32x2.cuh"
 #include "fmb_internal.cuh"
 
@@ -129,15 +131,19 @@ __device__ __forceinline__ float warp_sum(float x) {
 template <bool NORMALS, int NFLOW>
 __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
     backward_kernel(const __grid_constant__ Batch batch, Scene s, Consts k, const float4* __restrict__ records,
-                    BwdIn in, BwdOut out, int ray_tile) {
+                    BwdIn in, BwdOut out, int ray_tile, int* counter) {
   extern __shared__ float4 bsm[];
   constexpr int NPV = 12 * (1 + NFLOW);  // pose values reduced per CTA
   __shared__ float pose_ray[kBwdMaxThreads / 32][NPV];  // per-warp sums of the per-ray pose terms
   __shared__ float pose_gau[kBwdMaxThreads / 32][12];   // per-warp sums of the per-Gaussian pose terms
+  __shared__ int s_item;
 
-  const int vi = find_view(batch, blockIdx.x);
+  for (int round = 0;; ++round) {
+  const int item = next_item(counter, round, &s_item);
+  if (item < 0 || item >= batch.n_items) break;
+  int local;
+  const int vi = find_item(batch, item, local);
   const DevView& V = batch.v[vi];
-  const int local = blockIdx.x - V.cta_begin;
   const int tile = local / V.n_gblocks;
   const int gb = local - tile * V.n_gblocks;
   const int P = V.W * V.H;
@@ -419,35 +425,67 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
       }
     }
   }
+  }  // item loop
+}
+
+static int bwd_smem_bytes(int ray_tile, int threads) {
+  return std::max(ray_tile * kRayRec2 * static_cast<int>(sizeof(float4)),
+                  threads * kAccFloats * static_cast<int>(sizeof(float)));
+}
+
+template <bool NORMALS, int NFLOW>
+static cudaError_t prepare_bwd_t(int smem) {
+  // Dynamic plus static shared memory above the 48 KB default needs the opt-in.
+  if (smem + static_cast<int>(sizeof(float) * (kBwdMaxThreads / 32) * 48) > 48 * 1024)
+    return cudaFuncSetAttribute(backward_kernel<NORMALS, NFLOW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return cudaSuccess;
+}
+
+template <bool NORMALS, int NFLOW>
+static int bwd_ctas_per_sm_t(int ray_tile, int threads) {
+  const int smem = bwd_smem_bytes(ray_tile, threads);
+  if (prepare_bwd_t<NORMALS, NFLOW>(smem) != cudaSuccess) return 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, backward_kernel<NORMALS, NFLOW>, threads, smem) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
 }
 
 template <bool NORMALS, int NFLOW>
 static cudaError_t launch_bwd_t(const Batch& b, const Scene& s, const Consts& c, const float4* records,
-                                int ray_tile, int threads, const BwdIn& in, const BwdOut& out, cudaStream_t st) {
-  const int smem = max(ray_tile * kRayRec2 * static_cast<int>(sizeof(float4)),
-                       threads * kAccFloats * static_cast<int>(sizeof(float)));
-  auto kern = backward_kernel<NORMALS, NFLOW>;
-  // Dynamic plus static shared memory above the 48 KB default needs the opt-in.
-  if (smem + static_cast<int>(sizeof(float) * (kBwdMaxThreads / 32) * 48) > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
+                                int ray_tile, int threads, const BwdIn& in, const BwdOut& out, int* counter,
+                                cudaStream_t st) {
+  const int smem = bwd_smem_bytes(ray_tile, threads);
+  cudaError_t e = prepare_bwd_t<NORMALS, NFLOW>(smem);
+  if (e != cudaSuccess) return e;
+  int grid = b.n_items;
+  if (counter) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    grid = std::min(b.n_items, std::max(1, sms) * bwd_ctas_per_sm_t<NORMALS, NFLOW>(ray_tile, threads));
   }
-  kern<<<b.total_ctas, threads, smem, st>>>(b, s, c, records, in, out, ray_tile);
+  backward_kernel<NORMALS, NFLOW><<<grid, threads, smem, st>>>(b, s, c, records, in, out, ray_tile, counter);
   return cudaGetLastError();
 }
 
 cudaError_t launch_backward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
                             int n_flow, int ray_tile, int threads, const BwdIn& in, const BwdOut& out,
-                            int* status, cudaStream_t st) {
-  (void)status;
+                            int* counter, cudaStream_t st) {
   if (normals) {
-    if (n_flow == 0) return launch_bwd_t<true, 0>(b, s, c, records, ray_tile, threads, in, out, st);
-    if (n_flow == 1) return launch_bwd_t<true, 1>(b, s, c, records, ray_tile, threads, in, out, st);
-    return launch_bwd_t<true, 2>(b, s, c, records, ray_tile, threads, in, out, st);
+    if (n_flow == 0) return launch_bwd_t<true, 0>(b, s, c, records, ray_tile, threads, in, out, counter, st);
+    if (n_flow == 1) return launch_bwd_t<true, 1>(b, s, c, records, ray_tile, threads, in, out, counter, st);
+    return launch_bwd_t<true, 2>(b, s, c, records, ray_tile, threads, in, out, counter, st);
   }
-  if (n_flow == 0) return launch_bwd_t<false, 0>(b, s, c, records, ray_tile, threads, in, out, st);
-  if (n_flow == 1) return launch_bwd_t<false, 1>(b, s, c, records, ray_tile, threads, in, out, st);
-  return launch_bwd_t<false, 2>(b, s, c, records, ray_tile, threads, in, out, st);
+  if (n_flow == 0) return launch_bwd_t<false, 0>(b, s, c, records, ray_tile, threads, in, out, counter, st);
+  if (n_flow == 1) return launch_bwd_t<false, 1>(b, s, c, records, ray_tile, threads, in, out, counter, st);
+  return launch_bwd_t<false, 2>(b, s, c, records, ray_tile, threads, in, out, counter, st);
+}
+
+int backward_ctas_per_sm(bool normals, int n_flow, int ray_tile, int threads) {
+  (void)normals;
+  (void)n_flow;
+  return bwd_ctas_per_sm_t<true, 1>(ray_tile, threads);
 }
 
 // ------------------------------------------------- zeroing of the outputs
@@ -468,14 +506,22 @@ cudaError_t launch_zero(const ZeroJob& job, cudaStream_t st) {
 }
 
 // ------------------------------------------- deterministic second stage
-// One thread per (Gaussian, component): adds the partials of every (view, tile)
-// slot of this launch that covers the Gaussian, in view then tile order.
+// One warp per output value: lane l adds slots l, l+32, l+64, ... in order, then a
+// fixed butterfly combines the lanes, so the result does not depend on timing.
+__device__ __forceinline__ float warp_sum_fixed(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Gaussian gradients: warp w handles (Gaussian g, component comp), w = g * 10 + comp.
 __global__ void reduce_gauss_kernel(const __grid_constant__ Batch batch, const float* __restrict__ partials,
                                     float* gmeans, float* gchol, float* gweights, long long n_gauss) {
-  const long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-  if (idx >= n_gauss * 10) return;
-  const long long g = idx / 10;
-  const int comp = static_cast<int>(idx - g * 10);
+  const long long w = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n_gauss * 10) return;  // whole warps exit together
+  const long long g = w / 10;
+  const int comp = static_cast<int>(w - g * 10);
   float acc = 0.f;
   bool hit = false;
   for (int v = 0; v < batch.n_views; ++v) {
@@ -484,10 +530,11 @@ __global__ void reduce_gauss_kernel(const __grid_constant__ Batch batch, const f
     hit = true;
     const int gi = static_cast<int>(g - V.gauss_off);
     const int gbk = gi / V.GB, gl = gi - gbk * V.GB;
-    for (int t = 0; t < V.n_tiles; ++t)
+    for (int t = lane; t < V.n_tiles; t += 32)
       acc += partials[V.part_off + static_cast<long long>(t * V.n_gblocks + gbk) * V.slot_floats + 10 * gl + comp];
   }
-  if (!hit) return;
+  acc = warp_sum_fixed(acc);
+  if (!hit || lane != 0) return;
   if (comp < 3)
     gmeans[3 * g + comp] += acc;
   else if (comp < 9)
@@ -496,36 +543,37 @@ __global__ void reduce_gauss_kernel(const __grid_constant__ Batch batch, const f
     gweights[g] += acc;
 }
 
-// One thread per (pose, component).
+// Pose gradients: warp w handles (pose p, component comp), w = p * 12 + comp.
 __global__ void reduce_pose_kernel(const __grid_constant__ Batch batch, const float* __restrict__ partials,
                                    float* gposes, int n_poses, int n_flow) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n_poses * 12) return;
-  const int p = idx / 12, comp = idx % 12;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n_poses * 12) return;
+  const int p = w / 12, comp = w % 12;
   float acc = 0.f;
   for (int v = 0; v < batch.n_views; ++v) {
     const DevView& V = batch.v[v];
-    int part = -1;
     for (int j = -1; j < n_flow; ++j) {
       const int pidx = j < 0 ? V.pose : (j == 0 ? V.tgt0 : V.tgt1);
       if (pidx != p) continue;
-      part = 12 * (j + 1) + comp;
+      const int part = 12 * (j + 1) + comp;
       const int nslots = V.n_tiles * V.n_gblocks;
-      for (int sl = 0; sl < nslots; ++sl)
+      for (int sl = lane; sl < nslots; sl += 32)
         acc += partials[V.part_off + static_cast<long long>(sl) * V.slot_floats + 10 * V.GB + part];
     }
   }
-  gposes[12 * static_cast<long long>(p) + comp] += acc;
+  acc = warp_sum_fixed(acc);
+  if (lane == 0) gposes[12 * static_cast<long long>(p) + comp] += acc;
 }
 
 cudaError_t launch_backward_reduce(const Batch& b, int n_flow, long long n_gauss, int n_poses, const BwdOut& out,
                                    cudaStream_t st) {
-  const long long n = n_gauss * 10;
-  reduce_gauss_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(b, out.partials, out.gmeans,
-                                                                              out.gchol, out.gweights, n_gauss);
+  const long long warps = n_gauss * 10;
+  reduce_gauss_kernel<<<static_cast<unsigned>((warps * 32 + 255) / 256), 256, 0, st>>>(
+      b, out.partials, out.gmeans, out.gchol, out.gweights, n_gauss);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || out.gposes == nullptr) return e;
-  reduce_pose_kernel<<<(n_poses * 12 + 127) / 128, 128, 0, st>>>(b, out.partials, out.gposes, n_poses, n_flow);
+  reduce_pose_kernel<<<(n_poses * 12 * 32 + 255) / 256, 256, 0, st>>>(b, out.partials, out.gposes, n_poses, n_flow);
   return cudaGetLastError();
 }
 

@@ -21,11 +21,13 @@ __device__ __forceinline__ f2 dup(float x) { return pk(x, x); }
 __device__ __forceinline__ float lo(f2 a) {
   float l, h;
   asm("mov.b64 {%0,%1}, %2;" : "=f"(l), "=f"(h) : "l"(a.v));
+  (void)h;
   return l;
 }
 __device__ __forceinline__ float hi(f2 a) {
   float l, h;
   asm("mov.b64 {%0,%1}, %2;" : "=f"(l), "=f"(h) : "l"(a.v));
+  (void)l;
   return h;
 }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {

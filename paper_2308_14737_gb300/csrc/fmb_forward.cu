@@ -8,6 +8,8 @@
 // e = beta1 d - (beta2/eta) t.  The local normal Sigma^-1 (o + v t - mu) of Eq. 17 is
 // g = L u.  Everything is evaluated in the log2 domain so that the exponentials
 // are single ex2 instructions.
+#include <algorithm>
+
 #include "fmb_f32x2.cuh"
 #include "fmb_internal.cuh"
 
@@ -22,10 +24,14 @@ constexpr int kChunk = 256;  // records per shared-memory stage (16 KB)
 // transformations), so that the per-pair residual can be evaluated to full fp32
 // accuracy relative to its own size.
 __global__ void __launch_bounds__(128) prologue_kernel(const __grid_constant__ Batch batch, Scene s, Consts k,
-                                                        float4* __restrict__ records, int* status_to_clear) {
+                                                        float4* __restrict__ records, int* status_to_clear,
+                                                        int* counter_to_clear) {
   const DevView& V = batch.v[blockIdx.y];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (status_to_clear != nullptr && i == 0 && blockIdx.y == 0) *status_to_clear = kDevOk;
+  if (i == 0 && blockIdx.y == 0) {
+    if (status_to_clear != nullptr) *status_to_clear = kDevOk;
+    if (counter_to_clear != nullptr) *counter_to_clear = 0;
+  }
   if (i >= V.K) return;
   float R[9], t[3];
   load_pose(s.poses, V.pose, R, t);
@@ -56,9 +62,9 @@ __global__ void __launch_bounds__(128) prologue_kernel(const __grid_constant__ B
 }
 
 cudaError_t launch_prologue(const Batch& b, const Scene& s, const Consts& c, float4* records, int maxK,
-                            int* status_to_clear, cudaStream_t st) {
+                            int* status_to_clear, int* counter_to_clear, cudaStream_t st) {
   dim3 grid((maxK + 127) / 128, b.n_views);
-  prologue_kernel<<<grid, 128, 0, st>>>(b, s, c, records, status_to_clear);
+  prologue_kernel<<<grid, 128, 0, st>>>(b, s, c, records, status_to_clear, counter_to_clear);
   return cudaGetLastError();
 }
 
@@ -166,15 +172,27 @@ struct FwdOut {
 template <bool NORMALS, int NFLOW, int RPT>
 __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_constant__ Batch batch, Scene s,
                                                               Consts k, const float4* __restrict__ records,
-                                                              FwdOut out, int* status) {
-  extern __shared__ float4 fwd_smem[];  // 2 stages x kChunk records
+                                                              FwdOut out, int* status, int* counter) {
+  extern __shared__ float4 fwd_smem[];  // 1 or 2 stages x kChunk records
   __shared__ __align__(8) uint64_t bars[2];
-
-  const int vi = find_view(batch, blockIdx.x);
-  const DevView& V = batch.v[vi];
-  const int tile = blockIdx.x - V.cta_begin;
-  const int P = V.W * V.H;
+  __shared__ int s_item;
   const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  // Completed phases of each stage's barrier so far (their parity selects the next wait).
+  unsigned uses0 = 0, uses1 = 0;
+
+  for (int round = 0;; ++round) {
+  const int item = next_item(counter, round, &s_item);
+  if (item < 0 || item >= batch.n_items) break;
+  int tile;
+  const int vi = find_item(batch, item, tile);
+  const DevView& V = batch.v[vi];
+  const int P = V.W * V.H;
   const int K = V.K;
 
   float R[9], tp[3];
@@ -186,12 +204,6 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
   // Stage the first record chunks while the rays are set up.
   const float4* src = records + kRecFloat4 * V.rec_off;
   const int nchunks = (K + kChunk - 1) / kChunk;
-  if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
   if (tid == 0) {
     for (int c = 0; c < 2 && c < nchunks; ++c) {
       const int n = min(kChunk, K - c * kChunk);
@@ -246,7 +258,8 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
   bool failed = false;
   for (int c = 0; c < nchunks; ++c) {
     const int stage = c & 1;
-    const bool ok = mbar_wait_bounded(&bars[stage], (c >> 1) & 1, status);
+    const unsigned parity = ((stage == 0 ? uses0 : uses1) + (c >> 1)) & 1u;
+    const bool ok = mbar_wait_bounded(&bars[stage], parity, status);
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
@@ -275,6 +288,8 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
     }
   }
   if (failed) return;
+  uses0 += (nchunks + 1) / 2;
+  uses1 += nchunks / 2;
 
   // Flow targets (uniform over the CTA).
   float Rj[NFLOW > 0 ? NFLOW : 1][9], tj[NFLOW > 0 ? NFLOW : 1][3];
@@ -348,42 +363,72 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
     }
   }
   (void)vc;
+  }  // item loop
+}
+
+static int fwd_smem_bytes(int maxK) {
+  const int stages = maxK > kChunk ? 2 : 1;  // a second stage only when K spans several chunks
+  return stages * kChunk * kRecFloat4 * static_cast<int>(sizeof(float4));
+}
+
+template <bool NORMALS, int NFLOW, int RPT>
+static int fwd_ctas_per_sm_t(int maxK) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, forward_kernel<NORMALS, NFLOW, RPT>, kFwdThreads,
+                                                    fwd_smem_bytes(maxK)) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
 }
 
 template <bool NORMALS, int NFLOW, int RPT>
 static cudaError_t launch_fwd_t(const Batch& b, const Scene& s, const Consts& c, const float4* records,
-                                const FwdOut& o, int maxK, int* status, cudaStream_t st) {
+                                const FwdOut& o, int maxK, int* status, int* counter, cudaStream_t st) {
   auto kern = forward_kernel<NORMALS, NFLOW, RPT>;
-  const int stages = maxK > kChunk ? 2 : 1;  // a second stage only when K spans several chunks
-  const int smem = stages * kChunk * kRecFloat4 * static_cast<int>(sizeof(float4));
-  kern<<<b.total_ctas, kFwdThreads, smem, st>>>(b, s, c, records, o, status);
+  int grid = b.n_items;
+  if (counter) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    grid = std::min(b.n_items, std::max(1, sms) * fwd_ctas_per_sm_t<NORMALS, NFLOW, RPT>(maxK));
+  }
+  kern<<<grid, kFwdThreads, fwd_smem_bytes(maxK), st>>>(b, s, c, records, o, status, counter);
   return cudaGetLastError();
 }
 
 template <bool NORMALS, int NFLOW>
 static cudaError_t launch_fwd_r(int rpt, const Batch& b, const Scene& s, const Consts& c, const float4* records,
-                                const FwdOut& o, int maxK, int* status, cudaStream_t st) {
+                                const FwdOut& o, int maxK, int* status, int* counter, cudaStream_t st) {
   switch (rpt) {
-    case 1: return launch_fwd_t<NORMALS, NFLOW, 1>(b, s, c, records, o, maxK, status, st);
-    case 2: return launch_fwd_t<NORMALS, NFLOW, 2>(b, s, c, records, o, maxK, status, st);
-    default: return launch_fwd_t<NORMALS, NFLOW, 4>(b, s, c, records, o, maxK, status, st);
+    case 1: return launch_fwd_t<NORMALS, NFLOW, 1>(b, s, c, records, o, maxK, status, counter, st);
+    case 2: return launch_fwd_t<NORMALS, NFLOW, 2>(b, s, c, records, o, maxK, status, counter, st);
+    default: return launch_fwd_t<NORMALS, NFLOW, 4>(b, s, c, records, o, maxK, status, counter, st);
   }
 }
 
 cudaError_t launch_forward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
                            int n_flow, int rpt, int maxK, float* depth, float* alpha, float* normal, float* flow,
-                           float* saved, int* status, cudaStream_t st) {
+                           float* saved, int* status, int* counter, cudaStream_t st) {
   FwdOut o{depth, alpha, normal, flow, saved};
   if (normals) {
-    if (n_flow == 0) return launch_fwd_r<true, 0>(rpt, b, s, c, records, o, maxK, status, st);
-    if (n_flow == 1) return launch_fwd_r<true, 1>(rpt, b, s, c, records, o, maxK, status, st);
-    return launch_fwd_r<true, 2>(rpt, b, s, c, records, o, maxK, status, st);
+    if (n_flow == 0) return launch_fwd_r<true, 0>(rpt, b, s, c, records, o, maxK, status, counter, st);
+    if (n_flow == 1) return launch_fwd_r<true, 1>(rpt, b, s, c, records, o, maxK, status, counter, st);
+    return launch_fwd_r<true, 2>(rpt, b, s, c, records, o, maxK, status, counter, st);
   }
-  if (n_flow == 0) return launch_fwd_r<false, 0>(rpt, b, s, c, records, o, maxK, status, st);
-  if (n_flow == 1) return launch_fwd_r<false, 1>(rpt, b, s, c, records, o, maxK, status, st);
-  return launch_fwd_r<false, 2>(rpt, b, s, c, records, o, maxK, status, st);
+  if (n_flow == 0) return launch_fwd_r<false, 0>(rpt, b, s, c, records, o, maxK, status, counter, st);
+  if (n_flow == 1) return launch_fwd_r<false, 1>(rpt, b, s, c, records, o, maxK, status, counter, st);
+  return launch_fwd_r<false, 2>(rpt, b, s, c, records, o, maxK, status, counter, st);
 }
 
 int forward_rays_per_cta(int rpt) { return kFwdThreads * rpt; }
+
+int forward_ctas_per_sm(bool normals, int n_flow, int rpt, int maxK) {
+  (void)normals;
+  (void)n_flow;
+  switch (rpt) {
+    case 1: return fwd_ctas_per_sm_t<true, 1, 1>(maxK);
+    case 2: return fwd_ctas_per_sm_t<true, 1, 2>(maxK);
+    default: return fwd_ctas_per_sm_t<true, 1, 4>(maxK);
+  }
+}
 
 }  // namespace fmb

@@ -48,7 +48,6 @@ struct DevView {
   int pose, tgt0, tgt1;
   int K;           // Gaussians of the view's object
   int obj;
-  int cta_begin;   // first CTA of this view within the launch
   int n_tiles;     // ray tiles of this view
   int n_gblocks;   // backward: Gaussian blocks
   int GB, S;       // backward: Gaussians per block, ray subgroups per CTA
@@ -60,9 +59,15 @@ struct DevView {
   int pad_;
 };
 
+// A launch's views.  Work items (forward: one ray tile; backward: one ray tile x
+// Gaussian block) are numbered view by view in `order_view` order -- the views
+// sorted by decreasing cost per item -- so both the hardware's block dispatch and
+// the persistent work queue take the most expensive items first.
 struct Batch {
   int n_views;
-  int total_ctas;
+  int n_items;
+  int order_view[kMaxBatchViews];       // views by decreasing cost per item
+  int order_begin[kMaxBatchViews + 1];  // first item of order_view[j]
   DevView v[kMaxBatchViews];
 };
 
@@ -224,17 +229,29 @@ __device__ __forceinline__ GaussRec unpack_rec(const float4& r0, const float4& r
   return g;
 }
 
-// Index of the view owning CTA `b` (views sorted by cta_begin).
-__device__ __forceinline__ int find_view(const Batch& batch, int b) {
+// View and view-local index of work item `item`.
+__device__ __forceinline__ int find_item(const Batch& batch, int item, int& local) {
   int lo = 0, hi = batch.n_views - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    if (batch.v[mid].cta_begin <= b)
+    if (batch.order_begin[mid] <= item)
       lo = mid;
     else
       hi = mid - 1;
   }
-  return lo;
+  local = item - batch.order_begin[lo];
+  return batch.order_view[lo];
+}
+
+// Work-item source of a CTA: its block index (grid mode), or successive pops of a
+// shared counter (persistent mode, `counter` != null).  Returns -1 when done.
+// Every thread of the CTA must call it; it synchronises the CTA.
+__device__ __forceinline__ int next_item(int* counter, int round, int* s_item) {
+  if (counter == nullptr) return round == 0 ? static_cast<int>(blockIdx.x) : -1;
+  __syncthreads();  // the previous item is finished with s_item and shared memory
+  if (threadIdx.x == 0) *s_item = atomicAdd(counter, 1);
+  __syncthreads();
+  return *s_item;
 }
 
 // Pixel-centre ray of pixel p as an unevaluated float pair: camera-frame unit
@@ -336,12 +353,14 @@ struct Scene {
   const float* poses;
 };
 
-// status_to_clear: if not null, the prologue also zeroes this status word.
+// status_to_clear / counter_to_clear: if not null, the prologue also zeroes them.
 cudaError_t launch_prologue(const Batch& b, const Scene& s, const Consts& c, float4* records, int maxK,
-                            int* status_to_clear, cudaStream_t st);
+                            int* status_to_clear, int* counter_to_clear, cudaStream_t st);
+// counter: persistent mode's work counter (zeroed before the launch), or null for
+// one CTA per work item.
 cudaError_t launch_forward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
                            int n_flow, int rpt, int maxK, float* depth, float* alpha, float* normal, float* flow,
-                           float* saved, int* status, cudaStream_t st);
+                           float* saved, int* status, int* counter, cudaStream_t st);
 
 struct ZeroJob {
   static constexpr int kMax = 6;
@@ -368,7 +387,11 @@ struct BwdIn {
 };
 cudaError_t launch_backward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
                             int n_flow, int ray_tile, int threads, const BwdIn& in, const BwdOut& out,
-                            int* status, cudaStream_t st);
+                            int* counter, cudaStream_t st);
+// Resident CTAs per SM of the render kernels for this configuration (persistent
+// grid sizing).
+int forward_ctas_per_sm(bool normals, int n_flow, int rpt, int maxK);
+int backward_ctas_per_sm(bool normals, int n_flow, int ray_tile, int threads);
 cudaError_t launch_backward_reduce(const Batch& b, int n_flow, long long n_gauss, int n_poses,
                                    const BwdOut& out, cudaStream_t st);
 

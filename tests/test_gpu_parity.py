@@ -70,10 +70,8 @@ def test_rays_per_thread_variants(rpt):
     _full_check(s, n_flow=1, fwd_rays_per_thread=rpt)
 
 
-def test_ragged_objects_and_edge_sizes():
-    """K in {1, 2, 31, 33, 300} (300 crosses the 256-record staging chunk), images
-    from 1x1 to 65x9, several objects and views in one launch."""
-    rng = np.random.default_rng(7)
+def _ragged_scene(seed=7):
+    rng = np.random.default_rng(seed)
     objs, views, poses = [], [], []
     sizes = [(1, 1), (3, 5), (33, 17), (65, 9), (16, 16)]
     for o, K in enumerate([1, 2, 31, 33, 300]):
@@ -82,8 +80,39 @@ def test_ragged_objects_and_edge_sizes():
             poses.append(synth.look_at_pose(synth.sphere_positions(rng, 1)[0]))
             views.append(dict(W=W, H=H, fx=float(max(W, H)), fy=float(max(W, H)), cx=W / 2, cy=H / 2, object=o,
                               pose=len(poses) - 1, flow_target=(len(poses) % 3, -1)))
-    s = synth.make_scene(objs, views, poses)
-    _full_check(s, n_flow=1)
+    return synth.make_scene(objs, views, poses)
+
+
+def test_ragged_objects_and_edge_sizes():
+    """K in {1, 2, 31, 33, 300} (300 crosses the 256-record staging chunk), images
+    from 1x1 to 65x9, several objects and views in one launch."""
+    _full_check(_ragged_scene(), n_flow=1)
+
+
+@pytest.mark.parametrize("deterministic", [False, True])
+def test_persistent_launch(deterministic):
+    """Persistent mode: resident CTAs pop (view, tile) items, most expensive first."""
+    _full_check(_ragged_scene(), n_flow=1, use_persistent=1, deterministic=deterministic)
+    _full_check(synth.config1(K=100, n_views=5, W=64, H=48), n_flow=1, use_persistent=1,
+                deterministic=deterministic)
+
+
+def test_persistent_matches_grid_launch_bitwise():
+    """Work items compute the same thing in either launch mode: forward planes and
+    the deterministic backward agree bit for bit."""
+    s = synth.config2(n_objects=6, views_per_object=2, sides=(32, 48, 64))
+    rng = np.random.default_rng(0)
+    res = []
+    for pers in (0, 1):
+        p = fmb.default_params(n_flow=0, use_persistent=pers, deterministic=1)
+        gpu, r, dev = gpu_forward(s, p)
+        gd, ga, gn, _ = synth.upstream_grads(np.random.default_rng(5), s.n_pixels, 1)
+        g = gpu_backward(r, dev, dict(g_depth=gd, g_alpha=ga, g_normal=gn.reshape(-1), g_flow=None))
+        res.append((gpu, g))
+    for k in ("depth", "alpha", "normal", "saved"):
+        assert np.array_equal(res[0][0][k], res[1][0][k]), k
+    for k in ("means", "chol", "weights", "poses"):
+        assert np.array_equal(res[0][1][k], res[1][1][k]), k
 
 
 def test_deterministic_mode_is_bitwise_reproducible():
@@ -124,8 +153,8 @@ def test_permutation_invariance():
     assert np.all(np.abs(a["alpha"] - b["alpha"]) <= 1e-5)
 
 
-def _sampled_full_size(scene, n_flow, n_per_view, seed=0, deterministic=False):
-    params = fmb.default_params(n_flow=n_flow, deterministic=int(deterministic))
+def _sampled_full_size(scene, n_flow, n_per_view, seed=0, deterministic=False, persistent=False):
+    params = fmb.default_params(n_flow=n_flow, deterministic=int(deterministic), use_persistent=int(persistent))
     gpu, r, dev = gpu_forward(scene, params)
     pix = sample_pixels(scene, n_per_view, seed)
     ref = oracle_forward_sampled(scene, pix, n_flow)
@@ -166,6 +195,10 @@ def test_large_K4096_8x1024x768_sampled():
 
 def test_ragged_batch_64_objects_sampled():
     _sampled_full_size(synth.config2(), n_flow=0, n_per_view=64, deterministic=True)
+
+
+def test_ragged_batch_64_objects_persistent_sampled():
+    _sampled_full_size(synth.config2(), n_flow=0, n_per_view=48, persistent=True)
 
 
 def test_device_status_is_clear_and_outputs_finite():
