@@ -180,6 +180,29 @@ size_t fmb_workspace_bytes(const fmb_params* params, int n_objects, const long l
  * outputs of that call are invalid).  The word is cleared by every render call. */
 fmb_status fmb_read_device_status(const void* workspace, int* h_status, fmb_stream_t stream);
 
+/* Adam hyper-parameters (Kingma & Ba): learning rate, moment decays, epsilon. */
+typedef struct {
+  float lr;
+  float beta1;
+  float beta2;
+  float eps;
+} fmb_adam_params;
+
+/*
+ * One fused Adam step, in place, over n fp32 parameters param[0..n) with
+ * gradients grad and moment buffers m, v (device, zero-initialised by the caller
+ * before the first step).  The paper optimises with Adam (Sec. 4).  Entries
+ * [positive_begin, n) are positive parameters (the Gaussian weights lambda): their
+ * gradient is taken with respect to log(param) and the update is multiplicative,
+ * so they stay positive.  step_counter: device int holding the number of steps
+ * taken so far; the call uses step+1 for the bias correction and then increments
+ * it on the device, so the call can be captured once in a CUDA graph and replayed.
+ * Pack the scene as one buffer [means | chol | weights] (3G + 6G + G floats) and
+ * pass positive_begin = 9G.  Returns FMB_ERR_INVALID_ARG on bad arguments.
+ */
+fmb_status fmb_adam_step(const fmb_adam_params* p, float* param, const float* grad, float* m, float* v,
+                         long long n, long long positive_begin, int* step_counter, fmb_stream_t stream);
+
 /* ALU throughput probe (a measurement utility, not part of the paper's method):
  * launches `blocks` CTAs of 256 threads that each run 8 independent chains of
  * `iters` operations of one kind -- 0: FP32 FMA, 1: packed FP32x2 FMA (two FMAs per

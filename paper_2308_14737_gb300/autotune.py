@@ -1,0 +1,101 @@
+"""Tile autotuner: times forward + backward of a batch layout for each candidate
+(rays per forward thread, backward threads, backward ray tile, launch mode) and
+keeps the fastest, cached in a JSON file keyed by the layout's shape class
+(Gaussian counts, pixel count, flow slots, normals, pose gradients)."""
+
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+import torch
+
+from . import fmb
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "fmb_gb300", "autotune.json")
+
+CANDIDATES = [dict(fwd_rays_per_thread=r, bwd_threads=t, bwd_ray_tile=t * m, use_persistent=p)
+              for r in (2, 4) for t in (128, 160) for m in (2, 3) for p in (0, 1)]
+
+TUNED_FIELDS = ("fwd_rays_per_thread", "bwd_threads", "bwd_ray_tile", "use_persistent")
+
+
+def layout_key(obj_offsets, views, params: fmb.FmbParams, want_pose: bool) -> str:
+    """Shape class of a batch: log2 buckets of the per-view pair counts and of the
+    total pixel count, plus the render options."""
+    offs = np.asarray(obj_offsets, dtype=np.int64)
+    Ks = sorted({int(offs[v["object"] + 1] - offs[v["object"]]) for v in views})
+    kb = sorted({int(np.log2(max(k, 1))) for k in Ks})
+    P = int(sum(v["W"] * v["H"] for v in views))
+    return json.dumps(dict(k=kb, p=int(np.log2(max(P, 1))), v=len(views), f=int(params.n_flow),
+                           n=int(params.want_normals), pose=bool(want_pose)), sort_keys=True)
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(path, cache):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def apply(params: fmb.FmbParams, choice: dict) -> fmb.FmbParams:
+    p = fmb.FmbParams()
+    ctypes_copy = {name: getattr(params, name) for name, _ in fmb.FmbParams._fields_}
+    for k, v in ctypes_copy.items():
+        setattr(p, k, v)
+    for k in TUNED_FIELDS:
+        if k in choice:
+            setattr(p, k, int(choice[k]))
+    return p
+
+
+def tune(obj_offsets, views, n_poses, params: fmb.FmbParams, means, chol, weights, poses, upstream: dict,
+         want_pose=True, candidates=None, reps=3, cache_path=None, force=False, device="cuda"):
+    """Returns (params with the fastest tile choice, timings).  ``upstream`` holds
+    device tensors g_depth, g_alpha, g_normal, g_flow for the backward."""
+    path = cache_path or os.environ.get("FMB_AUTOTUNE_CACHE", DEFAULT_CACHE)
+    key = layout_key(obj_offsets, views, params, want_pose)
+    cache = _load(path)
+    if key in cache and not force:
+        return apply(params, cache[key]["best"]), cache[key]["timings"]
+    cands = candidates or CANDIDATES
+    G = means.shape[0]
+    out = dict(means=torch.empty(G, 3, device=device), chol=torch.empty(G, 6, device=device),
+               weights=torch.empty(G, device=device),
+               poses=torch.empty(poses.shape[0], 12, device=device) if want_pose else None)
+    timings = []
+    for c in cands:
+        p = apply(params, c)
+        try:
+            r = fmb.Renderer(obj_offsets, views, n_poses, p, device=device)
+        except fmb.FmbError:
+            continue
+        step = lambda: (r.forward(means, chol, weights, poses),
+                        r.backward(means, chol, weights, poses, upstream["g_depth"], upstream["g_alpha"],
+                                   upstream["g_normal"], upstream["g_flow"], want_pose=want_pose, out=out))
+        step()
+        torch.cuda.synchronize(device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            step()
+        e1.record()
+        torch.cuda.synchronize(device)
+        timings.append(dict(choice=c, ms=e0.elapsed_time(e1) / reps))
+        del r
+    if not timings:
+        raise RuntimeError("no autotune candidate could be run")
+    best = min(timings, key=lambda x: x["ms"])
+    cache[key] = dict(best=best["choice"], timings=timings)
+    _store(path, cache)
+    return apply(params, best["choice"]), timings

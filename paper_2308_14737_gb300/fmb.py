@@ -40,6 +40,11 @@ class FmbView(ctypes.Structure):
                 ("flow_target", ctypes.c_int * 2), ("pix_offset", ctypes.c_longlong)]
 
 
+class FmbAdamParams(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float)]
+
+
 class FmbError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -69,6 +74,9 @@ def load_library(path: str = LIB_PATH):
     L.fmb_render_backward.restype = ctypes.c_int
     L.fmb_render_forward_noalloc.argtypes = [P, i, LL, fp, fp, fp, i, fp, i, V, fp, fp, fp, fp, fp, vp]
     L.fmb_render_forward_noalloc.restype = ctypes.c_int
+    L.fmb_adam_step.argtypes = [ctypes.POINTER(FmbAdamParams), fp, fp, fp, fp, ctypes.c_longlong, ctypes.c_longlong,
+                                fp, vp]
+    L.fmb_adam_step.restype = ctypes.c_int
     L.fmb_workspace_bytes.argtypes = [P, i, LL, i, V]
     L.fmb_workspace_bytes.restype = sz
     L.fmb_read_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
@@ -183,6 +191,15 @@ def fmb_render_backward(params, obj_offsets, means, chol, weights, poses, views,
                                  _ptr(saved), _ptr(g_depth), _ptr(g_alpha), _ptr(g_normal), _ptr(g_flow),
                                  _ptr(grad_means), _ptr(grad_chol), _ptr(grad_weights), _ptr(grad_poses),
                                  _ptr(workspace), workspace.numel(), _stream(stream)))
+
+
+def fmb_adam_step(adam: FmbAdamParams, param, grad, m, v, positive_begin, step_counter, stream=None):
+    """One fused Adam step over the flat buffers (see include/fmb.h)."""
+    L = load_library()
+    if step_counter.dtype != torch.int32:
+        raise ValueError("step_counter must be an int32 device tensor")
+    _check(L.fmb_adam_step(ctypes.byref(adam), _ptr(param), _ptr(grad), _ptr(m), _ptr(v), int(param.numel()),
+                           int(positive_begin), ctypes.c_void_p(step_counter.data_ptr()), _stream(stream)))
 
 
 def fmb_read_device_status(workspace, stream=None) -> int:

@@ -1,0 +1,28 @@
+"""Host-side logic of the autotuner (no GPU needed)."""
+
+from paper_2308_14737_gb300 import autotune, fmb, synth
+
+
+def test_layout_key_groups_by_shape_class():
+    from paper_2308_14737_gb300 import build
+
+    build.build()
+    p = fmb.default_params(n_flow=1)
+    a = synth.config1(K=100, n_views=16, W=320, H=240)
+    b = synth.config1(seed=5, K=110, n_views=16, W=320, H=240)  # same log2 buckets
+    c = synth.config1(K=400, n_views=16, W=320, H=240)
+    ka = autotune.layout_key(a.obj_offsets, a.views, p, True)
+    assert ka == autotune.layout_key(b.obj_offsets, b.views, p, True)
+    assert ka != autotune.layout_key(c.obj_offsets, c.views, p, True)
+    assert ka != autotune.layout_key(a.obj_offsets, a.views, p, False)
+
+
+def test_apply_sets_only_tuned_fields():
+    from paper_2308_14737_gb300 import build
+
+    build.build()
+    p = fmb.default_params(n_flow=2, want_normals=0)
+    q = autotune.apply(p, dict(fwd_rays_per_thread=4, bwd_threads=128, bwd_ray_tile=256, use_persistent=1))
+    assert (q.fwd_rays_per_thread, q.bwd_threads, q.bwd_ray_tile, q.use_persistent) == (4, 128, 256, 1)
+    assert (q.n_flow, q.want_normals) == (2, 0) and abs(q.beta1 - 21.4) < 1e-6
+    assert p.fwd_rays_per_thread == 0  # the input is not modified
