@@ -11,6 +11,10 @@ steps, outside the timed events.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
+The batched arm's tiles come from the autotuner, run before the timed region; set
+FMB_AUTOTUNE_CACHE to a file to reuse a previous run's choice (e.g. when
+profiling, so the profiled run launches no tuning candidates).
+
 Prints one JSON line.  Under torchrun (N > 1) every rank renders its own replica
 of the batch (weak scaling) and rank 0 prints the aggregate.
 """
@@ -208,7 +212,8 @@ def run_gpu(args):
     tuned_params, tune_timings = autotune.tune(
         s.obj_offsets, s.views, len(s.poses), params, means, chol, weights, poses,
         dict(g_depth=gd, g_alpha=ga, g_normal=gn, g_flow=gf), want_pose=True,
-        cache_path=os.path.join(tempfile.gettempdir(), f"fmb_autotune_{os.getpid()}.json"))
+        cache_path=os.environ.get("FMB_AUTOTUNE_CACHE") or
+        os.path.join(tempfile.gettempdir(), f"fmb_autotune_{os.getpid()}.json"))
     batched = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), tuned_params, device=dev)
     side = torch.cuda.Stream(dev)
     side.wait_stream(torch.cuda.current_stream(dev))

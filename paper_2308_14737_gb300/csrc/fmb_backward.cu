@@ -32,10 +32,14 @@
 namespace fmb {
 
 constexpr int kBwdMaxThreads = 160;
+#ifndef FMB_BWD_UNROLL
+#define FMB_BWD_UNROLL 2  // pair-loop unrolling (independent rays the scheduler can interleave)
+#endif
 #ifndef FMB_BWD_MIN_BLOCKS
 #define FMB_BWD_MIN_BLOCKS 3
 #endif
-constexpr int kBwdMinBlocks = FMB_BWD_MIN_BLOCKS;  // resident CTAs per SM the register budget targets
+constexpr int kBwdMinBlocks = FMB_BWD_MIN_BLOCKS;
+constexpr int kBwdUnroll = FMB_BWD_UNROLL;  // resident CTAs per SM the register budget targets
 constexpr int kAccFloats = 38;  // 19 packed accumulators per thread in the reduction
 
 // Per-thread gradient sums of the thread's two Gaussians (one per lane).
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
     const f2 K2v = dup(k.K2), K3v = dup(k.K3), B1v = dup(k.beta1), nB1v = dup(-k.beta1), nB2E = dup(-k.b2e);
     const f2 tiny = dup(1e-30f);
     const ulonglong2* rays = reinterpret_cast<const ulonglong2*>(bsm);
-#pragma unroll 2
+#pragma unroll kBwdUnroll
     for (int r = sg; r < nr; r += S) bwd_pair2<NORMALS>(A, gr, rays + kRayRec2 * r, K2v, K3v, B1v, nB1v, nB2E, tiny);
   }
   __syncthreads();  // ray records are dead; the shared memory is reused below
