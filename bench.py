@@ -62,7 +62,7 @@ def csrc_sha256() -> str:
 
     d = os.path.join(ROOT, "paper_2308_14737_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("fmb_backward.cu", "fmb_internal.cuh"):
+    for name in ("fmb_backward.cu", "fmb_internal.cuh", "fmb_f32x2.cuh"):
         h.update(name.encode())
         with open(os.path.join(d, name), "rb") as fh:
             h.update(fh.read())
