@@ -11,7 +11,11 @@ multi-view scene the same way the batched output planes are laid out:
 * ``flow``: per view a (n_flow, 2, H*W) block at ``2 * n_flow * pix_offset``
   (pixels; a slot whose target pose is -1 is zero);
 * ``saved``: per view a (3, H*W) block at ``3 * pix_offset`` holding
-  (log-sum-exp of e_i in natural log, sum of delta_i, |N|).
+  (log-sum-exp of e_i in natural log, sum of delta_i, |N|); for the
+  alpha-compositing variant the first entry is W = sum of the weights instead.
+
+``variant`` selects the weights of Eq. 3: 0 = two-parameter model (Eq. 7),
+1 = alpha compositing (Eq. 9-10, Sec. 3.3).
 
 Parity unpinned: nothing.  Every function here is pinned by
 ``tests/test_oracle_pins.py`` (closed forms, brute force, invariants) and its
@@ -64,6 +68,10 @@ def lib():
         L.fmbo_forward.restype = ctypes.c_int
         L.fmbo_backward.argtypes = common + [dp, dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_int]
         L.fmbo_backward.restype = ctypes.c_int
+        L.fmbo_forward_ac.argtypes = L.fmbo_forward.argtypes
+        L.fmbo_forward_ac.restype = ctypes.c_int
+        L.fmbo_backward_ac.argtypes = L.fmbo_backward.argtypes
+        L.fmbo_backward_ac.restype = ctypes.c_int
         L.fmbo_max_threads.argtypes = []
         L.fmbo_max_threads.restype = ctypes.c_int
         _lib = L
@@ -85,7 +93,7 @@ def _f64(a):
 
 
 def render_view(means, chol, weights, pose, target_poses, cam, beta1=BETA1, beta2=BETA2, eta=ETA,
-                pixels=None, n_threads=0):
+                pixels=None, n_threads=0, variant=0):
     """Forward render of one view.
 
     ``cam`` = (W, H, fx, fy, cx, cy); ``target_poses`` is a (T, 12) array (T <= 2).
@@ -105,7 +113,8 @@ def render_view(means, chol, weights, pose, target_poses, cam, beta1=BETA1, beta
         n = pix.shape[0]
     out = dict(depth=np.zeros(n), alpha=np.zeros(n), normal=np.zeros((n, 3)),
                flow=np.zeros((n, max(T, 1), 2)), saved=np.zeros((n, 3)))
-    rc = lib().fmbo_forward(
+    fn = lib().fmbo_forward_ac if variant == 1 else lib().fmbo_forward
+    rc = fn(
         K, _dp(means), _dp(chol), _dp(weights), _dp(pose), T, _dp(tp) if T else None,
         int(W), int(H), float(fx), float(fy), float(cx), float(cy), float(beta1), float(beta2), float(eta),
         n, pix.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)) if pix is not None else None,
@@ -118,7 +127,7 @@ def render_view(means, chol, weights, pose, target_poses, cam, beta1=BETA1, beta
 
 
 def backward_view(means, chol, weights, pose, target_poses, cam, g_depth=None, g_alpha=None, g_normal=None,
-                  g_flow=None, beta1=BETA1, beta2=BETA2, eta=ETA, pixels=None, n_threads=0):
+                  g_flow=None, beta1=BETA1, beta2=BETA2, eta=ETA, pixels=None, n_threads=0, variant=0):
     """Analytic FP64 adjoint of one view.  Upstream layouts follow ``render_view``:
     g_depth (n,), g_alpha (n,), g_normal (n, 3), g_flow (n, T, 2).  Returns a dict
     with means (K, 3), chol (K, 6), weights (K,), pose (12,), target_poses (T, 12)."""
@@ -139,7 +148,8 @@ def backward_view(means, chol, weights, pose, target_poses, cam, g_depth=None, g
     gf = None if (g_flow is None or T == 0) else _f64(g_flow).reshape(n, T, 2)
     out = dict(means=np.zeros((K, 3)), chol=np.zeros((K, 6)), weights=np.zeros(K), pose=np.zeros(12),
                target_poses=np.zeros((max(T, 1), 12)))
-    rc = lib().fmbo_backward(
+    fn = lib().fmbo_backward_ac if variant == 1 else lib().fmbo_backward
+    rc = fn(
         K, _dp(means), _dp(chol), _dp(weights), _dp(pose), T, _dp(tp) if T else None,
         int(W), int(H), float(fx), float(fy), float(cx), float(cy), float(beta1), float(beta2), float(eta),
         n, pix.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)) if pix is not None else None,
@@ -162,7 +172,7 @@ def _cam(v):
     return (v["W"], v["H"], v["fx"], v["fy"], v["cx"], v["cy"])
 
 
-def render_scene(scene, n_flow=1, beta1=BETA1, beta2=BETA2, eta=ETA, n_threads=0):
+def render_scene(scene, n_flow=1, beta1=BETA1, beta2=BETA2, eta=ETA, n_threads=0, variant=0):
     """Forward render of every view of a ``synth.Scene`` into batched planes
     (layouts in the module docstring).  Returns float64 arrays."""
     P = scene.n_pixels
@@ -174,7 +184,7 @@ def render_scene(scene, n_flow=1, beta1=BETA1, beta2=BETA2, eta=ETA, n_threads=0
         used = [j for j in ft if j >= 0]
         tp = scene.poses[used] if used else None
         r = render_view(scene.means[sl], scene.chol[sl], scene.weights[sl], scene.poses[v["pose"]], tp, _cam(v),
-                        beta1, beta2, eta, n_threads=n_threads)
+                        beta1, beta2, eta, n_threads=n_threads, variant=variant)
         Pv = v["W"] * v["H"]
         o = v["pix_offset"]
         out["depth"][o:o + Pv] = r["depth"]
@@ -192,7 +202,7 @@ def render_scene(scene, n_flow=1, beta1=BETA1, beta2=BETA2, eta=ETA, n_threads=0
 
 
 def backward_scene(scene, g_depth, g_alpha, g_normal, g_flow, n_flow=1, beta1=BETA1, beta2=BETA2, eta=ETA,
-                   n_threads=0):
+                   n_threads=0, variant=0):
     """Adjoint over every view of a scene with upstream gradients in the batched
     plane layout.  Returns grads for means (sum K, 3), chol (sum K, 6), weights
     (sum K,) and poses (n_poses, 12), float64."""
@@ -213,7 +223,7 @@ def backward_scene(scene, g_depth, g_alpha, g_normal, g_flow, n_flow=1, beta1=BE
         r = backward_view(scene.means[sl], scene.chol[sl], scene.weights[sl], scene.poses[v["pose"]], tp, _cam(v),
                           None if g_depth is None else np.asarray(g_depth)[o:o + Pv],
                           None if g_alpha is None else np.asarray(g_alpha)[o:o + Pv],
-                          gn, gf, beta1, beta2, eta, n_threads=n_threads)
+                          gn, gf, beta1, beta2, eta, n_threads=n_threads, variant=variant)
         g["means"][sl] += r["means"]
         g["chol"][sl] += r["chol"]
         g["weights"][sl] += r["weights"]

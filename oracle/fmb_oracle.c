@@ -44,6 +44,22 @@
  * Saved per-pixel values (for comparison with the CUDA path's saved planes):
  *   saved[0] = log sum_i exp(e_i)  (natural log), saved[1] = sum_i delta_i,
  *   saved[2] = |N|.
+ *
+ * Alpha-compositing variant (Sec. 3.3, "zero parameter model"; the *_ac entry
+ * points): the weights of Eq. 3 become
+ *   w_i = T_i (1 - exp(-delta_i))                                        (Eq. 9)
+ *   T_i = exp(-sum_j delta_j [t_j < t_i])                                (Eq. 10)
+ * evaluated literally: for every i, a sum over all j with the strict indicator
+ * (so Gaussians at exactly equal depth do not attenuate each other).  Depth and
+ * normal use Eq. 3 with these w_i (normalised by W = sum_i w_i; W = 0 gives
+ * D = 0 and N = 0); alpha is Eq. 8 as before.  beta1, beta2 and eta are unused.
+ * saved[0] = W for this variant.  Its adjoint, with wbar_i the upstream gradient
+ * of w_i:
+ *   wbar_i     = (Dbar (t_i - D) + Nbar . (n_i - N)) / W
+ *   deltabar_k = wbar_k T_k exp(-delta_k) - sum_{i: t_k < t_i} wbar_i w_i
+ *                + Abar exp(-sum delta)
+ *   dbar_k = deltabar_k delta_k,  tbar_k (through Eq. 3) = Dbar w_k / W
+ * (the indicator is piecewise constant in t, so it contributes nothing).
  */
 
 #include <math.h>
@@ -88,6 +104,7 @@ typedef struct {
   int W, H;
   double fx, fy, cx, cy;
   double beta1, beta2, eta;
+  int variant; /* 0: two-parameter weights (Eq. 7); 1: alpha compositing (Eq. 9-10) */
 } fmbo_camera;
 
 /* Ray of pixel p: camera-frame unit direction, world direction, origin. */
@@ -150,31 +167,44 @@ typedef struct {
 
 /* Forward for one ray.  ``pairs`` (size K) receives every pair's values and
  * ``what`` the normalised weights w_i / sum w, so that the backward pass can reuse
- * them. */
+ * them; ``trans`` (alpha compositing only) the transmittances T_i. */
 static void forward_ray(int K, const double* means, const double* chol, const double* weights,
                         const fmbo_camera* cam, const double* R, const double* v, const double* o,
                         const double* pix_xy, int n_targets, const double* target_poses,
-                        pair_t* pairs, double* what, ray_out_t* out) {
+                        pair_t* pairs, double* what, double* trans, ray_out_t* out) {
   double m = -INFINITY;
   for (int i = 0; i < K; ++i) {
     eval_pair(means + 3 * i, chol + 6 * i, weights[i], v, o, cam, &pairs[i]);
     if (pairs[i].e > m) m = pairs[i].e;
   }
   double Sw = 0.0, Sdelta = 0.0;
-  for (int i = 0; i < K; ++i) {
-    what[i] = exp(pairs[i].e - m);
-    Sw += what[i];
-    Sdelta += pairs[i].delta;
+  if (cam->variant == 1) {
+    /* Eq. 10 and Eq. 9, literally: T_i from every j strictly in front of i */
+    for (int i = 0; i < K; ++i) {
+      double S = 0.0;
+      for (int j = 0; j < K; ++j)
+        if (pairs[j].t < pairs[i].t) S += pairs[j].delta;
+      trans[i] = exp(-S);
+      what[i] = trans[i] * -expm1(-pairs[i].delta);
+      Sw += what[i];
+      Sdelta += pairs[i].delta;
+    }
+  } else {
+    for (int i = 0; i < K; ++i) {
+      what[i] = exp(pairs[i].e - m);
+      Sw += what[i];
+      Sdelta += pairs[i].delta;
+    }
   }
   double D = 0.0, N[3] = {0, 0, 0};
   for (int i = 0; i < K; ++i) {
-    what[i] /= Sw;
+    what[i] = Sw > 0.0 ? what[i] / Sw : 0.0;
     D += what[i] * pairs[i].t;
     for (int k = 0; k < 3; ++k) N[k] += what[i] * pairs[i].n[k];
   }
   out->m = m;
   out->Sw = Sw;
-  out->lse = m + log(Sw);
+  out->lse = cam->variant == 1 ? Sw : m + log(Sw);
   out->D = D;
   out->Sdelta = Sdelta;
   out->A = -expm1(-Sdelta);
@@ -208,15 +238,15 @@ static int check_args(int K, int W, int H, int n_targets, double fx, double fy, 
  * frame), flow[n][n_targets][2] (pixels), saved[n][3].  Any output may be NULL.
  * Returns 0, or 1 on invalid arguments.
  */
-int fmbo_forward(int K, const double* means, const double* chol, const double* weights,
-                 const double* pose, int n_targets, const double* target_poses,
-                 int W, int H, double fx, double fy, double cx, double cy,
-                 double beta1, double beta2, double eta,
-                 long long n_pix, const long long* pix,
-                 double* depth, double* alpha, double* normal, double* flow, double* saved,
-                 int n_threads) {
+static int forward_impl(int variant, int K, const double* means, const double* chol, const double* weights,
+                        const double* pose, int n_targets, const double* target_poses,
+                        int W, int H, double fx, double fy, double cx, double cy,
+                        double beta1, double beta2, double eta,
+                        long long n_pix, const long long* pix,
+                        double* depth, double* alpha, double* normal, double* flow, double* saved,
+                        int n_threads) {
   if (check_args(K, W, H, n_targets, fx, fy, eta)) return 1;
-  fmbo_camera cam = {W, H, fx, fy, cx, cy, beta1, beta2, eta};
+  fmbo_camera cam = {W, H, fx, fy, cx, cy, beta1, beta2, eta, variant};
   if (!pix) n_pix = (long long)W * H;
   const double* R = pose;
   const double* t = pose + 9;
@@ -230,7 +260,8 @@ int fmbo_forward(int K, const double* means, const double* chol, const double* w
   {
     pair_t* pairs = (pair_t*)malloc(sizeof(pair_t) * (size_t)K);
     double* what = (double*)malloc(sizeof(double) * (size_t)K);
-    if (!pairs || !what) {
+    double* trans = (double*)malloc(sizeof(double) * (size_t)K);
+    if (!pairs || !what || !trans) {
 #pragma omp atomic write
       failed = 1;
     } else {
@@ -240,7 +271,8 @@ int fmbo_forward(int K, const double* means, const double* chol, const double* w
         double vcam[3], v[3], o[3], pxy[2];
         ray_out_t out;
         pixel_ray(&cam, R, t, p, vcam, v, o, pxy);
-        forward_ray(K, means, chol, weights, &cam, R, v, o, pxy, n_targets, target_poses, pairs, what, &out);
+        forward_ray(K, means, chol, weights, &cam, R, v, o, pxy, n_targets, target_poses, pairs, what, trans,
+                    &out);
         if (depth) depth[n] = out.D;
         if (alpha) alpha[n] = out.A;
         if (normal)
@@ -259,8 +291,32 @@ int fmbo_forward(int K, const double* means, const double* chol, const double* w
     }
     free(pairs);
     free(what);
+    free(trans);
   }
   return failed ? 2 : 0;
+}
+
+int fmbo_forward(int K, const double* means, const double* chol, const double* weights,
+                 const double* pose, int n_targets, const double* target_poses,
+                 int W, int H, double fx, double fy, double cx, double cy,
+                 double beta1, double beta2, double eta,
+                 long long n_pix, const long long* pix,
+                 double* depth, double* alpha, double* normal, double* flow, double* saved,
+                 int n_threads) {
+  return forward_impl(0, K, means, chol, weights, pose, n_targets, target_poses, W, H, fx, fy, cx, cy, beta1,
+                      beta2, eta, n_pix, pix, depth, alpha, normal, flow, saved, n_threads);
+}
+
+/* Alpha-compositing variant (Eq. 9-10); beta1, beta2 and eta are ignored. */
+int fmbo_forward_ac(int K, const double* means, const double* chol, const double* weights,
+                    const double* pose, int n_targets, const double* target_poses,
+                    int W, int H, double fx, double fy, double cx, double cy,
+                    double beta1, double beta2, double eta,
+                    long long n_pix, const long long* pix,
+                    double* depth, double* alpha, double* normal, double* flow, double* saved,
+                    int n_threads) {
+  return forward_impl(1, K, means, chol, weights, pose, n_targets, target_poses, W, H, fx, fy, cx, cy, beta1,
+                      beta2, eta, n_pix, pix, depth, alpha, normal, flow, saved, n_threads);
 }
 
 /* Accumulators of the backward pass (one set per thread). */
@@ -276,9 +332,9 @@ typedef struct {
 static void backward_ray(int K, const double* chol, const double* weights, const fmbo_camera* cam,
                          const double* R, const double* tpose, const double* vcam, const double* v,
                          const double* o, int n_targets, const double* target_poses,
-                         const pair_t* pairs, const double* what, const ray_out_t* out,
+                         const pair_t* pairs, const double* what, const double* trans, const ray_out_t* out,
                          double gD_in, double gA, const double* gN, const double* gF,
-                         double* ebar, grads_t* acc) {
+                         double* ebar, double* wbar, grads_t* acc) {
   double pbar[3] = {0, 0, 0};
   double vbar[3] = {0, 0, 0};
   double obar[3] = {0, 0, 0};
@@ -326,24 +382,48 @@ static void backward_ray(int K, const double* chol, const double* weights, const
     }
   }
 
-  /* blend: what_i = softmax(e)_i; D = sum what t; N = sum what n.
-   * what_bar_i = gD t_i + Nbar . n_i;  e_bar_i = what_i (what_bar_i - sum_j what_j what_bar_j) */
-  double sbar = 0.0;
-  for (int i = 0; i < K; ++i) {
-    double wb = gD * pairs[i].t + dot3(Nbar, pairs[i].n);
-    ebar[i] = wb;
-    sbar += what[i] * wb;
-  }
-  for (int i = 0; i < K; ++i) ebar[i] = what[i] * (ebar[i] - sbar);
-
   /* alpha: A = 1 - exp(-S), S = sum delta_i */
   double Sbar = gA * exp(-out->Sdelta);
 
+  if (cam->variant == 1) {
+    /* alpha compositing: D = sum w t / W, N = sum w n / W with w_i = T_i (1 - exp(-delta_i)),
+     * T_i = exp(-sum_j delta_j [t_j < t_i]); ebar[k] receives dbar_k = deltabar_k delta_k */
+    const double Wt = out->Sw;
+    for (int i = 0; i < K; ++i) {
+      double Nd[3];
+      for (int k = 0; k < 3; ++k) Nd[k] = pairs[i].n[k] - out->N[k];
+      wbar[i] = Wt > 0.0 ? (gD * (pairs[i].t - out->D) + dot3(Nbar, Nd)) / Wt : 0.0;
+    }
+    for (int k = 0; k < K; ++k) {
+      double behind = 0.0; /* sum over i strictly behind k of wbar_i w_i */
+      for (int i = 0; i < K; ++i)
+        if (pairs[k].t < pairs[i].t) behind += wbar[i] * what[i] * Wt;
+      double deltabar = wbar[k] * trans[k] * exp(-pairs[k].delta) - behind + Sbar;
+      ebar[k] = deltabar * pairs[k].delta;
+    }
+  } else {
+    /* blend: what_i = softmax(e)_i; D = sum what t; N = sum what n.
+     * what_bar_i = gD t_i + Nbar . n_i;  e_bar_i = what_i (what_bar_i - sum_j what_j what_bar_j) */
+    double sbar = 0.0;
+    for (int i = 0; i < K; ++i) {
+      double wb = gD * pairs[i].t + dot3(Nbar, pairs[i].n);
+      ebar[i] = wb;
+      sbar += what[i] * wb;
+    }
+    for (int i = 0; i < K; ++i) ebar[i] = what[i] * (ebar[i] - sbar);
+  }
+
   for (int i = 0; i < K; ++i) {
     const pair_t* s = &pairs[i];
-    /* e = beta1 d - (beta2/eta) t ; delta = exp(d) */
-    double dbar = cam->beta1 * ebar[i] + Sbar * s->delta;
-    double tbar_i = gD * what[i] - (cam->beta2 / cam->eta) * ebar[i];
+    double dbar, tbar_i;
+    if (cam->variant == 1) {
+      dbar = ebar[i];
+      tbar_i = gD * what[i];
+    } else {
+      /* e = beta1 d - (beta2/eta) t ; delta = exp(d) */
+      dbar = cam->beta1 * ebar[i] + Sbar * s->delta;
+      tbar_i = gD * what[i] - (cam->beta2 / cam->eta) * ebar[i];
+    }
     /* n = g/|g|, nbar = what_i Nbar */
     double gbar[3] = {0, 0, 0};
     if (s->gnorm > 0.0) {
@@ -432,16 +512,16 @@ static void backward_ray(int K, const double* chol, const double* weights, const
  * is deterministic for a fixed ``n_threads``.  Returns 0, 1 on invalid arguments,
  * 2 on allocation failure.
  */
-int fmbo_backward(int K, const double* means, const double* chol, const double* weights,
-                  const double* pose, int n_targets, const double* target_poses,
-                  int W, int H, double fx, double fy, double cx, double cy,
-                  double beta1, double beta2, double eta,
-                  long long n_pix, const long long* pix,
-                  const double* g_depth, const double* g_alpha, const double* g_normal, const double* g_flow,
-                  double* grad_means, double* grad_chol, double* grad_weights,
-                  double* grad_pose, double* grad_target_poses, int n_threads) {
+static int backward_impl(int variant, int K, const double* means, const double* chol, const double* weights,
+                         const double* pose, int n_targets, const double* target_poses,
+                         int W, int H, double fx, double fy, double cx, double cy,
+                         double beta1, double beta2, double eta,
+                         long long n_pix, const long long* pix,
+                         const double* g_depth, const double* g_alpha, const double* g_normal,
+                         const double* g_flow, double* grad_means, double* grad_chol, double* grad_weights,
+                         double* grad_pose, double* grad_target_poses, int n_threads) {
   if (check_args(K, W, H, n_targets, fx, fy, eta)) return 1;
-  fmbo_camera cam = {W, H, fx, fy, cx, cy, beta1, beta2, eta};
+  fmbo_camera cam = {W, H, fx, fy, cx, cy, beta1, beta2, eta, variant};
   if (!pix) n_pix = (long long)W * H;
   const double* R = pose;
   const double* t = pose + 9;
@@ -472,7 +552,9 @@ int fmbo_backward(int K, const double* means, const double* chol, const double* 
       pair_t* pairs = (pair_t*)malloc(sizeof(pair_t) * (size_t)K);
       double* what = (double*)malloc(sizeof(double) * (size_t)K);
       double* ebar = (double*)malloc(sizeof(double) * (size_t)K);
-      if (!pairs || !what || !ebar) {
+      double* trans = (double*)malloc(sizeof(double) * (size_t)K);
+      double* wbar = (double*)malloc(sizeof(double) * (size_t)K);
+      if (!pairs || !what || !ebar || !trans || !wbar) {
 #pragma omp atomic write
         failed = 1;
       } else {
@@ -482,7 +564,8 @@ int fmbo_backward(int K, const double* means, const double* chol, const double* 
           double vcam[3], v[3], o[3], pxy[2];
           ray_out_t out;
           pixel_ray(&cam, R, t, p, vcam, v, o, pxy);
-          forward_ray(K, means, chol, weights, &cam, R, v, o, pxy, n_targets, target_poses, pairs, what, &out);
+          forward_ray(K, means, chol, weights, &cam, R, v, o, pxy, n_targets, target_poses, pairs, what, trans,
+                      &out);
           double gD = g_depth ? g_depth[n] : 0.0;
           double gA = g_alpha ? g_alpha[n] : 0.0;
           double gN[3] = {0, 0, 0};
@@ -494,13 +577,15 @@ int fmbo_backward(int K, const double* means, const double* chol, const double* 
               gF[2 * j] = g_flow[(n * n_targets + j) * 2];
               gF[2 * j + 1] = g_flow[(n * n_targets + j) * 2 + 1];
             }
-          backward_ray(K, chol, weights, &cam, R, t, vcam, v, o, n_targets, target_poses, pairs, what, &out,
-                       gD, gA, gN, gF, ebar, acc);
+          backward_ray(K, chol, weights, &cam, R, t, vcam, v, o, n_targets, target_poses, pairs, what, trans,
+                       &out, gD, gA, gN, gF, ebar, wbar, acc);
         }
       }
       free(pairs);
       free(what);
       free(ebar);
+      free(trans);
+      free(wbar);
     }
   }
   if (!failed) {
@@ -530,6 +615,33 @@ int fmbo_backward(int K, const double* means, const double* chol, const double* 
   }
   free(accs);
   return failed ? 2 : 0;
+}
+
+int fmbo_backward(int K, const double* means, const double* chol, const double* weights,
+                  const double* pose, int n_targets, const double* target_poses,
+                  int W, int H, double fx, double fy, double cx, double cy,
+                  double beta1, double beta2, double eta,
+                  long long n_pix, const long long* pix,
+                  const double* g_depth, const double* g_alpha, const double* g_normal, const double* g_flow,
+                  double* grad_means, double* grad_chol, double* grad_weights,
+                  double* grad_pose, double* grad_target_poses, int n_threads) {
+  return backward_impl(0, K, means, chol, weights, pose, n_targets, target_poses, W, H, fx, fy, cx, cy, beta1,
+                       beta2, eta, n_pix, pix, g_depth, g_alpha, g_normal, g_flow, grad_means, grad_chol,
+                       grad_weights, grad_pose, grad_target_poses, n_threads);
+}
+
+/* Adjoint of the alpha-compositing variant (Eq. 9-10); beta1, beta2, eta ignored. */
+int fmbo_backward_ac(int K, const double* means, const double* chol, const double* weights,
+                     const double* pose, int n_targets, const double* target_poses,
+                     int W, int H, double fx, double fy, double cx, double cy,
+                     double beta1, double beta2, double eta,
+                     long long n_pix, const long long* pix,
+                     const double* g_depth, const double* g_alpha, const double* g_normal, const double* g_flow,
+                     double* grad_means, double* grad_chol, double* grad_weights,
+                     double* grad_pose, double* grad_target_poses, int n_threads) {
+  return backward_impl(1, K, means, chol, weights, pose, n_targets, target_poses, W, H, fx, fy, cx, cy, beta1,
+                       beta2, eta, n_pix, pix, g_depth, g_alpha, g_normal, g_flow, grad_means, grad_chol,
+                       grad_weights, grad_pose, grad_target_poses, n_threads);
 }
 
 /* Number of OpenMP threads a parallel region would use (1 without OpenMP). */

@@ -1,7 +1,7 @@
 """Independent float64 PyTorch-CPU restatement of the renderer (test infrastructure).
 
 A second, separately written evaluation of the same equations as ``fmb_oracle.c``
-(Sec. 3.1-3.2, Eq. 2, 3, 4, 7, 8, 17; flow of Sec. 5), vectorised over pixels x
+(Sec. 3.1-3.3, Eq. 2, 3, 4, 7, 8, 9, 10, 17; flow of Sec. 5), vectorised over pixels x
 Gaussians, whose gradients come from autograd instead of a hand-derived adjoint.
 It exists only to cross-check the oracle's analytic adjoint on tiny inputs.  Only
 the test suite imports it.
@@ -12,8 +12,10 @@ from __future__ import annotations
 import torch
 
 
-def render(means, chol, weights, R, t, target_R, target_t, cam, beta1=21.4, beta2=3.14, eta=1.0):
-    """All tensors float64.  means (K,3), chol (K,6) packed (L00,L10,L11,L20,L21,L22),
+def render(means, chol, weights, R, t, target_R, target_t, cam, beta1=21.4, beta2=3.14, eta=1.0, variant=0):
+    """``variant`` 0: two-parameter weights (Eq. 7); 1: alpha compositing (Eq. 9-10,
+    transmittance from a (P, K, K) indicator matrix of "j strictly in front of i").
+    All tensors float64.  means (K,3), chol (K,6) packed (L00,L10,L11,L20,L21,L22),
     weights (K,), R (3,3) and t (3,) world->camera, target_R (T,3,3), target_t (T,3),
     cam = (W, H, fx, fy, cx, cy).  Returns depth (P,), alpha (P,), normal (P,3) in the
     camera frame, flow (P,T,2)."""
@@ -44,8 +46,14 @@ def render(means, chol, weights, R, t, target_R, target_t, cam, beta1=21.4, beta
     q = (r * g).sum(-1)
     d = -0.5 * q + torch.log(weights)[None]
     delta = torch.exp(d)
-    e = beta1 * d - (beta2 / eta) * tt
-    w = torch.softmax(e, dim=1)
+    if variant == 1:
+        front = (tt[:, None, :] < tt[:, :, None]).to(torch.float64)  # [p, i, j] = 1 if t_j < t_i
+        trans = torch.exp(-torch.einsum("pij,pj->pi", front, delta))
+        wa = trans * -torch.expm1(-delta)
+        w = wa / wa.sum(1, keepdim=True)
+    else:
+        e = beta1 * d - (beta2 / eta) * tt
+        w = torch.softmax(e, dim=1)
     depth = (w * tt).sum(1)
     alpha = -torch.expm1(-delta.sum(1))
     n = g / g.norm(dim=-1, keepdim=True)

@@ -27,8 +27,8 @@ def tiny_scene(seed, K=3):
     return mu, chol.astype(np.float64), lam.astype(np.float64), pose, tgt, ups
 
 
-def loss(o, mu, chol, lam, pose, tgt, ups):
-    r = o.render_view(mu, chol, lam, pose, tgt[None], CAM)
+def loss(o, mu, chol, lam, pose, tgt, ups, variant=0):
+    r = o.render_view(mu, chol, lam, pose, tgt[None], CAM, variant=variant)
     return (np.sum(ups["g_depth"] * r["depth"]) + np.sum(ups["g_alpha"] * r["alpha"])
             + np.sum(ups["g_normal"] * r["normal"]) + np.sum(ups["g_flow"] * r["flow"]))
 
@@ -49,11 +49,14 @@ def fd_grad(f, x, h_rel=1e-6):
     return g
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_adjoint_matches_central_differences(oracle_mod, seed):
+def test_adjoint_matches_central_differences(oracle_mod, seed, variant):
+    """variant 1 (alpha compositing): the hit depths of the tiny scenes are far
+    apart, so no finite-difference step crosses a change of depth order."""
     mu, chol, lam, pose, tgt, ups = tiny_scene(seed)
-    g = oracle_mod.backward_view(mu, chol, lam, pose, tgt[None], CAM, **ups)
-    f = lambda: loss(oracle_mod, mu, chol, lam, pose, tgt, ups)
+    g = oracle_mod.backward_view(mu, chol, lam, pose, tgt[None], CAM, **ups, variant=variant)
+    f = lambda: loss(oracle_mod, mu, chol, lam, pose, tgt, ups, variant)
     checks = [("means", mu, g["means"]), ("chol", chol, g["chol"]), ("weights", lam, g["weights"]),
               ("pose", pose, g["pose"]), ("target", tgt, g["target_poses"][0])]
     for name, x, ga in checks:
@@ -63,16 +66,17 @@ def test_adjoint_matches_central_differences(oracle_mod, seed):
         assert err <= 1e-6 * scale, (name, err, scale)
 
 
-def test_adjoint_matches_torch_autograd(oracle_mod):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_adjoint_matches_torch_autograd(oracle_mod, variant):
     for seed in (3, 4):
         mu, chol, lam, pose, tgt, ups = tiny_scene(seed, K=4)
-        g = oracle_mod.backward_view(mu, chol, lam, pose, tgt[None], CAM, **ups)
+        g = oracle_mod.backward_view(mu, chol, lam, pose, tgt[None], CAM, **ups, variant=variant)
         f = lambda a: torch.tensor(a, dtype=torch.float64, requires_grad=True)
         tm, tc, tl = f(mu), f(chol), f(lam)
         tR, tt = f(pose[:9].reshape(3, 3)), f(pose[9:])
         gR, gt = f(tgt[:9].reshape(3, 3)[None]), f(tgt[9:][None])
-        d, a, n, fl = torch_ref.render(tm, tc, tl, tR, tt, gR, gt, CAM)
-        r = oracle_mod.render_view(mu, chol, lam, pose, tgt[None], CAM)
+        d, a, n, fl = torch_ref.render(tm, tc, tl, tR, tt, gR, gt, CAM, variant=variant)
+        r = oracle_mod.render_view(mu, chol, lam, pose, tgt[None], CAM, variant=variant)
         np.testing.assert_allclose(d.detach().numpy(), r["depth"], rtol=1e-12)
         np.testing.assert_allclose(a.detach().numpy(), r["alpha"], rtol=1e-12)
         np.testing.assert_allclose(n.detach().numpy(), r["normal"], atol=1e-12)

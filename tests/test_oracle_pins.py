@@ -298,3 +298,92 @@ def test_large_beta1_selects_densest_hit(oracle_mod):
     assert ok.sum() > 10
     rows = np.arange(len(ts))[ok]
     np.testing.assert_allclose(r["depth"][ok], ts[rows, np.argmax(ds, 1)[ok]], atol=1e-9)
+
+
+# ---------------------------------------------------------------- alpha compositing
+# Pins of the zero-parameter variant (Sec. 3.3, Eq. 9-10): w_i = T_i (1 - e^-delta_i),
+# T_i = exp(-sum of delta_j strictly in front of i).
+
+
+def test_ac_single_gaussian(oracle_mod):
+    """K = 1: T = 1, so W = 1 - e^-delta and the depth is the hit depth itself; on a
+    ray through an isotropic centre delta = lambda and t = |mu - o|."""
+    pose = synth.look_at_pose((1.0, 0.5, -4.0))
+    for (x, y, rho, s, lam) in [(3, 2, 3.7, 2.0, 0.8), (8, 6, 4.2, 5.0, 1.3)]:
+        v, o, _ = ray_of_pixel(pose, CAM, x, y)
+        r = render1(oracle_mod, o + rho * v, [s, 0, s, 0, 0, s], lam, pose, CAM, pixels=[y * CAM[0] + x], variant=1)
+        assert abs(r["depth"][0] - rho) < 1e-12
+        assert abs(r["saved"][0, 0] - (1 - np.exp(-lam))) < 1e-12
+        assert abs(r["alpha"][0] - (1 - np.exp(-lam))) < 1e-12
+
+
+def test_ac_two_centred_gaussians_closed_form(oracle_mod):
+    """Two Gaussians centred on one ray at rho1 < rho2 (q = 0, delta_i = lambda_i):
+    the front one has T = 1, the back one T = e^-lambda1, so
+    w1 = 1 - e^-l1, w2 = e^-l1 (1 - e^-l2), D = (w1 rho1 + w2 rho2) / (w1 + w2),
+    and W = w1 + w2 = 1 - e^-(l1 + l2) = alpha.  Listing the back one first changes
+    nothing."""
+    pose = synth.look_at_pose((0.0, 0.0, -4.0))
+    x, y = 5, 7
+    v, o, _ = ray_of_pixel(pose, CAM, x, y)
+    chol = np.array([[3, 0.2, 2, -0.1, 0.3, 4], [1.5, 0, 1.5, 0, 0, 1.5]], dtype=np.float64)
+    for (r1, r2, l1, l2) in [(3.5, 4.5, 1.0, 1.0), (3.0, 3.2, 0.3, 2.1), (3.9, 4.4, 2.5, 0.7)]:
+        w1 = 1 - np.exp(-l1)
+        w2 = np.exp(-l1) * (1 - np.exp(-l2))
+        for order in ((0, 1), (1, 0)):
+            mu = np.stack([o + r1 * v, o + r2 * v])[list(order)]
+            lam = np.array([l1, l2])[list(order)]
+            r = oracle_mod.render_view(mu, chol[list(order)], lam, pose, None, CAM, pixels=[y * CAM[0] + x],
+                                       variant=1)
+            assert abs(r["depth"][0] - (w1 * r1 + w2 * r2) / (w1 + w2)) < 1e-12
+            assert abs(r["saved"][0, 0] - (w1 + w2)) < 1e-12
+            assert abs(r["alpha"][0] - (w1 + w2)) < 1e-12
+
+
+def test_ac_weights_telescope_to_alpha(oracle_mod):
+    """With distinct hit depths the transmittances telescope: sum_i w_i =
+    1 - exp(-sum delta) = alpha on every pixel (and W <= 1)."""
+    s = synth.config0(seed=5, K=17, W=16, H=12)
+    r = oracle_mod.render_view(s.means, s.chol, s.weights, s.poses[0], None, CAM, variant=1)
+    np.testing.assert_allclose(r["saved"][:, 0], r["alpha"], rtol=1e-12, atol=1e-15)
+
+
+def test_ac_ties_do_not_attenuate(oracle_mod):
+    """Eq. 10's indicator is strict: an exact duplicate sits at the same depth as
+    its twin, so neither attenuates the other -- both get w = 1 - e^-delta, W is
+    twice the single-copy W, the depth is unchanged, while alpha = 1 - e^-2 sum delta."""
+    pose = synth.look_at_pose((0.0, 0.0, -4.0))
+    v, o, _ = ray_of_pixel(pose, CAM, 5, 7)
+    mu = o + 3.7 * v
+    c = [2.0, 0.1, 1.5, 0.0, 0.2, 2.5]
+    one = render1(oracle_mod, mu, c, 0.9, pose, CAM, pixels=[7 * CAM[0] + 5], variant=1)
+    two = oracle_mod.render_view(np.stack([mu, mu]), np.array([c, c], dtype=np.float64), np.array([0.9, 0.9]), pose,
+                                 None, CAM, pixels=[7 * CAM[0] + 5], variant=1)
+    assert abs(two["saved"][0, 0] - 2 * one["saved"][0, 0]) < 1e-13
+    assert abs(two["depth"][0] - one["depth"][0]) < 1e-12
+    assert abs(two["alpha"][0] - (1 - np.exp(-2 * one["saved"][0, 1]))) < 1e-13
+
+
+def test_ac_permutation_invariance(oracle_mod):
+    """The variant sorts by depth internally: outputs do not depend on the order in
+    which the Gaussians are given."""
+    s = synth.config0(seed=6, K=19, W=20, H=16)
+    cam = (20, 16, 20.0, 20.0, 10.0, 8.0)
+    tp = synth.look_at_pose((1.0, 0.3, -3.8))[None]
+    a = oracle_mod.render_view(s.means, s.chol, s.weights, s.poses[0], tp, cam, variant=1)
+    perm = np.random.default_rng(1).permutation(19)
+    b = oracle_mod.render_view(s.means[perm], s.chol[perm], s.weights[perm], s.poses[0], tp, cam, variant=1)
+    for k in ("depth", "alpha", "normal", "flow", "saved"):
+        np.testing.assert_allclose(b[k], a[k], rtol=1e-12, atol=1e-12, err_msg=k)
+
+
+def test_ac_dense_front_gaussian_occludes(oracle_mod):
+    """A very dense Gaussian in front (lambda = 60: T of everything behind it is
+    e^-60) makes the depth that of the front hit, whatever lies behind."""
+    pose = synth.look_at_pose((0.0, 0.0, -4.0))
+    v, o, _ = ray_of_pixel(pose, CAM, 4, 4)
+    mu = np.stack([o + 4.6 * v, o + 3.1 * v, o + 5.0 * v])
+    chol = np.array([[2, 0, 2, 0, 0, 2]] * 3, dtype=np.float64)
+    r = oracle_mod.render_view(mu, chol, np.array([3.0, 60.0, 5.0]), pose, None, CAM, pixels=[4 * CAM[0] + 4],
+                               variant=1)
+    assert abs(r["depth"][0] - 3.1) < 1e-12
