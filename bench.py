@@ -10,6 +10,15 @@ planes (about 50 MB) fit in L2, so L2 is flushed (256 MiB write) between timed
 steps, outside the timed events.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload orbit|single|ragged|recon|largek]
+
+The default workload is the orbit above (the headline line).  The others print
+the same line for: a single 64x64 view with K = 40 (depth + alpha, Gaussian
+gradients); a ragged batch of 64 objects (K from 20 to 400, square images of side
+64..512, 4 views each); the reconstruction workload (100 views at 640x480, K =
+256, two flow slots; its line adds the full reconstruction step: forward, loss,
+backward and Adam replayed from one CUDA graph); and a large-K stress case (8
+views at 1024x768, K = 4096).
 
 The batched arm's tiles come from the autotuner, run before the timed region; set
 FMB_AUTOTUNE_CACHE to a file to reuse a previous run's choice (e.g. when
@@ -40,17 +49,38 @@ METRIC = "ray-Gaussian pairs/s fwd+bwd, batched vs plain, at <=1e-4 rel err vs F
 WORKLOAD = ("object orbit: 16 views 320x240 (f=320) on a radius-4 ring, K=100 Gaussians, depth+alpha+normal "
             "planes, flow to the next view, backward w.r.t. means, Cholesky factors, weights and poses")
 
-# Algorithmic per-pair work of the implemented formulation (FP32-pipe ops and
-# MUFU ops; counted from the kernels' arithmetic, loads and control excluded).
-FWD_FP32, FWD_MUFU = 58, 4
-BWD_FP32, BWD_MUFU = 110, 4
+# Algorithmic per-pair work of the implemented formulation: FP32 add/mul/fma lane
+# operations (an FMA counts once; negations, comparisons, loads and control
+# excluded) and MUFU operations (ex2, rcp, rsqrt), counted from the kernels'
+# arithmetic, with and without the normal plane.
+OPS = {  # normals -> (fwd FP32, fwd MUFU, bwd FP32, bwd MUFU)
+    True: (56, 4, 110, 4),
+    False: (42, 3, 70, 3),
+}
+# Alpha-compositing variant (Sec. 3.3): per pair, the same geometry plus the
+# transmittance and weight arithmetic (prefix sums, T = e^-S, 1 - e^-delta by its
+# series), and in the backward a re-render, the per-pair weight adjoint and the
+# packed pair loop; the per-ray 64-bit sort network (integer compares and
+# shuffles) is extra and not counted.
+OPS_AC = {True: (82, 4, 206, 7), False: (67, 3, 146, 5)}
+FWD_FP32, FWD_MUFU, BWD_FP32, BWD_MUFU = OPS[True]
+MUFU_MIX = {True: {"ex2": 2, "rcp": 1, "rsqrt": 1}, False: {"ex2": 2, "rcp": 1}}  # per pair, each pass
 N_SM = 152
 LANES_PER_SM = 128
+# MUFU lanes per SM and clock: ex2 at 32 (the ALU probe measures 9.2 T ex2/s =
+# 29 per SM-clock at 2.07 GHz), rcp and rsqrt at 16.
+MUFU_RATE = {"ex2": 32, "rcp": 16, "rsqrt": 16}
 
 
-def peak_issue_ginstr(clock_mhz: float) -> float:
-    """FP32-pipe / issue-slot peak in G lane-instructions per second."""
+def peak_fp32_gops(clock_mhz: float) -> float:
+    """FP32-pipe peak in G lane-operations per second (152 SMs x 128 lanes x clock)."""
     return N_SM * LANES_PER_SM * clock_mhz * 1e6 / 1e9
+
+
+def mufu_busy_frac(pairs_per_s: float, clock_mhz: float, normals: bool = True) -> float:
+    """Fraction of the MUFU pipe's time the per-pair ex2/rcp/rsqrt need at this rate."""
+    sm_clocks_per_pair = sum(n / MUFU_RATE[k] for k, n in MUFU_MIX[bool(normals)].items())
+    return pairs_per_s * sm_clocks_per_pair / (N_SM * clock_mhz * 1e6)
 
 
 PROFILE = os.path.join(ROOT, "profiles", "backward_kernel_orbit16x320x240_K100.md")
@@ -94,13 +124,36 @@ def dist_env():
     return ws, rank, local
 
 
-def scene_and_inputs(seed=0):
+WORKLOADS = {
+    "orbit": dict(config=1, n_flow=1, normals=1, want_pose=True, desc=WORKLOAD),
+    "single": dict(config=0, n_flow=0, normals=0, want_pose=False,
+                   desc="single view 64x64 (f=64), camera at distance 4, K=40 Gaussians, depth+alpha planes, "
+                        "backward w.r.t. means, Cholesky factors and weights"),
+    "ragged": dict(config=2, n_flow=0, normals=1, want_pose=True,
+                   desc="ragged batch: 64 objects, K ~ U{20..400}, square images of side in {64,128,256,512} "
+                        "(f = side), 4 sphere views each (256 views), depth+alpha+normal planes, backward "
+                        "w.r.t. all Gaussian parameters and poses"),
+    "recon": dict(config=3, n_flow=2, normals=0, want_pose=False,
+                  desc="reconstruction workload: 100 sphere views 640x480 (f=640), K=256 Gaussians, "
+                       "depth+alpha planes, flow to the next and the previous view, backward w.r.t. means, "
+                       "Cholesky factors and weights"),
+    "largek": dict(config=4, n_flow=1, normals=1, want_pose=True,
+                   desc="large-K stress: 8 sphere views 1024x768 (f=1024), K=4096 diagonal-precision Gaussians, "
+                        "all four planes, backward w.r.t. Gaussians and poses"),
+}
+
+
+def scene_and_inputs(seed=0, workload="orbit"):
     from paper_2308_14737_gb300 import synth
 
-    s = synth.config1(seed=seed)
+    wl = WORKLOADS[workload]
+    s = synth.CONFIGS[wl["config"]](seed=seed)
     rng = np.random.default_rng(seed + 1)
-    gd, ga, gn, gf = synth.upstream_grads(rng, s.n_pixels, 1)
-    return s, dict(g_depth=gd, g_alpha=ga, g_normal=gn.reshape(-1), g_flow=gf.reshape(-1))
+    nf = max(wl["n_flow"], 1)
+    gd, ga, gn, gf = synth.upstream_grads(rng, s.n_pixels, nf)
+    ups = dict(g_depth=gd, g_alpha=ga, g_normal=gn.reshape(-1) if wl["normals"] else None,
+               g_flow=gf.reshape(-1) if wl["n_flow"] else None)
+    return s, ups
 
 
 class ClockSampler:
@@ -162,6 +215,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def workload_config(s, wl):
+    """The `config` object of a workload: its description and shape."""
+    sizes = sorted({(v["W"], v["H"]) for v in s.views})
+    Ks = sorted({s.K(v["object"]) for v in s.views})
+    c = {"workload": wl["desc"], "views": len(s.views)}
+    if len(sizes) == 1:
+        c.update(width=sizes[0][0], height=sizes[0][1])
+    else:
+        c.update(sizes=f"{len(sizes)} sizes from {sizes[0][0]}x{sizes[0][1]} to {sizes[-1][0]}x{sizes[-1][1]}")
+    c["K"] = Ks[0] if len(Ks) == 1 else f"{len(Ks)} values from {Ks[0]} to {Ks[-1]}"
+    return c
+
+
 def run_gpu(args):
     import torch
 
@@ -177,16 +243,20 @@ def run_gpu(args):
     torch.cuda.set_device(dev)
     fmb.load_library()
 
-    s, ups = scene_and_inputs()
+    wl = WORKLOADS[args.workload]
+    nf, want_pose = wl["n_flow"], wl["want_pose"]
+    s, ups = scene_and_inputs(workload=args.workload)
     pairs = s.n_pairs
-    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    T = lambda a: None if a is None else torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     means, chol, weights, poses = T(s.means), T(s.chol), T(s.weights), T(s.poses)
     gd, ga, gn, gf = (T(ups[k]) for k in ("g_depth", "g_alpha", "g_normal", "g_flow"))
-    params = fmb.default_params(n_flow=1, want_normals=1)
+    ac = args.variant == "ac"
+    params = fmb.default_params(n_flow=nf, want_normals=wl["normals"], variant=1 if ac else 0)
     batched = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), params, device=dev)
     G = means.shape[0]
     grads = dict(means=torch.empty(G, 3, device=dev), chol=torch.empty(G, 6, device=dev),
-                 weights=torch.empty(G, device=dev), poses=torch.empty(len(s.poses), 12, device=dev))
+                 weights=torch.empty(G, device=dev),
+                 poses=torch.empty(len(s.poses), 12, device=dev) if want_pose else None)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
     stream = torch.cuda.current_stream(dev)
     # Like the paper's losses (Sec. 4), weight the depth, normal and flow upstream
@@ -199,11 +269,13 @@ def run_gpu(args):
     gd.mul_(m)
     for v in s.views:
         o, P = v["pix_offset"], v["W"] * v["H"]
-        mn = m[o:o + P] * (batched.saved[3 * o + 2 * P:3 * o + 3 * P] >= 0.05).float()
-        gn[3 * o:3 * (o + P)].view(3, P).mul_(mn)
-        gf[2 * o:2 * (o + P)].view(2, P).mul_(m[o:o + P])
+        if gn is not None:
+            mn = m[o:o + P] * (batched.saved[3 * o + 2 * P:3 * o + 3 * P] >= 0.05).float()
+            gn[3 * o:3 * (o + P)].view(3, P).mul_(mn)
+        if gf is not None:
+            gf[2 * nf * o:2 * nf * (o + P)].view(2 * nf, P).mul_(m[o:o + P])
     for k, t in (("g_depth", gd), ("g_normal", gn), ("g_flow", gf)):
-        ups[k] = t.cpu().numpy()
+        ups[k] = None if t is None else t.cpu().numpy()
 
     # Batched arm: tiles chosen by the autotuner (before the timed region), forward and
     # backward each replayed from a CUDA graph.
@@ -211,7 +283,8 @@ def run_gpu(args):
 
     tuned_params, tune_timings = autotune.tune(
         s.obj_offsets, s.views, len(s.poses), params, means, chol, weights, poses,
-        dict(g_depth=gd, g_alpha=ga, g_normal=gn, g_flow=gf), want_pose=True,
+        dict(g_depth=gd, g_alpha=ga, g_normal=gn, g_flow=gf), want_pose=want_pose,
+        candidates=autotune.CANDIDATES_AC if ac else None,
         cache_path=os.environ.get("FMB_AUTOTUNE_CACHE") or
         os.path.join(tempfile.gettempdir(), f"fmb_autotune_{os.getpid()}.json"))
     batched = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), tuned_params, device=dev)
@@ -220,13 +293,13 @@ def run_gpu(args):
     with torch.cuda.stream(side):
         for _ in range(2):
             batched.forward(means, chol, weights, poses)
-            batched.backward(means, chol, weights, poses, gd, ga, gn, gf, out=grads)
+            batched.backward(means, chol, weights, poses, gd, ga, gn, gf, want_pose=want_pose, out=grads)
     torch.cuda.current_stream(dev).wait_stream(side)
     graph_f, graph_b = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph_f):
         batched.forward(means, chol, weights, poses)
     with torch.cuda.graph(graph_b):
-        batched.backward(means, chol, weights, poses, gd, ga, gn, gf, out=grads)
+        batched.backward(means, chol, weights, poses, gd, ga, gn, gf, want_pose=want_pose, out=grads)
 
     def step(r):
         graph_f.replay()
@@ -241,14 +314,15 @@ def run_gpu(args):
 
     # per-view gradient buffers, summed over the views after the calls (as a caller of
     # per-view launches has to)
-    pgrads = [{k: torch.empty_like(v) for k, v in grads.items()} for _ in plain]
-    psum = {k: torch.empty_like(v) for k, v in grads.items()}
+    pgrads = [{k: None if v is None else torch.empty_like(v) for k, v in grads.items()} for _ in plain]
+    psum = {k: torch.empty_like(v) for k, v in grads.items() if v is not None}
+    sl = lambda t, c, o, P: None if t is None else t[c * o:c * (o + P)]
 
     def plain_step():
         for (r, o, P), g in zip(plain, pgrads):
             r.forward(means, chol, weights, poses)
-            r.backward(means, chol, weights, poses, gd[o:o + P], ga[o:o + P], gn[3 * o:3 * (o + P)],
-                       gf[2 * o:2 * (o + P)], out=g)
+            r.backward(means, chol, weights, poses, gd[o:o + P], ga[o:o + P], sl(gn, 3, o, P),
+                       sl(gf, 2 * nf, o, P), want_pose=want_pose, out=g)
         for k in psum:
             torch.sum(torch.stack([g[k] for g in pgrads]), dim=0, out=psum[k])
 
@@ -314,16 +388,24 @@ def run_gpu(args):
 
     bwd_ms = t_bw / args.steps
     clock_for_peak = 2070.0
+    peak = peak_fp32_gops(clock_for_peak)
+    fwd_ms_ = t_f / args.steps
+    f32f, mf, f32b, mb = (OPS_AC if ac else OPS)[bool(wl["normals"])]
     roofline = {
         "bound": "alu",
         "kernel": "backward_kernel (fmb_render_backward call)",
-        "achieved": pairs * (BWD_FP32 + BWD_MUFU) / (bwd_ms * 1e-3) / 1e9,
-        "peak": peak_issue_ginstr(clock_for_peak),
-        "unit": "Ginstr/s",
+        "achieved": pairs * f32b / (bwd_ms * 1e-3) / 1e9,
+        "peak": peak,
+        "unit": "G FP32 lane-ops/s",
         "frac": None,
         "traffic": None,
-        "per_pair_ops": {"fwd_fp32": FWD_FP32, "fwd_mufu": FWD_MUFU, "bwd_fp32": BWD_FP32, "bwd_mufu": BWD_MUFU},
-        "peak_basis": "152 SMs x 128 FP32 lanes (one warp-instruction issue per SMSP per clock) x 2070 MHz max SM clock",
+        "per_pair_ops": {"fwd_fp32": f32f, "fwd_mufu": mf, "bwd_fp32": f32b, "bwd_mufu": mb},
+        "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz max SM clock (an FMA counts as one operation); "
+                      "the MUFU pipe is the lesser bound (mufu_busy_frac)",
+        "mufu_busy_frac": mufu_busy_frac(pairs / (bwd_ms * 1e-3), clock_for_peak, wl["normals"]),
+        "forward": {"achieved": pairs * f32f / (fwd_ms_ * 1e-3) / 1e9,
+                    "frac": pairs * f32f / (fwd_ms_ * 1e-3) / 1e9 / peak},
+        "step_frac": pairs * (f32f + f32b) / (ms_step * 1e-3) / 1e9 / peak,
     }
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
     roofline["traffic"] = profiled_traffic()
@@ -341,7 +423,8 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded; stands in for the paper's CO3D sequences)",
-        "config": {"workload": WORKLOAD, "views": len(s.views), "width": 320, "height": 240, "K": s.K(0),
+        "config": {**workload_config(s, wl),
+                   "variant": "alpha compositing (Eq. 9-10)" if ac else "two-parameter model (Eq. 7)",
                    "pairs_per_step": pairs,
                    "launch": "batched: one forward and one backward call for all views, autotuned tiles, "
                              "each pass replayed from a CUDA graph",
@@ -359,12 +442,113 @@ def run_gpu(args):
         "gpu_launches": 5 * args.steps,  # prologue + forward; zeroing + prologue + backward per step
         "e2e": e2e,
     }
+    if args.workload == "recon" or args.stored:
+        line["stored_vs_recompute"] = stored_adjoint_measure(args, s, (gd, ga, gn, gf), tuned_params, dev)
+    if args.workload == "recon":
+        line["recon_step"] = recon_step_measure(args, s, dev)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(s, ups, batched, grads, args)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+
+
+def stored_adjoint_measure(args, s, ups_dev, tuned_params, dev):
+    """Recompute-adjoint versus stored-intermediate adjoint on the same batch and
+    tiles: the stored variant's forward also writes 12 bytes per pair (t, log2
+    weight, density) into its workspace and its backward reads them.  Both arms are
+    timed the same way (plain calls, CUDA events, L2 flushed between steps)."""
+    import torch
+
+    from paper_2308_14737_gb300 import autotune, fmb
+
+    wl = WORKLOADS[args.workload]
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    m, c, w, po = T(s.means), T(s.chol), T(s.weights), T(s.poses)
+    gd, ga, gn, gf = ups_dev
+    G = m.shape[0]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    n = max(args.steps // 4, 3)
+    res, grads = {}, {}
+    for arm, store in (("recompute", 0), ("stored", 1)):
+        p = autotune.apply(tuned_params, {})
+        p.store_pairs = store
+        p.fwd_rays_per_thread = 2
+        r = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), p, device=dev)
+        out = dict(means=torch.empty(G, 3, device=dev), chol=torch.empty(G, 6, device=dev),
+                   weights=torch.empty(G, device=dev),
+                   poses=torch.empty(len(s.poses), 12, device=dev) if wl["want_pose"] else None)
+        for _ in range(3):
+            r.forward(m, c, w, po)
+            r.backward(m, c, w, po, gd, ga, gn, gf, want_pose=wl["want_pose"], out=out)
+        torch.cuda.synchronize(dev)
+        tf = tb = 0.0
+        for _ in range(n):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            r.forward(m, c, w, po)
+            e[1].record()
+            r.backward(m, c, w, po, gd, ga, gn, gf, want_pose=wl["want_pose"], out=out)
+            e[2].record()
+            torch.cuda.synchronize(dev)
+            tf += e[0].elapsed_time(e[1])
+            tb += e[1].elapsed_time(e[2])
+        tf, tb = tf / n, tb / n
+        res[arm] = {"fwd_ms": tf, "bwd_ms": tb, "value": s.n_pairs / ((tf + tb) * 1e-3), "unit": "pairs/s",
+                    "workspace_bytes": int(r.ws.numel() * r.ws.element_size())}
+        grads[arm] = out
+        del r
+        torch.cuda.empty_cache()
+    res["stored"]["per_pair_bytes"] = 12
+    res["recompute"]["saved_bytes_per_pixel"] = 12
+    res["grad_max_rel_diff"] = {k: float((grads["stored"][k] - grads["recompute"][k]).abs().max() /
+                                         grads["recompute"][k].abs().max())
+                                for k in grads["stored"] if grads["stored"][k] is not None}
+    res["steps"] = n
+    res["timing"] = "plain calls (no graph) with the autotuned tiles, CUDA events, L2 flushed between steps"
+    return res
+
+
+def recon_step_measure(args, s, dev):
+    """The full reconstruction step (render, loss, adjoint, fused Adam, replayed
+    from one CUDA graph) on the reconstruction workload.  The target planes are
+    rendered by the same GPU renderer from a second seed's Gaussians seen by the
+    same cameras."""
+    import torch
+
+    from paper_2308_14737_gb300 import fmb, synth
+    from paper_2308_14737_gb300.step import ReconstructionStep
+
+    nf = WORKLOADS[args.workload]["n_flow"]
+    params = fmb.default_params(n_flow=nf, want_normals=0)
+    tgt_obj = synth.random_gaussians(np.random.default_rng(1), s.K(0), "cholesky")
+    ts = synth.make_scene([tgt_obj], [{k: v for k, v in vv.items() if k != "pix_offset"} for vv in s.views],
+                          s.poses)
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    r = fmb.Renderer(ts.obj_offsets, ts.views, len(ts.poses), params, device=dev)
+    out = r.forward(T(ts.means), T(ts.chol), T(ts.weights), T(ts.poses))
+    targets = {k: out[k].cpu().numpy() for k in ("depth", "alpha", "flow")}
+    del r, out
+    st = ReconstructionStep(s, targets, params=params, lr=1e-2, device=dev)
+    st.capture(warmup=2)
+    for _ in range(3):
+        st.replay()
+    torch.cuda.synchronize(dev)
+    loss0 = float(st.loss)
+    n = max(args.steps // 20, 5)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(n):
+        st.replay()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / n
+    return {"ms_per_step": ms, "value": s.n_pairs / (ms * 1e-3), "unit": "pairs/s", "steps": n,
+            "loss_first": loss0, "loss_last": float(st.loss),
+            "what": "forward, L1 depth + BCE alpha + L2 flow loss, backward, Adam (lr 1e-2), one CUDA graph; "
+                    "targets rendered by the GPU renderer from a second seed"}
 
 
 def e2e_measure(args, s, ups, params, dev):
@@ -376,25 +560,29 @@ def e2e_measure(args, s, ups, params, dev):
 
     from paper_2308_14737_gb300 import fmb
 
-    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).pin_memory()
+    want_pose = WORKLOADS[args.workload]["want_pose"]
+    pin = lambda a: None if a is None else torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).pin_memory()
     h_in = [pin(s.means), pin(s.chol), pin(s.weights), pin(s.poses), pin(ups["g_depth"]), pin(ups["g_alpha"]),
             pin(ups["g_normal"]), pin(ups["g_flow"])]
-    d_in = [torch.empty_like(h, device=dev) for h in h_in]
+    d_in = [None if h is None else torch.empty_like(h, device=dev) for h in h_in]
     r = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), params, device=dev)
     G = s.means.shape[0]
     grads = dict(means=torch.empty(G, 3, device=dev), chol=torch.empty(G, 6, device=dev),
-                 weights=torch.empty(G, device=dev), poses=torch.empty(len(s.poses), 12, device=dev))
-    outs_d = [r.depth, r.alpha, r.normal, r.flow, grads["means"], grads["chol"], grads["weights"], grads["poses"]]
+                 weights=torch.empty(G, device=dev),
+                 poses=torch.empty(len(s.poses), 12, device=dev) if want_pose else None)
+    outs_d = [o for o in (r.depth, r.alpha, r.normal, r.flow, grads["means"], grads["chol"], grads["weights"],
+                          grads["poses"]) if o is not None]
     outs_h = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs_d]
-    h2d = sum(h.numel() * 4 for h in h_in)
+    h2d = sum(h.numel() * 4 for h in h_in if h is not None)
     d2h = sum(o.numel() * 4 for o in outs_d)
 
     def step():
         for h, d in zip(h_in, d_in):
-            d.copy_(h, non_blocking=True)
+            if h is not None:
+                d.copy_(h, non_blocking=True)
         m, c, w, p, gd, ga, gn, gf = d_in
         r.forward(m, c, w, p)
-        r.backward(m, c, w, p, gd, ga, gn, gf, out=grads)
+        r.backward(m, c, w, p, gd, ga, gn, gf, want_pose=want_pose, out=grads)
         for d, h in zip(outs_d, outs_h):
             h.copy_(d, non_blocking=True)
 
@@ -413,16 +601,56 @@ def e2e_measure(args, s, ups, params, dev):
             "d2h_bytes_per_step": d2h, "ms_per_step": ms}
 
 
+def oracle_sample(workload, s, ups):
+    """Bounded sample of a workload for timing the oracle: two of the orbit's views,
+    the whole single view, else the central 64x48 crop of every view (random
+    upstream gradients of the same distribution).  Returns (scene, upstream, text)."""
+    from paper_2308_14737_gb300 import synth
+
+    wl = WORKLOADS[workload]
+    nf = wl["n_flow"]
+    if workload == "orbit":
+        sub = synth.make_scene([(s.means, s.chol, s.weights)],
+                               [{k: v for k, v in vv.items() if k != "pix_offset"} for vv in s.views[:2]], s.poses)
+        P = sub.n_pixels
+        u = dict(g_depth=np.ascontiguousarray(ups["g_depth"][:P]), g_alpha=np.ascontiguousarray(ups["g_alpha"][:P]))
+        u["g_normal"] = np.concatenate([ups["g_normal"][3 * v["pix_offset"]:3 * (v["pix_offset"] + v["W"] * v["H"])]
+                                        for v in s.views[:2]])
+        u["g_flow"] = np.concatenate([ups["g_flow"][2 * v["pix_offset"]:2 * (v["pix_offset"] + v["W"] * v["H"])]
+                                      for v in s.views[:2]])
+        return sub, u, "2 of the 16 views (320x240, K=100), forward + backward"
+    sub = s if workload == "single" else synth.crop_views(s, 64, 48)
+    gd, ga, gn, gf = synth.upstream_grads(np.random.default_rng(7), sub.n_pixels, max(nf, 1))
+    u = dict(g_depth=gd, g_alpha=ga, g_normal=gn.reshape(-1) if wl["normals"] else None,
+             g_flow=gf.reshape(-1) if nf else None)
+    what = "the whole view" if workload == "single" else f"the central 64x48 crop of all {len(s.views)} views"
+    return sub, u, what + ", forward + backward"
+
+
 def cpu_baseline(s, ups, renderer, grads, args):
     """The FP64 oracle (test infrastructure, not tuned) timed on the host cores on
-    one full step of the same workload, and compared with the GPU result on sampled
-    pixels of that step."""
+    one full step of the orbit workload, and compared with the GPU result of that
+    step; for the other workloads, on a bounded sample of it (no comparison here:
+    the parity tests cover those)."""
     import oracle
 
     oracle.build()
+    if args.workload != "orbit":
+        wl = WORKLOADS[args.workload]
+        sub, u, what = oracle_sample(args.workload, s, ups)
+        t0 = time.perf_counter()
+        var = 1 if args.variant == "ac" else 0
+        oracle.render_scene(sub, n_flow=wl["n_flow"], variant=var)
+        oracle.backward_scene(sub, u["g_depth"], u["g_alpha"], u["g_normal"], u["g_flow"], n_flow=wl["n_flow"],
+                              variant=var)
+        dt = time.perf_counter() - t0
+        return {"value": sub.n_pairs / dt, "unit": "pairs/s", "cores": oracle.max_threads(), "kind": "oracle",
+                "sample": what + " (FP64, OpenMP over pixels)", "seconds": dt}
     t0 = time.perf_counter()
-    ref = oracle.render_scene(s, n_flow=1)
-    refg = oracle.backward_scene(s, ups["g_depth"], ups["g_alpha"], ups["g_normal"], ups["g_flow"], n_flow=1)
+    var = 1 if args.variant == "ac" else 0
+    ref = oracle.render_scene(s, n_flow=1, variant=var)
+    refg = oracle.backward_scene(s, ups["g_depth"], ups["g_alpha"], ups["g_normal"], ups["g_flow"], n_flow=1,
+                                 variant=var)
     dt = time.perf_counter() - t0
     out = {"value": s.n_pairs / dt, "unit": "pairs/s", "cores": oracle.max_threads(), "kind": "oracle",
            "sample": "one full step: all 16 views, forward + backward (FP64, OpenMP over pixels)",
@@ -455,22 +683,15 @@ def run_reference(args):
     import oracle
 
     oracle.build()
-    s, ups = scene_and_inputs()
-    from paper_2308_14737_gb300 import synth
-
-    sub = synth.make_scene([(s.means, s.chol, s.weights)],
-                           [{k: v for k, v in vv.items() if k != "pix_offset"} for vv in s.views[:2]], s.poses)
-    P = sub.n_pixels
-    sl = lambda a, c: np.ascontiguousarray(a[:c * P])
-    u = dict(g_depth=sl(ups["g_depth"], 1), g_alpha=sl(ups["g_alpha"], 1))
-    u["g_normal"] = np.concatenate([ups["g_normal"][3 * v["pix_offset"]:3 * (v["pix_offset"] + v["W"] * v["H"])]
-                                    for v in s.views[:2]])
-    u["g_flow"] = np.concatenate([ups["g_flow"][2 * v["pix_offset"]:2 * (v["pix_offset"] + v["W"] * v["H"])]
-                                  for v in s.views[:2]])
+    wl = WORKLOADS[args.workload]
+    s, ups = scene_and_inputs(workload=args.workload)
+    sub, u, what = oracle_sample(args.workload, s, ups)
+    nf = wl["n_flow"]
+    var = 1 if args.variant == "ac" else 0
 
     def step():
-        oracle.render_scene(sub, n_flow=1)
-        oracle.backward_scene(sub, u["g_depth"], u["g_alpha"], u["g_normal"], u["g_flow"], n_flow=1)
+        oracle.render_scene(sub, n_flow=nf, variant=var)
+        oracle.backward_scene(sub, u["g_depth"], u["g_alpha"], u["g_normal"], u["g_flow"], n_flow=nf, variant=var)
 
     for _ in range(args.warmup):
         step()
@@ -482,10 +703,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "views": 16, "width": 320, "height": 240, "K": 100,
-                       "pairs_per_step": sub.n_pairs, "sample": "2 of the 16 views per step"},
+            "config": dict(workload_config(s, wl), pairs_per_step=sub.n_pairs, sample=what + " per step"),
             "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": oracle.max_threads(), "kind": "oracle",
-                             "sample": "2 of the 16 views (320x240, K=100), forward + backward, per step"},
+                             "sample": what + ", per step"},
             "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -497,6 +717,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="fmb", choices=["fmb", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="orbit", choices=sorted(WORKLOADS))
+    ap.add_argument("--variant", default="two-param", choices=["two-param", "ac"],
+                    help="weights of Eq. 3: the two-parameter model (Eq. 7) or alpha compositing (Eq. 9-10)")
+    ap.add_argument("--stored", action="store_true",
+                    help="also time the stored-intermediate adjoint (always on for --workload recon)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

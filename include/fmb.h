@@ -73,10 +73,18 @@ typedef struct {
   int use_persistent;/* 1: persistent launch (one grid of resident CTAs popping (view, tile)
                         work items, most expensive first, from a counter in the workspace);
                         0: one CTA per work item */
-  int fwd_rays_per_thread; /* tile hints; 0 = library default */
-  int fwd_threads;
-  int bwd_ray_tile;
-  int bwd_threads;
+  int fwd_rays_per_thread; /* tile hints; 0 = library default.  rays per forward thread: 1, 2 or 4 */
+  int fwd_threads;         /* 128 */
+  int bwd_ray_tile;        /* rays per backward CTA, 32..1024 */
+  int bwd_threads;         /* backward threads per CTA: a multiple of 32 up to 160 */
+  int store_pairs;   /* 1: stored-intermediate adjoint.  The forward also writes every
+                        pair's hit depth t, log2 weight and density (Eq. 2, 4, 7) into
+                        the workspace -- 12 bytes per (pixel, Gaussian) pair, what a
+                        reverse-mode autodiff of the renderer (the paper's JAX code,
+                        Sec. 4) keeps -- and the backward reads them instead of
+                        recomputing them.  The backward must then be given the
+                        workspace of the forward call of the same batch, unchanged.
+                        0 (default): recompute from the saved per-pixel normalisers. */
 } fmb_params;
 
 /* One camera view of one object.  Planes of the view start at pixel `pix_offset`
@@ -114,7 +122,10 @@ typedef struct {
  *                             The backward pass needs it.
  * Views may not overlap in the output planes (checked).
  * workspace: >= fmb_workspace_bytes(...) bytes, 256-byte aligned; its contents
- * are scratch and need not be preserved between calls.
+ * are scratch and need not be preserved between calls, except with
+ * store_pairs = 1, where the forward leaves the per-pair values there for the
+ * backward of the same batch (workspace size then grows by 12 bytes per pair,
+ * rounded up: 12 x sum over views of P_v x (K_v rounded up to a multiple of 4)).
  */
 fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
                               const float* means, const float* chol, const float* weights, int n_poses,
@@ -124,9 +135,11 @@ fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const lon
 
 /*
  * Adjoint of fmb_render_forward (the derivative of the renderer defined above;
- * the paper differentiates its JAX renderer automatically, Sec. 4).  It recomputes
- * every ray-Gaussian term from the saved per-pixel log-normaliser instead of
- * storing per-pair values.
+ * the paper differentiates its JAX renderer automatically, Sec. 4).  By default it
+ * recomputes every ray-Gaussian term from the saved per-pixel log-normaliser
+ * instead of storing per-pair values; with store_pairs = 1 it reads the forward's
+ * stored t, log2 weight and density from the workspace (the forward call of the
+ * same batch must have used this workspace and these params).
  *
  * Inputs: the same scene, poses, views and params as the forward call; the
  * forward's depth, normal (NULL if !want_normals) and saved planes; the upstream

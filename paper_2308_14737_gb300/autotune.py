@@ -18,6 +18,9 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "fmb_gb300", "au
 CANDIDATES = [dict(fwd_rays_per_thread=r, bwd_threads=t, bwd_ray_tile=t * m, use_persistent=p)
               for r in (2, 4) for t in (128, 160) for m in (2, 3) for p in (0, 1)]
 
+# The alpha-compositing variant has fixed 32-ray tiles: only the launch mode is tuned.
+CANDIDATES_AC = [dict(use_persistent=p) for p in (0, 1)]
+
 TUNED_FIELDS = ("fwd_rays_per_thread", "bwd_threads", "bwd_ray_tile", "use_persistent")
 
 
@@ -29,7 +32,8 @@ def layout_key(obj_offsets, views, params: fmb.FmbParams, want_pose: bool) -> st
     kb = sorted({int(np.log2(max(k, 1))) for k in Ks})
     P = int(sum(v["W"] * v["H"] for v in views))
     return json.dumps(dict(k=kb, p=int(np.log2(max(P, 1))), v=len(views), f=int(params.n_flow),
-                           n=int(params.want_normals), pose=bool(want_pose)), sort_keys=True)
+                           n=int(params.want_normals), pose=bool(want_pose), variant=int(params.variant)),
+                      sort_keys=True)
 
 
 def _load(path):

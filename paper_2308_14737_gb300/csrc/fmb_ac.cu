@@ -1,0 +1,861 @@
+// fmb_ac.cu -- the zero-parameter alpha-compositing variant of the renderer
+// (Sec. 3.3, Eq. 9-10) and its adjoint.
+//
+// The weights of Eq. 3 become w_i = T_i (1 - e^-delta_i) with the transmittance
+// T_i = exp(-sum_j delta_j [t_j < t_i]) of the hits strictly in front of hit i.
+// That needs the hits of a ray in depth order, so one warp takes one ray: lane l
+// evaluates Gaussians e = m * 32 + l (m < M, K <= 32 M), and a bitonic network over
+// the warp sorts 32 M 64-bit keys (an order-preserving integer image of t in the
+// high word, the Gaussian index in the low word).  Prefix sums of delta in that
+// order give T; hits at exactly equal depth share the sum in front of their run
+// (the indicator is strict).  The weights go back to index order through shared
+// memory and the blend of Eq. 3 is a warp reduction.  Alpha is Eq. 8, as in the
+// two-parameter model; the saved planes are (W = sum w, sum delta, |N|).
+//
+// The adjoint keeps the Gaussian-parallel layout of the two-parameter backward.  A
+// warp-per-ray phase re-renders each ray of a 32-ray tile and turns the upstream
+// gradients into, per (ray, Gaussian), dbar (the gradient of d_i = log delta_i)
+// and c_i = w_i / W, kept in shared memory:
+//   wbar_i     = (Dbar (t_i - D) + Nbar . (n_i - N)) / W
+//   deltabar_k = wbar_k T_k e^-delta_k - sum_{i: t_i > t_k} wbar_i w_i + Abar e^-sum delta
+//   dbar_k     = deltabar_k delta_k
+// (the suffix sum runs over the sorted order, again run-aware for equal depths).
+// A packed pair loop (two Gaussians per thread) then recomputes the geometry of
+// every pair and accumulates the same per-Gaussian sums as the two-parameter
+// backward, with t's direct gradient Dbar c_i and the normal's scale c_i.
+#include <algorithm>
+
+#include "fmb_f32x2.cuh"
+#include "fmb_internal.cuh"
+
+namespace fmb {
+
+constexpr int kAcWarps = 4;
+constexpr int kAcThreads = 32 * kAcWarps;
+constexpr int kAcRays = 32;          // rays per work item (forward and backward)
+constexpr int kAcRayRec = 5;         // backward per-ray record, float4s (values duplicated)
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr unsigned long long kNoKey = ~0ull;
+
+int ac_rays_per_item() { return kAcRays; }
+
+// Order-preserving map of a float to an unsigned integer (and back).
+__device__ __forceinline__ unsigned order_bits(float t) {
+  const unsigned u = __float_as_uint(t);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float from_order_bits(unsigned u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// 1 - e^-x for x >= 0 without cancellation: the Maclaurin series for small x
+// (relative truncation error below x^7 / 8! < 2e-9 for x < 1/4), else 1 - 2^(-x log2 e).
+__device__ __forceinline__ float one_minus_exp_neg(float x) {
+  const float series =
+      x * (1.f - x * 0.5f * (1.f - x * (1.f / 3.f) * (1.f - x * 0.25f * (1.f - x * 0.2f * (1.f - x * (1.f / 6.f) *
+                                                                                          (1.f - x * (1.f / 7.f)))))));
+  return x < 0.25f ? series : 1.f - ex2_approx(-x * kLog2e);
+}
+
+// Ascending bitonic sort of the warp's 32 M keys; element i = m * 32 + lane.
+template <int M>
+__device__ __forceinline__ void warp_bitonic_sort(unsigned long long (&key)[M], int lane) {
+  constexpr int N = 32 * M;
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {  // partner in another register of the same lane
+        const int jm = j >> 5;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          if ((m & jm) == 0) {
+            const int m2 = m | jm;
+            const bool up = ((m << 5) & k) == 0;
+            const unsigned long long a = key[m], b = key[m2];
+            const bool swap = up ? (a > b) : (a < b);
+            key[m] = swap ? b : a;
+            key[m2] = swap ? a : b;
+          }
+        }
+      } else {  // partner in lane ^ j
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const unsigned long long other = __shfl_xor_sync(kFull, key[m], j);
+          const int i = (m << 5) | lane;
+          const bool take_min = ((i & j) == 0) == ((i & k) == 0);
+          const bool other_smaller = other < key[m];
+          key[m] = (take_min == other_smaller) ? other : key[m];
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ float warp_incl_sum(float x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+__device__ __forceinline__ float warp_incl_max(float x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x = fmaxf(x, y);
+  }
+  return x;
+}
+__device__ __forceinline__ float warp_allsum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+
+// One ray of the alpha-compositing render, by one warp.  Per lane, for its
+// Gaussians e = m * 32 + lane: hit depth t[m], density dl[m], Eq. 17 normal n[m]
+// (NORMALS).  sd / sw / sT: the warp's shared scratch, indexed by Gaussian (32 M
+// floats each).  Leaves w_e in sw and T_e in sT, and returns the warp-uniform sums.
+struct AcSums {
+  float W, WT, WN0, WN1, WN2, Sd;
+};
+
+template <bool NORMALS, int M>
+__device__ __forceinline__ AcSums ac_render_ray(const float4* __restrict__ rec, int K, const float v[3],
+                                                const float vl[3], const Consts& k, int lane, float (&t)[M],
+                                                float (&dl)[M], float (&n)[M][3], float* sd, float* sw, float* sT) {
+  unsigned long long key[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int e = (m << 5) | lane;
+    t[m] = 0.f;
+    dl[m] = 0.f;
+    n[m][0] = n[m][1] = n[m][2] = 0.f;
+    key[m] = kNoKey;
+    if (e < K) {
+      const GaussRec g = unpack_rec(rec[kRecFloat4 * e], rec[kRecFloat4 * e + 1], rec[kRecFloat4 * e + 2],
+                                    rec[kRecFloat4 * e + 3]);
+      const PairGeom G = pair_geom(g.L, g.b, g.mh, g.nbl, v[0], v[1], v[2], vl[0], vl[1], vl[2]);
+      t[m] = G.t;
+      dl[m] = ex2_approx(fmaf(G.q, k.K3, g.l2));  // delta (Eq. 4)
+      if (NORMALS) {
+        const float g0 = g.L[0] * G.u0;
+        const float g1 = fmaf(g.L[2], G.u1, g.L[1] * G.u0);
+        const float g2 = fmaf(g.L[5], G.u2, fmaf(g.L[4], G.u1, g.L[3] * G.u0));
+        const float rs = rsqrt_approx(fmaxf(fmaf(g2, g2, fmaf(g1, g1, g0 * g0)), 1e-30f));
+        n[m][0] = g0 * rs;
+        n[m][1] = g1 * rs;
+        n[m][2] = g2 * rs;
+      }
+      sd[e] = dl[m];
+      key[m] = (static_cast<unsigned long long>(order_bits(G.t)) << 32) | static_cast<unsigned>(e);
+    }
+  }
+  __syncwarp();
+  warp_bitonic_sort<M>(key, lane);
+  // Sorted order: exclusive prefix sums of delta, run-aware (Eq. 10's strict <).
+  float carry = 0.f, carry_t = 0.f, carry_S = 0.f;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const bool valid = key[m] != kNoKey;
+    const int idx = static_cast<int>(key[m] & 0xffffffffu);
+    const float ts = valid ? from_order_bits(static_cast<unsigned>(key[m] >> 32)) : INFINITY;
+    const float ds = valid ? sd[idx] : 0.f;
+    const float incl = warp_incl_sum(ds, lane);
+    float excl = __shfl_up_sync(kFull, incl, 1);
+    if (lane == 0) excl = 0.f;
+    excl += carry;
+    float prev_t = __shfl_up_sync(kFull, ts, 1);
+    if (lane == 0) prev_t = carry_t;
+    const bool start = (m == 0 && lane == 0) || ts != prev_t;
+    // P (the exclusive sums) never decreases, so the sum in front of this hit's
+    // run is the largest P at a run start so far.
+    const float S = fmaxf(warp_incl_max(start ? excl : 0.f, lane), carry_S);
+    const float T = ex2_approx(-S * kLog2e);
+    if (valid) {
+      sT[idx] = T;
+      sw[idx] = T * one_minus_exp_neg(ds);
+    }
+    carry += __shfl_sync(kFull, incl, 31);
+    carry_t = __shfl_sync(kFull, ts, 31);
+    carry_S = __shfl_sync(kFull, S, 31);
+  }
+  __syncwarp();
+  AcSums r{0.f, 0.f, 0.f, 0.f, 0.f, carry};
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int e = (m << 5) | lane;
+    if (e < K) {
+      const float w = sw[e];
+      r.W += w;
+      r.WT = fmaf(w, t[m], r.WT);
+      if (NORMALS) {
+        r.WN0 = fmaf(w, n[m][0], r.WN0);
+        r.WN1 = fmaf(w, n[m][1], r.WN1);
+        r.WN2 = fmaf(w, n[m][2], r.WN2);
+      }
+    }
+  }
+  r.W = warp_allsum(r.W);
+  r.WT = warp_allsum(r.WT);
+  if (NORMALS) {
+    r.WN0 = warp_allsum(r.WN0);
+    r.WN1 = warp_allsum(r.WN1);
+    r.WN2 = warp_allsum(r.WN2);
+  }
+  return r;
+}
+
+// Stages a view's K records into shared memory with one bulk copy; every thread
+// waits (bounded).  Returns false (after recording the timeout) if the copy did
+// not arrive.
+__device__ __forceinline__ bool ac_stage_records(float4* dst, const float4* src, int K, uint64_t* bar,
+                                                 unsigned& uses, int* status) {
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(bar, static_cast<uint32_t>(K) * kRecBytes);
+    bulk_g2s(dst, src, static_cast<uint32_t>(K) * kRecBytes, bar);
+  }
+  const bool ok = mbar_wait_bounded(bar, uses & 1u, status);
+  ++uses;
+  return !__syncthreads_or(!ok);
+}
+
+// ------------------------------------------------------------------ forward
+template <bool NORMALS, int NFLOW, int M>
+__global__ void __launch_bounds__(kAcThreads) forward_ac_kernel(const __grid_constant__ Batch batch, Scene s,
+                                                                Consts k, const float4* __restrict__ records,
+                                                                FwdOut out, int* status, int* counter) {
+  extern __shared__ float4 ac_smem[];  // records [32 M][4 float4] | per warp: sd, sw, sT [32 M floats each]
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_item;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float4* srec = ac_smem;
+  float* scratch = reinterpret_cast<float*>(ac_smem + 32 * M * kRecFloat4) + warp * 3 * 32 * M;
+  float* sd = scratch;
+  float* sw = scratch + 32 * M;
+  float* sT = scratch + 64 * M;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  unsigned uses = 0;
+  for (int round = 0;; ++round) {
+    const int item = next_item(counter, round, &s_item);
+    if (item < 0 || item >= batch.n_items) break;
+    int tile;
+    const int vi = find_item(batch, item, tile);
+    const DevView& V = batch.v[vi];
+    const int P = V.W * V.H;
+    if (round > 0) __syncthreads();  // the previous item's records are dead
+    if (!ac_stage_records(srec, records + kRecFloat4 * V.rec_off, V.K, &bar, uses, status)) return;
+    float R[9], tp[3];
+    load_pose(s.poses, V.pose, R, tp);
+    const float o0 = -fmaf(R[6], tp[2], fmaf(R[3], tp[1], R[0] * tp[0]));
+    const float o1 = -fmaf(R[7], tp[2], fmaf(R[4], tp[1], R[1] * tp[0]));
+    const float o2 = -fmaf(R[8], tp[2], fmaf(R[5], tp[1], R[2] * tp[0]));
+    float Rj[NFLOW > 0 ? NFLOW : 1][9], tj[NFLOW > 0 ? NFLOW : 1][3];
+    bool has_t[NFLOW > 0 ? NFLOW : 1];
+#pragma unroll
+    for (int j = 0; j < NFLOW; ++j) {
+      const int tg = j == 0 ? V.tgt0 : V.tgt1;
+      has_t[j] = tg >= 0;
+      if (has_t[j]) load_pose(s.poses, tg, Rj[j], tj[j]);
+    }
+    const long long off = V.pix_off;
+    for (int rr = warp; rr < kAcRays; rr += kAcWarps) {
+      const int p = tile * kAcRays + rr;
+      if (p >= P) break;
+      float vc[3], v[3], vl[3], pxy[2];
+      pixel_ray_dd(V, R, p, vc, v, vl, pxy);
+      float t[M], dl[M], n[M][3];
+      const AcSums a = ac_render_ray<NORMALS, M>(srec, V.K, v, vl, k, lane, t, dl, n, sd, sw, sT);
+      if (lane == 0) {
+        const float iW = a.W > 0.f ? 1.0f / a.W : 0.f;
+        const float D = a.WT * iW;
+        out.depth[off + p] = D;
+        out.alpha[off + p] = -expm1f(-a.Sd);
+        float* sv = out.saved + 3 * off;
+        sv[p] = a.W;
+        sv[P + p] = a.Sd;
+        if (NORMALS) {
+          const float N0 = a.WN0 * iW, N1 = a.WN1 * iW, N2 = a.WN2 * iW;
+          const float Nn = sqrtf(fmaf(N0, N0, fmaf(N1, N1, N2 * N2)));
+          const float iN = Nn > 0.f ? 1.0f / Nn : 0.f;
+          const float n0 = N0 * iN, n1 = N1 * iN, n2 = N2 * iN;
+          float* nrm = out.normal + 3 * off;
+          nrm[p] = fmaf(R[2], n2, fmaf(R[1], n1, R[0] * n0));
+          nrm[P + p] = fmaf(R[5], n2, fmaf(R[4], n1, R[3] * n0));
+          nrm[2 * P + p] = fmaf(R[8], n2, fmaf(R[7], n1, R[6] * n0));
+          sv[2 * P + p] = Nn;
+        } else {
+          sv[2 * P + p] = 0.f;
+        }
+        if (NFLOW > 0) {
+          const float p0 = fmaf(v[0], D, o0), p1 = fmaf(v[1], D, o1), p2 = fmaf(v[2], D, o2);
+          float* fl = out.flow + 2 * NFLOW * off;
+#pragma unroll
+          for (int j = 0; j < NFLOW; ++j) {
+            float fu = 0.f, fv = 0.f;
+            if (has_t[j]) {
+              const float X0 = fmaf(Rj[j][2], p2, fmaf(Rj[j][1], p1, fmaf(Rj[j][0], p0, tj[j][0])));
+              const float X1 = fmaf(Rj[j][5], p2, fmaf(Rj[j][4], p1, fmaf(Rj[j][3], p0, tj[j][1])));
+              const float X2 = fmaf(Rj[j][8], p2, fmaf(Rj[j][7], p1, fmaf(Rj[j][6], p0, tj[j][2])));
+              const float iz = 1.0f / X2;
+              fu = fmaf(V.fx * X0, iz, V.cx) - pxy[0];
+              fv = fmaf(V.fy * X1, iz, V.cy) - pxy[1];
+            }
+            fl[(2 * j) * P + p] = fu;
+            fl[(2 * j + 1) * P + p] = fv;
+          }
+        }
+      }
+      __syncwarp();  // the scratch of this ray is read before the next ray overwrites it
+    }
+  }
+}
+
+// ----------------------------------------------------------------- backward
+struct AcAcc2 {
+  f2 nSd, Y0, Y1, Y2, G00, G10, G11, G20, G21, G22, M[9];
+};
+
+// One packed step: two Gaussians (lanes) against one ray.  rr: the ray's record
+// (5 x 16 bytes, duplicated values), pd: (dbar, c) of both Gaussians.
+template <bool NORMALS>
+__device__ __forceinline__ void bwd_pair_ac2(AcAcc2& A, const GaussRec2& gr, const ulonglong2* __restrict__ rr,
+                                             float4 pd, f2 tiny) {
+  const ulonglong2 q0 = rr[0], q1 = rr[1], q2 = rr[2], q3 = rr[3], q4 = rr[4];
+  const f2 v0 = as_f2(q0.x), v1 = as_f2(q0.y), v2 = as_f2(q1.x), Dbar = as_f2(q1.y);
+  const f2 ndbar = pk(-pd.x, -pd.z), c = pk(pd.y, pd.w);
+  const PairGeom2 G = pair_geom2(gr, v0, v1, v2, as_f2(q3.y), as_f2(q4.x), as_f2(q4.y));
+  const f2 t = G.t;
+  f2 ub0, ub1, ub2, tbar, gb0, gb1, gb2;
+  if (NORMALS) {
+    const f2 Nb0 = as_f2(q2.x), Nb1 = as_f2(q2.y), Nb2 = as_f2(q3.x);
+    const f2 g0 = mul2(gr.L[0], G.u0);
+    const f2 g1 = fma2(gr.L[2], G.u1, mul2(gr.L[1], G.u0));
+    const f2 g2 = fma2(gr.L[5], G.u2, fma2(gr.L[4], G.u1, mul2(gr.L[3], G.u0)));
+    const f2 gg = add2(fma2(g2, g2, fma2(g1, g1, mul2(g0, g0))), tiny);
+    const f2 rs = rsqrt_2(gg);
+    const f2 n0 = mul2(g0, rs), n1 = mul2(g1, rs), n2 = mul2(g2, rs);
+    const f2 nN = fma2(n2, Nb2, fma2(n1, Nb1, mul2(n0, Nb0)));
+    const f2 sc = mul2(c, rs);
+    const f2 sN = mul2(sc, nN);
+    const f2 nsN = pk(-lo(sN), -hi(sN));
+    gb0 = fma2(nsN, n0, mul2(sc, Nb0));
+    gb1 = fma2(nsN, n1, mul2(sc, Nb1));
+    gb2 = fma2(nsN, n2, mul2(sc, Nb2));
+    ub0 = fma2(gr.L[3], gb2, fma2(gr.L[1], gb1, mul2(gr.L[0], gb0)));
+    ub1 = fma2(gr.L[4], gb2, mul2(gr.L[2], gb1));
+    ub2 = mul2(gr.L[5], gb2);
+    tbar = fma2(ub2, G.a2, fma2(ub1, G.a1, fma2(ub0, G.a0, mul2(Dbar, c))));
+  } else {
+    ub0 = ub1 = ub2 = gb0 = gb1 = gb2 = dup(0.f);
+    tbar = mul2(Dbar, c);
+  }
+  ub0 = fma2(ndbar, G.u0, ub0);
+  ub1 = fma2(ndbar, G.u1, ub1);
+  ub2 = fma2(ndbar, G.u2, ub2);
+  const f2 ns2 = mul2(tbar, G.ninv);  // -tbar / a.a
+  const f2 y0 = fma2(ns2, G.a0, ub0);
+  const f2 y1 = fma2(ns2, G.a1, ub1);
+  const f2 y2 = fma2(ns2, G.a2, ub2);
+  const f2 ab0 = fma2(t, y0, mul2(ns2, G.u0));
+  const f2 ab1 = fma2(t, y1, mul2(ns2, G.u1));
+  const f2 ab2 = fma2(t, y2, mul2(ns2, G.u2));
+  A.nSd = add2(A.nSd, ndbar);
+  A.Y0 = add2(A.Y0, y0);
+  A.Y1 = add2(A.Y1, y1);
+  A.Y2 = add2(A.Y2, y2);
+  if (NORMALS) {
+    A.G00 = fma2(gb0, G.u0, A.G00);
+    A.G10 = fma2(gb1, G.u0, A.G10);
+    A.G11 = fma2(gb1, G.u1, A.G11);
+    A.G20 = fma2(gb2, G.u0, A.G20);
+    A.G21 = fma2(gb2, G.u1, A.G21);
+    A.G22 = fma2(gb2, G.u2, A.G22);
+  }
+  A.M[0] = fma2(v0, ab0, A.M[0]);
+  A.M[1] = fma2(v0, ab1, A.M[1]);
+  A.M[2] = fma2(v0, ab2, A.M[2]);
+  A.M[3] = fma2(v1, ab0, A.M[3]);
+  A.M[4] = fma2(v1, ab1, A.M[4]);
+  A.M[5] = fma2(v1, ab2, A.M[5]);
+  A.M[6] = fma2(v2, ab0, A.M[6]);
+  A.M[7] = fma2(v2, ab1, A.M[7]);
+  A.M[8] = fma2(v2, ab2, A.M[8]);
+}
+
+// Shared memory of the backward, in floats after the records:
+//   ray records [kAcRays][kAcRayRec float4] | pair values [kAcRays][32 M][2] |
+//   per warp scratch sd, sw, sT, sq [32 M floats each]
+// The pair values region is reused for the per-thread sums of the reduction.
+constexpr int kAcAccFloats = 38;
+template <int M>
+__host__ __device__ constexpr int ac_pairv_floats() {
+  return kAcRays * 32 * M * 2 > kAcThreads * kAcAccFloats ? kAcRays * 32 * M * 2 : kAcThreads * kAcAccFloats;
+}
+template <int M>
+__host__ __device__ constexpr int ac_bwd_smem_floats() {
+  return 32 * M * 4 * kRecFloat4 + kAcRays * kAcRayRec * 4 + ac_pairv_floats<M>() + kAcWarps * 4 * 32 * M;
+}
+
+template <bool NORMALS, int NFLOW, int M>
+__global__ void __launch_bounds__(kAcThreads) backward_ac_kernel(const __grid_constant__ Batch batch, Scene s,
+                                                                 Consts k, const float4* __restrict__ records,
+                                                                 BwdIn in, BwdOut out, int* status, int* counter) {
+  extern __shared__ float4 ac_smem[];
+  constexpr int NPV = 12 * (1 + NFLOW);
+  __shared__ float pose_ray[kAcWarps][NPV];
+  __shared__ float pose_gau[kAcWarps][12];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_item;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float4* srec = ac_smem;
+  float4* rays = ac_smem + 32 * M * kRecFloat4;
+  float* pairv = reinterpret_cast<float*>(rays + kAcRays * kAcRayRec);
+  float* scratch = pairv + ac_pairv_floats<M>() + warp * 4 * 32 * M;
+  float* sd = scratch;
+  float* sw = scratch + 32 * M;
+  float* sT = scratch + 64 * M;
+  float* sq = scratch + 96 * M;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  unsigned uses = 0;
+  const bool want_pose = out.gposes != nullptr;
+  for (int round = 0;; ++round) {
+    const int item = next_item(counter, round, &s_item);
+    if (item < 0 || item >= batch.n_items) break;
+    int tile;
+    const int vi = find_item(batch, item, tile);
+    const DevView& V = batch.v[vi];
+    const int P = V.W * V.H;
+    const int K = V.K;
+    const int pix0 = tile * kAcRays;
+    const int nr = min(kAcRays, P - pix0);
+    const long long off = V.pix_off;
+    if (round > 0) __syncthreads();
+    if (!ac_stage_records(srec, records + kRecFloat4 * V.rec_off, K, &bar, uses, status)) return;
+
+    // ------------- phase A: one warp per ray -> per-ray record and per-pair (dbar, c)
+    float R[9], tp[3];
+    load_pose(s.poses, V.pose, R, tp);
+    const float o0 = -fmaf(R[6], tp[2], fmaf(R[3], tp[1], R[0] * tp[0]));
+    const float o1 = -fmaf(R[7], tp[2], fmaf(R[4], tp[1], R[1] * tp[0]));
+    const float o2 = -fmaf(R[8], tp[2], fmaf(R[5], tp[1], R[2] * tp[0]));
+    float Rj[NFLOW > 0 ? NFLOW : 1][9], tj[NFLOW > 0 ? NFLOW : 1][3];
+    bool has_t[NFLOW > 0 ? NFLOW : 1];
+#pragma unroll
+    for (int j = 0; j < NFLOW; ++j) {
+      const int tg = j == 0 ? V.tgt0 : V.tgt1;
+      has_t[j] = tg >= 0 && in.g_flow != nullptr;
+      if (has_t[j]) load_pose(s.poses, tg, Rj[j], tj[j]);
+    }
+    float pose_acc[NPV];
+#pragma unroll
+    for (int i = 0; i < NPV; ++i) pose_acc[i] = 0.f;
+    for (int rr = warp; rr < nr; rr += kAcWarps) {
+      const int p = pix0 + rr;
+      float vc[3], v[3], vl[3], pxy[2];
+      pixel_ray_dd(V, R, p, vc, v, vl, pxy);
+      float t[M], dl[M], n[M][3];
+      const AcSums a = ac_render_ray<NORMALS, M>(srec, K, v, vl, k, lane, t, dl, n, sd, sw, sT);
+      const float iW = a.W > 0.f ? 1.0f / a.W : 0.f;
+      const float D = a.WT * iW;
+      const float gD = in.g_depth ? in.g_depth[off + p] : 0.f;
+      const float gA = in.g_alpha ? in.g_alpha[off + p] : 0.f;
+      // flow (Sec. 5): p3 = o + v D, X = R_j p3 + t_j, flow = pi(X) - pixel
+      float pb0 = 0.f, pb1 = 0.f, pb2 = 0.f;
+      if (NFLOW > 0) {
+        const float p0 = fmaf(v[0], D, o0), p1 = fmaf(v[1], D, o1), p2 = fmaf(v[2], D, o2);
+        const float* gf = in.g_flow + 2 * NFLOW * off;
+#pragma unroll
+        for (int j = 0; j < NFLOW; ++j) {
+          if (!has_t[j]) continue;
+          const float X0 = fmaf(Rj[j][2], p2, fmaf(Rj[j][1], p1, fmaf(Rj[j][0], p0, tj[j][0])));
+          const float X1 = fmaf(Rj[j][5], p2, fmaf(Rj[j][4], p1, fmaf(Rj[j][3], p0, tj[j][1])));
+          const float X2 = fmaf(Rj[j][8], p2, fmaf(Rj[j][7], p1, fmaf(Rj[j][6], p0, tj[j][2])));
+          const float iz = 1.0f / X2;
+          const float gu = gf[(2 * j) * P + p], gv = gf[(2 * j + 1) * P + p];
+          const float Xb0 = gu * V.fx * iz;
+          const float Xb1 = gv * V.fy * iz;
+          const float Xb2 = -(Xb0 * X0 + Xb1 * X1) * iz;
+          pb0 += fmaf(Rj[j][6], Xb2, fmaf(Rj[j][3], Xb1, Rj[j][0] * Xb0));
+          pb1 += fmaf(Rj[j][7], Xb2, fmaf(Rj[j][4], Xb1, Rj[j][1] * Xb0));
+          pb2 += fmaf(Rj[j][8], Xb2, fmaf(Rj[j][5], Xb1, Rj[j][2] * Xb0));
+          if (want_pose && lane == 0) {
+            float* pa = pose_acc + 12 * (1 + j);
+            const float Xb[3] = {Xb0, Xb1, Xb2};
+            const float pp[3] = {p0, p1, p2};
+#pragma unroll
+            for (int a3 = 0; a3 < 3; ++a3) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) pa[3 * a3 + c] = fmaf(Xb[a3], pp[c], pa[3 * a3 + c]);
+              pa[9 + a3] += Xb[a3];
+            }
+          }
+        }
+      }
+      const float Dbar = fmaf(v[2], pb2, fmaf(v[1], pb1, fmaf(v[0], pb0, gD)));
+      if (NFLOW > 0 && want_pose && lane == 0) {
+        const float w3[3] = {fmaf(D, vc[0], -tp[0]), fmaf(D, vc[1], -tp[1]), fmaf(D, vc[2], -tp[2])};
+        const float pb[3] = {pb0, pb1, pb2};
+#pragma unroll
+        for (int a3 = 0; a3 < 3; ++a3) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) pose_acc[3 * a3 + c] = fmaf(w3[a3], pb[c], pose_acc[3 * a3 + c]);
+          pose_acc[9 + a3] -= fmaf(R[3 * a3 + 2], pb2, fmaf(R[3 * a3 + 1], pb1, R[3 * a3] * pb0));
+        }
+      }
+      // normal: ncam = R n_f, n_f = N / |N|, N = sum w n / W
+      float N[3] = {a.WN0 * iW, a.WN1 * iW, a.WN2 * iW};
+      float Nb[3] = {0.f, 0.f, 0.f};
+      if (NORMALS && in.g_normal != nullptr) {
+        const float Nn = sqrtf(fmaf(N[0], N[0], fmaf(N[1], N[1], N[2] * N[2])));
+        const float iN = Nn > 0.f ? 1.0f / Nn : 0.f;
+        const float nf[3] = {N[0] * iN, N[1] * iN, N[2] * iN};
+        const float* gn3 = in.g_normal + 3 * off;
+        const float gn[3] = {gn3[p], gn3[P + p], gn3[2 * P + p]};
+        float nfb[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) nfb[c] = fmaf(R[6 + c], gn[2], fmaf(R[3 + c], gn[1], R[c] * gn[0]));
+        if (want_pose && lane == 0) {
+#pragma unroll
+          for (int a3 = 0; a3 < 3; ++a3)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) pose_acc[3 * a3 + c] = fmaf(gn[a3], nf[c], pose_acc[3 * a3 + c]);
+        }
+        if (Nn > 0.f) {
+          const float sdot = fmaf(nf[2], nfb[2], fmaf(nf[1], nfb[1], nf[0] * nfb[0]));
+#pragma unroll
+          for (int c = 0; c < 3; ++c) Nb[c] = fmaf(-sdot, nf[c], nfb[c]) * iN;
+        }
+      }
+      const float KA = gA * __expf(-a.Sd);
+      // wbar_e (index order) and q_e = wbar_e w_e
+      float wbar[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const int e = (m << 5) | lane;
+        wbar[m] = 0.f;
+        if (e < K) {
+          float x = Dbar * (t[m] - D);
+          if (NORMALS)
+            x = fmaf(Nb[0], n[m][0] - N[0], fmaf(Nb[1], n[m][1] - N[1], fmaf(Nb[2], n[m][2] - N[2], x)));
+          wbar[m] = x * iW;
+          sq[e] = wbar[m] * sw[e];
+        }
+      }
+      __syncwarp();
+      // Suffix sums of q over the hits strictly behind each hit, in sorted order:
+      // U = total - (inclusive prefix at the end of the hit's run of equal depth).
+      {
+        unsigned long long key[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const int e = (m << 5) | lane;
+          key[m] = e < K ? (static_cast<unsigned long long>(order_bits(t[m])) << 32) | static_cast<unsigned>(e)
+                         : kNoKey;
+        }
+        warp_bitonic_sort<M>(key, lane);
+        float Q[M], ts[M];
+        float carry = 0.f;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const bool valid = key[m] != kNoKey;
+          const int idx = static_cast<int>(key[m] & 0xffffffffu);
+          ts[m] = valid ? from_order_bits(static_cast<unsigned>(key[m] >> 32)) : INFINITY;
+          Q[m] = warp_incl_sum(valid ? sq[idx] : 0.f, lane) + carry;
+          carry = __shfl_sync(kFull, Q[m], 31);
+        }
+        const float Qtot = carry;
+        // value of Q at the end of each run, copied leftwards within the run
+        float nxt_val = 0.f, nxt_t = INFINITY;
+#pragma unroll
+        for (int m = M - 1; m >= 0; --m) {
+          float right_t = __shfl_down_sync(kFull, ts[m], 1);
+          if (lane == 31) right_t = nxt_t;
+          bool flag = ts[m] != right_t;  // last hit of its run
+          float val = Q[m];
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const float ov = __shfl_down_sync(kFull, val, o);
+            const bool of = __shfl_down_sync(kFull, flag ? 1 : 0, o) != 0;
+            if (!flag && lane + o < 32) {
+              val = ov;
+              flag = of;
+            }
+          }
+          if (!flag) val = nxt_val;  // the run continues into the next register
+          if (key[m] != kNoKey) sd[static_cast<int>(key[m] & 0xffffffffu)] = Qtot - val;  // sd now holds U
+          nxt_val = __shfl_sync(kFull, val, 0);
+          nxt_t = __shfl_sync(kFull, ts[m], 0);
+        }
+      }
+      __syncwarp();
+      // dbar and c per (ray, Gaussian) into the pair buffer; the ray record
+      float2* pv = reinterpret_cast<float2*>(pairv) + rr * 32 * M;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const int e = (m << 5) | lane;
+        float2 val = make_float2(0.f, 0.f);
+        if (e < K) {
+          const float U = sd[e];
+          const float deltabar = fmaf(wbar[m] * sT[e], ex2_approx(-dl[m] * kLog2e), KA - U);
+          val = make_float2(deltabar * dl[m], sw[e] * iW);
+        }
+        pv[e] = val;
+      }
+      if (lane == 0) {
+        float4* rec = rays + rr * kAcRayRec;
+        rec[0] = make_float4(v[0], v[0], v[1], v[1]);
+        rec[1] = make_float4(v[2], v[2], Dbar, Dbar);
+        rec[2] = make_float4(Nb[0], Nb[0], Nb[1], Nb[1]);
+        rec[3] = make_float4(Nb[2], Nb[2], vl[0], vl[0]);
+        rec[4] = make_float4(vl[1], vl[1], vl[2], vl[2]);
+      }
+      __syncwarp();
+    }
+    if (want_pose) {
+#pragma unroll
+      for (int i = 0; i < NPV; ++i)
+        if (lane == 0) pose_ray[warp][i] = pose_acc[i];
+    }
+    __syncthreads();
+
+    // ------------- phase B: Gaussian-parallel packed pair loop over the tile's rays
+    const int GB2 = (K + 1) / 2;
+    const int S = max(1, kAcThreads / GB2);
+    const int gl2 = tid % GB2;
+    const int sg = tid / GB2;
+    const int g0 = 2 * gl2;
+    const bool active = sg < S;
+    AcAcc2 A;
+    A.nSd = A.Y0 = A.Y1 = A.Y2 = dup(0.f);
+    A.G00 = A.G10 = A.G11 = A.G20 = A.G21 = A.G22 = dup(0.f);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) A.M[i] = dup(0.f);
+    if (active) {
+      const GaussRec ga = unpack_rec(srec[kRecFloat4 * g0], srec[kRecFloat4 * g0 + 1], srec[kRecFloat4 * g0 + 2],
+                                     srec[kRecFloat4 * g0 + 3]);
+      const int g1 = g0 + 1 < K ? g0 + 1 : g0;
+      const GaussRec gbr = unpack_rec(srec[kRecFloat4 * g1], srec[kRecFloat4 * g1 + 1],
+                                      srec[kRecFloat4 * g1 + 2], srec[kRecFloat4 * g1 + 3]);
+      const GaussRec2 gr = pair_rec(ga, gbr);
+      const f2 tiny = dup(1e-30f);
+      const ulonglong2* rrec = reinterpret_cast<const ulonglong2*>(rays);
+      const float4* pv4 = reinterpret_cast<const float4*>(pairv);
+#pragma unroll 2
+      for (int r = sg; r < nr; r += S)
+        bwd_pair_ac2<NORMALS>(A, gr, rrec + kAcRayRec * r, pv4[(r * 32 * M + g0) / 2], tiny);
+    }
+    __syncthreads();  // the pair buffer is dead; reuse it for the reduction
+
+    // ------------- phase C: combine subgroups, finalise per Gaussian
+    float* red = pairv;
+    if (active) {
+      float* d = red + kAcAccFloats * tid;
+      const f2 vv[19] = {A.nSd, A.Y0, A.Y1, A.Y2, A.G00, A.G10, A.G11, A.G20, A.G21, A.G22,
+                         A.M[0], A.M[1], A.M[2], A.M[3], A.M[4], A.M[5], A.M[6], A.M[7], A.M[8]};
+#pragma unroll
+      for (int i = 0; i < 19; ++i) {
+        d[i] = lo(vv[i]);
+        d[19 + i] = hi(vv[i]);
+      }
+    }
+    __syncthreads();
+    float* slot = nullptr;
+    if (out.partials) slot = out.partials + V.part_off + static_cast<long long>(tile) * V.slot_floats;
+    float pose_g[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) pose_g[i] = 0.f;
+    for (int gi = tid; gi < K; gi += kAcThreads) {
+      float acc[19];
+#pragma unroll
+      for (int i = 0; i < 19; ++i) acc[i] = 0.f;
+      for (int s2 = 0; s2 < S; ++s2) {
+        const float* d = red + kAcAccFloats * (s2 * GB2 + (gi >> 1)) + 19 * (gi & 1);
+#pragma unroll
+        for (int i = 0; i < 19; ++i) acc[i] += d[i];
+      }
+      const GaussRec g = unpack_rec(srec[kRecFloat4 * gi], srec[kRecFloat4 * gi + 1], srec[kRecFloat4 * gi + 2],
+                                    srec[kRecFloat4 * gi + 3]);
+      const long long gg = V.gauss_off + gi;
+      const float L00 = g.L[0], L10 = g.L[1], L11 = g.L[2], L20 = g.L[3], L21 = g.L[4], L22 = g.L[5];
+      const float Bb0 = -acc[1], Bb1 = -acc[2], Bb2 = -acc[3];
+      float gm[3], gL[6];
+      gm[0] = L00 * Bb0;
+      gm[1] = fmaf(L11, Bb1, L10 * Bb0);
+      gm[2] = fmaf(L22, Bb2, fmaf(L21, Bb1, L20 * Bb0));
+      const float m0 = g.mh[0], m1 = g.mh[1], m2 = g.mh[2];
+      const float* Mx = acc + 10;
+      gL[0] = acc[4] + Mx[0] + m0 * Bb0;
+      gL[1] = acc[5] + Mx[3] + m1 * Bb0;
+      gL[2] = acc[6] + Mx[4] + m1 * Bb1;
+      gL[3] = acc[7] + Mx[6] + m2 * Bb0;
+      gL[4] = acc[8] + Mx[7] + m2 * Bb1;
+      gL[5] = acc[9] + Mx[8] + m2 * Bb2;
+      const float glam = -acc[0] / s.weights[gg];
+      if (want_pose) {
+        float ML[9];
+        const float Lf[9] = {L00, 0.f, 0.f, L10, L11, 0.f, L20, L21, L22};
+#pragma unroll
+        for (int a3 = 0; a3 < 3; ++a3)
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            ML[3 * a3 + c] =
+                fmaf(Mx[3 * a3 + 2], Lf[3 * c + 2], fmaf(Mx[3 * a3 + 1], Lf[3 * c + 1], Mx[3 * a3] * Lf[3 * c]));
+#pragma unroll
+        for (int a3 = 0; a3 < 3; ++a3) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            pose_g[3 * a3 + c] +=
+                fmaf(R[3 * a3 + 2], ML[6 + c], fmaf(R[3 * a3 + 1], ML[3 + c], R[3 * a3] * ML[c])) + tp[a3] * gm[c];
+          pose_g[9 + a3] += fmaf(R[3 * a3 + 2], gm[2], fmaf(R[3 * a3 + 1], gm[1], R[3 * a3] * gm[0]));
+        }
+      }
+      if (slot == nullptr) {
+        atomicAdd(out.gmeans + 3 * gg + 0, gm[0]);
+        atomicAdd(out.gmeans + 3 * gg + 1, gm[1]);
+        atomicAdd(out.gmeans + 3 * gg + 2, gm[2]);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) atomicAdd(out.gchol + 6 * gg + i, gL[i]);
+        atomicAdd(out.gweights + gg, glam);
+      } else {
+        float* d = slot + 10 * gi;
+        d[0] = gm[0];
+        d[1] = gm[1];
+        d[2] = gm[2];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) d[3 + i] = gL[i];
+        d[9] = glam;
+      }
+    }
+
+    // ------------- phase D: pose gradient of this CTA
+    if (want_pose) {
+#pragma unroll
+      for (int i = 0; i < 12; ++i) {
+        const float x = warp_allsum(pose_g[i]);
+        if (lane == 0) pose_gau[warp][i] = x;
+      }
+      __syncthreads();
+      if (tid < NPV) {
+        float x = 0.f;
+        for (int w = 0; w < kAcWarps; ++w) x += pose_ray[w][tid] + (tid < 12 ? pose_gau[w][tid] : 0.f);
+        if (slot != nullptr) {
+          slot[10 * V.GB + tid] = x;
+        } else {
+          const int j = tid / 12 - 1;
+          const int pidx = j < 0 ? V.pose : (j == 0 ? V.tgt0 : V.tgt1);
+          if (pidx >= 0) atomicAdd(out.gposes + 12 * static_cast<long long>(pidx) + tid % 12, x);
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <int M>
+static int ac_fwd_smem() {
+  return 32 * M * kRecBytes + kAcWarps * 3 * 32 * M * static_cast<int>(sizeof(float));
+}
+
+template <bool NORMALS, int NFLOW, int M>
+static cudaError_t launch_fwd_ac_t(const Batch& b, const Scene& s, const Consts& c, const float4* records,
+                                   const FwdOut& o, int* status, int* counter, cudaStream_t st) {
+  auto kern = forward_ac_kernel<NORMALS, NFLOW, M>;
+  const int smem = ac_fwd_smem<M>();
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  int grid = b.n_items;
+  if (counter) {
+    int dev = 0, sms = 0, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kAcThreads, smem);
+    grid = std::min(b.n_items, std::max(1, sms) * std::max(1, per));
+  }
+  kern<<<grid, kAcThreads, smem, st>>>(b, s, c, records, o, status, counter);
+  return cudaGetLastError();
+}
+
+template <bool NORMALS, int NFLOW, int M>
+static cudaError_t launch_bwd_ac_t(const Batch& b, const Scene& s, const Consts& c, const float4* records,
+                                   const BwdIn& in, const BwdOut& out, int* status, int* counter, cudaStream_t st) {
+  auto kern = backward_ac_kernel<NORMALS, NFLOW, M>;
+  const int smem = ac_bwd_smem_floats<M>() * static_cast<int>(sizeof(float));
+  if (smem > 40 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  int grid = b.n_items;
+  if (counter) {
+    int dev = 0, sms = 0, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kAcThreads, smem);
+    grid = std::min(b.n_items, std::max(1, sms) * std::max(1, per));
+  }
+  kern<<<grid, kAcThreads, smem, st>>>(b, s, c, records, in, out, status, counter);
+  return cudaGetLastError();
+}
+
+template <int M>
+static cudaError_t fwd_ac_m(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
+                            int n_flow, const FwdOut& o, int* status, int* counter, cudaStream_t st) {
+  if (normals) {
+    if (n_flow == 0) return launch_fwd_ac_t<true, 0, M>(b, s, c, records, o, status, counter, st);
+    if (n_flow == 1) return launch_fwd_ac_t<true, 1, M>(b, s, c, records, o, status, counter, st);
+    return launch_fwd_ac_t<true, 2, M>(b, s, c, records, o, status, counter, st);
+  }
+  if (n_flow == 0) return launch_fwd_ac_t<false, 0, M>(b, s, c, records, o, status, counter, st);
+  if (n_flow == 1) return launch_fwd_ac_t<false, 1, M>(b, s, c, records, o, status, counter, st);
+  return launch_fwd_ac_t<false, 2, M>(b, s, c, records, o, status, counter, st);
+}
+
+template <int M>
+static cudaError_t bwd_ac_m(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
+                            int n_flow, const BwdIn& in, const BwdOut& out, int* status, int* counter,
+                            cudaStream_t st) {
+  if (normals) {
+    if (n_flow == 0) return launch_bwd_ac_t<true, 0, M>(b, s, c, records, in, out, status, counter, st);
+    if (n_flow == 1) return launch_bwd_ac_t<true, 1, M>(b, s, c, records, in, out, status, counter, st);
+    return launch_bwd_ac_t<true, 2, M>(b, s, c, records, in, out, status, counter, st);
+  }
+  if (n_flow == 0) return launch_bwd_ac_t<false, 0, M>(b, s, c, records, in, out, status, counter, st);
+  if (n_flow == 1) return launch_bwd_ac_t<false, 1, M>(b, s, c, records, in, out, status, counter, st);
+  return launch_bwd_ac_t<false, 2, M>(b, s, c, records, in, out, status, counter, st);
+}
+
+int ac_lanes_per_ray_elements(int maxK) { return maxK <= 64 ? 2 : (maxK <= 128 ? 4 : 8); }
+
+cudaError_t launch_forward_ac(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
+                              int n_flow, int maxK, const FwdOut& o, int* status, int* counter, cudaStream_t st) {
+  switch (ac_lanes_per_ray_elements(maxK)) {
+    case 2: return fwd_ac_m<2>(b, s, c, records, normals, n_flow, o, status, counter, st);
+    case 4: return fwd_ac_m<4>(b, s, c, records, normals, n_flow, o, status, counter, st);
+    default: return fwd_ac_m<8>(b, s, c, records, normals, n_flow, o, status, counter, st);
+  }
+}
+
+cudaError_t launch_backward_ac(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
+                               int n_flow, int maxK, const BwdIn& in, const BwdOut& out, int* status, int* counter,
+                               cudaStream_t st) {
+  switch (ac_lanes_per_ray_elements(maxK)) {
+    case 2: return bwd_ac_m<2>(b, s, c, records, normals, n_flow, in, out, status, counter, st);
+    case 4: return bwd_ac_m<4>(b, s, c, records, normals, n_flow, in, out, status, counter, st);
+    default: return bwd_ac_m<8>(b, s, c, records, normals, n_flow, in, out, status, counter, st);
+  }
+}
+
+}  // namespace fmb

@@ -32,6 +32,7 @@ constexpr size_t kBwdCounterOffset = 128;
 constexpr int kDefaultRpt = 2;
 constexpr int kMaxGaussPerCta = 256;
 constexpr long long kMaxK = 1 << 22;
+constexpr int kMaxKAlphaCompositing = 256;
 
 fmb_status fail(fmb_status s, const std::string& msg) {
   g_err = msg;
@@ -87,6 +88,7 @@ struct Plan {
   std::vector<fmb::Batch> bwd;  // backward launches (ray tiles x Gaussian blocks)
   long long n_records = 0;
   long long part_floats = 0;
+  long long pair_stride = 0;  // stored-intermediate mode: floats per per-pair array
   long long n_gauss = 0;
   int maxK = 0;
   int rpt = kDefaultRpt;
@@ -99,15 +101,21 @@ fmb_status validate_scene(const fmb_params* p, int n_objects, const long long* o
   if (!p) return fail(FMB_ERR_INVALID_ARG, "params is NULL");
   if (!std::isfinite(p->beta1) || !std::isfinite(p->beta2)) return fail(FMB_ERR_INVALID_ARG, "beta1/beta2 not finite");
   if (!(p->eta > 0.0f) || !std::isfinite(p->eta)) return fail(FMB_ERR_INVALID_ARG, "eta must be > 0");
-  if (p->variant != 0) return fail(FMB_ERR_INVALID_ARG, "only variant 0 (two-parameter model) is implemented");
+  if (p->variant != 0 && p->variant != 1)
+    return fail(FMB_ERR_INVALID_ARG, "variant must be 0 (two-parameter model) or 1 (alpha compositing)");
+  if (p->variant == 1 && p->store_pairs)
+    return fail(FMB_ERR_INVALID_ARG, "store_pairs is not available with variant 1 (alpha compositing)");
   if (p->n_flow < 0 || p->n_flow > 2) return fail(FMB_ERR_INVALID_ARG, "n_flow must be 0, 1 or 2");
   if (p->use_persistent != 0 && p->use_persistent != 1) return fail(FMB_ERR_INVALID_ARG, "use_persistent must be 0 or 1");
+  if (p->store_pairs != 0 && p->store_pairs != 1) return fail(FMB_ERR_INVALID_ARG, "store_pairs must be 0 or 1");
+  if (p->store_pairs && (p->fwd_rays_per_thread == 1 || p->fwd_rays_per_thread == 4))
+    return fail(FMB_ERR_INVALID_ARG, "store_pairs needs fwd_rays_per_thread 0 or 2");
   if (p->fwd_rays_per_thread != 0 && p->fwd_rays_per_thread != 1 && p->fwd_rays_per_thread != 2 &&
       p->fwd_rays_per_thread != 4)
     return fail(FMB_ERR_INVALID_ARG, "fwd_rays_per_thread must be 0, 1, 2 or 4");
   if (p->fwd_threads != 0 && p->fwd_threads != 128) return fail(FMB_ERR_INVALID_ARG, "fwd_threads must be 0 or 128");
-  if (p->bwd_ray_tile < 0 || p->bwd_ray_tile > 1024 || (p->bwd_ray_tile % 32) != 0)
-    return fail(FMB_ERR_INVALID_ARG, "bwd_ray_tile must be a multiple of 32 in [32, 1024] (0 = default)");
+  if (p->bwd_ray_tile != 0 && (p->bwd_ray_tile < 32 || p->bwd_ray_tile > 1024))
+    return fail(FMB_ERR_INVALID_ARG, "bwd_ray_tile must be in [32, 1024] (0 = default)");
   if (p->bwd_threads != 0 && (p->bwd_threads < 32 || p->bwd_threads > 160 || (p->bwd_threads % 32) != 0))
     return fail(FMB_ERR_INVALID_ARG, "bwd_threads must be a multiple of 32 in [32, 160] (0 = default)");
   if (n_objects < 1) return fail(FMB_ERR_INVALID_ARG, "n_objects must be >= 1");
@@ -117,6 +125,9 @@ fmb_status validate_scene(const fmb_params* p, int n_objects, const long long* o
     const long long K = offs[k + 1] - offs[k];
     if (K < 1) return fail(FMB_ERR_INVALID_ARG, "object " + std::to_string(k) + " has no Gaussians");
     if (K > kMaxK) return fail(FMB_ERR_INVALID_ARG, "object " + std::to_string(k) + " has too many Gaussians");
+    if (p->variant == 1 && K > kMaxKAlphaCompositing)
+      return fail(FMB_ERR_INVALID_ARG, "object " + std::to_string(k) +
+                                           " has more than 256 Gaussians (the alpha-compositing limit)");
   }
   if (n_views < 1) return fail(FMB_ERR_INVALID_ARG, "n_views must be >= 1");
   if (!views) return fail(FMB_ERR_INVALID_ARG, "h_views is NULL");
@@ -171,9 +182,10 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
   // enough to amortise the per-CTA reductions)
   pl.ray_tile = p->bwd_ray_tile > 0 ? p->bwd_ray_tile : 3 * pl.bwd_threads;
   pl.n_gauss = offs[n_objects];
-  const int rays_fwd = fmb::forward_rays_per_cta(pl.rpt);
+  const bool ac = p->variant == 1;
+  const int rays_fwd = ac ? fmb::ac_rays_per_item() : fmb::forward_rays_per_cta(pl.rpt);
   const int n_flow = p->n_flow;
-  long long rec = 0, part = 0;
+  long long rec = 0, part = 0, pairs = 0;
   for (int base = 0; base < n_views; base += fmb::kMaxBatchViews) {
     const int nb = std::min(fmb::kMaxBatchViews, n_views - base);
     fmb::Batch bf;
@@ -202,6 +214,9 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
       d.pix_off = v.pix_offset;
       rec += d.K;
       const long long P = static_cast<long long>(v.W) * v.H;
+      d.Kp = (d.K + 3) / 4 * 4;  // rows of 16-byte multiples
+      d.pair_off = pairs;
+      pairs += P * d.Kp;
       // forward
       fmb::DevView df = d;
       df.n_tiles = static_cast<int>((P + rays_fwd - 1) / rays_fwd);
@@ -211,7 +226,9 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
       // backward
       fmb::DevView db = d;
       BwdBlocking bk = bwd_blocking(d.K, pl.bwd_threads);
-      db.n_tiles = static_cast<int>((P + pl.ray_tile - 1) / pl.ray_tile);
+      if (ac) bk = BwdBlocking{1, d.K, 1};  // one 32-ray tile x all K Gaussians per item
+      const int tile_b = ac ? fmb::ac_rays_per_item() : pl.ray_tile;
+      db.n_tiles = static_cast<int>((P + tile_b - 1) / tile_b);
       db.n_gblocks = bk.n_gb;
       db.GB = bk.GB;
       db.S = bk.S;
@@ -233,12 +250,22 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
   }
   pl.n_records = rec;
   pl.part_floats = part;
+  pl.pair_stride = (pairs + 63) / 64 * 64;
+  if (p->store_pairs) pl.rpt = 2;
   return pl;
 }
 
-size_t workspace_needed(const fmb_params* p, const Plan& pl) {
+// Workspace: header (status word, work counters) | records | deterministic
+// partials (if deterministic) | per-pair t, e2, delta arrays (if store_pairs).
+size_t pairs_offset(const fmb_params* p, const Plan& pl) {
   size_t bytes = kHeaderBytes + align256(static_cast<size_t>(pl.n_records) * 16 * fmb::kRecFloat4);
   if (p->deterministic) bytes += align256(static_cast<size_t>(pl.part_floats) * sizeof(float));
+  return bytes;
+}
+
+size_t workspace_needed(const fmb_params* p, const Plan& pl) {
+  size_t bytes = pairs_offset(p, pl);
+  if (p->store_pairs) bytes += 3 * static_cast<size_t>(pl.pair_stride) * sizeof(float);
   return bytes;
 }
 
@@ -323,6 +350,9 @@ fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const lon
     float4* records = reinterpret_cast<float4*>(static_cast<char*>(workspace) + kHeaderBytes);
     const fmb::Scene sc{means, chol, weights, poses};
     const fmb::Consts c = make_consts(params);
+    float* pairs = params->store_pairs
+                       ? reinterpret_cast<float*>(static_cast<char*>(workspace) + pairs_offset(params, pl))
+                       : nullptr;
     cudaError_t e = cudaSuccess;
     int* counter = params->use_persistent
                        ? reinterpret_cast<int*>(reinterpret_cast<char*>(status) + kFwdCounterOffset)
@@ -331,8 +361,14 @@ fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const lon
       const fmb::Batch& b = pl.fwd[bi];
       e = fmb::launch_prologue(b, sc, c, records, pl.maxK, bi == 0 ? status : nullptr, counter, s);
       if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
-      e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, pl.maxK, depth,
-                              alpha, normal, flow, saved, status, counter, s);
+      if (params->variant == 1) {
+        const fmb::FwdOut fo{depth, alpha, normal, flow, saved, nullptr, 0};
+        e = fmb::launch_forward_ac(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.maxK, fo, status,
+                                   counter, s);
+      } else {
+        e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, pl.maxK,
+                                depth, alpha, normal, flow, saved, pairs, pl.pair_stride, status, counter, s);
+      }
       if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     }
     return FMB_OK;
@@ -377,8 +413,10 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
     const fmb::Scene sc{means, chol, weights, poses};
     const fmb::Consts c = make_consts(params);
     const bool normals = params->want_normals != 0;
-    fmb::BwdIn in{depth, normals ? normal : nullptr, saved, g_depth, g_alpha, normals ? g_normal : nullptr,
-                  params->n_flow > 0 ? g_flow : nullptr};
+    const float* pairs =
+        params->store_pairs ? reinterpret_cast<const float*>(base + pairs_offset(params, pl)) : nullptr;
+    fmb::BwdIn in{depth,   normals ? normal : nullptr, saved, g_depth, g_alpha, normals ? g_normal : nullptr,
+                  params->n_flow > 0 ? g_flow : nullptr, pairs, pl.pair_stride};
     fmb::BwdOut out{grad_means, grad_chol, grad_weights, grad_poses, partials};
 
     fmb::ZeroJob zj{};
@@ -398,8 +436,11 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
     for (const fmb::Batch& b : pl.bwd) {
       e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, counter, s);
       if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
-      e = fmb::launch_backward(b, sc, c, records, normals, params->n_flow, pl.ray_tile, pl.bwd_threads, in, out,
-                               counter, s);
+      if (params->variant == 1)
+        e = fmb::launch_backward_ac(b, sc, c, records, normals, params->n_flow, pl.maxK, in, out, status, counter, s);
+      else
+        e = fmb::launch_backward(b, sc, c, records, normals, params->n_flow, pl.ray_tile, pl.bwd_threads, in, out,
+                                 counter, s);
       if (e != cudaSuccess) return cuda_fail(e, "backward launch");
       if (partials) {
         e = fmb::launch_backward_reduce(b, params->n_flow, pl.n_gauss, n_poses, out, s);
@@ -488,6 +529,8 @@ extern "C" fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n
     if (params->n_flow > 0 && !flow) return fail(FMB_ERR_INVALID_ARG, "flow is NULL but n_flow > 0");
     st = validate_views(n_objects, n_poses, n_views, h_views);
     if (st != FMB_OK) return st;
+    if (params->store_pairs)
+      return fail(FMB_ERR_INVALID_ARG, "store_pairs needs a workspace (use fmb_render_forward)");
     Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views);
     const size_t need = kHeaderBytes + align256(static_cast<size_t>(pl.n_records) * 16 * fmb::kRecFloat4);
     if (need > kStaticScratchBytes)
@@ -503,6 +546,7 @@ extern "C" fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n
     float4* records = reinterpret_cast<float4*>(static_cast<char*>(ws) + kHeaderBytes);
     const fmb::Scene sc{means, chol, weights, poses};
     const fmb::Consts c = make_consts(params);
+    float* pairs = nullptr;  // stored-intermediate mode is rejected above
     cudaError_t e = cudaSuccess;
     int* counter = params->use_persistent
                        ? reinterpret_cast<int*>(reinterpret_cast<char*>(status) + kFwdCounterOffset)
@@ -511,8 +555,14 @@ extern "C" fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n
       const fmb::Batch& b = pl.fwd[bi];
       e = fmb::launch_prologue(b, sc, c, records, pl.maxK, bi == 0 ? status : nullptr, counter, s);
       if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
-      e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, pl.maxK, depth,
-                              alpha, normal, flow, saved, status, counter, s);
+      if (params->variant == 1) {
+        const fmb::FwdOut fo{depth, alpha, normal, flow, saved, nullptr, 0};
+        e = fmb::launch_forward_ac(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.maxK, fo, status,
+                                   counter, s);
+      } else {
+        e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, pl.maxK,
+                                depth, alpha, normal, flow, saved, pairs, pl.pair_stride, status, counter, s);
+      }
       if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     }
     return FMB_OK;

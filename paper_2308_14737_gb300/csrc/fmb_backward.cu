@@ -55,17 +55,27 @@ struct BwdAcc2 {
 //    Nb1 Nb1 Nb2 Nb2 | vl0 vl0 vl1 vl1 | vl2 vl2 0 0]
 constexpr int kRayRec2 = 7;
 
-template <bool NORMALS>
+// STORED: the pair's t, log2 weight and density come from the forward (`st`,
+// `se`, `sd`) instead of being recomputed.
+template <bool NORMALS, bool STORED>
 __device__ __forceinline__ void bwd_pair2(BwdAcc2& A, const GaussRec2& gr, const ulonglong2* __restrict__ rr, f2 K2,
-                                          f2 K3, f2 B1, f2 nB1, f2 nB2E, f2 tiny) {
+                                          f2 K3, f2 B1, f2 nB1, f2 nB2E, f2 tiny, f2 st, f2 se, f2 sd) {
   const ulonglong2 q0 = rr[0], q1 = rr[1], q2 = rr[2], q3 = rr[3], q4 = rr[4], q5 = rr[5], q6 = rr[6];
   const f2 v0 = as_f2(q0.x), v1 = as_f2(q0.y), v2 = as_f2(q1.x), nlse = as_f2(q1.y);
   const f2 Dbar = as_f2(q2.x), nKA = as_f2(q2.y), nC = as_f2(q3.x);
-  const PairGeom2 G = pair_geom2(gr, v0, v1, v2, as_f2(q5.x), as_f2(q5.y), as_f2(q6.x));
+  PairGeom2 G;
+  f2 what, delta;
+  if (STORED) {
+    G = pair_geom2_given_t(gr, st, v0, v1, v2, as_f2(q5.x), as_f2(q5.y), as_f2(q6.x));
+    what = ex2_2(add2(se, nlse));
+    delta = sd;
+  } else {
+    G = pair_geom2(gr, v0, v1, v2, as_f2(q5.x), as_f2(q5.y), as_f2(q6.x));
+    const f2 x = fma2(G.q, K3, gr.l2);  // log2(delta)
+    what = ex2_2(fma2(x, B1, fma2(G.t, K2, nlse)));
+    delta = ex2_2(x);
+  }
   const f2 t = G.t;
-  const f2 x = fma2(G.q, K3, gr.l2);  // log2(delta)
-  const f2 what = ex2_2(fma2(x, B1, fma2(t, K2, nlse)));
-  const f2 delta = ex2_2(x);
   f2 ebar, ub0, ub1, ub2, tbar, gb0, gb1, gb2;
   if (NORMALS) {
     const f2 Nb0 = as_f2(q3.y), Nb1 = as_f2(q4.x), Nb2 = as_f2(q4.y);
@@ -132,7 +142,7 @@ __device__ __forceinline__ float warp_sum(float x) {
   return x;
 }
 
-template <bool NORMALS, int NFLOW>
+template <bool NORMALS, int NFLOW, bool STORED>
 __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
     backward_kernel(const __grid_constant__ Batch batch, Scene s, Consts k, const float4* __restrict__ records,
                     BwdIn in, BwdOut out, int ray_tile, int* counter) {
@@ -309,8 +319,23 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
     const f2 K2v = dup(k.K2), K3v = dup(k.K3), B1v = dup(k.beta1), nB1v = dup(-k.beta1), nB2E = dup(-k.b2e);
     const f2 tiny = dup(1e-30f);
     const ulonglong2* rays = reinterpret_cast<const ulonglong2*>(bsm);
+    if (STORED) {
+      // the two Gaussians' stored values are adjacent in the row of pixel p (g0 is even)
+      const unsigned long long* pt =
+          reinterpret_cast<const unsigned long long*>(in.pairs + V.pair_off + static_cast<long long>(pix0) * V.Kp + g0);
+      const long long st2 = in.pair_stride / 2, row2 = V.Kp / 2;
 #pragma unroll kBwdUnroll
-    for (int r = sg; r < nr; r += S) bwd_pair2<NORMALS>(A, gr, rays + kRayRec2 * r, K2v, K3v, B1v, nB1v, nB2E, tiny);
+      for (int r = sg; r < nr; r += S) {
+        const unsigned long long* q = pt + static_cast<long long>(r) * row2;
+        bwd_pair2<NORMALS, true>(A, gr, rays + kRayRec2 * r, K2v, K3v, B1v, nB1v, nB2E, tiny, as_f2(__ldg(q)),
+                                 as_f2(__ldg(q + st2)), as_f2(__ldg(q + 2 * st2)));
+      }
+    } else {
+      const f2 z = dup(0.f);
+#pragma unroll kBwdUnroll
+      for (int r = sg; r < nr; r += S)
+        bwd_pair2<NORMALS, false>(A, gr, rays + kRayRec2 * r, K2v, K3v, B1v, nB1v, nB2E, tiny, z, z, z);
+    }
   }
   __syncthreads();  // ray records are dead; the shared memory is reused below
 
@@ -437,11 +462,12 @@ static int bwd_smem_bytes(int ray_tile, int threads) {
                   threads * kAccFloats * static_cast<int>(sizeof(float)));
 }
 
-template <bool NORMALS, int NFLOW>
+template <bool NORMALS, int NFLOW, bool STORED = false>
 static cudaError_t prepare_bwd_t(int smem) {
   // Dynamic plus static shared memory above the 48 KB default needs the opt-in.
   if (smem + static_cast<int>(sizeof(float) * (kBwdMaxThreads / 32) * 48) > 48 * 1024)
-    return cudaFuncSetAttribute(backward_kernel<NORMALS, NFLOW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return cudaFuncSetAttribute(backward_kernel<NORMALS, NFLOW, STORED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem);
   return cudaSuccess;
 }
 
@@ -450,17 +476,18 @@ static int bwd_ctas_per_sm_t(int ray_tile, int threads) {
   const int smem = bwd_smem_bytes(ray_tile, threads);
   if (prepare_bwd_t<NORMALS, NFLOW>(smem) != cudaSuccess) return 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, backward_kernel<NORMALS, NFLOW>, threads, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, backward_kernel<NORMALS, NFLOW, false>, threads, smem) !=
+      cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }
 
-template <bool NORMALS, int NFLOW>
-static cudaError_t launch_bwd_t(const Batch& b, const Scene& s, const Consts& c, const float4* records,
+template <bool NORMALS, int NFLOW, bool STORED>
+static cudaError_t launch_bwd_s(const Batch& b, const Scene& s, const Consts& c, const float4* records,
                                 int ray_tile, int threads, const BwdIn& in, const BwdOut& out, int* counter,
                                 cudaStream_t st) {
   const int smem = bwd_smem_bytes(ray_tile, threads);
-  cudaError_t e = prepare_bwd_t<NORMALS, NFLOW>(smem);
+  cudaError_t e = prepare_bwd_t<NORMALS, NFLOW, STORED>(smem);
   if (e != cudaSuccess) return e;
   int grid = b.n_items;
   if (counter) {
@@ -469,8 +496,17 @@ static cudaError_t launch_bwd_t(const Batch& b, const Scene& s, const Consts& c,
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     grid = std::min(b.n_items, std::max(1, sms) * bwd_ctas_per_sm_t<NORMALS, NFLOW>(ray_tile, threads));
   }
-  backward_kernel<NORMALS, NFLOW><<<grid, threads, smem, st>>>(b, s, c, records, in, out, ray_tile, counter);
+  backward_kernel<NORMALS, NFLOW, STORED><<<grid, threads, smem, st>>>(b, s, c, records, in, out, ray_tile, counter);
   return cudaGetLastError();
+}
+
+template <bool NORMALS, int NFLOW>
+static cudaError_t launch_bwd_t(const Batch& b, const Scene& s, const Consts& c, const float4* records,
+                                int ray_tile, int threads, const BwdIn& in, const BwdOut& out, int* counter,
+                                cudaStream_t st) {
+  if (in.pairs != nullptr)
+    return launch_bwd_s<NORMALS, NFLOW, true>(b, s, c, records, ray_tile, threads, in, out, counter, st);
+  return launch_bwd_s<NORMALS, NFLOW, false>(b, s, c, records, ray_tile, threads, in, out, counter, st);
 }
 
 cudaError_t launch_backward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,

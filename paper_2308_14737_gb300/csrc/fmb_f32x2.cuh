@@ -125,4 +125,33 @@ __device__ __forceinline__ PairGeom2 pair_geom2(const GaussRec2& g, f2 v0, f2 v1
   return G;
 }
 
+// pair_geom2 for a given hit depth t (the stored-intermediate backward, which
+// reads the forward's t instead of recomputing it): the same operations after t,
+// so with the forward's t the results are those pair_geom2 would give; q is not
+// formed (the density comes stored too).
+__device__ __forceinline__ PairGeom2 pair_geom2_given_t(const GaussRec2& g, f2 t, f2 v0, f2 v1, f2 v2, f2 vl0,
+                                                        f2 vl1, f2 vl2) {
+  PairGeom2 G;
+  G.a0 = fma2(g.L[3], v2, fma2(g.L[1], v1, mul2(g.L[0], v0)));
+  G.a1 = fma2(g.L[4], v2, mul2(g.L[2], v1));
+  G.a2 = mul2(g.L[5], v2);
+  const f2 aa = fma2(G.a2, G.a2, fma2(G.a1, G.a1, mul2(G.a0, G.a0)));
+  const f2 inv = rcp_2(aa);
+  const f2 ninv = pk(-lo(inv), -hi(inv));
+  G.ninv = ninv;
+  G.t = t;
+  const f2 r0 = fma2(vl0, t, fma2(v0, t, g.nmh[0]));
+  const f2 r1 = fma2(vl1, t, fma2(v1, t, g.nmh[1]));
+  const f2 r2 = fma2(vl2, t, fma2(v2, t, g.nmh[2]));
+  const f2 u0 = fma2(g.L[0], r0, fma2(g.L[1], r1, fma2(g.L[3], r2, g.nbl[0])));
+  const f2 u1 = fma2(g.L[2], r1, fma2(g.L[4], r2, g.nbl[1]));
+  const f2 u2 = fma2(g.L[5], r2, g.nbl[2]);
+  const f2 nk = mul2(fma2(u2, G.a2, fma2(u1, G.a1, mul2(u0, G.a0))), ninv);
+  G.u0 = fma2(nk, G.a0, u0);
+  G.u1 = fma2(nk, G.a1, u1);
+  G.u2 = fma2(nk, G.a2, u2);
+  G.q = dup(0.f);
+  return G;
+}
+
 }  // namespace fmb

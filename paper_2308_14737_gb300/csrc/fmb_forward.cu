@@ -116,11 +116,18 @@ struct RayAcc2 {
   f2 m, Sw, Swt, Sd, N0, N1, N2;
 };
 
+// Per-pair values the stored-intermediate mode keeps for the backward: the hit
+// depth t, the log2 weight e2 of Eq. 7 and the density delta of Eq. 4.
+struct PairOut2 {
+  f2 t, e2, delta;
+};
+
 template <bool NORMALS>
-__device__ __forceinline__ void fwd_pair2(RayAcc2& A, const GaussRec2& g, f2 K2, f2 K3, f2 beta1, f2 tiny) {
+__device__ __forceinline__ PairOut2 fwd_pair2(RayAcc2& A, const GaussRec2& g, f2 K2, f2 K3, f2 beta1, f2 tiny) {
   const PairGeom2 G = pair_geom2(g, A.v0, A.v1, A.v2, A.vl0, A.vl1, A.vl2);
   const f2 x = fma2(G.q, K3, g.l2);  // log2(delta)
-  A.Sd = add2(A.Sd, ex2_2(x));
+  const f2 delta = ex2_2(x);
+  A.Sd = add2(A.Sd, delta);
   const f2 e2 = fma2(x, beta1, mul2(G.t, K2));
   f2 d = sub2(e2, A.m);
   if (fmaxf(lo(d), hi(d)) > kLazyShift) {  // rare: raise the shift of the lane(s) it no longer bounds
@@ -159,17 +166,11 @@ __device__ __forceinline__ void fwd_pair2(RayAcc2& A, const GaussRec2& g, f2 K2,
     A.N1 = fma2(ws, g1, A.N1);
     A.N2 = fma2(ws, g2, A.N2);
   }
+  return PairOut2{G.t, e2, delta};
 }
 
-struct FwdOut {
-  float* depth;
-  float* alpha;
-  float* normal;
-  float* flow;
-  float* saved;
-};
 
-template <bool NORMALS, int NFLOW, int RPT>
+template <bool NORMALS, int NFLOW, int RPT, bool STORE>
 __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_constant__ Batch batch, Scene s,
                                                               Consts k, const float4* __restrict__ records,
                                                               FwdOut out, int* status, int* counter) {
@@ -266,17 +267,54 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
     }
     const int n = min(kChunk, K - c * kChunk);
     const float4* rec = fwd_smem + stage * kChunk * kRecFloat4;
+    if (STORE) {
+      // Stored-intermediate mode (two rays per thread): the values of four
+      // consecutive Gaussians are buffered and written as one 16-byte store per
+      // ray and array into row p of the view's [pixel][Kp] block (Kp a multiple
+      // of 4; the padding past K is written as zeros).
+      const int p0 = pix[0], p1 = pix[1];
+      for (int i0 = 0; i0 < n; i0 += 4) {
+        float bt[2][4], be[2][4], bd[2][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u;
+          if (i < n) {
+            const GaussRec g = unpack_rec(rec[kRecFloat4 * i + 0], rec[kRecFloat4 * i + 1],
+                                          rec[kRecFloat4 * i + 2], rec[kRecFloat4 * i + 3]);
+            const PairOut2 po = fwd_pair2<NORMALS>(A2[0], broadcast_rec(g), K2v, K3v, B1v, tiny);
+            bt[0][u] = lo(po.t), bt[1][u] = hi(po.t);
+            be[0][u] = lo(po.e2), be[1][u] = hi(po.e2);
+            bd[0][u] = lo(po.delta), bd[1][u] = hi(po.delta);
+          } else {
+            bt[0][u] = bt[1][u] = be[0][u] = be[1][u] = bd[0][u] = bd[1][u] = 0.f;
+          }
+        }
+        const long long kk = static_cast<long long>(c) * kChunk + i0;
+        float* base = out.pairs + V.pair_off + kk;
+        const long long S2 = out.pair_stride;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int pp = h == 0 ? p0 : p1;
+          if (pp >= P) continue;
+          float* row = base + static_cast<long long>(pp) * V.Kp;
+          *reinterpret_cast<float4*>(row) = make_float4(bt[h][0], bt[h][1], bt[h][2], bt[h][3]);
+          *reinterpret_cast<float4*>(row + S2) = make_float4(be[h][0], be[h][1], be[h][2], be[h][3]);
+          *reinterpret_cast<float4*>(row + 2 * S2) = make_float4(bd[h][0], bd[h][1], bd[h][2], bd[h][3]);
+        }
+      }
+    } else {
 #pragma unroll 2
-    for (int i = 0; i < n; ++i) {
-      const GaussRec g = unpack_rec(rec[kRecFloat4 * i + 0], rec[kRecFloat4 * i + 1], rec[kRecFloat4 * i + 2],
-                                    rec[kRecFloat4 * i + 3]);
-      if (PACKED) {
-        const GaussRec2 g2 = broadcast_rec(g);
+      for (int i = 0; i < n; ++i) {
+        const GaussRec g = unpack_rec(rec[kRecFloat4 * i + 0], rec[kRecFloat4 * i + 1], rec[kRecFloat4 * i + 2],
+                                      rec[kRecFloat4 * i + 3]);
+        if (PACKED) {
+          const GaussRec2 g2 = broadcast_rec(g);
 #pragma unroll
-        for (int q = 0; q < NP; ++q) fwd_pair2<NORMALS>(A2[q], g2, K2v, K3v, B1v, tiny);
-      } else {
+          for (int q = 0; q < NP; ++q) fwd_pair2<NORMALS>(A2[q], g2, K2v, K3v, B1v, tiny);
+        } else {
 #pragma unroll
-        for (int r = 0; r < NA; ++r) fwd_pair<NORMALS>(A[r], g, k);
+          for (int r = 0; r < NA; ++r) fwd_pair<NORMALS>(A[r], g, k);
+        }
       }
     }
     __syncthreads();  // every thread is done with this stage before it is refilled
@@ -374,16 +412,16 @@ static int fwd_smem_bytes(int maxK) {
 template <bool NORMALS, int NFLOW, int RPT>
 static int fwd_ctas_per_sm_t(int maxK) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, forward_kernel<NORMALS, NFLOW, RPT>, kFwdThreads,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, forward_kernel<NORMALS, NFLOW, RPT, false>, kFwdThreads,
                                                     fwd_smem_bytes(maxK)) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }
 
-template <bool NORMALS, int NFLOW, int RPT>
+template <bool NORMALS, int NFLOW, int RPT, bool STORE = false>
 static cudaError_t launch_fwd_t(const Batch& b, const Scene& s, const Consts& c, const float4* records,
                                 const FwdOut& o, int maxK, int* status, int* counter, cudaStream_t st) {
-  auto kern = forward_kernel<NORMALS, NFLOW, RPT>;
+  auto kern = forward_kernel<NORMALS, NFLOW, RPT, STORE>;
   int grid = b.n_items;
   if (counter) {
     int dev = 0, sms = 0;
@@ -398,6 +436,8 @@ static cudaError_t launch_fwd_t(const Batch& b, const Scene& s, const Consts& c,
 template <bool NORMALS, int NFLOW>
 static cudaError_t launch_fwd_r(int rpt, const Batch& b, const Scene& s, const Consts& c, const float4* records,
                                 const FwdOut& o, int maxK, int* status, int* counter, cudaStream_t st) {
+  if (o.pairs != nullptr)  // stored-intermediate mode: two rays per thread only
+    return launch_fwd_t<NORMALS, NFLOW, 2, true>(b, s, c, records, o, maxK, status, counter, st);
   switch (rpt) {
     case 1: return launch_fwd_t<NORMALS, NFLOW, 1>(b, s, c, records, o, maxK, status, counter, st);
     case 2: return launch_fwd_t<NORMALS, NFLOW, 2>(b, s, c, records, o, maxK, status, counter, st);
@@ -407,8 +447,9 @@ static cudaError_t launch_fwd_r(int rpt, const Batch& b, const Scene& s, const C
 
 cudaError_t launch_forward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
                            int n_flow, int rpt, int maxK, float* depth, float* alpha, float* normal, float* flow,
-                           float* saved, int* status, int* counter, cudaStream_t st) {
-  FwdOut o{depth, alpha, normal, flow, saved};
+                           float* saved, float* pairs, long long pair_stride, int* status, int* counter,
+                           cudaStream_t st) {
+  FwdOut o{depth, alpha, normal, flow, saved, pairs, pair_stride};
   if (normals) {
     if (n_flow == 0) return launch_fwd_r<true, 0>(rpt, b, s, c, records, o, maxK, status, counter, st);
     if (n_flow == 1) return launch_fwd_r<true, 1>(rpt, b, s, c, records, o, maxK, status, counter, st);

@@ -56,7 +56,8 @@ struct DevView {
   long long pix_off;    // first pixel of this view in the planes
   long long part_off;   // backward deterministic mode: float offset of the view's first slot
   int slot_floats;      // floats per (tile, gblock) slot in deterministic mode
-  int pad_;
+  int Kp;               // stored-intermediate mode: row length (K rounded up to a multiple of 4)
+  long long pair_off;   // stored-intermediate mode: first float of the view's [P][Kp] block
 };
 
 // A launch's views.  Work items (forward: one ray tile; backward: one ray tile x
@@ -360,7 +361,18 @@ cudaError_t launch_prologue(const Batch& b, const Scene& s, const Consts& c, flo
 // one CTA per work item.
 cudaError_t launch_forward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
                            int n_flow, int rpt, int maxK, float* depth, float* alpha, float* normal, float* flow,
-                           float* saved, int* status, int* counter, cudaStream_t st);
+                           float* saved, float* pairs, long long pair_stride, int* status, int* counter,
+                           cudaStream_t st);
+
+struct FwdOut {
+  float* depth;
+  float* alpha;
+  float* normal;
+  float* flow;
+  float* saved;
+  float* pairs;             // stored-intermediate mode: [t | e2 | delta] arrays, else null
+  long long pair_stride;    // floats per array
+};
 
 struct ZeroJob {
   static constexpr int kMax = 6;
@@ -384,6 +396,8 @@ struct BwdIn {
   const float* g_alpha;
   const float* g_normal;
   const float* g_flow;
+  const float* pairs;      // stored-intermediate mode: [t | e2 | delta] arrays, else null
+  long long pair_stride;   // floats per array
 };
 cudaError_t launch_backward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
                             int n_flow, int ray_tile, int threads, const BwdIn& in, const BwdOut& out,
@@ -392,6 +406,14 @@ cudaError_t launch_backward(const Batch& b, const Scene& s, const Consts& c, con
 // grid sizing).
 int forward_ctas_per_sm(bool normals, int n_flow, int rpt, int maxK);
 int backward_ctas_per_sm(bool normals, int n_flow, int ray_tile, int threads);
+// Alpha-compositing variant (Sec. 3.3): work items are 32-ray tiles, K <= 256 per
+// view (maxK: the batch's largest K).
+int ac_rays_per_item();
+cudaError_t launch_forward_ac(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
+                              int n_flow, int maxK, const FwdOut& o, int* status, int* counter, cudaStream_t st);
+cudaError_t launch_backward_ac(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
+                               int n_flow, int maxK, const BwdIn& in, const BwdOut& out, int* status, int* counter,
+                               cudaStream_t st);
 cudaError_t launch_backward_reduce(const Batch& b, int n_flow, long long n_gauss, int n_poses,
                                    const BwdOut& out, cudaStream_t st);
 

@@ -31,7 +31,7 @@ class FmbParams(ctypes.Structure):
                 ("variant", ctypes.c_int), ("want_normals", ctypes.c_int), ("n_flow", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("use_persistent", ctypes.c_int),
                 ("fwd_rays_per_thread", ctypes.c_int), ("fwd_threads", ctypes.c_int),
-                ("bwd_ray_tile", ctypes.c_int), ("bwd_threads", ctypes.c_int)]
+                ("bwd_ray_tile", ctypes.c_int), ("bwd_threads", ctypes.c_int), ("store_pairs", ctypes.c_int)]
 
 
 class FmbView(ctypes.Structure):

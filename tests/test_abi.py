@@ -42,7 +42,8 @@ def test_exports_every_declared_function(fmb):
 def test_struct_layouts(fmb):
     assert ctypes.sizeof(fmb.FmbView) == 48
     assert fmb.FmbView.pix_offset.offset == 40
-    assert ctypes.sizeof(fmb.FmbParams) == 48
+    assert ctypes.sizeof(fmb.FmbParams) == 52
+    assert fmb.FmbParams.store_pairs.offset == 48
 
 
 def test_default_params_and_version(fmb):
@@ -59,6 +60,20 @@ def test_workspace_bytes(fmb):
     assert n >= 256 + 48 * 30 and n % 256 == 0
     p.deterministic = 1
     assert fmb.fmb_workspace_bytes(p, s.obj_offsets, s.views) > n
+
+
+def test_workspace_bytes_stored_pairs(fmb):
+    """store_pairs adds three per-pair arrays of sum_v P_v x (K rounded up to a
+    multiple of 4) floats each (the stride rounded up to 64 floats)."""
+    for K in (10, 11, 12, 13):
+        s = synth.config1(K=K, n_views=3, W=8, H=6)
+        p = fmb.default_params()
+        n0 = fmb.fmb_workspace_bytes(p, s.obj_offsets, s.views)
+        p.store_pairs = 1
+        n1 = fmb.fmb_workspace_bytes(p, s.obj_offsets, s.views)
+        Kp = (K + 3) // 4 * 4
+        stride = (3 * 48 * Kp + 63) // 64 * 64
+        assert n1 - n0 == 3 * 4 * stride
 
 
 class _Fake:
@@ -113,12 +128,43 @@ def test_forward_rejects_bad_views(fmb, bad, msg):
 
 
 def test_forward_rejects_bad_params(fmb):
-    for k, v, msg in [("eta", 0.0, "eta"), ("variant", 1, "variant"), ("n_flow", 3, "n_flow"),
-                      ("fwd_rays_per_thread", 3, "fwd_rays_per_thread"), ("bwd_threads", 100, "bwd_threads"), ("bwd_threads", 192, "bwd_threads")]:
+    for k, v, msg in [("eta", 0.0, "eta"), ("variant", 3, "variant"), ("n_flow", 3, "n_flow"),
+                      ("fwd_rays_per_thread", 3, "fwd_rays_per_thread"), ("bwd_threads", 100, "bwd_threads"),
+                      ("bwd_threads", 192, "bwd_threads"), ("bwd_ray_tile", 16, "bwd_ray_tile"),
+                      ("store_pairs", 2, "store_pairs")]:
         p = fmb.default_params()
         setattr(p, k, v)
         st, err = _call_fwd(fmb, p, [0, 5], [_view()])
         assert st == 1 and msg in err, (k, err)
+
+
+def test_stored_pairs_needs_two_rays_per_thread_and_a_workspace(fmb):
+    p = fmb.default_params(store_pairs=1, fwd_rays_per_thread=4)
+    st, err = _call_fwd(fmb, p, [0, 5], [_view()])
+    assert st == 1 and "store_pairs" in err
+    L = fmb.load_library()
+    f = _Fake()
+    fp = ctypes.c_void_p(f.data_ptr())
+    va = fmb.make_views([_view()])
+    o = np.asarray([0, 5], dtype=np.int64)
+    p = fmb.default_params(store_pairs=1)
+    st = L.fmb_render_forward_noalloc(ctypes.byref(p), 1, o.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), fp,
+                                      fp, fp, 1, fp, 1, va, fp, fp, fp, fp, fp, None)
+    assert st == 1 and "store_pairs" in L.fmb_last_error().decode()
+
+
+def test_alpha_compositing_limits(fmb):
+    """variant 1 takes at most 256 Gaussians per object and no stored pairs."""
+    p = fmb.default_params(variant=1)
+    st, err = _call_fwd(fmb, p, [0, 257], [_view()])
+    assert st == 1 and "256" in err
+    assert fmb.fmb_workspace_bytes(p, [0, 256], [_view()]) > 0  # 256 is accepted (no launch here)
+    p = fmb.default_params(variant=1, store_pairs=1)
+    st, err = _call_fwd(fmb, p, [0, 5], [_view()])
+    assert st == 1 and "store_pairs" in err
+    p = fmb.default_params(variant=2)
+    st, err = _call_fwd(fmb, p, [0, 5], [_view()])
+    assert st == 1 and "variant" in err
 
 
 def test_forward_rejects_bad_scene_and_buffers(fmb):

@@ -12,7 +12,8 @@ import torch
 import oracle
 from paper_2308_14737_gb300 import fmb, synth
 
-from gpu_util import (compare_forward, compare_grads, gpu_backward, gpu_forward, masked_upstream, nnorm_batched,
+from gpu_util import (ac_order_ambiguous, compare_forward, compare_grads, gpu_backward, gpu_forward, masked_upstream,
+                      nnorm_batched,
                       oracle_backward_sampled, oracle_forward_sampled, pixel_mask_from, sample_pixels)
 
 pytestmark = pytest.mark.gpu
@@ -30,16 +31,19 @@ def _lib():
 
 
 def _full_check(scene, n_flow, normals=True, deterministic=False, want_pose=True, seed=1, **pk):
+    variant = pk.get("variant", 0)
     params = fmb.default_params(n_flow=n_flow, want_normals=int(normals), deterministic=int(deterministic), **pk)
     gpu, r, dev = gpu_forward(scene, params)
-    ref = oracle.render_scene(scene, n_flow=n_flow)
-    stats = compare_forward(scene, gpu, ref, n_flow, normals)
-    ups = masked_upstream(scene, ref["alpha"], n_flow, seed=seed, nnorm_ref=nnorm_batched(scene, ref["saved"]))
+    ref = oracle.render_scene(scene, n_flow=n_flow, variant=variant)
+    amb = ac_order_ambiguous(scene) if variant == 1 else None
+    stats = compare_forward(scene, gpu, ref, n_flow, normals, variant=variant, ambiguous=amb)
+    ups = masked_upstream(scene, ref["alpha"], n_flow, seed=seed, nnorm_ref=nnorm_batched(scene, ref["saved"]),
+                          exclude=amb)
     if not normals:
         ups["g_normal"] = np.zeros_like(ups["g_normal"])
     g = gpu_backward(r, dev, ups, want_pose=want_pose)
     refg = oracle.backward_scene(scene, ups["g_depth"], ups["g_alpha"], ups["g_normal"] if normals else None,
-                                 ups["g_flow"], n_flow=n_flow)
+                                 ups["g_flow"], n_flow=n_flow, variant=variant)
     errs = compare_grads(g, refg, keys=("means", "chol", "weights") + (("poses",) if want_pose else ()))
     return stats, errs, g
 
@@ -126,7 +130,7 @@ def test_deterministic_mode_is_bitwise_reproducible():
         np.testing.assert_allclose(g1[k], ga[k], rtol=0, atol=1e-5 * np.abs(g1[k]).max())
 
 
-@pytest.mark.parametrize("ray_tile,threads", [(32, 64), (128, 128), (512, 96), (1024, 160), (320, 160)])
+@pytest.mark.parametrize("ray_tile,threads", [(32, 64), (128, 128), (512, 96), (1024, 160), (320, 160), (450, 160), (33, 32)])
 def test_backward_tilings(ray_tile, threads):
     s = synth.config1(K=70, n_views=2, W=50, H=31)
     _full_check(s, n_flow=1, bwd_ray_tile=ray_tile, bwd_threads=threads)
@@ -207,3 +211,100 @@ def test_device_status_is_clear_and_outputs_finite():
     for k in ("depth", "alpha", "normal", "flow", "saved"):
         assert np.all(np.isfinite(gpu[k])), k
     assert fmb.fmb_read_device_status(r.ws) == 0
+
+
+@pytest.mark.parametrize("deterministic", [False, True])
+def test_stored_intermediate_adjoint(deterministic):
+    """store_pairs = 1: the forward keeps every pair's t, log2 weight and density
+    and the backward reads them; same tolerances against the oracle, and the
+    gradients agree with the recomputing adjoint (only the rounding of the log2
+    weight's last add differs).  Odd K (the rows are padded to even) included."""
+    for scene, nf in ((synth.config1(K=101, n_views=3, W=40, H=30), 1), (_ragged_scene(), 1),
+                      (synth.config0(), 0)):
+        _, _, gs = _full_check(scene, n_flow=nf, store_pairs=1, deterministic=deterministic,
+                               normals=(nf == 1))
+        _, _, gr = _full_check(scene, n_flow=nf, deterministic=deterministic, normals=(nf == 1))
+        for k in gs:
+            np.testing.assert_allclose(gs[k], gr[k], rtol=0, atol=2e-5 * np.abs(gr[k]).max())
+
+
+def test_stored_intermediate_adjoint_full_size_sampled():
+    s = synth.config1()
+    params = fmb.default_params(n_flow=1, store_pairs=1)
+    gpu, r, dev = gpu_forward(s, params)
+    pix = sample_pixels(s, 200, 3)
+    ref = oracle_forward_sampled(s, pix, 1)
+    compare_forward(s, gpu, None, 1, True, pixels_per_view=ref)
+    alpha_ref = np.zeros(s.n_pixels)
+    nn_ref = np.zeros(s.n_pixels)
+    for vi, v in enumerate(s.views):
+        alpha_ref[v["pix_offset"] + ref[vi][0]] = ref[vi][1]["alpha"]
+        nn_ref[v["pix_offset"] + ref[vi][0]] = ref[vi][1]["saved"][:, 2]
+    ups = masked_upstream(s, alpha_ref, 1, seed=4, pixel_mask=pixel_mask_from(s, pix), nnorm_ref=nn_ref)
+    g = gpu_backward(r, dev, ups)
+    compare_grads(g, oracle_backward_sampled(s, ups, pix, 1))
+
+
+# ---------------------------------------------- alpha-compositing variant (Sec. 3.3)
+
+def _ac_ragged_scene(seed=8):
+    """K in {1, 2, 31, 33, 64, 65, 129, 256} (every sort width: 64, 128 and 256
+    keys per ray), images from 1x1 to 65x9, several objects in one launch."""
+    rng = np.random.default_rng(seed)
+    objs, views, poses = [], [], []
+    sizes = [(1, 1), (3, 5), (33, 17), (65, 9), (16, 16), (20, 7), (9, 31), (12, 12)]
+    for o, K in enumerate([1, 2, 31, 33, 64, 65, 129, 256]):
+        objs.append(synth.random_gaussians(rng, K, "cholesky"))
+        W, H = sizes[o]
+        poses.append(synth.look_at_pose(synth.sphere_positions(rng, 1)[0]))
+        views.append(dict(W=W, H=H, fx=float(max(W, H)), fy=float(max(W, H)), cx=W / 2, cy=H / 2, object=o,
+                          pose=len(poses) - 1, flow_target=((len(poses) + 2) % 8, -1)))
+    while len(poses) < 8:
+        poses.append(synth.look_at_pose(synth.sphere_positions(rng, 1)[0]))
+    return synth.make_scene(objs, views, poses)
+
+
+@pytest.mark.parametrize("deterministic", [False, True])
+def test_alpha_compositing_parity(deterministic):
+    """variant 1 against the oracle's literal Eq. 9-10: forward planes and every
+    gradient, on each sort width, with and without normals and flow."""
+    _full_check(synth.config0(), n_flow=0, normals=False, variant=1, deterministic=deterministic)
+    _full_check(synth.config1(K=100, n_views=3, W=48, H=40), n_flow=1, variant=1, deterministic=deterministic)
+    _full_check(synth.config3(n_views=3, K=37, W=40, H=30), n_flow=2, variant=1, deterministic=deterministic)
+    _full_check(_ac_ragged_scene(), n_flow=1, variant=1, deterministic=deterministic)
+
+
+def test_alpha_compositing_persistent():
+    _full_check(_ac_ragged_scene(), n_flow=1, variant=1, use_persistent=1)
+
+
+def test_alpha_compositing_equal_depth_ties():
+    """Exact duplicates hit at bitwise-equal depths on the GPU too, so the strict
+    indicator of Eq. 10 leaves them unattenuated by each other, as in the oracle."""
+    s = synth.config1(K=50, n_views=2, W=32, H=24)
+    s2 = synth.make_scene([(np.concatenate([s.means] * 2), np.concatenate([s.chol] * 2),
+                            np.concatenate([s.weights] * 2))],
+                          [{k: v for k, v in vv.items() if k != "pix_offset"} for vv in s.views], s.poses)
+    _full_check(s2, n_flow=1, variant=1)
+
+
+def test_alpha_compositing_full_size_sampled():
+    """The 16-view 320x240 K=100 orbit, sampled pixels, forward and backward."""
+    s = synth.config1()
+    params = fmb.default_params(n_flow=1, variant=1)
+    gpu, r, dev = gpu_forward(s, params)
+    pix = sample_pixels(s, 150, 5)
+    ref = oracle_forward_sampled(s, pix, 1, variant=1)
+    amb = ac_order_ambiguous(s, pix)
+    compare_forward(s, gpu, None, 1, True, pixels_per_view=ref, variant=1, ambiguous=amb)
+    alpha_ref = np.zeros(s.n_pixels)
+    nn_ref = np.zeros(s.n_pixels)
+    amb_b = np.zeros(s.n_pixels, dtype=bool)
+    for vi, v in enumerate(s.views):
+        alpha_ref[v["pix_offset"] + ref[vi][0]] = ref[vi][1]["alpha"]
+        nn_ref[v["pix_offset"] + ref[vi][0]] = ref[vi][1]["saved"][:, 2]
+        amb_b[v["pix_offset"] + ref[vi][0]] = amb[vi]
+    ups = masked_upstream(s, alpha_ref, 1, seed=6, pixel_mask=pixel_mask_from(s, pix), nnorm_ref=nn_ref,
+                          exclude=amb_b)
+    g = gpu_backward(r, dev, ups)
+    compare_grads(g, oracle_backward_sampled(s, ups, pix, 1, variant=1))
