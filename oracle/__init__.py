@@ -72,6 +72,11 @@ def lib():
         L.fmbo_forward_ac.restype = ctypes.c_int
         L.fmbo_backward_ac.argtypes = L.fmbo_backward.argtypes
         L.fmbo_backward_ac.restype = ctypes.c_int
+        L.fmbo_points.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_longlong, lp,
+                                  dp, dp, dp, dp, ctypes.c_int]
+        L.fmbo_points.restype = ctypes.c_int
         L.fmbo_max_threads.argtypes = []
         L.fmbo_max_threads.restype = ctypes.c_int
         _lib = L
@@ -159,6 +164,50 @@ def backward_view(means, chol, weights, pose, target_poses, cam, g_depth=None, g
     if rc != 0:
         raise ValueError(f"fmbo_backward failed with status {rc}")
     out["target_poses"] = out["target_poses"][:T]
+    return out
+
+
+def points_view(means, chol, weights, pose, cam, variant=0, beta1=BETA1, beta2=BETA2, eta=ETA, pixels=None,
+                n_threads=0):
+    """Oriented point export of one view (Sec. 6; see fmbo_points): world-frame
+    points (n, 3), normals at the rendered depth (n, 3), screen-space cross-product
+    normals of Eq. 16 (n, 3) and the max-weight quality (n,)."""
+    means, chol, weights, pose = _f64(means), _f64(chol), _f64(weights), _f64(pose)
+    K = weights.shape[0]
+    W, H, fx, fy, cx, cy = cam
+    if pixels is None:
+        n = int(W) * int(H)
+        pix = None
+    else:
+        pix = np.ascontiguousarray(np.asarray(pixels, dtype=np.int64))
+        n = pix.shape[0]
+    out = dict(points=np.zeros((n, 3)), normal_tf=np.zeros((n, 3)), normal_screen=np.zeros((n, 3)),
+               quality=np.zeros(n))
+    rc = lib().fmbo_points(
+        int(variant), K, _dp(means), _dp(chol), _dp(weights), _dp(pose), int(W), int(H), float(fx), float(fy),
+        float(cx), float(cy), float(beta1), float(beta2), float(eta), n,
+        pix.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)) if pix is not None else None,
+        _dp(out["points"]), _dp(out["normal_tf"]), _dp(out["normal_screen"]), _dp(out["quality"]), int(n_threads))
+    if rc != 0:
+        raise ValueError(f"fmbo_points failed with status {rc}")
+    return out
+
+
+def points_scene(scene, variant=0, n_threads=0):
+    """points_view over every view, in the batched planar layouts: points,
+    normal_tf, normal_screen per view a (3, H*W) block at 3 * pix_offset; quality
+    one value per pixel."""
+    P = scene.n_pixels
+    out = dict(points=np.zeros(3 * P), normal_tf=np.zeros(3 * P), normal_screen=np.zeros(3 * P),
+               quality=np.zeros(P))
+    for v in scene.views:
+        sl = scene.object_slice(v["object"])
+        r = points_view(scene.means[sl], scene.chol[sl], scene.weights[sl], scene.poses[v["pose"]], _cam(v),
+                        variant=variant, n_threads=n_threads)
+        o, Pv = v["pix_offset"], v["W"] * v["H"]
+        for k in ("points", "normal_tf", "normal_screen"):
+            out[k][3 * o:3 * (o + Pv)] = r[k].T.reshape(-1)
+        out["quality"][o:o + Pv] = r["quality"]
     return out
 
 

@@ -644,6 +644,114 @@ int fmbo_backward_ac(int K, const double* means, const double* chol, const doubl
                        grad_weights, grad_pose, grad_target_poses, n_threads);
 }
 
+/*
+ * Oriented point export of Sec. 6, for ``n_pix`` pixels of one view (``pix`` = NULL:
+ * all), with the variant's weights (0: Eq. 7, 1: Eq. 9-10).  Per pixel, world frame:
+ *   points[n][3]        p = o + v D, the rendered point (D from Eq. 3)
+ *   normal_tf[n][3]     Eq. 17's per-Gaussian normal evaluated at the rendered depth
+ *                       instead of the hit depth, n_i = P_i (o + v D - mu_i) / |.|,
+ *                       blended by Eq. 3, renormalised, and turned to face the camera
+ *                       (negated when n . v > 0); 0 where the blend vanishes
+ *   normal_screen[n][3] Eq. 16: (p - p_x) x (p - p_y) / |.| with p_x, p_y the rendered
+ *                       points of the right and lower neighbour pixels (the left /
+ *                       upper one on the last column / row), turned to face the camera;
+ *                       0 without a neighbour or for a zero cross product
+ *   quality[n]          max_i w_i / sum_j w_j, the direct-intersection quality Sec. 6
+ *                       thresholds (typically at 0.9)
+ * Any output may be NULL.  Returns 0, 1 on invalid arguments, 2 on allocation failure.
+ */
+static void face_camera(double* n, const double* v) {
+  if (dot3(n, v) > 0.0)
+    for (int k = 0; k < 3; ++k) n[k] = -n[k];
+}
+
+int fmbo_points(int variant, int K, const double* means, const double* chol, const double* weights,
+                const double* pose, int W, int H, double fx, double fy, double cx, double cy,
+                double beta1, double beta2, double eta, long long n_pix, const long long* pix,
+                double* points, double* normal_tf, double* normal_screen, double* quality, int n_threads) {
+  if (check_args(K, W, H, 0, fx, fy, eta) || (variant != 0 && variant != 1)) return 1;
+  fmbo_camera cam = {W, H, fx, fy, cx, cy, beta1, beta2, eta, variant};
+  if (!pix) n_pix = (long long)W * H;
+  const double* R = pose;
+  const double* t = pose + 9;
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+  (void)n_threads;
+#endif
+  int failed = 0;
+#pragma omp parallel
+  {
+    pair_t* pairs = (pair_t*)malloc(sizeof(pair_t) * (size_t)K);
+    double* what = (double*)malloc(sizeof(double) * (size_t)K);
+    double* trans = (double*)malloc(sizeof(double) * (size_t)K);
+    if (!pairs || !what || !trans) {
+#pragma omp atomic write
+      failed = 1;
+    } else {
+#pragma omp for schedule(static)
+      for (long long n = 0; n < n_pix; ++n) {
+        long long p = pix ? pix[n] : n;
+        double vcam[3], v[3], o[3], pxy[2];
+        ray_out_t out;
+        pixel_ray(&cam, R, t, p, vcam, v, o, pxy);
+        forward_ray(K, means, chol, weights, &cam, R, v, o, pxy, 0, NULL, pairs, what, trans, &out);
+        if (points)
+          for (int k = 0; k < 3; ++k) points[3 * n + k] = out.p[k];
+        if (quality) {
+          double q = 0.0;
+          for (int i = 0; i < K; ++i)
+            if (what[i] > q) q = what[i];
+          quality[n] = q;
+        }
+        if (normal_tf) {
+          double N[3] = {0, 0, 0};
+          for (int i = 0; i < K; ++i) {
+            double L[9], P[9], r[3], g[3];
+            unpack_L(chol + 6 * i, L);
+            precision_from_L(L, P);
+            for (int k = 0; k < 3; ++k) r[k] = out.p[k] - means[3 * i + k];
+            matvec(P, r, g);
+            double gn = sqrt(dot3(g, g));
+            if (gn > 0.0)
+              for (int k = 0; k < 3; ++k) N[k] += what[i] * g[k] / gn;
+          }
+          double Nn = sqrt(dot3(N, N));
+          for (int k = 0; k < 3; ++k) normal_tf[3 * n + k] = Nn > 0.0 ? N[k] / Nn : 0.0;
+          face_camera(normal_tf + 3 * n, v);
+        }
+        if (normal_screen) {
+          int x = (int)(p % W), y = (int)(p / W);
+          double* ns = normal_screen + 3 * n;
+          ns[0] = ns[1] = ns[2] = 0.0;
+          if (W > 1 && H > 1) {
+            long long nb[2] = {(long long)y * W + (x + 1 < W ? x + 1 : x - 1),
+                               (long long)(y + 1 < H ? y + 1 : y - 1) * W + x};
+            double d[2][3];
+            for (int j = 0; j < 2; ++j) {
+              double vc2[3], v2[3], o2[3], pxy2[2];
+              ray_out_t o_nb;
+              pixel_ray(&cam, R, t, nb[j], vc2, v2, o2, pxy2);
+              forward_ray(K, means, chol, weights, &cam, R, v2, o2, pxy2, 0, NULL, pairs, what, trans, &o_nb);
+              for (int k = 0; k < 3; ++k) d[j][k] = out.p[k] - o_nb.p[k];
+            }
+            double c[3] = {d[0][1] * d[1][2] - d[0][2] * d[1][1], d[0][2] * d[1][0] - d[0][0] * d[1][2],
+                           d[0][0] * d[1][1] - d[0][1] * d[1][0]};
+            double cn = sqrt(dot3(c, c));
+            if (cn > 0.0)
+              for (int k = 0; k < 3; ++k) ns[k] = c[k] / cn;
+            face_camera(ns, v);
+          }
+        }
+      }
+    }
+    free(pairs);
+    free(what);
+    free(trans);
+  }
+  return failed ? 2 : 0;
+}
+
 /* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
 int fmbo_max_threads(void) {
 #ifdef _OPENMP

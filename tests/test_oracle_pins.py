@@ -387,3 +387,77 @@ def test_ac_dense_front_gaussian_occludes(oracle_mod):
     r = oracle_mod.render_view(mu, chol, np.array([3.0, 60.0, 5.0]), pose, None, CAM, pixels=[4 * CAM[0] + 4],
                                variant=1)
     assert abs(r["depth"][0] - 3.1) < 1e-12
+
+
+# ------------------------------------------------------ oriented point export (Sec. 6)
+
+
+def test_points_quality_closed_forms(oracle_mod):
+    """quality = max_i w_i / sum w: 1 for one Gaussian; for two Gaussians centred on
+    one ray, Eq. 7 gives s = w2/w1 = (l2/l1)^beta1 e^(-beta2 (r2 - r1)) and
+    quality = max(1, s) / (1 + s), and Eq. 9-10 give w1 = 1 - e^-l1,
+    w2 = e^-l1 (1 - e^-l2); exact duplicates under Eq. 7 split the weight: 1/2."""
+    pose = synth.look_at_pose((0.0, 0.0, -4.0))
+    x, y = 5, 7
+    v, o, _ = ray_of_pixel(pose, CAM, x, y)
+    pixel = [y * CAM[0] + x]
+    one = oracle_mod.points_view(np.atleast_2d(o + 3.7 * v), np.array([[2.0, 0, 2.0, 0, 0, 2.0]]), np.array([0.8]),
+                                 pose, CAM, pixels=pixel)
+    assert one["quality"][0] == 1.0
+    np.testing.assert_allclose(one["points"][0], o + 3.7 * v, atol=1e-12)  # through the centre: p = mu
+    chol = np.array([[3, 0.2, 2, -0.1, 0.3, 4], [1.5, 0, 1.5, 0, 0, 1.5]], dtype=np.float64)
+    for (r1, r2, l1, l2) in [(3.5, 4.5, 1.0, 1.0), (3.0, 3.2, 0.9, 1.1), (3.9, 4.4, 1.2, 0.7)]:
+        mu = np.stack([o + r1 * v, o + r2 * v])
+        lam = np.array([l1, l2])
+        s = np.exp(B1 * np.log(l2 / l1) - B2 * (r2 - r1))
+        q0 = oracle_mod.points_view(mu, chol, lam, pose, CAM, pixels=pixel)["quality"][0]
+        assert abs(q0 - max(1.0, s) / (1.0 + s)) < 1e-12
+        w1, w2 = 1 - np.exp(-l1), np.exp(-l1) * (1 - np.exp(-l2))
+        q1 = oracle_mod.points_view(mu, chol, lam, pose, CAM, pixels=pixel, variant=1)["quality"][0]
+        assert abs(q1 - max(w1, w2) / (w1 + w2)) < 1e-12
+    dup = oracle_mod.points_view(np.stack([o + 3.7 * v] * 2), chol[[1, 1]], np.array([0.8, 0.8]), pose, CAM,
+                                 pixels=pixel)
+    assert abs(dup["quality"][0] - 0.5) < 1e-15
+
+
+def test_points_normal_at_rendered_depth_two_centred(oracle_mod):
+    """Two isotropic Gaussians centred on one ray at r1 < r2: the rendered depth lies
+    between them, so the normal of each evaluated there points along the ray
+    (+v for the front one, -v for the back one) and their blend, turned to face the
+    camera, is -v -- whichever of the two weighs more (both cases are run)."""
+    pose = synth.look_at_pose((0.3, -0.2, -4.0))
+    x, y = 9, 4
+    v, o, _ = ray_of_pixel(pose, CAM, x, y)
+    for lam in ([1.0, 0.6], [0.6, 1.0]):
+        for variant in (0, 1):
+            mu = np.stack([o + 3.4 * v, o + 4.1 * v])
+            chol = np.array([[2.0, 0, 2.0, 0, 0, 2.0], [1.2, 0, 1.2, 0, 0, 1.2]])
+            r = oracle_mod.points_view(mu, chol, np.array(lam), pose, CAM, pixels=[y * CAM[0] + x], variant=variant)
+            np.testing.assert_allclose(r["normal_tf"][0], -v, atol=1e-12)
+
+
+def _plane_gaussian(nrm, centre, eps=1e-6):
+    """A Gaussian whose precision is n n^T + eps^2 I: its max-likelihood depth along
+    any ray is the ray's intersection with the plane through ``centre`` with normal
+    ``nrm`` up to a relative O(eps^2)."""
+    P = np.outer(nrm, nrm) + eps ** 2 * np.eye(3)
+    L = np.linalg.cholesky(P)
+    return centre[None], np.array([[L[0, 0], L[1, 0], L[1, 1], L[2, 0], L[2, 1], L[2, 2]]]), np.array([1.0])
+
+
+def test_points_screen_normal_of_a_plane(oracle_mod):
+    """Eq. 16 on a rendered plane: every pixel's cross-product normal is the plane's
+    normal, turned towards the camera (also on the last column and row, whose
+    neighbours are taken on the other side), and the points lie on the plane."""
+    pose = synth.look_at_pose((0.5, 0.4, -4.0))
+    R = np.asarray(pose[:9]).reshape(3, 3)
+    cam_dir = R.T @ np.array([0.0, 0.0, 1.0])
+    for nrm in (np.array([0.2, -0.3, 1.0]), np.array([0.5, 0.1, -1.0])):
+        nrm = nrm / np.linalg.norm(nrm)
+        mu, chol, lam = _plane_gaussian(nrm, np.array([0.1, -0.2, 0.3]))
+        r = oracle_mod.points_view(mu, chol, lam, pose, CAM)
+        want = -np.sign(nrm @ cam_dir) * nrm
+        np.testing.assert_allclose(r["normal_screen"], np.broadcast_to(want, r["normal_screen"].shape), atol=1e-8)
+        np.testing.assert_allclose((r["points"] - mu[0]) @ nrm, 0.0, atol=1e-9)
+    line = oracle_mod.points_view(mu, chol, lam, pose, (7, 1, 7.0, 7.0, 3.5, 0.5))
+    assert np.all(line["normal_screen"] == 0.0)  # one row: no vertical neighbour
