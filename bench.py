@@ -442,6 +442,22 @@ def run_gpu(args):
         "gpu_launches": 5 * args.steps,  # prologue + forward; zeroing + prologue + backward per step
         "e2e": e2e,
     }
+    if args.points:
+        # oriented point export (Sec. 6) of the batch just rendered, timed alone
+        for _ in range(3):
+            batched.points(means, chol, weights, poses)
+        torch.cuda.synchronize(dev)
+        n_p = max(args.steps // 4, 3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n_p):
+            batched.points(means, chol, weights, poses)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms_p = e0.elapsed_time(e1) / n_p
+        line["points_export"] = {"ms": ms_p, "value": pairs / (ms_p * 1e-3), "unit": "pairs/s", "steps": n_p,
+                                 "what": "points, normals at the rendered depth, Eq. 16 screen normals and the "
+                                         "max-weight quality of every pixel (fmb_render_points)"}
     if args.workload == "recon" or args.stored:
         line["stored_vs_recompute"] = stored_adjoint_measure(args, s, (gd, ga, gn, gf), tuned_params, dev)
     if args.workload == "recon":
@@ -662,6 +678,16 @@ def cpu_baseline(s, ups, renderer, grads, args):
     # the plain arm compares too: its summed per-view gradients must equal the batched ones
     out["plain_vs_batched_grad_max_rel"] = {
         k: float((args.psum[k] - grads[k]).abs().max() / grads[k].abs().max()) for k in grads}
+    if var == 1:
+        # Alpha compositing: depth, normal, flow and their gradients jump where two
+        # hits are closer in depth than fp32 resolves (a discrete order decision);
+        # the parity tests flag those pixels, this whole-image report would not.
+        a = renderer.alpha.cpu().numpy().astype(np.float64)
+        out["parity"] = {"alpha_max_abs": float(np.max(np.abs(a - ref["alpha"])))}
+        out["parity_note"] = ("alpha compositing: only the order-independent alpha plane is compared here; depth, "
+                              "normal, flow and gradients are compared by the parity tests away from fp32 "
+                              "depth-order ties")
+        return out
     d = renderer.depth.cpu().numpy().astype(np.float64)
     mask = ref["alpha"] >= 1e-2
     err = {"depth_max_abs": float(np.max(np.abs(d - ref["depth"])[mask]))}
@@ -720,6 +746,7 @@ def main():
     ap.add_argument("--workload", default="orbit", choices=sorted(WORKLOADS))
     ap.add_argument("--variant", default="two-param", choices=["two-param", "ac"],
                     help="weights of Eq. 3: the two-parameter model (Eq. 7) or alpha compositing (Eq. 9-10)")
+    ap.add_argument("--points", action="store_true", help="also time the oriented point export (Sec. 6)")
     ap.add_argument("--stored", action="store_true",
                     help="also time the stored-intermediate adjoint (always on for --workload recon)")
     args = ap.parse_args()

@@ -66,7 +66,10 @@ typedef struct {
   float beta1;
   float beta2;
   float eta;
-  int variant;       /* 0 = two-parameter model of Sec. 3.2 (the only one implemented) */
+  int variant;       /* 0 = two-parameter model of Sec. 3.2 (Eq. 7 weights);
+                        1 = alpha compositing of Sec. 3.3 (Eq. 9-10 weights, hits sorted by
+                        depth per ray; at most 256 Gaussians per object; saved[0] then
+                        holds W = sum of the weights instead of the log2 normaliser) */
   int want_normals;  /* 1: compute the blended normal plane (Eq. 17) and its adjoint */
   int n_flow;        /* flow slots per view, 0..2 (Sec. 5: forward i+1 and backward i-1) */
   int deterministic; /* backward: 1 = fixed-order two-stage reduction, 0 = fp32 atomics */
@@ -118,6 +121,7 @@ typedef struct {
  *                             n_flow == 0
  *   saved  [3*P_total]        per view a [3][P_v] block at 3*pix_offset:
  *                             0: log2 of sum_i 2^(e_i log2 e), e_i = beta1 d_i - (beta2/eta) t_i
+ *                                (variant 1: W = sum_i w_i)
  *                             1: sum_i delta_i;  2: |N| (0 without normals)
  *                             The backward pass needs it.
  * Views may not overlap in the output planes (checked).
@@ -181,6 +185,31 @@ fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n_objects, c
                                       const float* means, const float* chol, const float* weights, int n_poses,
                                       const float* poses, int n_views, const fmb_view* h_views, float* depth,
                                       float* alpha, float* normal, float* flow, float* saved, fmb_stream_t stream);
+
+/*
+ * Oriented point export (Sec. 6: the oriented point set a Poisson surface
+ * reconstruction takes; the Poisson solve itself is not part of this library).
+ * For every pixel of the batch, from the depth and saved planes of a
+ * fmb_render_forward call with the same scene, views and params:
+ *   points        [3*P_total] per view a [3][P_v] block at 3*pix_offset: the
+ *                 rendered point o + v D (world frame)
+ *   normal_tf     same layout: Eq. 17's per-Gaussian normal evaluated at the
+ *                 rendered depth D instead of the hit depth, blended by Eq. 3 with
+ *                 the variant's weights, unit length and turned to face the camera
+ *                 (world frame; 0 where the blend vanishes)
+ *   normal_screen same layout: Eq. 16, the normalised cross product of the
+ *                 differences to the rendered points of the right and lower
+ *                 neighbour pixels (left / upper on the last column / row), turned
+ *                 to face the camera (world frame; 0 for one-pixel-wide images)
+ *   quality       [P_total]: max_i w_i / sum_j w_j, the direct-intersection quality
+ *                 that Sec. 6 thresholds (typically at 0.9)
+ * Any output may be NULL.  workspace as for fmb_render_forward (it is rewritten).
+ */
+fmb_status fmb_render_points(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
+                             const float* means, const float* chol, const float* weights, int n_poses,
+                             const float* poses, int n_views, const fmb_view* h_views, const float* depth,
+                             const float* saved, float* points, float* normal_tf, float* normal_screen,
+                             float* quality, void* workspace, size_t workspace_bytes, fmb_stream_t stream);
 
 /* Workspace bytes needed by fmb_render_forward and fmb_render_backward for this
  * batch (the larger of the two).  Returns 0 on invalid arguments (see

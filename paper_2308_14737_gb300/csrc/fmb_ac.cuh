@@ -1,0 +1,204 @@
+// fmb_ac.cuh -- device helpers of the alpha-compositing variant (Sec. 3.3,
+// Eq. 9-10), shared by its render, adjoint and point-export kernels: one warp per
+// ray, a bitonic network over the warp's 32 M keys (t's order-preserving integer
+// image in the high word, the Gaussian index in the low word), run-aware prefix
+// sums of delta for the transmittance.
+#pragma once
+
+#include "fmb_internal.cuh"
+
+namespace fmb {
+
+
+constexpr int kAcWarps = 4;
+constexpr int kAcThreads = 32 * kAcWarps;
+constexpr int kAcRays = 32;          // rays per work item (forward and backward)
+constexpr int kAcRayRec = 5;         // backward per-ray record, float4s (values duplicated)
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr unsigned long long kNoKey = ~0ull;
+
+// Order-preserving map of a float to an unsigned integer (and back).
+__device__ __forceinline__ unsigned order_bits(float t) {
+  const unsigned u = __float_as_uint(t);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float from_order_bits(unsigned u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// 1 - e^-x for x >= 0 without cancellation: the Maclaurin series for small x
+// (relative truncation error below x^7 / 8! < 2e-9 for x < 1/4), else 1 - 2^(-x log2 e).
+__device__ __forceinline__ float one_minus_exp_neg(float x) {
+  const float series =
+      x * (1.f - x * 0.5f * (1.f - x * (1.f / 3.f) * (1.f - x * 0.25f * (1.f - x * 0.2f * (1.f - x * (1.f / 6.f) *
+                                                                                          (1.f - x * (1.f / 7.f)))))));
+  return x < 0.25f ? series : 1.f - ex2_approx(-x * kLog2e);
+}
+
+// Ascending bitonic sort of the warp's 32 M keys; element i = m * 32 + lane.
+template <int M>
+__device__ __forceinline__ void warp_bitonic_sort(unsigned long long (&key)[M], int lane) {
+  constexpr int N = 32 * M;
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {  // partner in another register of the same lane
+        const int jm = j >> 5;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          if ((m & jm) == 0) {
+            const int m2 = m | jm;
+            const bool up = ((m << 5) & k) == 0;
+            const unsigned long long a = key[m], b = key[m2];
+            const bool swap = up ? (a > b) : (a < b);
+            key[m] = swap ? b : a;
+            key[m2] = swap ? a : b;
+          }
+        }
+      } else {  // partner in lane ^ j
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const unsigned long long other = __shfl_xor_sync(kFull, key[m], j);
+          const int i = (m << 5) | lane;
+          const bool take_min = ((i & j) == 0) == ((i & k) == 0);
+          const bool other_smaller = other < key[m];
+          key[m] = (take_min == other_smaller) ? other : key[m];
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ float warp_incl_sum(float x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+__device__ __forceinline__ float warp_incl_max(float x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x = fmaxf(x, y);
+  }
+  return x;
+}
+__device__ __forceinline__ float warp_allsum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+
+// One ray of the alpha-compositing render, by one warp.  Per lane, for its
+// Gaussians e = m * 32 + lane: hit depth t[m], density dl[m], Eq. 17 normal n[m]
+// (NORMALS).  sd / sw / sT: the warp's shared scratch, indexed by Gaussian (32 M
+// floats each).  Leaves w_e in sw and T_e in sT, and returns the warp-uniform sums.
+struct AcSums {
+  float W, WT, WN0, WN1, WN2, Sd;
+};
+
+template <bool NORMALS, int M>
+__device__ __forceinline__ AcSums ac_render_ray(const float4* __restrict__ rec, int K, const float v[3],
+                                                const float vl[3], const Consts& k, int lane, float (&t)[M],
+                                                float (&dl)[M], float (&n)[M][3], float* sd, float* sw, float* sT) {
+  unsigned long long key[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int e = (m << 5) | lane;
+    t[m] = 0.f;
+    dl[m] = 0.f;
+    n[m][0] = n[m][1] = n[m][2] = 0.f;
+    key[m] = kNoKey;
+    if (e < K) {
+      const GaussRec g = unpack_rec(rec[kRecFloat4 * e], rec[kRecFloat4 * e + 1], rec[kRecFloat4 * e + 2],
+                                    rec[kRecFloat4 * e + 3]);
+      const PairGeom G = pair_geom(g.L, g.b, g.mh, g.nbl, v[0], v[1], v[2], vl[0], vl[1], vl[2]);
+      t[m] = G.t;
+      dl[m] = ex2_approx(fmaf(G.q, k.K3, g.l2));  // delta (Eq. 4)
+      if (NORMALS) {
+        const float g0 = g.L[0] * G.u0;
+        const float g1 = fmaf(g.L[2], G.u1, g.L[1] * G.u0);
+        const float g2 = fmaf(g.L[5], G.u2, fmaf(g.L[4], G.u1, g.L[3] * G.u0));
+        const float rs = rsqrt_approx(fmaxf(fmaf(g2, g2, fmaf(g1, g1, g0 * g0)), 1e-30f));
+        n[m][0] = g0 * rs;
+        n[m][1] = g1 * rs;
+        n[m][2] = g2 * rs;
+      }
+      sd[e] = dl[m];
+      key[m] = (static_cast<unsigned long long>(order_bits(G.t)) << 32) | static_cast<unsigned>(e);
+    }
+  }
+  __syncwarp();
+  warp_bitonic_sort<M>(key, lane);
+  // Sorted order: exclusive prefix sums of delta, run-aware (Eq. 10's strict <).
+  float carry = 0.f, carry_t = 0.f, carry_S = 0.f;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const bool valid = key[m] != kNoKey;
+    const int idx = static_cast<int>(key[m] & 0xffffffffu);
+    const float ts = valid ? from_order_bits(static_cast<unsigned>(key[m] >> 32)) : INFINITY;
+    const float ds = valid ? sd[idx] : 0.f;
+    const float incl = warp_incl_sum(ds, lane);
+    float excl = __shfl_up_sync(kFull, incl, 1);
+    if (lane == 0) excl = 0.f;
+    excl += carry;
+    float prev_t = __shfl_up_sync(kFull, ts, 1);
+    if (lane == 0) prev_t = carry_t;
+    const bool start = (m == 0 && lane == 0) || ts != prev_t;
+    // P (the exclusive sums) never decreases, so the sum in front of this hit's
+    // run is the largest P at a run start so far.
+    const float S = fmaxf(warp_incl_max(start ? excl : 0.f, lane), carry_S);
+    const float T = ex2_approx(-S * kLog2e);
+    if (valid) {
+      sT[idx] = T;
+      sw[idx] = T * one_minus_exp_neg(ds);
+    }
+    carry += __shfl_sync(kFull, incl, 31);
+    carry_t = __shfl_sync(kFull, ts, 31);
+    carry_S = __shfl_sync(kFull, S, 31);
+  }
+  __syncwarp();
+  AcSums r{0.f, 0.f, 0.f, 0.f, 0.f, carry};
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int e = (m << 5) | lane;
+    if (e < K) {
+      const float w = sw[e];
+      r.W += w;
+      r.WT = fmaf(w, t[m], r.WT);
+      if (NORMALS) {
+        r.WN0 = fmaf(w, n[m][0], r.WN0);
+        r.WN1 = fmaf(w, n[m][1], r.WN1);
+        r.WN2 = fmaf(w, n[m][2], r.WN2);
+      }
+    }
+  }
+  r.W = warp_allsum(r.W);
+  r.WT = warp_allsum(r.WT);
+  if (NORMALS) {
+    r.WN0 = warp_allsum(r.WN0);
+    r.WN1 = warp_allsum(r.WN1);
+    r.WN2 = warp_allsum(r.WN2);
+  }
+  return r;
+}
+
+// Stages a view's K records into shared memory with one bulk copy; every thread
+// waits (bounded).  Returns false (after recording the timeout) if the copy did
+// not arrive.
+__device__ __forceinline__ bool ac_stage_records(float4* dst, const float4* src, int K, uint64_t* bar,
+                                                 unsigned& uses, int* status) {
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(bar, static_cast<uint32_t>(K) * kRecBytes);
+    bulk_g2s(dst, src, static_cast<uint32_t>(K) * kRecBytes, bar);
+  }
+  const bool ok = mbar_wait_bounded(bar, uses & 1u, status);
+  ++uses;
+  return !__syncthreads_or(!ok);
+}
+
+}  // namespace fmb

@@ -455,6 +455,49 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
   }
 }
 
+fmb_status fmb_render_points(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
+                             const float* means, const float* chol, const float* weights, int n_poses,
+                             const float* poses, int n_views, const fmb_view* h_views, const float* depth,
+                             const float* saved, float* points, float* normal_tf, float* normal_screen,
+                             float* quality, void* workspace, size_t workspace_bytes, fmb_stream_t stream) {
+  try {
+    g_err.clear();
+    fmb_status st = validate_scene(params, n_objects, h_obj_offsets, n_views, h_views);
+    if (st != FMB_OK) return st;
+    if (n_poses < 1 || !poses) return fail(FMB_ERR_INVALID_ARG, "poses missing");
+    if (!means || !chol || !weights) return fail(FMB_ERR_INVALID_ARG, "means, chol and weights are required");
+    if (!depth || !saved) return fail(FMB_ERR_INVALID_ARG, "depth and saved (forward outputs) are required");
+    st = validate_views(n_objects, n_poses, n_views, h_views);
+    if (st != FMB_OK) return st;
+    Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views);
+    st = check_workspace(workspace, workspace_bytes, workspace_needed(params, pl));
+    if (st != FMB_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    float4* records = reinterpret_cast<float4*>(static_cast<char*>(workspace) + kHeaderBytes);
+    const fmb::Scene sc{means, chol, weights, poses};
+    const fmb::Consts c = make_consts(params);
+    const int per = fmb::points_rays_per_item(params->variant);
+    for (fmb::Batch b : pl.fwd) {
+      for (int i = 0; i < b.n_views; ++i) {
+        const long long P = static_cast<long long>(b.v[i].W) * b.v[i].H;
+        b.v[i].n_tiles = static_cast<int>((P + per - 1) / per);
+      }
+      order_items(b, [&](const fmb::DevView& v) { return static_cast<double>(v.K); },
+                  [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles); });
+      cudaError_t e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, nullptr, s);
+      if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
+      e = fmb::launch_points(b, sc, c, records, params->variant, pl.maxK, depth, saved, points, normal_tf,
+                             normal_screen, quality, s);
+      if (e != cudaSuccess) return cuda_fail(e, "points launch");
+    }
+    return FMB_OK;
+  } catch (const std::exception& e) {
+    return fail(FMB_ERR_INVALID_ARG, e.what());
+  } catch (...) {
+    return fail(FMB_ERR_INVALID_ARG, "unknown error");
+  }
+}
+
 fmb_status fmb_read_device_status(const void* workspace, int* h_status, fmb_stream_t stream) {
   if (!workspace || !h_status) return fail(FMB_ERR_INVALID_ARG, "workspace and h_status are required");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

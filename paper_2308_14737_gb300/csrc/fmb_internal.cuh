@@ -414,6 +414,11 @@ cudaError_t launch_forward_ac(const Batch& b, const Scene& s, const Consts& c, c
 cudaError_t launch_backward_ac(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
                                int n_flow, int maxK, const BwdIn& in, const BwdOut& out, int* status, int* counter,
                                cudaStream_t st);
+// Oriented point export (Sec. 6): work items of points_rays_per_item(variant) pixels.
+int points_rays_per_item(int variant);
+cudaError_t launch_points(const Batch& b, const Scene& s, const Consts& c, const float4* records, int variant,
+                          int maxK, const float* depth, const float* saved, float* points, float* normal_tf,
+                          float* normal_scr, float* quality, cudaStream_t st);
 cudaError_t launch_backward_reduce(const Batch& b, int n_flow, long long n_gauss, int n_poses,
                                    const BwdOut& out, cudaStream_t st);
 

@@ -77,6 +77,8 @@ def load_library(path: str = LIB_PATH):
     L.fmb_adam_step.argtypes = [ctypes.POINTER(FmbAdamParams), fp, fp, fp, fp, ctypes.c_longlong, ctypes.c_longlong,
                                 fp, vp]
     L.fmb_adam_step.restype = ctypes.c_int
+    L.fmb_render_points.argtypes = [P, i, LL, fp, fp, fp, i, fp, i, V, fp, fp, fp, fp, fp, fp, vp, sz, vp]
+    L.fmb_render_points.restype = ctypes.c_int
     L.fmb_workspace_bytes.argtypes = [P, i, LL, i, V]
     L.fmb_workspace_bytes.restype = sz
     L.fmb_read_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
@@ -180,6 +182,17 @@ def fmb_render_forward_noalloc(params, obj_offsets, means, chol, weights, poses,
                                         _ptr(alpha), _ptr(normal), _ptr(flow), _ptr(saved), _stream(stream)))
 
 
+def fmb_render_points(params, obj_offsets, means, chol, weights, poses, views, depth, saved, points, normal_tf,
+                      normal_screen, quality, workspace, stream=None):
+    L = load_library()
+    o, op = _offsets(obj_offsets)
+    va = views if isinstance(views, ctypes.Array) else make_views(views)
+    _check(L.fmb_render_points(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol), _ptr(weights),
+                               int(poses.shape[0]), _ptr(poses), len(va), va, _ptr(depth), _ptr(saved), _ptr(points),
+                               _ptr(normal_tf), _ptr(normal_screen), _ptr(quality), _ptr(workspace),
+                               workspace.numel(), _stream(stream)))
+
+
 def fmb_render_backward(params, obj_offsets, means, chol, weights, poses, views, depth, normal, saved, g_depth,
                         g_alpha, g_normal, g_flow, grad_means, grad_chol, grad_weights, grad_poses, workspace,
                         stream=None):
@@ -244,6 +257,18 @@ class Renderer:
         fmb_render_forward(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, self.depth,
                            self.alpha, self.normal, self.flow, self.saved, self.ws, stream)
         return dict(depth=self.depth, alpha=self.alpha, normal=self.normal, flow=self.flow, saved=self.saved)
+
+    def points(self, means, chol, weights, poses, stream=None):
+        """Oriented point export (Sec. 6) of the last forward call's depth: world
+        points, normals at the rendered depth, screen-space normals (Eq. 16), each
+        a planar [3][P_v] block per view, and the max-weight quality [P]."""
+        f32 = dict(dtype=torch.float32, device=self.depth.device)
+        out = dict(points=torch.empty(3 * self.P, **f32), normal_tf=torch.empty(3 * self.P, **f32),
+                   normal_screen=torch.empty(3 * self.P, **f32), quality=torch.empty(self.P, **f32))
+        fmb_render_points(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, self.depth,
+                          self.saved, out["points"], out["normal_tf"], out["normal_screen"], out["quality"], self.ws,
+                          stream)
+        return out
 
     def backward(self, means, chol, weights, poses, g_depth, g_alpha, g_normal, g_flow, want_pose=True,
                  out=None, stream=None):

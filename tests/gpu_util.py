@@ -336,3 +336,90 @@ def pixel_mask_from(scene, pix_per_view):
     for vi, v in enumerate(scene.views):
         m[v["pix_offset"] + np.asarray(pix_per_view[vi], dtype=np.int64)] = 1.0
     return m
+
+
+def _view_pairs_fp64(scene, v):
+    """FP64 per (pixel, Gaussian) quantities of one whole view: world rays, hit
+    depths t, densities delta and the precision matrices (test-side restatement of
+    Eq. 2 and Eq. 4, used only to bound how much fp32 rounding can move an output)."""
+    idx = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
+    sl = scene.object_slice(v["object"])
+    K = sl.stop - sl.start
+    R = scene.poses[v["pose"]][:9].astype(np.float64).reshape(3, 3)
+    t = scene.poses[v["pose"]][9:].astype(np.float64)
+    P = v["W"] * v["H"]
+    pix = np.arange(P)
+    x = pix % v["W"] + 0.5
+    y = pix // v["W"] + 0.5
+    c = np.stack([(x - v["cx"]) / v["fx"], (y - v["cy"]) / v["fy"], np.ones(P)], 1)
+    vw = (c / np.linalg.norm(c, axis=1, keepdims=True)) @ R
+    o = -R.T @ t
+    L = np.zeros((K, 3, 3))
+    ch = scene.chol[sl].astype(np.float64)
+    for k, (a, b) in enumerate(idx):
+        L[:, a, b] = ch[:, k]
+    Pm = L @ L.transpose(0, 2, 1)
+    m = scene.means[sl].astype(np.float64) - o
+    Pv = np.einsum("kab,pb->pka", Pm, vw)
+    tt = np.einsum("ka,pka->pk", m, Pv) / np.einsum("pa,pka->pk", vw, Pv)
+    r = vw[:, None, :] * tt[..., None] - m[None]
+    q = np.einsum("pka,kab,pkb->pk", r, Pm, r)
+    d = -0.5 * q + np.log(scene.weights[sl].astype(np.float64))[None]
+    return vw, o, m, Pm, Pv, tt, d
+
+
+def points_tolerances(scene, ref, variant, dD, beta1=21.4, beta2=3.14):
+    """Per-pixel tolerances of the point export.  The GPU evaluates the export at
+    its own fp32 depth, the oracle at its FP64 depth; ``dD`` (batched) is the depth
+    difference to propagate (the parity test passes the measured |D_gpu - D_ref|,
+    itself checked against 1e-4 + 1e-5 |D|, plus 1e-6 |D|):
+      points         1e-4 + 1e-5 |D| per component (p = o + v D, |v| = 1)
+      normal_tf      2 dD max_i(|Sigma_i^-1 v| / |g_i|) / |N| + 1e-4, the rate at
+                     which a per-Gaussian normal at depth D turns with D (over
+                     Gaussians with weight > 1e-4), through the renormalisation
+      normal_screen  4 dD (|d_x| + |d_y|) / |d_x x d_y| + 1e-4, the cross product
+                     of two point differences each off by up to 2 dD (dD the largest
+                     of the three pixels')
+    Returns batched arrays (points, normal_tf, normal_screen) and, for the two
+    normals, where their camera-facing sign is not decided at that tolerance
+    (|n_ref . v| <= tol: the normal lies within tol of the plane perpendicular to
+    the ray -- at the hit depth every Eq. 17 normal lies in that plane, and a
+    sharply peaked two-parameter blend renders close to one hit depth)."""
+    Pn = scene.n_pixels
+    tp, tn, ts = np.zeros(Pn), np.zeros(Pn), np.zeros(Pn)
+    amb_n, amb_s = np.zeros(Pn, dtype=bool), np.zeros(Pn, dtype=bool)
+    for v in scene.views:
+        o_, Pv_ = v["pix_offset"], v["W"] * v["H"]
+        vw, o, m, Pm, Pv, tt, d = _view_pairs_fp64(scene, v)
+        D = ref["depth"][o_:o_ + Pv_]
+        tolD = 1e-4 + 1e-5 * np.abs(D)
+        dDv = dD[o_:o_ + Pv_]
+        if variant == 1:
+            delta = np.exp(d)
+            front = (tt[:, None, :] < tt[:, :, None])
+            S = np.einsum("pij,pj->pi", front, delta)
+            w = np.exp(-S) * -np.expm1(-delta)
+        else:
+            e = beta1 * d - beta2 * tt
+            w = np.exp(e - e.max(1, keepdims=True))
+        w = w / np.maximum(w.sum(1, keepdims=True), 1e-300)
+        g = np.einsum("kab,pkb->pka", Pm, vw[:, None, :] * D[:, None, None] - m[None])
+        gn = np.linalg.norm(g, axis=-1)
+        N = np.einsum("pk,pka->pa", w, g / np.maximum(gn, 1e-300)[..., None])
+        rate = np.where(w > 1e-4, np.linalg.norm(Pv, axis=-1) / np.maximum(gn, 1e-300), 0.0).max(1)
+        tp[o_:o_ + Pv_] = tolD
+        tn[o_:o_ + Pv_] = 2 * dDv * rate / np.maximum(np.linalg.norm(N, axis=1), 1e-300) + 1e-4
+        pts = plane_view(ref["points"], v, 3).T
+        W_, H_ = v["W"], v["H"]
+        pix = np.arange(Pv_)
+        xx, yy = pix % W_, pix // W_
+        nx = yy * W_ + np.where(xx + 1 < W_, xx + 1, xx - 1)
+        ny = np.where(yy + 1 < H_, yy + 1, yy - 1) * W_ + xx
+        dx, dy = pts - pts[nx], pts - pts[ny]
+        cr = np.linalg.norm(np.cross(dx, dy), axis=1)
+        tolDn = np.maximum(np.maximum(dDv, dDv[nx]), dDv[ny])
+        ts[o_:o_ + Pv_] = 4 * tolDn * (np.linalg.norm(dx, axis=1) + np.linalg.norm(dy, axis=1)) / np.maximum(
+            cr, 1e-300) + 1e-4
+        amb_n[o_:o_ + Pv_] = np.abs(np.sum(plane_view(ref["normal_tf"], v, 3).T * vw, 1)) <= tn[o_:o_ + Pv_]
+        amb_s[o_:o_ + Pv_] = np.abs(np.sum(plane_view(ref["normal_screen"], v, 3).T * vw, 1)) <= ts[o_:o_ + Pv_]
+    return tp, tn, ts, amb_n, amb_s

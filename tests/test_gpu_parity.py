@@ -13,6 +13,7 @@ import oracle
 from paper_2308_14737_gb300 import fmb, synth
 
 from gpu_util import (ac_order_ambiguous, compare_forward, compare_grads, gpu_backward, gpu_forward, masked_upstream,
+                      plane_view, points_tolerances,
                       nnorm_batched,
                       oracle_backward_sampled, oracle_forward_sampled, pixel_mask_from, sample_pixels)
 
@@ -308,3 +309,45 @@ def test_alpha_compositing_full_size_sampled():
                           exclude=amb_b)
     g = gpu_backward(r, dev, ups)
     compare_grads(g, oracle_backward_sampled(s, ups, pix, 1, variant=1))
+
+
+# ---------------------------------------------------- oriented point export (Sec. 6)
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_points_export_parity(variant):
+    """fmb_render_points against the oracle: points, normals at the rendered depth,
+    Eq. 16 screen-space normals and the max-weight quality, with the tolerances the
+    fp32 depth error propagates to (gpu_util.points_tolerances), where the oracle's
+    alpha >= 1e-2 (at the pixel and, for Eq. 16, its two neighbours) and the depth
+    order is unambiguous in fp32."""
+    for scene, nf in ((synth.config1(K=100, n_views=3, W=48, H=40), 1), (synth.config0(), 0)):
+        params = fmb.default_params(n_flow=nf, variant=variant)
+        gpu, r, dev = gpu_forward(scene, params)
+        pts = {k: v.cpu().numpy().astype(np.float64) for k, v in r.points(*dev).items()}
+        torch.cuda.synchronize()
+        ref = oracle.points_scene(scene, variant=variant)
+        fr = oracle.render_scene(scene, n_flow=0, variant=variant)
+        ref["depth"] = fr["depth"]
+        dD = np.abs(gpu["depth"] - fr["depth"]) + 1e-6 * np.abs(fr["depth"])
+        tp, tn, ts, amb_n, amb_s = points_tolerances(scene, ref, variant, dD)
+        ok = fr["alpha"] >= 1e-2
+        if variant == 1:
+            ok &= ~ac_order_ambiguous(scene)
+        for v in scene.views:
+            o, P = v["pix_offset"], v["W"] * v["H"]
+            W_, H_ = v["W"], v["H"]
+            pix = np.arange(P)
+            xx, yy = pix % W_, pix // W_
+            nx = yy * W_ + np.where(xx + 1 < W_, xx + 1, xx - 1)
+            ny = np.where(yy + 1 < H_, yy + 1, yy - 1) * W_ + xx
+            okv = ok[o:o + P]
+            okn = okv & okv[nx] & okv[ny]
+            for key, tol, msk, amb in (("points", tp, okv, None), ("normal_tf", tn, okv, amb_n),
+                                       ("normal_screen", ts, okn, amb_s)):
+                g_, r_ = plane_view(pts[key], v, 3), plane_view(ref[key], v, 3)
+                e = np.abs(g_ - r_).max(0)
+                if amb is not None:  # facing sign undecided at the tolerance: compare up to sign
+                    e = np.where(amb[o:o + P], np.minimum(e, np.abs(g_ + r_).max(0)), e)
+                assert np.all((e <= tol[o:o + P])[msk]), (key, float(e[msk].max()))
+            eq = np.abs(pts["quality"][o:o + P] - ref["quality"][o:o + P])
+            assert np.all((eq <= 1e-4)[okv]), ("quality", float(eq[okv].max()))
