@@ -137,6 +137,10 @@ WORKLOADS = {
                   desc="reconstruction workload: 100 sphere views 640x480 (f=640), K=256 Gaussians, "
                        "depth+alpha planes, flow to the next and the previous view, backward w.r.t. means, "
                        "Cholesky factors and weights"),
+    "minibatch": dict(config=3, n_flow=2, normals=0, want_pose=False, rays=50000,
+                      desc="ray minibatch: 50 000 rays drawn uniformly across the 100 sphere views 640x480 (f=640) "
+                           "of the reconstruction workload, K=256, depth+alpha planes, flow to the next and the "
+                           "previous view, backward w.r.t. means, Cholesky factors and weights"),
     "largek": dict(config=4, n_flow=1, normals=1, want_pose=True,
                    desc="large-K stress: 8 sphere views 1024x768 (f=1024), K=4096 diagonal-precision Gaussians, "
                         "all four planes, backward w.r.t. Gaussians and poses"),
@@ -148,6 +152,8 @@ def scene_and_inputs(seed=0, workload="orbit"):
 
     wl = WORKLOADS[workload]
     s = synth.CONFIGS[wl["config"]](seed=seed)
+    if wl.get("rays"):
+        s = synth.ray_batch(s, wl["rays"], seed=seed)
     rng = np.random.default_rng(seed + 1)
     nf = max(wl["n_flow"], 1)
     gd, ga, gn, gf = synth.upstream_grads(rng, s.n_pixels, nf)
@@ -217,6 +223,9 @@ class ClockSampler:
 
 def workload_config(s, wl):
     """The `config` object of a workload: its description and shape."""
+    if wl.get("rays"):
+        return {"workload": wl["desc"], "views": len(s.views), "rays": s.n_pixels, "width": s.views[0]["W"],
+                "height": s.views[0]["H"], "K": s.K(0)}
     sizes = sorted({(v["W"], v["H"]) for v in s.views})
     Ks = sorted({s.K(v["object"]) for v in s.views})
     c = {"workload": wl["desc"], "views": len(s.views)}
@@ -231,7 +240,7 @@ def workload_config(s, wl):
 def run_gpu(args):
     import torch
 
-    from paper_2308_14737_gb300 import fmb
+    from paper_2308_14737_gb300 import fmb, synth
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -268,7 +277,7 @@ def run_gpu(args):
     m = (batched.alpha >= 1e-2).float()
     gd.mul_(m)
     for v in s.views:
-        o, P = v["pix_offset"], v["W"] * v["H"]
+        o, P = v["pix_offset"], synth.view_entries(v)
         if gn is not None:
             mn = m[o:o + P] * (batched.saved[3 * o + 2 * P:3 * o + 3 * P] >= 0.05).float()
             gn[3 * o:3 * (o + P)].view(3, P).mul_(mn)
@@ -310,7 +319,7 @@ def run_gpu(args):
     for v in s.views:
         vv = dict(v, pix_offset=0)  # each single-view renderer owns its own planes
         plain.append((fmb.Renderer(s.obj_offsets, [vv], len(s.poses), params, device=dev), v["pix_offset"],
-                      v["W"] * v["H"]))
+                      synth.view_entries(v)))
 
     # per-view gradient buffers, summed over the views after the calls (as a caller of
     # per-view launches has to)
@@ -635,11 +644,12 @@ def oracle_sample(workload, s, ups):
         u["g_flow"] = np.concatenate([ups["g_flow"][2 * v["pix_offset"]:2 * (v["pix_offset"] + v["W"] * v["H"])]
                                       for v in s.views[:2]])
         return sub, u, "2 of the 16 views (320x240, K=100), forward + backward"
-    sub = s if workload == "single" else synth.crop_views(s, 64, 48)
+    sub = s if workload in ("single", "minibatch") else synth.crop_views(s, 64, 48)
     gd, ga, gn, gf = synth.upstream_grads(np.random.default_rng(7), sub.n_pixels, max(nf, 1))
     u = dict(g_depth=gd, g_alpha=ga, g_normal=gn.reshape(-1) if wl["normals"] else None,
              g_flow=gf.reshape(-1) if nf else None)
-    what = "the whole view" if workload == "single" else f"the central 64x48 crop of all {len(s.views)} views"
+    what = {"single": "the whole view", "minibatch": f"the whole batch of {s.n_pixels} rays"}.get(
+        workload, f"the central 64x48 crop of all {len(s.views)} views")
     return sub, u, what + ", forward + backward"
 
 

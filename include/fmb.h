@@ -91,7 +91,13 @@ typedef struct {
 } fmb_params;
 
 /* One camera view of one object.  Planes of the view start at pixel `pix_offset`
- * of the batched output buffers (see fmb_render_forward). */
+ * of the batched output buffers (see fmb_render_forward).
+ *
+ * Ray batches (the random ray minibatches of Sec. 4, drawn across all frames):
+ * with `rays` set, the view renders only the pixels listed there (device array of
+ * n_rays row-major pixel indices y * W + x, any order, repeats allowed; indices
+ * outside the image give the rays through those pixel coordinates) and its planes
+ * hold n_rays entries in list order instead of W * H.  NULL: the whole image. */
 typedef struct {
   int W, H;               /* image size in pixels, >= 1 */
   float fx, fy, cx, cy;   /* pinhole intrinsics; fx, fy > 0 (Sec. 5 uses fx = fy, centred) */
@@ -99,6 +105,9 @@ typedef struct {
   int pose;               /* index into poses: the camera's pose */
   int flow_target[2];     /* pose indices of the flow targets of slots 0 and 1, or -1 */
   long long pix_offset;   /* first pixel of this view in the batched planes */
+  const int* rays;        /* device: pixel indices of a ray batch, or NULL */
+  int n_rays;             /* entries of rays (>= 1 when rays is set) */
+  int reserved;           /* 0 */
 } fmb_view;
 
 /*
@@ -210,6 +219,25 @@ fmb_status fmb_render_points(const fmb_params* params, int n_objects, const long
                              const float* poses, int n_views, const fmb_view* h_views, const float* depth,
                              const float* saved, float* points, float* normal_tf, float* normal_screen,
                              float* quality, void* workspace, size_t workspace_bytes, fmb_stream_t stream);
+
+/*
+ * Loss attribution of Sec. 8, the input of the splitting criterion (Eq. 19): for
+ * every Gaussian i, attribution[i] = sum over the batch's rays j of
+ * ray_loss[j] * w_ij / sum_k w_kj, with the weights of params->variant (Eq. 7 or
+ * Eq. 9-10).  The paper averages over a random batch of M rays (about 5 % of the
+ * data): give the batch as ray batches (fmb_view.rays) and divide by M.
+ * ray_loss: [P_total] in the layout of the depth plane (rays with zero loss are
+ * skipped); saved: the forward's saved planes for the same batch and params
+ * (two-parameter weights are rebuilt from its log2 normaliser; NULL is allowed for
+ * variant 1, which re-renders).  attribution: [G] (overwritten; fp32 atomics, so
+ * the summation order varies between runs).  workspace as for fmb_render_forward
+ * (rewritten).
+ */
+fmb_status fmb_loss_attribution(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
+                                const float* means, const float* chol, const float* weights, int n_poses,
+                                const float* poses, int n_views, const fmb_view* h_views, const float* saved,
+                                const float* ray_loss, float* attribution, void* workspace, size_t workspace_bytes,
+                                fmb_stream_t stream);
 
 /* Workspace bytes needed by fmb_render_forward and fmb_render_backward for this
  * batch (the larger of the two).  Returns 0 on invalid arguments (see

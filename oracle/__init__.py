@@ -10,6 +10,8 @@ multi-view scene the same way the batched output planes are laid out:
 * ``normal``: per view a (3, H*W) block at ``3 * pix_offset`` (camera frame);
 * ``flow``: per view a (n_flow, 2, H*W) block at ``2 * n_flow * pix_offset``
   (pixels; a slot whose target pose is -1 is zero);
+* a view with ``rays`` (a ray batch: pixel indices) contributes only those
+  pixels, in list order, so its blocks have len(rays) entries instead of H*W;
 * ``saved``: per view a (3, H*W) block at ``3 * pix_offset`` holding
   (log-sum-exp of e_i in natural log, sum of delta_i, |N|); for the
   alpha-compositing variant the first entry is W = sum of the weights instead.
@@ -77,6 +79,11 @@ def lib():
                                   ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_longlong, lp,
                                   dp, dp, dp, dp, ctypes.c_int]
         L.fmbo_points.restype = ctypes.c_int
+        L.fmbo_attribution.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_longlong, lp,
+                                       dp, dp]
+        L.fmbo_attribution.restype = ctypes.c_int
         L.fmbo_max_threads.argtypes = []
         L.fmbo_max_threads.restype = ctypes.c_int
         _lib = L
@@ -211,10 +218,40 @@ def points_scene(scene, variant=0, n_threads=0):
     return out
 
 
+def attribution_scene(scene, ray_loss, variant=0, beta1=BETA1, beta2=BETA2, eta=ETA):
+    """Loss attribution of Sec. 8 over every view (ray batches included):
+    sum over the rendered rays j of ray_loss[j] (batched per-pixel layout) times the
+    normalised weight of Gaussian i on ray j.  Returns (sum K,) float64."""
+    out = np.zeros(scene.weights.shape[0])
+    loss = _f64(ray_loss)
+    for v in scene.views:
+        sl = scene.object_slice(v["object"])
+        o, Pv = v["pix_offset"], _entries(v)
+        rays = v.get("rays")
+        pix = None if rays is None else np.ascontiguousarray(np.asarray(rays, dtype=np.int64))
+        a = np.zeros(sl.stop - sl.start)
+        W, H, fx, fy, cx, cy = _cam(v)
+        rc = lib().fmbo_attribution(
+            int(variant), sl.stop - sl.start, _dp(_f64(scene.means[sl])), _dp(_f64(scene.chol[sl])),
+            _dp(_f64(scene.weights[sl])), _dp(_f64(scene.poses[v["pose"]])), int(W), int(H), float(fx), float(fy),
+            float(cx), float(cy), float(beta1), float(beta2), float(eta), Pv,
+            pix.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)) if pix is not None else None,
+            _dp(np.ascontiguousarray(loss[o:o + Pv])), _dp(a))
+        if rc != 0:
+            raise ValueError(f"fmbo_attribution failed with status {rc}")
+        out[sl] += a
+    return out
+
+
 def _view_targets(scene, v, n_flow):
     """Target pose indices of a view's flow slots (first n_flow entries)."""
     ft = list(v.get("flow_target", (-1, -1)))[:n_flow]
     return ft + [-1] * (n_flow - len(ft))
+
+
+def _entries(v):
+    """Plane entries of a view: its ray batch ("rays"), else W*H."""
+    return int(len(v["rays"])) if v.get("rays") is not None else int(v["W"]) * int(v["H"])
 
 
 def _cam(v):
@@ -233,8 +270,8 @@ def render_scene(scene, n_flow=1, beta1=BETA1, beta2=BETA2, eta=ETA, n_threads=0
         used = [j for j in ft if j >= 0]
         tp = scene.poses[used] if used else None
         r = render_view(scene.means[sl], scene.chol[sl], scene.weights[sl], scene.poses[v["pose"]], tp, _cam(v),
-                        beta1, beta2, eta, n_threads=n_threads, variant=variant)
-        Pv = v["W"] * v["H"]
+                        beta1, beta2, eta, pixels=v.get("rays"), n_threads=n_threads, variant=variant)
+        Pv = _entries(v)
         o = v["pix_offset"]
         out["depth"][o:o + Pv] = r["depth"]
         out["alpha"][o:o + Pv] = r["alpha"]
@@ -262,7 +299,7 @@ def backward_scene(scene, g_depth, g_alpha, g_normal, g_flow, n_flow=1, beta1=BE
         ft = _view_targets(scene, v, n_flow)
         used = [(s, j) for s, j in enumerate(ft) if j >= 0]
         tp = scene.poses[[j for _, j in used]] if used else None
-        Pv = v["W"] * v["H"]
+        Pv = _entries(v)
         o = v["pix_offset"]
         gn = None if g_normal is None else np.asarray(g_normal)[3 * o:3 * o + 3 * Pv].reshape(3, Pv).T
         gf = None
@@ -272,7 +309,7 @@ def backward_scene(scene, g_depth, g_alpha, g_normal, g_flow, n_flow=1, beta1=BE
         r = backward_view(scene.means[sl], scene.chol[sl], scene.weights[sl], scene.poses[v["pose"]], tp, _cam(v),
                           None if g_depth is None else np.asarray(g_depth)[o:o + Pv],
                           None if g_alpha is None else np.asarray(g_alpha)[o:o + Pv],
-                          gn, gf, beta1, beta2, eta, n_threads=n_threads, variant=variant)
+                          gn, gf, beta1, beta2, eta, pixels=v.get("rays"), n_threads=n_threads, variant=variant)
         g["means"][sl] += r["means"]
         g["chol"][sl] += r["chol"]
         g["weights"][sl] += r["weights"]

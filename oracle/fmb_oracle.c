@@ -752,6 +752,43 @@ int fmbo_points(int variant, int K, const double* means, const double* chol, con
   return failed ? 2 : 0;
 }
 
+/*
+ * Loss attribution of Sec. 8 (the input of the splitting criterion, Eq. 19): for
+ * every Gaussian i, attribution[i] = sum over the given pixels j of
+ * ray_loss[j] * w_ij / sum_k w_kj, with the variant's weights (0: Eq. 7,
+ * 1: Eq. 9-10).  The paper's average over a batch of M rays is this sum / M.
+ * Deterministic (serial over pixels).  Returns 0, or 1 on invalid arguments, 2 on
+ * allocation failure.
+ */
+int fmbo_attribution(int variant, int K, const double* means, const double* chol, const double* weights,
+                     const double* pose, int W, int H, double fx, double fy, double cx, double cy,
+                     double beta1, double beta2, double eta, long long n_pix, const long long* pix,
+                     const double* ray_loss, double* attribution) {
+  if (check_args(K, W, H, 0, fx, fy, eta) || (variant != 0 && variant != 1) || !ray_loss || !attribution)
+    return 1;
+  fmbo_camera cam = {W, H, fx, fy, cx, cy, beta1, beta2, eta, variant};
+  if (!pix) n_pix = (long long)W * H;
+  pair_t* pairs = (pair_t*)malloc(sizeof(pair_t) * (size_t)K);
+  double* what = (double*)malloc(sizeof(double) * (size_t)K);
+  double* trans = (double*)malloc(sizeof(double) * (size_t)K);
+  int failed = !pairs || !what || !trans;
+  if (!failed) {
+    for (int i = 0; i < K; ++i) attribution[i] = 0.0;
+    for (long long n = 0; n < n_pix; ++n) {
+      long long p = pix ? pix[n] : n;
+      double vcam[3], v[3], o[3], pxy[2];
+      ray_out_t out;
+      pixel_ray(&cam, pose, pose + 9, p, vcam, v, o, pxy);
+      forward_ray(K, means, chol, weights, &cam, pose, v, o, pxy, 0, NULL, pairs, what, trans, &out);
+      for (int i = 0; i < K; ++i) attribution[i] += ray_loss[n] * what[i];
+    }
+  }
+  free(pairs);
+  free(what);
+  free(trans);
+  return failed ? 2 : 0;
+}
+
 /* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
 int fmbo_max_threads(void) {
 #ifdef _OPENMP

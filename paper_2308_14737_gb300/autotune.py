@@ -30,7 +30,7 @@ def layout_key(obj_offsets, views, params: fmb.FmbParams, want_pose: bool) -> st
     offs = np.asarray(obj_offsets, dtype=np.int64)
     Ks = sorted({int(offs[v["object"] + 1] - offs[v["object"]]) for v in views})
     kb = sorted({int(np.log2(max(k, 1))) for k in Ks})
-    P = int(sum(v["W"] * v["H"] for v in views))
+    P = int(sum(fmb.view_entries(v) for v in views))
     return json.dumps(dict(k=kb, p=int(np.log2(max(P, 1))), v=len(views), f=int(params.n_flow),
                            n=int(params.want_normals), pose=bool(want_pose), variant=int(params.variant)),
                       sort_keys=True)

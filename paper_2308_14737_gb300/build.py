@@ -20,8 +20,8 @@ BUILD_DIR = os.path.join(PKG, "_build")
 LIB_DIR = os.path.join(PKG, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libfmb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fmb_forward.cu", "fmb_backward.cu", "fmb_ac.cu", "fmb_points.cu", "fmb_api.cu", "fmb_probe.cu",
-           "fmb_adam.cu"]
+SOURCES = ["fmb_forward.cu", "fmb_backward.cu", "fmb_ac.cu", "fmb_points.cu", "fmb_attrib.cu", "fmb_api.cu",
+           "fmb_probe.cu", "fmb_adam.cu"]
 
 
 def nvcc() -> str:

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kAcThreads) forward_ac_kernel(const __grid_con
     int tile;
     const int vi = find_item(batch, item, tile);
     const DevView& V = batch.v[vi];
-    const int P = V.W * V.H;
+    const int P = V.P;
     if (round > 0) __syncthreads();  // the previous item's records are dead
     if (!ac_stage_records(srec, records + kRecFloat4 * V.rec_off, V.K, &bar, uses, status)) return;
     float R[9], tp[3];
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kAcThreads) forward_ac_kernel(const __grid_con
       const int p = tile * kAcRays + rr;
       if (p >= P) break;
       float vc[3], v[3], vl[3], pxy[2];
-      pixel_ray_dd(V, R, p, vc, v, vl, pxy);
+      pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
       float t[M], dl[M], n[M][3];
       const AcSums a = ac_render_ray<NORMALS, M>(srec, V.K, v, vl, k, lane, t, dl, n, sd, sw, sT);
       if (lane == 0) {
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(kAcThreads) backward_ac_kernel(const __grid_co
     int tile;
     const int vi = find_item(batch, item, tile);
     const DevView& V = batch.v[vi];
-    const int P = V.W * V.H;
+    const int P = V.P;
     const int K = V.K;
     const int pix0 = tile * kAcRays;
     const int nr = min(kAcRays, P - pix0);
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kAcThreads) backward_ac_kernel(const __grid_co
     for (int rr = warp; rr < nr; rr += kAcWarps) {
       const int p = pix0 + rr;
       float vc[3], v[3], vl[3], pxy[2];
-      pixel_ray_dd(V, R, p, vc, v, vl, pxy);
+      pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
       float t[M], dl[M], n[M][3];
       const AcSums a = ac_render_ray<NORMALS, M>(srec, K, v, vl, k, lane, t, dl, n, sd, sw, sT);
       const float iW = a.W > 0.f ? 1.0f / a.W : 0.f;

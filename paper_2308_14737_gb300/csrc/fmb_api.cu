@@ -41,6 +41,11 @@ fmb_status fail(fmb_status s, const std::string& msg) {
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
+// Plane entries of a view: its ray batch, or the whole image.
+long long view_entries(const fmb_view& v) {
+  return v.rays != nullptr ? static_cast<long long>(v.n_rays) : static_cast<long long>(v.W) * v.H;
+}
+
 struct BwdBlocking {
   int n_gb, GB, S;
 };
@@ -151,7 +156,8 @@ fmb_status validate_views(int n_objects, int n_poses, int n_views, const fmb_vie
       if (v.flow_target[j] < -1 || v.flow_target[j] >= n_poses)
         return fail(FMB_ERR_INVALID_ARG, id + "flow_target out of range");
     if (v.pix_offset < 0) return fail(FMB_ERR_INVALID_ARG, id + "pix_offset < 0");
-    spans.emplace_back(v.pix_offset, v.pix_offset + static_cast<long long>(v.W) * v.H);
+    if (v.rays != nullptr && v.n_rays < 1) return fail(FMB_ERR_INVALID_ARG, id + "n_rays must be >= 1 with rays");
+    spans.emplace_back(v.pix_offset, v.pix_offset + view_entries(v));
   }
   std::sort(spans.begin(), spans.end());
   for (size_t i = 1; i < spans.size(); ++i)
@@ -213,7 +219,9 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
       d.rec_off = rec;
       d.pix_off = v.pix_offset;
       rec += d.K;
-      const long long P = static_cast<long long>(v.W) * v.H;
+      const long long P = view_entries(v);
+      d.rays = v.rays;
+      d.P = static_cast<int>(P);
       d.Kp = (d.K + 3) / 4 * 4;  // rows of 16-byte multiples
       d.pair_off = pairs;
       pairs += P * d.Kp;
@@ -469,6 +477,11 @@ fmb_status fmb_render_points(const fmb_params* params, int n_objects, const long
     if (!depth || !saved) return fail(FMB_ERR_INVALID_ARG, "depth and saved (forward outputs) are required");
     st = validate_views(n_objects, n_poses, n_views, h_views);
     if (st != FMB_OK) return st;
+    if (normal_screen != nullptr)
+      for (int i = 0; i < n_views; ++i)
+        if (h_views[i].rays != nullptr)
+          return fail(FMB_ERR_INVALID_ARG, "normal_screen needs whole images (Eq. 16 takes image neighbours); "
+                                           "pass NULL for ray batches");
     Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views);
     st = check_workspace(workspace, workspace_bytes, workspace_needed(params, pl));
     if (st != FMB_OK) return st;
@@ -478,10 +491,7 @@ fmb_status fmb_render_points(const fmb_params* params, int n_objects, const long
     const fmb::Consts c = make_consts(params);
     const int per = fmb::points_rays_per_item(params->variant);
     for (fmb::Batch b : pl.fwd) {
-      for (int i = 0; i < b.n_views; ++i) {
-        const long long P = static_cast<long long>(b.v[i].W) * b.v[i].H;
-        b.v[i].n_tiles = static_cast<int>((P + per - 1) / per);
-      }
+      for (int i = 0; i < b.n_views; ++i) b.v[i].n_tiles = (b.v[i].P + per - 1) / per;
       order_items(b, [&](const fmb::DevView& v) { return static_cast<double>(v.K); },
                   [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles); });
       cudaError_t e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, nullptr, s);
@@ -489,6 +499,55 @@ fmb_status fmb_render_points(const fmb_params* params, int n_objects, const long
       e = fmb::launch_points(b, sc, c, records, params->variant, pl.maxK, depth, saved, points, normal_tf,
                              normal_screen, quality, s);
       if (e != cudaSuccess) return cuda_fail(e, "points launch");
+    }
+    return FMB_OK;
+  } catch (const std::exception& e) {
+    return fail(FMB_ERR_INVALID_ARG, e.what());
+  } catch (...) {
+    return fail(FMB_ERR_INVALID_ARG, "unknown error");
+  }
+}
+
+fmb_status fmb_loss_attribution(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
+                                const float* means, const float* chol, const float* weights, int n_poses,
+                                const float* poses, int n_views, const fmb_view* h_views, const float* saved,
+                                const float* ray_loss, float* attribution, void* workspace, size_t workspace_bytes,
+                                fmb_stream_t stream) {
+  try {
+    g_err.clear();
+    fmb_status st = validate_scene(params, n_objects, h_obj_offsets, n_views, h_views);
+    if (st != FMB_OK) return st;
+    if (n_poses < 1 || !poses) return fail(FMB_ERR_INVALID_ARG, "poses missing");
+    if (!means || !chol || !weights) return fail(FMB_ERR_INVALID_ARG, "means, chol and weights are required");
+    if (!saved && params->variant != 1) return fail(FMB_ERR_INVALID_ARG, "saved (forward output) is required");
+    if (!ray_loss || !attribution) return fail(FMB_ERR_INVALID_ARG, "ray_loss and attribution are required");
+    st = validate_views(n_objects, n_poses, n_views, h_views);
+    if (st != FMB_OK) return st;
+    Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views);
+    st = check_workspace(workspace, workspace_bytes, workspace_needed(params, pl));
+    if (st != FMB_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    float4* records = reinterpret_cast<float4*>(static_cast<char*>(workspace) + kHeaderBytes);
+    const fmb::Scene sc{means, chol, weights, poses};
+    const fmb::Consts c = make_consts(params);
+    fmb::ZeroJob zj{};
+    zj.ptr[0] = attribution;
+    zj.n[0] = pl.n_gauss;
+    cudaError_t e = fmb::launch_zero(zj, s);
+    if (e != cudaSuccess) return cuda_fail(e, "zeroing launch");
+    const int per = fmb::attribution_rays_per_item();
+    const int blk = 32 * (pl.maxK <= 64 ? 2 : (pl.maxK <= 128 ? 4 : 8));
+    for (fmb::Batch b : pl.fwd) {
+      for (int i = 0; i < b.n_views; ++i) {
+        b.v[i].n_tiles = (b.v[i].P + per - 1) / per;
+        b.v[i].n_gblocks = (b.v[i].K + blk - 1) / blk;
+      }
+      order_items(b, [&](const fmb::DevView& v) { return static_cast<double>(std::min(v.K, blk)); },
+                  [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles) * v.n_gblocks; });
+      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, nullptr, s);
+      if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
+      e = fmb::launch_attribution(b, sc, c, records, params->variant, pl.maxK, saved, ray_loss, attribution, s);
+      if (e != cudaSuccess) return cuda_fail(e, "attribution launch");
     }
     return FMB_OK;
   } catch (const std::exception& e) {

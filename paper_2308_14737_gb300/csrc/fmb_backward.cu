@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
   const DevView& V = batch.v[vi];
   const int tile = local / V.n_gblocks;
   const int gb = local - tile * V.n_gblocks;
-  const int P = V.W * V.H;
+  const int P = V.P;
   const int pix0 = tile * ray_tile;
   const int nr = min(ray_tile, P - pix0);
   const int tid = threadIdx.x;
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
     for (int r = tid; r < nr; r += T) {
       const int p = pix0 + r;
       float vc[3], v[3], vl[3], pxy[2];
-      pixel_ray_dd(V, R, p, vc, v, vl, pxy);
+      pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
       const float D = in.depth[off + p];
       const float* sv = in.saved + 3 * off;
       const float lse2 = sv[p];

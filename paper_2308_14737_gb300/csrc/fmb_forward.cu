@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
   int tile;
   const int vi = find_item(batch, item, tile);
   const DevView& V = batch.v[vi];
-  const int P = V.W * V.H;
+  const int P = V.P;
   const int K = V.K;
 
   float R[9], tp[3];
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
     pix[r] = p;
     p = min(p, P - 1);  // rays past the end compute a valid pixel and store nothing
     float v[3], vl[3];
-    pixel_ray_dd(V, R, p, vc[r], v, vl, pxy[r]);
+    pixel_ray_dd(V, R, ray_pixel(V, p), vc[r], v, vl, pxy[r]);
     if (!PACKED) {
       RayAcc& a = A[PACKED ? 0 : r];
       a.v0 = v[0];

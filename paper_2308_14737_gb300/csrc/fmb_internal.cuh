@@ -58,7 +58,13 @@ struct DevView {
   int slot_floats;      // floats per (tile, gblock) slot in deterministic mode
   int Kp;               // stored-intermediate mode: row length (K rounded up to a multiple of 4)
   long long pair_off;   // stored-intermediate mode: first float of the view's [P][Kp] block
+  const int* rays;      // ray batch: pixel index of each plane entry, or null (whole image)
+  int P;                // plane entries of the view: n_rays, or W * H
+  int pad2_;
 };
+
+// Pixel rendered by plane entry i of a view.
+__device__ __forceinline__ int ray_pixel(const DevView& V, int i) { return V.rays ? __ldg(V.rays + i) : i; }
 
 // A launch's views.  Work items (forward: one ray tile; backward: one ray tile x
 // Gaussian block) are numbered view by view in `order_view` order -- the views
@@ -419,6 +425,11 @@ int points_rays_per_item(int variant);
 cudaError_t launch_points(const Batch& b, const Scene& s, const Consts& c, const float4* records, int variant,
                           int maxK, const float* depth, const float* saved, float* points, float* normal_tf,
                           float* normal_scr, float* quality, cudaStream_t st);
+// Loss attribution (Sec. 8, Eq. 19): work items of attribution_rays_per_item() rays x
+// one block of up to 256 Gaussians (32 x M, M from the batch's largest K).
+int attribution_rays_per_item();
+cudaError_t launch_attribution(const Batch& b, const Scene& s, const Consts& c, const float4* records, int variant,
+                               int maxK, const float* saved, const float* loss, float* out, cudaStream_t st);
 cudaError_t launch_backward_reduce(const Batch& b, int n_flow, long long n_gauss, int n_poses,
                                    const BwdOut& out, cudaStream_t st);
 

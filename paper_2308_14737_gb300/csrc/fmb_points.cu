@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kPtsThreads) points_kernel(const __grid_consta
   int tile;
   const int vi = find_item(batch, blockIdx.x, tile);
   const DevView& V = batch.v[vi];
-  const int P = V.W * V.H;
+  const int P = V.P;
   const int p = tile * kPtsThreads + threadIdx.x;
   if (p >= P) return;
   const long long off = V.pix_off;
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kPtsThreads) points_kernel(const __grid_consta
                       -fmaf(R[7], tp[2], fmaf(R[4], tp[1], R[1] * tp[0])),
                       -fmaf(R[8], tp[2], fmaf(R[5], tp[1], R[2] * tp[0]))};
   float vc[3], v[3], vl[3], pxy[2];
-  pixel_ray_dd(V, R, p, vc, v, vl, pxy);
+  pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
   const float D = depth[off + p];
   const float lse2 = saved[3 * off + p];
   const float4* rec = records + kRecFloat4 * V.rec_off;
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kAcThreads) points_ac_kernel(const __grid_cons
   int tile;
   const int vi = find_item(batch, blockIdx.x, tile);
   const DevView& V = batch.v[vi];
-  const int P = V.W * V.H;
+  const int P = V.P;
   const long long off = V.pix_off;
   float R[9], tp[3];
   load_pose(s.poses, V.pose, R, tp);
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kAcThreads) points_ac_kernel(const __grid_cons
     const int p = tile * kAcRays + rr;
     if (p >= P) break;
     float vc[3], v[3], vl[3], pxy[2];
-    pixel_ray_dd(V, R, p, vc, v, vl, pxy);
+    pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
     float t[M], dl[M], n[M][3];
     const AcSums a = ac_render_ray<false, M>(rec, V.K, v, vl, k, lane, t, dl, n, sd, sw, sT);
     const float D = depth[off + p];

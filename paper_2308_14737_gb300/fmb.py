@@ -37,7 +37,8 @@ class FmbParams(ctypes.Structure):
 class FmbView(ctypes.Structure):
     _fields_ = [("W", ctypes.c_int), ("H", ctypes.c_int), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
                 ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("object", ctypes.c_int), ("pose", ctypes.c_int),
-                ("flow_target", ctypes.c_int * 2), ("pix_offset", ctypes.c_longlong)]
+                ("flow_target", ctypes.c_int * 2), ("pix_offset", ctypes.c_longlong), ("rays", ctypes.c_void_p),
+                ("n_rays", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class FmbAdamParams(ctypes.Structure):
@@ -79,6 +80,8 @@ def load_library(path: str = LIB_PATH):
     L.fmb_adam_step.restype = ctypes.c_int
     L.fmb_render_points.argtypes = [P, i, LL, fp, fp, fp, i, fp, i, V, fp, fp, fp, fp, fp, fp, vp, sz, vp]
     L.fmb_render_points.restype = ctypes.c_int
+    L.fmb_loss_attribution.argtypes = [P, i, LL, fp, fp, fp, i, fp, i, V, fp, fp, fp, vp, sz, vp]
+    L.fmb_loss_attribution.restype = ctypes.c_int
     L.fmb_workspace_bytes.argtypes = [P, i, LL, i, V]
     L.fmb_workspace_bytes.restype = sz
     L.fmb_read_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
@@ -103,9 +106,15 @@ def default_params(**overrides) -> FmbParams:
     return p
 
 
-def make_views(views) -> ctypes.Array:
+def view_entries(v) -> int:
+    """Plane entries of a view dict: the length of its ray batch ("rays"), else W*H."""
+    return int(len(v["rays"])) if v.get("rays") is not None else int(v["W"]) * int(v["H"])
+
+
+def make_views(views, ray_tensors=None) -> ctypes.Array:
     """ctypes array of FmbView from a list of dicts (W, H, fx, fy, cx, cy, object, pose,
-    flow_target, pix_offset)."""
+    flow_target, pix_offset[, rays]).  A view with "rays" (a ray batch) needs its
+    pixel indices as a device int32 tensor in ``ray_tensors[k]``."""
     arr = (FmbView * len(views))()
     for k, v in enumerate(views):
         a = arr[k]
@@ -116,6 +125,12 @@ def make_views(views) -> ctypes.Array:
         a.flow_target[0] = int(ft[0]) if len(ft) > 0 else -1
         a.flow_target[1] = int(ft[1]) if len(ft) > 1 else -1
         a.pix_offset = int(v["pix_offset"])
+        if v.get("rays") is not None:
+            t = None if ray_tensors is None else ray_tensors[k]
+            if t is None or not t.is_cuda or t.dtype != torch.int32:
+                raise ValueError("a ray batch needs its pixel indices as a device int32 tensor")
+            a.rays = t.data_ptr()
+            a.n_rays = int(t.numel())
     return arr
 
 
@@ -193,6 +208,16 @@ def fmb_render_points(params, obj_offsets, means, chol, weights, poses, views, d
                                workspace.numel(), _stream(stream)))
 
 
+def fmb_loss_attribution(params, obj_offsets, means, chol, weights, poses, views, saved, ray_loss, attribution,
+                         workspace, stream=None):
+    L = load_library()
+    o, op = _offsets(obj_offsets)
+    va = views if isinstance(views, ctypes.Array) else make_views(views)
+    _check(L.fmb_loss_attribution(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol), _ptr(weights),
+                                  int(poses.shape[0]), _ptr(poses), len(va), va, _ptr(saved), _ptr(ray_loss),
+                                  _ptr(attribution), _ptr(workspace), workspace.numel(), _stream(stream)))
+
+
 def fmb_render_backward(params, obj_offsets, means, chol, weights, poses, views, depth, normal, saved, g_depth,
                         g_alpha, g_normal, g_flow, grad_means, grad_chol, grad_weights, grad_poses, workspace,
                         stream=None):
@@ -240,9 +265,12 @@ class Renderer:
         self.params = params if params is not None else default_params()
         self.obj_offsets = np.ascontiguousarray(np.asarray(obj_offsets, dtype=np.int64))
         self.views = [dict(v) for v in views]
-        self.c_views = make_views(self.views)
+        self.rays = [None if v.get("rays") is None else
+                     torch.as_tensor(np.asarray(v["rays"], dtype=np.int32), device=device).contiguous()
+                     for v in self.views]  # kept alive: the views point at them
+        self.c_views = make_views(self.views, self.rays)
         self.n_poses = int(n_poses)
-        self.P = int(sum(v["W"] * v["H"] for v in self.views))
+        self.P = int(sum(view_entries(v) for v in self.views))
         self.device = device
         self.ws = alloc_workspace(fmb_workspace_bytes(self.params, self.obj_offsets, self.c_views), device)
         nf = self.params.n_flow
@@ -268,6 +296,15 @@ class Renderer:
         fmb_render_points(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, self.depth,
                           self.saved, out["points"], out["normal_tf"], out["normal_screen"], out["quality"], self.ws,
                           stream)
+        return out
+
+    def attribution(self, means, chol, weights, poses, ray_loss, out=None, stream=None):
+        """Sec. 8 loss attribution of the batch's rays (after a forward call of the
+        same batch): per Gaussian, the sum of ray_loss times its normalised weight."""
+        if out is None:
+            out = torch.empty(means.shape[0], dtype=torch.float32, device=means.device)
+        fmb_loss_attribution(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, self.saved,
+                             ray_loss, out, self.ws, stream)
         return out
 
     def backward(self, means, chol, weights, poses, g_depth, g_alpha, g_normal, g_flow, want_pose=True,

@@ -42,6 +42,8 @@ __all__ = [
     "config3",
     "config4",
     "CONFIGS",
+    "ray_batch",
+    "view_entries",
 ]
 
 
@@ -64,15 +66,16 @@ class Scene:
 
     @property
     def n_pixels(self) -> int:
-        return int(sum(v["W"] * v["H"] for v in self.views))
+        """Entries of the batched planes: every view's pixels, or its ray batch."""
+        return int(sum(view_entries(v) for v in self.views))
 
     def K(self, obj: int) -> int:
         return int(self.obj_offsets[obj + 1] - self.obj_offsets[obj])
 
     @property
     def n_pairs(self) -> int:
-        """Ray-Gaussian pairs of one full render: sum over views of W*H*K."""
-        return int(sum(v["W"] * v["H"] * self.K(v["object"]) for v in self.views))
+        """Ray-Gaussian pairs of one render: sum over views of (rays of the view) x K."""
+        return int(sum(view_entries(v) * self.K(v["object"]) for v in self.views))
 
     def object_slice(self, obj: int) -> slice:
         return slice(int(self.obj_offsets[obj]), int(self.obj_offsets[obj + 1]))
@@ -138,6 +141,11 @@ def random_gaussians(rng: np.random.Generator, K: int, kind: str = "cholesky"):
     return mu.astype(np.float32), chol.astype(np.float32), lam.astype(np.float32)
 
 
+def view_entries(v) -> int:
+    """Rays a view renders: the length of its ray batch ("rays"), else W*H."""
+    return int(len(v["rays"])) if v.get("rays") is not None else int(v["W"]) * int(v["H"])
+
+
 def make_scene(objects, views, poses, name="", meta=None) -> Scene:
     """Assemble a Scene from a list of (means, chol, weights) objects, a list of view
     dicts (without ``pix_offset``) and an array of poses."""
@@ -153,7 +161,7 @@ def make_scene(objects, views, poses, name="", meta=None) -> Scene:
         v.setdefault("flow_target", (-1, -1))
         v["flow_target"] = tuple(int(x) for x in v["flow_target"])
         v["pix_offset"] = pix
-        pix += int(v["W"]) * int(v["H"])
+        pix += view_entries(v)
         out_views.append(v)
     return Scene(
         means=np.ascontiguousarray(means),
@@ -230,6 +238,27 @@ def config4(seed: int = 0, K: int = 4096, n_views: int = 8, W: int = 1024, H: in
 
 
 CONFIGS = {0: config0, 1: config1, 2: config2, 3: config3, 4: config4}
+
+
+def ray_batch(scene: Scene, n_rays: int, seed: int = 0) -> Scene:
+    """A random ray minibatch drawn across all frames (Sec. 4 optimises on batches of
+    rays sampled from every frame): ``n_rays`` (view, pixel) pairs uniform over all
+    pixels of all views, without repeats, each view keeping its sampled pixel
+    indices (sorted) as ``rays``; views that drew no ray are left out."""
+    rng = np.random.default_rng(seed)
+    sizes = np.array([int(v["W"]) * int(v["H"]) for v in scene.views], dtype=np.int64)
+    flat = np.sort(rng.choice(int(sizes.sum()), size=min(int(n_rays), int(sizes.sum())), replace=False))
+    starts = np.concatenate([[0], np.cumsum(sizes)])
+    views = []
+    for i, v in enumerate(scene.views):
+        sel = flat[(flat >= starts[i]) & (flat < starts[i + 1])] - starts[i]
+        if len(sel):
+            nv = {k: val for k, val in v.items() if k != "pix_offset"}
+            nv["rays"] = sel.astype(np.int64)
+            views.append(nv)
+    objs = [(scene.means[scene.object_slice(o)], scene.chol[scene.object_slice(o)],
+             scene.weights[scene.object_slice(o)]) for o in range(scene.n_objects)]
+    return make_scene(objs, views, scene.poses, name=scene.name + f"_rays{len(flat)}")
 
 
 def crop_views(scene: Scene, cw: int, ch: int) -> Scene:

@@ -60,13 +60,13 @@ def gpu_backward(r, dev, ups, want_pose=True):
 
 def view_slices(scene, n_flow):
     for v in scene.views:
-        o, P = v["pix_offset"], v["W"] * v["H"]
+        o, P = v["pix_offset"], synth.view_entries(v)
         yield v, o, P
 
 
 def plane_view(arr, v, n_ch):
     """The (n_ch, P_v) block of view v in a batched plane."""
-    o, P = v["pix_offset"], v["W"] * v["H"]
+    o, P = v["pix_offset"], synth.view_entries(v)
     return arr[n_ch * o:n_ch * (o + P)].reshape(n_ch, P)
 
 
@@ -108,7 +108,7 @@ def compare_forward(scene, gpu, ref, n_flow, want_normals, pixels_per_view=None,
     flow comparisons (alpha, sum delta and W do not depend on the order)."""
     stats = dict(depth=0.0, alpha=0.0, normal=0.0, flow=0.0, sdelta=0.0, lse=0.0)
     for vi, v in enumerate(scene.views):
-        o, P = v["pix_offset"], v["W"] * v["H"]
+        o, P = v["pix_offset"], synth.view_entries(v)
         if pixels_per_view is None:
             pix = np.arange(P)
             rd = ref["depth"][o:o + P]
@@ -163,7 +163,8 @@ def compare_forward(scene, gpu, ref, n_flow, want_normals, pixels_per_view=None,
             assert np.all((np.abs(gs[2] - rs[2]) <= 1e-4 + 1e-4 * rs[2])[unique]), f"view {vi}: |N| err"
         if n_flow:
             gf = plane_view(gpu["flow"], v, 2 * n_flow)[:, pix]
-            sens = flow_sensitivity(scene, v, rd, n_flow, pix)
+            ray_pix = pix if v.get("rays") is None else np.asarray(v["rays"])[pix]  # image pixels of the entries
+            sens = flow_sensitivity(scene, v, rd, n_flow, ray_pix)
             for j in range(n_flow):
                 for c in range(2):
                     e = np.abs(gf[2 * j + c] - rf[2 * j + c])
@@ -195,7 +196,7 @@ def masked_upstream(scene, alpha_ref, n_flow, seed=1, pixel_mask=None, nnorm_ref
     gn_b = np.zeros(3 * P, dtype=np.float32)
     gf_b = np.zeros(2 * n_flow * P, dtype=np.float32)
     for v in scene.views:
-        o, Pv = v["pix_offset"], v["W"] * v["H"]
+        o, Pv = v["pix_offset"], synth.view_entries(v)
         gn_b[3 * o:3 * (o + Pv)] = (gn[:, o:o + Pv] * mn[o:o + Pv]).reshape(-1)
         if n_flow:
             gf_b[2 * n_flow * o:2 * n_flow * (o + Pv)] = (gf[:n_flow, :, o:o + Pv] * m[o:o + Pv]).reshape(-1)
@@ -231,8 +232,11 @@ def ac_order_ambiguous(scene, pix_per_view=None, rel=1e-6, bound=1e-6):
         K = sl.stop - sl.start
         R = scene.poses[v["pose"]][:9].astype(np.float64).reshape(3, 3)
         t = scene.poses[v["pose"]][9:].astype(np.float64)
-        P = v["W"] * v["H"]
-        pix = np.arange(P) if pix_per_view is None else np.asarray(pix_per_view[vi], dtype=np.int64)
+        P = synth.view_entries(v)
+        if pix_per_view is None:  # every plane entry: the image's pixels, or the view's ray batch
+            pix = np.arange(P) if v.get("rays") is None else np.asarray(v["rays"], dtype=np.int64)
+        else:
+            pix = np.asarray(pix_per_view[vi], dtype=np.int64)
         x = pix % v["W"] + 0.5
         y = pix // v["W"] + 0.5
         c = np.stack([(x - v["cx"]) / v["fx"], (y - v["cy"]) / v["fy"], np.ones(len(pix))], 1)
@@ -270,7 +274,7 @@ def nnorm_batched(scene, saved):
     """Per-pixel |N| (channel 2 of the saved planes) in the batched pixel layout."""
     out = np.zeros(scene.n_pixels)
     for v in scene.views:
-        o, P = v["pix_offset"], v["W"] * v["H"]
+        o, P = v["pix_offset"], synth.view_entries(v)
         out[o:o + P] = saved[3 * o + 2 * P:3 * o + 3 * P]
     return out
 

@@ -351,3 +351,61 @@ def test_points_export_parity(variant):
                 assert np.all((e <= tol[o:o + P])[msk]), (key, float(e[msk].max()))
             eq = np.abs(pts["quality"][o:o + P] - ref["quality"][o:o + P])
             assert np.all((eq <= 1e-4)[okv]), ("quality", float(eq[okv].max()))
+
+
+
+# ------------------------------------------------ ray minibatches across frames (Sec. 4)
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_ray_batch_parity(variant):
+    """Views that render only a list of pixels (random minibatch across all frames):
+    forward planes hold the listed rays in order and the gradients are the sums over
+    those rays alone -- against the oracle on the same pixel lists."""
+    base = synth.config1(K=100, n_views=6, W=48, H=40)
+    s = synth.ray_batch(base, 3000, seed=2)
+    assert s.n_pixels == 3000 and all(v.get("rays") is not None for v in s.views)
+    _full_check(s, n_flow=1, variant=variant)
+    _full_check(s, n_flow=1, variant=variant, deterministic=True)
+    if variant == 0:
+        _full_check(s, n_flow=1, use_persistent=1)
+        _full_check(s, n_flow=1, store_pairs=1)
+
+
+def test_ray_batch_matches_full_render():
+    """A ray batch renders exactly the listed pixels of the full image: bitwise the
+    same depth, alpha, normal and flow values."""
+    base = synth.config1(K=60, n_views=2, W=40, H=30)
+    s = synth.ray_batch(base, 700, seed=3)
+    p = fmb.default_params(n_flow=1)
+    full, _, _ = gpu_forward(base, p)
+    part, _, _ = gpu_forward(s, p)
+    for v in s.views:
+        bv = next(b for b in base.views if b["pose"] == v["pose"])
+        rays = np.asarray(v["rays"])
+        for key, ch in (("depth", 1), ("alpha", 1), ("normal", 3), ("flow", 2)):
+            a = plane_view(part[key], v, ch)
+            b = plane_view(full[key], bv, ch)[:, rays]
+            assert np.array_equal(a, b), key
+
+
+
+# --------------------------------------------------- loss attribution (Sec. 8, Eq. 19)
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_loss_attribution_parity(variant):
+    """Per-Gaussian sums of ray loss x normalised weight against the oracle, on a ray
+    batch across frames (the paper's ~5 % sample), on whole images, and for K above
+    one 256-Gaussian block (two-parameter only); relative to the total loss."""
+    cases = [synth.ray_batch(synth.config1(K=100, n_views=8, W=48, H=40), 800, seed=4),
+             synth.config1(K=37, n_views=2, W=30, H=20), _ac_ragged_scene()]
+    if variant == 0:
+        cases.append(synth.config1(K=300, n_views=2, W=24, H=20))
+    for s in cases:
+        params = fmb.default_params(n_flow=0, variant=variant)
+        gpu, r, dev = gpu_forward(s, params)
+        loss = np.random.default_rng(7).uniform(0.0, 1.0, s.n_pixels).astype(np.float32)
+        loss[::5] = 0.0  # skipped rays
+        a = r.attribution(*dev, torch.as_tensor(loss, device="cuda")).cpu().numpy().astype(np.float64)
+        ref = oracle.attribution_scene(s, loss, variant=variant)
+        assert np.max(np.abs(a - ref)) <= 1e-5 * loss.sum(), float(np.max(np.abs(a - ref)) / loss.sum())
+        assert abs(a.sum() - loss.astype(np.float64).sum()) <= 1e-4 * loss.sum()

@@ -461,3 +461,46 @@ def test_points_screen_normal_of_a_plane(oracle_mod):
         np.testing.assert_allclose((r["points"] - mu[0]) @ nrm, 0.0, atol=1e-9)
     line = oracle_mod.points_view(mu, chol, lam, pose, (7, 1, 7.0, 7.0, 3.5, 0.5))
     assert np.all(line["normal_screen"] == 0.0)  # one row: no vertical neighbour
+
+
+# ----------------------------------------------- loss attribution (Sec. 8, Eq. 19)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_attribution_partition_of_unity(oracle_mod, variant):
+    """The normalised weights of every ray sum to one over the Gaussians, so the
+    attributions sum to the total ray loss; one Gaussian takes all of it; exact
+    duplicates (equal weights under Eq. 7, equal depths under Eq. 10's strict
+    indicator) take equal shares; reordering the Gaussians reorders the result."""
+    s = synth.config1(K=9, n_views=2, W=12, H=10)
+    loss = np.random.default_rng(0).uniform(0.0, 2.0, s.n_pixels)
+    a = oracle_mod.attribution_scene(s, loss, variant=variant)
+    assert abs(a.sum() - loss.sum()) < 1e-9 * loss.sum()
+    one = synth.make_scene([(s.means[:1], s.chol[:1], s.weights[:1])],
+                           [{k: v for k, v in vv.items() if k != "pix_offset"} for vv in s.views], s.poses)
+    assert abs(oracle_mod.attribution_scene(one, loss, variant=variant)[0] - loss.sum()) < 1e-9 * loss.sum()
+    dup = synth.make_scene([(np.concatenate([s.means[:3]] * 2), np.concatenate([s.chol[:3]] * 2),
+                             np.concatenate([s.weights[:3]] * 2))],
+                           [{k: v for k, v in vv.items() if k != "pix_offset"} for vv in s.views], s.poses)
+    ad = oracle_mod.attribution_scene(dup, loss, variant=variant)
+    np.testing.assert_allclose(ad[:3], ad[3:], rtol=1e-12)
+    perm = np.random.default_rng(1).permutation(9)
+    sp = synth.make_scene([(s.means[perm], s.chol[perm], s.weights[perm])],
+                          [{k: v for k, v in vv.items() if k != "pix_offset"} for vv in s.views], s.poses)
+    np.testing.assert_allclose(oracle_mod.attribution_scene(sp, loss, variant=variant), a[perm], rtol=1e-12,
+                               atol=1e-15)
+
+
+def test_attribution_two_centred_closed_form(oracle_mod):
+    """One pixel, two Gaussians centred on its ray: under Eq. 7 the shares are
+    1/(1+s) and s/(1+s) with s = (l2/l1)^beta1 e^(-beta2 (r2 - r1))."""
+    pose = synth.look_at_pose((0.0, 0.0, -4.0))
+    v, o, _ = ray_of_pixel(pose, CAM, 5, 7)
+    scene = synth.make_scene([(np.stack([o + 3.5 * v, o + 4.0 * v]),
+                               np.array([[3, 0.2, 2, -0.1, 0.3, 4], [1.5, 0, 1.5, 0, 0, 1.5]]),
+                               np.array([1.0, 1.1]))],
+                             [dict(W=CAM[0], H=CAM[1], fx=CAM[2], fy=CAM[3], cx=CAM[4], cy=CAM[5], object=0, pose=0,
+                                   rays=np.array([7 * CAM[0] + 5]))], [pose])
+    a = oracle_mod.attribution_scene(scene, np.array([2.0]))
+    s_ = np.exp(B1 * np.log(1.1 / 1.0) - B2 * 0.5)
+    np.testing.assert_allclose(a, 2.0 * np.array([1.0, s_]) / (1.0 + s_), rtol=1e-6)
