@@ -70,6 +70,13 @@ def lib():
         L.fmbo_forward.restype = ctypes.c_int
         L.fmbo_backward.argtypes = common + [dp, dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_int]
         L.fmbo_backward.restype = ctypes.c_int
+        cf = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, ctypes.c_int, dp,
+              ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+              ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_longlong, lp]
+        L.fmbo_forward_c.argtypes = cf + [dp, dp, dp, dp, dp, dp, ctypes.c_int]
+        L.fmbo_forward_c.restype = ctypes.c_int
+        L.fmbo_backward_c.argtypes = cf + [dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_int]
+        L.fmbo_backward_c.restype = ctypes.c_int
         L.fmbo_forward_ac.argtypes = L.fmbo_forward.argtypes
         L.fmbo_forward_ac.restype = ctypes.c_int
         L.fmbo_backward_ac.argtypes = L.fmbo_backward.argtypes
@@ -105,7 +112,7 @@ def _f64(a):
 
 
 def render_view(means, chol, weights, pose, target_poses, cam, beta1=BETA1, beta2=BETA2, eta=ETA,
-                pixels=None, n_threads=0, variant=0):
+                pixels=None, n_threads=0, variant=0, colors=None):
     """Forward render of one view.
 
     ``cam`` = (W, H, fx, fy, cx, cy); ``target_poses`` is a (T, 12) array (T <= 2).
@@ -125,13 +132,21 @@ def render_view(means, chol, weights, pose, target_poses, cam, beta1=BETA1, beta
         n = pix.shape[0]
     out = dict(depth=np.zeros(n), alpha=np.zeros(n), normal=np.zeros((n, 3)),
                flow=np.zeros((n, max(T, 1), 2)), saved=np.zeros((n, 3)))
-    fn = lib().fmbo_forward_ac if variant == 1 else lib().fmbo_forward
-    rc = fn(
-        K, _dp(means), _dp(chol), _dp(weights), _dp(pose), T, _dp(tp) if T else None,
-        int(W), int(H), float(fx), float(fy), float(cx), float(cy), float(beta1), float(beta2), float(eta),
-        n, pix.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)) if pix is not None else None,
-        _dp(out["depth"]), _dp(out["alpha"]), _dp(out["normal"]), _dp(out["flow"]), _dp(out["saved"]),
-        int(n_threads))
+    pp = pix.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)) if pix is not None else None
+    if colors is not None:
+        out["color"] = np.zeros((n, 3))
+        rc = lib().fmbo_forward_c(
+            int(variant), K, _dp(means), _dp(chol), _dp(weights), _dp(_f64(colors).reshape(K, 3)), _dp(pose), T,
+            _dp(tp) if T else None, int(W), int(H), float(fx), float(fy), float(cx), float(cy), float(beta1),
+            float(beta2), float(eta), n, pp, _dp(out["depth"]), _dp(out["alpha"]), _dp(out["normal"]),
+            _dp(out["flow"]), _dp(out["saved"]), _dp(out["color"]), int(n_threads))
+    else:
+        fn = lib().fmbo_forward_ac if variant == 1 else lib().fmbo_forward
+        rc = fn(
+            K, _dp(means), _dp(chol), _dp(weights), _dp(pose), T, _dp(tp) if T else None,
+            int(W), int(H), float(fx), float(fy), float(cx), float(cy), float(beta1), float(beta2), float(eta),
+            n, pp, _dp(out["depth"]), _dp(out["alpha"]), _dp(out["normal"]), _dp(out["flow"]), _dp(out["saved"]),
+            int(n_threads))
     if rc != 0:
         raise ValueError(f"fmbo_forward failed with status {rc}")
     out["flow"] = out["flow"][:, :T, :]
@@ -139,7 +154,8 @@ def render_view(means, chol, weights, pose, target_poses, cam, beta1=BETA1, beta
 
 
 def backward_view(means, chol, weights, pose, target_poses, cam, g_depth=None, g_alpha=None, g_normal=None,
-                  g_flow=None, beta1=BETA1, beta2=BETA2, eta=ETA, pixels=None, n_threads=0, variant=0):
+                  g_flow=None, beta1=BETA1, beta2=BETA2, eta=ETA, pixels=None, n_threads=0, variant=0,
+                  colors=None, g_color=None):
     """Analytic FP64 adjoint of one view.  Upstream layouts follow ``render_view``:
     g_depth (n,), g_alpha (n,), g_normal (n, 3), g_flow (n, T, 2).  Returns a dict
     with means (K, 3), chol (K, 6), weights (K,), pose (12,), target_poses (T, 12)."""
@@ -160,14 +176,24 @@ def backward_view(means, chol, weights, pose, target_poses, cam, g_depth=None, g
     gf = None if (g_flow is None or T == 0) else _f64(g_flow).reshape(n, T, 2)
     out = dict(means=np.zeros((K, 3)), chol=np.zeros((K, 6)), weights=np.zeros(K), pose=np.zeros(12),
                target_poses=np.zeros((max(T, 1), 12)))
-    fn = lib().fmbo_backward_ac if variant == 1 else lib().fmbo_backward
-    rc = fn(
-        K, _dp(means), _dp(chol), _dp(weights), _dp(pose), T, _dp(tp) if T else None,
-        int(W), int(H), float(fx), float(fy), float(cx), float(cy), float(beta1), float(beta2), float(eta),
-        n, pix.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)) if pix is not None else None,
-        _dp(gd), _dp(ga), _dp(gn), _dp(gf),
-        _dp(out["means"]), _dp(out["chol"]), _dp(out["weights"]), _dp(out["pose"]), _dp(out["target_poses"]),
-        int(n_threads))
+    pp = pix.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)) if pix is not None else None
+    if colors is not None:
+        out["colors"] = np.zeros((K, 3))
+        gc = None if g_color is None else _f64(g_color).reshape(n, 3)
+        rc = lib().fmbo_backward_c(
+            int(variant), K, _dp(means), _dp(chol), _dp(weights), _dp(_f64(colors).reshape(K, 3)), _dp(pose), T,
+            _dp(tp) if T else None, int(W), int(H), float(fx), float(fy), float(cx), float(cy), float(beta1),
+            float(beta2), float(eta), n, pp, _dp(gd), _dp(ga), _dp(gn), _dp(gf), _dp(gc), _dp(out["means"]),
+            _dp(out["chol"]), _dp(out["weights"]), _dp(out["colors"]), _dp(out["pose"]), _dp(out["target_poses"]),
+            int(n_threads))
+    else:
+        fn = lib().fmbo_backward_ac if variant == 1 else lib().fmbo_backward
+        rc = fn(
+            K, _dp(means), _dp(chol), _dp(weights), _dp(pose), T, _dp(tp) if T else None,
+            int(W), int(H), float(fx), float(fy), float(cx), float(cy), float(beta1), float(beta2), float(eta),
+            n, pp, _dp(gd), _dp(ga), _dp(gn), _dp(gf),
+            _dp(out["means"]), _dp(out["chol"]), _dp(out["weights"]), _dp(out["pose"]), _dp(out["target_poses"]),
+            int(n_threads))
     if rc != 0:
         raise ValueError(f"fmbo_backward failed with status {rc}")
     out["target_poses"] = out["target_poses"][:T]
@@ -258,25 +284,30 @@ def _cam(v):
     return (v["W"], v["H"], v["fx"], v["fy"], v["cx"], v["cy"])
 
 
-def render_scene(scene, n_flow=1, beta1=BETA1, beta2=BETA2, eta=ETA, n_threads=0, variant=0):
+def render_scene(scene, n_flow=1, beta1=BETA1, beta2=BETA2, eta=ETA, n_threads=0, variant=0, colors=None):
     """Forward render of every view of a ``synth.Scene`` into batched planes
     (layouts in the module docstring).  Returns float64 arrays."""
     P = scene.n_pixels
     out = dict(depth=np.zeros(P), alpha=np.zeros(P), normal=np.zeros(3 * P), flow=np.zeros(2 * n_flow * P),
                saved=np.zeros(3 * P))
+    if colors is not None:
+        out["color"] = np.zeros(3 * P)
     for v in scene.views:
         sl = scene.object_slice(v["object"])
         ft = _view_targets(scene, v, n_flow)
         used = [j for j in ft if j >= 0]
         tp = scene.poses[used] if used else None
         r = render_view(scene.means[sl], scene.chol[sl], scene.weights[sl], scene.poses[v["pose"]], tp, _cam(v),
-                        beta1, beta2, eta, pixels=v.get("rays"), n_threads=n_threads, variant=variant)
+                        beta1, beta2, eta, pixels=v.get("rays"), n_threads=n_threads, variant=variant,
+                        colors=None if colors is None else np.asarray(colors).reshape(-1, 3)[sl])
         Pv = _entries(v)
         o = v["pix_offset"]
         out["depth"][o:o + Pv] = r["depth"]
         out["alpha"][o:o + Pv] = r["alpha"]
         out["normal"][3 * o:3 * o + 3 * Pv] = r["normal"].T.reshape(-1)
         out["saved"][3 * o:3 * o + 3 * Pv] = r["saved"].T.reshape(-1)
+        if colors is not None:
+            out["color"][3 * o:3 * o + 3 * Pv] = r["color"].T.reshape(-1)
         fl = np.zeros((n_flow, 2, Pv))
         k = 0
         for s, j in enumerate(ft):
@@ -288,12 +319,14 @@ def render_scene(scene, n_flow=1, beta1=BETA1, beta2=BETA2, eta=ETA, n_threads=0
 
 
 def backward_scene(scene, g_depth, g_alpha, g_normal, g_flow, n_flow=1, beta1=BETA1, beta2=BETA2, eta=ETA,
-                   n_threads=0, variant=0):
+                   n_threads=0, variant=0, colors=None, g_color=None):
     """Adjoint over every view of a scene with upstream gradients in the batched
     plane layout.  Returns grads for means (sum K, 3), chol (sum K, 6), weights
     (sum K,) and poses (n_poses, 12), float64."""
     g = dict(means=np.zeros(scene.means.shape), chol=np.zeros(scene.chol.shape),
              weights=np.zeros(scene.weights.shape), poses=np.zeros(scene.poses.shape))
+    if colors is not None:
+        g["colors"] = np.zeros((scene.weights.shape[0], 3))
     for v in scene.views:
         sl = scene.object_slice(v["object"])
         ft = _view_targets(scene, v, n_flow)
@@ -309,10 +342,15 @@ def backward_scene(scene, g_depth, g_alpha, g_normal, g_flow, n_flow=1, beta1=BE
         r = backward_view(scene.means[sl], scene.chol[sl], scene.weights[sl], scene.poses[v["pose"]], tp, _cam(v),
                           None if g_depth is None else np.asarray(g_depth)[o:o + Pv],
                           None if g_alpha is None else np.asarray(g_alpha)[o:o + Pv],
-                          gn, gf, beta1, beta2, eta, pixels=v.get("rays"), n_threads=n_threads, variant=variant)
+                          gn, gf, beta1, beta2, eta, pixels=v.get("rays"), n_threads=n_threads, variant=variant,
+                          colors=None if colors is None else np.asarray(colors).reshape(-1, 3)[sl],
+                          g_color=None if (colors is None or g_color is None)
+                          else np.asarray(g_color)[3 * o:3 * o + 3 * Pv].reshape(3, Pv).T)
         g["means"][sl] += r["means"]
         g["chol"][sl] += r["chol"]
         g["weights"][sl] += r["weights"]
+        if colors is not None:
+            g["colors"][sl] += r["colors"]
         g["poses"][v["pose"]] += r["pose"]
         for k, (_, j) in enumerate(used):
             g["poses"][j] += r["target_poses"][k]

@@ -60,6 +60,11 @@
  *                + Abar exp(-sum delta)
  *   dbar_k = deltabar_k delta_k,  tbar_k (through Eq. 3) = Dbar w_k / W
  * (the indicator is piecewise constant in t, so it contributes nothing).
+ *
+ * Per-Gaussian colours (the *_c entry points): Eq. 3 with c_i in place of t_i,
+ * C = sum_i w_i c_i / sum w (Sec. 3.1 blends normals and colours like depth);
+ * its adjoint adds Cbar . (c_i - C) to the weight gradient of each Gaussian and
+ * gives cbar_i = sum over pixels of (w_i / sum w) Cbar.
  */
 
 #include <math.h>
@@ -105,6 +110,7 @@ typedef struct {
   double fx, fy, cx, cy;
   double beta1, beta2, eta;
   int variant; /* 0: two-parameter weights (Eq. 7); 1: alpha compositing (Eq. 9-10) */
+  const double* colors; /* K x 3 per-Gaussian colours, or NULL */
 } fmbo_camera;
 
 /* Ray of pixel p: camera-frame unit direction, world direction, origin. */
@@ -159,7 +165,7 @@ static void project(const fmbo_camera* cam, const double* X, double* uv) {
 }
 
 typedef struct {
-  double D, A, Sdelta, lse, m, Sw;
+  double D, A, Sdelta, lse, m, Sw, C[3];
   double N[3], Nnorm, nf[3], ncam[3];
   double p[3];
   double flow[FMBO_MAX_TARGETS][2];
@@ -213,6 +219,10 @@ static void forward_ray(int K, const double* means, const double* chol, const do
   for (int k = 0; k < 3; ++k) out->nf[k] = out->Nnorm > 0.0 ? N[k] / out->Nnorm : 0.0;
   matvec(R, out->nf, out->ncam);
   for (int k = 0; k < 3; ++k) out->p[k] = o[k] + v[k] * D;
+  for (int k = 0; k < 3; ++k) out->C[k] = 0.0;
+  if (cam->colors)
+    for (int i = 0; i < K; ++i)
+      for (int k = 0; k < 3; ++k) out->C[k] += what[i] * cam->colors[3 * i + k];
   for (int j = 0; j < n_targets; ++j) {
     const double* Rj = target_poses + 12 * j;
     const double* tj = Rj + 9;
@@ -239,14 +249,14 @@ static int check_args(int K, int W, int H, int n_targets, double fx, double fy, 
  * Returns 0, or 1 on invalid arguments.
  */
 static int forward_impl(int variant, int K, const double* means, const double* chol, const double* weights,
-                        const double* pose, int n_targets, const double* target_poses,
+                        const double* colors, const double* pose, int n_targets, const double* target_poses,
                         int W, int H, double fx, double fy, double cx, double cy,
                         double beta1, double beta2, double eta,
                         long long n_pix, const long long* pix,
                         double* depth, double* alpha, double* normal, double* flow, double* saved,
-                        int n_threads) {
+                        double* color, int n_threads) {
   if (check_args(K, W, H, n_targets, fx, fy, eta)) return 1;
-  fmbo_camera cam = {W, H, fx, fy, cx, cy, beta1, beta2, eta, variant};
+  fmbo_camera cam = {W, H, fx, fy, cx, cy, beta1, beta2, eta, variant, colors};
   if (!pix) n_pix = (long long)W * H;
   const double* R = pose;
   const double* t = pose + 9;
@@ -287,6 +297,8 @@ static int forward_impl(int variant, int K, const double* means, const double* c
           saved[3 * n + 1] = out.Sdelta;
           saved[3 * n + 2] = out.Nnorm;
         }
+        if (color)
+          for (int k = 0; k < 3; ++k) color[3 * n + k] = out.C[k];
       }
     }
     free(pairs);
@@ -303,8 +315,21 @@ int fmbo_forward(int K, const double* means, const double* chol, const double* w
                  long long n_pix, const long long* pix,
                  double* depth, double* alpha, double* normal, double* flow, double* saved,
                  int n_threads) {
-  return forward_impl(0, K, means, chol, weights, pose, n_targets, target_poses, W, H, fx, fy, cx, cy, beta1,
-                      beta2, eta, n_pix, pix, depth, alpha, normal, flow, saved, n_threads);
+  return forward_impl(0, K, means, chol, weights, NULL, pose, n_targets, target_poses, W, H, fx, fy, cx, cy, beta1,
+                      beta2, eta, n_pix, pix, depth, alpha, normal, flow, saved, NULL, n_threads);
+}
+
+/* Either variant with per-Gaussian colours (K x 3) and the colour plane color[n][3]. */
+int fmbo_forward_c(int variant, int K, const double* means, const double* chol, const double* weights,
+                   const double* colors, const double* pose, int n_targets, const double* target_poses,
+                   int W, int H, double fx, double fy, double cx, double cy,
+                   double beta1, double beta2, double eta,
+                   long long n_pix, const long long* pix,
+                   double* depth, double* alpha, double* normal, double* flow, double* saved, double* color,
+                   int n_threads) {
+  if (variant != 0 && variant != 1) return 1;
+  return forward_impl(variant, K, means, chol, weights, colors, pose, n_targets, target_poses, W, H, fx, fy, cx,
+                      cy, beta1, beta2, eta, n_pix, pix, depth, alpha, normal, flow, saved, color, n_threads);
 }
 
 /* Alpha-compositing variant (Eq. 9-10); beta1, beta2 and eta are ignored. */
@@ -315,13 +340,14 @@ int fmbo_forward_ac(int K, const double* means, const double* chol, const double
                     long long n_pix, const long long* pix,
                     double* depth, double* alpha, double* normal, double* flow, double* saved,
                     int n_threads) {
-  return forward_impl(1, K, means, chol, weights, pose, n_targets, target_poses, W, H, fx, fy, cx, cy, beta1,
-                      beta2, eta, n_pix, pix, depth, alpha, normal, flow, saved, n_threads);
+  return forward_impl(1, K, means, chol, weights, NULL, pose, n_targets, target_poses, W, H, fx, fy, cx, cy, beta1,
+                      beta2, eta, n_pix, pix, depth, alpha, normal, flow, saved, NULL, n_threads);
 }
 
 /* Accumulators of the backward pass (one set per thread). */
 typedef struct {
   double *gmu, *gchol, *glam; /* K x 3, K x 6, K */
+  double* gcol;                /* K x 3 (colours), or NULL */
   double gpose[12];
   double gtgt[FMBO_MAX_TARGETS][12];
 } grads_t;
@@ -333,7 +359,7 @@ static void backward_ray(int K, const double* chol, const double* weights, const
                          const double* R, const double* tpose, const double* vcam, const double* v,
                          const double* o, int n_targets, const double* target_poses,
                          const pair_t* pairs, const double* what, const double* trans, const ray_out_t* out,
-                         double gD_in, double gA, const double* gN, const double* gF,
+                         double gD_in, double gA, const double* gN, const double* gF, const double* gC,
                          double* ebar, double* wbar, grads_t* acc) {
   double pbar[3] = {0, 0, 0};
   double vbar[3] = {0, 0, 0};
@@ -392,7 +418,10 @@ static void backward_ray(int K, const double* chol, const double* weights, const
     for (int i = 0; i < K; ++i) {
       double Nd[3];
       for (int k = 0; k < 3; ++k) Nd[k] = pairs[i].n[k] - out->N[k];
-      wbar[i] = Wt > 0.0 ? (gD * (pairs[i].t - out->D) + dot3(Nbar, Nd)) / Wt : 0.0;
+      double cterm = 0.0;
+      if (cam->colors && gC)
+        for (int k = 0; k < 3; ++k) cterm += gC[k] * (cam->colors[3 * i + k] - out->C[k]);
+      wbar[i] = Wt > 0.0 ? (gD * (pairs[i].t - out->D) + dot3(Nbar, Nd) + cterm) / Wt : 0.0;
     }
     for (int k = 0; k < K; ++k) {
       double behind = 0.0; /* sum over i strictly behind k of wbar_i w_i */
@@ -407,6 +436,8 @@ static void backward_ray(int K, const double* chol, const double* weights, const
     double sbar = 0.0;
     for (int i = 0; i < K; ++i) {
       double wb = gD * pairs[i].t + dot3(Nbar, pairs[i].n);
+      if (cam->colors && gC)
+        for (int k = 0; k < 3; ++k) wb += gC[k] * cam->colors[3 * i + k];
       ebar[i] = wb;
       sbar += what[i] * wb;
     }
@@ -435,6 +466,8 @@ static void backward_ray(int K, const double* chol, const double* weights, const
     /* d = -q/2 + ln(lambda) */
     double qbar = -0.5 * dbar;
     acc->glam[i] += dbar / weights[i];
+    if (acc->gcol && gC)
+      for (int k = 0; k < 3; ++k) acc->gcol[3 * i + k] += what[i] * gC[k];
     /* q = r^T P r, g = P r  (P symmetric) */
     double Pbar[9];
     double rbar[3];
@@ -513,15 +546,16 @@ static void backward_ray(int K, const double* chol, const double* weights, const
  * 2 on allocation failure.
  */
 static int backward_impl(int variant, int K, const double* means, const double* chol, const double* weights,
-                         const double* pose, int n_targets, const double* target_poses,
+                         const double* colors, const double* pose, int n_targets, const double* target_poses,
                          int W, int H, double fx, double fy, double cx, double cy,
                          double beta1, double beta2, double eta,
                          long long n_pix, const long long* pix,
                          const double* g_depth, const double* g_alpha, const double* g_normal,
-                         const double* g_flow, double* grad_means, double* grad_chol, double* grad_weights,
-                         double* grad_pose, double* grad_target_poses, int n_threads) {
+                         const double* g_flow, const double* g_color, double* grad_means, double* grad_chol,
+                         double* grad_weights, double* grad_colors, double* grad_pose, double* grad_target_poses,
+                         int n_threads) {
   if (check_args(K, W, H, n_targets, fx, fy, eta)) return 1;
-  fmbo_camera cam = {W, H, fx, fy, cx, cy, beta1, beta2, eta, variant};
+  fmbo_camera cam = {W, H, fx, fy, cx, cy, beta1, beta2, eta, variant, colors};
   if (!pix) n_pix = (long long)W * H;
   const double* R = pose;
   const double* t = pose + 9;
@@ -539,7 +573,8 @@ static int backward_impl(int variant, int K, const double* means, const double* 
     accs[a].gmu = (double*)calloc((size_t)K * 3, sizeof(double));
     accs[a].gchol = (double*)calloc((size_t)K * 6, sizeof(double));
     accs[a].glam = (double*)calloc((size_t)K, sizeof(double));
-    if (!accs[a].gmu || !accs[a].gchol || !accs[a].glam) failed = 1;
+    accs[a].gcol = (colors && grad_colors) ? (double*)calloc((size_t)K * 3, sizeof(double)) : NULL;
+    if (!accs[a].gmu || !accs[a].gchol || !accs[a].glam || ((colors && grad_colors) && !accs[a].gcol)) failed = 1;
   }
   if (!failed) {
 #pragma omp parallel num_threads(nt)
@@ -577,8 +612,11 @@ static int backward_impl(int variant, int K, const double* means, const double* 
               gF[2 * j] = g_flow[(n * n_targets + j) * 2];
               gF[2 * j + 1] = g_flow[(n * n_targets + j) * 2 + 1];
             }
+          double gC[3] = {0, 0, 0};
+          if (g_color)
+            for (int k = 0; k < 3; ++k) gC[k] = g_color[3 * n + k];
           backward_ray(K, chol, weights, &cam, R, t, vcam, v, o, n_targets, target_poses, pairs, what, trans,
-                       &out, gD, gA, gN, gF, ebar, wbar, acc);
+                       &out, gD, gA, gN, gF, g_color ? gC : NULL, ebar, wbar, acc);
         }
       }
       free(pairs);
@@ -593,6 +631,8 @@ static int backward_impl(int variant, int K, const double* means, const double* 
     for (int i = 0; i < 3 * K; ++i) grad_means[i] = 0.0;
     for (int i = 0; i < 6 * K; ++i) grad_chol[i] = 0.0;
     for (int i = 0; i < K; ++i) grad_weights[i] = 0.0;
+    if (colors && grad_colors)
+      for (int i = 0; i < 3 * K; ++i) grad_colors[i] = 0.0;
     if (grad_pose)
       for (int i = 0; i < 12; ++i) grad_pose[i] = 0.0;
     if (grad_target_poses)
@@ -601,6 +641,8 @@ static int backward_impl(int variant, int K, const double* means, const double* 
       for (int i = 0; i < 3 * K; ++i) grad_means[i] += accs[a].gmu[i];
       for (int i = 0; i < 6 * K; ++i) grad_chol[i] += accs[a].gchol[i];
       for (int i = 0; i < K; ++i) grad_weights[i] += accs[a].glam[i];
+      if (accs[a].gcol)
+        for (int i = 0; i < 3 * K; ++i) grad_colors[i] += accs[a].gcol[i];
       if (grad_pose)
         for (int i = 0; i < 12; ++i) grad_pose[i] += accs[a].gpose[i];
       if (grad_target_poses)
@@ -612,6 +654,7 @@ static int backward_impl(int variant, int K, const double* means, const double* 
     free(accs[a].gmu);
     free(accs[a].gchol);
     free(accs[a].glam);
+    free(accs[a].gcol);
   }
   free(accs);
   return failed ? 2 : 0;
@@ -625,9 +668,24 @@ int fmbo_backward(int K, const double* means, const double* chol, const double* 
                   const double* g_depth, const double* g_alpha, const double* g_normal, const double* g_flow,
                   double* grad_means, double* grad_chol, double* grad_weights,
                   double* grad_pose, double* grad_target_poses, int n_threads) {
-  return backward_impl(0, K, means, chol, weights, pose, n_targets, target_poses, W, H, fx, fy, cx, cy, beta1,
-                       beta2, eta, n_pix, pix, g_depth, g_alpha, g_normal, g_flow, grad_means, grad_chol,
-                       grad_weights, grad_pose, grad_target_poses, n_threads);
+  return backward_impl(0, K, means, chol, weights, NULL, pose, n_targets, target_poses, W, H, fx, fy, cx, cy,
+                       beta1, beta2, eta, n_pix, pix, g_depth, g_alpha, g_normal, g_flow, NULL, grad_means,
+                       grad_chol, grad_weights, NULL, grad_pose, grad_target_poses, n_threads);
+}
+
+/* Either variant with per-Gaussian colours: g_color[n][3] upstream, grad_colors [K][3]. */
+int fmbo_backward_c(int variant, int K, const double* means, const double* chol, const double* weights,
+                    const double* colors, const double* pose, int n_targets, const double* target_poses,
+                    int W, int H, double fx, double fy, double cx, double cy,
+                    double beta1, double beta2, double eta,
+                    long long n_pix, const long long* pix,
+                    const double* g_depth, const double* g_alpha, const double* g_normal, const double* g_flow,
+                    const double* g_color, double* grad_means, double* grad_chol, double* grad_weights,
+                    double* grad_colors, double* grad_pose, double* grad_target_poses, int n_threads) {
+  if (variant != 0 && variant != 1) return 1;
+  return backward_impl(variant, K, means, chol, weights, colors, pose, n_targets, target_poses, W, H, fx, fy, cx,
+                       cy, beta1, beta2, eta, n_pix, pix, g_depth, g_alpha, g_normal, g_flow, g_color, grad_means,
+                       grad_chol, grad_weights, grad_colors, grad_pose, grad_target_poses, n_threads);
 }
 
 /* Adjoint of the alpha-compositing variant (Eq. 9-10); beta1, beta2, eta ignored. */
@@ -639,9 +697,9 @@ int fmbo_backward_ac(int K, const double* means, const double* chol, const doubl
                      const double* g_depth, const double* g_alpha, const double* g_normal, const double* g_flow,
                      double* grad_means, double* grad_chol, double* grad_weights,
                      double* grad_pose, double* grad_target_poses, int n_threads) {
-  return backward_impl(1, K, means, chol, weights, pose, n_targets, target_poses, W, H, fx, fy, cx, cy, beta1,
-                       beta2, eta, n_pix, pix, g_depth, g_alpha, g_normal, g_flow, grad_means, grad_chol,
-                       grad_weights, grad_pose, grad_target_poses, n_threads);
+  return backward_impl(1, K, means, chol, weights, NULL, pose, n_targets, target_poses, W, H, fx, fy, cx, cy,
+                       beta1, beta2, eta, n_pix, pix, g_depth, g_alpha, g_normal, g_flow, NULL, grad_means,
+                       grad_chol, grad_weights, NULL, grad_pose, grad_target_poses, n_threads);
 }
 
 /*
@@ -670,7 +728,7 @@ int fmbo_points(int variant, int K, const double* means, const double* chol, con
                 double beta1, double beta2, double eta, long long n_pix, const long long* pix,
                 double* points, double* normal_tf, double* normal_screen, double* quality, int n_threads) {
   if (check_args(K, W, H, 0, fx, fy, eta) || (variant != 0 && variant != 1)) return 1;
-  fmbo_camera cam = {W, H, fx, fy, cx, cy, beta1, beta2, eta, variant};
+  fmbo_camera cam = {W, H, fx, fy, cx, cy, beta1, beta2, eta, variant, NULL};
   if (!pix) n_pix = (long long)W * H;
   const double* R = pose;
   const double* t = pose + 9;
@@ -766,7 +824,7 @@ int fmbo_attribution(int variant, int K, const double* means, const double* chol
                      const double* ray_loss, double* attribution) {
   if (check_args(K, W, H, 0, fx, fy, eta) || (variant != 0 && variant != 1) || !ray_loss || !attribution)
     return 1;
-  fmbo_camera cam = {W, H, fx, fy, cx, cy, beta1, beta2, eta, variant};
+  fmbo_camera cam = {W, H, fx, fy, cx, cy, beta1, beta2, eta, variant, NULL};
   if (!pix) n_pix = (long long)W * H;
   pair_t* pairs = (pair_t*)malloc(sizeof(pair_t) * (size_t)K);
   double* what = (double*)malloc(sizeof(double) * (size_t)K);

@@ -12,13 +12,14 @@ from __future__ import annotations
 import torch
 
 
-def render(means, chol, weights, R, t, target_R, target_t, cam, beta1=21.4, beta2=3.14, eta=1.0, variant=0):
+def render(means, chol, weights, R, t, target_R, target_t, cam, beta1=21.4, beta2=3.14, eta=1.0, variant=0,
+           colors=None):
     """``variant`` 0: two-parameter weights (Eq. 7); 1: alpha compositing (Eq. 9-10,
     transmittance from a (P, K, K) indicator matrix of "j strictly in front of i").
     All tensors float64.  means (K,3), chol (K,6) packed (L00,L10,L11,L20,L21,L22),
     weights (K,), R (3,3) and t (3,) world->camera, target_R (T,3,3), target_t (T,3),
     cam = (W, H, fx, fy, cx, cy).  Returns depth (P,), alpha (P,), normal (P,3) in the
-    camera frame, flow (P,T,2)."""
+    camera frame, flow (P,T,2), and with ``colors`` (K,3) the blended colour (P,3)."""
     W, H, fx, fy, cx, cy = cam
     K = means.shape[0]
     ys, xs = torch.meshgrid(torch.arange(H, dtype=torch.float64), torch.arange(W, dtype=torch.float64),
@@ -68,4 +69,6 @@ def render(means, chol, weights, R, t, target_R, target_t, cam, beta1=21.4, beta
         vv = fy * X[:, 1] / X[:, 2] + cy - py
         flows.append(torch.stack([u, vv], dim=1))
     flow = torch.stack(flows, dim=1) if flows else torch.zeros(depth.shape[0], 0, 2, dtype=torch.float64)
+    if colors is not None:  # Eq. 3 with per-Gaussian colours: (P, 3)
+        return depth, alpha, normal, flow, w @ colors
     return depth, alpha, normal, flow

@@ -375,39 +375,54 @@ __global__ void __launch_bounds__(kAcThreads) backward_ac_kernel(const __grid_co
                          : kNoKey;
         }
         warp_bitonic_sort<M>(key, lane);
-        float Q[M], ts[M];
-        float carry = 0.f;
+        // sorted order, lane holding positions lane M + m: inclusive prefix Q of q
+        float ts[M], Q[M];
+        int idx[M];
+        float lane_sum = 0.f;
 #pragma unroll
         for (int m = 0; m < M; ++m) {
           const bool valid = key[m] != kNoKey;
-          const int idx = static_cast<int>(key[m] & 0xffffffffu);
+          idx[m] = valid ? static_cast<int>(key[m] & 0xffffffffu) : -1;
           ts[m] = valid ? from_order_bits(static_cast<unsigned>(key[m] >> 32)) : INFINITY;
-          Q[m] = warp_incl_sum(valid ? sq[idx] : 0.f, lane) + carry;
-          carry = __shfl_sync(kFull, Q[m], 31);
+          lane_sum += valid ? sq[idx[m]] : 0.f;
+          Q[m] = lane_sum;
         }
-        const float Qtot = carry;
-        // value of Q at the end of each run, copied leftwards within the run
-        float nxt_val = 0.f, nxt_t = INFINITY;
+        const float incl_lane = warp_incl_sum(lane_sum, lane);
+        const float Qtot = __shfl_sync(kFull, incl_lane, 31);
+        const float before = incl_lane - lane_sum;
+        float next_t = __shfl_down_sync(kFull, ts[0], 1);
+        if (lane == 31) next_t = INFINITY;
+        // Q at the end of each hit's run of equal depth: the first run end at or after
+        // the position, within the lane (a backward pass) or in the lanes after it
+        // (a segmented copy-from-the-right scan of each lane's first run end).
+        float vloc[M];
+        bool has[M];
+        bool h = false;
+        float vv = 0.f;
 #pragma unroll
         for (int m = M - 1; m >= 0; --m) {
-          float right_t = __shfl_down_sync(kFull, ts[m], 1);
-          if (lane == 31) right_t = nxt_t;
-          bool flag = ts[m] != right_t;  // last hit of its run
-          float val = Q[m];
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const float ov = __shfl_down_sync(kFull, val, o);
-            const bool of = __shfl_down_sync(kFull, flag ? 1 : 0, o) != 0;
-            if (!flag && lane + o < 32) {
-              val = ov;
-              flag = of;
-            }
+          if (ts[m] != (m == M - 1 ? next_t : ts[m + 1])) {
+            h = true;
+            vv = before + Q[m];
           }
-          if (!flag) val = nxt_val;  // the run continues into the next register
-          if (key[m] != kNoKey) sd[static_cast<int>(key[m] & 0xffffffffu)] = Qtot - val;  // sd now holds U
-          nxt_val = __shfl_sync(kFull, val, 0);
-          nxt_t = __shfl_sync(kFull, ts[m], 0);
+          has[m] = h;
+          vloc[m] = vv;
         }
+        float F = vloc[0];
+        bool Ff = has[0];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const float ov = __shfl_down_sync(kFull, F, o);
+          const bool of = __shfl_down_sync(kFull, Ff ? 1 : 0, o) != 0;
+          if (!Ff && lane + o < 32) {
+            F = ov;
+            Ff = of;
+          }
+        }
+        const float cin = __shfl_down_sync(kFull, F, 1);
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+          if (idx[m] >= 0) sd[idx[m]] = Qtot - (has[m] ? vloc[m] : cin);  // sd now holds U
       }
       __syncwarp();
       // dbar and c per (ray, Gaussian) into the pair buffer; the ray record

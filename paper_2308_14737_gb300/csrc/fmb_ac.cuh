@@ -36,7 +36,12 @@ __device__ __forceinline__ float one_minus_exp_neg(float x) {
   return x < 0.25f ? series : 1.f - ex2_approx(-x * kLog2e);
 }
 
-// Ascending bitonic sort of the warp's 32 M keys; element i = m * 32 + lane.
+// Ascending bitonic sort of the warp's 32 M keys in a blocked layout: sorting
+// position i = lane * M + m, so lane l ends up holding the consecutive sorted
+// positions l M .. l M + M - 1.  Partners closer than M are registers of the same
+// lane; the log2(32) x (log2(32) + 1) / 2 + ... steps whose partner is another lane
+// exchange one key per register by shuffle.  (Which key starts where does not
+// matter: the network sorts any input arrangement.)
 template <int M>
 __device__ __forceinline__ void warp_bitonic_sort(unsigned long long (&key)[M], int lane) {
   constexpr int N = 32 * M;
@@ -44,27 +49,27 @@ __device__ __forceinline__ void warp_bitonic_sort(unsigned long long (&key)[M], 
   for (int k = 2; k <= N; k <<= 1) {
 #pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j >= 32) {  // partner in another register of the same lane
-        const int jm = j >> 5;
+      if (j < M) {  // partner in register m ^ j of the same lane
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-          if ((m & jm) == 0) {
-            const int m2 = m | jm;
-            const bool up = ((m << 5) & k) == 0;
+          if ((m & j) == 0) {
+            const int m2 = m | j;
+            const bool up = (((lane * M) + m) & k) == 0;
             const unsigned long long a = key[m], b = key[m2];
             const bool swap = up ? (a > b) : (a < b);
             key[m] = swap ? b : a;
             key[m2] = swap ? a : b;
           }
         }
-      } else {  // partner in lane ^ j
+      } else {  // partner in lane ^ (j / M), same register
+        const int jl = j / M;
+        const bool lower = (lane & jl) == 0;
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-          const unsigned long long other = __shfl_xor_sync(kFull, key[m], j);
-          const int i = (m << 5) | lane;
-          const bool take_min = ((i & j) == 0) == ((i & k) == 0);
+          const unsigned long long other = __shfl_xor_sync(kFull, key[m], jl);
+          const bool up = (((lane * M) + m) & k) == 0;
           const bool other_smaller = other < key[m];
-          key[m] = (take_min == other_smaller) ? other : key[m];
+          key[m] = ((lower == up) == other_smaller) ? other : key[m];
         }
       }
     }
@@ -134,34 +139,52 @@ __device__ __forceinline__ AcSums ac_render_ray(const float4* __restrict__ rec, 
   }
   __syncwarp();
   warp_bitonic_sort<M>(key, lane);
-  // Sorted order: exclusive prefix sums of delta, run-aware (Eq. 10's strict <).
-  float carry = 0.f, carry_t = 0.f, carry_S = 0.f;
+  // Sorted order (lane holds positions lane M + m): exclusive prefix sums of
+  // delta, run-aware (Eq. 10's strict <).
+  float ts[M], ds[M];
+  int idx[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) {
     const bool valid = key[m] != kNoKey;
-    const int idx = static_cast<int>(key[m] & 0xffffffffu);
-    const float ts = valid ? from_order_bits(static_cast<unsigned>(key[m] >> 32)) : INFINITY;
-    const float ds = valid ? sd[idx] : 0.f;
-    const float incl = warp_incl_sum(ds, lane);
-    float excl = __shfl_up_sync(kFull, incl, 1);
-    if (lane == 0) excl = 0.f;
-    excl += carry;
-    float prev_t = __shfl_up_sync(kFull, ts, 1);
-    if (lane == 0) prev_t = carry_t;
-    const bool start = (m == 0 && lane == 0) || ts != prev_t;
-    // P (the exclusive sums) never decreases, so the sum in front of this hit's
-    // run is the largest P at a run start so far.
-    const float S = fmaxf(warp_incl_max(start ? excl : 0.f, lane), carry_S);
-    const float T = ex2_approx(-S * kLog2e);
-    if (valid) {
-      sT[idx] = T;
-      sw[idx] = T * one_minus_exp_neg(ds);
+    idx[m] = valid ? static_cast<int>(key[m] & 0xffffffffu) : -1;
+    ts[m] = valid ? from_order_bits(static_cast<unsigned>(key[m] >> 32)) : INFINITY;
+    ds[m] = valid ? sd[idx[m]] : 0.f;
+  }
+  float lane_sum = 0.f;
+  float lex[M];  // exclusive sums within the lane
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    lex[m] = lane_sum;
+    lane_sum += ds[m];
+  }
+  const float incl_lane = warp_incl_sum(lane_sum, lane);
+  const float before = incl_lane - lane_sum;  // sum over the lanes in front
+  const float total = __shfl_sync(kFull, incl_lane, 31);
+  float prev_t = __shfl_up_sync(kFull, ts[M - 1], 1);
+  // The sums P never decrease, so the sum in front of a hit's run is the largest
+  // P at a run start up to it.
+  float lmax = 0.f;
+  float Sl[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const float P = before + lex[m];
+    const bool start = (lane == 0 && m == 0) || ts[m] != (m == 0 ? prev_t : ts[m - 1]);
+    if (start) lmax = fmaxf(lmax, P);
+    Sl[m] = lmax;
+  }
+  const float pmax_incl = warp_incl_max(lmax, lane);
+  float pmax = __shfl_up_sync(kFull, pmax_incl, 1);
+  if (lane == 0) pmax = 0.f;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    if (idx[m] >= 0) {
+      const float T = ex2_approx(-fmaxf(Sl[m], pmax) * kLog2e);
+      sT[idx[m]] = T;
+      sw[idx[m]] = T * one_minus_exp_neg(ds[m]);
     }
-    carry += __shfl_sync(kFull, incl, 31);
-    carry_t = __shfl_sync(kFull, ts, 31);
-    carry_S = __shfl_sync(kFull, S, 31);
   }
   __syncwarp();
+  const float carry = total;
   AcSums r{0.f, 0.f, 0.f, 0.f, 0.f, carry};
 #pragma unroll
   for (int m = 0; m < M; ++m) {

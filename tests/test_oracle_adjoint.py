@@ -143,3 +143,39 @@ def test_scene_backward_sums_views(oracle_mod):
         acc_pose[tgt] += r["target_poses"][0]
     np.testing.assert_allclose(g["means"], acc_mu, rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(g["poses"], acc_pose, rtol=1e-12, atol=1e-12)
+
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_colour_adjoint_matches_differences_and_autograd(oracle_mod, variant):
+    """The colour plane's adjoint: the colours' gradient and the colour term of every
+    other gradient, against central differences and the torch restatement."""
+    mu, chol, lam, pose, tgt, ups = tiny_scene(11, K=4)
+    rng = np.random.default_rng(12)
+    col = rng.uniform(0.0, 1.0, (4, 3))
+    gcol = rng.standard_normal((20, 3))
+
+    def f():
+        r = oracle_mod.render_view(mu, chol, lam, pose, tgt[None], CAM, variant=variant, colors=col)
+        return (np.sum(ups["g_depth"] * r["depth"]) + np.sum(ups["g_alpha"] * r["alpha"])
+                + np.sum(ups["g_normal"] * r["normal"]) + np.sum(ups["g_flow"] * r["flow"]) + np.sum(gcol * r["color"]))
+
+    g = oracle_mod.backward_view(mu, chol, lam, pose, tgt[None], CAM, **ups, variant=variant, colors=col,
+                                 g_color=gcol)
+    for name, x, ga in (("colors", col, g["colors"]), ("means", mu, g["means"]), ("chol", chol, g["chol"]),
+                        ("weights", lam, g["weights"])):
+        gfd = fd_grad(f, x)
+        assert np.max(np.abs(ga - gfd)) <= 1e-6 * np.max(np.abs(gfd)), name
+    t = lambda a: torch.tensor(a, dtype=torch.float64, requires_grad=True)
+    tm, tc, tl, tcol = t(mu), t(chol), t(lam), t(col)
+    tR, tt_ = t(pose[:9].reshape(3, 3)), t(pose[9:])
+    gR, gt = t(tgt[:9].reshape(3, 3)[None]), t(tgt[9:][None])
+    d, a, n, fl, c = torch_ref.render(tm, tc, tl, tR, tt_, gR, gt, CAM, variant=variant, colors=tcol)
+    L = ((d * torch.tensor(ups["g_depth"])).sum() + (a * torch.tensor(ups["g_alpha"])).sum()
+         + (n * torch.tensor(ups["g_normal"])).sum() + (fl * torch.tensor(ups["g_flow"])).sum()
+         + (c * torch.tensor(gcol)).sum())
+    L.backward()
+    for name, tg, og in (("colors", tcol.grad, g["colors"]), ("means", tm.grad, g["means"]),
+                         ("chol", tc.grad, g["chol"]), ("weights", tl.grad, g["weights"])):
+        tg = tg.numpy()
+        assert np.max(np.abs(tg - og)) <= 1e-10 * max(1.0, np.max(np.abs(tg))), name

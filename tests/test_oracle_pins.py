@@ -504,3 +504,37 @@ def test_attribution_two_centred_closed_form(oracle_mod):
     a = oracle_mod.attribution_scene(scene, np.array([2.0]))
     s_ = np.exp(B1 * np.log(1.1 / 1.0) - B2 * 0.5)
     np.testing.assert_allclose(a, 2.0 * np.array([1.0, s_]) / (1.0 + s_), rtol=1e-6)
+
+
+# ------------------------------------------------------------ per-Gaussian colours
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_colour_blend_closed_forms(oracle_mod, variant):
+    """Eq. 3 with colours: one Gaussian gives its own colour; two centred on one ray
+    give the depth blend's weights applied to the colours (Eq. 7: 1/(1+s), s/(1+s);
+    Eq. 9-10: w1 = 1 - e^-l1, w2 = e^-l1 (1 - e^-l2)); a constant colour blends to
+    itself anywhere (weights normalised)."""
+    pose = synth.look_at_pose((0.0, 0.0, -4.0))
+    x, y = 5, 7
+    v, o, _ = ray_of_pixel(pose, CAM, x, y)
+    pix = [y * CAM[0] + x]
+    c1, c2 = np.array([0.9, 0.2, 0.1]), np.array([0.1, 0.5, 0.8])
+    one = oracle_mod.render_view(np.atleast_2d(o + 3.7 * v), np.array([[2.0, 0, 2.0, 0, 0, 2.0]]), np.array([0.8]),
+                                 pose, None, CAM, pixels=pix, variant=variant, colors=c1[None])
+    np.testing.assert_allclose(one["color"][0], c1, atol=1e-15)
+    chol = np.array([[3, 0.2, 2, -0.1, 0.3, 4], [1.5, 0, 1.5, 0, 0, 1.5]], dtype=np.float64)
+    r1, r2, l1, l2 = 3.2, 4.1, 0.9, 1.3
+    r = oracle_mod.render_view(np.stack([o + r1 * v, o + r2 * v]), chol, np.array([l1, l2]), pose, None, CAM,
+                               pixels=pix, variant=variant, colors=np.stack([c1, c2]))
+    if variant == 0:
+        s_ = np.exp(B1 * np.log(l2 / l1) - B2 * (r2 - r1))
+        w1, w2 = 1.0, s_
+    else:
+        w1, w2 = 1 - np.exp(-l1), np.exp(-l1) * (1 - np.exp(-l2))
+    np.testing.assert_allclose(r["color"][0], (w1 * c1 + w2 * c2) / (w1 + w2), atol=1e-12)
+    s = synth.config0(seed=3, K=11, W=10, H=8)
+    const = oracle_mod.render_view(s.means, s.chol, s.weights, s.poses[0], None, (10, 8, 10.0, 10.0, 5.0, 4.0),
+                                   variant=variant, colors=np.tile([0.3, 0.6, 0.2], (11, 1)))
+    hit = const["alpha"] > 1e-6
+    np.testing.assert_allclose(const["color"][hit], np.broadcast_to([0.3, 0.6, 0.2], (hit.sum(), 3)), atol=1e-12)
