@@ -88,6 +88,11 @@ typedef struct {
                         recomputing them.  The backward must then be given the
                         workspace of the forward call of the same batch, unchanged.
                         0 (default): recompute from the saved per-pixel normalisers. */
+  int colors;        /* 1: every Gaussian carries an RGB colour, blended by Eq. 3 like the
+                        depth (Sec. 3.1) into a colour plane, with its adjoint (the
+                        colours and color/g_color/grad_colors arguments are then
+                        required / used); 0: no colours (those arguments are ignored).
+                        Not with store_pairs. */
 } fmb_params;
 
 /* One camera view of one object.  Planes of the view start at pixel `pix_offset`
@@ -117,7 +122,8 @@ typedef struct {
  * h_obj_offsets[k+1]) (host int64 array of n_objects + 1 entries, starting at 0,
  * non-decreasing, every object with >= 1 Gaussian).  means: [G][3]; chol: [G][6]
  * packed (L00, L10, L11, L20, L21, L22); weights: [G] (lambda > 0), with
- * G = h_obj_offsets[n_objects].  poses: [n_poses][12].
+ * G = h_obj_offsets[n_objects].  colors: [G][3] (params->colors; else ignored,
+ * may be NULL).  poses: [n_poses][12].
  *
  * Outputs (device, overwritten for every pixel of every view; P_v = W*H):
  *   depth  [P_total]          depth[pix_offset + p]
@@ -128,6 +134,9 @@ typedef struct {
  *                             2*n_flow*pix_offset, in pixels (u then v); a slot
  *                             whose flow_target is -1 is written as 0; NULL if
  *                             n_flow == 0
+ *   color  [3*P_total]        per view a [3][P_v] block at 3*pix_offset: Eq. 3
+ *                             with the Gaussians' colours (params->colors; else
+ *                             ignored, may be NULL)
  *   saved  [3*P_total]        per view a [3][P_v] block at 3*pix_offset:
  *                             0: log2 of sum_i 2^(e_i log2 e), e_i = beta1 d_i - (beta2/eta) t_i
  *                                (variant 1: W = sum_i w_i)
@@ -141,10 +150,10 @@ typedef struct {
  * rounded up: 12 x sum over views of P_v x (K_v rounded up to a multiple of 4)).
  */
 fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
-                              const float* means, const float* chol, const float* weights, int n_poses,
-                              const float* poses, int n_views, const fmb_view* h_views, float* depth,
-                              float* alpha, float* normal, float* flow, float* saved, void* workspace,
-                              size_t workspace_bytes, fmb_stream_t stream);
+                              const float* means, const float* chol, const float* weights, const float* colors,
+                              int n_poses, const float* poses, int n_views, const fmb_view* h_views,
+                              float* depth, float* alpha, float* normal, float* flow, float* color, float* saved,
+                              void* workspace, size_t workspace_bytes, fmb_stream_t stream);
 
 /*
  * Adjoint of fmb_render_forward (the derivative of the renderer defined above;
@@ -155,22 +164,24 @@ fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const lon
  * same batch must have used this workspace and these params).
  *
  * Inputs: the same scene, poses, views and params as the forward call; the
- * forward's depth, normal (NULL if !want_normals) and saved planes; the upstream
- * gradients g_depth, g_alpha, g_normal, g_flow in the layouts of the forward
- * outputs (each may be NULL = zero).
+ * forward's depth, normal (NULL if !want_normals), color (colour mode) and saved
+ * planes; the upstream gradients g_depth, g_alpha, g_normal, g_flow, g_color in
+ * the layouts of the forward outputs (each may be NULL = zero).
  * Outputs (overwritten, never accumulated): grad_means [G][3], grad_chol [G][6],
- * grad_weights [G] (d/d lambda), grad_poses [n_poses][12] (d/dR as a free 3x3
- * matrix, row-major, then d/dt; NULL = pose gradients not computed).
+ * grad_weights [G] (d/d lambda), grad_colors [G][3] (colour mode), grad_poses
+ * [n_poses][12] (d/dR as a free 3x3 matrix, row-major, then d/dt; NULL = pose
+ * gradients not computed).
  * deterministic = 1 gives bitwise-reproducible results (fixed-order two-stage
  * reduction through the workspace); 0 uses fp32 atomics.
  */
 fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
-                               const float* means, const float* chol, const float* weights, int n_poses,
-                               const float* poses, int n_views, const fmb_view* h_views, const float* depth,
-                               const float* normal, const float* saved, const float* g_depth,
-                               const float* g_alpha, const float* g_normal, const float* g_flow,
-                               float* grad_means, float* grad_chol, float* grad_weights, float* grad_poses,
-                               void* workspace, size_t workspace_bytes, fmb_stream_t stream);
+                               const float* means, const float* chol, const float* weights, const float* colors,
+                               int n_poses, const float* poses, int n_views, const fmb_view* h_views,
+                               const float* depth, const float* normal, const float* color, const float* saved,
+                               const float* g_depth, const float* g_alpha, const float* g_normal,
+                               const float* g_flow, const float* g_color, float* grad_means, float* grad_chol,
+                               float* grad_weights, float* grad_colors, float* grad_poses, void* workspace,
+                               size_t workspace_bytes, fmb_stream_t stream);
 
 /*
  * fmb_render_forward without a workspace argument, for callers that cannot
@@ -182,7 +193,8 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
  *
  * Its scratch is one fixed 1 MiB array in the library (held on every device that
  * loads the library until the process exits): a batch needs 256 + 64 x (sum over
- * views of the view's Gaussian count) bytes, and a larger batch is rejected with
+ * views of the view's Gaussian count) bytes (plus 16 more per view and Gaussian
+ * with colours, each region rounded up to 256), and a larger batch is rejected with
  * FMB_ERR_WORKSPACE.  Nothing is allocated.  The first call on each device looks up
  * the array's device address (cudaGetSymbolAddress); make that first call before
  * any stream capture.  All calls share the array: calls whose GPU work overlaps
@@ -191,9 +203,10 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
  * reader.
  */
 fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
-                                      const float* means, const float* chol, const float* weights, int n_poses,
-                                      const float* poses, int n_views, const fmb_view* h_views, float* depth,
-                                      float* alpha, float* normal, float* flow, float* saved, fmb_stream_t stream);
+                                      const float* means, const float* chol, const float* weights,
+                                      const float* colors, int n_poses, const float* poses, int n_views,
+                                      const fmb_view* h_views, float* depth, float* alpha, float* normal,
+                                      float* flow, float* color, float* saved, fmb_stream_t stream);
 
 /*
  * Oriented point export (Sec. 6: the oriented point set a Poisson surface

@@ -82,10 +82,17 @@ __global__ void __launch_bounds__(kAcThreads) forward_ac_kernel(const __grid_con
       float vc[3], v[3], vl[3], pxy[2];
       pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
       float t[M], dl[M], n[M][3];
-      const AcSums a = ac_render_ray<NORMALS, M>(srec, V.K, v, vl, k, lane, t, dl, n, sd, sw, sT);
+      const float4* crec = s.crec != nullptr && out.color != nullptr ? s.crec + V.rec_off : nullptr;
+      const AcSums a = ac_render_ray<NORMALS, M>(srec, V.K, v, vl, k, lane, t, dl, n, sd, sw, sT, crec);
       if (lane == 0) {
         const float iW = a.W > 0.f ? 1.0f / a.W : 0.f;
         const float D = a.WT * iW;
+        if (crec != nullptr) {
+          float* col = out.color + 3 * off;
+          col[p] = a.WC0 * iW;
+          col[P + p] = a.WC1 * iW;
+          col[2 * P + p] = a.WC2 * iW;
+        }
         out.depth[off + p] = D;
         out.alpha[off + p] = -expm1f(-a.Sd);
         float* sv = out.saved + 3 * off;
@@ -131,11 +138,12 @@ __global__ void __launch_bounds__(kAcThreads) forward_ac_kernel(const __grid_con
 // ----------------------------------------------------------------- backward
 struct AcAcc2 {
   f2 nSd, Y0, Y1, Y2, G00, G10, G11, G20, G21, G22, M[9];
+  f2 Cb0, Cb1, Cb2;  // colour mode: sum (w / W) Cbar
 };
 
 // One packed step: two Gaussians (lanes) against one ray.  rr: the ray's record
 // (5 x 16 bytes, duplicated values), pd: (dbar, c) of both Gaussians.
-template <bool NORMALS>
+template <bool NORMALS, bool COLOR = false>
 __device__ __forceinline__ void bwd_pair_ac2(AcAcc2& A, const GaussRec2& gr, const ulonglong2* __restrict__ rr,
                                              float4 pd, f2 tiny) {
   const ulonglong2 q0 = rr[0], q1 = rr[1], q2 = rr[2], q3 = rr[3], q4 = rr[4];
@@ -198,13 +206,19 @@ __device__ __forceinline__ void bwd_pair_ac2(AcAcc2& A, const GaussRec2& gr, con
   A.M[6] = fma2(v2, ab0, A.M[6]);
   A.M[7] = fma2(v2, ab1, A.M[7]);
   A.M[8] = fma2(v2, ab2, A.M[8]);
+  if (COLOR) {  // record slots 5-6: [Cb0 Cb0 Cb1 Cb1 | Cb2 Cb2 0 0]
+    const ulonglong2 q5 = rr[5], q6 = rr[6];
+    A.Cb0 = fma2(c, as_f2(q5.x), A.Cb0);
+    A.Cb1 = fma2(c, as_f2(q5.y), A.Cb1);
+    A.Cb2 = fma2(c, as_f2(q6.x), A.Cb2);
+  }
 }
 
 // Shared memory of the backward, in floats after the records:
 //   ray records [kAcRays][kAcRayRec float4] | pair values [kAcRays][32 M][2] |
 //   per warp scratch sd, sw, sT, sq [32 M floats each]
 // The pair values region is reused for the per-thread sums of the reduction.
-constexpr int kAcAccFloats = 38;
+constexpr int kAcAccFloats = 44;  // 22 sums per thread, two Gaussians (with the colour sums)
 template <int M>
 __host__ __device__ constexpr int ac_pairv_floats() {
   return kAcRays * 32 * M * 2 > kAcThreads * kAcAccFloats ? kAcRays * 32 * M * 2 : kAcThreads * kAcAccFloats;
@@ -215,7 +229,7 @@ __host__ __device__ constexpr int ac_bwd_smem_floats() {
 }
 
 template <bool NORMALS, int NFLOW, int M>
-__global__ void __launch_bounds__(kAcThreads) backward_ac_kernel(const __grid_constant__ Batch batch, Scene s,
+__global__ void __launch_bounds__(kAcThreads, M >= 8 ? 2 : 3) backward_ac_kernel(const __grid_constant__ Batch batch, Scene s,
                                                                  Consts k, const float4* __restrict__ records,
                                                                  BwdIn in, BwdOut out, int* status, int* counter) {
   extern __shared__ float4 ac_smem[];
@@ -240,6 +254,8 @@ __global__ void __launch_bounds__(kAcThreads) backward_ac_kernel(const __grid_co
   __syncthreads();
   unsigned uses = 0;
   const bool want_pose = out.gposes != nullptr;
+  const bool color = s.crec != nullptr && out.gcolors != nullptr;  // colour mode (uniform)
+  const int NC = color ? 13 : 10;  // gradient values per Gaussian in a partial slot
   for (int round = 0;; ++round) {
     const int item = next_item(counter, round, &s_item);
     if (item < 0 || item >= batch.n_items) break;
@@ -276,9 +292,17 @@ __global__ void __launch_bounds__(kAcThreads) backward_ac_kernel(const __grid_co
       float vc[3], v[3], vl[3], pxy[2];
       pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
       float t[M], dl[M], n[M][3];
-      const AcSums a = ac_render_ray<NORMALS, M>(srec, K, v, vl, k, lane, t, dl, n, sd, sw, sT);
+      const float4* crec = color ? s.crec + V.rec_off : nullptr;
+      const AcSums a = ac_render_ray<NORMALS, M>(srec, K, v, vl, k, lane, t, dl, n, sd, sw, sT, crec);
       const float iW = a.W > 0.f ? 1.0f / a.W : 0.f;
       const float D = a.WT * iW;
+      // colour mode: Cbar and the blended colour C = sum w c / W
+      float Cb[3] = {0.f, 0.f, 0.f}, Cc[3] = {a.WC0 * iW, a.WC1 * iW, a.WC2 * iW};
+      if (color && in.g_color != nullptr) {
+        const float* gc3 = in.g_color + 3 * off;
+#pragma unroll
+        for (int k3 = 0; k3 < 3; ++k3) Cb[k3] = gc3[k3 * P + p];
+      }
       const float gD = in.g_depth ? in.g_depth[off + p] : 0.f;
       const float gA = in.g_alpha ? in.g_alpha[off + p] : 0.f;
       // flow (Sec. 5): p3 = o + v D, X = R_j p3 + t_j, flow = pi(X) - pixel
@@ -359,6 +383,10 @@ __global__ void __launch_bounds__(kAcThreads) backward_ac_kernel(const __grid_co
           float x = Dbar * (t[m] - D);
           if (NORMALS)
             x = fmaf(Nb[0], n[m][0] - N[0], fmaf(Nb[1], n[m][1] - N[1], fmaf(Nb[2], n[m][2] - N[2], x)));
+          if (color) {
+            const float4 c = __ldg(crec + e);
+            x = fmaf(Cb[0], c.x - Cc[0], fmaf(Cb[1], c.y - Cc[1], fmaf(Cb[2], c.z - Cc[2], x)));
+          }
           wbar[m] = x * iW;
           sq[e] = wbar[m] * sw[e];
         }
@@ -445,6 +473,8 @@ __global__ void __launch_bounds__(kAcThreads) backward_ac_kernel(const __grid_co
         rec[2] = make_float4(Nb[0], Nb[0], Nb[1], Nb[1]);
         rec[3] = make_float4(Nb[2], Nb[2], vl[0], vl[0]);
         rec[4] = make_float4(vl[1], vl[1], vl[2], vl[2]);
+        rec[5] = make_float4(Cb[0], Cb[0], Cb[1], Cb[1]);
+        rec[6] = make_float4(Cb[2], Cb[2], 0.f, 0.f);
       }
       __syncwarp();
     }
@@ -464,6 +494,7 @@ __global__ void __launch_bounds__(kAcThreads) backward_ac_kernel(const __grid_co
     const bool active = sg < S;
     AcAcc2 A;
     A.nSd = A.Y0 = A.Y1 = A.Y2 = dup(0.f);
+    A.Cb0 = A.Cb1 = A.Cb2 = dup(0.f);
     A.G00 = A.G10 = A.G11 = A.G20 = A.G21 = A.G22 = dup(0.f);
 #pragma unroll
     for (int i = 0; i < 9; ++i) A.M[i] = dup(0.f);
@@ -477,9 +508,15 @@ __global__ void __launch_bounds__(kAcThreads) backward_ac_kernel(const __grid_co
       const f2 tiny = dup(1e-30f);
       const ulonglong2* rrec = reinterpret_cast<const ulonglong2*>(rays);
       const float4* pv4 = reinterpret_cast<const float4*>(pairv);
+      if (color) {
 #pragma unroll 2
-      for (int r = sg; r < nr; r += S)
-        bwd_pair_ac2<NORMALS>(A, gr, rrec + kAcRayRec * r, pv4[(r * 32 * M + g0) / 2], tiny);
+        for (int r = sg; r < nr; r += S)
+          bwd_pair_ac2<NORMALS, true>(A, gr, rrec + kAcRayRec * r, pv4[(r * 32 * M + g0) / 2], tiny);
+      } else {
+#pragma unroll 2
+        for (int r = sg; r < nr; r += S)
+          bwd_pair_ac2<NORMALS>(A, gr, rrec + kAcRayRec * r, pv4[(r * 32 * M + g0) / 2], tiny);
+      }
     }
     __syncthreads();  // the pair buffer is dead; reuse it for the reduction
 
@@ -487,12 +524,12 @@ __global__ void __launch_bounds__(kAcThreads) backward_ac_kernel(const __grid_co
     float* red = pairv;
     if (active) {
       float* d = red + kAcAccFloats * tid;
-      const f2 vv[19] = {A.nSd, A.Y0, A.Y1, A.Y2, A.G00, A.G10, A.G11, A.G20, A.G21, A.G22,
-                         A.M[0], A.M[1], A.M[2], A.M[3], A.M[4], A.M[5], A.M[6], A.M[7], A.M[8]};
+      const f2 vv[22] = {A.nSd, A.Y0, A.Y1, A.Y2, A.G00, A.G10, A.G11, A.G20, A.G21, A.G22, A.M[0],
+                         A.M[1], A.M[2], A.M[3], A.M[4], A.M[5], A.M[6], A.M[7], A.M[8], A.Cb0, A.Cb1, A.Cb2};
 #pragma unroll
-      for (int i = 0; i < 19; ++i) {
+      for (int i = 0; i < 22; ++i) {
         d[i] = lo(vv[i]);
-        d[19 + i] = hi(vv[i]);
+        d[22 + i] = hi(vv[i]);
       }
     }
     __syncthreads();
@@ -502,13 +539,13 @@ __global__ void __launch_bounds__(kAcThreads) backward_ac_kernel(const __grid_co
 #pragma unroll
     for (int i = 0; i < 12; ++i) pose_g[i] = 0.f;
     for (int gi = tid; gi < K; gi += kAcThreads) {
-      float acc[19];
+      float acc[22];
 #pragma unroll
-      for (int i = 0; i < 19; ++i) acc[i] = 0.f;
+      for (int i = 0; i < 22; ++i) acc[i] = 0.f;
       for (int s2 = 0; s2 < S; ++s2) {
-        const float* d = red + kAcAccFloats * (s2 * GB2 + (gi >> 1)) + 19 * (gi & 1);
+        const float* d = red + kAcAccFloats * (s2 * GB2 + (gi >> 1)) + 22 * (gi & 1);
 #pragma unroll
-        for (int i = 0; i < 19; ++i) acc[i] += d[i];
+        for (int i = 0; i < 22; ++i) acc[i] += d[i];
       }
       const GaussRec g = unpack_rec(srec[kRecFloat4 * gi], srec[kRecFloat4 * gi + 1], srec[kRecFloat4 * gi + 2],
                                     srec[kRecFloat4 * gi + 3]);
@@ -553,14 +590,18 @@ __global__ void __launch_bounds__(kAcThreads) backward_ac_kernel(const __grid_co
 #pragma unroll
         for (int i = 0; i < 6; ++i) atomicAdd(out.gchol + 6 * gg + i, gL[i]);
         atomicAdd(out.gweights + gg, glam);
+        if (color)
+          for (int k3 = 0; k3 < 3; ++k3) atomicAdd(out.gcolors + 3 * gg + k3, acc[19 + k3]);
       } else {
-        float* d = slot + 10 * gi;
+        float* d = slot + NC * gi;
         d[0] = gm[0];
         d[1] = gm[1];
         d[2] = gm[2];
 #pragma unroll
         for (int i = 0; i < 6; ++i) d[3 + i] = gL[i];
         d[9] = glam;
+        if (color)
+          for (int k3 = 0; k3 < 3; ++k3) d[10 + k3] = acc[19 + k3];
       }
     }
 
@@ -576,7 +617,7 @@ __global__ void __launch_bounds__(kAcThreads) backward_ac_kernel(const __grid_co
         float x = 0.f;
         for (int w = 0; w < kAcWarps; ++w) x += pose_ray[w][tid] + (tid < 12 ? pose_gau[w][tid] : 0.f);
         if (slot != nullptr) {
-          slot[10 * V.GB + tid] = x;
+          slot[NC * V.GB + tid] = x;
         } else {
           const int j = tid / 12 - 1;
           const int pidx = j < 0 ? V.pose : (j == 0 ? V.tgt0 : V.tgt1);

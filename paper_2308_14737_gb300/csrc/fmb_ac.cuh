@@ -13,7 +13,7 @@ namespace fmb {
 constexpr int kAcWarps = 4;
 constexpr int kAcThreads = 32 * kAcWarps;
 constexpr int kAcRays = 32;          // rays per work item (forward and backward)
-constexpr int kAcRayRec = 5;         // backward per-ray record, float4s (values duplicated)
+constexpr int kAcRayRec = 7;         // backward per-ray record, float4s (values duplicated)
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr unsigned long long kNoKey = ~0ull;
@@ -104,12 +104,14 @@ __device__ __forceinline__ float warp_allsum(float x) {
 // floats each).  Leaves w_e in sw and T_e in sT, and returns the warp-uniform sums.
 struct AcSums {
   float W, WT, WN0, WN1, WN2, Sd;
+  float WC0 = 0.f, WC1 = 0.f, WC2 = 0.f;  // colour mode: sum w c
 };
 
 template <bool NORMALS, int M>
 __device__ __forceinline__ AcSums ac_render_ray(const float4* __restrict__ rec, int K, const float v[3],
                                                 const float vl[3], const Consts& k, int lane, float (&t)[M],
-                                                float (&dl)[M], float (&n)[M][3], float* sd, float* sw, float* sT) {
+                                                float (&dl)[M], float (&n)[M][3], float* sd, float* sw, float* sT,
+                                                const float4* __restrict__ crec = nullptr) {
   unsigned long long key[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) {
@@ -198,6 +200,12 @@ __device__ __forceinline__ AcSums ac_render_ray(const float4* __restrict__ rec, 
         r.WN1 = fmaf(w, n[m][1], r.WN1);
         r.WN2 = fmaf(w, n[m][2], r.WN2);
       }
+      if (crec != nullptr) {
+        const float4 c = __ldg(crec + e);
+        r.WC0 = fmaf(w, c.x, r.WC0);
+        r.WC1 = fmaf(w, c.y, r.WC1);
+        r.WC2 = fmaf(w, c.z, r.WC2);
+      }
     }
   }
   r.W = warp_allsum(r.W);
@@ -206,6 +214,11 @@ __device__ __forceinline__ AcSums ac_render_ray(const float4* __restrict__ rec, 
     r.WN0 = warp_allsum(r.WN0);
     r.WN1 = warp_allsum(r.WN1);
     r.WN2 = warp_allsum(r.WN2);
+  }
+  if (crec != nullptr) {
+    r.WC0 = warp_allsum(r.WC0);
+    r.WC1 = warp_allsum(r.WC1);
+    r.WC2 = warp_allsum(r.WC2);
   }
   return r;
 }

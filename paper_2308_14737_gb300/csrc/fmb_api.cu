@@ -113,6 +113,8 @@ fmb_status validate_scene(const fmb_params* p, int n_objects, const long long* o
   if (p->n_flow < 0 || p->n_flow > 2) return fail(FMB_ERR_INVALID_ARG, "n_flow must be 0, 1 or 2");
   if (p->use_persistent != 0 && p->use_persistent != 1) return fail(FMB_ERR_INVALID_ARG, "use_persistent must be 0 or 1");
   if (p->store_pairs != 0 && p->store_pairs != 1) return fail(FMB_ERR_INVALID_ARG, "store_pairs must be 0 or 1");
+  if (p->colors != 0 && p->colors != 1) return fail(FMB_ERR_INVALID_ARG, "colors must be 0 or 1");
+  if (p->colors && p->store_pairs) return fail(FMB_ERR_INVALID_ARG, "colors is not available with store_pairs");
   if (p->store_pairs && (p->fwd_rays_per_thread == 1 || p->fwd_rays_per_thread == 4))
     return fail(FMB_ERR_INVALID_ARG, "store_pairs needs fwd_rays_per_thread 0 or 2");
   if (p->fwd_rays_per_thread != 0 && p->fwd_rays_per_thread != 1 && p->fwd_rays_per_thread != 2 &&
@@ -240,7 +242,7 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
       db.n_gblocks = bk.n_gb;
       db.GB = bk.GB;
       db.S = bk.S;
-      db.slot_floats = 10 * bk.GB + 12 * (1 + n_flow);
+      db.slot_floats = (p->colors ? 13 : 10) * bk.GB + 12 * (1 + n_flow);
       db.part_off = part;
       part += static_cast<long long>(db.n_tiles) * db.n_gblocks * db.slot_floats;
       ctas_b += static_cast<long long>(db.n_tiles) * db.n_gblocks;
@@ -263,10 +265,17 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
   return pl;
 }
 
-// Workspace: header (status word, work counters) | records | deterministic
-// partials (if deterministic) | per-pair t, e2, delta arrays (if store_pairs).
+// Workspace: header (status word, work counters) | records | colour records (if
+// colors) | deterministic partials (if deterministic) | per-pair t, e2, delta
+// arrays (if store_pairs).
+size_t crec_offset(const Plan& pl) {
+  return kHeaderBytes + align256(static_cast<size_t>(pl.n_records) * 16 * fmb::kRecFloat4);
+}
+size_t partials_offset(const fmb_params* p, const Plan& pl) {
+  return crec_offset(pl) + (p->colors ? align256(static_cast<size_t>(pl.n_records) * 16) : 0);
+}
 size_t pairs_offset(const fmb_params* p, const Plan& pl) {
-  size_t bytes = kHeaderBytes + align256(static_cast<size_t>(pl.n_records) * 16 * fmb::kRecFloat4);
+  size_t bytes = partials_offset(p, pl);
   if (p->deterministic) bytes += align256(static_cast<size_t>(pl.part_floats) * sizeof(float));
   return bytes;
 }
@@ -334,10 +343,10 @@ size_t fmb_workspace_bytes(const fmb_params* params, int n_objects, const long l
 }
 
 fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
-                              const float* means, const float* chol, const float* weights, int n_poses,
-                              const float* poses, int n_views, const fmb_view* h_views, float* depth,
-                              float* alpha, float* normal, float* flow, float* saved, void* workspace,
-                              size_t workspace_bytes, fmb_stream_t stream) {
+                              const float* means, const float* chol, const float* weights, const float* colors,
+                              int n_poses, const float* poses, int n_views, const fmb_view* h_views,
+                              float* depth, float* alpha, float* normal, float* flow, float* color, float* saved,
+                              void* workspace, size_t workspace_bytes, fmb_stream_t stream) {
   try {
     g_err.clear();
     fmb_status st = validate_scene(params, n_objects, h_obj_offsets, n_views, h_views);
@@ -347,6 +356,8 @@ fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const lon
     if (!depth || !alpha || !saved) return fail(FMB_ERR_INVALID_ARG, "depth, alpha and saved are required");
     if (params->want_normals && !normal) return fail(FMB_ERR_INVALID_ARG, "normal is NULL but want_normals is set");
     if (params->n_flow > 0 && !flow) return fail(FMB_ERR_INVALID_ARG, "flow is NULL but n_flow > 0");
+    if (params->colors && (!colors || !color))
+      return fail(FMB_ERR_INVALID_ARG, "colors and color are required when params->colors is set");
     st = validate_views(n_objects, n_poses, n_views, h_views);
     if (st != FMB_OK) return st;
     Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views);
@@ -356,7 +367,12 @@ fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const lon
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int* status = static_cast<int*>(workspace);
     float4* records = reinterpret_cast<float4*>(static_cast<char*>(workspace) + kHeaderBytes);
-    const fmb::Scene sc{means, chol, weights, poses};
+    fmb::Scene sc{means, chol, weights, poses};
+    if (params->colors) {
+      sc.colors = colors;
+      sc.crec = reinterpret_cast<float4*>(static_cast<char*>(workspace) + crec_offset(pl));
+    }
+    if (!params->colors) color = nullptr;
     const fmb::Consts c = make_consts(params);
     float* pairs = params->store_pairs
                        ? reinterpret_cast<float*>(static_cast<char*>(workspace) + pairs_offset(params, pl))
@@ -369,13 +385,15 @@ fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const lon
       const fmb::Batch& b = pl.fwd[bi];
       e = fmb::launch_prologue(b, sc, c, records, pl.maxK, bi == 0 ? status : nullptr, counter, s);
       if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
+      fmb::FwdOut fo{depth, alpha, normal, flow, saved, pairs, pl.pair_stride};
+      fo.color = color;
       if (params->variant == 1) {
-        const fmb::FwdOut fo{depth, alpha, normal, flow, saved, nullptr, 0};
+        fo.pairs = nullptr;
         e = fmb::launch_forward_ac(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.maxK, fo, status,
                                    counter, s);
       } else {
-        e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, pl.maxK,
-                                depth, alpha, normal, flow, saved, pairs, pl.pair_stride, status, counter, s);
+        e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, pl.maxK, fo,
+                                status, counter, s);
       }
       if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     }
@@ -388,12 +406,13 @@ fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const lon
 }
 
 fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
-                               const float* means, const float* chol, const float* weights, int n_poses,
-                               const float* poses, int n_views, const fmb_view* h_views, const float* depth,
-                               const float* normal, const float* saved, const float* g_depth,
-                               const float* g_alpha, const float* g_normal, const float* g_flow,
-                               float* grad_means, float* grad_chol, float* grad_weights, float* grad_poses,
-                               void* workspace, size_t workspace_bytes, fmb_stream_t stream) {
+                               const float* means, const float* chol, const float* weights, const float* colors,
+                               int n_poses, const float* poses, int n_views, const fmb_view* h_views,
+                               const float* depth, const float* normal, const float* color, const float* saved,
+                               const float* g_depth, const float* g_alpha, const float* g_normal,
+                               const float* g_flow, const float* g_color, float* grad_means, float* grad_chol,
+                               float* grad_weights, float* grad_colors, float* grad_poses, void* workspace,
+                               size_t workspace_bytes, fmb_stream_t stream) {
   try {
     g_err.clear();
     fmb_status st = validate_scene(params, n_objects, h_obj_offsets, n_views, h_views);
@@ -405,6 +424,8 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
       return fail(FMB_ERR_INVALID_ARG, "normal (forward output) is required with g_normal");
     if (!grad_means || !grad_chol || !grad_weights)
       return fail(FMB_ERR_INVALID_ARG, "grad_means, grad_chol and grad_weights are required");
+    if (params->colors && (!colors || !color || !grad_colors))
+      return fail(FMB_ERR_INVALID_ARG, "colors, color and grad_colors are required when params->colors is set");
     st = validate_views(n_objects, n_poses, n_views, h_views);
     if (st != FMB_OK) return st;
     Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views);
@@ -416,9 +437,12 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
     char* base = static_cast<char*>(workspace);
     float4* records = reinterpret_cast<float4*>(base + kHeaderBytes);
     float* partials = nullptr;
-    if (params->deterministic)
-      partials = reinterpret_cast<float*>(base + kHeaderBytes + align256(static_cast<size_t>(pl.n_records) * 16 * fmb::kRecFloat4));
-    const fmb::Scene sc{means, chol, weights, poses};
+    if (params->deterministic) partials = reinterpret_cast<float*>(base + partials_offset(params, pl));
+    fmb::Scene sc{means, chol, weights, poses};
+    if (params->colors) {
+      sc.colors = colors;
+      sc.crec = reinterpret_cast<float4*>(base + crec_offset(pl));
+    }
     const fmb::Consts c = make_consts(params);
     const bool normals = params->want_normals != 0;
     const float* pairs =
@@ -426,6 +450,11 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
     fmb::BwdIn in{depth,   normals ? normal : nullptr, saved, g_depth, g_alpha, normals ? g_normal : nullptr,
                   params->n_flow > 0 ? g_flow : nullptr, pairs, pl.pair_stride};
     fmb::BwdOut out{grad_means, grad_chol, grad_weights, grad_poses, partials};
+    if (params->colors) {
+      in.color = color;
+      in.g_color = g_color;
+      out.gcolors = grad_colors;
+    }
 
     fmb::ZeroJob zj{};
     zj.ptr[0] = reinterpret_cast<float*>(status);
@@ -438,6 +467,8 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
     zj.n[3] = pl.n_gauss;
     zj.ptr[4] = grad_poses;
     zj.n[4] = grad_poses ? 12ll * n_poses : 0;
+    zj.ptr[5] = params->colors ? grad_colors : nullptr;
+    zj.n[5] = params->colors ? 3 * pl.n_gauss : 0;
     cudaError_t e = fmb::launch_zero(zj, s);
     if (e != cudaSuccess) return cuda_fail(e, "zeroing launch");
     int* counter = params->use_persistent ? reinterpret_cast<int*>(base + kBwdCounterOffset) : nullptr;
@@ -616,10 +647,10 @@ fmb_status static_scratch_address(void** out) {
 
 extern "C" fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n_objects,
                                                  const long long* h_obj_offsets, const float* means,
-                                                 const float* chol, const float* weights, int n_poses,
-                                                 const float* poses, int n_views, const fmb_view* h_views,
-                                                 float* depth, float* alpha, float* normal, float* flow,
-                                                 float* saved, fmb_stream_t stream) {
+                                                 const float* chol, const float* weights, const float* colors,
+                                                 int n_poses, const float* poses, int n_views,
+                                                 const fmb_view* h_views, float* depth, float* alpha, float* normal,
+                                                 float* flow, float* color, float* saved, fmb_stream_t stream) {
   try {
     g_err.clear();
     fmb_status st = validate_scene(params, n_objects, h_obj_offsets, n_views, h_views);
@@ -634,11 +665,13 @@ extern "C" fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n
     if (params->store_pairs)
       return fail(FMB_ERR_INVALID_ARG, "store_pairs needs a workspace (use fmb_render_forward)");
     Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views);
-    const size_t need = kHeaderBytes + align256(static_cast<size_t>(pl.n_records) * 16 * fmb::kRecFloat4);
+    if (params->colors && (!colors || !color))
+      return fail(FMB_ERR_INVALID_ARG, "colors and color are required when params->colors is set");
+    const size_t need = partials_offset(params, pl);
     if (need > kStaticScratchBytes)
       return fail(FMB_ERR_WORKSPACE, "batch needs " + std::to_string(need) + " bytes of scratch; the static scratch " +
                                          "holds " + std::to_string(kStaticScratchBytes) +
-                                         " (64 bytes per view and Gaussian, plus 256)");
+                                         " (64 bytes per view and Gaussian, 80 with colours, plus 256)");
     void* ws = nullptr;
     st = static_scratch_address(&ws);
     if (st != FMB_OK) return st;
@@ -646,7 +679,12 @@ extern "C" fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int* status = static_cast<int*>(ws);
     float4* records = reinterpret_cast<float4*>(static_cast<char*>(ws) + kHeaderBytes);
-    const fmb::Scene sc{means, chol, weights, poses};
+    fmb::Scene sc{means, chol, weights, poses};
+    if (params->colors) {
+      sc.colors = colors;
+      sc.crec = reinterpret_cast<float4*>(static_cast<char*>(ws) + crec_offset(pl));
+    }
+    if (!params->colors) color = nullptr;
     const fmb::Consts c = make_consts(params);
     float* pairs = nullptr;  // stored-intermediate mode is rejected above
     cudaError_t e = cudaSuccess;
@@ -657,13 +695,15 @@ extern "C" fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n
       const fmb::Batch& b = pl.fwd[bi];
       e = fmb::launch_prologue(b, sc, c, records, pl.maxK, bi == 0 ? status : nullptr, counter, s);
       if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
+      fmb::FwdOut fo{depth, alpha, normal, flow, saved, pairs, pl.pair_stride};
+      fo.color = color;
       if (params->variant == 1) {
-        const fmb::FwdOut fo{depth, alpha, normal, flow, saved, nullptr, 0};
+        fo.pairs = nullptr;
         e = fmb::launch_forward_ac(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.maxK, fo, status,
                                    counter, s);
       } else {
-        e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, pl.maxK,
-                                depth, alpha, normal, flow, saved, pairs, pl.pair_stride, status, counter, s);
+        e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, pl.maxK, fo,
+                                status, counter, s);
       }
       if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     }

@@ -41,6 +41,11 @@ constexpr int kBwdMaxThreads = 160;
 constexpr int kBwdMinBlocks = FMB_BWD_MIN_BLOCKS;
 constexpr int kBwdUnroll = FMB_BWD_UNROLL;  // resident CTAs per SM the register budget targets
 constexpr int kAccFloats = 38;  // 19 packed accumulators per thread in the reduction
+// Colour mode adds three (sum of what x Cbar per channel).
+template <bool COLOR>
+__host__ __device__ constexpr int acc_floats() {
+  return COLOR ? 44 : kAccFloats;
+}
 
 // Per-thread gradient sums of the thread's two Gaussians (one per lane).
 struct BwdAcc2 {
@@ -48,19 +53,35 @@ struct BwdAcc2 {
   f2 Y0, Y1, Y2;          // sum y   (= -sum bbar)
   f2 G00, G10, G11, G20, G21, G22;  // sum gbar u^T (lower)
   f2 M[9];                // sum v abar^T (row-major)
+  f2 Cb0, Cb1, Cb2;       // colour mode: sum what Cbar
 };
 
 // Shared-memory record of one ray, 7 x 16 bytes, every value duplicated:
 //   [v0 v0 v1 v1 | v2 v2 -lse2 -lse2 | Dbar Dbar -KA -KA | -C -C Nb0 Nb0 |
 //    Nb1 Nb1 Nb2 Nb2 | vl0 vl0 vl1 vl1 | vl2 vl2 0 0]
+// Colour mode: 8 x 16 bytes, the last two [vl2 vl2 Cb0 Cb0 | Cb1 Cb1 Cb2 Cb2].
 constexpr int kRayRec2 = 7;
+template <bool COLOR>
+__host__ __device__ constexpr int ray_rec2() {
+  return COLOR ? 8 : kRayRec2;
+}
 
 // STORED: the pair's t, log2 weight and density come from the forward (`st`,
 // `se`, `sd`) instead of being recomputed.
-template <bool NORMALS, bool STORED>
+template <bool NORMALS, bool STORED, bool COLOR = false>
 __device__ __forceinline__ void bwd_pair2(BwdAcc2& A, const GaussRec2& gr, const ulonglong2* __restrict__ rr, f2 K2,
-                                          f2 K3, f2 B1, f2 nB1, f2 nB2E, f2 tiny, f2 st, f2 se, f2 sd) {
+                                          f2 K3, f2 B1, f2 nB1, f2 nB2E, f2 tiny, f2 st, f2 se, f2 sd,
+                                          f2 c0 = f2{}, f2 c1 = f2{}, f2 c2 = f2{}) {
   const ulonglong2 q0 = rr[0], q1 = rr[1], q2 = rr[2], q3 = rr[3], q4 = rr[4], q5 = rr[5], q6 = rr[6];
+  // colour mode: Cbar . c_i joins the weight's gradient (Eq. 3 with colours)
+  f2 cc = dup(0.f), Cb0 = dup(0.f), Cb1 = dup(0.f), Cb2 = dup(0.f);
+  if (COLOR) {
+    const ulonglong2 q7 = rr[7];
+    Cb0 = as_f2(q6.y);
+    Cb1 = as_f2(q7.x);
+    Cb2 = as_f2(q7.y);
+    cc = fma2(Cb2, c2, fma2(Cb1, c1, mul2(Cb0, c0)));
+  }
   const f2 v0 = as_f2(q0.x), v1 = as_f2(q0.y), v2 = as_f2(q1.x), nlse = as_f2(q1.y);
   const f2 Dbar = as_f2(q2.x), nKA = as_f2(q2.y), nC = as_f2(q3.x);
   PairGeom2 G;
@@ -86,7 +107,7 @@ __device__ __forceinline__ void bwd_pair2(BwdAcc2& A, const GaussRec2& gr, const
     const f2 rs = rsqrt_2(gg);
     const f2 n0 = mul2(g0, rs), n1 = mul2(g1, rs), n2 = mul2(g2, rs);
     const f2 nN = fma2(n2, Nb2, fma2(n1, Nb1, mul2(n0, Nb0)));
-    ebar = mul2(what, add2(fma2(Dbar, t, nC), nN));
+    ebar = mul2(what, COLOR ? add2(add2(fma2(Dbar, t, nC), nN), cc) : add2(fma2(Dbar, t, nC), nN));
     const f2 sc = mul2(what, rs);
     const f2 sN = mul2(sc, nN);
     const f2 nsN = pk(-lo(sN), -hi(sN));
@@ -98,7 +119,7 @@ __device__ __forceinline__ void bwd_pair2(BwdAcc2& A, const GaussRec2& gr, const
     ub2 = mul2(gr.L[5], gb2);
     tbar = fma2(ub2, G.a2, fma2(ub1, G.a1, fma2(ub0, G.a0, fma2(Dbar, what, mul2(nB2E, ebar)))));
   } else {
-    ebar = mul2(what, fma2(Dbar, t, nC));
+    ebar = mul2(what, COLOR ? add2(fma2(Dbar, t, nC), cc) : fma2(Dbar, t, nC));
     ub0 = ub1 = ub2 = gb0 = gb1 = gb2 = dup(0.f);
     tbar = fma2(Dbar, what, mul2(nB2E, ebar));
   }
@@ -134,6 +155,11 @@ __device__ __forceinline__ void bwd_pair2(BwdAcc2& A, const GaussRec2& gr, const
   A.M[6] = fma2(v2, ab0, A.M[6]);
   A.M[7] = fma2(v2, ab1, A.M[7]);
   A.M[8] = fma2(v2, ab2, A.M[8]);
+  if (COLOR) {
+    A.Cb0 = fma2(what, Cb0, A.Cb0);
+    A.Cb1 = fma2(what, Cb1, A.Cb1);
+    A.Cb2 = fma2(what, Cb2, A.Cb2);
+  }
 }
 
 __device__ __forceinline__ float warp_sum(float x) {
@@ -142,7 +168,7 @@ __device__ __forceinline__ float warp_sum(float x) {
   return x;
 }
 
-template <bool NORMALS, int NFLOW, bool STORED>
+template <bool NORMALS, int NFLOW, bool STORED, bool COLOR = false>
 __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
     backward_kernel(const __grid_constant__ Batch batch, Scene s, Consts k, const float4* __restrict__ records,
                     BwdIn in, BwdOut out, int ray_tile, int* counter) {
@@ -269,17 +295,29 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
           Nb2 = fmaf(-sdot, nf[2], nfb[2]) * iN;
         }
       }
-      // Nbar is orthogonal to N, so the softmax centring term is Dbar * D alone.
-      const float C = Dbar * D;
+      // Nbar is orthogonal to N, so the softmax centring term is Dbar * D alone (plus
+      // Cbar . C, the blended colour's, in colour mode).
+      float C = Dbar * D;
+      float Cb[3] = {0.f, 0.f, 0.f};
+      if (COLOR && in.g_color != nullptr) {
+        const float* gc3 = in.g_color + 3 * off;
+        const float* cp3 = in.color + 3 * off;
+#pragma unroll
+        for (int k3 = 0; k3 < 3; ++k3) {
+          Cb[k3] = gc3[k3 * P + p];
+          C = fmaf(Cb[k3], cp3[k3 * P + p], C);
+        }
+      }
       const float KA = gA * expf(-Sd);
-      float4* rr = bsm + kRayRec2 * r;
+      float4* rr = bsm + ray_rec2<COLOR>() * r;
       rr[0] = make_float4(v[0], v[0], v[1], v[1]);
       rr[1] = make_float4(v[2], v[2], -lse2, -lse2);
       rr[2] = make_float4(Dbar, Dbar, -KA, -KA);
       rr[3] = make_float4(-C, -C, Nb0, Nb0);
       rr[4] = make_float4(Nb1, Nb1, Nb2, Nb2);
       rr[5] = make_float4(vl[0], vl[0], vl[1], vl[1]);
-      rr[6] = make_float4(vl[2], vl[2], 0.f, 0.f);
+      rr[6] = make_float4(vl[2], vl[2], Cb[0], Cb[0]);
+      if (COLOR) rr[7] = make_float4(Cb[1], Cb[1], Cb[2], Cb[2]);
     }
     // Reduce the per-ray pose terms now, so that they hold no registers in the loop.
     if (want_pose) {
@@ -305,6 +343,7 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
   A.G00 = A.G10 = A.G11 = A.G20 = A.G21 = A.G22 = dup(0.f);
 #pragma unroll
   for (int i = 0; i < 9; ++i) A.M[i] = dup(0.f);
+  A.Cb0 = A.Cb1 = A.Cb2 = dup(0.f);
   GaussRec ga{}, gbr{};
   if (active) {
     const float4* rec = records + kRecFloat4 * (V.rec_off + g0);
@@ -330,6 +369,15 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
         bwd_pair2<NORMALS, true>(A, gr, rays + kRayRec2 * r, K2v, K3v, B1v, nB1v, nB2E, tiny, as_f2(__ldg(q)),
                                  as_f2(__ldg(q + st2)), as_f2(__ldg(q + 2 * st2)));
       }
+    } else if (COLOR) {
+      // the two Gaussians' colours, one per lane
+      const float4 ca = __ldg(s.crec + V.rec_off + g0), cb = has1 ? __ldg(s.crec + V.rec_off + g0 + 1) : ca;
+      const f2 c0 = pk(ca.x, cb.x), c1 = pk(ca.y, cb.y), c2 = pk(ca.z, cb.z);
+      const f2 z = dup(0.f);
+#pragma unroll kBwdUnroll
+      for (int r = sg; r < nr; r += S)
+        bwd_pair2<NORMALS, false, true>(A, gr, rays + ray_rec2<true>() * r, K2v, K3v, B1v, nB1v, nB2E, tiny, z, z, z,
+                                        c0, c1, c2);
     } else {
       const f2 z = dup(0.f);
 #pragma unroll kBwdUnroll
@@ -340,15 +388,18 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
   __syncthreads();  // ray records are dead; the shared memory is reused below
 
   // ---------------- phase 3: combine ray subgroups, finalise per Gaussian
+  constexpr int NV = COLOR ? 22 : 19;  // sums per Gaussian
+  constexpr int ACC = acc_floats<COLOR>();
+  constexpr int NC = COLOR ? 13 : 10;  // gradient values per Gaussian in a partial slot
   float* red = reinterpret_cast<float*>(bsm);
   if (sg < S) {
-    float* d = red + kAccFloats * tid;
-    const f2 v[19] = {A.nSd, A.Y0, A.Y1, A.Y2, A.G00, A.G10, A.G11, A.G20, A.G21, A.G22,
-                      A.M[0], A.M[1], A.M[2], A.M[3], A.M[4], A.M[5], A.M[6], A.M[7], A.M[8]};
+    float* d = red + ACC * tid;
+    const f2 v[22] = {A.nSd, A.Y0, A.Y1, A.Y2, A.G00, A.G10, A.G11, A.G20, A.G21, A.G22, A.M[0],
+                      A.M[1], A.M[2], A.M[3], A.M[4], A.M[5], A.M[6], A.M[7], A.M[8], A.Cb0, A.Cb1, A.Cb2};
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
+    for (int i = 0; i < NV; ++i) {
       d[i] = lo(v[i]);
-      d[19 + i] = hi(v[i]);
+      d[NV + i] = hi(v[i]);
     }
   }
   __syncthreads();
@@ -368,13 +419,13 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
       const int gi = 2 * gl2 + lane2;  // Gaussian index within the block
       if (gi >= GB) break;
       const int g = gb * GB + gi;
-      float acc[19];
+      float acc[NV];
 #pragma unroll
-      for (int i = 0; i < 19; ++i) acc[i] = 0.f;
+      for (int i = 0; i < NV; ++i) acc[i] = 0.f;
       for (int s2 = 0; s2 < S; ++s2) {
-        const float* d = red + kAccFloats * (s2 * GB2 + gl2) + 19 * lane2;
+        const float* d = red + ACC * (s2 * GB2 + gl2) + NV * lane2;
 #pragma unroll
-        for (int i = 0; i < 19; ++i) acc[i] += d[i];
+        for (int i = 0; i < NV; ++i) acc[i] += d[i];
       }
       float gm[3] = {0, 0, 0}, gL[6] = {0, 0, 0, 0, 0, 0}, glam = 0.f;
       if (g < V.K && active) {
@@ -421,14 +472,22 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
 #pragma unroll
           for (int i = 0; i < 6; ++i) atomicAdd(out.gchol + 6 * gg + i, gL[i]);
           atomicAdd(out.gweights + gg, glam);
+          if (COLOR) {
+#pragma unroll
+            for (int k3 = 0; k3 < 3; ++k3) atomicAdd(out.gcolors + 3 * gg + k3, acc[19 + k3]);
+          }
         }
       }
       if (slot != nullptr) {
-        float* d = slot + 10 * gi;
+        float* d = slot + NC * gi;
         d[0] = gm[0]; d[1] = gm[1]; d[2] = gm[2];
 #pragma unroll
         for (int i = 0; i < 6; ++i) d[3 + i] = gL[i];
         d[9] = glam;
+        if (COLOR) {
+#pragma unroll
+          for (int k3 = 0; k3 < 3; ++k3) d[10 + k3] = (g < V.K && active) ? acc[19 + k3] : 0.f;
+        }
       }
     }
   }
@@ -446,7 +505,7 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
       const int nw = (T + 31) / 32;
       for (int w = 0; w < nw; ++w) x += pose_ray[w][tid] + (tid < 12 ? pose_gau[w][tid] : 0.f);
       if (slot != nullptr) {
-        slot[10 * GB + tid] = x;
+        slot[NC * GB + tid] = x;
       } else {
         const int j = tid / 12 - 1;
         const int pidx = j < 0 ? V.pose : (j == 0 ? V.tgt0 : V.tgt1);
@@ -457,17 +516,17 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
   }  // item loop
 }
 
-static int bwd_smem_bytes(int ray_tile, int threads) {
-  return std::max(ray_tile * kRayRec2 * static_cast<int>(sizeof(float4)),
-                  threads * kAccFloats * static_cast<int>(sizeof(float)));
+static int bwd_smem_bytes(int ray_tile, int threads, bool color = false) {
+  return std::max(ray_tile * (color ? ray_rec2<true>() : kRayRec2) * static_cast<int>(sizeof(float4)),
+                  threads * (color ? acc_floats<true>() : kAccFloats) * static_cast<int>(sizeof(float)));
 }
 
-template <bool NORMALS, int NFLOW, bool STORED = false>
+template <bool NORMALS, int NFLOW, bool STORED = false, bool COLOR = false>
 static cudaError_t prepare_bwd_t(int smem) {
   // Dynamic plus static shared memory above the 48 KB default needs the opt-in.
   if (smem + static_cast<int>(sizeof(float) * (kBwdMaxThreads / 32) * 48) > 48 * 1024)
-    return cudaFuncSetAttribute(backward_kernel<NORMALS, NFLOW, STORED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem);
+    return cudaFuncSetAttribute(backward_kernel<NORMALS, NFLOW, STORED, COLOR>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return cudaSuccess;
 }
 
@@ -482,12 +541,12 @@ static int bwd_ctas_per_sm_t(int ray_tile, int threads) {
   return n > 0 ? n : 1;
 }
 
-template <bool NORMALS, int NFLOW, bool STORED>
+template <bool NORMALS, int NFLOW, bool STORED, bool COLOR = false>
 static cudaError_t launch_bwd_s(const Batch& b, const Scene& s, const Consts& c, const float4* records,
                                 int ray_tile, int threads, const BwdIn& in, const BwdOut& out, int* counter,
                                 cudaStream_t st) {
-  const int smem = bwd_smem_bytes(ray_tile, threads);
-  cudaError_t e = prepare_bwd_t<NORMALS, NFLOW, STORED>(smem);
+  const int smem = bwd_smem_bytes(ray_tile, threads, COLOR);
+  cudaError_t e = prepare_bwd_t<NORMALS, NFLOW, STORED, COLOR>(smem);
   if (e != cudaSuccess) return e;
   int grid = b.n_items;
   if (counter) {
@@ -496,7 +555,8 @@ static cudaError_t launch_bwd_s(const Batch& b, const Scene& s, const Consts& c,
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     grid = std::min(b.n_items, std::max(1, sms) * bwd_ctas_per_sm_t<NORMALS, NFLOW>(ray_tile, threads));
   }
-  backward_kernel<NORMALS, NFLOW, STORED><<<grid, threads, smem, st>>>(b, s, c, records, in, out, ray_tile, counter);
+  backward_kernel<NORMALS, NFLOW, STORED, COLOR><<<grid, threads, smem, st>>>(b, s, c, records, in, out, ray_tile,
+                                                                               counter);
   return cudaGetLastError();
 }
 
@@ -506,6 +566,8 @@ static cudaError_t launch_bwd_t(const Batch& b, const Scene& s, const Consts& c,
                                 cudaStream_t st) {
   if (in.pairs != nullptr)
     return launch_bwd_s<NORMALS, NFLOW, true>(b, s, c, records, ray_tile, threads, in, out, counter, st);
+  if (out.gcolors != nullptr)
+    return launch_bwd_s<NORMALS, NFLOW, false, true>(b, s, c, records, ray_tile, threads, in, out, counter, st);
   return launch_bwd_s<NORMALS, NFLOW, false>(b, s, c, records, ray_tile, threads, in, out, counter, st);
 }
 
@@ -554,14 +616,16 @@ __device__ __forceinline__ float warp_sum_fixed(float x) {
   return x;
 }
 
-// Gaussian gradients: warp w handles (Gaussian g, component comp), w = g * 10 + comp.
+// Gaussian gradients: warp w handles (Gaussian g, component comp), w = g * nc + comp
+// (nc = 10, or 13 with colours: means 3, chol 6, weight 1, colour 3).
 __global__ void reduce_gauss_kernel(const __grid_constant__ Batch batch, const float* __restrict__ partials,
-                                    float* gmeans, float* gchol, float* gweights, long long n_gauss) {
+                                    float* gmeans, float* gchol, float* gweights, float* gcolors, long long n_gauss,
+                                    int nc) {
   const long long w = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= n_gauss * 10) return;  // whole warps exit together
-  const long long g = w / 10;
-  const int comp = static_cast<int>(w - g * 10);
+  if (w >= n_gauss * nc) return;  // whole warps exit together
+  const long long g = w / nc;
+  const int comp = static_cast<int>(w - g * nc);
   float acc = 0.f;
   bool hit = false;
   for (int v = 0; v < batch.n_views; ++v) {
@@ -571,7 +635,7 @@ __global__ void reduce_gauss_kernel(const __grid_constant__ Batch batch, const f
     const int gi = static_cast<int>(g - V.gauss_off);
     const int gbk = gi / V.GB, gl = gi - gbk * V.GB;
     for (int t = lane; t < V.n_tiles; t += 32)
-      acc += partials[V.part_off + static_cast<long long>(t * V.n_gblocks + gbk) * V.slot_floats + 10 * gl + comp];
+      acc += partials[V.part_off + static_cast<long long>(t * V.n_gblocks + gbk) * V.slot_floats + nc * gl + comp];
   }
   acc = warp_sum_fixed(acc);
   if (!hit || lane != 0) return;
@@ -579,13 +643,15 @@ __global__ void reduce_gauss_kernel(const __grid_constant__ Batch batch, const f
     gmeans[3 * g + comp] += acc;
   else if (comp < 9)
     gchol[6 * g + comp - 3] += acc;
-  else
+  else if (comp == 9)
     gweights[g] += acc;
+  else
+    gcolors[3 * g + comp - 10] += acc;
 }
 
 // Pose gradients: warp w handles (pose p, component comp), w = p * 12 + comp.
 __global__ void reduce_pose_kernel(const __grid_constant__ Batch batch, const float* __restrict__ partials,
-                                   float* gposes, int n_poses, int n_flow) {
+                                   float* gposes, int n_poses, int n_flow, int nc) {
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= n_poses * 12) return;
@@ -599,7 +665,7 @@ __global__ void reduce_pose_kernel(const __grid_constant__ Batch batch, const fl
       const int part = 12 * (j + 1) + comp;
       const int nslots = V.n_tiles * V.n_gblocks;
       for (int sl = lane; sl < nslots; sl += 32)
-        acc += partials[V.part_off + static_cast<long long>(sl) * V.slot_floats + 10 * V.GB + part];
+        acc += partials[V.part_off + static_cast<long long>(sl) * V.slot_floats + nc * V.GB + part];
     }
   }
   acc = warp_sum_fixed(acc);
@@ -608,12 +674,14 @@ __global__ void reduce_pose_kernel(const __grid_constant__ Batch batch, const fl
 
 cudaError_t launch_backward_reduce(const Batch& b, int n_flow, long long n_gauss, int n_poses, const BwdOut& out,
                                    cudaStream_t st) {
-  const long long warps = n_gauss * 10;
+  const int nc = out.gcolors != nullptr ? 13 : 10;
+  const long long warps = n_gauss * nc;
   reduce_gauss_kernel<<<static_cast<unsigned>((warps * 32 + 255) / 256), 256, 0, st>>>(
-      b, out.partials, out.gmeans, out.gchol, out.gweights, n_gauss);
+      b, out.partials, out.gmeans, out.gchol, out.gweights, out.gcolors, n_gauss, nc);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || out.gposes == nullptr) return e;
-  reduce_pose_kernel<<<(n_poses * 12 * 32 + 255) / 256, 256, 0, st>>>(b, out.partials, out.gposes, n_poses, n_flow);
+  reduce_pose_kernel<<<(n_poses * 12 * 32 + 255) / 256, 256, 0, st>>>(b, out.partials, out.gposes, n_poses, n_flow,
+                                                                       nc);
   return cudaGetLastError();
 }
 

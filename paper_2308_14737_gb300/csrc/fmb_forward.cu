@@ -58,6 +58,10 @@ __global__ void __launch_bounds__(128) prologue_kernel(const __grid_constant__ B
   r[1] = make_float4(L21, L22, b0, b1);
   r[2] = make_float4(b2, mh[0], mh[1], mh[2]);
   r[3] = make_float4(nb0, nb1, nb2, l2);
+  if (s.crec != nullptr) {
+    const float* c = s.colors + 3 * g;
+    s.crec[V.rec_off + i] = make_float4(c[0], c[1], c[2], 0.f);
+  }
   (void)k;
 }
 
@@ -114,6 +118,7 @@ __device__ __forceinline__ void fwd_pair(RayAcc& A, const GaussRec& g, const Con
 struct RayAcc2 {
   f2 v0, v1, v2, vl0, vl1, vl2;
   f2 m, Sw, Swt, Sd, N0, N1, N2;
+  f2 C0, C1, C2;  // colour mode: sum w c
 };
 
 // Per-pair values the stored-intermediate mode keeps for the backward: the hit
@@ -122,8 +127,9 @@ struct PairOut2 {
   f2 t, e2, delta;
 };
 
-template <bool NORMALS>
-__device__ __forceinline__ PairOut2 fwd_pair2(RayAcc2& A, const GaussRec2& g, f2 K2, f2 K3, f2 beta1, f2 tiny) {
+template <bool NORMALS, bool COLOR = false>
+__device__ __forceinline__ PairOut2 fwd_pair2(RayAcc2& A, const GaussRec2& g, f2 K2, f2 K3, f2 beta1, f2 tiny,
+                                              float4 col = float4{}) {
   const PairGeom2 G = pair_geom2(g, A.v0, A.v1, A.v2, A.vl0, A.vl1, A.vl2);
   const f2 x = fma2(G.q, K3, g.l2);  // log2(delta)
   const f2 delta = ex2_2(x);
@@ -150,12 +156,22 @@ __device__ __forceinline__ PairOut2 fwd_pair2(RayAcc2& A, const GaussRec2& g, f2
       A.N1 = mul2(A.N1, sc);
       A.N2 = mul2(A.N2, sc);
     }
+    if (COLOR) {
+      A.C0 = mul2(A.C0, sc);
+      A.C1 = mul2(A.C1, sc);
+      A.C2 = mul2(A.C2, sc);
+    }
     A.m = pk(ml, mh);
     d = pk(dl, dh);
   }
   const f2 w = ex2_2(d);
   A.Sw = add2(A.Sw, w);
   A.Swt = fma2(w, G.t, A.Swt);
+  if (COLOR) {
+    A.C0 = fma2(w, dup(col.x), A.C0);
+    A.C1 = fma2(w, dup(col.y), A.C1);
+    A.C2 = fma2(w, dup(col.z), A.C2);
+  }
   if (NORMALS) {
     const f2 g0 = mul2(g.L[0], G.u0);
     const f2 g1 = fma2(g.L[2], G.u1, mul2(g.L[1], G.u0));
@@ -170,7 +186,14 @@ __device__ __forceinline__ PairOut2 fwd_pair2(RayAcc2& A, const GaussRec2& g, f2
 }
 
 
-template <bool NORMALS, int NFLOW, int RPT, bool STORE>
+// Shared-memory stage: kChunk records (4 float4 each), then in colour mode their
+// kChunk colour records (1 float4 each).
+template <bool COLOR>
+__host__ __device__ constexpr int fwd_stage_float4() {
+  return kChunk * (kRecFloat4 + (COLOR ? 1 : 0));
+}
+
+template <bool NORMALS, int NFLOW, int RPT, bool STORE, bool COLOR = false>
 __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_constant__ Batch batch, Scene s,
                                                               Consts k, const float4* __restrict__ records,
                                                               FwdOut out, int* status, int* counter) {
@@ -205,11 +228,14 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
   // Stage the first record chunks while the rays are set up.
   const float4* src = records + kRecFloat4 * V.rec_off;
   const int nchunks = (K + kChunk - 1) / kChunk;
+  constexpr int SST = fwd_stage_float4<COLOR>();
+  const float4* csrc = COLOR ? s.crec + V.rec_off : nullptr;
   if (tid == 0) {
     for (int c = 0; c < 2 && c < nchunks; ++c) {
       const int n = min(kChunk, K - c * kChunk);
-      mbar_arrive_expect_tx(&bars[c], n * 16u * kRecFloat4);
-      bulk_g2s(fwd_smem + c * kChunk * kRecFloat4, src + c * kChunk * kRecFloat4, n * 16u * kRecFloat4, &bars[c]);
+      mbar_arrive_expect_tx(&bars[c], n * 16u * (kRecFloat4 + (COLOR ? 1 : 0)));
+      bulk_g2s(fwd_smem + c * SST, src + c * kChunk * kRecFloat4, n * 16u * kRecFloat4, &bars[c]);
+      if (COLOR) bulk_g2s(fwd_smem + c * SST + kChunk * kRecFloat4, csrc + c * kChunk, n * 16u, &bars[c]);
     }
   }
 
@@ -252,6 +278,7 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
       a.m = dup(-INFINITY);
       a.Sw = a.Swt = a.Sd = dup(0.f);
       a.N0 = a.N1 = a.N2 = dup(0.f);
+      a.C0 = a.C1 = a.C2 = dup(0.f);
     }
   }
   const f2 K2v = dup(k.K2), K3v = dup(k.K3), B1v = dup(k.beta1), tiny = dup(1e-30f);
@@ -266,7 +293,8 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
       break;
     }
     const int n = min(kChunk, K - c * kChunk);
-    const float4* rec = fwd_smem + stage * kChunk * kRecFloat4;
+    const float4* rec = fwd_smem + stage * SST;
+    const float4* crs = rec + kChunk * kRecFloat4;  // colour mode: this stage's colour records
     if (STORE) {
       // Stored-intermediate mode (two rays per thread): the values of four
       // consecutive Gaussians are buffered and written as one 16-byte store per
@@ -309,8 +337,9 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
                                       rec[kRecFloat4 * i + 3]);
         if (PACKED) {
           const GaussRec2 g2 = broadcast_rec(g);
+          const float4 col = COLOR ? crs[i] : float4{};
 #pragma unroll
-          for (int q = 0; q < NP; ++q) fwd_pair2<NORMALS>(A2[q], g2, K2v, K3v, B1v, tiny);
+          for (int q = 0; q < NP; ++q) fwd_pair2<NORMALS, COLOR>(A2[q], g2, K2v, K3v, B1v, tiny, col);
         } else {
 #pragma unroll
           for (int r = 0; r < NA; ++r) fwd_pair<NORMALS>(A[r], g, k);
@@ -320,8 +349,10 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
     __syncthreads();  // every thread is done with this stage before it is refilled
     if (tid == 0 && c + 2 < nchunks) {
       const int n2 = min(kChunk, K - (c + 2) * kChunk);
-      mbar_arrive_expect_tx(&bars[stage], n2 * 16u * kRecFloat4);
-      bulk_g2s(fwd_smem + stage * kChunk * kRecFloat4, src + (c + 2) * kChunk * kRecFloat4, n2 * 16u * kRecFloat4,
+      mbar_arrive_expect_tx(&bars[stage], n2 * 16u * (kRecFloat4 + (COLOR ? 1 : 0)));
+      if (COLOR)
+        bulk_g2s(fwd_smem + stage * SST + kChunk * kRecFloat4, csrc + (c + 2) * kChunk, n2 * 16u, &bars[stage]);
+      bulk_g2s(fwd_smem + stage * SST, src + (c + 2) * kChunk * kRecFloat4, n2 * 16u * kRecFloat4,
                &bars[stage]);
     }
   }
@@ -363,6 +394,14 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
     }
     const float iSw = 1.0f / a.Sw;
     const float D = a.Swt * iSw;
+    if (COLOR) {
+      const RayAcc2& b = A2[r / 2];
+      const bool h = (r & 1) != 0;
+      float* col = out.color + 3 * off;
+      col[p] = (h ? hi(b.C0) : lo(b.C0)) * iSw;
+      col[P + p] = (h ? hi(b.C1) : lo(b.C1)) * iSw;
+      col[2 * P + p] = (h ? hi(b.C2) : lo(b.C2)) * iSw;
+    }
     out.depth[off + p] = D;
     out.alpha[off + p] = -expm1f(-a.Sd);
     float* sv = out.saved + 3 * off;
@@ -404,9 +443,9 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
   }  // item loop
 }
 
-static int fwd_smem_bytes(int maxK) {
+static int fwd_smem_bytes(int maxK, bool color = false) {
   const int stages = maxK > kChunk ? 2 : 1;  // a second stage only when K spans several chunks
-  return stages * kChunk * kRecFloat4 * static_cast<int>(sizeof(float4));
+  return stages * (color ? fwd_stage_float4<true>() : fwd_stage_float4<false>()) * static_cast<int>(sizeof(float4));
 }
 
 template <bool NORMALS, int NFLOW, int RPT>
@@ -418,10 +457,15 @@ static int fwd_ctas_per_sm_t(int maxK) {
   return n > 0 ? n : 1;
 }
 
-template <bool NORMALS, int NFLOW, int RPT, bool STORE = false>
+template <bool NORMALS, int NFLOW, int RPT, bool STORE = false, bool COLOR = false>
 static cudaError_t launch_fwd_t(const Batch& b, const Scene& s, const Consts& c, const float4* records,
                                 const FwdOut& o, int maxK, int* status, int* counter, cudaStream_t st) {
-  auto kern = forward_kernel<NORMALS, NFLOW, RPT, STORE>;
+  auto kern = forward_kernel<NORMALS, NFLOW, RPT, STORE, COLOR>;
+  const int smem = fwd_smem_bytes(maxK, COLOR);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
   int grid = b.n_items;
   if (counter) {
     int dev = 0, sms = 0;
@@ -429,7 +473,7 @@ static cudaError_t launch_fwd_t(const Batch& b, const Scene& s, const Consts& c,
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     grid = std::min(b.n_items, std::max(1, sms) * fwd_ctas_per_sm_t<NORMALS, NFLOW, RPT>(maxK));
   }
-  kern<<<grid, kFwdThreads, fwd_smem_bytes(maxK), st>>>(b, s, c, records, o, status, counter);
+  kern<<<grid, kFwdThreads, smem, st>>>(b, s, c, records, o, status, counter);
   return cudaGetLastError();
 }
 
@@ -438,6 +482,8 @@ static cudaError_t launch_fwd_r(int rpt, const Batch& b, const Scene& s, const C
                                 const FwdOut& o, int maxK, int* status, int* counter, cudaStream_t st) {
   if (o.pairs != nullptr)  // stored-intermediate mode: two rays per thread only
     return launch_fwd_t<NORMALS, NFLOW, 2, true>(b, s, c, records, o, maxK, status, counter, st);
+  if (o.color != nullptr)  // colour mode: two rays per thread only
+    return launch_fwd_t<NORMALS, NFLOW, 2, false, true>(b, s, c, records, o, maxK, status, counter, st);
   switch (rpt) {
     case 1: return launch_fwd_t<NORMALS, NFLOW, 1>(b, s, c, records, o, maxK, status, counter, st);
     case 2: return launch_fwd_t<NORMALS, NFLOW, 2>(b, s, c, records, o, maxK, status, counter, st);
@@ -446,10 +492,8 @@ static cudaError_t launch_fwd_r(int rpt, const Batch& b, const Scene& s, const C
 }
 
 cudaError_t launch_forward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
-                           int n_flow, int rpt, int maxK, float* depth, float* alpha, float* normal, float* flow,
-                           float* saved, float* pairs, long long pair_stride, int* status, int* counter,
+                           int n_flow, int rpt, int maxK, const FwdOut& o, int* status, int* counter,
                            cudaStream_t st) {
-  FwdOut o{depth, alpha, normal, flow, saved, pairs, pair_stride};
   if (normals) {
     if (n_flow == 0) return launch_fwd_r<true, 0>(rpt, b, s, c, records, o, maxK, status, counter, st);
     if (n_flow == 1) return launch_fwd_r<true, 1>(rpt, b, s, c, records, o, maxK, status, counter, st);

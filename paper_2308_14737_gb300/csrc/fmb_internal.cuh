@@ -358,6 +358,8 @@ struct Scene {
   const float* chol;
   const float* weights;
   const float* poses;
+  const float* colors = nullptr;  // per-Gaussian RGB [G][3], or null
+  float4* crec = nullptr;         // colour records (r, g, b, 0) per (view, Gaussian) in the workspace
 };
 
 // status_to_clear / counter_to_clear: if not null, the prologue also zeroes them.
@@ -365,9 +367,9 @@ cudaError_t launch_prologue(const Batch& b, const Scene& s, const Consts& c, flo
                             int* status_to_clear, int* counter_to_clear, cudaStream_t st);
 // counter: persistent mode's work counter (zeroed before the launch), or null for
 // one CTA per work item.
+struct FwdOut;
 cudaError_t launch_forward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
-                           int n_flow, int rpt, int maxK, float* depth, float* alpha, float* normal, float* flow,
-                           float* saved, float* pairs, long long pair_stride, int* status, int* counter,
+                           int n_flow, int rpt, int maxK, const FwdOut& o, int* status, int* counter,
                            cudaStream_t st);
 
 struct FwdOut {
@@ -378,10 +380,11 @@ struct FwdOut {
   float* saved;
   float* pairs;             // stored-intermediate mode: [t | e2 | delta] arrays, else null
   long long pair_stride;    // floats per array
+  float* color = nullptr;   // colour plane [3][P_v] per view (colour mode)
 };
 
 struct ZeroJob {
-  static constexpr int kMax = 6;
+  static constexpr int kMax = 7;
   float* ptr[kMax];
   long long n[kMax];
 };
@@ -393,6 +396,7 @@ struct BwdOut {
   float* gweights;
   float* gposes;  // may be null
   float* partials;  // deterministic mode: workspace region, else null
+  float* gcolors = nullptr;  // colour mode: [G][3]
 };
 struct BwdIn {
   const float* depth;
@@ -404,6 +408,8 @@ struct BwdIn {
   const float* g_flow;
   const float* pairs;      // stored-intermediate mode: [t | e2 | delta] arrays, else null
   long long pair_stride;   // floats per array
+  const float* color = nullptr;    // colour mode: the forward's colour plane
+  const float* g_color = nullptr;  // colour mode: its upstream gradient (may be null)
 };
 cudaError_t launch_backward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
                             int n_flow, int ray_tile, int threads, const BwdIn& in, const BwdOut& out,

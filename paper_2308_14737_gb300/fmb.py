@@ -31,7 +31,8 @@ class FmbParams(ctypes.Structure):
                 ("variant", ctypes.c_int), ("want_normals", ctypes.c_int), ("n_flow", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("use_persistent", ctypes.c_int),
                 ("fwd_rays_per_thread", ctypes.c_int), ("fwd_threads", ctypes.c_int),
-                ("bwd_ray_tile", ctypes.c_int), ("bwd_threads", ctypes.c_int), ("store_pairs", ctypes.c_int)]
+                ("bwd_ray_tile", ctypes.c_int), ("bwd_threads", ctypes.c_int), ("store_pairs", ctypes.c_int),
+                ("colors", ctypes.c_int)]
 
 
 class FmbView(ctypes.Structure):
@@ -68,12 +69,12 @@ def load_library(path: str = LIB_PATH):
     P = ctypes.POINTER(FmbParams)
     V = ctypes.POINTER(FmbView)
     LL = ctypes.POINTER(ctypes.c_longlong)
-    L.fmb_render_forward.argtypes = [P, i, LL, fp, fp, fp, i, fp, i, V, fp, fp, fp, fp, fp, vp, sz, vp]
+    L.fmb_render_forward.argtypes = [P, i, LL, fp, fp, fp, fp, i, fp, i, V, fp, fp, fp, fp, fp, fp, vp, sz, vp]
     L.fmb_render_forward.restype = ctypes.c_int
-    L.fmb_render_backward.argtypes = [P, i, LL, fp, fp, fp, i, fp, i, V, fp, fp, fp, fp, fp, fp, fp, fp, fp, fp,
-                                      fp, vp, sz, vp]
+    L.fmb_render_backward.argtypes = [P, i, LL, fp, fp, fp, fp, i, fp, i, V, fp, fp, fp, fp, fp, fp, fp, fp, fp,
+                                      fp, fp, fp, fp, fp, vp, sz, vp]
     L.fmb_render_backward.restype = ctypes.c_int
-    L.fmb_render_forward_noalloc.argtypes = [P, i, LL, fp, fp, fp, i, fp, i, V, fp, fp, fp, fp, fp, vp]
+    L.fmb_render_forward_noalloc.argtypes = [P, i, LL, fp, fp, fp, fp, i, fp, i, V, fp, fp, fp, fp, fp, fp, vp]
     L.fmb_render_forward_noalloc.restype = ctypes.c_int
     L.fmb_adam_step.argtypes = [ctypes.POINTER(FmbAdamParams), fp, fp, fp, fp, ctypes.c_longlong, ctypes.c_longlong,
                                 fp, vp]
@@ -175,26 +176,27 @@ def fmb_workspace_bytes(params: FmbParams, obj_offsets, views) -> int:
 
 
 def fmb_render_forward(params, obj_offsets, means, chol, weights, poses, views, depth, alpha, normal, flow, saved,
-                       workspace, stream=None):
+                       workspace, stream=None, colors=None, color=None):
     L = load_library()
     o, op = _offsets(obj_offsets)
     va = views if isinstance(views, ctypes.Array) else make_views(views)
     _check(L.fmb_render_forward(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol), _ptr(weights),
-                                int(poses.shape[0]), _ptr(poses), len(va), va, _ptr(depth), _ptr(alpha),
-                                _ptr(normal), _ptr(flow), _ptr(saved), _ptr(workspace), workspace.numel(),
-                                _stream(stream)))
+                                _ptr(colors), int(poses.shape[0]), _ptr(poses), len(va), va, _ptr(depth),
+                                _ptr(alpha), _ptr(normal), _ptr(flow), _ptr(color), _ptr(saved), _ptr(workspace),
+                                workspace.numel(), _stream(stream)))
 
 
 def fmb_render_forward_noalloc(params, obj_offsets, means, chol, weights, poses, views, depth, alpha, normal, flow,
-                               saved, stream=None):
+                               saved, stream=None, colors=None, color=None):
     """fmb_render_forward with the library's fixed scratch instead of a workspace
     (for callers that cannot allocate device memory)."""
     L = load_library()
     o, op = _offsets(obj_offsets)
     va = views if isinstance(views, ctypes.Array) else make_views(views)
     _check(L.fmb_render_forward_noalloc(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol),
-                                        _ptr(weights), int(poses.shape[0]), _ptr(poses), len(va), va, _ptr(depth),
-                                        _ptr(alpha), _ptr(normal), _ptr(flow), _ptr(saved), _stream(stream)))
+                                        _ptr(weights), _ptr(colors), int(poses.shape[0]), _ptr(poses), len(va), va,
+                                        _ptr(depth), _ptr(alpha), _ptr(normal), _ptr(flow), _ptr(color), _ptr(saved),
+                                        _stream(stream)))
 
 
 def fmb_render_points(params, obj_offsets, means, chol, weights, poses, views, depth, saved, points, normal_tf,
@@ -220,15 +222,16 @@ def fmb_loss_attribution(params, obj_offsets, means, chol, weights, poses, views
 
 def fmb_render_backward(params, obj_offsets, means, chol, weights, poses, views, depth, normal, saved, g_depth,
                         g_alpha, g_normal, g_flow, grad_means, grad_chol, grad_weights, grad_poses, workspace,
-                        stream=None):
+                        stream=None, colors=None, color=None, g_color=None, grad_colors=None):
     L = load_library()
     o, op = _offsets(obj_offsets)
     va = views if isinstance(views, ctypes.Array) else make_views(views)
     _check(L.fmb_render_backward(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol), _ptr(weights),
-                                 int(poses.shape[0]), _ptr(poses), len(va), va, _ptr(depth), _ptr(normal),
-                                 _ptr(saved), _ptr(g_depth), _ptr(g_alpha), _ptr(g_normal), _ptr(g_flow),
-                                 _ptr(grad_means), _ptr(grad_chol), _ptr(grad_weights), _ptr(grad_poses),
-                                 _ptr(workspace), workspace.numel(), _stream(stream)))
+                                 _ptr(colors), int(poses.shape[0]), _ptr(poses), len(va), va, _ptr(depth),
+                                 _ptr(normal), _ptr(color), _ptr(saved), _ptr(g_depth), _ptr(g_alpha),
+                                 _ptr(g_normal), _ptr(g_flow), _ptr(g_color), _ptr(grad_means), _ptr(grad_chol),
+                                 _ptr(grad_weights), _ptr(grad_colors), _ptr(grad_poses), _ptr(workspace),
+                                 workspace.numel(), _stream(stream)))
 
 
 def fmb_adam_step(adam: FmbAdamParams, param, grad, m, v, positive_begin, step_counter, stream=None):
@@ -280,11 +283,16 @@ class Renderer:
         self.normal = torch.empty(3 * self.P, **f32) if self.params.want_normals else None
         self.flow = torch.empty(2 * nf * self.P, **f32) if nf > 0 else None
         self.saved = torch.empty(3 * self.P, **f32)
+        self.color = torch.empty(3 * self.P, **f32) if self.params.colors else None
 
-    def forward(self, means, chol, weights, poses, stream=None):
+    def forward(self, means, chol, weights, poses, stream=None, colors=None):
+        """colors: [G][3] device tensor when params.colors (the colour plane is then
+        returned as "color")."""
         fmb_render_forward(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, self.depth,
-                           self.alpha, self.normal, self.flow, self.saved, self.ws, stream)
-        return dict(depth=self.depth, alpha=self.alpha, normal=self.normal, flow=self.flow, saved=self.saved)
+                           self.alpha, self.normal, self.flow, self.saved, self.ws, stream, colors=colors,
+                           color=self.color)
+        return dict(depth=self.depth, alpha=self.alpha, normal=self.normal, flow=self.flow, saved=self.saved,
+                    color=self.color)
 
     def points(self, means, chol, weights, poses, stream=None):
         """Oriented point export (Sec. 6) of the last forward call's depth: world
@@ -308,15 +316,18 @@ class Renderer:
         return out
 
     def backward(self, means, chol, weights, poses, g_depth, g_alpha, g_normal, g_flow, want_pose=True,
-                 out=None, stream=None):
+                 out=None, stream=None, colors=None, g_color=None):
         G = means.shape[0]
         if out is None:
             f32 = dict(dtype=torch.float32, device=means.device)
             out = dict(means=torch.empty(G, 3, **f32), chol=torch.empty(G, 6, **f32), weights=torch.empty(G, **f32),
                        poses=torch.empty(poses.shape[0], 12, **f32) if want_pose else None)
+            if self.params.colors:
+                out["colors"] = torch.empty(G, 3, **f32)
         fmb_render_backward(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, self.depth,
                             self.normal, self.saved, g_depth, g_alpha, g_normal, g_flow, out["means"], out["chol"],
-                            out["weights"], out["poses"], self.ws, stream)
+                            out["weights"], out["poses"], self.ws, stream, colors=colors, color=self.color,
+                            g_color=g_color, grad_colors=out.get("colors"))
         return out
 
 

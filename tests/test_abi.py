@@ -43,8 +43,8 @@ def test_struct_layouts(fmb):
     assert ctypes.sizeof(fmb.FmbView) == 64
     assert fmb.FmbView.pix_offset.offset == 40
     assert fmb.FmbView.rays.offset == 48 and fmb.FmbView.n_rays.offset == 56
-    assert ctypes.sizeof(fmb.FmbParams) == 52
-    assert fmb.FmbParams.store_pairs.offset == 48
+    assert ctypes.sizeof(fmb.FmbParams) == 56
+    assert fmb.FmbParams.store_pairs.offset == 48 and fmb.FmbParams.colors.offset == 52
 
 
 def test_default_params_and_version(fmb):
@@ -98,13 +98,14 @@ def _call_fwd(fmb, params, offs, views, n_poses=1, **override):
     f = _Fake()
     va = fmb.make_views(views)
     o = np.asarray(offs, dtype=np.int64)
-    args = dict(means=f, chol=f, weights=f, poses=f, depth=f, alpha=f, normal=f, flow=f, saved=f, ws=f)
+    args = dict(means=f, chol=f, weights=f, colors=f, poses=f, depth=f, alpha=f, normal=f, flow=f, color=f, saved=f,
+                ws=f)
     args.update(override)
     P = lambda k: None if args[k] is None else ctypes.c_void_p(args[k].data_ptr())
     ws = args["ws"]
     return L.fmb_render_forward(ctypes.byref(params), len(o) - 1, o.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
-                                P("means"), P("chol"), P("weights"), n_poses, P("poses"), len(va), va, P("depth"),
-                                P("alpha"), P("normal"), P("flow"), P("saved"),
+                                P("means"), P("chol"), P("weights"), P("colors"), n_poses, P("poses"), len(va), va,
+                                P("depth"), P("alpha"), P("normal"), P("flow"), P("color"), P("saved"),
                                 None if ws is None else ctypes.c_void_p(ws.data_ptr()), 0 if ws is None else ws.n,
                                 None), L.fmb_last_error().decode()
 
@@ -150,7 +151,7 @@ def test_stored_pairs_needs_two_rays_per_thread_and_a_workspace(fmb):
     o = np.asarray([0, 5], dtype=np.int64)
     p = fmb.default_params(store_pairs=1)
     st = L.fmb_render_forward_noalloc(ctypes.byref(p), 1, o.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), fp,
-                                      fp, fp, 1, fp, 1, va, fp, fp, fp, fp, fp, None)
+                                      fp, fp, fp, 1, fp, 1, va, fp, fp, fp, fp, fp, fp, None)
     assert st == 1 and "store_pairs" in L.fmb_last_error().decode()
 
 
@@ -166,6 +167,16 @@ def test_alpha_compositing_limits(fmb):
     p = fmb.default_params(variant=2)
     st, err = _call_fwd(fmb, p, [0, 5], [_view()])
     assert st == 1 and "variant" in err
+
+
+def test_colour_mode_needs_its_buffers(fmb):
+    p = fmb.default_params(colors=1)
+    st, err = _call_fwd(fmb, p, [0, 5], [_view()], colors=None)
+    assert st == 1 and "colors" in err
+    st, err = _call_fwd(fmb, fmb.default_params(colors=1, store_pairs=1), [0, 5], [_view()])
+    assert st == 1 and "store_pairs" in err
+    st, err = _call_fwd(fmb, fmb.default_params(colors=2), [0, 5], [_view()])
+    assert st == 1 and "colors" in err
 
 
 def test_forward_rejects_bad_scene_and_buffers(fmb):
@@ -193,5 +204,6 @@ def test_backward_rejects_missing_outputs(fmb):
     o = np.asarray([0, 5], dtype=np.int64)
     fp = ctypes.c_void_p(f.data_ptr())
     st = L.fmb_render_backward(ctypes.byref(p), 1, o.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), fp, fp, fp,
-                               1, fp, 1, va, fp, fp, fp, fp, fp, fp, fp, None, fp, fp, None, fp, 1 << 20, None)
+                               fp, 1, fp, 1, va, fp, fp, fp, fp, fp, fp, fp, fp, fp, None, fp, fp, fp, None, fp,
+                               1 << 20, None)
     assert st == 1 and "grad_means" in L.fmb_last_error().decode()

@@ -12,7 +12,8 @@ import torch
 import oracle
 from paper_2308_14737_gb300 import fmb, synth
 
-from gpu_util import (ac_order_ambiguous, compare_forward, compare_grads, gpu_backward, gpu_forward, masked_upstream,
+from gpu_util import (ac_order_ambiguous, compare_forward, compare_grads, dev_scene, gpu_backward, gpu_forward,
+                      masked_upstream,
                       plane_view, points_tolerances,
                       nnorm_batched,
                       oracle_backward_sampled, oracle_forward_sampled, pixel_mask_from, sample_pixels)
@@ -409,3 +410,46 @@ def test_loss_attribution_parity(variant):
         ref = oracle.attribution_scene(s, loss, variant=variant)
         assert np.max(np.abs(a - ref)) <= 1e-5 * loss.sum(), float(np.max(np.abs(a - ref)) / loss.sum())
         assert abs(a.sum() - loss.astype(np.float64).sum()) <= 1e-4 * loss.sum()
+
+
+# ------------------------------------------------------------ per-Gaussian colours
+
+@pytest.mark.parametrize("variant,deterministic", [(0, False), (0, True), (1, False), (1, True)])
+def test_colour_parity(variant, deterministic):
+    """Colour mode: the colour plane (Eq. 3 with per-Gaussian RGB) and every gradient,
+    colours' included, against the oracle; the other planes and gradients are those
+    of the colour-free render."""
+    for s, nf in ((synth.config1(K=100, n_views=3, W=40, H=30), 1), (synth.config0(), 0)):
+        rng = np.random.default_rng(9)
+        colors = rng.uniform(0.0, 1.0, (s.means.shape[0], 3)).astype(np.float32)
+        params = fmb.default_params(n_flow=nf, variant=variant, colors=1, deterministic=int(deterministic))
+        r = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), params)
+        dev = dev_scene(s)
+        cdev = torch.as_tensor(colors, device="cuda")
+        out = r.forward(*dev, colors=cdev)
+        torch.cuda.synchronize()
+        gpu = {k: v.cpu().numpy().astype(np.float64) for k, v in out.items() if v is not None}
+        ref = oracle.render_scene(s, n_flow=nf, variant=variant, colors=colors)
+        amb = ac_order_ambiguous(s) if variant == 1 else None
+        compare_forward(s, gpu, ref, nf, True, variant=variant, ambiguous=amb)
+        ok = ref["alpha"] >= 1e-2
+        if amb is not None:
+            ok &= ~amb
+        for v in s.views:
+            o, P = v["pix_offset"], synth.view_entries(v)
+            e = np.abs(plane_view(gpu["color"], v, 3) - plane_view(ref["color"], v, 3)).max(0)
+            assert np.all((e <= 1e-4)[ok[o:o + P]]), float(e[ok[o:o + P]].max())
+        ups = masked_upstream(s, ref["alpha"], nf, seed=3, nnorm_ref=nnorm_batched(s, ref["saved"]), exclude=amb)
+        gcol = np.random.default_rng(10).standard_normal(3 * s.n_pixels).astype(np.float32)
+        for v in s.views:  # colour gradient only where the colour is unique (alpha >= 1e-2, order resolved)
+            o, P = v["pix_offset"], synth.view_entries(v)
+            gcol[3 * o:3 * (o + P)] *= np.tile(ok[o:o + P], 3)
+        T = lambda a: None if a is None else torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32,
+                                                              device="cuda")
+        g = r.backward(*dev, T(ups["g_depth"]), T(ups["g_alpha"]), T(ups["g_normal"]), T(ups["g_flow"]),
+                       colors=cdev, g_color=T(gcol))
+        torch.cuda.synchronize()
+        g = {k: v.cpu().numpy().astype(np.float64) for k, v in g.items() if v is not None}
+        refg = oracle.backward_scene(s, ups["g_depth"], ups["g_alpha"], ups["g_normal"], ups["g_flow"], n_flow=nf,
+                                     variant=variant, colors=colors, g_color=gcol)
+        compare_grads(g, refg, keys=("means", "chol", "weights", "poses", "colors"))
