@@ -32,6 +32,7 @@
 namespace fmb {
 
 int ac_rays_per_item() { return kAcRays; }
+int ac_fwd_rays_per_item() { return kAcFwdRays; }
 
 // ------------------------------------------------------------------ forward
 template <bool NORMALS, int NFLOW, int M>
@@ -76,14 +77,19 @@ __global__ void __launch_bounds__(kAcThreads) forward_ac_kernel(const __grid_con
       if (has_t[j]) load_pose(s.poses, tg, Rj[j], tj[j]);
     }
     const long long off = V.pix_off;
-    for (int rr = warp; rr < kAcRays; rr += kAcWarps) {
-      const int p = tile * kAcRays + rr;
+    // each warp takes a run of neighbouring rays, so each starts from the previous
+    // ray's depth order
+    constexpr int kPerWarp = kAcFwdRays / kAcWarps;
+    unsigned long long key[M];
+    for (int m = 0; m < M; ++m) key[m] = kNoKey;
+    for (int j = 0; j < kPerWarp; ++j) {
+      const int p = tile * kAcFwdRays + warp * kPerWarp + j;
       if (p >= P) break;
       float vc[3], v[3], vl[3], pxy[2];
       pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
       float t[M], dl[M], n[M][3];
       const float4* crec = s.crec != nullptr && out.color != nullptr ? s.crec + V.rec_off : nullptr;
-      const AcSums a = ac_render_ray<NORMALS, M>(srec, V.K, v, vl, k, lane, t, dl, n, sd, sw, sT, crec);
+      const AcSums a = ac_render_ray<NORMALS, M>(srec, V.K, v, vl, k, lane, t, dl, n, sd, sw, sT, key, j > 0, crec);
       if (lane == 0) {
         const float iW = a.W > 0.f ? 1.0f / a.W : 0.f;
         const float D = a.WT * iW;
@@ -287,13 +293,18 @@ __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 2 : 3) backward_ac_kernel
     float pose_acc[NPV];
 #pragma unroll
     for (int i = 0; i < NPV; ++i) pose_acc[i] = 0.f;
-    for (int rr = warp; rr < nr; rr += kAcWarps) {
+    constexpr int kPerWarp = kAcRays / kAcWarps;
+    unsigned long long key[M];
+    for (int m = 0; m < M; ++m) key[m] = kNoKey;
+    for (int j = 0; j < kPerWarp; ++j) {
+      const int rr = warp * kPerWarp + j;  // a run of neighbouring rays per warp
+      if (rr >= nr) break;
       const int p = pix0 + rr;
       float vc[3], v[3], vl[3], pxy[2];
       pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
       float t[M], dl[M], n[M][3];
       const float4* crec = color ? s.crec + V.rec_off : nullptr;
-      const AcSums a = ac_render_ray<NORMALS, M>(srec, K, v, vl, k, lane, t, dl, n, sd, sw, sT, crec);
+      const AcSums a = ac_render_ray<NORMALS, M>(srec, K, v, vl, k, lane, t, dl, n, sd, sw, sT, key, j > 0, crec);
       const float iW = a.W > 0.f ? 1.0f / a.W : 0.f;
       const float D = a.WT * iW;
       // colour mode: Cbar and the blended colour C = sum w c / W
@@ -392,17 +403,10 @@ __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 2 : 3) backward_ac_kernel
         }
       }
       __syncwarp();
-      // Suffix sums of q over the hits strictly behind each hit, in sorted order:
-      // U = total - (inclusive prefix at the end of the hit's run of equal depth).
+      // Suffix sums of q over the hits strictly behind each hit, in sorted order (the
+      // keys ac_render_ray left sorted): U = total - (inclusive prefix at the end of
+      // the hit's run of equal depth).
       {
-        unsigned long long key[M];
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-          const int e = (m << 5) | lane;
-          key[m] = e < K ? (static_cast<unsigned long long>(order_bits(t[m])) << 32) | static_cast<unsigned>(e)
-                         : kNoKey;
-        }
-        warp_bitonic_sort<M>(key, lane);
         // sorted order, lane holding positions lane M + m: inclusive prefix Q of q
         float ts[M], Q[M];
         int idx[M];

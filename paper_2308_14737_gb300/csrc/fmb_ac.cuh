@@ -12,7 +12,8 @@ namespace fmb {
 
 constexpr int kAcWarps = 4;
 constexpr int kAcThreads = 32 * kAcWarps;
-constexpr int kAcRays = 32;          // rays per work item (forward and backward)
+constexpr int kAcRays = 32;          // rays per backward / export work item (8 per warp)
+constexpr int kAcFwdRays = 128;      // rays per forward work item (32 per warp)
 constexpr int kAcRayRec = 7;         // backward per-ray record, float4s (values duplicated)
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kLog2e = 1.4426950408889634f;
@@ -76,6 +77,47 @@ __device__ __forceinline__ void warp_bitonic_sort(unsigned long long (&key)[M], 
   }
 }
 
+// Ascending odd-even transposition passes over the same blocked layout until no
+// pair is out of order (at most 32 M passes, which sort any input): cheap when the
+// keys arrive nearly sorted -- the previous, neighbouring ray's depth order.
+template <int M>
+__device__ __forceinline__ void warp_refine_sort(unsigned long long (&key)[M], int lane) {
+  constexpr int N = 32 * M;
+  for (int pass = 0; pass < N; ++pass) {
+    bool swapped = false;
+#pragma unroll
+    for (int m = 0; m + 1 < M; m += 2) {  // even pairs (lane M + m, lane M + m + 1), m even
+      const unsigned long long a = key[m], b = key[m + 1];
+      if (a > b) {
+        key[m] = b;
+        key[m + 1] = a;
+        swapped = true;
+      }
+    }
+#pragma unroll
+    for (int m = 1; m + 1 < M; m += 2) {  // odd pairs inside the lane
+      const unsigned long long a = key[m], b = key[m + 1];
+      if (a > b) {
+        key[m] = b;
+        key[m + 1] = a;
+        swapped = true;
+      }
+    }
+    // odd pair across lanes: (lane M + M - 1, (lane + 1) M)
+    const unsigned long long next_first = __shfl_down_sync(kFull, key[0], 1);
+    const unsigned long long prev_last = __shfl_up_sync(kFull, key[M - 1], 1);
+    if (lane < 31 && key[M - 1] > next_first) {
+      key[M - 1] = next_first;
+      swapped = true;
+    }
+    if (lane > 0 && prev_last > key[0]) {
+      key[0] = prev_last;
+      swapped = true;
+    }
+    if (!__any_sync(kFull, swapped)) break;
+  }
+}
+
 __device__ __forceinline__ float warp_incl_sum(float x, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -111,8 +153,13 @@ template <bool NORMALS, int M>
 __device__ __forceinline__ AcSums ac_render_ray(const float4* __restrict__ rec, int K, const float v[3],
                                                 const float vl[3], const Consts& k, int lane, float (&t)[M],
                                                 float (&dl)[M], float (&n)[M][3], float* sd, float* sw, float* sT,
+                                                unsigned long long (&key)[M], bool reuse_order,
                                                 const float4* __restrict__ crec = nullptr) {
-  unsigned long long key[M];
+  // key: in, with reuse_order, the previous ray's sorted keys (their Gaussian
+  // indices give the starting order); out, this ray's sorted keys.
+  int prev[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) prev[m] = key[m] != kNoKey ? static_cast<int>(key[m] & 0xffffffffu) : -1;
 #pragma unroll
   for (int m = 0; m < M; ++m) {
     const int e = (m << 5) | lane;
@@ -136,11 +183,23 @@ __device__ __forceinline__ AcSums ac_render_ray(const float4* __restrict__ rec, 
         n[m][2] = g2 * rs;
       }
       sd[e] = dl[m];
+      sT[e] = G.t;  // for the reordering below (overwritten by T afterwards)
       key[m] = (static_cast<unsigned long long>(order_bits(G.t)) << 32) | static_cast<unsigned>(e);
     }
   }
   __syncwarp();
-  warp_bitonic_sort<M>(key, lane);
+  if (reuse_order) {
+    // start from the previous ray's order (sorting position lane M + m) and refine
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+      key[m] = prev[m] >= 0 ? (static_cast<unsigned long long>(order_bits(sT[prev[m]])) << 32) |
+                                  static_cast<unsigned>(prev[m])
+                            : kNoKey;
+    __syncwarp();
+    warp_refine_sort<M>(key, lane);
+  } else {
+    warp_bitonic_sort<M>(key, lane);
+  }
   // Sorted order (lane holds positions lane M + m): exclusive prefix sums of
   // delta, run-aware (Eq. 10's strict <).
   float ts[M], ds[M];

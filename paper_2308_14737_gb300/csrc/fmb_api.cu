@@ -191,7 +191,7 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
   pl.ray_tile = p->bwd_ray_tile > 0 ? p->bwd_ray_tile : 3 * pl.bwd_threads;
   pl.n_gauss = offs[n_objects];
   const bool ac = p->variant == 1;
-  const int rays_fwd = ac ? fmb::ac_rays_per_item() : fmb::forward_rays_per_cta(pl.rpt);
+  const int rays_fwd = ac ? fmb::ac_fwd_rays_per_item() : fmb::forward_rays_per_cta(pl.rpt);
   const int n_flow = p->n_flow;
   long long rec = 0, part = 0, pairs = 0;
   for (int base = 0; base < n_views; base += fmb::kMaxBatchViews) {

@@ -43,6 +43,9 @@ __global__ void __launch_bounds__(kAcThreads) attribution_kernel(const __grid_co
 #pragma unroll
   for (int m = 0; m < M; ++m) acc[m] = 0.f;
   const int p0 = tile * kAttRays + warp * kAttRaysPerWarp;
+  unsigned long long key[M];  // alpha compositing: the last rendered ray's depth order
+  for (int m = 0; m < M; ++m) key[m] = kNoKey;
+  bool have_order = false;
   for (int rr = 0; rr < kAttRaysPerWarp; ++rr) {
     const int p = p0 + rr;
     if (p >= P) break;
@@ -53,7 +56,9 @@ __global__ void __launch_bounds__(kAcThreads) attribution_kernel(const __grid_co
     if (AC) {
       float t[M], dl[M], n[M][3];
       float* sd = scratch[warp];
-      const AcSums a = ac_render_ray<false, M>(rec, Kb, v, vl, k, lane, t, dl, n, sd, sd + 32 * M, sd + 64 * M);
+      const AcSums a = ac_render_ray<false, M>(rec, Kb, v, vl, k, lane, t, dl, n, sd, sd + 32 * M, sd + 64 * M,
+                                               key, have_order);
+      have_order = true;
       const float c = a.W > 0.f ? Lj / a.W : 0.f;
 #pragma unroll
       for (int m = 0; m < M; ++m) {

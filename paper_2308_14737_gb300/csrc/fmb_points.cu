@@ -180,13 +180,16 @@ __global__ void __launch_bounds__(kAcThreads) points_ac_kernel(const __grid_cons
   float* sd = scratch[warp];
   float* sw = sd + 32 * M;
   float* sT = sd + 64 * M;
-  for (int rr = warp; rr < kAcRays; rr += kAcWarps) {
-    const int p = tile * kAcRays + rr;
+  constexpr int kPerWarp = kAcRays / kAcWarps;
+  unsigned long long key[M];
+  for (int m = 0; m < M; ++m) key[m] = kNoKey;
+  for (int j = 0; j < kPerWarp; ++j) {
+    const int p = tile * kAcRays + warp * kPerWarp + j;  // neighbouring rays: reuse the depth order
     if (p >= P) break;
     float vc[3], v[3], vl[3], pxy[2];
     pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
     float t[M], dl[M], n[M][3];
-    const AcSums a = ac_render_ray<false, M>(rec, V.K, v, vl, k, lane, t, dl, n, sd, sw, sT);
+    const AcSums a = ac_render_ray<false, M>(rec, V.K, v, vl, k, lane, t, dl, n, sd, sw, sT, key, j > 0);
     const float D = depth[off + p];
     const float iW = a.W > 0.f ? 1.0f / a.W : 0.f;
     float qmax = 0.f, N[3] = {0.f, 0.f, 0.f};
