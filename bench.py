@@ -472,6 +472,25 @@ def run_gpu(args):
         line["points_export"] = {"ms": ms_p, "value": pairs / (ms_p * 1e-3), "unit": "pairs/s", "steps": n_p,
                                  "what": "points, normals at the rendered depth, Eq. 16 screen normals and the "
                                          "max-weight quality of every pixel (fmb_render_points)"}
+    if args.attribution:
+        # Sec. 8 loss attribution of the batch just rendered, timed alone; the per-ray
+        # loss is the magnitude of the synthetic upstream depth gradient
+        ray_loss = gd.abs()
+        att = torch.empty(means.shape[0], dtype=torch.float32, device=dev)
+        for _ in range(3):
+            batched.attribution(means, chol, weights, poses, ray_loss, out=att)
+        torch.cuda.synchronize(dev)
+        n_a = max(args.steps // 4, 3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n_a):
+            batched.attribution(means, chol, weights, poses, ray_loss, out=att)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms_a = e0.elapsed_time(e1) / n_a
+        line["loss_attribution"] = {"ms": ms_a, "value": pairs / (ms_a * 1e-3), "unit": "pairs/s", "steps": n_a,
+                                    "what": "per-Gaussian sum of ray loss x normalised weight over every ray of the "
+                                            "batch (fmb_loss_attribution, Sec. 8 splitting criterion)"}
     if args.workload == "recon" or args.stored:
         line["stored_vs_recompute"] = stored_adjoint_measure(args, s, (gd, ga, gn, gf), tuned_params, dev)
     if args.workload == "recon":
@@ -762,6 +781,8 @@ def main():
     ap.add_argument("--variant", default="two-param", choices=["two-param", "ac"],
                     help="weights of Eq. 3: the two-parameter model (Eq. 7) or alpha compositing (Eq. 9-10)")
     ap.add_argument("--points", action="store_true", help="also time the oriented point export (Sec. 6)")
+    ap.add_argument("--attribution", action="store_true",
+                    help="also time the loss attribution of the splitting criterion (Sec. 8)")
     ap.add_argument("--stored", action="store_true",
                     help="also time the stored-intermediate adjoint (always on for --workload recon)")
     args = ap.parse_args()

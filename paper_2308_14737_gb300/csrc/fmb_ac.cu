@@ -32,13 +32,23 @@
 namespace fmb {
 
 int ac_rays_per_item() { return kAcRays; }
-int ac_fwd_rays_per_item() { return kAcFwdRays; }
+// Forward run length (rays per warp; a work item is kAcWarps runs): the longest power
+// of two up to kAcMaxRun that still gives every SM about 32 warps of work, so that
+// large batches keep long runs of incrementally ordered neighbouring rays while small
+// ones (a single 64x64 view) spread over the whole GPU instead of a few SMs.
+int ac_fwd_run(long long total_rays, int sms) {
+  const long long target_warps = 32ll * std::max(sms, 1);
+  int run = kAcMaxRun;
+  while (run > 1 && total_rays < target_warps * run) run >>= 1;
+  return run;
+}
+int ac_fwd_rays_per_item(int run) { return kAcWarps * run; }
 
 // ------------------------------------------------------------------ forward
 template <bool NORMALS, int NFLOW, int M>
 __global__ void __launch_bounds__(kAcThreads) forward_ac_kernel(const __grid_constant__ Batch batch, Scene s,
                                                                 Consts k, const float4* __restrict__ records,
-                                                                FwdOut out, int* status, int* counter) {
+                                                                FwdOut out, int run, int* status, int* counter) {
   extern __shared__ float4 ac_smem[];  // records [32 M][4 float4] | per warp: sd, sw, sT [32 M floats each]
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_item;
@@ -79,11 +89,10 @@ __global__ void __launch_bounds__(kAcThreads) forward_ac_kernel(const __grid_con
     const long long off = V.pix_off;
     // each warp takes a run of neighbouring rays, so each starts from the previous
     // ray's depth order
-    constexpr int kPerWarp = kAcFwdRays / kAcWarps;
     unsigned long long key[M];
     for (int m = 0; m < M; ++m) key[m] = kNoKey;
-    for (int j = 0; j < kPerWarp; ++j) {
-      const int p = tile * kAcFwdRays + warp * kPerWarp + j;
+    for (int j = 0; j < run; ++j) {
+      const int p = (tile * kAcWarps + warp) * run + j;
       if (p >= P) break;
       float vc[3], v[3], vl[3], pxy[2];
       pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
@@ -640,7 +649,7 @@ static int ac_fwd_smem() {
 
 template <bool NORMALS, int NFLOW, int M>
 static cudaError_t launch_fwd_ac_t(const Batch& b, const Scene& s, const Consts& c, const float4* records,
-                                   const FwdOut& o, int* status, int* counter, cudaStream_t st) {
+                                   const FwdOut& o, int run, int* status, int* counter, cudaStream_t st) {
   auto kern = forward_ac_kernel<NORMALS, NFLOW, M>;
   const int smem = ac_fwd_smem<M>();
   if (smem > 48 * 1024) {
@@ -655,7 +664,7 @@ static cudaError_t launch_fwd_ac_t(const Batch& b, const Scene& s, const Consts&
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kAcThreads, smem);
     grid = std::min(b.n_items, std::max(1, sms) * std::max(1, per));
   }
-  kern<<<grid, kAcThreads, smem, st>>>(b, s, c, records, o, status, counter);
+  kern<<<grid, kAcThreads, smem, st>>>(b, s, c, records, o, run, status, counter);
   return cudaGetLastError();
 }
 
@@ -682,15 +691,15 @@ static cudaError_t launch_bwd_ac_t(const Batch& b, const Scene& s, const Consts&
 
 template <int M>
 static cudaError_t fwd_ac_m(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
-                            int n_flow, const FwdOut& o, int* status, int* counter, cudaStream_t st) {
+                            int n_flow, const FwdOut& o, int run, int* status, int* counter, cudaStream_t st) {
   if (normals) {
-    if (n_flow == 0) return launch_fwd_ac_t<true, 0, M>(b, s, c, records, o, status, counter, st);
-    if (n_flow == 1) return launch_fwd_ac_t<true, 1, M>(b, s, c, records, o, status, counter, st);
-    return launch_fwd_ac_t<true, 2, M>(b, s, c, records, o, status, counter, st);
+    if (n_flow == 0) return launch_fwd_ac_t<true, 0, M>(b, s, c, records, o, run, status, counter, st);
+    if (n_flow == 1) return launch_fwd_ac_t<true, 1, M>(b, s, c, records, o, run, status, counter, st);
+    return launch_fwd_ac_t<true, 2, M>(b, s, c, records, o, run, status, counter, st);
   }
-  if (n_flow == 0) return launch_fwd_ac_t<false, 0, M>(b, s, c, records, o, status, counter, st);
-  if (n_flow == 1) return launch_fwd_ac_t<false, 1, M>(b, s, c, records, o, status, counter, st);
-  return launch_fwd_ac_t<false, 2, M>(b, s, c, records, o, status, counter, st);
+  if (n_flow == 0) return launch_fwd_ac_t<false, 0, M>(b, s, c, records, o, run, status, counter, st);
+  if (n_flow == 1) return launch_fwd_ac_t<false, 1, M>(b, s, c, records, o, run, status, counter, st);
+  return launch_fwd_ac_t<false, 2, M>(b, s, c, records, o, run, status, counter, st);
 }
 
 template <int M>
@@ -710,11 +719,13 @@ static cudaError_t bwd_ac_m(const Batch& b, const Scene& s, const Consts& c, con
 int ac_lanes_per_ray_elements(int maxK) { return maxK <= 64 ? 2 : (maxK <= 128 ? 4 : 8); }
 
 cudaError_t launch_forward_ac(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
-                              int n_flow, int maxK, const FwdOut& o, int* status, int* counter, cudaStream_t st) {
+                              int n_flow, int maxK, const FwdOut& o, int run, int* status, int* counter,
+                              cudaStream_t st) {
+  if (run < 1 || run > kAcMaxRun) return cudaErrorInvalidValue;
   switch (ac_lanes_per_ray_elements(maxK)) {
-    case 2: return fwd_ac_m<2>(b, s, c, records, normals, n_flow, o, status, counter, st);
-    case 4: return fwd_ac_m<4>(b, s, c, records, normals, n_flow, o, status, counter, st);
-    default: return fwd_ac_m<8>(b, s, c, records, normals, n_flow, o, status, counter, st);
+    case 2: return fwd_ac_m<2>(b, s, c, records, normals, n_flow, o, run, status, counter, st);
+    case 4: return fwd_ac_m<4>(b, s, c, records, normals, n_flow, o, run, status, counter, st);
+    default: return fwd_ac_m<8>(b, s, c, records, normals, n_flow, o, run, status, counter, st);
   }
 }
 

@@ -13,7 +13,7 @@ namespace fmb {
 constexpr int kAcWarps = 4;
 constexpr int kAcThreads = 32 * kAcWarps;
 constexpr int kAcRays = 32;          // rays per backward / export work item (8 per warp)
-constexpr int kAcFwdRays = 128;      // rays per forward work item (32 per warp)
+constexpr int kAcMaxRun = 32;        // longest forward run of neighbouring rays per warp
 constexpr int kAcRayRec = 7;         // backward per-ray record, float4s (values duplicated)
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kLog2e = 1.4426950408889634f;

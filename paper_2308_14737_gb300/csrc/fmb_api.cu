@@ -99,6 +99,7 @@ struct Plan {
   int rpt = kDefaultRpt;
   int ray_tile = 480;
   int bwd_threads = 160;
+  int ac_run = 1;  // alpha compositing: forward rays per warp
 };
 
 fmb_status validate_scene(const fmb_params* p, int n_objects, const long long* offs, int n_views,
@@ -191,7 +192,18 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
   pl.ray_tile = p->bwd_ray_tile > 0 ? p->bwd_ray_tile : 3 * pl.bwd_threads;
   pl.n_gauss = offs[n_objects];
   const bool ac = p->variant == 1;
-  const int rays_fwd = ac ? fmb::ac_fwd_rays_per_item() : fmb::forward_rays_per_cta(pl.rpt);
+  if (ac) {
+    long long total = 0;
+    for (int i = 0; i < n_views; ++i) total += view_entries(views[i]);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();  // no device (a host-only size query): plan for 152 SMs
+      sms = 152;
+    }
+    pl.ac_run = fmb::ac_fwd_run(total, sms);
+  }
+  const int rays_fwd = ac ? fmb::ac_fwd_rays_per_item(pl.ac_run) : fmb::forward_rays_per_cta(pl.rpt);
   const int n_flow = p->n_flow;
   long long rec = 0, part = 0, pairs = 0;
   for (int base = 0; base < n_views; base += fmb::kMaxBatchViews) {
@@ -389,8 +401,8 @@ fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const lon
       fo.color = color;
       if (params->variant == 1) {
         fo.pairs = nullptr;
-        e = fmb::launch_forward_ac(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.maxK, fo, status,
-                                   counter, s);
+        e = fmb::launch_forward_ac(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.maxK, fo, pl.ac_run,
+                                   status, counter, s);
       } else {
         e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, pl.maxK, fo,
                                 status, counter, s);
@@ -699,8 +711,8 @@ extern "C" fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n
       fo.color = color;
       if (params->variant == 1) {
         fo.pairs = nullptr;
-        e = fmb::launch_forward_ac(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.maxK, fo, status,
-                                   counter, s);
+        e = fmb::launch_forward_ac(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.maxK, fo, pl.ac_run,
+                                   status, counter, s);
       } else {
         e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, pl.maxK, fo,
                                 status, counter, s);

@@ -421,9 +421,11 @@ int backward_ctas_per_sm(bool normals, int n_flow, int ray_tile, int threads);
 // Alpha-compositing variant (Sec. 3.3): work items are 32-ray tiles, K <= 256 per
 // view (maxK: the batch's largest K).
 int ac_rays_per_item();
-int ac_fwd_rays_per_item();
+int ac_fwd_run(long long total_rays, int sms);  // forward rays per warp for a batch of total_rays
+int ac_fwd_rays_per_item(int run);
 cudaError_t launch_forward_ac(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
-                              int n_flow, int maxK, const FwdOut& o, int* status, int* counter, cudaStream_t st);
+                              int n_flow, int maxK, const FwdOut& o, int run, int* status, int* counter,
+                              cudaStream_t st);
 cudaError_t launch_backward_ac(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
                                int n_flow, int maxK, const BwdIn& in, const BwdOut& out, int* status, int* counter,
                                cudaStream_t st);
