@@ -578,6 +578,27 @@ fmb_status fmb_loss_attribution(const fmb_params* params, int n_objects, const l
     zj.n[0] = pl.n_gauss;
     cudaError_t e = fmb::launch_zero(zj, s);
     if (e != cudaSuccess) return cuda_fail(e, "zeroing launch");
+    if (params->variant == 0) {
+      // two-parameter model: the backward's blocking (two Gaussians per thread)
+      const int T = pl.bwd_threads;
+      const int tile = fmb::attribution2_ray_tile(T);
+      for (fmb::Batch b : pl.fwd) {
+        for (int i = 0; i < b.n_views; ++i) {
+          const BwdBlocking bk = bwd_blocking(b.v[i].K, T);
+          b.v[i].n_tiles = (b.v[i].P + tile - 1) / tile;
+          b.v[i].n_gblocks = bk.n_gb;
+          b.v[i].GB = bk.GB;
+          b.v[i].S = bk.S;
+        }
+        order_items(b, [&](const fmb::DevView& v) { return static_cast<double>(v.GB); },
+                    [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles) * v.n_gblocks; });
+        e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, nullptr, s);
+        if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
+        e = fmb::launch_attribution2(b, sc, c, records, T, tile, saved, ray_loss, attribution, s);
+        if (e != cudaSuccess) return cuda_fail(e, "attribution launch");
+      }
+      return FMB_OK;
+    }
     const int per = fmb::attribution_rays_per_item();
     const int blk = 32 * (pl.maxK <= 64 ? 2 : (pl.maxK <= 128 ? 4 : 8));
     for (fmb::Batch b : pl.fwd) {
@@ -589,7 +610,7 @@ fmb_status fmb_loss_attribution(const fmb_params* params, int n_objects, const l
                   [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles) * v.n_gblocks; });
       e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, nullptr, s);
       if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
-      e = fmb::launch_attribution(b, sc, c, records, params->variant, pl.maxK, saved, ray_loss, attribution, s);
+      e = fmb::launch_attribution_ac(b, sc, c, records, pl.maxK, ray_loss, attribution, s);
       if (e != cudaSuccess) return cuda_fail(e, "attribution launch");
     }
     return FMB_OK;

@@ -434,11 +434,18 @@ int points_rays_per_item(int variant);
 cudaError_t launch_points(const Batch& b, const Scene& s, const Consts& c, const float4* records, int variant,
                           int maxK, const float* depth, const float* saved, float* points, float* normal_tf,
                           float* normal_scr, float* quality, cudaStream_t st);
-// Loss attribution (Sec. 8, Eq. 19): work items of attribution_rays_per_item() rays x
-// one block of up to 256 Gaussians (32 x M, M from the batch's largest K).
+// Loss attribution (Sec. 8, Eq. 19).  Two-parameter model: work items of ray_tile
+// rays x a block of GB Gaussians (the backward's blocking, two Gaussians per thread);
+// threads <= kAtt2MaxThreads.
+constexpr int kAtt2MaxThreads = 256;
+int attribution2_ray_tile(int threads);
+cudaError_t launch_attribution2(const Batch& b, const Scene& s, const Consts& c, const float4* records, int threads,
+                                int ray_tile, const float* saved, const float* loss, float* out, cudaStream_t st);
+// Alpha compositing: work items of attribution_rays_per_item() rays x one block of up
+// to 256 Gaussians (32 x M, M from the batch's largest K).
 int attribution_rays_per_item();
-cudaError_t launch_attribution(const Batch& b, const Scene& s, const Consts& c, const float4* records, int variant,
-                               int maxK, const float* saved, const float* loss, float* out, cudaStream_t st);
+cudaError_t launch_attribution_ac(const Batch& b, const Scene& s, const Consts& c, const float4* records, int maxK,
+                                  const float* loss, float* out, cudaStream_t st);
 cudaError_t launch_backward_reduce(const Batch& b, int n_flow, long long n_gauss, int n_poses,
                                    const BwdOut& out, cudaStream_t st);
 

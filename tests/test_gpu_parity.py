@@ -412,6 +412,27 @@ def test_loss_attribution_parity(variant):
         assert abs(a.sum() - loss.astype(np.float64).sum()) <= 1e-4 * loss.sum()
 
 
+@pytest.mark.parametrize("variant", [0, 1])
+def test_loss_attribution_full_size(variant):
+    """The 16-view 320x240 orbit at full size in the bench's configuration: the
+    normalised weights of a ray sum to one (the softmax of Eq. 3 on every ray; the
+    alpha-compositing weights w / W wherever W > 0, i.e. alpha > 0), so the
+    attribution adds up to the loss of those rays; no entry is negative; a zero loss
+    attributes nothing."""
+    s = synth.config1()
+    params = fmb.default_params(n_flow=1, variant=variant)
+    gpu, r, dev = gpu_forward(s, params)
+    loss = np.random.default_rng(11).uniform(0.0, 1.0, s.n_pixels).astype(np.float32)
+    loss[::7] = 0.0
+    a = r.attribution(*dev, torch.as_tensor(loss, device="cuda")).cpu().numpy().astype(np.float64)
+    covered = gpu["alpha"].reshape(-1) > 0.0 if variant == 1 else np.ones(s.n_pixels, dtype=bool)
+    want = float(loss.astype(np.float64)[covered].sum())
+    assert np.all(a >= 0.0)
+    assert abs(a.sum() - want) <= 1e-4 * want, (a.sum(), want)
+    z = r.attribution(*dev, torch.zeros(s.n_pixels, device="cuda")).cpu().numpy()
+    assert np.all(z == 0.0)
+
+
 # ------------------------------------------------------------ per-Gaussian colours
 
 @pytest.mark.parametrize("variant,deterministic", [(0, False), (0, True), (1, False), (1, True)])
