@@ -1,0 +1,64 @@
+"""The host-fed pipeline (copies overlapped with neighbouring steps' kernels) gives
+each step exactly the results of a plain device-resident call on that step's
+inputs: same kernels, same tiles, so the comparison is bitwise."""
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2308_14737_gb300 import fmb, pipeline, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_14737_gb300 import build
+
+    build.build()
+    fmb.load_library()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_host_pipeline_matches_plain_calls(variant):
+    s = synth.config1(K=60, n_views=4, W=64, H=48)
+    n_flow = 1
+    params = fmb.default_params(n_flow=n_flow, variant=variant)
+    P = s.n_pixels
+    rng = np.random.default_rng(3)
+    steps = []
+    for i in range(5):  # every step has its own inputs (moved means, new upstream planes)
+        means = (s.means + 0.01 * i).astype(np.float32)
+        ups = synth.upstream_grads(rng, P, n_flow)
+        steps.append(dict(means=means, chol=s.chol, weights=s.weights, poses=s.poses, g_depth=ups[0],
+                          g_alpha=ups[1], g_normal=ups[2].reshape(-1), g_flow=ups[3].reshape(-1)))
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).pin_memory()
+    h_in = [{k: pin(v) for k, v in st.items()} for st in steps]
+    pipe = pipeline.HostPipeline(s.obj_offsets, s.views, len(s.poses), params, h_in[0], want_pose=True)
+    h_out = [pipe.host_outputs() for _ in steps]
+    events = [pipe.submit(h_in[i], h_out[i]) for i in range(2)]
+    events[0].synchronize()
+    for i in range(2, len(steps)):  # a slot is reused only after its previous step is out
+        events[i - 2].synchronize()
+        events.append(pipe.submit(h_in[i], h_out[i]))
+    torch.cuda.synchronize()
+
+    r = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), params)
+    for i, st in enumerate(steps):
+        d = {k: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float32, device="cuda").reshape(-1)
+             for k, v in st.items()}
+        out = r.forward(d["means"], d["chol"], d["weights"], d["poses"])
+        g = r.backward(d["means"], d["chol"], d["weights"], d["poses"], d["g_depth"], d["g_alpha"], d["g_normal"],
+                       d["g_flow"], want_pose=True)
+        torch.cuda.synchronize()
+        want = dict(depth=out["depth"], alpha=out["alpha"], normal=out["normal"], flow=out["flow"],
+                    grad_means=g["means"], grad_chol=g["chol"], grad_weights=g["weights"], grad_poses=g["poses"])
+        for k, v in want.items():
+            a, b = h_out[i][k].numpy(), v.cpu().numpy()
+            # the gradients are sums of fp32 atomics (order-dependent): equal up to rounding
+            if k.startswith("grad"):
+                assert np.allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max()), (i, k)
+            else:
+                assert np.array_equal(a, b), (i, k)
