@@ -47,8 +47,7 @@ def test_host_pipeline_matches_plain_calls(variant):
 
     r = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), params)
     for i, st in enumerate(steps):
-        d = {k: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float32, device="cuda").reshape(-1)
-             for k, v in st.items()}
+        d = {k: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float32, device="cuda") for k, v in st.items()}
         out = r.forward(d["means"], d["chol"], d["weights"], d["poses"])
         g = r.backward(d["means"], d["chol"], d["weights"], d["poses"], d["g_depth"], d["g_alpha"], d["g_normal"],
                        d["g_flow"], want_pose=True)
