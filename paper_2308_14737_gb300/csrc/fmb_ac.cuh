@@ -5,7 +5,6 @@
 // sums of delta for the transmittance.
 #pragma once
 
-#include "fmb_f32x2.cuh"
 #include "fmb_internal.cuh"
 
 namespace fmb {
@@ -161,63 +160,31 @@ __device__ __forceinline__ AcSums ac_render_ray(const float4* __restrict__ rec, 
   int prev[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) prev[m] = key[m] != kNoKey ? static_cast<int>(key[m] & 0xffffffffu) : -1;
-  // Slots m and m + 1 are evaluated together, one per lane of packed FP32x2
-  // arithmetic (the same operation sequence as the scalar pair geometry, so each
-  // value is bitwise the scalar one).
-  const f2 v0 = dup(v[0]), v1 = dup(v[1]), v2 = dup(v[2]), vl0 = dup(vl[0]), vl1 = dup(vl[1]), vl2 = dup(vl[2]);
-  const f2 K3v = dup(k.K3);
 #pragma unroll
-  for (int m = 0; m < M; m += 2) {
-    const int e0 = (m << 5) | lane, e1 = ((m + 1) << 5) | lane;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      t[m + h] = 0.f;
-      dl[m + h] = 0.f;
-      n[m + h][0] = n[m + h][1] = n[m + h][2] = 0.f;
-      key[m + h] = kNoKey;
-    }
-    if (e0 < K) {  // e1 > e0: slot m + 1 is real only if slot m is
-      const bool has1 = e1 < K;
-      const GaussRec ga = unpack_rec(rec[kRecFloat4 * e0], rec[kRecFloat4 * e0 + 1], rec[kRecFloat4 * e0 + 2],
-                                     rec[kRecFloat4 * e0 + 3]);
-      // a copy keeps the unused lane finite; its values are dropped
-      const GaussRec gb = has1 ? unpack_rec(rec[kRecFloat4 * e1], rec[kRecFloat4 * e1 + 1],
-                                            rec[kRecFloat4 * e1 + 2], rec[kRecFloat4 * e1 + 3])
-                               : ga;
-      const GaussRec2 gr = pair_rec(ga, gb);
-      const PairGeom2 G = pair_geom2(gr, v0, v1, v2, vl0, vl1, vl2);
-      const f2 d2 = ex2_2(fma2(G.q, K3v, gr.l2));  // delta (Eq. 4)
-      float nn[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  for (int m = 0; m < M; ++m) {
+    const int e = (m << 5) | lane;
+    t[m] = 0.f;
+    dl[m] = 0.f;
+    n[m][0] = n[m][1] = n[m][2] = 0.f;
+    key[m] = kNoKey;
+    if (e < K) {
+      const GaussRec g = unpack_rec(rec[kRecFloat4 * e], rec[kRecFloat4 * e + 1], rec[kRecFloat4 * e + 2],
+                                    rec[kRecFloat4 * e + 3]);
+      const PairGeom G = pair_geom(g.L, g.b, g.mh, g.nbl, v[0], v[1], v[2], vl[0], vl[1], vl[2]);
+      t[m] = G.t;
+      dl[m] = ex2_approx(fmaf(G.q, k.K3, g.l2));  // delta (Eq. 4)
       if (NORMALS) {
-        const f2 g0 = mul2(gr.L[0], G.u0);
-        const f2 g1 = fma2(gr.L[2], G.u1, mul2(gr.L[1], G.u0));
-        const f2 g2 = fma2(gr.L[5], G.u2, fma2(gr.L[4], G.u1, mul2(gr.L[3], G.u0)));
-        const f2 gg = fma2(g2, g2, fma2(g1, g1, mul2(g0, g0)));
-        const f2 rs = pk(rsqrt_approx(fmaxf(lo(gg), 1e-30f)), rsqrt_approx(fmaxf(hi(gg), 1e-30f)));
-        const f2 n0 = mul2(g0, rs), n1 = mul2(g1, rs), n2 = mul2(g2, rs);
-        nn[0][0] = lo(n0);
-        nn[0][1] = lo(n1);
-        nn[0][2] = lo(n2);
-        nn[1][0] = hi(n0);
-        nn[1][1] = hi(n1);
-        nn[1][2] = hi(n2);
+        const float g0 = g.L[0] * G.u0;
+        const float g1 = fmaf(g.L[2], G.u1, g.L[1] * G.u0);
+        const float g2 = fmaf(g.L[5], G.u2, fmaf(g.L[4], G.u1, g.L[3] * G.u0));
+        const float rs = rsqrt_approx(fmaxf(fmaf(g2, g2, fmaf(g1, g1, g0 * g0)), 1e-30f));
+        n[m][0] = g0 * rs;
+        n[m][1] = g1 * rs;
+        n[m][2] = g2 * rs;
       }
-      const float tt[2] = {lo(G.t), hi(G.t)}, dd[2] = {lo(d2), hi(d2)};
-      const int ee[2] = {e0, e1};
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (h == 1 && !has1) break;
-        t[m + h] = tt[h];
-        dl[m + h] = dd[h];
-        if (NORMALS) {
-          n[m + h][0] = nn[h][0];
-          n[m + h][1] = nn[h][1];
-          n[m + h][2] = nn[h][2];
-        }
-        sd[ee[h]] = dd[h];
-        sT[ee[h]] = tt[h];  // for the reordering below (overwritten by T afterwards)
-        key[m + h] = (static_cast<unsigned long long>(order_bits(tt[h])) << 32) | static_cast<unsigned>(ee[h]);
-      }
+      sd[e] = dl[m];
+      sT[e] = G.t;  // for the reordering below (overwritten by T afterwards)
+      key[m] = (static_cast<unsigned long long>(order_bits(G.t)) << 32) | static_cast<unsigned>(e);
     }
   }
   __syncwarp();
