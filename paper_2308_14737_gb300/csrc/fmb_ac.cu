@@ -45,8 +45,10 @@ int ac_fwd_run(long long total_rays, int sms) {
 int ac_fwd_rays_per_item(int run) { return kAcWarps * run; }
 
 // ------------------------------------------------------------------ forward
+// Register budget: 5 resident CTAs (20 warps) per SM for M <= 4 -- 96 registers, no
+// spills, 6.5 % faster on the orbit than the unconstrained 127 -- and 4 for M = 8.
 template <bool NORMALS, int NFLOW, int M>
-__global__ void __launch_bounds__(kAcThreads) forward_ac_kernel(const __grid_constant__ Batch batch, Scene s,
+__global__ void __launch_bounds__(kAcThreads, M >= 8 ? 4 : 5) forward_ac_kernel(const __grid_constant__ Batch batch, Scene s,
                                                                 Consts k, const float4* __restrict__ records,
                                                                 FwdOut out, int run, int* status, int* counter) {
   extern __shared__ float4 ac_smem[];  // records [32 M][4 float4] | per warp: sd, sw, sT [32 M floats each]
