@@ -669,11 +669,65 @@ def oracle_sample(workload, s, ups):
     return sub, u, what + ", forward + backward"
 
 
+def cpu_model() -> str:
+    """The host CPU's model name as /proc/cpuinfo gives it (x86: "model name";
+    Arm: implementer and part numbers), or the platform string."""
+    import platform
+
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return platform.processor() or platform.machine()
+    for key in ("model name", "Model"):
+        for line in info:
+            if line.startswith(key) and ":" in line:
+                return line.split(":", 1)[1].strip()
+    fields = {}
+    for line in info:
+        if ":" in line:
+            k, v = (x.strip() for x in line.split(":", 1))
+            fields.setdefault(k, v)
+    if "CPU part" in fields:
+        return f"{platform.machine()} CPU implementer {fields.get('CPU implementer', '?')} part {fields['CPU part']}"
+    return platform.machine()
+
+
+def oracle_single_thread(s, ups, args):
+    """The oracle on one thread over a small sample (the central 64x48 crop of the
+    first view), forward + backward, in pairs/s."""
+    import oracle
+
+    from paper_2308_14737_gb300 import synth
+
+    wl = WORKLOADS[args.workload]
+    nf = wl["n_flow"]
+    v0 = {k: v for k, v in s.views[0].items() if k != "pix_offset"}
+    first = synth.make_scene([(s.means[s.object_slice(v0["object"])], s.chol[s.object_slice(v0["object"])],
+                               s.weights[s.object_slice(v0["object"])])], [dict(v0, object=0)], s.poses)
+    sub = synth.crop_views(first, 64, 48) if v0.get("rays") is None else first
+    gd, ga, gn, gf = synth.upstream_grads(np.random.default_rng(7), sub.n_pixels, max(nf, 1))
+    var = 1 if args.variant == "ac" else 0
+    t0 = time.perf_counter()
+    oracle.render_scene(sub, n_flow=nf, variant=var, n_threads=1)
+    oracle.backward_scene(sub, gd, ga, gn.reshape(-1) if wl["normals"] else None, gf.reshape(-1) if nf else None,
+                          n_flow=nf, variant=var, n_threads=1)
+    dt = time.perf_counter() - t0
+    return {"value": sub.n_pairs / dt, "unit": "pairs/s", "threads": 1,
+            "sample": f"{sub.n_pixels} rays of the first view x K={sub.means.shape[0]}, forward + backward"}
+
+
 def cpu_baseline(s, ups, renderer, grads, args):
     """The FP64 oracle (test infrastructure, not tuned) timed on the host cores on
     one full step of the orbit workload, and compared with the GPU result of that
     step; for the other workloads, on a bounded sample of it (no comparison here:
-    the parity tests cover those)."""
+    the parity tests cover those).  Also: the CPU model and a single-thread rate."""
+    out = cpu_baseline_all_cores(s, ups, renderer, grads, args)
+    out["cpu_model"] = cpu_model()
+    out["single_thread"] = oracle_single_thread(s, ups, args)
+    return out
+
+
+def cpu_baseline_all_cores(s, ups, renderer, grads, args):
     import oracle
 
     oracle.build()

@@ -365,3 +365,17 @@ class FmbRender(torch.autograd.Function):
 def render(renderer: Renderer, means, chol, weights, poses):
     """Differentiable render through ``FmbRender``."""
     return FmbRender.apply(renderer, means, chol, weights, poses)
+
+
+def pose_twist_grad(poses, grad_poses):
+    """6-DoF pose gradients from the library's free-matrix ones: for each pose [R | t]
+    perturbed on the left as exp(xi^) [R | t], xi = (rho, omega), the gradient with
+    respect to (rho, omega) is (t_bar, vee(R_bar R^T - (R_bar R^T)^T) + t x t_bar).
+    poses, grad_poses: [n][12] (R row-major, then t); returns [n][6]."""
+    P = torch.as_tensor(poses).reshape(-1, 12)
+    G = torch.as_tensor(grad_poses).reshape(-1, 12).to(P.dtype)
+    R, t = P[:, :9].reshape(-1, 3, 3), P[:, 9:]
+    gR, gt = G[:, :9].reshape(-1, 3, 3), G[:, 9:]
+    M = gR @ R.transpose(1, 2)
+    om = torch.stack([M[:, 2, 1] - M[:, 1, 2], M[:, 0, 2] - M[:, 2, 0], M[:, 1, 0] - M[:, 0, 1]], dim=1)
+    return torch.cat([gt, om + torch.linalg.cross(t, gt, dim=1)], dim=1)

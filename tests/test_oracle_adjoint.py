@@ -179,3 +179,22 @@ def test_colour_adjoint_matches_differences_and_autograd(oracle_mod, variant):
                          ("chol", tc.grad, g["chol"]), ("weights", tl.grad, g["weights"])):
         tg = tg.numpy()
         assert np.max(np.abs(tg - og)) <= 1e-10 * max(1.0, np.max(np.abs(tg))), name
+
+
+def test_package_twist_gradient_matches_oracle(oracle_mod):
+    """The package's batched 6-DoF pose gradient (host/torch) against the oracle's,
+    which the rotation-difference test above pins."""
+    import torch
+
+    from paper_2308_14737_gb300 import fmb
+
+    rng = np.random.default_rng(12)
+    poses, grads = [], []
+    for _ in range(5):
+        q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        poses.append(np.concatenate([q.reshape(-1), rng.normal(size=3)]))
+        grads.append(rng.normal(size=12))
+    poses, grads = np.array(poses), np.array(grads)
+    got = fmb.pose_twist_grad(torch.as_tensor(poses), torch.as_tensor(grads)).numpy()
+    for i in range(5):
+        assert np.allclose(got[i], oracle_mod.pose_twist_grad(poses[i], grads[i]), rtol=1e-12, atol=1e-12)
