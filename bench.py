@@ -125,23 +125,23 @@ def dist_env():
 
 
 WORKLOADS = {
-    "orbit": dict(config=1, n_flow=1, normals=1, want_pose=True, desc=WORKLOAD),
-    "single": dict(config=0, n_flow=0, normals=0, want_pose=False,
+    "orbit": dict(scene="object_orbit", n_flow=1, normals=1, want_pose=True, desc=WORKLOAD),
+    "single": dict(scene="single_view", n_flow=0, normals=0, want_pose=False,
                    desc="single view 64x64 (f=64), camera at distance 4, K=40 Gaussians, depth+alpha planes, "
                         "backward w.r.t. means, Cholesky factors and weights"),
-    "ragged": dict(config=2, n_flow=0, normals=1, want_pose=True,
+    "ragged": dict(scene="ragged_batch", n_flow=0, normals=1, want_pose=True,
                    desc="ragged batch: 64 objects, K ~ U{20..400}, square images of side in {64,128,256,512} "
                         "(f = side), 4 sphere views each (256 views), depth+alpha+normal planes, backward "
                         "w.r.t. all Gaussian parameters and poses"),
-    "recon": dict(config=3, n_flow=2, normals=0, want_pose=False,
+    "recon": dict(scene="reconstruction", n_flow=2, normals=0, want_pose=False,
                   desc="reconstruction workload: 100 sphere views 640x480 (f=640), K=256 Gaussians, "
                        "depth+alpha planes, flow to the next and the previous view, backward w.r.t. means, "
                        "Cholesky factors and weights"),
-    "minibatch": dict(config=3, n_flow=2, normals=0, want_pose=False, rays=50000,
+    "minibatch": dict(scene="reconstruction", n_flow=2, normals=0, want_pose=False, rays=50000,
                       desc="ray minibatch: 50 000 rays drawn uniformly across the 100 sphere views 640x480 (f=640) "
                            "of the reconstruction workload, K=256, depth+alpha planes, flow to the next and the "
                            "previous view, backward w.r.t. means, Cholesky factors and weights"),
-    "largek": dict(config=4, n_flow=1, normals=1, want_pose=True,
+    "largek": dict(scene="large_k", n_flow=1, normals=1, want_pose=True,
                    desc="large-K stress: 8 sphere views 1024x768 (f=1024), K=4096 diagonal-precision Gaussians, "
                         "all four planes, backward w.r.t. Gaussians and poses"),
 }
@@ -151,7 +151,7 @@ def scene_and_inputs(seed=0, workload="orbit"):
     from paper_2308_14737_gb300 import synth
 
     wl = WORKLOADS[workload]
-    s = synth.CONFIGS[wl["config"]](seed=seed)
+    s = synth.SCENES[wl["scene"]](seed=seed)
     if wl.get("rays"):
         s = synth.ray_batch(s, wl["rays"], seed=seed)
     rng = np.random.default_rng(seed + 1)

@@ -36,12 +36,12 @@ __all__ = [
     "ring_positions",
     "sphere_positions",
     "make_scene",
-    "config0",
-    "config1",
-    "config2",
-    "config3",
-    "config4",
-    "CONFIGS",
+    "single_view",
+    "object_orbit",
+    "ragged_batch",
+    "reconstruction",
+    "large_k",
+    "SCENES",
     "ray_batch",
     "view_entries",
 ]
@@ -180,25 +180,25 @@ def _view(W, H, f, obj, pose, flow_target=(-1, -1)):
                 object=int(obj), pose=int(pose), flow_target=tuple(flow_target))
 
 
-def config0(seed: int = 0, K: int = 40, W: int = 64, H: int = 64) -> Scene:
+def single_view(seed: int = 0, K: int = 40, W: int = 64, H: int = 64) -> Scene:
     """Single view, 64x64, f=64, camera at (0,0,-4) looking at the origin, K=40."""
     rng = np.random.default_rng(seed)
     obj = random_gaussians(rng, K, "cholesky")
     pose = look_at_pose((0.0, 0.0, -4.0))
-    return make_scene([obj], [_view(W, H, W, 0, 0)], [pose], name="config0_single_view_64x64_K40")
+    return make_scene([obj], [_view(W, H, W, 0, 0)], [pose], name="single_view_64x64_K40")
 
 
-def config1(seed: int = 0, K: int = 100, n_views: int = 16, W: int = 320, H: int = 240) -> Scene:
+def object_orbit(seed: int = 0, K: int = 100, n_views: int = 16, W: int = 320, H: int = 240) -> Scene:
     """Object orbit: 16 views at 320x240 (f = W) on the y=0 ring of radius 4, K=100,
     forward flow to the next view (the ring wraps)."""
     rng = np.random.default_rng(seed)
     obj = random_gaussians(rng, K, "cholesky")
     poses = [look_at_pose(p) for p in ring_positions(n_views)]
     views = [_view(W, H, W, 0, i, ((i + 1) % n_views, -1)) for i in range(n_views)]
-    return make_scene([obj], views, poses, name=f"config1_orbit_{n_views}x{W}x{H}_K{K}")
+    return make_scene([obj], views, poses, name=f"orbit_{n_views}x{W}x{H}_K{K}")
 
 
-def config2(seed: int = 0, n_objects: int = 64, views_per_object: int = 4,
+def ragged_batch(seed: int = 0, n_objects: int = 64, views_per_object: int = 4,
             K_range=(20, 400), sides=(64, 128, 256, 512)) -> Scene:
     """Ragged batch: objects with K ~ U{20..400}, square sides from {64..512},
     4 random sphere views each (f = side); no flow."""
@@ -211,10 +211,10 @@ def config2(seed: int = 0, n_objects: int = 64, views_per_object: int = 4,
         for p in sphere_positions(rng, views_per_object):
             poses.append(look_at_pose(p))
             views.append(_view(side, side, side, o, len(poses) - 1))
-    return make_scene(objects, views, poses, name=f"config2_ragged_{n_objects}obj")
+    return make_scene(objects, views, poses, name=f"ragged_{n_objects}obj")
 
 
-def config3(seed: int = 0, n_views: int = 100, K: int = 256, W: int = 640, H: int = 480) -> Scene:
+def reconstruction(seed: int = 0, n_views: int = 100, K: int = 256, W: int = 640, H: int = 480) -> Scene:
     """Reconstruction step: 100 sphere views at 640x480 (f=640), K=256, flow to the
     next view (i+1) and the previous one (i-1) where they exist."""
     rng = np.random.default_rng(seed)
@@ -224,20 +224,21 @@ def config3(seed: int = 0, n_views: int = 100, K: int = 256, W: int = 640, H: in
     for i in range(n_views):
         ft = (i + 1 if i + 1 < n_views else -1, i - 1 if i > 0 else -1)
         views.append(_view(W, H, W, 0, i, ft))
-    return make_scene([obj], views, poses, name=f"config3_recon_{n_views}x{W}x{H}_K{K}")
+    return make_scene([obj], views, poses, name=f"recon_{n_views}x{W}x{H}_K{K}")
 
 
-def config4(seed: int = 0, K: int = 4096, n_views: int = 8, W: int = 1024, H: int = 768) -> Scene:
+def large_k(seed: int = 0, K: int = 4096, n_views: int = 8, W: int = 1024, H: int = 768) -> Scene:
     """Large-K stress: K=4096 diagonal-precision Gaussians, 8 sphere views at
     1024x768 (f=1024), forward flow to the next view."""
     rng = np.random.default_rng(seed)
     obj = random_gaussians(rng, K, "diag")
     poses = [look_at_pose(p) for p in sphere_positions(rng, n_views)]
     views = [_view(W, H, W, 0, i, ((i + 1) % n_views, -1)) for i in range(n_views)]
-    return make_scene([obj], views, poses, name=f"config4_largeK_{n_views}x{W}x{H}_K{K}")
+    return make_scene([obj], views, poses, name=f"largeK_{n_views}x{W}x{H}_K{K}")
 
 
-CONFIGS = {0: config0, 1: config1, 2: config2, 3: config3, 4: config4}
+SCENES = {"single_view": single_view, "object_orbit": object_orbit, "ragged_batch": ragged_batch,
+          "reconstruction": reconstruction, "large_k": large_k}
 
 
 def ray_batch(scene: Scene, n_rays: int, seed: int = 0) -> Scene:

@@ -55,7 +55,7 @@ def test_default_params_and_version(fmb):
 
 
 def test_workspace_bytes(fmb):
-    s = synth.config1(K=10, n_views=3, W=8, H=6)
+    s = synth.object_orbit(K=10, n_views=3, W=8, H=6)
     p = fmb.default_params()
     n = fmb.fmb_workspace_bytes(p, s.obj_offsets, s.views)
     assert n >= 256 + 48 * 30 and n % 256 == 0
@@ -67,7 +67,7 @@ def test_workspace_bytes_stored_pairs(fmb):
     """store_pairs adds three per-pair arrays of sum_v P_v x (K rounded up to a
     multiple of 4) floats each (the stride rounded up to 64 floats)."""
     for K in (10, 11, 12, 13):
-        s = synth.config1(K=K, n_views=3, W=8, H=6)
+        s = synth.object_orbit(K=K, n_views=3, W=8, H=6)
         p = fmb.default_params()
         n0 = fmb.fmb_workspace_bytes(p, s.obj_offsets, s.views)
         p.store_pairs = 1

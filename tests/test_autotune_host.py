@@ -8,9 +8,9 @@ def test_layout_key_groups_by_shape_class():
 
     build.build()
     p = fmb.default_params(n_flow=1)
-    a = synth.config1(K=100, n_views=16, W=320, H=240)
-    b = synth.config1(seed=5, K=110, n_views=16, W=320, H=240)  # same log2 buckets
-    c = synth.config1(K=400, n_views=16, W=320, H=240)
+    a = synth.object_orbit(K=100, n_views=16, W=320, H=240)
+    b = synth.object_orbit(seed=5, K=110, n_views=16, W=320, H=240)  # same log2 buckets
+    c = synth.object_orbit(K=400, n_views=16, W=320, H=240)
     ka = autotune.layout_key(a.obj_offsets, a.views, p, True)
     assert ka == autotune.layout_key(b.obj_offsets, b.views, p, True)
     assert ka != autotune.layout_key(c.obj_offsets, c.views, p, True)

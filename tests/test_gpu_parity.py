@@ -50,29 +50,29 @@ def _full_check(scene, n_flow, normals=True, deterministic=False, want_pose=True
     return stats, errs, g
 
 
-def test_config0_single_view_64x64_K40():
-    s = synth.config0()
+def test_single_view_64x64_K40():
+    s = synth.single_view()
     _full_check(s, n_flow=0)
 
 
 def test_orbit_small_with_flow_and_pose():
-    s = synth.config1(K=100, n_views=4, W=64, H=48)
+    s = synth.object_orbit(K=100, n_views=4, W=64, H=48)
     _full_check(s, n_flow=1)
 
 
 def test_two_flow_slots_with_missing_targets():
-    s = synth.config3(n_views=3, K=37, W=40, H=30)
+    s = synth.reconstruction(n_views=3, K=37, W=40, H=30)
     _full_check(s, n_flow=2)
 
 
 def test_normals_off():
-    s = synth.config1(K=30, n_views=2, W=33, H=17)
+    s = synth.object_orbit(K=30, n_views=2, W=33, H=17)
     _full_check(s, n_flow=1, normals=False)
 
 
 @pytest.mark.parametrize("rpt", [1, 2, 4])
 def test_rays_per_thread_variants(rpt):
-    s = synth.config1(K=45, n_views=2, W=37, H=29)
+    s = synth.object_orbit(K=45, n_views=2, W=37, H=29)
     _full_check(s, n_flow=1, fwd_rays_per_thread=rpt)
 
 
@@ -99,14 +99,14 @@ def test_ragged_objects_and_edge_sizes():
 def test_persistent_launch(deterministic):
     """Persistent mode: resident CTAs pop (view, tile) items, most expensive first."""
     _full_check(_ragged_scene(), n_flow=1, use_persistent=1, deterministic=deterministic)
-    _full_check(synth.config1(K=100, n_views=5, W=64, H=48), n_flow=1, use_persistent=1,
+    _full_check(synth.object_orbit(K=100, n_views=5, W=64, H=48), n_flow=1, use_persistent=1,
                 deterministic=deterministic)
 
 
 def test_persistent_matches_grid_launch_bitwise():
     """Work items compute the same thing in either launch mode: forward planes and
     the deterministic backward agree bit for bit."""
-    s = synth.config2(n_objects=6, views_per_object=2, sides=(32, 48, 64))
+    s = synth.ragged_batch(n_objects=6, views_per_object=2, sides=(32, 48, 64))
     rng = np.random.default_rng(0)
     res = []
     for pers in (0, 1):
@@ -122,7 +122,7 @@ def test_persistent_matches_grid_launch_bitwise():
 
 
 def test_deterministic_mode_is_bitwise_reproducible():
-    s = synth.config1(K=100, n_views=3, W=48, H=40)
+    s = synth.object_orbit(K=100, n_views=3, W=48, H=40)
     _, _, g1 = _full_check(s, n_flow=1, deterministic=True)
     _, _, g2 = _full_check(s, n_flow=1, deterministic=True)
     for k in g1:
@@ -134,7 +134,7 @@ def test_deterministic_mode_is_bitwise_reproducible():
 
 @pytest.mark.parametrize("ray_tile,threads", [(32, 64), (128, 128), (512, 96), (1024, 160), (320, 160), (450, 160), (33, 32)])
 def test_backward_tilings(ray_tile, threads):
-    s = synth.config1(K=70, n_views=2, W=50, H=31)
+    s = synth.object_orbit(K=70, n_views=2, W=50, H=31)
     _full_check(s, n_flow=1, bwd_ray_tile=ray_tile, bwd_threads=threads)
 
 
@@ -142,12 +142,12 @@ def test_gaussian_blocks_over_128():
     """K = 300 splits into several Gaussian blocks per CTA; K = 129 leaves a block
     with one Gaussian."""
     for K in (129, 300):
-        s = synth.config1(K=K, n_views=2, W=24, H=20)
+        s = synth.object_orbit(K=K, n_views=2, W=24, H=20)
         _full_check(s, n_flow=1, deterministic=(K == 300))
 
 
 def test_permutation_invariance():
-    s = synth.config1(K=60, n_views=2, W=40, H=30)
+    s = synth.object_orbit(K=60, n_views=2, W=40, H=30)
     p = fmb.default_params(n_flow=1)
     a, _, _ = gpu_forward(s, p)
     perm = np.random.default_rng(3).permutation(60)
@@ -179,13 +179,13 @@ def _sampled_full_size(scene, n_flow, n_per_view, seed=0, deterministic=False, p
 
 
 def test_orbit_full_size_16x320x240_K100_sampled():
-    _sampled_full_size(synth.config1(), n_flow=1, n_per_view=400)
+    _sampled_full_size(synth.object_orbit(), n_flow=1, n_per_view=400)
 
 
 def test_orbit_full_size_dense_gradients():
     """Every pixel of the 16-view 320x240 K=100 orbit contributes to the gradients
     (the benchmark's workload and launch configuration)."""
-    s = synth.config1()
+    s = synth.object_orbit()
     params = fmb.default_params(n_flow=1)
     gpu, r, dev = gpu_forward(s, params)
     ref = oracle.render_scene(s, n_flow=1)
@@ -196,19 +196,19 @@ def test_orbit_full_size_dense_gradients():
 
 
 def test_large_K4096_8x1024x768_sampled():
-    _sampled_full_size(synth.config4(), n_flow=1, n_per_view=48)
+    _sampled_full_size(synth.large_k(), n_flow=1, n_per_view=48)
 
 
 def test_ragged_batch_64_objects_sampled():
-    _sampled_full_size(synth.config2(), n_flow=0, n_per_view=64, deterministic=True)
+    _sampled_full_size(synth.ragged_batch(), n_flow=0, n_per_view=64, deterministic=True)
 
 
 def test_ragged_batch_64_objects_persistent_sampled():
-    _sampled_full_size(synth.config2(), n_flow=0, n_per_view=48, persistent=True)
+    _sampled_full_size(synth.ragged_batch(), n_flow=0, n_per_view=48, persistent=True)
 
 
 def test_device_status_is_clear_and_outputs_finite():
-    s = synth.config1(K=20, n_views=2, W=16, H=12)
+    s = synth.object_orbit(K=20, n_views=2, W=16, H=12)
     gpu, r, _ = gpu_forward(s, fmb.default_params())
     for k in ("depth", "alpha", "normal", "flow", "saved"):
         assert np.all(np.isfinite(gpu[k])), k
@@ -221,8 +221,8 @@ def test_stored_intermediate_adjoint(deterministic):
     and the backward reads them; same tolerances against the oracle, and the
     gradients agree with the recomputing adjoint (only the rounding of the log2
     weight's last add differs).  Odd K (the rows are padded to even) included."""
-    for scene, nf in ((synth.config1(K=101, n_views=3, W=40, H=30), 1), (_ragged_scene(), 1),
-                      (synth.config0(), 0)):
+    for scene, nf in ((synth.object_orbit(K=101, n_views=3, W=40, H=30), 1), (_ragged_scene(), 1),
+                      (synth.single_view(), 0)):
         _, _, gs = _full_check(scene, n_flow=nf, store_pairs=1, deterministic=deterministic,
                                normals=(nf == 1))
         _, _, gr = _full_check(scene, n_flow=nf, deterministic=deterministic, normals=(nf == 1))
@@ -231,7 +231,7 @@ def test_stored_intermediate_adjoint(deterministic):
 
 
 def test_stored_intermediate_adjoint_full_size_sampled():
-    s = synth.config1()
+    s = synth.object_orbit()
     params = fmb.default_params(n_flow=1, store_pairs=1)
     gpu, r, dev = gpu_forward(s, params)
     pix = sample_pixels(s, 200, 3)
@@ -270,9 +270,9 @@ def _ac_ragged_scene(seed=8):
 def test_alpha_compositing_parity(deterministic):
     """variant 1 against the oracle's literal Eq. 9-10: forward planes and every
     gradient, on each sort width, with and without normals and flow."""
-    _full_check(synth.config0(), n_flow=0, normals=False, variant=1, deterministic=deterministic)
-    _full_check(synth.config1(K=100, n_views=3, W=48, H=40), n_flow=1, variant=1, deterministic=deterministic)
-    _full_check(synth.config3(n_views=3, K=37, W=40, H=30), n_flow=2, variant=1, deterministic=deterministic)
+    _full_check(synth.single_view(), n_flow=0, normals=False, variant=1, deterministic=deterministic)
+    _full_check(synth.object_orbit(K=100, n_views=3, W=48, H=40), n_flow=1, variant=1, deterministic=deterministic)
+    _full_check(synth.reconstruction(n_views=3, K=37, W=40, H=30), n_flow=2, variant=1, deterministic=deterministic)
     _full_check(_ac_ragged_scene(), n_flow=1, variant=1, deterministic=deterministic)
 
 
@@ -283,7 +283,7 @@ def test_alpha_compositing_persistent():
 def test_alpha_compositing_equal_depth_ties():
     """Exact duplicates hit at bitwise-equal depths on the GPU too, so the strict
     indicator of Eq. 10 leaves them unattenuated by each other, as in the oracle."""
-    s = synth.config1(K=50, n_views=2, W=32, H=24)
+    s = synth.object_orbit(K=50, n_views=2, W=32, H=24)
     s2 = synth.make_scene([(np.concatenate([s.means] * 2), np.concatenate([s.chol] * 2),
                             np.concatenate([s.weights] * 2))],
                           [{k: v for k, v in vv.items() if k != "pix_offset"} for vv in s.views], s.poses)
@@ -292,7 +292,7 @@ def test_alpha_compositing_equal_depth_ties():
 
 def test_alpha_compositing_full_size_sampled():
     """The 16-view 320x240 K=100 orbit, sampled pixels, forward and backward."""
-    s = synth.config1()
+    s = synth.object_orbit()
     params = fmb.default_params(n_flow=1, variant=1)
     gpu, r, dev = gpu_forward(s, params)
     pix = sample_pixels(s, 150, 5)
@@ -321,7 +321,7 @@ def test_points_export_parity(variant):
     fp32 depth error propagates to (gpu_util.points_tolerances), where the oracle's
     alpha >= 1e-2 (at the pixel and, for Eq. 16, its two neighbours) and the depth
     order is unambiguous in fp32."""
-    for scene, nf in ((synth.config1(K=100, n_views=3, W=48, H=40), 1), (synth.config0(), 0)):
+    for scene, nf in ((synth.object_orbit(K=100, n_views=3, W=48, H=40), 1), (synth.single_view(), 0)):
         params = fmb.default_params(n_flow=nf, variant=variant)
         gpu, r, dev = gpu_forward(scene, params)
         pts = {k: v.cpu().numpy().astype(np.float64) for k, v in r.points(*dev).items()}
@@ -362,7 +362,7 @@ def test_ray_batch_parity(variant):
     """Views that render only a list of pixels (random minibatch across all frames):
     forward planes hold the listed rays in order and the gradients are the sums over
     those rays alone -- against the oracle on the same pixel lists."""
-    base = synth.config1(K=100, n_views=6, W=48, H=40)
+    base = synth.object_orbit(K=100, n_views=6, W=48, H=40)
     s = synth.ray_batch(base, 3000, seed=2)
     assert s.n_pixels == 3000 and all(v.get("rays") is not None for v in s.views)
     _full_check(s, n_flow=1, variant=variant)
@@ -375,7 +375,7 @@ def test_ray_batch_parity(variant):
 def test_ray_batch_matches_full_render():
     """A ray batch renders exactly the listed pixels of the full image: bitwise the
     same depth, alpha, normal and flow values."""
-    base = synth.config1(K=60, n_views=2, W=40, H=30)
+    base = synth.object_orbit(K=60, n_views=2, W=40, H=30)
     s = synth.ray_batch(base, 700, seed=3)
     p = fmb.default_params(n_flow=1)
     full, _, _ = gpu_forward(base, p)
@@ -397,10 +397,10 @@ def test_loss_attribution_parity(variant):
     """Per-Gaussian sums of ray loss x normalised weight against the oracle, on a ray
     batch across frames (the paper's ~5 % sample), on whole images, and for K above
     one 256-Gaussian block (two-parameter only); relative to the total loss."""
-    cases = [synth.ray_batch(synth.config1(K=100, n_views=8, W=48, H=40), 800, seed=4),
-             synth.config1(K=37, n_views=2, W=30, H=20), _ac_ragged_scene()]
+    cases = [synth.ray_batch(synth.object_orbit(K=100, n_views=8, W=48, H=40), 800, seed=4),
+             synth.object_orbit(K=37, n_views=2, W=30, H=20), _ac_ragged_scene()]
     if variant == 0:
-        cases.append(synth.config1(K=300, n_views=2, W=24, H=20))
+        cases.append(synth.object_orbit(K=300, n_views=2, W=24, H=20))
     for s in cases:
         params = fmb.default_params(n_flow=0, variant=variant)
         gpu, r, dev = gpu_forward(s, params)
@@ -419,7 +419,7 @@ def test_loss_attribution_full_size(variant):
     alpha-compositing weights w / W wherever W > 0, i.e. alpha > 0), so the
     attribution adds up to the loss of those rays; no entry is negative; a zero loss
     attributes nothing."""
-    s = synth.config1()
+    s = synth.object_orbit()
     params = fmb.default_params(n_flow=1, variant=variant)
     gpu, r, dev = gpu_forward(s, params)
     loss = np.random.default_rng(11).uniform(0.0, 1.0, s.n_pixels).astype(np.float32)
@@ -440,7 +440,7 @@ def test_colour_parity(variant, deterministic):
     """Colour mode: the colour plane (Eq. 3 with per-Gaussian RGB) and every gradient,
     colours' included, against the oracle; the other planes and gradients are those
     of the colour-free render."""
-    for s, nf in ((synth.config1(K=100, n_views=3, W=40, H=30), 1), (synth.config0(), 0)):
+    for s, nf in ((synth.object_orbit(K=100, n_views=3, W=40, H=30), 1), (synth.single_view(), 0)):
         rng = np.random.default_rng(9)
         colors = rng.uniform(0.0, 1.0, (s.means.shape[0], 3)).astype(np.float32)
         params = fmb.default_params(n_flow=nf, variant=variant, colors=1, deterministic=int(deterministic))

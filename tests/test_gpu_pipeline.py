@@ -23,7 +23,7 @@ def _lib():
 
 @pytest.mark.parametrize("variant", [0, 1])
 def test_host_pipeline_matches_plain_calls(variant):
-    s = synth.config1(K=60, n_views=4, W=64, H=48)
+    s = synth.object_orbit(K=60, n_views=4, W=64, H=48)
     n_flow = 1
     params = fmb.default_params(n_flow=n_flow, variant=variant)
     P = s.n_pixels

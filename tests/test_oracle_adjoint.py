@@ -125,7 +125,7 @@ def test_twist_gradient_matches_rotation_differences(oracle_mod):
 def test_scene_backward_sums_views(oracle_mod):
     """The multi-view wrapper adds each view's gradients into the shared object and
     into the right pose rows (own pose and flow target)."""
-    s = synth.config1(K=5, n_views=3, W=6, H=5)
+    s = synth.object_orbit(K=5, n_views=3, W=6, H=5)
     rng = np.random.default_rng(0)
     gd, ga, gn, gf = synth.upstream_grads(rng, s.n_pixels, 1)
     g = oracle_mod.backward_scene(s, gd, ga, gn.reshape(-1), gf.reshape(-1), n_flow=1)

@@ -156,7 +156,7 @@ def test_two_centred_gaussians_blend_closed_form(oracle_mod):
 def test_duplicated_gaussians(oracle_mod):
     """Duplicating every Gaussian leaves the normalised weights of Eq. 3 unchanged
     (depth, normal, flow identical) and doubles sum delta (Eq. 8)."""
-    s = synth.config0(seed=2, K=7, W=16, H=12)
+    s = synth.single_view(seed=2, K=7, W=16, H=12)
     tp = synth.look_at_pose((0.5, 0.0, -4.0))
     a = oracle_mod.render_view(s.means, s.chol, s.weights, s.poses[0], tp[None], (16, 12, 16.0, 16.0, 8.0, 6.0))
     b = oracle_mod.render_view(np.concatenate([s.means] * 2), np.concatenate([s.chol] * 2),
@@ -171,7 +171,7 @@ def test_duplicated_gaussians(oracle_mod):
 def test_permutation_invariance(oracle_mod):
     """Sort-free blending (Sec. 3): every output is invariant under any reordering
     of the Gaussians."""
-    s = synth.config0(seed=4, K=23, W=20, H=16)
+    s = synth.single_view(seed=4, K=23, W=20, H=16)
     cam = (20, 16, 20.0, 20.0, 10.0, 8.0)
     tp = synth.look_at_pose((1.0, 0.3, -3.8))[None]
     a = oracle_mod.render_view(s.means, s.chol, s.weights, s.poses[0], tp, cam)
@@ -201,7 +201,7 @@ def test_rigid_motion_invariance(oracle_mod):
     """Moving scene and cameras together by one rigid motion changes no output
     (normals are reported in the camera frame, flow is a reprojection)."""
     rng = np.random.default_rng(9)
-    s = synth.config0(seed=6, K=11, W=18, H=14)
+    s = synth.single_view(seed=6, K=11, W=18, H=14)
     cam = (18, 14, 18.0, 18.0, 9.0, 7.0)
     tp = synth.look_at_pose((-1.0, 0.4, -3.9))
     a = oracle_mod.render_view(s.means, s.chol, s.weights, s.poses[0], tp[None], cam)
@@ -224,7 +224,7 @@ def test_eta_scale_covariance(oracle_mod):
     Scaling the world by k (means k mu, precision factors L/k, camera translation
     k t) together with eta -> k eta scales depth by k and leaves alpha, normal and
     flow unchanged."""
-    s = synth.config0(seed=8, K=9, W=16, H=12)
+    s = synth.single_view(seed=8, K=9, W=16, H=12)
     cam = (16, 12, 16.0, 16.0, 8.0, 6.0)
     tp = synth.look_at_pose((0.7, -0.4, -3.9))
     a = oracle_mod.render_view(s.means, s.chol, s.weights, s.poses[0], tp[None], cam, eta=1.0)
@@ -244,7 +244,7 @@ def test_eta_scale_covariance(oracle_mod):
 def test_identical_pose_flow_is_zero(oracle_mod):
     """Flow (Sec. 5) is the change of a pixel's coordinates under the target pose:
     the view's own pose moves nothing."""
-    s = synth.config0(seed=1, K=13, W=24, H=20)
+    s = synth.single_view(seed=1, K=13, W=24, H=20)
     cam = (24, 20, 24.0, 24.0, 12.0, 10.0)
     r = oracle_mod.render_view(s.means, s.chol, s.weights, s.poses[0], np.stack([s.poses[0]] * 2), cam)
     assert np.max(np.abs(r["flow"])) < 1e-11
@@ -254,7 +254,7 @@ def test_flow_of_sideways_translation(oracle_mod):
     """A camera translated by delta along its own x axis sees a point at z-depth Z
     move by -fx delta / Z pixels horizontally and not at all vertically.  The
     z-depth of the rendered point is D times the z component of the unit ray."""
-    s = synth.config0(seed=3, K=10, W=16, H=12)
+    s = synth.single_view(seed=3, K=10, W=16, H=12)
     cam = (16, 12, 14.0, 14.0, 8.0, 6.0)
     pose = np.asarray(s.poses[0], dtype=np.float64)
     for delta in (0.05, -0.2):
@@ -273,7 +273,7 @@ def test_blended_normal_perpendicular_to_ray(oracle_mod):
     derivative along the ray vanishes: v^T Sigma^-1 (v t_i - mu) = 0.  So every n_i,
     and the blended normal, is perpendicular to the ray, and the blended normal has
     unit length (Sec. 6)."""
-    s = synth.config0(seed=12, K=17, W=16, H=12)
+    s = synth.single_view(seed=12, K=17, W=16, H=12)
     cam = (16, 12, 16.0, 16.0, 8.0, 6.0)
     r = oracle_mod.render_view(s.means, s.chol, s.weights, s.poses[0], None, cam)
     for p in range(16 * 12):
@@ -286,7 +286,7 @@ def test_large_beta1_selects_densest_hit(oracle_mod):
     """With beta2 = 0 and a very large beta1, Eq. 7 puts all the weight on the
     Gaussian with the largest d_i, so D tends to that Gaussian's t_i.  The per-
     Gaussian t_i and d_i come from K = 1 renders (D = t_i, sum delta = e^{d_i})."""
-    s = synth.config0(seed=13, K=6, W=8, H=6)
+    s = synth.single_view(seed=13, K=6, W=8, H=6)
     cam = (8, 6, 8.0, 8.0, 4.0, 3.0)
     singles = [oracle_mod.render_view(s.means[i:i + 1], s.chol[i:i + 1], s.weights[i:i + 1], s.poses[0], None, cam)
                for i in range(6)]
@@ -343,7 +343,7 @@ def test_ac_two_centred_gaussians_closed_form(oracle_mod):
 def test_ac_weights_telescope_to_alpha(oracle_mod):
     """With distinct hit depths the transmittances telescope: sum_i w_i =
     1 - exp(-sum delta) = alpha on every pixel (and W <= 1)."""
-    s = synth.config0(seed=5, K=17, W=16, H=12)
+    s = synth.single_view(seed=5, K=17, W=16, H=12)
     r = oracle_mod.render_view(s.means, s.chol, s.weights, s.poses[0], None, CAM, variant=1)
     np.testing.assert_allclose(r["saved"][:, 0], r["alpha"], rtol=1e-12, atol=1e-15)
 
@@ -367,7 +367,7 @@ def test_ac_ties_do_not_attenuate(oracle_mod):
 def test_ac_permutation_invariance(oracle_mod):
     """The variant sorts by depth internally: outputs do not depend on the order in
     which the Gaussians are given."""
-    s = synth.config0(seed=6, K=19, W=20, H=16)
+    s = synth.single_view(seed=6, K=19, W=20, H=16)
     cam = (20, 16, 20.0, 20.0, 10.0, 8.0)
     tp = synth.look_at_pose((1.0, 0.3, -3.8))[None]
     a = oracle_mod.render_view(s.means, s.chol, s.weights, s.poses[0], tp, cam, variant=1)
@@ -472,7 +472,7 @@ def test_attribution_partition_of_unity(oracle_mod, variant):
     attributions sum to the total ray loss; one Gaussian takes all of it; exact
     duplicates (equal weights under Eq. 7, equal depths under Eq. 10's strict
     indicator) take equal shares; reordering the Gaussians reorders the result."""
-    s = synth.config1(K=9, n_views=2, W=12, H=10)
+    s = synth.object_orbit(K=9, n_views=2, W=12, H=10)
     loss = np.random.default_rng(0).uniform(0.0, 2.0, s.n_pixels)
     a = oracle_mod.attribution_scene(s, loss, variant=variant)
     assert abs(a.sum() - loss.sum()) < 1e-9 * loss.sum()
@@ -533,7 +533,7 @@ def test_colour_blend_closed_forms(oracle_mod, variant):
     else:
         w1, w2 = 1 - np.exp(-l1), np.exp(-l1) * (1 - np.exp(-l2))
     np.testing.assert_allclose(r["color"][0], (w1 * c1 + w2 * c2) / (w1 + w2), atol=1e-12)
-    s = synth.config0(seed=3, K=11, W=10, H=8)
+    s = synth.single_view(seed=3, K=11, W=10, H=8)
     const = oracle_mod.render_view(s.means, s.chol, s.weights, s.poses[0], None, (10, 8, 10.0, 10.0, 5.0, 4.0),
                                    variant=variant, colors=np.tile([0.3, 0.6, 0.2], (11, 1)))
     hit = const["alpha"] > 1e-6

@@ -18,7 +18,7 @@ from paper_2308_14737_gb300 import shard, synth
 
 def _scene():
     """Five orbit views whose flow targets (the next view) cross the shards."""
-    return synth.config1(K=7, n_views=5, W=9, H=7)
+    return synth.object_orbit(K=7, n_views=5, W=9, H=7)
 
 
 def _view_upstream(scene, vi, v):
@@ -60,7 +60,7 @@ def _free_port():
 
 
 def test_shard_views_balances_and_covers():
-    s = synth.config2(n_objects=6, views_per_object=2, sides=(16, 24, 32))
+    s = synth.ragged_batch(n_objects=6, views_per_object=2, sides=(16, 24, 32))
     for world in (1, 2, 3, 5):
         sh = shard.shard_views(s, world)
         assert sorted(i for x in sh for i in x) == list(range(len(s.views)))

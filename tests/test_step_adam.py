@@ -62,8 +62,8 @@ def test_adam_matches_reference(lib):
 def _recon_problem():
     """Targets rendered by the FP64 oracle from a second seed; the model starts from
     the first seed."""
-    tgt_scene = synth.config3(seed=1, n_views=4, K=24, W=40, H=30)
-    model = synth.config3(seed=0, n_views=4, K=24, W=40, H=30)
+    tgt_scene = synth.reconstruction(seed=1, n_views=4, K=24, W=40, H=30)
+    model = synth.reconstruction(seed=0, n_views=4, K=24, W=40, H=30)
     model.poses = tgt_scene.poses.copy()  # same cameras
     ref = oracle.render_scene(tgt_scene, n_flow=1)
     return model, dict(depth=ref["depth"], alpha=ref["alpha"], flow=ref["flow"])
@@ -91,7 +91,7 @@ def test_graph_replay_matches_eager_and_loss_decreases(lib):
 
 @gpu
 def test_autotune_picks_a_candidate_and_caches(lib, tmp_path):
-    s = synth.config1(K=40, n_views=2, W=48, H=32)
+    s = synth.object_orbit(K=40, n_views=2, W=48, H=32)
     T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
     P = s.n_pixels
     ups = dict(g_depth=torch.randn(P, device="cuda"), g_alpha=torch.randn(P, device="cuda"),

@@ -42,7 +42,7 @@ def _planes(P, n_flow):
 
 
 def test_noalloc_matches_workspace_forward_on_two_calls():
-    scenes = [synth.config1(K=100, n_views=4, W=64, H=48), synth.config1(seed=3, K=30, n_views=2, W=40, H=30)]
+    scenes = [synth.object_orbit(K=100, n_views=4, W=64, H=48), synth.object_orbit(seed=3, K=30, n_views=2, W=40, H=30)]
     for s in scenes:
         params = fmb.default_params(n_flow=1, want_normals=1)
         means, chol, weights, poses = _dev(s)
@@ -59,7 +59,7 @@ def test_noalloc_matches_workspace_forward_on_two_calls():
 
 
 def test_noalloc_rejects_batches_beyond_the_fixed_scratch():
-    s = synth.config1(K=5000, n_views=4, W=8, H=8)  # 20000 records x 64 bytes > 1 MiB
+    s = synth.object_orbit(K=5000, n_views=4, W=8, H=8)  # 20000 records x 64 bytes > 1 MiB
     params = fmb.default_params(n_flow=1, want_normals=1)
     means, chol, weights, poses = _dev(s)
     out = _planes(s.n_pixels, 1)
