@@ -355,6 +355,45 @@ def test_points_export_parity(variant):
 
 
 
+@pytest.mark.parametrize("variant", [0, 1])
+def test_points_export_full_size_sampled(variant):
+    """The 16-view 320x240 orbit at full size, in the bench's configuration: the
+    exported points and the max-weight quality at 200 sampled pixels per view
+    against the oracle (points within the depth tolerance plus the measured depth
+    difference, quality within 1e-4), where the oracle's alpha >= 1e-2 and the
+    depth order is unambiguous in fp32.  The normals are compared on every pixel of
+    the small cases above."""
+    s = synth.object_orbit()
+    params = fmb.default_params(n_flow=1, variant=variant)
+    gpu, r, dev = gpu_forward(s, params)
+    pts = {k: v.cpu().numpy().astype(np.float64) for k, v in r.points(*dev).items()}
+    samp = sample_pixels(s, 200, seed=5)
+    amb = ac_order_ambiguous(s, samp) if variant == 1 else None
+    n_checked = 0
+    for vi, v in enumerate(s.views):
+        sl = s.object_slice(v["object"])
+        cam = (v["W"], v["H"], v["fx"], v["fy"], v["cx"], v["cy"])
+        pix = samp[vi]
+        ref = oracle.points_view(s.means[sl], s.chol[sl], s.weights[sl], s.poses[v["pose"]], cam,
+                                 variant=variant, pixels=pix)
+        fr = oracle.render_view(s.means[sl], s.chol[sl], s.weights[sl], s.poses[v["pose"]], None, cam,
+                                pixels=pix, variant=variant)
+        o, P = v["pix_offset"], v["W"] * v["H"]
+        ok = fr["alpha"] >= 1e-2
+        if amb is not None:
+            ok &= ~amb[vi]
+        D = fr["depth"]
+        dD = np.abs(gpu["depth"][o + pix] - D)
+        assert np.all((dD <= 1e-4 + 1e-5 * np.abs(D))[ok])
+        g_pts = pts["points"][3 * o:3 * (o + P)].reshape(3, P)[:, pix].T
+        e = np.abs(g_pts - ref["points"]).max(1)
+        assert np.all((e <= 1e-4 + 1e-5 * np.abs(D) + dD)[ok]), float(e[ok].max())
+        eq = np.abs(pts["quality"][o + pix] - ref["quality"])
+        assert np.all((eq <= 1e-4)[ok]), float(eq[ok].max())
+        n_checked += int(ok.sum())
+    assert n_checked > 1000
+
+
 # ------------------------------------------------ ray minibatches across frames (Sec. 4)
 
 @pytest.mark.parametrize("variant", [0, 1])
