@@ -688,7 +688,12 @@ def cpu_model() -> str:
             k, v = (x.strip() for x in line.split(":", 1))
             fields.setdefault(k, v)
     if "CPU part" in fields:
-        return f"{platform.machine()} CPU implementer {fields.get('CPU implementer', '?')} part {fields['CPU part']}"
+        # Arm's published part numbers for the server cores this may run on
+        known = {"0xd4f": "Neoverse-V2", "0xd40": "Neoverse-V1", "0xd0c": "Neoverse-N1", "0xd49": "Neoverse-N2",
+                 "0xd8e": "Neoverse-N3", "0xd84": "Neoverse-V3"}
+        part = fields["CPU part"].lower()
+        name = known.get(part, f"part {part}") if fields.get("CPU implementer", "").lower() == "0x41" else part
+        return f"{platform.machine()} {name} (implementer {fields.get('CPU implementer', '?')}, part {part})"
     return platform.machine()
 
 
