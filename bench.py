@@ -53,10 +53,13 @@ WORKLOAD = ("object orbit: 16 views 320x240 (f=320) on a radius-4 ring, K=100 Ga
 # operations (an FMA counts once; negations, comparisons, loads and control
 # excluded) and MUFU operations (ex2, rcp, rsqrt), counted from the kernels'
 # arithmetic, with and without the normal plane.
-OPS = {  # normals -> (fwd FP32, fwd MUFU, bwd FP32, bwd MUFU)
+OPS = {  # normals -> (fwd FP32, fwd MUFU, bwd FP32, bwd MUFU), with pose gradients
     True: (56, 4, 110, 4),
     False: (42, 3, 70, 3),
 }
+# Without pose gradients the two-parameter adjoint needs only the lower triangle of
+# sum v abar^T (6 of its 9 accumulations per pair).
+NO_POSE_SAVING = 3
 # Alpha-compositing variant (Sec. 3.3): per pair, the same geometry plus the
 # transmittance and weight arithmetic (prefix sums, T = e^-S, 1 - e^-delta by its
 # series), and in the backward a re-render, the per-pair weight adjoint and the
@@ -400,6 +403,8 @@ def run_gpu(args):
     peak = peak_fp32_gops(clock_for_peak)
     fwd_ms_ = t_f / args.steps
     f32f, mf, f32b, mb = (OPS_AC if ac else OPS)[bool(wl["normals"])]
+    if not ac and not want_pose:
+        f32b -= NO_POSE_SAVING
     roofline = {
         "bound": "alu",
         "kernel": ("backward_ac_kernel" if ac else "backward_kernel") + " (fmb_render_backward call)",

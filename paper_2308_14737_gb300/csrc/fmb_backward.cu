@@ -67,8 +67,10 @@ __host__ __device__ constexpr int ray_rec2() {
 }
 
 // STORED: the pair's t, log2 weight and density come from the forward (`st`,
-// `se`, `sd`) instead of being recomputed.
-template <bool NORMALS, bool STORED, bool COLOR = false>
+// `se`, `sd`) instead of being recomputed.  POSE = false (no pose gradient
+// requested): only the lower triangle of sum v abar^T is needed, for Lbar, so it
+// is accumulated together with sum gbar u^T into the six G sums and M stays zero.
+template <bool NORMALS, bool STORED, bool COLOR = false, bool POSE = true>
 __device__ __forceinline__ void bwd_pair2(BwdAcc2& A, const GaussRec2& gr, const ulonglong2* __restrict__ rr, f2 K2,
                                           f2 K3, f2 B1, f2 nB1, f2 nB2E, f2 tiny, f2 st, f2 se, f2 sd,
                                           f2 c0 = f2{}, f2 c1 = f2{}, f2 c2 = f2{}) {
@@ -138,23 +140,32 @@ __device__ __forceinline__ void bwd_pair2(BwdAcc2& A, const GaussRec2& gr, const
   A.Y0 = add2(A.Y0, y0);
   A.Y1 = add2(A.Y1, y1);
   A.Y2 = add2(A.Y2, y2);
-  if (NORMALS) {
-    A.G00 = fma2(gb0, G.u0, A.G00);
-    A.G10 = fma2(gb1, G.u0, A.G10);
-    A.G11 = fma2(gb1, G.u1, A.G11);
-    A.G20 = fma2(gb2, G.u0, A.G20);
-    A.G21 = fma2(gb2, G.u1, A.G21);
-    A.G22 = fma2(gb2, G.u2, A.G22);
+  if (POSE) {
+    if (NORMALS) {
+      A.G00 = fma2(gb0, G.u0, A.G00);
+      A.G10 = fma2(gb1, G.u0, A.G10);
+      A.G11 = fma2(gb1, G.u1, A.G11);
+      A.G20 = fma2(gb2, G.u0, A.G20);
+      A.G21 = fma2(gb2, G.u1, A.G21);
+      A.G22 = fma2(gb2, G.u2, A.G22);
+    }
+    A.M[0] = fma2(v0, ab0, A.M[0]);
+    A.M[1] = fma2(v0, ab1, A.M[1]);
+    A.M[2] = fma2(v0, ab2, A.M[2]);
+    A.M[3] = fma2(v1, ab0, A.M[3]);
+    A.M[4] = fma2(v1, ab1, A.M[4]);
+    A.M[5] = fma2(v1, ab2, A.M[5]);
+    A.M[6] = fma2(v2, ab0, A.M[6]);
+    A.M[7] = fma2(v2, ab1, A.M[7]);
+    A.M[8] = fma2(v2, ab2, A.M[8]);
+  } else {
+    A.G00 = fma2(v0, ab0, NORMALS ? fma2(gb0, G.u0, A.G00) : A.G00);
+    A.G10 = fma2(v1, ab0, NORMALS ? fma2(gb1, G.u0, A.G10) : A.G10);
+    A.G11 = fma2(v1, ab1, NORMALS ? fma2(gb1, G.u1, A.G11) : A.G11);
+    A.G20 = fma2(v2, ab0, NORMALS ? fma2(gb2, G.u0, A.G20) : A.G20);
+    A.G21 = fma2(v2, ab1, NORMALS ? fma2(gb2, G.u1, A.G21) : A.G21);
+    A.G22 = fma2(v2, ab2, NORMALS ? fma2(gb2, G.u2, A.G22) : A.G22);
   }
-  A.M[0] = fma2(v0, ab0, A.M[0]);
-  A.M[1] = fma2(v0, ab1, A.M[1]);
-  A.M[2] = fma2(v0, ab2, A.M[2]);
-  A.M[3] = fma2(v1, ab0, A.M[3]);
-  A.M[4] = fma2(v1, ab1, A.M[4]);
-  A.M[5] = fma2(v1, ab2, A.M[5]);
-  A.M[6] = fma2(v2, ab0, A.M[6]);
-  A.M[7] = fma2(v2, ab1, A.M[7]);
-  A.M[8] = fma2(v2, ab2, A.M[8]);
   if (COLOR) {
     A.Cb0 = fma2(what, Cb0, A.Cb0);
     A.Cb1 = fma2(what, Cb1, A.Cb1);
@@ -168,7 +179,7 @@ __device__ __forceinline__ float warp_sum(float x) {
   return x;
 }
 
-template <bool NORMALS, int NFLOW, bool STORED, bool COLOR = false>
+template <bool NORMALS, int NFLOW, bool STORED, bool COLOR = false, bool POSE = true>
 __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
     backward_kernel(const __grid_constant__ Batch batch, Scene s, Consts k, const float4* __restrict__ records,
                     BwdIn in, BwdOut out, int ray_tile, int* counter) {
@@ -382,7 +393,7 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
       const f2 z = dup(0.f);
 #pragma unroll kBwdUnroll
       for (int r = sg; r < nr; r += S)
-        bwd_pair2<NORMALS, false>(A, gr, rays + kRayRec2 * r, K2v, K3v, B1v, nB1v, nB2E, tiny, z, z, z);
+        bwd_pair2<NORMALS, false, false, POSE>(A, gr, rays + kRayRec2 * r, K2v, K3v, B1v, nB1v, nB2E, tiny, z, z, z);
     }
   }
   __syncthreads();  // ray records are dead; the shared memory is reused below
@@ -521,11 +532,11 @@ static int bwd_smem_bytes(int ray_tile, int threads, bool color = false) {
                   threads * (color ? acc_floats<true>() : kAccFloats) * static_cast<int>(sizeof(float)));
 }
 
-template <bool NORMALS, int NFLOW, bool STORED = false, bool COLOR = false>
+template <bool NORMALS, int NFLOW, bool STORED = false, bool COLOR = false, bool POSE = true>
 static cudaError_t prepare_bwd_t(int smem) {
   // Dynamic plus static shared memory above the 48 KB default needs the opt-in.
   if (smem + static_cast<int>(sizeof(float) * (kBwdMaxThreads / 32) * 48) > 48 * 1024)
-    return cudaFuncSetAttribute(backward_kernel<NORMALS, NFLOW, STORED, COLOR>,
+    return cudaFuncSetAttribute(backward_kernel<NORMALS, NFLOW, STORED, COLOR, POSE>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return cudaSuccess;
 }
@@ -541,12 +552,12 @@ static int bwd_ctas_per_sm_t(int ray_tile, int threads) {
   return n > 0 ? n : 1;
 }
 
-template <bool NORMALS, int NFLOW, bool STORED, bool COLOR = false>
+template <bool NORMALS, int NFLOW, bool STORED, bool COLOR = false, bool POSE = true>
 static cudaError_t launch_bwd_s(const Batch& b, const Scene& s, const Consts& c, const float4* records,
                                 int ray_tile, int threads, const BwdIn& in, const BwdOut& out, int* counter,
                                 cudaStream_t st) {
   const int smem = bwd_smem_bytes(ray_tile, threads, COLOR);
-  cudaError_t e = prepare_bwd_t<NORMALS, NFLOW, STORED, COLOR>(smem);
+  cudaError_t e = prepare_bwd_t<NORMALS, NFLOW, STORED, COLOR, POSE>(smem);
   if (e != cudaSuccess) return e;
   int grid = b.n_items;
   if (counter) {
@@ -555,7 +566,7 @@ static cudaError_t launch_bwd_s(const Batch& b, const Scene& s, const Consts& c,
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     grid = std::min(b.n_items, std::max(1, sms) * bwd_ctas_per_sm_t<NORMALS, NFLOW>(ray_tile, threads));
   }
-  backward_kernel<NORMALS, NFLOW, STORED, COLOR><<<grid, threads, smem, st>>>(b, s, c, records, in, out, ray_tile,
+  backward_kernel<NORMALS, NFLOW, STORED, COLOR, POSE><<<grid, threads, smem, st>>>(b, s, c, records, in, out, ray_tile,
                                                                                counter);
   return cudaGetLastError();
 }
@@ -568,6 +579,9 @@ static cudaError_t launch_bwd_t(const Batch& b, const Scene& s, const Consts& c,
     return launch_bwd_s<NORMALS, NFLOW, true>(b, s, c, records, ray_tile, threads, in, out, counter, st);
   if (out.gcolors != nullptr)
     return launch_bwd_s<NORMALS, NFLOW, false, true>(b, s, c, records, ray_tile, threads, in, out, counter, st);
+  if (out.gposes == nullptr)
+    return launch_bwd_s<NORMALS, NFLOW, false, false, false>(b, s, c, records, ray_tile, threads, in, out, counter,
+                                                              st);
   return launch_bwd_s<NORMALS, NFLOW, false>(b, s, c, records, ray_tile, threads, in, out, counter, st);
 }
 

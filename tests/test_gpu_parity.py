@@ -70,6 +70,21 @@ def test_normals_off():
     _full_check(s, n_flow=1, normals=False)
 
 
+@pytest.mark.parametrize("normals,n_flow,deterministic", [(True, 1, False), (False, 2, False), (True, 0, True),
+                                                         (False, 0, True)])
+def test_backward_without_pose_gradients(normals, n_flow, deterministic):
+    """No pose gradient requested: the kernel specialisation that accumulates the
+    lower triangle of sum v abar^T together with sum gbar u^T gives the oracle's
+    Gaussian gradients, and those of the run that also returns pose gradients."""
+    s = (synth.object_orbit(K=100, n_views=3, W=48, H=40) if n_flow < 2 else
+         synth.reconstruction(n_views=3, K=37, W=40, H=30))
+    _, _, g1 = _full_check(s, n_flow=n_flow, normals=normals, deterministic=deterministic, want_pose=False)
+    _, _, g2 = _full_check(s, n_flow=n_flow, normals=normals, deterministic=deterministic, want_pose=True)
+    assert g1["poses"] is None
+    for k in ("means", "chol", "weights"):
+        assert np.allclose(g1[k], g2[k], rtol=1e-5, atol=1e-6 * np.abs(g2[k]).max()), k
+
+
 @pytest.mark.parametrize("rpt", [1, 2, 4])
 def test_rays_per_thread_variants(rpt):
     s = synth.object_orbit(K=45, n_views=2, W=37, H=29)
