@@ -18,6 +18,7 @@
 // (w_i / sum w = 2^(e2_i - lse2)), the alpha-compositing weights from a re-render
 // of the ray (they need the depth order).
 #include "fmb_ac.cuh"
+#include "fmb_f32x2.cuh"
 #include "fmb_internal.cuh"
 
 namespace fmb {
@@ -108,7 +109,11 @@ __device__ __forceinline__ void store_vec(float* plane, long long off, int P, in
   b[2 * P + p] = a[2];
 }
 
-// Two-parameter weights: one thread per pixel, 128 pixels per work item.
+// Two-parameter weights: two pixels per thread (p and p + 128 of a 256-pixel work
+// item), one per lane of packed FP32x2 arithmetic, so every packed instruction
+// serves both pixels' pair with the same Gaussian (each lane's weight is bitwise
+// the scalar evaluation's; the normal sum folds the weight into the normalisation,
+// w rs g).  Pixels past the end compute a clamped pixel and store nothing.
 __global__ void __launch_bounds__(kPtsThreads) points_kernel(const __grid_constant__ Batch batch, Scene s, Consts k,
                                                              const float4* __restrict__ records,
                                                              const float* __restrict__ depth,
@@ -117,44 +122,77 @@ __global__ void __launch_bounds__(kPtsThreads) points_kernel(const __grid_consta
   const int vi = find_item(batch, blockIdx.x, tile);
   const DevView& V = batch.v[vi];
   const int P = V.P;
-  const int p = tile * kPtsThreads + threadIdx.x;
-  if (p >= P) return;
+  const int pa = tile * (2 * kPtsThreads) + threadIdx.x;
+  if (pa >= P) return;  // the second pixel (pa + 128) is then past the end too
+  const int pb = pa + kPtsThreads;
+  const bool has_b = pb < P;
+  const int pbc = has_b ? pb : pa;
   const long long off = V.pix_off;
   float R[9], tp[3];
   load_pose(s.poses, V.pose, R, tp);
   const float o[3] = {-fmaf(R[6], tp[2], fmaf(R[3], tp[1], R[0] * tp[0])),
                       -fmaf(R[7], tp[2], fmaf(R[4], tp[1], R[1] * tp[0])),
                       -fmaf(R[8], tp[2], fmaf(R[5], tp[1], R[2] * tp[0]))};
-  float vc[3], v[3], vl[3], pxy[2];
-  pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
-  const float D = depth[off + p];
-  const float lse2 = saved[3 * off + p];
+  float vca[3], va[3], vla[3], pxya[2], vcb[3], vb[3], vlb[3], pxyb[2];
+  pixel_ray_dd(V, R, ray_pixel(V, pa), vca, va, vla, pxya);
+  pixel_ray_dd(V, R, ray_pixel(V, pbc), vcb, vb, vlb, pxyb);
+  const float Da = depth[off + pa], Db = depth[off + pbc];
+  const f2 v0 = pk(va[0], vb[0]), v1 = pk(va[1], vb[1]), v2 = pk(va[2], vb[2]);
+  const f2 vl0 = pk(vla[0], vlb[0]), vl1 = pk(vla[1], vlb[1]), vl2 = pk(vla[2], vlb[2]);
+  const f2 D = pk(Da, Db);
+  const f2 nlse = pk(-saved[3 * off + pa], -saved[3 * off + pbc]);
+  const f2 K2v = dup(k.K2), K3v = dup(k.K3), B1v = dup(k.beta1);
+  const bool want_n = out.normal_tf != nullptr;
   const float4* rec = records + kRecFloat4 * V.rec_off;
-  float qmax = 0.f, N[3] = {0.f, 0.f, 0.f};
+  float qa = 0.f, qb = 0.f;
+  f2 N0 = dup(0.f), N1 = dup(0.f), N2 = dup(0.f);
   for (int i = 0; i < V.K; ++i) {
-    const GaussRec g = unpack_rec(__ldg(rec + 4 * i), __ldg(rec + 4 * i + 1), __ldg(rec + 4 * i + 2),
-                                  __ldg(rec + 4 * i + 3));
-    const PairGeom G = pair_geom(g.L, g.b, g.mh, g.nbl, v[0], v[1], v[2], vl[0], vl[1], vl[2]);
-    const float x = fmaf(G.q, k.K3, g.l2);
-    const float w = ex2_approx(fmaf(x, k.beta1, fmaf(G.t, k.K2, -lse2)));  // w_i / sum w
-    qmax = fmaxf(qmax, w);
-    if (out.normal_tf != nullptr) {
-      float n[3];
-      normal_at_depth(g, v, vl, D, n);
-      N[0] = fmaf(w, n[0], N[0]);
-      N[1] = fmaf(w, n[1], N[1]);
-      N[2] = fmaf(w, n[2], N[2]);
+    const GaussRec g1 = unpack_rec(__ldg(rec + 4 * i), __ldg(rec + 4 * i + 1), __ldg(rec + 4 * i + 2),
+                                   __ldg(rec + 4 * i + 3));
+    const GaussRec2 g = broadcast_rec(g1);
+    const PairGeom2 G = pair_geom2(g, v0, v1, v2, vl0, vl1, vl2);
+    const f2 x = fma2(G.q, K3v, g.l2);
+    const f2 w = ex2_2(fma2(x, B1v, fma2(G.t, K2v, nlse)));  // w_i / sum w
+    qa = fmaxf(qa, lo(w));
+    qb = fmaxf(qb, hi(w));
+    if (want_n) {
+      // Eq. 17's normal at the rendered depth (the compensated residual at t = D)
+      const f2 r0 = fma2(vl0, D, fma2(v0, D, g.nmh[0]));
+      const f2 r1 = fma2(vl1, D, fma2(v1, D, g.nmh[1]));
+      const f2 r2 = fma2(vl2, D, fma2(v2, D, g.nmh[2]));
+      const f2 u0 = fma2(g.L[0], r0, fma2(g.L[1], r1, fma2(g.L[3], r2, g.nbl[0])));
+      const f2 u1 = fma2(g.L[2], r1, fma2(g.L[4], r2, g.nbl[1]));
+      const f2 u2 = fma2(g.L[5], r2, g.nbl[2]);
+      const f2 gg0 = mul2(g.L[0], u0);
+      const f2 gg1 = fma2(g.L[2], u1, mul2(g.L[1], u0));
+      const f2 gg2 = fma2(g.L[5], u2, fma2(g.L[4], u1, mul2(g.L[3], u0)));
+      const f2 gg = fma2(gg2, gg2, fma2(gg1, gg1, mul2(gg0, gg0)));
+      const f2 rs = pk(lo(gg) > 0.f ? rsqrt_approx(lo(gg)) : 0.f, hi(gg) > 0.f ? rsqrt_approx(hi(gg)) : 0.f);
+      const f2 wr = mul2(w, rs);
+      N0 = fma2(wr, gg0, N0);
+      N1 = fma2(wr, gg1, N1);
+      N2 = fma2(wr, gg2, N2);
     }
   }
-  unit_facing(N[0], N[1], N[2], v);
-  const float pt[3] = {fmaf(v[0], D, o[0]), fmaf(v[1], D, o[1]), fmaf(v[2], D, o[2])};
-  store_vec(out.points, off, P, p, pt);
-  store_vec(out.normal_tf, off, P, p, N);
-  if (out.quality) out.quality[off + p] = qmax;
-  if (out.normal_scr) {
-    float ns[3];
-    screen_normal(V, R, o, depth + off, p, ns);
-    store_vec(out.normal_scr, off, P, p, ns);
+  const float* vv[2] = {va, vb};
+  const float Dv[2] = {Da, Db}, qv[2] = {qa, qb};
+  const int pp[2] = {pa, pb};
+  const float Nl[2][3] = {{lo(N0), lo(N1), lo(N2)}, {hi(N0), hi(N1), hi(N2)}};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (h == 1 && !has_b) break;
+    const float* v = vv[h];
+    float N[3] = {Nl[h][0], Nl[h][1], Nl[h][2]};
+    unit_facing(N[0], N[1], N[2], v);
+    const float pt[3] = {fmaf(v[0], Dv[h], o[0]), fmaf(v[1], Dv[h], o[1]), fmaf(v[2], Dv[h], o[2])};
+    store_vec(out.points, off, P, pp[h], pt);
+    store_vec(out.normal_tf, off, P, pp[h], N);
+    if (out.quality) out.quality[off + pp[h]] = qv[h];
+    if (out.normal_scr) {
+      float ns[3];
+      screen_normal(V, R, o, depth + off, pp[h], ns);
+      store_vec(out.normal_scr, off, P, pp[h], ns);
+    }
   }
 }
 
@@ -231,7 +269,7 @@ __global__ void __launch_bounds__(kAcThreads) points_ac_kernel(const __grid_cons
   }
 }
 
-int points_rays_per_item(int variant) { return variant == 1 ? kAcRays : kPtsThreads; }
+int points_rays_per_item(int variant) { return variant == 1 ? kAcRays : 2 * kPtsThreads; }
 
 cudaError_t launch_points(const Batch& b, const Scene& s, const Consts& c, const float4* records, int variant,
                           int maxK, const float* depth, const float* saved, float* points, float* normal_tf,
