@@ -532,14 +532,15 @@ fmb_status fmb_render_points(const fmb_params* params, int n_objects, const long
     float4* records = reinterpret_cast<float4*>(static_cast<char*>(workspace) + kHeaderBytes);
     const fmb::Scene sc{means, chol, weights, poses};
     const fmb::Consts c = make_consts(params);
-    const int per = fmb::points_rays_per_item(params->variant);
+    // alpha compositing: the forward's run of neighbouring rays per warp
+    const int per = params->variant == 1 ? fmb::ac_fwd_rays_per_item(pl.ac_run) : fmb::points_rays_per_item();
     for (fmb::Batch b : pl.fwd) {
       for (int i = 0; i < b.n_views; ++i) b.v[i].n_tiles = (b.v[i].P + per - 1) / per;
       order_items(b, [&](const fmb::DevView& v) { return static_cast<double>(v.K); },
                   [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles); });
       cudaError_t e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, nullptr, s);
       if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
-      e = fmb::launch_points(b, sc, c, records, params->variant, pl.maxK, depth, saved, points, normal_tf,
+      e = fmb::launch_points(b, sc, c, records, params->variant, pl.maxK, pl.ac_run, depth, saved, points, normal_tf,
                              normal_screen, quality, s);
       if (e != cudaSuccess) return cuda_fail(e, "points launch");
     }

@@ -429,10 +429,11 @@ cudaError_t launch_forward_ac(const Batch& b, const Scene& s, const Consts& c, c
 cudaError_t launch_backward_ac(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
                                int n_flow, int maxK, const BwdIn& in, const BwdOut& out, int* status, int* counter,
                                cudaStream_t st);
-// Oriented point export (Sec. 6): work items of points_rays_per_item(variant) pixels.
-int points_rays_per_item(int variant);
+// Oriented point export (Sec. 6): two-parameter work items of points_rays_per_item()
+// pixels; alpha-compositing items of ac_fwd_rays_per_item(ac_run) pixels.
+int points_rays_per_item();
 cudaError_t launch_points(const Batch& b, const Scene& s, const Consts& c, const float4* records, int variant,
-                          int maxK, const float* depth, const float* saved, float* points, float* normal_tf,
+                          int maxK, int ac_run, const float* depth, const float* saved, float* points, float* normal_tf,
                           float* normal_scr, float* quality, cudaStream_t st);
 // Loss attribution (Sec. 8, Eq. 19).  Two-parameter model: work items of ray_tile
 // rays x a block of GB Gaussians (the backward's blocking, two Gaussians per thread);

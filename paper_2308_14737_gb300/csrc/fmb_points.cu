@@ -196,12 +196,14 @@ __global__ void __launch_bounds__(kPtsThreads) points_kernel(const __grid_consta
   }
 }
 
-// Alpha-compositing weights: one warp per pixel (the weights need the depth order),
-// 32 pixels per work item.
+// Alpha-compositing weights: one warp per pixel (the weights need the depth order);
+// a work item is 4 runs of `run` neighbouring pixels, one run per warp, each pixel
+// starting from the previous one's depth order (the forward's run length).
 template <int M>
 __global__ void __launch_bounds__(kAcThreads) points_ac_kernel(const __grid_constant__ Batch batch, Scene s,
                                                                Consts k, const float4* __restrict__ records,
-                                                               const float* __restrict__ depth, PtsOut out) {
+                                                               const float* __restrict__ depth, PtsOut out,
+                                                               int run) {
   __shared__ float scratch[kAcWarps][3 * 32 * M];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int tile;
@@ -218,11 +220,10 @@ __global__ void __launch_bounds__(kAcThreads) points_ac_kernel(const __grid_cons
   float* sd = scratch[warp];
   float* sw = sd + 32 * M;
   float* sT = sd + 64 * M;
-  constexpr int kPerWarp = kAcRays / kAcWarps;
   unsigned long long key[M];
   for (int m = 0; m < M; ++m) key[m] = kNoKey;
-  for (int j = 0; j < kPerWarp; ++j) {
-    const int p = tile * kAcRays + warp * kPerWarp + j;  // neighbouring rays: reuse the depth order
+  for (int j = 0; j < run; ++j) {
+    const int p = (tile * kAcWarps + warp) * run + j;  // a run of neighbouring rays: reuse the depth order
     if (p >= P) break;
     float vc[3], v[3], vl[3], pxy[2];
     pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
@@ -269,17 +270,18 @@ __global__ void __launch_bounds__(kAcThreads) points_ac_kernel(const __grid_cons
   }
 }
 
-int points_rays_per_item(int variant) { return variant == 1 ? kAcRays : 2 * kPtsThreads; }
+int points_rays_per_item() { return 2 * kPtsThreads; }
 
 cudaError_t launch_points(const Batch& b, const Scene& s, const Consts& c, const float4* records, int variant,
-                          int maxK, const float* depth, const float* saved, float* points, float* normal_tf,
+                          int maxK, int ac_run, const float* depth, const float* saved, float* points, float* normal_tf,
                           float* normal_scr, float* quality, cudaStream_t st) {
   const PtsOut o{points, normal_tf, normal_scr, quality};
   if (variant == 1) {
     const int M = maxK <= 64 ? 2 : (maxK <= 128 ? 4 : 8);
-    if (M == 2) points_ac_kernel<2><<<b.n_items, kAcThreads, 0, st>>>(b, s, c, records, depth, o);
-    else if (M == 4) points_ac_kernel<4><<<b.n_items, kAcThreads, 0, st>>>(b, s, c, records, depth, o);
-    else points_ac_kernel<8><<<b.n_items, kAcThreads, 0, st>>>(b, s, c, records, depth, o);
+    if (ac_run < 1 || ac_run > kAcMaxRun) return cudaErrorInvalidValue;
+    if (M == 2) points_ac_kernel<2><<<b.n_items, kAcThreads, 0, st>>>(b, s, c, records, depth, o, ac_run);
+    else if (M == 4) points_ac_kernel<4><<<b.n_items, kAcThreads, 0, st>>>(b, s, c, records, depth, o, ac_run);
+    else points_ac_kernel<8><<<b.n_items, kAcThreads, 0, st>>>(b, s, c, records, depth, o, ac_run);
   } else {
     points_kernel<<<b.n_items, kPtsThreads, 0, st>>>(b, s, c, records, depth, saved, o);
   }
