@@ -389,8 +389,18 @@ def run_gpu(args):
     value = ws * pairs / (ms_step * 1e-3)
     plain_value = ws * pairs / (ms_plain * 1e-3)
 
-    # e2e: through the public API with host buffers (pinned), copies inside the timed region
-    e2e = e2e_measure(args, s, ups, tuned_params, dev) if rank == 0 else None
+    # e2e: through the public API with host buffers (pinned), copies inside the timed region;
+    # every rank runs it (replicas), the slowest rank's step time sets the whole-job rate
+    if ws > 1:
+        torch.distributed.barrier()
+    e2e = e2e_measure(args, s, ups, tuned_params, dev)
+    if ws > 1:
+        x = torch.tensor([e2e["ms_per_step"]], device=dev)
+        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+        e2e["ms_per_step"] = float(x[0])
+        e2e["value"] = ws * pairs / (e2e["ms_per_step"] * 1e-3)
+        e2e["h2d_bytes_per_step"] *= ws
+        e2e["d2h_bytes_per_step"] *= ws
 
     if rank != 0:
         if ws > 1:
