@@ -50,38 +50,57 @@ struct BwdBlocking {
   int n_gb, GB, S;
 };
 
+// Fraction of a CTA's thread lanes that carry a real (ray, Gaussian) pair when K
+// Gaussians are split into n blocks for T threads.
+static double bwd_lane_fill(int K, int T, int n) {
+  const int GB = (K + n - 1) / n;
+  const int gb2 = (GB + 1) / 2;
+  const int S = std::max(1, T / gb2);
+  return (static_cast<double>(gb2) * S / T) * (static_cast<double>(K) / (n * 2.0 * gb2));
+}
+
 // Backward blocking of K Gaussians for T threads: each thread owns two Gaussians
 // (one per packed lane), so a CTA covers GB <= min(2T, 256) Gaussians with
-// ceil(GB/2) threads per ray subgroup and S subgroups.
+// ceil(GB/2) threads per ray subgroup and S = T / ceil(GB/2) subgroups.  The block
+// count is the fewest that fit, or up to three more where that fills the threads
+// better: the modelled cost per ray is K / fill (pair work) plus 5 per block (the
+// per-ray records each block builds), e.g. K = 200 at T = 160 runs as two blocks of
+// 100 (3 subgroups of 50 threads) instead of one of 200 (one subgroup of 100).
 BwdBlocking bwd_blocking(int K, int T) {
   const int gbmax = std::min(2 * T, kMaxGaussPerCta);
+  const int n_min = (K + gbmax - 1) / gbmax;
+  int best_n = n_min;
+  double best_cost = 0.0;
+  for (int n = n_min; n <= std::min(K, n_min + 3); ++n) {
+    const double cost = K / bwd_lane_fill(K, T, n) + 5.0 * n;
+    if (n == n_min || cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best_n = n;
+    }
+  }
   BwdBlocking b;
-  b.n_gb = (K + gbmax - 1) / gbmax;
+  b.n_gb = best_n;
   b.GB = (K + b.n_gb - 1) / b.n_gb;
   b.S = std::max(1, T / ((b.GB + 1) / 2));
   return b;
 }
 
-// Threads per backward CTA: the candidate that wastes the fewest thread slots over
-// the batch, weighted by each view's pairs.
+// Threads per backward CTA: the candidate with the lowest modelled cost over the
+// batch (each view's rays x (K / lane fill + 5 per Gaussian block), as in
+// bwd_blocking).
 int choose_bwd_threads(const fmb_view* views, int n_views, const long long* offs) {
   const int cand[] = {128, 160};
   int best = 160;
-  double best_eff = -1.0;
+  double best_cost = -1.0;
   for (int T : cand) {
-    double num = 0.0, den = 0.0;
+    double cost = 0.0;
     for (int i = 0; i < n_views; ++i) {
       const int K = static_cast<int>(offs[views[i].object + 1] - offs[views[i].object]);
-      const double pairs = static_cast<double>(views[i].W) * views[i].H * K;
-      BwdBlocking b = bwd_blocking(K, T);
-      const int gb2 = (b.GB + 1) / 2;
-      const double eff = (static_cast<double>(gb2) * b.S / T) * (static_cast<double>(K) / (b.n_gb * 2.0 * gb2));
-      num += pairs * eff;
-      den += pairs;
+      const BwdBlocking b = bwd_blocking(K, T);
+      cost += static_cast<double>(view_entries(views[i])) * (K / bwd_lane_fill(K, T, b.n_gb) + 5.0 * b.n_gb);
     }
-    const double eff = den > 0 ? num / den : 0.0;
-    if (eff > best_eff + 1e-9 || (std::fabs(eff - best_eff) <= 1e-9 && T > best)) {
-      best_eff = eff;
+    if (best_cost < 0.0 || cost < best_cost - 1e-9 || (std::fabs(cost - best_cost) <= 1e-9 && T > best)) {
+      best_cost = cost;
       best = T;
     }
   }
