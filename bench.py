@@ -102,18 +102,23 @@ def csrc_sha256() -> str:
     return h.hexdigest()
 
 
-def profiled_traffic():
+def profiled_traffic(tiles=None):
     """DRAM bytes (read + write) per launch of the backward kernel from the
-    committed ncu summary, or None if the kernel sources changed since the capture."""
+    committed ncu summary, or None if the kernel sources or the launch tiles
+    changed since the capture."""
     try:
         txt = open(PROFILE).read()
     except OSError:
         return None
     vals = dict(line.split(":", 1) for line in txt.splitlines() if line.startswith(("dram_bytes_per_launch",
-                                                                                    "source_sha256")))
+                                                                                    "source_sha256", "tiles")))
     sha = next((v for k, v in vals.items() if k.startswith("source_sha256")), "").strip()
     if not sha or sha.split()[-1] != csrc_sha256():
         return None
+    if tiles is not None:
+        want = " ".join(f"{k}={int(v)}" for k, v in sorted(tiles.items()))
+        if vals.get("tiles", "").strip() != want:
+            return None
     try:
         return int(vals["dram_bytes_per_launch"])
     except (KeyError, ValueError):
@@ -433,7 +438,8 @@ def run_gpu(args):
     }
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
     # the committed ncu summary covers the two-parameter backward on the orbit workload
-    roofline["traffic"] = profiled_traffic() if args.workload == "orbit" and not ac else None
+    roofline["traffic"] = (profiled_traffic({k: int(getattr(tuned_params, k)) for k in autotune.TUNED_FIELDS})
+                           if args.workload == "orbit" and not ac else None)
     fwd_ms = t_f / args.steps
     line = {
         "metric": METRIC,
