@@ -305,6 +305,7 @@ def run_gpu(args):
         cache_path=os.environ.get("FMB_AUTOTUNE_CACHE") or
         os.path.join(tempfile.gettempdir(), f"fmb_autotune_{os.getpid()}.json"))
     batched = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), tuned_params, device=dev)
+    ksplit = fmb.fmb_forward_ksplit(tuned_params, s.obj_offsets, batched.c_views)
     side = torch.cuda.Stream(dev)
     side.wait_stream(torch.cuda.current_stream(dev))
     with torch.cuda.stream(side):
@@ -460,6 +461,7 @@ def run_gpu(args):
                    "launch": "batched: one forward and one backward call for all views, autotuned tiles, "
                              "each pass replayed from a CUDA graph",
                    "tiles": {k: int(getattr(tuned_params, k)) for k in autotune.TUNED_FIELDS},
+                   "fwd_ksplit": ksplit,
                    "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "plain": {"value": plain_value, "ms_per_step": ms_plain,
@@ -475,7 +477,8 @@ def run_gpu(args):
                           "variant": "weighted blending" if not ac else "alpha compositing"},
         "roofline": roofline,
         "clocks": clocks,
-        "gpu_launches": 5 * args.steps,  # prologue + forward; zeroing + prologue + backward per step
+        # prologue + forward (+ the merge of a Gaussian-split forward); zeroing + prologue + backward
+        "gpu_launches": (5 + (1 if ksplit > 1 else 0)) * args.steps,
         "e2e": e2e,
     }
     if args.points:

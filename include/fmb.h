@@ -93,6 +93,16 @@ typedef struct {
                         colours and color/g_color/grad_colors arguments are then
                         required / used); 0: no colours (those arguments are ignored).
                         Not with store_pairs. */
+  int fwd_ksplit;    /* forward Gaussian splitting, for batches with too few rays to fill
+                        the GPU (a ray minibatch, one small view): each of n splits renders
+                        a share of every object's Gaussians into per-ray partial sums (32
+                        bytes per ray and split, in the workspace), which a second kernel
+                        merges (the max-shifted sums of Eq. 3 combine exactly) and turns
+                        into the planes.  0 = automatic (split when the rays fill fewer
+                        than two waves of the GPU, at least 16 Gaussians per split),
+                        1 = never, 2..8 = that many splits.  Two-parameter model only;
+                        ignored with colors or store_pairs. */
+  int reserved;      /* 0 */
 } fmb_params;
 
 /* One camera view of one object.  Planes of the view start at pixel `pix_offset`
@@ -257,6 +267,14 @@ fmb_status fmb_loss_attribution(const fmb_params* params, int n_objects, const l
  * fmb_last_error). */
 size_t fmb_workspace_bytes(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
                            int n_views, const fmb_view* h_views);
+
+/* Gaussian splits the two-parameter forward uses for this batch (params->fwd_ksplit
+ * resolved: 1 = unsplit; a split forward launches one more kernel, the merge of the
+ * per-ray partial sums).  Host-only query, like fmb_workspace_bytes; 0 on invalid
+ * input (message in fmb_last_error).  The paper has no counterpart: this reports
+ * a launch decision of this implementation. */
+int fmb_forward_ksplit(const fmb_params* params, int n_objects, const long long* h_obj_offsets, int n_views,
+                       const fmb_view* h_views);
 
 /* Copies the device status word of a workspace to *h_status and synchronises
  * `stream`: 0 = no device-side error; nonzero = a bounded wait gave up (the

@@ -119,6 +119,9 @@ struct Plan {
   int ray_tile = 480;
   int bwd_threads = 160;
   int ac_run = 1;  // alpha compositing: forward rays per warp
+  int ksplit = 1;  // two-parameter forward: Gaussian splits per view (1 = unsplit)
+  long long fwd_part_floats = 0;  // split forward: per-ray partial sums
+  std::vector<fmb::Batch> fmerge;  // split forward: merge launches (one per forward launch)
 };
 
 fmb_status validate_scene(const fmb_params* p, int n_objects, const long long* offs, int n_views,
@@ -141,6 +144,7 @@ fmb_status validate_scene(const fmb_params* p, int n_objects, const long long* o
       p->fwd_rays_per_thread != 4)
     return fail(FMB_ERR_INVALID_ARG, "fwd_rays_per_thread must be 0, 1, 2 or 4");
   if (p->fwd_threads != 0 && p->fwd_threads != 128) return fail(FMB_ERR_INVALID_ARG, "fwd_threads must be 0 or 128");
+  if (p->fwd_ksplit < 0 || p->fwd_ksplit > 8) return fail(FMB_ERR_INVALID_ARG, "fwd_ksplit must be in [0, 8]");
   if (p->bwd_ray_tile != 0 && (p->bwd_ray_tile < 32 || p->bwd_ray_tile > 1024))
     return fail(FMB_ERR_INVALID_ARG, "bwd_ray_tile must be in [32, 1024] (0 = default)");
   if (p->bwd_threads != 0 && (p->bwd_threads < 32 || p->bwd_threads > 160 || (p->bwd_threads % 32) != 0))
@@ -211,18 +215,38 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
   pl.ray_tile = p->bwd_ray_tile > 0 ? p->bwd_ray_tile : 3 * pl.bwd_threads;
   pl.n_gauss = offs[n_objects];
   const bool ac = p->variant == 1;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();  // no device (a host-only size query): plan for 152 SMs
+    sms = 152;
+  }
   if (ac) {
     long long total = 0;
     for (int i = 0; i < n_views; ++i) total += view_entries(views[i]);
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-      cudaGetLastError();  // no device (a host-only size query): plan for 152 SMs
-      sms = 152;
-    }
     pl.ac_run = fmb::ac_fwd_run(total, sms);
   }
   const int rays_fwd = ac ? fmb::ac_fwd_rays_per_item(pl.ac_run) : fmb::forward_rays_per_cta(pl.rpt);
+  // Gaussian split of the two-parameter forward: when the batch's ray tiles fill
+  // fewer than two waves of the GPU (about 6 resident forward CTAs per SM), each
+  // tile's Gaussians are spread over up to 8 CTAs of at least 16 Gaussians each.
+  if (!ac && !p->colors && !p->store_pairs && pl.rpt % 2 == 0 && p->fwd_ksplit != 1) {
+    if (p->fwd_ksplit > 1) {
+      pl.ksplit = p->fwd_ksplit;
+    } else {
+      long long tiles = 0;
+      int maxK = 1;
+      for (int i = 0; i < n_views; ++i) {
+        tiles += (view_entries(views[i]) + rays_fwd - 1) / rays_fwd;
+        maxK = std::max(maxK, static_cast<int>(offs[views[i].object + 1] - offs[views[i].object]));
+      }
+      const long long want = 2ll * std::max(sms, 1) * 6;
+      if (tiles > 0 && tiles < want) {
+        const long long k = (want + tiles - 1) / tiles;
+        pl.ksplit = static_cast<int>(std::max(1ll, std::min({k, 8ll, static_cast<long long>(maxK / 16)})));
+      }
+    }
+  }
   const int n_flow = p->n_flow;
   long long rec = 0, part = 0, pairs = 0;
   for (int base = 0; base < n_views; base += fmb::kMaxBatchViews) {
@@ -261,8 +285,16 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
       // forward
       fmb::DevView df = d;
       df.n_tiles = static_cast<int>((P + rays_fwd - 1) / rays_fwd);
-      df.n_gblocks = 1;
-      ctas_f += df.n_tiles;
+      {
+        // split s renders Gaussians [s GB, min(K, (s + 1) GB)); every split is non-empty
+        const int S0 = std::min(pl.ksplit, d.K);
+        df.GB = (d.K + S0 - 1) / S0;
+        df.n_gblocks = (d.K + df.GB - 1) / df.GB;
+        df.S = df.n_gblocks;
+        df.part_off = pl.fwd_part_floats;
+        if (df.n_gblocks > 1) pl.fwd_part_floats += 8 * P * df.n_gblocks;
+      }
+      ctas_f += static_cast<long long>(df.n_tiles) * df.n_gblocks;
       bf.v[i] = df;
       // backward
       fmb::DevView db = d;
@@ -282,8 +314,21 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
     if (ctas_f > 0x7fffffffll || ctas_b > 0x7fffffffll) throw std::runtime_error("grid too large");
     // Work items view by view, the views ordered by decreasing cost per item
     // (forward: K x rays per tile; backward: Gaussians per block x rays per tile).
-    order_items(bf, [&](const fmb::DevView& v) { return static_cast<double>(v.K); },
-                [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles); });
+    order_items(bf, [&](const fmb::DevView& v) { return static_cast<double>(v.GB); },
+                [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles) * v.n_gblocks; });
+    if (pl.ksplit > 1) {
+      // the merge: one item per tile of forward_merge_rays_per_item() rays of a view
+      fmb::Batch bm = bf;
+      const int rm = fmb::forward_merge_rays_per_item();
+      for (int i = 0; i < nb; ++i) {
+        // views left unsplit (fewer Gaussians than splits) were finished by the forward
+        bm.v[i].n_tiles = bm.v[i].S > 1 ? (bm.v[i].P + rm - 1) / rm : 0;
+        bm.v[i].n_gblocks = 1;
+      }
+      order_items(bm, [&](const fmb::DevView& v) { return static_cast<double>(v.S); },
+                  [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles); });
+      pl.fmerge.push_back(bm);
+    }
     order_items(bb, [&](const fmb::DevView& v) { return static_cast<double>(v.GB); },
                 [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles) * v.n_gblocks; });
     pl.fwd.push_back(bf);
@@ -311,10 +356,14 @@ size_t pairs_offset(const fmb_params* p, const Plan& pl) {
   return bytes;
 }
 
-size_t workspace_needed(const fmb_params* p, const Plan& pl) {
+size_t fwd_part_offset(const fmb_params* p, const Plan& pl) {
   size_t bytes = pairs_offset(p, pl);
-  if (p->store_pairs) bytes += 3 * static_cast<size_t>(pl.pair_stride) * sizeof(float);
+  if (p->store_pairs) bytes += align256(3 * static_cast<size_t>(pl.pair_stride) * sizeof(float));
   return bytes;
+}
+
+size_t workspace_needed(const fmb_params* p, const Plan& pl) {
+  return fwd_part_offset(p, pl) + align256(static_cast<size_t>(pl.fwd_part_floats) * sizeof(float));
 }
 
 fmb::Consts make_consts(const fmb_params* p) {
@@ -357,6 +406,17 @@ void fmb_default_params(fmb_params* p) {
 const char* fmb_last_error(void) { return g_err.c_str(); }
 
 const char* fmb_version(void) { return "fmb-gb300 0.1 (sm_103a)"; }
+
+int fmb_forward_ksplit(const fmb_params* params, int n_objects, const long long* h_obj_offsets, int n_views,
+                       const fmb_view* h_views) {
+  try {
+    if (validate_scene(params, n_objects, h_obj_offsets, n_views, h_views) != FMB_OK) return 0;
+    return make_plan(params, h_obj_offsets, n_objects, n_views, h_views).ksplit;
+  } catch (const std::exception& e) {
+    fail(FMB_ERR_INVALID_ARG, e.what());
+    return 0;
+  }
+}
 
 size_t fmb_workspace_bytes(const fmb_params* params, int n_objects, const long long* h_obj_offsets, int n_views,
                            const fmb_view* h_views) {
@@ -418,6 +478,7 @@ fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const lon
       if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
       fmb::FwdOut fo{depth, alpha, normal, flow, saved, pairs, pl.pair_stride};
       fo.color = color;
+      fo.part = reinterpret_cast<float*>(static_cast<char*>(workspace) + fwd_part_offset(params, pl));
       if (params->variant == 1) {
         fo.pairs = nullptr;
         e = fmb::launch_forward_ac(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.maxK, fo, pl.ac_run,
@@ -425,6 +486,8 @@ fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const lon
       } else {
         e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, pl.maxK, fo,
                                 status, counter, s);
+        if (e == cudaSuccess && pl.ksplit > 1)
+          e = fmb::launch_forward_merge(pl.fmerge[bi], sc, params->want_normals != 0, params->n_flow, fo, s);
       }
       if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     }
@@ -717,6 +780,9 @@ extern "C" fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n
     if (st != FMB_OK) return st;
     if (params->store_pairs)
       return fail(FMB_ERR_INVALID_ARG, "store_pairs needs a workspace (use fmb_render_forward)");
+    fmb_params unsplit = *params;  // the fixed scratch holds the records only: no Gaussian split
+    unsplit.fwd_ksplit = 1;
+    params = &unsplit;
     Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views);
     if (params->colors && (!colors || !color))
       return fail(FMB_ERR_INVALID_ARG, "colors and color are required when params->colors is set");

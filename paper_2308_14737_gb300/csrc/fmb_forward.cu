@@ -186,6 +186,76 @@ __device__ __forceinline__ PairOut2 fwd_pair2(RayAcc2& A, const GaussRec2& g, f2
 }
 
 
+// The accumulator of ray r of a thread (unpacked from its f32x2 lane when packed).
+template <bool PACKED, int NA, int NP>
+__device__ __forceinline__ RayAcc ray_acc_of(const RayAcc (&A)[NA], const RayAcc2 (&A2)[NP], int r) {
+  if (!PACKED) return A[r];
+  RayAcc a;
+  const RayAcc2& b = A2[r / 2];
+  const bool h = (r & 1) != 0;
+  a.v0 = h ? hi(b.v0) : lo(b.v0);
+  a.v1 = h ? hi(b.v1) : lo(b.v1);
+  a.v2 = h ? hi(b.v2) : lo(b.v2);
+  a.vl0 = a.vl1 = a.vl2 = 0.f;
+  a.m = h ? hi(b.m) : lo(b.m);
+  a.Sw = h ? hi(b.Sw) : lo(b.Sw);
+  a.Swt = h ? hi(b.Swt) : lo(b.Swt);
+  a.Sd = h ? hi(b.Sd) : lo(b.Sd);
+  a.N0 = h ? hi(b.N0) : lo(b.N0);
+  a.N1 = h ? hi(b.N1) : lo(b.N1);
+  a.N2 = h ? hi(b.N2) : lo(b.N2);
+  return a;
+}
+
+// Per-pixel epilogue (Eq. 3, Eq. 8, Sec. 5, Sec. 6) from a ray's sums: depth, alpha,
+// the saved normalisers, the camera-frame unit normal and the flow to each target.
+template <bool NORMALS, int NFLOW>
+__device__ __forceinline__ void write_ray_outputs(const DevView& V, const float R[9], const float o[3],
+                                                  const float (*Rj)[9], const float (*tj)[3], const bool* has_t,
+                                                  const RayAcc& a, const float pxy[2], long long p,
+                                                  const FwdOut& out) {
+  const int P = V.P;
+  const long long off = V.pix_off;
+  const float iSw = 1.0f / a.Sw;
+  const float D = a.Swt * iSw;
+  out.depth[off + p] = D;
+  out.alpha[off + p] = -expm1f(-a.Sd);
+  float* sv = out.saved + 3 * off;
+  sv[p] = a.m + log2f(a.Sw);
+  sv[P + p] = a.Sd;
+  if (NORMALS) {
+    const float N0 = a.N0 * iSw, N1 = a.N1 * iSw, N2 = a.N2 * iSw;
+    const float Nn = sqrtf(fmaf(N0, N0, fmaf(N1, N1, N2 * N2)));
+    const float iN = Nn > 0.f ? 1.0f / Nn : 0.f;
+    const float n0 = N0 * iN, n1 = N1 * iN, n2 = N2 * iN;
+    float* nrm = out.normal + 3 * off;
+    nrm[p] = fmaf(R[2], n2, fmaf(R[1], n1, R[0] * n0));
+    nrm[P + p] = fmaf(R[5], n2, fmaf(R[4], n1, R[3] * n0));
+    nrm[2 * P + p] = fmaf(R[8], n2, fmaf(R[7], n1, R[6] * n0));
+    sv[2 * P + p] = Nn;
+  } else {
+    sv[2 * P + p] = 0.f;
+  }
+  if (NFLOW > 0) {
+    const float p0 = fmaf(a.v0, D, o[0]), p1 = fmaf(a.v1, D, o[1]), p2 = fmaf(a.v2, D, o[2]);
+    float* fl = out.flow + 2 * NFLOW * off;
+#pragma unroll
+    for (int j = 0; j < NFLOW; ++j) {
+      float fu = 0.f, fv = 0.f;
+      if (has_t[j]) {
+        const float X0 = fmaf(Rj[j][2], p2, fmaf(Rj[j][1], p1, fmaf(Rj[j][0], p0, tj[j][0])));
+        const float X1 = fmaf(Rj[j][5], p2, fmaf(Rj[j][4], p1, fmaf(Rj[j][3], p0, tj[j][1])));
+        const float X2 = fmaf(Rj[j][8], p2, fmaf(Rj[j][7], p1, fmaf(Rj[j][6], p0, tj[j][2])));
+        const float iz = 1.0f / X2;
+        fu = fmaf(V.fx * X0, iz, V.cx) - pxy[0];
+        fv = fmaf(V.fy * X1, iz, V.cy) - pxy[1];
+      }
+      fl[(2 * j) * P + p] = fu;
+      fl[(2 * j + 1) * P + p] = fv;
+    }
+  }
+}
+
 // Shared-memory stage: kChunk records (4 float4 each), then in colour mode their
 // kChunk colour records (1 float4 each).
 template <bool COLOR>
@@ -213,11 +283,16 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
   for (int round = 0;; ++round) {
   const int item = next_item(counter, round, &s_item);
   if (item < 0 || item >= batch.n_items) break;
-  int tile;
-  const int vi = find_item(batch, item, tile);
+  int local;
+  const int vi = find_item(batch, item, local);
   const DevView& V = batch.v[vi];
   const int P = V.P;
-  const int K = V.K;
+  // Gaussian split ks of n_gblocks (1 unless the batch is split): Gaussians
+  // [ks GB, min(K, (ks + 1) GB)) of the view's object
+  const int tile = local / V.n_gblocks;
+  const int ks = local - tile * V.n_gblocks;
+  const int kbeg = ks * V.GB;
+  const int K = min(V.GB, V.K - kbeg);
 
   float R[9], tp[3];
   load_pose(s.poses, V.pose, R, tp);
@@ -226,10 +301,10 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
   const float o2 = -fmaf(R[8], tp[2], fmaf(R[5], tp[1], R[2] * tp[0]));
 
   // Stage the first record chunks while the rays are set up.
-  const float4* src = records + kRecFloat4 * V.rec_off;
+  const float4* src = records + kRecFloat4 * (V.rec_off + kbeg);
   const int nchunks = (K + kChunk - 1) / kChunk;
   constexpr int SST = fwd_stage_float4<COLOR>();
-  const float4* csrc = COLOR ? s.crec + V.rec_off : nullptr;
+  const float4* csrc = COLOR ? s.crec + V.rec_off + kbeg : nullptr;
   if (tid == 0) {
     for (int c = 0; c < 2 && c < nchunks; ++c) {
       const int n = min(kChunk, K - c * kChunk);
@@ -360,6 +435,20 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
   uses0 += (nchunks + 1) / 2;
   uses1 += nchunks / 2;
 
+  if (V.n_gblocks > 1) {
+    // Gaussian split: this split's partial sums for fwd_merge_kernel
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      if (pix[r] >= P) continue;
+      const RayAcc a = ray_acc_of<PACKED, NA, NP>(A, A2, r);
+      float4* q = reinterpret_cast<float4*>(out.part + V.part_off +
+                                            8 * (static_cast<long long>(pix[r]) * V.n_gblocks + ks));
+      q[0] = make_float4(a.m, a.Sw, a.Swt, a.Sd);
+      q[1] = make_float4(a.N0, a.N1, a.N2, 0.f);
+    }
+    continue;
+  }
+
   // Flow targets (uniform over the CTA).
   float Rj[NFLOW > 0 ? NFLOW : 1][9], tj[NFLOW > 0 ? NFLOW : 1][3];
   bool has_t[NFLOW > 0 ? NFLOW : 1];
@@ -371,30 +460,14 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
   }
 
   const long long off = V.pix_off;
+  const float o[3] = {o0, o1, o2};
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     if (pix[r] >= P) continue;
     const long long p = pix[r];
-    RayAcc a;
-    if (PACKED) {
-      const RayAcc2& b = A2[r / 2];
-      const bool h = (r & 1) != 0;
-      a.v0 = h ? hi(b.v0) : lo(b.v0);
-      a.v1 = h ? hi(b.v1) : lo(b.v1);
-      a.v2 = h ? hi(b.v2) : lo(b.v2);
-      a.m = h ? hi(b.m) : lo(b.m);
-      a.Sw = h ? hi(b.Sw) : lo(b.Sw);
-      a.Swt = h ? hi(b.Swt) : lo(b.Swt);
-      a.Sd = h ? hi(b.Sd) : lo(b.Sd);
-      a.N0 = h ? hi(b.N0) : lo(b.N0);
-      a.N1 = h ? hi(b.N1) : lo(b.N1);
-      a.N2 = h ? hi(b.N2) : lo(b.N2);
-    } else {
-      a = A[PACKED ? 0 : r];
-    }
-    const float iSw = 1.0f / a.Sw;
-    const float D = a.Swt * iSw;
+    const RayAcc a = ray_acc_of<PACKED, NA, NP>(A, A2, r);
     if (COLOR) {
+      const float iSw = 1.0f / a.Sw;
       const RayAcc2& b = A2[r / 2];
       const bool h = (r & 1) != 0;
       float* col = out.color + 3 * off;
@@ -402,42 +475,7 @@ __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_const
       col[P + p] = (h ? hi(b.C1) : lo(b.C1)) * iSw;
       col[2 * P + p] = (h ? hi(b.C2) : lo(b.C2)) * iSw;
     }
-    out.depth[off + p] = D;
-    out.alpha[off + p] = -expm1f(-a.Sd);
-    float* sv = out.saved + 3 * off;
-    sv[p] = a.m + log2f(a.Sw);
-    sv[P + p] = a.Sd;
-    if (NORMALS) {
-      const float N0 = a.N0 * iSw, N1 = a.N1 * iSw, N2 = a.N2 * iSw;
-      const float Nn = sqrtf(fmaf(N0, N0, fmaf(N1, N1, N2 * N2)));
-      const float iN = Nn > 0.f ? 1.0f / Nn : 0.f;
-      const float n0 = N0 * iN, n1 = N1 * iN, n2 = N2 * iN;
-      float* nrm = out.normal + 3 * off;
-      nrm[p] = fmaf(R[2], n2, fmaf(R[1], n1, R[0] * n0));
-      nrm[P + p] = fmaf(R[5], n2, fmaf(R[4], n1, R[3] * n0));
-      nrm[2 * P + p] = fmaf(R[8], n2, fmaf(R[7], n1, R[6] * n0));
-      sv[2 * P + p] = Nn;
-    } else {
-      sv[2 * P + p] = 0.f;
-    }
-    if (NFLOW > 0) {
-      const float p0 = fmaf(a.v0, D, o0), p1 = fmaf(a.v1, D, o1), p2 = fmaf(a.v2, D, o2);
-      float* fl = out.flow + 2 * NFLOW * off;
-#pragma unroll
-      for (int j = 0; j < NFLOW; ++j) {
-        float fu = 0.f, fv = 0.f;
-        if (has_t[j]) {
-          const float X0 = fmaf(Rj[j][2], p2, fmaf(Rj[j][1], p1, fmaf(Rj[j][0], p0, tj[j][0])));
-          const float X1 = fmaf(Rj[j][5], p2, fmaf(Rj[j][4], p1, fmaf(Rj[j][3], p0, tj[j][1])));
-          const float X2 = fmaf(Rj[j][8], p2, fmaf(Rj[j][7], p1, fmaf(Rj[j][6], p0, tj[j][2])));
-          const float iz = 1.0f / X2;
-          fu = fmaf(V.fx * X0, iz, V.cx) - pxy[r][0];
-          fv = fmaf(V.fy * X1, iz, V.cy) - pxy[r][1];
-        }
-        fl[(2 * j) * P + p] = fu;
-        fl[(2 * j + 1) * P + p] = fv;
-      }
-    }
+    write_ray_outputs<NORMALS, NFLOW>(V, R, o, Rj, tj, has_t, a, pxy[r], p, out);
   }
   (void)vc;
   }  // item loop
@@ -505,6 +543,81 @@ cudaError_t launch_forward(const Batch& b, const Scene& s, const Consts& c, cons
 }
 
 int forward_rays_per_cta(int rpt) { return kFwdThreads * rpt; }
+
+// ------------------------------------------------ merge of a Gaussian-split forward
+// One thread per ray.  Each split left its max-shifted sums (m_s, Sw_s, Swt_s, Sd_s,
+// N_s); brought to the largest shift m they add exactly like the terms of one pass:
+// Sw = sum_s 2^(m_s - m) Sw_s (likewise Swt and N), Sd = sum_s Sd_s.  The epilogue
+// then writes the planes as the unsplit forward does.
+constexpr int kMergeThreads = 128;
+int forward_merge_rays_per_item() { return kMergeThreads; }
+
+template <bool NORMALS, int NFLOW>
+__global__ void __launch_bounds__(kMergeThreads) fwd_merge_kernel(const __grid_constant__ Batch batch, Scene s,
+                                                                  FwdOut out) {
+  int local;
+  const int vi = find_item(batch, blockIdx.x, local);
+  const DevView& V = batch.v[vi];
+  const int P = V.P;
+  const long long p = static_cast<long long>(local) * kMergeThreads + threadIdx.x;
+  if (p >= P) return;
+  float R[9], tp[3];
+  load_pose(s.poses, V.pose, R, tp);
+  const float o[3] = {-fmaf(R[6], tp[2], fmaf(R[3], tp[1], R[0] * tp[0])),
+                      -fmaf(R[7], tp[2], fmaf(R[4], tp[1], R[1] * tp[0])),
+                      -fmaf(R[8], tp[2], fmaf(R[5], tp[1], R[2] * tp[0]))};
+  float Rj[NFLOW > 0 ? NFLOW : 1][9], tj[NFLOW > 0 ? NFLOW : 1][3];
+  bool has_t[NFLOW > 0 ? NFLOW : 1];
+#pragma unroll
+  for (int j = 0; j < NFLOW; ++j) {
+    const int tg = j == 0 ? V.tgt0 : V.tgt1;
+    has_t[j] = tg >= 0;
+    if (has_t[j]) load_pose(s.poses, tg, Rj[j], tj[j]);
+  }
+  float vc[3], v[3], vl[3], pxy[2];
+  pixel_ray_dd(V, R, ray_pixel(V, static_cast<int>(p)), vc, v, vl, pxy);
+  const int S = V.S;  // splits of this view
+  const float4* q = reinterpret_cast<const float4*>(out.part + V.part_off + 8 * p * S);
+  float m = -INFINITY;
+  for (int k = 0; k < S; ++k) m = fmaxf(m, q[2 * k].x);
+  RayAcc a;
+  a.v0 = v[0];
+  a.v1 = v[1];
+  a.v2 = v[2];
+  a.vl0 = vl[0];
+  a.vl1 = vl[1];
+  a.vl2 = vl[2];
+  a.m = m;
+  a.Sw = a.Swt = a.Sd = a.N0 = a.N1 = a.N2 = 0.f;
+  for (int k = 0; k < S; ++k) {
+    const float4 q0 = q[2 * k], q1 = q[2 * k + 1];
+    const float sc = ex2_approx(q0.x - m);
+    a.Sw = fmaf(sc, q0.y, a.Sw);
+    a.Swt = fmaf(sc, q0.z, a.Swt);
+    a.Sd += q0.w;
+    if (NORMALS) {
+      a.N0 = fmaf(sc, q1.x, a.N0);
+      a.N1 = fmaf(sc, q1.y, a.N1);
+      a.N2 = fmaf(sc, q1.z, a.N2);
+    }
+  }
+  write_ray_outputs<NORMALS, NFLOW>(V, R, o, Rj, tj, has_t, a, pxy, p, out);
+}
+
+cudaError_t launch_forward_merge(const Batch& b, const Scene& s, bool normals, int n_flow, const FwdOut& o,
+                                 cudaStream_t st) {
+  if (b.n_items <= 0) return cudaSuccess;
+  if (normals) {
+    if (n_flow == 0) fwd_merge_kernel<true, 0><<<b.n_items, kMergeThreads, 0, st>>>(b, s, o);
+    else if (n_flow == 1) fwd_merge_kernel<true, 1><<<b.n_items, kMergeThreads, 0, st>>>(b, s, o);
+    else fwd_merge_kernel<true, 2><<<b.n_items, kMergeThreads, 0, st>>>(b, s, o);
+  } else {
+    if (n_flow == 0) fwd_merge_kernel<false, 0><<<b.n_items, kMergeThreads, 0, st>>>(b, s, o);
+    else if (n_flow == 1) fwd_merge_kernel<false, 1><<<b.n_items, kMergeThreads, 0, st>>>(b, s, o);
+    else fwd_merge_kernel<false, 2><<<b.n_items, kMergeThreads, 0, st>>>(b, s, o);
+  }
+  return cudaGetLastError();
+}
 
 int forward_ctas_per_sm(bool normals, int n_flow, int rpt, int maxK) {
   (void)normals;

@@ -371,6 +371,11 @@ struct FwdOut;
 cudaError_t launch_forward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
                            int n_flow, int rpt, int maxK, const FwdOut& o, int* status, int* counter,
                            cudaStream_t st);
+// Gaussian-split forward: the merge of the splits' partial sums (o.part) into the
+// planes; work items of forward_merge_rays_per_item() rays, the split count in DevView::S.
+int forward_merge_rays_per_item();
+cudaError_t launch_forward_merge(const Batch& b, const Scene& s, bool normals, int n_flow, const FwdOut& o,
+                                 cudaStream_t st);
 
 struct FwdOut {
   float* depth;
@@ -381,6 +386,7 @@ struct FwdOut {
   float* pairs;             // stored-intermediate mode: [t | e2 | delta] arrays, else null
   long long pair_stride;    // floats per array
   float* color = nullptr;   // colour plane [3][P_v] per view (colour mode)
+  float* part = nullptr;    // Gaussian-split forward: per-ray partial sums, 8 floats per (ray, split)
 };
 
 struct ZeroJob {

@@ -32,7 +32,7 @@ class FmbParams(ctypes.Structure):
                 ("deterministic", ctypes.c_int), ("use_persistent", ctypes.c_int),
                 ("fwd_rays_per_thread", ctypes.c_int), ("fwd_threads", ctypes.c_int),
                 ("bwd_ray_tile", ctypes.c_int), ("bwd_threads", ctypes.c_int), ("store_pairs", ctypes.c_int),
-                ("colors", ctypes.c_int)]
+                ("colors", ctypes.c_int), ("fwd_ksplit", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class FmbView(ctypes.Structure):
@@ -85,6 +85,8 @@ def load_library(path: str = LIB_PATH):
     L.fmb_loss_attribution.restype = ctypes.c_int
     L.fmb_workspace_bytes.argtypes = [P, i, LL, i, V]
     L.fmb_workspace_bytes.restype = sz
+    L.fmb_forward_ksplit.argtypes = [P, i, LL, i, V]
+    L.fmb_forward_ksplit.restype = ctypes.c_int
     L.fmb_read_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
     L.fmb_read_device_status.restype = ctypes.c_int
     L.fmb_last_error.argtypes = []
@@ -170,6 +172,17 @@ def fmb_workspace_bytes(params: FmbParams, obj_offsets, views) -> int:
     o, op = _offsets(obj_offsets)
     va = views if isinstance(views, ctypes.Array) else make_views(views)
     n = L.fmb_workspace_bytes(ctypes.byref(params), len(o) - 1, op, len(va), va)
+    if n == 0:
+        raise FmbError(1, L.fmb_last_error().decode())
+    return int(n)
+
+
+def fmb_forward_ksplit(params: FmbParams, obj_offsets, views) -> int:
+    """Gaussian splits the two-parameter forward uses for this batch (1 = unsplit)."""
+    L = load_library()
+    o, op = _offsets(obj_offsets)
+    va = views if isinstance(views, ctypes.Array) else make_views(views)
+    n = L.fmb_forward_ksplit(ctypes.byref(params), len(o) - 1, op, len(va), va)
     if n == 0:
         raise FmbError(1, L.fmb_last_error().decode())
     return int(n)

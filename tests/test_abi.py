@@ -43,7 +43,7 @@ def test_struct_layouts(fmb):
     assert ctypes.sizeof(fmb.FmbView) == 64
     assert fmb.FmbView.pix_offset.offset == 40
     assert fmb.FmbView.rays.offset == 48 and fmb.FmbView.n_rays.offset == 56
-    assert ctypes.sizeof(fmb.FmbParams) == 56
+    assert ctypes.sizeof(fmb.FmbParams) == 64
     assert fmb.FmbParams.store_pairs.offset == 48 and fmb.FmbParams.colors.offset == 52
 
 

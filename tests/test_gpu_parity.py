@@ -70,6 +70,36 @@ def test_normals_off():
     _full_check(s, n_flow=1, normals=False)
 
 
+@pytest.mark.parametrize("ksplit", [2, 3, 8])
+def test_gaussian_split_forward(ksplit):
+    """Forward with each object's Gaussians split over ksplit CTAs per ray tile and the
+    per-ray partial sums merged: planes and (through the saved normalisers) gradients
+    against the oracle, including objects with fewer Gaussians than splits (those
+    views stay unsplit in the same launch, and the merge must leave them alone)."""
+    _full_check(synth.object_orbit(K=100, n_views=3, W=48, H=40), n_flow=1, fwd_ksplit=ksplit)
+    _full_check(_ragged_scene(), n_flow=1, fwd_ksplit=ksplit)
+    _full_check(synth.reconstruction(n_views=3, K=37, W=40, H=30), n_flow=2, normals=False, fwd_ksplit=ksplit)
+
+
+def test_gaussian_split_forward_ray_batch_and_auto():
+    """The automatic split (a 50 000-ray minibatch and a single 64x64 view both fill
+    less than two waves of the GPU) against the unsplit forward: the same planes up to
+    the rounding of the merge."""
+    from paper_2308_14737_gb300 import synth as sy
+
+    for scene, nf, nrm in ((sy.ray_batch(sy.reconstruction(n_views=20, K=256, W=160, H=120), 6000, seed=2), 2, 0),
+                           (sy.single_view(), 0, 1)):
+        outs = []
+        for ks in (1, 0):
+            params = fmb.default_params(n_flow=nf, want_normals=nrm, fwd_ksplit=ks)
+            gpu, r, dev = gpu_forward(scene, params)
+            outs.append(gpu)
+        for k in ("depth", "alpha"):
+            assert np.allclose(outs[0][k], outs[1][k], rtol=1e-5, atol=1e-6), k
+        sv0, sv1 = outs[0]["saved"], outs[1]["saved"]
+        assert np.allclose(sv0, sv1, rtol=1e-5, atol=1e-5)
+
+
 @pytest.mark.parametrize("normals,n_flow,deterministic", [(True, 1, False), (False, 2, False), (True, 0, True),
                                                          (False, 0, True)])
 def test_backward_without_pose_gradients(normals, n_flow, deterministic):
