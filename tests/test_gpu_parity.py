@@ -82,9 +82,9 @@ def test_gaussian_split_forward(ksplit):
 
 
 def test_gaussian_split_forward_ray_batch_and_auto():
-    """The automatic split (a 50 000-ray minibatch and a single 64x64 view both fill
-    less than two waves of the GPU) against the unsplit forward: the same planes up to
-    the rounding of the merge."""
+    """The automatic choice against the unsplit forward (a 6000-ray minibatch at
+    K = 256 is split, a single 64x64 view at K = 40 is not): the same planes up to the
+    rounding of the merge."""
     from paper_2308_14737_gb300 import synth as sy
 
     for scene, nf, nrm in ((sy.ray_batch(sy.reconstruction(n_views=20, K=256, W=160, H=120), 6000, seed=2), 2, 0),
@@ -94,6 +94,8 @@ def test_gaussian_split_forward_ray_batch_and_auto():
             params = fmb.default_params(n_flow=nf, want_normals=nrm, fwd_ksplit=ks)
             gpu, r, dev = gpu_forward(scene, params)
             outs.append(gpu)
+            if ks == 0:
+                assert fmb.fmb_forward_ksplit(params, scene.obj_offsets, r.c_views) == (4 if nf == 2 else 1)
         for k in ("depth", "alpha"):
             assert np.allclose(outs[0][k], outs[1][k], rtol=1e-5, atol=1e-6), k
         sv0, sv1 = outs[0]["saved"], outs[1]["saved"]
