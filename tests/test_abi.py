@@ -133,7 +133,8 @@ def test_forward_rejects_bad_params(fmb):
     for k, v, msg in [("eta", 0.0, "eta"), ("variant", 3, "variant"), ("n_flow", 3, "n_flow"),
                       ("fwd_rays_per_thread", 3, "fwd_rays_per_thread"), ("bwd_threads", 100, "bwd_threads"),
                       ("bwd_threads", 192, "bwd_threads"), ("bwd_ray_tile", 16, "bwd_ray_tile"),
-                      ("store_pairs", 2, "store_pairs")]:
+                      ("store_pairs", 2, "store_pairs"), ("fwd_ksplit", 9, "fwd_ksplit"),
+                      ("fwd_ksplit", -1, "fwd_ksplit")]:
         p = fmb.default_params()
         setattr(p, k, v)
         st, err = _call_fwd(fmb, p, [0, 5], [_view()])
@@ -207,3 +208,19 @@ def test_backward_rejects_missing_outputs(fmb):
                                fp, 1, fp, 1, va, fp, fp, fp, fp, fp, fp, fp, fp, fp, None, fp, fp, fp, None, fp,
                                1 << 20, None)
     assert st == 1 and "grad_means" in L.fmb_last_error().decode()
+
+
+def test_forward_split_query(fmb):
+    """The split count the planner takes (no GPU needed): unsplit by default for a
+    full 320x240 orbit, forced when asked, never with colours or stored pairs, and
+    the workspace grows by 32 bytes per ray and split."""
+    s = synth.object_orbit(K=100, n_views=2, W=32, H=24)
+    p = fmb.default_params()
+    assert fmb.fmb_forward_ksplit(p, s.obj_offsets, s.views) == 1
+    base = fmb.fmb_workspace_bytes(p, s.obj_offsets, s.views)
+    p3 = fmb.default_params(fwd_ksplit=3)
+    assert fmb.fmb_forward_ksplit(p3, s.obj_offsets, s.views) == 3
+    grown = fmb.fmb_workspace_bytes(p3, s.obj_offsets, s.views)
+    assert grown - base >= 32 * 3 * s.n_pixels
+    assert fmb.fmb_forward_ksplit(fmb.default_params(fwd_ksplit=3, colors=1), s.obj_offsets, s.views) == 1
+    assert fmb.fmb_forward_ksplit(fmb.default_params(fwd_ksplit=3, store_pairs=1), s.obj_offsets, s.views) == 1
