@@ -158,6 +158,8 @@ typedef struct {
  * store_pairs = 1, where the forward leaves the per-pair values there for the
  * backward of the same batch (workspace size then grows by 12 bytes per pair,
  * rounded up: 12 x sum over views of P_v x (K_v rounded up to a multiple of 4)).
+ * A Gaussian-split forward (fwd_ksplit, fmb_forward_ksplit) also keeps 32 bytes per
+ * ray and split of partial sums there between its two kernels.
  */
 fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
                               const float* means, const float* chol, const float* weights, const float* colors,
