@@ -100,7 +100,9 @@ __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 4 : 5) forward_ac_kernel(
       pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
       float t[M], dl[M], n[M][3];
       const float4* crec = s.crec != nullptr && out.color != nullptr ? s.crec + V.rec_off : nullptr;
-      const AcSums a = ac_render_ray<NORMALS, M>(srec, V.K, v, vl, k, lane, t, dl, n, sd, sw, sT, key, j > 0, crec);
+      // a ray batch's consecutive entries are not neighbouring pixels: sort each afresh
+      const AcSums a = ac_render_ray<NORMALS, M>(srec, V.K, v, vl, k, lane, t, dl, n, sd, sw, sT, key,
+                                                 j > 0 && V.rays == nullptr, crec);
       if (lane == 0) {
         const float iW = a.W > 0.f ? 1.0f / a.W : 0.f;
         const float D = a.WT * iW;
@@ -315,7 +317,8 @@ __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 2 : 3) backward_ac_kernel
       pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
       float t[M], dl[M], n[M][3];
       const float4* crec = color ? s.crec + V.rec_off : nullptr;
-      const AcSums a = ac_render_ray<NORMALS, M>(srec, K, v, vl, k, lane, t, dl, n, sd, sw, sT, key, j > 0, crec);
+      const AcSums a = ac_render_ray<NORMALS, M>(srec, K, v, vl, k, lane, t, dl, n, sd, sw, sT, key,
+                                                 j > 0 && V.rays == nullptr, crec);
       const float iW = a.W > 0.f ? 1.0f / a.W : 0.f;
       const float D = a.WT * iW;
       // colour mode: Cbar and the blended colour C = sum w c / W

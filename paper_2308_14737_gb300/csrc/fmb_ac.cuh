@@ -78,12 +78,14 @@ __device__ __forceinline__ void warp_bitonic_sort(unsigned long long (&key)[M], 
 }
 
 // Ascending odd-even transposition passes over the same blocked layout until no
-// pair is out of order (at most 32 M passes, which sort any input): cheap when the
-// keys arrive nearly sorted -- the previous, neighbouring ray's depth order.
+// pair is out of order: cheap when the keys arrive nearly sorted -- the previous,
+// neighbouring ray's depth order.  At most max_passes passes (32 M sort any input);
+// returns whether the keys are sorted.  Rays that are not neighbours (the entries of
+// a random ray batch) are sorted by the bitonic network instead: from an unrelated
+// order the refinement needs up to 32 M passes.
 template <int M>
-__device__ __forceinline__ void warp_refine_sort(unsigned long long (&key)[M], int lane) {
-  constexpr int N = 32 * M;
-  for (int pass = 0; pass < N; ++pass) {
+__device__ __forceinline__ bool warp_refine_sort(unsigned long long (&key)[M], int lane, int max_passes) {
+  for (int pass = 0; pass < max_passes; ++pass) {
     bool swapped = false;
 #pragma unroll
     for (int m = 0; m + 1 < M; m += 2) {  // even pairs (lane M + m, lane M + m + 1), m even
@@ -114,9 +116,12 @@ __device__ __forceinline__ void warp_refine_sort(unsigned long long (&key)[M], i
       key[0] = prev_last;
       swapped = true;
     }
-    if (!__any_sync(kFull, swapped)) break;
+    if (!__any_sync(kFull, swapped)) return true;
   }
+  return false;
 }
+
+
 
 __device__ __forceinline__ float warp_incl_sum(float x, int lane) {
 #pragma unroll
@@ -196,7 +201,7 @@ __device__ __forceinline__ AcSums ac_render_ray(const float4* __restrict__ rec, 
                                   static_cast<unsigned>(prev[m])
                             : kNoKey;
     __syncwarp();
-    warp_refine_sort<M>(key, lane);
+    warp_refine_sort<M>(key, lane, 32 * M);  // 32 M passes sort any input
   } else {
     warp_bitonic_sort<M>(key, lane);
   }

@@ -306,6 +306,9 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
       if (ac) bk = BwdBlocking{1, d.K, 1};  // one 32-ray tile x all K Gaussians per item
       const int tile_b = ac ? fmb::ac_rays_per_item() : pl.ray_tile;
       db.n_tiles = static_cast<int>((P + tile_b - 1) / tile_b);
+      // two-parameter model: the view's rays spread evenly over its tiles (a
+      // 500-ray view runs as two tiles of 250, not 320 + 180)
+      db.rt = ac || db.n_tiles == 0 ? 0 : static_cast<int>((P + db.n_tiles - 1) / db.n_tiles);
       db.n_gblocks = bk.n_gb;
       db.GB = bk.GB;
       db.S = bk.S;

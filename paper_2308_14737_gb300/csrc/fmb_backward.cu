@@ -198,8 +198,9 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
   const int tile = local / V.n_gblocks;
   const int gb = local - tile * V.n_gblocks;
   const int P = V.P;
-  const int pix0 = tile * ray_tile;
-  const int nr = min(ray_tile, P - pix0);
+  const int rt = V.rt > 0 ? V.rt : ray_tile;  // the view's tiles are balanced: rt <= ray_tile
+  const int pix0 = tile * rt;
+  const int nr = min(rt, P - pix0);
   const int tid = threadIdx.x;
   const int T = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5;

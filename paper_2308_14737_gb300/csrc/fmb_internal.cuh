@@ -60,7 +60,7 @@ struct DevView {
   long long pair_off;   // stored-intermediate mode: first float of the view's [P][Kp] block
   const int* rays;      // ray batch: pixel index of each plane entry, or null (whole image)
   int P;                // plane entries of the view: n_rays, or W * H
-  int pad2_;
+  int rt;               // backward: rays per tile of this view (0: the launch's ray tile)
 };
 
 // Pixel rendered by plane entry i of a view.
