@@ -6,6 +6,10 @@
 // Gaussians.  Phase 1 turns each ray's upstream gradients into a record in shared
 // memory (the per-pixel part of the adjoint: flow, normal renormalisation, alpha),
 // every value stored twice so that one 16-byte load yields two broadcast pairs.
+// When every view runs as two Gaussian blocks, grid mode launches the two CTAs of
+// a ray tile as one 2-CTA cluster: each builds half of the tile's records and
+// writes them into both CTAs' shared memory (distributed shared memory), so the
+// per-ray work is done once per ray instead of once per block.
 // Phase 2 is Gaussian-parallel: each thread owns two Gaussians, one per lane of
 // packed FP32x2 arithmetic, recomputes their pair terms for every ray of its
 // subgroup from the saved log-normaliser (no per-pair state was stored by the
@@ -179,7 +183,9 @@ __device__ __forceinline__ float warp_sum(float x) {
   return x;
 }
 
-template <bool NORMALS, int NFLOW, bool STORED, bool COLOR = false, bool POSE = true>
+// CL = 2: launched as clusters of two CTAs, the two Gaussian blocks of one ray tile
+// (grid mode, every view of the batch in two blocks); CL = 1: no cluster.
+template <bool NORMALS, int NFLOW, bool STORED, bool COLOR = false, bool POSE = true, int CL = 1>
 __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
     backward_kernel(const __grid_constant__ Batch batch, Scene s, Consts k, const float4* __restrict__ records,
                     BwdIn in, BwdOut out, int ray_tile, int* counter) {
@@ -206,7 +212,15 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
   const int lane = tid & 31, warp = tid >> 5;
   const long long off = V.pix_off;
   const bool want_pose = out.gposes != nullptr;
-  const bool ray_pose = want_pose && gb == 0;  // per-ray pose terms: once per tile
+  // In a cluster (CL = 2) each CTA builds the records of its half of the tile's
+  // rays and writes them to both CTAs (its own shared memory and, through
+  // distributed shared memory, its peer's), so a ray's record is built once, not
+  // once per Gaussian block.
+  const int crank = CL == 2 ? static_cast<int>(cluster_ctarank()) : 0;
+  const int r_lo = CL == 2 ? (nr * crank) / 2 : 0;
+  const int r_hi = CL == 2 ? (nr * (crank + 1)) / 2 : nr;
+  // per-ray pose terms: once per ray (by the CTA that builds its record)
+  const bool ray_pose = want_pose && (CL == 2 || gb == 0);
 
   // ---------------- phase 1: per-ray records (and the per-ray pose terms)
   {
@@ -226,7 +240,7 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
       has_t[j] = tg >= 0 && in.g_flow != nullptr;
       if (has_t[j]) load_pose(s.poses, tg, Rj[j], tj[j]);
     }
-    for (int r = tid; r < nr; r += T) {
+    for (int r = r_lo + tid; r < r_hi; r += T) {
       const int p = pix0 + r;
       float vc[3], v[3], vl[3], pxy[2];
       pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
@@ -322,14 +336,15 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
       }
       const float KA = gA * expf(-Sd);
       float4* rr = bsm + ray_rec2<COLOR>() * r;
-      rr[0] = make_float4(v[0], v[0], v[1], v[1]);
-      rr[1] = make_float4(v[2], v[2], -lse2, -lse2);
-      rr[2] = make_float4(Dbar, Dbar, -KA, -KA);
-      rr[3] = make_float4(-C, -C, Nb0, Nb0);
-      rr[4] = make_float4(Nb1, Nb1, Nb2, Nb2);
-      rr[5] = make_float4(vl[0], vl[0], vl[1], vl[1]);
-      rr[6] = make_float4(vl[2], vl[2], Cb[0], Cb[0]);
-      if (COLOR) rr[7] = make_float4(Cb[1], Cb[1], Cb[2], Cb[2]);
+      const float4 rec[8] = {make_float4(v[0], v[0], v[1], v[1]),     make_float4(v[2], v[2], -lse2, -lse2),
+                             make_float4(Dbar, Dbar, -KA, -KA),       make_float4(-C, -C, Nb0, Nb0),
+                             make_float4(Nb1, Nb1, Nb2, Nb2),         make_float4(vl[0], vl[0], vl[1], vl[1]),
+                             make_float4(vl[2], vl[2], Cb[0], Cb[0]), make_float4(Cb[1], Cb[1], Cb[2], Cb[2])};
+#pragma unroll
+      for (int i = 0; i < ray_rec2<COLOR>(); ++i) {
+        rr[i] = rec[i];
+        if (CL == 2) st_cluster_f4(rr + i, crank ^ 1, rec[i]);
+      }
     }
     // Reduce the per-ray pose terms now, so that they hold no registers in the loop.
     if (want_pose) {
@@ -340,7 +355,11 @@ __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
       }
     }
   }
-  __syncthreads();
+  // the records (the cluster's, through distributed shared memory) are complete
+  if (CL == 2)
+    cluster_sync();
+  else
+    __syncthreads();
 
   // ---------------- phase 2: Gaussian-parallel pair loop (two Gaussians per thread)
   const int GB = V.GB, S = V.S;
@@ -533,11 +552,11 @@ static int bwd_smem_bytes(int ray_tile, int threads, bool color = false) {
                   threads * (color ? acc_floats<true>() : kAccFloats) * static_cast<int>(sizeof(float)));
 }
 
-template <bool NORMALS, int NFLOW, bool STORED = false, bool COLOR = false, bool POSE = true>
+template <bool NORMALS, int NFLOW, bool STORED = false, bool COLOR = false, bool POSE = true, int CL = 1>
 static cudaError_t prepare_bwd_t(int smem) {
   // Dynamic plus static shared memory above the 48 KB default needs the opt-in.
   if (smem + static_cast<int>(sizeof(float) * (kBwdMaxThreads / 32) * 48) > 48 * 1024)
-    return cudaFuncSetAttribute(backward_kernel<NORMALS, NFLOW, STORED, COLOR, POSE>,
+    return cudaFuncSetAttribute(backward_kernel<NORMALS, NFLOW, STORED, COLOR, POSE, CL>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return cudaSuccess;
 }
@@ -553,6 +572,23 @@ static int bwd_ctas_per_sm_t(int ray_tile, int threads) {
   return n > 0 ? n : 1;
 }
 
+// Cluster size of a grid-mode backward launch: 2 when every view of the batch runs
+// as two Gaussian blocks (then each tile's two items are consecutive and 2-aligned,
+// one cluster), else 1 (no cluster).
+static int bwd_cluster_size(const Batch& b) {
+  int C = 0;
+  for (int i = 0; i < b.n_views; ++i) {
+    const DevView& v = b.v[i];
+    if (v.n_tiles <= 0) continue;
+    if (C == 0) C = v.n_gblocks;
+    if (v.n_gblocks != C) return 1;
+  }
+  if (C != 2 || b.n_items % C != 0) return 1;
+  for (int j = 0; j < b.n_views; ++j)
+    if (b.order_begin[j] % C != 0) return 1;
+  return C;
+}
+
 template <bool NORMALS, int NFLOW, bool STORED, bool COLOR = false, bool POSE = true>
 static cudaError_t launch_bwd_s(const Batch& b, const Scene& s, const Consts& c, const float4* records,
                                 int ray_tile, int threads, const BwdIn& in, const BwdOut& out, int* counter,
@@ -566,6 +602,26 @@ static cudaError_t launch_bwd_s(const Batch& b, const Scene& s, const Consts& c,
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     grid = std::min(b.n_items, std::max(1, sms) * bwd_ctas_per_sm_t<NORMALS, NFLOW>(ray_tile, threads));
+  }
+  if constexpr (!STORED && !COLOR) {
+    if (counter == nullptr && bwd_cluster_size(b) == 2) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = prepare_bwd_t<NORMALS, NFLOW, STORED, COLOR, POSE, 2>(smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, backward_kernel<NORMALS, NFLOW, STORED, COLOR, POSE, 2>, b, s, c, records, in, out,
+                              ray_tile, counter);
+    }
   }
   backward_kernel<NORMALS, NFLOW, STORED, COLOR, POSE><<<grid, threads, smem, st>>>(b, s, c, records, in, out, ray_tile,
                                                                                counter);

@@ -108,6 +108,19 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+// Thread-block clusters (CUDA runtime intrinsics): this CTA's rank in its
+// cluster; a 16-byte store to the same shared-memory offset of CTA `rank` of the
+// cluster (distributed shared memory); and a barrier of all threads of the cluster
+// (arrive with release, wait with acquire), after which such stores are visible
+// to every CTA of the cluster.
+__device__ __forceinline__ uint32_t cluster_ctarank() { return __clusterRelativeBlockRank(); }
+__device__ __forceinline__ void st_cluster_f4(float4* local, int rank, float4 v) {
+  *static_cast<float4*>(__cluster_map_shared_rank(local, static_cast<unsigned>(rank))) = v;
+}
+__device__ __forceinline__ void cluster_sync() {
+  __cluster_barrier_arrive();
+  __cluster_barrier_wait();
+}
 __device__ __forceinline__ unsigned long long global_timer_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -193,6 +193,26 @@ def test_gaussian_blocks_over_128():
         _full_check(s, n_flow=1, deterministic=(K == 300))
 
 
+@pytest.mark.parametrize("deterministic", [False, True])
+def test_cluster_backward(deterministic):
+    """K = 100 at 128 backward threads runs as two Gaussian blocks, which grid mode
+    launches as 2-CTA clusters sharing the per-ray records (each CTA builds half
+    of them); persistent mode runs the same blocks as single CTAs.  Both match the
+    oracle, and each other up to the order of the fp32 sums."""
+    s = synth.object_orbit(K=100, n_views=4, W=64, H=48)
+    res = []
+    for pers in (0, 1):
+        _, _, g = _full_check(s, n_flow=1, deterministic=deterministic, bwd_threads=128, bwd_ray_tile=384,
+                              use_persistent=pers)
+        res.append(g)
+    for k in res[0]:
+        np.testing.assert_allclose(res[0][k], res[1][k], rtol=0, atol=2e-5 * np.abs(res[1][k]).max(), err_msg=k)
+    if deterministic:
+        _, _, g2 = _full_check(s, n_flow=1, deterministic=True, bwd_threads=128, bwd_ray_tile=384)
+        for k in g2:
+            assert np.array_equal(res[0][k], g2[k]), k
+
+
 def test_permutation_invariance():
     s = synth.object_orbit(K=60, n_views=2, W=40, H=30)
     p = fmb.default_params(n_flow=1)
@@ -206,8 +226,9 @@ def test_permutation_invariance():
     assert np.all(np.abs(a["alpha"] - b["alpha"]) <= 1e-5)
 
 
-def _sampled_full_size(scene, n_flow, n_per_view, seed=0, deterministic=False, persistent=False):
-    params = fmb.default_params(n_flow=n_flow, deterministic=int(deterministic), use_persistent=int(persistent))
+def _sampled_full_size(scene, n_flow, n_per_view, seed=0, deterministic=False, persistent=False, **pk):
+    params = fmb.default_params(n_flow=n_flow, deterministic=int(deterministic), use_persistent=int(persistent),
+                                **pk)
     gpu, r, dev = gpu_forward(scene, params)
     pix = sample_pixels(scene, n_per_view, seed)
     ref = oracle_forward_sampled(scene, pix, n_flow)
@@ -227,6 +248,13 @@ def _sampled_full_size(scene, n_flow, n_per_view, seed=0, deterministic=False, p
 
 def test_orbit_full_size_16x320x240_K100_sampled():
     _sampled_full_size(synth.object_orbit(), n_flow=1, n_per_view=400)
+
+
+def test_orbit_full_size_benchmark_tiles_sampled():
+    """The benchmark's tuned tiles (128 backward threads, 384-ray tiles: two
+    Gaussian blocks per tile, launched as 2-CTA clusters)."""
+    _sampled_full_size(synth.object_orbit(), n_flow=1, n_per_view=200, seed=3, bwd_threads=128, bwd_ray_tile=384,
+                       fwd_rays_per_thread=2)
 
 
 def test_orbit_full_size_dense_gradients():
