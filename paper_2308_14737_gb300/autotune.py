@@ -18,6 +18,20 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "fmb_gb300", "au
 CANDIDATES = [dict(fwd_rays_per_thread=r, bwd_threads=t, bwd_ray_tile=t * m, use_persistent=p)
               for r in (2, 4) for t in (128, 160) for m in (2, 3) for p in (0, 1)]
 
+# Extra candidates for small batches (fewer 256-ray tiles than two waves of the
+# GPU's SMs): short ray tiles and narrow CTAs spread a few thousand rays over more
+# SMs, at the price of more per-tile overhead.
+SMALL_CANDIDATES = [dict(fwd_rays_per_thread=r, bwd_threads=t, bwd_ray_tile=m, use_persistent=0)
+                    for r in (1, 2) for t, m in ((64, 64), (64, 128), (128, 128))]
+
+
+def candidates_for(views, n_sms: int) -> list:
+    """Candidate tiles of a batch: ``CANDIDATES``, plus ``SMALL_CANDIDATES`` when
+    the batch has fewer rays than two waves of 256-ray tiles on ``n_sms`` SMs."""
+    P = sum(fmb.view_entries(v) for v in views)
+    return list(CANDIDATES) + (list(SMALL_CANDIDATES) if P < 2 * n_sms * 256 else [])
+
+
 # The alpha-compositing variant has fixed 32-ray tiles: only the launch mode is tuned.
 CANDIDATES_AC = [dict(use_persistent=p) for p in (0, 1)]
 
@@ -72,7 +86,10 @@ def tune(obj_offsets, views, n_poses, params: fmb.FmbParams, means, chol, weight
     cache = _load(path)
     if key in cache and not force:
         return apply(params, cache[key]["best"]), cache[key]["timings"]
-    cands = candidates or CANDIDATES
+    if candidates is None:
+        n_sms = torch.cuda.get_device_properties(torch.device(device)).multi_processor_count
+        candidates = CANDIDATES_AC if int(params.variant) == 1 else candidates_for(views, n_sms)
+    cands = candidates
     G = means.shape[0]
     out = dict(means=torch.empty(G, 3, device=device), chol=torch.empty(G, 6, device=device),
                weights=torch.empty(G, device=device),

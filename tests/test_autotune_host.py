@@ -26,3 +26,17 @@ def test_apply_sets_only_tuned_fields():
     assert (q.fwd_rays_per_thread, q.bwd_threads, q.bwd_ray_tile, q.use_persistent) == (4, 128, 256, 1)
     assert (q.n_flow, q.want_normals) == (2, 0) and abs(q.beta1 - 21.4) < 1e-6
     assert p.fwd_rays_per_thread == 0  # the input is not modified
+
+
+def test_small_batches_get_short_tile_candidates():
+    """A batch with fewer rays than two waves of 256-ray tiles also tries the short
+    tiles; a full-size batch keeps the standard list."""
+    small = synth.single_view()  # one 64 x 64 view
+    big = synth.object_orbit()   # 16 views of 320 x 240
+    cs = autotune.candidates_for(small.views, 152)
+    cb = autotune.candidates_for(big.views, 152)
+    assert cb == autotune.CANDIDATES
+    assert cs == autotune.CANDIDATES + autotune.SMALL_CANDIDATES
+    for c in autotune.SMALL_CANDIDATES:
+        assert c["bwd_ray_tile"] % 32 == 0 and 32 <= c["bwd_threads"] <= 160 and c["bwd_threads"] % 32 == 0
+        assert c["fwd_rays_per_thread"] in (1, 2, 4)
