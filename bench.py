@@ -477,8 +477,9 @@ def run_gpu(args):
                           "variant": "weighted blending" if not ac else "alpha compositing"},
         "roofline": roofline,
         "clocks": clocks,
-        # prologue + forward (+ the merge of a Gaussian-split forward); zeroing + prologue + backward
-        "gpu_launches": (5 + (1 if ksplit > 1 else 0)) * args.steps,
+        # prologue + forward (+ the merge of a Gaussian-split forward); prologue (which also clears the
+        # gradient outputs) + backward
+        "gpu_launches": (4 + (1 if ksplit > 1 else 0)) * args.steps,
         "e2e": e2e,
     }
     if args.points:

@@ -570,11 +570,12 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
     zj.n[4] = grad_poses ? 12ll * n_poses : 0;
     zj.ptr[5] = params->colors ? grad_colors : nullptr;
     zj.n[5] = params->colors ? 3 * pl.n_gauss : 0;
-    cudaError_t e = fmb::launch_zero(zj, s);
-    if (e != cudaSuccess) return cuda_fail(e, "zeroing launch");
+    cudaError_t e = cudaSuccess;
     int* counter = params->use_persistent ? reinterpret_cast<int*>(base + kBwdCounterOffset) : nullptr;
+    bool first = true;  // the first batch's prologue clears the outputs and the status word
     for (const fmb::Batch& b : pl.bwd) {
-      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, counter, s);
+      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, counter, s, first ? &zj : nullptr);
+      first = false;
       if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
       if (params->variant == 1)
         e = fmb::launch_backward_ac(b, sc, c, records, normals, params->n_flow, pl.maxK, in, out, status, counter, s);
@@ -586,6 +587,10 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
         e = fmb::launch_backward_reduce(b, params->n_flow, pl.n_gauss, n_poses, out, s);
         if (e != cudaSuccess) return cuda_fail(e, "reduction launch");
       }
+    }
+    if (first) {  // nothing to render: the outputs are still cleared
+      e = fmb::launch_zero(zj, s);
+      if (e != cudaSuccess) return cuda_fail(e, "zeroing launch");
     }
     return FMB_OK;
   } catch (const std::exception& e) {
@@ -666,8 +671,8 @@ fmb_status fmb_loss_attribution(const fmb_params* params, int n_objects, const l
     fmb::ZeroJob zj{};
     zj.ptr[0] = attribution;
     zj.n[0] = pl.n_gauss;
-    cudaError_t e = fmb::launch_zero(zj, s);
-    if (e != cudaSuccess) return cuda_fail(e, "zeroing launch");
+    cudaError_t e = cudaSuccess;
+    bool first = true;  // the first batch's prologue clears the attribution output
     if (params->variant == 0) {
       // two-parameter model: the backward's blocking (two Gaussians per thread)
       const int T = pl.bwd_threads;
@@ -682,26 +687,32 @@ fmb_status fmb_loss_attribution(const fmb_params* params, int n_objects, const l
         }
         order_items(b, [&](const fmb::DevView& v) { return static_cast<double>(v.GB); },
                     [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles) * v.n_gblocks; });
-        e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, nullptr, s);
+        e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, nullptr, s, first ? &zj : nullptr);
+        first = false;
         if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
         e = fmb::launch_attribution2(b, sc, c, records, T, tile, saved, ray_loss, attribution, s);
         if (e != cudaSuccess) return cuda_fail(e, "attribution launch");
       }
-      return FMB_OK;
-    }
-    const int per = fmb::attribution_rays_per_item();
-    const int blk = 32 * (pl.maxK <= 64 ? 2 : (pl.maxK <= 128 ? 4 : 8));
-    for (fmb::Batch b : pl.fwd) {
-      for (int i = 0; i < b.n_views; ++i) {
-        b.v[i].n_tiles = (b.v[i].P + per - 1) / per;
-        b.v[i].n_gblocks = (b.v[i].K + blk - 1) / blk;
+    } else {
+      const int per = fmb::attribution_rays_per_item();
+      const int blk = 32 * (pl.maxK <= 64 ? 2 : (pl.maxK <= 128 ? 4 : 8));
+      for (fmb::Batch b : pl.fwd) {
+        for (int i = 0; i < b.n_views; ++i) {
+          b.v[i].n_tiles = (b.v[i].P + per - 1) / per;
+          b.v[i].n_gblocks = (b.v[i].K + blk - 1) / blk;
+        }
+        order_items(b, [&](const fmb::DevView& v) { return static_cast<double>(std::min(v.K, blk)); },
+                    [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles) * v.n_gblocks; });
+        e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, nullptr, s, first ? &zj : nullptr);
+        first = false;
+        if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
+        e = fmb::launch_attribution_ac(b, sc, c, records, pl.maxK, ray_loss, attribution, s);
+        if (e != cudaSuccess) return cuda_fail(e, "attribution launch");
       }
-      order_items(b, [&](const fmb::DevView& v) { return static_cast<double>(std::min(v.K, blk)); },
-                  [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles) * v.n_gblocks; });
-      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, nullptr, s);
-      if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
-      e = fmb::launch_attribution_ac(b, sc, c, records, pl.maxK, ray_loss, attribution, s);
-      if (e != cudaSuccess) return cuda_fail(e, "attribution launch");
+    }
+    if (first) {  // nothing to render: the output is still cleared
+      e = fmb::launch_zero(zj, s);
+      if (e != cudaSuccess) return cuda_fail(e, "zeroing launch");
     }
     return FMB_OK;
   } catch (const std::exception& e) {

@@ -22,15 +22,25 @@ constexpr int kChunk = 256;  // records per shared-memory stage (16 KB)
 // One thread per (view, Gaussian): the record of unpack_rec.  The camera centre
 // o = -R^T t and m = mu - o are formed as exact float pairs (error-free
 // transformations), so that the per-pair residual can be evaluated to full fp32
-// accuracy relative to its own size.
+// accuracy relative to its own size.  The same launch clears the arrays of `zero`
+// (the backward's gradient outputs and status word, which its kernels then
+// accumulate into), grid-stride over all its threads.
 __global__ void __launch_bounds__(128) prologue_kernel(const __grid_constant__ Batch batch, Scene s, Consts k,
                                                         float4* __restrict__ records, int* status_to_clear,
-                                                        int* counter_to_clear) {
+                                                        int* counter_to_clear, ZeroJob zero) {
   const DevView& V = batch.v[blockIdx.y];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0 && blockIdx.y == 0) {
     if (status_to_clear != nullptr) *status_to_clear = kDevOk;
     if (counter_to_clear != nullptr) *counter_to_clear = 0;
+  }
+  {
+    const long long stride = static_cast<long long>(gridDim.x) * gridDim.y * blockDim.x;
+    const long long j0 = (static_cast<long long>(blockIdx.y) * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
+    for (int b = 0; b < ZeroJob::kMax; ++b) {
+      if (zero.ptr[b] == nullptr) continue;
+      for (long long j = j0; j < zero.n[b]; j += stride) zero.ptr[b][j] = 0.f;
+    }
   }
   if (i >= V.K) return;
   float R[9], t[3];
@@ -66,9 +76,10 @@ __global__ void __launch_bounds__(128) prologue_kernel(const __grid_constant__ B
 }
 
 cudaError_t launch_prologue(const Batch& b, const Scene& s, const Consts& c, float4* records, int maxK,
-                            int* status_to_clear, int* counter_to_clear, cudaStream_t st) {
+                            int* status_to_clear, int* counter_to_clear, cudaStream_t st, const ZeroJob* zero) {
   dim3 grid((maxK + 127) / 128, b.n_views);
-  prologue_kernel<<<grid, 128, 0, st>>>(b, s, c, records, status_to_clear, counter_to_clear);
+  prologue_kernel<<<grid, 128, 0, st>>>(b, s, c, records, status_to_clear, counter_to_clear,
+                                        zero != nullptr ? *zero : ZeroJob{});
   return cudaGetLastError();
 }
 

@@ -375,9 +375,18 @@ struct Scene {
   float4* crec = nullptr;         // colour records (r, g, b, 0) per (view, Gaussian) in the workspace
 };
 
-// status_to_clear / counter_to_clear: if not null, the prologue also zeroes them.
+// Float arrays to clear (null entries skipped).
+struct ZeroJob {
+  static constexpr int kMax = 7;
+  float* ptr[kMax];
+  long long n[kMax];
+};
+
+// status_to_clear / counter_to_clear: if not null, the prologue also zeroes them;
+// so it does with every array of `zero` (if not null).
 cudaError_t launch_prologue(const Batch& b, const Scene& s, const Consts& c, float4* records, int maxK,
-                            int* status_to_clear, int* counter_to_clear, cudaStream_t st);
+                            int* status_to_clear, int* counter_to_clear, cudaStream_t st,
+                            const ZeroJob* zero = nullptr);
 // counter: persistent mode's work counter (zeroed before the launch), or null for
 // one CTA per work item.
 struct FwdOut;
@@ -402,11 +411,6 @@ struct FwdOut {
   float* part = nullptr;    // Gaussian-split forward: per-ray partial sums, 8 floats per (ray, split)
 };
 
-struct ZeroJob {
-  static constexpr int kMax = 7;
-  float* ptr[kMax];
-  long long n[kMax];
-};
 cudaError_t launch_zero(const ZeroJob& job, cudaStream_t st);
 
 struct BwdOut {
