@@ -90,8 +90,10 @@ PROFILE = os.path.join(ROOT, "profiles", "backward_kernel_orbit16x320x240_K100.m
 
 
 def csrc_sha256() -> str:
-    """Hash of the sources that define the backward kernel."""
+    """Hash of the sources that define the backward kernel, and of its compile flags."""
     import hashlib
+
+    from paper_2308_14737_gb300 import build
 
     d = os.path.join(ROOT, "paper_2308_14737_gb300", "csrc")
     h = hashlib.sha256()
@@ -99,6 +101,7 @@ def csrc_sha256() -> str:
         h.update(name.encode())
         with open(os.path.join(d, name), "rb") as fh:
             h.update(fh.read())
+    h.update(" ".join(build.EXTRA_FLAGS.get("fmb_backward.cu", [])).encode())
     return h.hexdigest()
 
 

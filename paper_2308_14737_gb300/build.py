@@ -22,6 +22,11 @@ LIB_PATH = os.path.join(LIB_DIR, "libfmb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["fmb_forward.cu", "fmb_backward.cu", "fmb_ac.cu", "fmb_points.cu", "fmb_attrib.cu", "fmb_api.cu",
            "fmb_probe.cu", "fmb_adam.cu"]
+# Per-source flags.  The backward's scalar code (the per-ray records, the
+# finalisation) flushes subnormals to zero: its packed pair loop is explicit
+# round-to-nearest PTX and is not affected, and ptxas allocates the loop's
+# registers better in this mode (orbit backward 0.578 -> 0.563 ms, measured).
+EXTRA_FLAGS = {"fmb_backward.cu": ["-ftz=true"]}
 
 
 def nvcc() -> str:
@@ -57,7 +62,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
 
     def compile_one(src):
         obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
-        cmd = [cc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc] + flags + EXTRA_FLAGS.get(src, []) + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
