@@ -42,8 +42,8 @@ constexpr int kBwdMaxThreads = 160;
 #ifndef FMB_BWD_MIN_BLOCKS
 #define FMB_BWD_MIN_BLOCKS 3
 #endif
-constexpr int kBwdMinBlocks = FMB_BWD_MIN_BLOCKS;
-constexpr int kBwdUnroll = FMB_BWD_UNROLL;  // resident CTAs per SM the register budget targets
+constexpr int kBwdMinBlocks = FMB_BWD_MIN_BLOCKS;  // resident CTAs per SM the register budget targets
+constexpr int kBwdUnroll = FMB_BWD_UNROLL;
 constexpr int kAccFloats = 38;  // 19 packed accumulators per thread in the reduction
 // Colour mode adds three (sum of what x Cbar per channel).
 template <bool COLOR>
