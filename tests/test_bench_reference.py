@@ -22,3 +22,22 @@ def test_reference_arm_prints_one_json_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "pairs/s"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_profile_gate_follows_sources_and_compile_flags(monkeypatch):
+    """The committed backward ncu summary is used for roofline.traffic only while
+    the backward's sources, its compile flags and the launch tiles are the ones it
+    was captured with."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2308_14737_gb300 import build
+
+    for src in build.EXTRA_FLAGS:
+        assert src in build.SOURCES, src
+    tiles = {"bwd_ray_tile": 384, "bwd_threads": 128, "fwd_rays_per_thread": 2, "use_persistent": 0}
+    sha = bench.csrc_sha256()
+    assert bench.profiled_traffic(tiles) is not None, "profile summary out of date with the sources"
+    assert bench.profiled_traffic(dict(tiles, bwd_ray_tile=256)) is None
+    monkeypatch.setitem(build.EXTRA_FLAGS, "fmb_backward.cu", [])
+    assert bench.csrc_sha256() != sha
+    assert bench.profiled_traffic(tiles) is None
