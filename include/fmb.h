@@ -210,15 +210,27 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
  * FMB_ERR_WORKSPACE.  Nothing is allocated.  The first call on each device looks up
  * the array's device address (cudaGetSymbolAddress); make that first call before
  * any stream capture.  All calls share the array: calls whose GPU work overlaps
- * (different streams or host threads) race on it.  Errors are reported as for
- * fmb_render_forward; the device status word lives in the fixed array and has no
- * reader.
+ * (different streams or host threads) race on it.  The device address is cached
+ * per device for the life of the process: after a device reset (cudaDeviceReset,
+ * or any teardown of the device's primary context) this entry point must not be
+ * called again.  Errors are reported as for fmb_render_forward; the device status
+ * word (nonzero when a bounded wait gave up and the planes are invalid) lives in
+ * the fixed array, cleared by every call, and is read by fmb_read_noalloc_status.
  */
 fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n_objects, const long long* h_obj_offsets,
                                       const float* means, const float* chol, const float* weights,
                                       const float* colors, int n_poses, const float* poses, int n_views,
                                       const fmb_view* h_views, float* depth, float* alpha, float* normal,
                                       float* flow, float* color, float* saved, fmb_stream_t stream);
+
+/* Copies the status word of fmb_render_forward_noalloc's fixed scratch to
+ * *h_status and synchronises `stream` (the stream of the call being checked):
+ * 0 = no device-side error; nonzero = a bounded wait of that call gave up and its
+ * outputs are invalid.  Allocates nothing.  The paper has no counterpart (like
+ * fmb_read_device_status, this reports on the execution, not on the method).
+ * With calls on several streams in flight, the word is that of whichever call
+ * wrote it last. */
+fmb_status fmb_read_noalloc_status(int* h_status, fmb_stream_t stream);
 
 /*
  * Oriented point export (Sec. 6: the oriented point set a Poisson surface

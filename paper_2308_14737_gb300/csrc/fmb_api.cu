@@ -746,10 +746,14 @@ fmb_status fmb_read_device_status(const void* workspace, int* h_status, fmb_stre
 //
 // The array's name is only a host-side stand-in: the device address is obtained
 // once per device with cudaGetSymbolAddress, during that device's first call
-// (so the first call on a device should come before any stream capture).  All
-// calls share the array and it keeps the last call's contents; the status word is
-// cleared by every call and the records are rewritten, but calls whose work
-// overlaps on the GPU (different streams, or different host threads) race on it.
+// (so the first call on a device should come before any stream capture).  The
+// address is cached for the life of the process: a device reset (or any other
+// teardown of the device's primary context) invalidates it, and the entry point
+// must not be used after one.  All calls share the array and it keeps the last
+// call's contents; the status word is cleared by every call and the records are
+// rewritten, but calls whose work overlaps on the GPU (different streams, or
+// different host threads) race on it.  fmb_read_noalloc_status reads the status
+// word back.
 
 namespace {
 
@@ -850,4 +854,19 @@ extern "C" fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n
   } catch (...) {
     return fail(FMB_ERR_INVALID_ARG, "unknown error");
   }
+}
+
+// Status word of the fixed scratch (its first int), copied to the host after the
+// work already enqueued on `stream` (the caller's last allocation-free forward) has
+// run.  Uses the same cached device address as the render call; no allocation.
+extern "C" fmb_status fmb_read_noalloc_status(int* h_status, fmb_stream_t stream) {
+  if (!h_status) return fail(FMB_ERR_INVALID_ARG, "h_status is required");
+  void* ws = nullptr;
+  fmb_status st = static_scratch_address(&ws);
+  if (st != FMB_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(h_status, ws, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the fixed scratch's status word");
+  return FMB_OK;
 }

@@ -76,6 +76,8 @@ def load_library(path: str = LIB_PATH):
     L.fmb_render_backward.restype = ctypes.c_int
     L.fmb_render_forward_noalloc.argtypes = [P, i, LL, fp, fp, fp, fp, i, fp, i, V, fp, fp, fp, fp, fp, fp, vp]
     L.fmb_render_forward_noalloc.restype = ctypes.c_int
+    L.fmb_read_noalloc_status.argtypes = [ctypes.POINTER(ctypes.c_int), vp]
+    L.fmb_read_noalloc_status.restype = ctypes.c_int
     L.fmb_adam_step.argtypes = [ctypes.POINTER(FmbAdamParams), fp, fp, fp, fp, ctypes.c_longlong, ctypes.c_longlong,
                                 fp, vp]
     L.fmb_adam_step.restype = ctypes.c_int
@@ -210,6 +212,15 @@ def fmb_render_forward_noalloc(params, obj_offsets, means, chol, weights, poses,
                                         _ptr(weights), _ptr(colors), int(poses.shape[0]), _ptr(poses), len(va), va,
                                         _ptr(depth), _ptr(alpha), _ptr(normal), _ptr(flow), _ptr(color), _ptr(saved),
                                         _stream(stream)))
+
+
+def fmb_read_noalloc_status(stream=None) -> int:
+    """Status word of the last allocation-free forward (0 = no device-side error);
+    synchronises the stream."""
+    L = load_library()
+    st = ctypes.c_int(0)
+    _check(L.fmb_read_noalloc_status(ctypes.byref(st), _stream(stream)))
+    return int(st.value)
 
 
 def fmb_render_points(params, obj_offsets, means, chol, weights, poses, views, depth, saved, points, normal_tf,

@@ -224,3 +224,10 @@ def test_forward_split_query(fmb):
     assert grown - base >= 32 * 3 * s.n_pixels
     assert fmb.fmb_forward_ksplit(fmb.default_params(fwd_ksplit=3, colors=1), s.obj_offsets, s.views) == 1
     assert fmb.fmb_forward_ksplit(fmb.default_params(fwd_ksplit=3, store_pairs=1), s.obj_offsets, s.views) == 1
+
+
+def test_noalloc_status_reader_rejects_a_null_pointer(fmb):
+    """fmb_read_noalloc_status validates its argument on the host before touching a device."""
+    L = fmb.load_library()
+    assert L.fmb_read_noalloc_status(None, None) == 1
+    assert "h_status" in L.fmb_last_error().decode()

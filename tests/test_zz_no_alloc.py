@@ -6,8 +6,10 @@ cudaMalloc's implicit device synchronisation is not allowed.  For them the forwa
 render keeps its scratch in a fixed array inside the library.  These tests call it
 through the C ABI and check it against fmb_render_forward, which takes a workspace,
 on two calls in a row with different batches (the second reuses the scratch the
-first one left behind), and check that a batch too large for the fixed scratch is
-rejected before any work is enqueued.
+first one left behind), in both launch modes, both weightings and with and without
+colours; check that its status word reads 0 after each call and that the device's
+free memory does not change across the calls; and check that a batch too large for
+the fixed scratch is rejected before any work is enqueued.
 """
 
 import numpy as np
@@ -38,24 +40,58 @@ def _planes(P, n_flow):
     f = dict(dtype=torch.float32, device="cuda")
     return dict(depth=torch.full((P,), -1.0, **f), alpha=torch.full((P,), -1.0, **f),
                 normal=torch.full((3 * P,), -1.0, **f), flow=torch.full((2 * n_flow * P,), -1.0, **f),
-                saved=torch.full((3 * P,), -1.0, **f))
+                saved=torch.full((3 * P,), -1.0, **f), color=torch.full((3 * P,), -1.0, **f))
 
 
-def test_noalloc_matches_workspace_forward_on_two_calls():
+def _colours(scene, seed):
+    rng = np.random.default_rng(seed)
+    return torch.as_tensor(rng.uniform(0.0, 1.0, (scene.means.shape[0], 3)).astype(np.float32), device="cuda")
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("colors", [0, 1])
+def test_noalloc_matches_workspace_forward_on_two_calls(persistent, variant, colors):
     scenes = [synth.object_orbit(K=100, n_views=4, W=64, H=48), synth.object_orbit(seed=3, K=30, n_views=2, W=40, H=30)]
-    for s in scenes:
-        params = fmb.default_params(n_flow=1, want_normals=1)
+    keys = ("depth", "alpha", "normal", "flow", "saved") + (("color",) if colors else ())
+    cases = []
+    for i, s in enumerate(scenes):
+        params = fmb.default_params(n_flow=1, want_normals=1, use_persistent=persistent, variant=variant,
+                                    colors=colors)
         means, chol, weights, poses = _dev(s)
-        ref = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), params).forward(means, chol, weights, poses)
+        col = _colours(s, i) if colors else None
+        ref = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), params).forward(means, chol, weights, poses,
+                                                                                colors=col)
         out = _planes(s.n_pixels, 1)
+        cases.append((s, params, (means, chol, weights, poses), col, ref, out))
+
+    def call(case):
+        s, params, (means, chol, weights, poses), col, _, out = case
         fmb.fmb_render_forward_noalloc(params, s.obj_offsets, means, chol, weights, poses, s.views, out["depth"],
-                                       out["alpha"], out["normal"], out["flow"], out["saved"])
-        torch.cuda.synchronize()
-        for k in ("depth", "alpha", "normal", "flow", "saved"):
+                                       out["alpha"], out["normal"], out["flow"], out["saved"], colors=col,
+                                       color=out["color"] if colors else None)
+
+    # one untimed call per batch first, so that every kernel the calls launch is
+    # loaded before the free device memory is recorded
+    for c in cases:
+        call(c)
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    for c in cases:
+        for k in c[5]:
+            c[5][k].fill_(-1.0)
+    torch.cuda.synchronize()
+    for c in cases:  # two calls in a row, the second on another batch
+        call(c)
+        assert fmb.fmb_read_noalloc_status() == 0
+        ref, out = c[4], c[5]
+        for k in keys:
             a = out[k].cpu().numpy().astype(np.float64)
             b = ref[k].cpu().numpy().astype(np.float64)
             assert np.all(np.isfinite(a)), k
             assert np.all(np.abs(a - b) <= 1e-4 + 1e-5 * np.abs(b)), (k, float(np.max(np.abs(a - b))))
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free_before
 
 
 def test_noalloc_rejects_batches_beyond_the_fixed_scratch():
