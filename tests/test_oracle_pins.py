@@ -133,6 +133,49 @@ def test_isotropic_offcentre_normal_direction(oracle_mod):
         assert abs(r["depth"][0] - 3.5) < 1e-12
 
 
+def test_offcentre_isotropic_normals_blend_closed_form(oracle_mod):
+    """Eq. 17 blended by Eq. 3 over K = 2 and K = 3 Gaussians.  Isotropic Gaussian i
+    (L = s_i I) with its centre displaced from the ray by eps_i along a unit vector
+    e_i perpendicular to the ray, at distance rho_i along it: the hit depth is
+    t_i = rho_i, the residual o + v t_i - mu_i = -eps_i e_i, so q_i = s_i^2 eps_i^2
+    (Eq. 2), the unit normal is n_i = -e_i (Eq. 17), and the Eq. 7 log-weights are
+    beta1 (ln lambda_i - q_i / 2) - beta2 rho_i / eta.  With w_i their normalised
+    exponentials (Eq. 3): N = -sum_i w_i e_i, the output normal is R N / |N| in the
+    camera frame, the saved magnitude is |N| and the depth is sum_i w_i rho_i.
+    Blending Sigma^-1 r instead of the unit n_i, or leaving out the
+    renormalisation, or a wrong frame, fails this."""
+    pose = synth.look_at_pose((0.7, -0.4, -4.0))
+    R = np.asarray(pose[:9], dtype=np.float64).reshape(3, 3)
+    x, y = 6, 4
+    v, o, _ = ray_of_pixel(pose, CAM, x, y)
+    b1 = np.cross(v, [0.0, 1.0, 0.0])
+    b1 /= np.linalg.norm(b1)
+    b2 = np.cross(v, b1)  # (v, b1, b2) orthonormal
+    cases = [  # (angle of e_i in the plane normal to the ray, eps_i, s_i, rho_i, lambda_i) per Gaussian, eta
+        ([(0.0, 0.10, 2.0, 3.5, 1.0), (np.pi / 2, 0.12, 1.5, 3.6, 1.0)], 1.0),
+        ([(0.3, 0.05, 3.0, 3.4, 1.0), (1.4, 0.20, 1.0, 3.45, 1.02)], 1.0),
+        ([(0.0, 0.08, 2.5, 3.5, 1.0), (2.1, 0.10, 2.0, 3.55, 0.95), (4.2, 0.06, 3.5, 3.52, 1.05)], 1.0),
+        ([(1.0, 0.15, 1.2, 3.3, 1.0), (2.5, 0.09, 2.2, 3.5, 1.03)], 2.0),
+    ]
+    for gs, eta in cases:
+        e = np.stack([np.cos(a) * b1 + np.sin(a) * b2 for a, *_ in gs])
+        eps = np.array([g[1] for g in gs])
+        sc = np.array([g[2] for g in gs])
+        rho = np.array([g[3] for g in gs])
+        lam = np.array([g[4] for g in gs])
+        mu = o + rho[:, None] * v + eps[:, None] * e
+        chol = np.stack([[s_, 0, s_, 0, 0, s_] for s_ in sc])
+        r = oracle_mod.render_view(mu, chol, lam, pose, None, CAM, pixels=[y * CAM[0] + x], eta=eta)
+        lw = B1 * (np.log(lam) - 0.5 * sc ** 2 * eps ** 2) - B2 * rho / eta
+        w = np.exp(lw - lw.max())
+        w /= w.sum()
+        assert 0.05 < w.min() and w.max() < 0.95  # a real blend, not one dominant Gaussian
+        N = -(w[:, None] * e).sum(0)
+        np.testing.assert_allclose(r["normal"][0], R @ (N / np.linalg.norm(N)), atol=1e-12)
+        assert abs(r["saved"][0, 2] - np.linalg.norm(N)) < 1e-12
+        assert abs(r["depth"][0] - w @ rho) < 1e-12
+
+
 def test_two_centred_gaussians_blend_closed_form(oracle_mod):
     """Two Gaussians centred on the same ray at distances rho1 < rho2: both have
     q = 0 and t = rho, so Eq. 7 gives w_i = lambda_i^beta1 exp(-beta2 rho_i / eta)
