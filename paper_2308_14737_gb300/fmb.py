@@ -300,23 +300,32 @@ class Renderer:
         self.P = int(sum(view_entries(v) for v in self.views))
         self.device = device
         self.ws = alloc_workspace(fmb_workspace_bytes(self.params, self.obj_offsets, self.c_views), device)
-        nf = self.params.n_flow
-        f32 = dict(dtype=torch.float32, device=device)
-        self.depth = torch.empty(self.P, **f32)
-        self.alpha = torch.empty(self.P, **f32)
-        self.normal = torch.empty(3 * self.P, **f32) if self.params.want_normals else None
-        self.flow = torch.empty(2 * nf * self.P, **f32) if nf > 0 else None
-        self.saved = torch.empty(3 * self.P, **f32)
-        self.color = torch.empty(3 * self.P, **f32) if self.params.colors else None
+        planes = self.new_planes()
+        self.depth, self.alpha, self.normal = planes["depth"], planes["alpha"], planes["normal"]
+        self.flow, self.saved, self.color = planes["flow"], planes["saved"], planes["color"]
 
-    def forward(self, means, chol, weights, poses, stream=None, colors=None):
+    def new_planes(self) -> dict:
+        """Freshly allocated output planes of this batch layout (depth, alpha, normal,
+        flow, color, saved; None for the planes the params do not produce)."""
+        nf = self.params.n_flow
+        f32 = dict(dtype=torch.float32, device=self.device)
+        return dict(depth=torch.empty(self.P, **f32), alpha=torch.empty(self.P, **f32),
+                    normal=torch.empty(3 * self.P, **f32) if self.params.want_normals else None,
+                    flow=torch.empty(2 * nf * self.P, **f32) if nf > 0 else None,
+                    color=torch.empty(3 * self.P, **f32) if self.params.colors else None,
+                    saved=torch.empty(3 * self.P, **f32))
+
+    def forward(self, means, chol, weights, poses, stream=None, colors=None, out=None):
         """colors: [G][3] device tensor when params.colors (the colour plane is then
-        returned as "color")."""
-        fmb_render_forward(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, self.depth,
-                           self.alpha, self.normal, self.flow, self.saved, self.ws, stream, colors=colors,
-                           color=self.color)
-        return dict(depth=self.depth, alpha=self.alpha, normal=self.normal, flow=self.flow, saved=self.saved,
-                    color=self.color)
+        returned as "color").  out: planes to render into (``new_planes()``); by
+        default the renderer's own, which the next call overwrites."""
+        if out is None:
+            out = dict(depth=self.depth, alpha=self.alpha, normal=self.normal, flow=self.flow, saved=self.saved,
+                       color=self.color)
+        fmb_render_forward(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, out["depth"],
+                           out["alpha"], out["normal"], out["flow"], out["saved"], self.ws, stream, colors=colors,
+                           color=out["color"])
+        return out
 
     def points(self, means, chol, weights, poses, stream=None):
         """Oriented point export (Sec. 6) of the last forward call's depth: world
@@ -340,55 +349,69 @@ class Renderer:
         return out
 
     def backward(self, means, chol, weights, poses, g_depth, g_alpha, g_normal, g_flow, want_pose=True,
-                 out=None, stream=None, colors=None, g_color=None):
+                 out=None, stream=None, colors=None, g_color=None, planes=None):
+        """Gradients of the forward call whose planes are ``planes`` (default: the
+        renderer's own, i.e. its last forward call into them)."""
         G = means.shape[0]
+        pl = planes if planes is not None else dict(depth=self.depth, normal=self.normal, saved=self.saved,
+                                                    color=self.color)
         if out is None:
             f32 = dict(dtype=torch.float32, device=means.device)
             out = dict(means=torch.empty(G, 3, **f32), chol=torch.empty(G, 6, **f32), weights=torch.empty(G, **f32),
                        poses=torch.empty(poses.shape[0], 12, **f32) if want_pose else None)
             if self.params.colors:
                 out["colors"] = torch.empty(G, 3, **f32)
-        fmb_render_backward(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, self.depth,
-                            self.normal, self.saved, g_depth, g_alpha, g_normal, g_flow, out["means"], out["chol"],
-                            out["weights"], out["poses"], self.ws, stream, colors=colors, color=self.color,
+        fmb_render_backward(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, pl["depth"],
+                            pl["normal"], pl["saved"], g_depth, g_alpha, g_normal, g_flow, out["means"], out["chol"],
+                            out["weights"], out["poses"], self.ws, stream, colors=colors, color=pl["color"],
                             g_color=g_color, grad_colors=out.get("colors"))
         return out
 
 
 class FmbRender(torch.autograd.Function):
-    """Differentiable render: (means, chol, weights, poses) -> (depth, alpha,
-    normal, flow) planes, with the library's adjoint as the backward."""
+    """Differentiable render: (means, chol, weights, poses[, colors]) -> (depth,
+    alpha, normal, flow[, color]) planes, with the library's adjoint
+    (``fmb_render_backward``) as the backward.
+
+    Every call renders into freshly allocated planes (``Renderer.new_planes``), so
+    several calls on one renderer may be alive in one autograd graph; the saved
+    per-pixel normalisers of each call stay with its graph node.  Planes the
+    renderer's params do not produce are returned as empty tensors.  Pose gradients
+    are computed only when ``poses`` requires a gradient.  The backward may run
+    more than once (``retain_graph``): each run recomputes from the saved planes.
+    Inside ``torch.cuda.graph`` the planes come from the graph's memory pool."""
 
     @staticmethod
-    def forward(ctx, renderer: Renderer, means, chol, weights, poses):
-        out = renderer.forward(means, chol, weights, poses)
+    def forward(ctx, renderer: Renderer, means, chol, weights, poses, colors=None):
+        out = renderer.forward(means, chol, weights, poses, colors=colors, out=renderer.new_planes())
+        empty = lambda t: t if t is not None else torch.zeros(0, device=means.device)
+        res = (out["depth"], out["alpha"], empty(out["normal"]), empty(out["flow"]))
+        if renderer.params.colors:
+            res = res + (out["color"],)
         ctx.renderer = renderer
-        ctx.save_for_backward(means, chol, weights, poses)
-        # outputs are copies so that the renderer's planes can be reused by the next call
-        res = [out["depth"].clone(), out["alpha"].clone(),
-               out["normal"].clone() if out["normal"] is not None else torch.zeros(0, device=means.device),
-               out["flow"].clone() if out["flow"] is not None else torch.zeros(0, device=means.device)]
-        ctx.saved_planes = (res[0], out["saved"].clone(), res[2] if out["normal"] is not None else None)
-        return tuple(res)
+        ctx.saved_plane = out["saved"]  # not an output: nothing else holds it
+        ctx.has_colors = colors is not None
+        ctx.save_for_backward(means, chol, weights, poses, colors, out["depth"], out["normal"], out["color"])
+        return res
 
     @staticmethod
-    def backward(ctx, g_depth, g_alpha, g_normal, g_flow):
+    def backward(ctx, g_depth, g_alpha, g_normal, g_flow, g_color=None):
         r: Renderer = ctx.renderer
-        means, chol, weights, poses = ctx.saved_tensors
-        depth, saved, normal = ctx.saved_planes
-        r.depth.copy_(depth)
-        r.saved.copy_(saved)
-        if normal is not None:
-            r.normal.copy_(normal)
+        means, chol, weights, poses, colors, depth, normal, color = ctx.saved_tensors
         c = lambda g: None if g is None or g.numel() == 0 else g.contiguous()
+        want_pose = bool(ctx.needs_input_grad[4])
         out = r.backward(means, chol, weights, poses, c(g_depth), c(g_alpha), c(g_normal), c(g_flow),
-                         want_pose=poses.requires_grad)
-        return None, out["means"], out["chol"], out["weights"], out["poses"]
+                         want_pose=want_pose, colors=colors, g_color=c(g_color),
+                         planes=dict(depth=depth, normal=normal, saved=ctx.saved_plane, color=color))
+        return (None, out["means"], out["chol"], out["weights"], out["poses"] if want_pose else None,
+                out.get("colors") if ctx.has_colors else None)
 
 
-def render(renderer: Renderer, means, chol, weights, poses):
-    """Differentiable render through ``FmbRender``."""
-    return FmbRender.apply(renderer, means, chol, weights, poses)
+def render(renderer: Renderer, means, chol, weights, poses, colors=None):
+    """Differentiable render through ``FmbRender``: a tuple (depth, alpha, normal,
+    flow) of planes in the batched layouts of ``fmb_render_forward`` (plus the
+    colour plane when the renderer's params have colours)."""
+    return FmbRender.apply(renderer, means, chol, weights, poses, colors)
 
 
 def pose_twist_grad(poses, grad_poses):

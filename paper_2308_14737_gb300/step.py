@@ -2,12 +2,13 @@
 planes, back-propagate through the renderer's adjoint, take one Adam step -- all
 captured once in a CUDA graph and replayed.
 
-The render and its adjoint are the library's kernels (``fmb_render_forward`` /
-``fmb_render_backward``), the optimiser is its fused Adam (``fmb_adam_step``); the
-loss is ordinary PyTorch elementwise code on preallocated buffers (the caller's
-choice of loss; here L1 depth and L2 flow weighted by the target mask, plus binary
-cross-entropy on alpha with the prediction clipped to [1e-6, 1 - 1e-6] as in
-Sec. 4).
+The render is ``fmb.FmbRender`` (a ``torch.autograd.Function`` over the library's
+``fmb_render_forward`` / ``fmb_render_backward`` kernels); the loss is ordinary
+PyTorch code on the rendered planes (the caller's choice of loss; here L1 depth and
+L2 flow weighted by the target mask, plus binary cross-entropy on alpha with the
+prediction clipped to [1e-6, 1 - 1e-6] as in Sec. 4), differentiated by autograd
+down to the planes, from where the library's adjoint takes over; the optimiser is
+the library's fused Adam (``fmb_adam_step``) over the packed parameters.
 """
 
 from __future__ import annotations
@@ -30,8 +31,10 @@ class ReconstructionStep:
         T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
         G = int(scene.means.shape[0])
         self.G = G
+        # the packed parameters [means | chol | weights], the leaf autograd differentiates to
         self.theta = torch.cat([T(scene.means).reshape(-1), T(scene.chol).reshape(-1), T(scene.weights)])
-        self.grad = torch.zeros_like(self.theta)
+        self.theta.requires_grad_(True)
+        self.grad = torch.zeros_like(self.theta, requires_grad=False)
         self.m = torch.zeros_like(self.theta)
         self.v = torch.zeros_like(self.theta)
         self.step_counter = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -57,45 +60,38 @@ class ReconstructionStep:
                 o, Pv = v["pix_offset"], v["W"] * v["H"]
                 mf[2 * nf * o:2 * nf * (o + Pv)] = np.tile(ta[o:o + Pv], 2 * nf)
             self.mask_flow = T(mf)
-        self.g_depth = torch.zeros(P, device=dev)
-        self.g_alpha = torch.zeros(P, device=dev)
-        self.g_flow = torch.zeros(2 * nf * P, device=dev) if nf else None
         self.loss = torch.zeros((), device=dev)
         self.w = (w_depth / P, w_alpha / P, w_flow / P)
         self.graph = None
 
     def views(self):
+        """means, chol, weights as differentiable views of the packed parameters."""
         G = self.G
         return self.theta[:3 * G].view(G, 3), self.theta[3 * G:9 * G].view(G, 6), self.theta[9 * G:]
 
-    def _loss_and_upstream(self, out):
+    def loss_of(self, depth, alpha, flow):
+        """The Sec. 4 loss of rendered planes (autograd-differentiable)."""
         wd, wa, wf = self.w
-        d = out["depth"] - self.t_depth
-        l_depth = (self.t_alpha * d.abs()).sum()
-        torch.mul(torch.sign(d), self.t_alpha * wd, out=self.g_depth)
-        a = out["alpha"]
-        ac = a.clamp(1e-6, 1.0 - 1e-6)
-        l_alpha = -(self.t_alpha * torch.log(ac) + (1.0 - self.t_alpha) * torch.log1p(-ac)).sum()
-        inside = ((a > 1e-6) & (a < 1.0 - 1e-6)).float()
-        torch.mul((ac - self.t_alpha) / (ac * (1.0 - ac)), inside * wa, out=self.g_alpha)
-        loss = wd * l_depth + wa * l_alpha
-        if self.g_flow is not None:
-            f = (out["flow"] - self.t_flow) * self.flow_scale
+        loss = wd * (self.t_alpha * (depth - self.t_depth).abs()).sum()
+        ac = alpha.clamp(1e-6, 1.0 - 1e-6)
+        loss = loss - wa * (self.t_alpha * torch.log(ac) + (1.0 - self.t_alpha) * torch.log1p(-ac)).sum()
+        if self.t_flow is not None:
+            f = (flow - self.t_flow) * self.flow_scale
             loss = loss + wf * (self.mask_flow * f * f).sum()
-            torch.mul(f * self.flow_scale, self.mask_flow * (2.0 * wf), out=self.g_flow)
-        self.loss.copy_(loss)
+        return loss
 
     def step(self):
-        """One iteration on the current stream (eager)."""
+        """One iteration on the current stream (eager): render through FmbRender, the
+        loss, its gradient with respect to the packed parameters by autograd (the
+        library's adjoint for the render), then the fused Adam step."""
         means, chol, weights = self.views()
-        out = self.renderer.forward(means, chol, weights, self.poses)
-        self._loss_and_upstream(out)
-        G = self.G
-        gd = dict(means=self.grad[:3 * G].view(G, 3), chol=self.grad[3 * G:9 * G].view(G, 6),
-                  weights=self.grad[9 * G:], poses=None)
-        self.renderer.backward(means, chol, weights, self.poses, self.g_depth, self.g_alpha, None, self.g_flow,
-                               want_pose=False, out=gd)
-        fmb.fmb_adam_step(self.adam, self.theta, self.grad, self.m, self.v, 9 * G, self.step_counter)
+        depth, alpha, _, flow = fmb.render(self.renderer, means, chol, weights, self.poses)
+        loss = self.loss_of(depth, alpha, flow)
+        (g,) = torch.autograd.grad(loss, [self.theta])
+        self.grad.copy_(g)
+        self.loss.copy_(loss.detach())
+        with torch.no_grad():
+            fmb.fmb_adam_step(self.adam, self.theta, self.grad, self.m, self.v, 9 * self.G, self.step_counter)
 
     def capture(self, warmup: int = 2):
         """Runs `warmup` eager steps on a side stream, then records one step in a

@@ -226,13 +226,14 @@ def test_permutation_invariance():
     assert np.all(np.abs(a["alpha"] - b["alpha"]) <= 1e-5)
 
 
-def _sampled_full_size(scene, n_flow, n_per_view, seed=0, deterministic=False, persistent=False, **pk):
+def _sampled_full_size(scene, n_flow, n_per_view, seed=0, deterministic=False, persistent=False, normals=True,
+                       want_pose=True, **pk):
     params = fmb.default_params(n_flow=n_flow, deterministic=int(deterministic), use_persistent=int(persistent),
-                                **pk)
+                                want_normals=int(normals), **pk)
     gpu, r, dev = gpu_forward(scene, params)
     pix = sample_pixels(scene, n_per_view, seed)
     ref = oracle_forward_sampled(scene, pix, n_flow)
-    stats = compare_forward(scene, gpu, None, n_flow, True, pixels_per_view=ref)
+    stats = compare_forward(scene, gpu, None, n_flow, normals, pixels_per_view=ref)
     alpha_ref = np.zeros(scene.n_pixels)
     nn_ref = np.zeros(scene.n_pixels)
     for vi, v in enumerate(scene.views):
@@ -240,9 +241,11 @@ def _sampled_full_size(scene, n_flow, n_per_view, seed=0, deterministic=False, p
         nn_ref[v["pix_offset"] + ref[vi][0]] = ref[vi][1]["saved"][:, 2]
     ups = masked_upstream(scene, alpha_ref, n_flow, seed=seed + 1, pixel_mask=pixel_mask_from(scene, pix),
                           nnorm_ref=nn_ref)
-    g = gpu_backward(r, dev, ups)
+    if not normals:
+        ups["g_normal"] = np.zeros_like(ups["g_normal"])
+    g = gpu_backward(r, dev, dict(ups, g_normal=ups["g_normal"] if normals else None), want_pose=want_pose)
     refg = oracle_backward_sampled(scene, ups, pix, n_flow)
-    errs = compare_grads(g, refg)
+    errs = compare_grads(g, refg, keys=("means", "chol", "weights") + (("poses",) if want_pose else ()))
     return stats, errs
 
 
@@ -280,6 +283,25 @@ def test_ragged_batch_64_objects_sampled():
 
 def test_ragged_batch_64_objects_persistent_sampled():
     _sampled_full_size(synth.ragged_batch(), n_flow=0, n_per_view=48, persistent=True)
+
+
+@pytest.mark.parametrize("deterministic,ray_tile", [(False, 256), (True, 384)])
+def test_reconstruction_full_size_100x640x480_K256_sampled(deterministic, ray_tile):
+    """The reconstruction workload at full size: 100 sphere views 640x480, K=256,
+    flow to the next and the previous view, depth + alpha (no normal plane), no pose
+    gradients, in the tiles its benchmark tunes to (128 backward threads, so one
+    block of all 256 Gaussians per ray tile; the no-pose adjoint), in both
+    reduction modes."""
+    _sampled_full_size(synth.reconstruction(), n_flow=2, n_per_view=40, seed=5, deterministic=deterministic,
+                       normals=False, want_pose=False, bwd_threads=128, bwd_ray_tile=ray_tile,
+                       fwd_rays_per_thread=2)
+
+
+def test_reconstruction_stored_intermediate_full_size_sampled():
+    """The stored-intermediate adjoint at the reconstruction workload's view size
+    and K (10 of its 640x480 views: 12 bytes per pair, 9.4 GB of stored values)."""
+    _sampled_full_size(synth.reconstruction(n_views=10), n_flow=2, n_per_view=60, seed=6, normals=False,
+                       want_pose=False, bwd_threads=128, bwd_ray_tile=384, fwd_rays_per_thread=2, store_pairs=1)
 
 
 def test_device_status_is_clear_and_outputs_finite():
