@@ -290,6 +290,16 @@ size_t fmb_workspace_bytes(const fmb_params* params, int n_objects, const long l
 int fmb_forward_ksplit(const fmb_params* params, int n_objects, const long long* h_obj_offsets, int n_views,
                        const fmb_view* h_views);
 
+/* Kernel launches one call of this batch enqueues: pass 0 = fmb_render_forward,
+ * pass 1 = fmb_render_backward (want_pose: grad_poses given).  Host-only query,
+ * like fmb_workspace_bytes; -1 on invalid input (message in fmb_last_error).  The
+ * paper has no counterpart: this reports a launch decision of this
+ * implementation (the batch is split into launches of at most a fixed number of
+ * views; a Gaussian-split forward adds a merge; deterministic mode adds the
+ * second-stage reductions). */
+int fmb_launch_count(const fmb_params* params, int n_objects, const long long* h_obj_offsets, int n_views,
+                     const fmb_view* h_views, int pass, int want_pose);
+
 /* Copies the device status word of a workspace to *h_status and synchronises
  * `stream`: 0 = no device-side error; nonzero = a bounded wait gave up (the
  * outputs of that call are invalid).  The word is cleared by every render call. */

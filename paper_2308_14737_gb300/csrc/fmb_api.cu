@@ -425,6 +425,26 @@ int fmb_forward_ksplit(const fmb_params* params, int n_objects, const long long*
   }
 }
 
+int fmb_launch_count(const fmb_params* params, int n_objects, const long long* h_obj_offsets, int n_views,
+                     const fmb_view* h_views, int pass, int want_pose) {
+  try {
+    if (validate_scene(params, n_objects, h_obj_offsets, n_views, h_views) != FMB_OK) return -1;
+    if (pass != 0 && pass != 1) {
+      fail(FMB_ERR_INVALID_ARG, "pass must be 0 (forward) or 1 (backward)");
+      return -1;
+    }
+    const Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views);
+    const int nb = static_cast<int>(pass == 0 ? pl.fwd.size() : pl.bwd.size());
+    if (pass == 0) return nb * (2 + (params->variant == 0 && pl.ksplit > 1 ? 1 : 0));  // prologue, forward, merge
+    if (nb == 0) return 1;  // the zeroing launch
+    // prologue and backward per batch; deterministic mode adds the Gaussian (and pose) reductions
+    return nb * (2 + (params->deterministic ? 1 + (want_pose ? 1 : 0) : 0));
+  } catch (const std::exception& e) {
+    fail(FMB_ERR_INVALID_ARG, e.what());
+    return -1;
+  }
+}
+
 size_t fmb_workspace_bytes(const fmb_params* params, int n_objects, const long long* h_obj_offsets, int n_views,
                            const fmb_view* h_views) {
   try {

@@ -87,6 +87,8 @@ def load_library(path: str = LIB_PATH):
     L.fmb_loss_attribution.restype = ctypes.c_int
     L.fmb_workspace_bytes.argtypes = [P, i, LL, i, V]
     L.fmb_workspace_bytes.restype = sz
+    L.fmb_launch_count.argtypes = [P, i, LL, i, V, i, i]
+    L.fmb_launch_count.restype = ctypes.c_int
     L.fmb_forward_ksplit.argtypes = [P, i, LL, i, V]
     L.fmb_forward_ksplit.restype = ctypes.c_int
     L.fmb_read_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
@@ -186,6 +188,17 @@ def fmb_forward_ksplit(params: FmbParams, obj_offsets, views) -> int:
     va = views if isinstance(views, ctypes.Array) else make_views(views)
     n = L.fmb_forward_ksplit(ctypes.byref(params), len(o) - 1, op, len(va), va)
     if n == 0:
+        raise FmbError(1, L.fmb_last_error().decode())
+    return int(n)
+
+
+def fmb_launch_count(params: FmbParams, obj_offsets, views, backward: bool, want_pose: bool = True) -> int:
+    """Kernel launches of one forward (backward=False) or backward call of this batch."""
+    L = load_library()
+    o, op = _offsets(obj_offsets)
+    va = views if isinstance(views, ctypes.Array) else make_views(views)
+    n = L.fmb_launch_count(ctypes.byref(params), len(o) - 1, op, len(va), va, int(bool(backward)), int(want_pose))
+    if n < 0:
         raise FmbError(1, L.fmb_last_error().decode())
     return int(n)
 

@@ -41,9 +41,54 @@ def measure(iters: int = 4096, blocks_per_sm: int = 8, reps: int = 5, device="cu
     return res
 
 
+def sample_clocks(fn, period_ms: int = 100):
+    """Runs fn() while nvidia-smi samples the SM clock; returns (fn's result, median
+    SM MHz of the samples, max SM MHz, throttle reasons seen)."""
+    import os
+    import statistics
+    import subprocess
+    import tempfile
+
+    fd, path = tempfile.mkstemp(suffix=".csv")
+    os.close(fd)
+    fields = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    idx = torch.cuda.current_device()
+    with open(path, "w") as fh:
+        try:
+            proc = subprocess.Popen(["nvidia-smi", "-i", str(idx), f"--query-gpu={fields}",
+                                     "--format=csv,noheader,nounits", "-lms", str(period_ms)], stdout=fh,
+                                    stderr=subprocess.DEVNULL)
+        except OSError:
+            proc = None
+        try:
+            res = fn()
+        finally:
+            if proc is not None:
+                proc.terminate()
+                proc.wait(timeout=5)
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        p = [x.strip() for x in line.split(",")]
+        try:
+            sm.append(float(p[0]))
+            smax.append(float(p[1]))
+        except (ValueError, IndexError):
+            continue
+        reasons.update(n for n, v in zip(names, p[2:6]) if v.lower().startswith("active"))
+    os.unlink(path)
+    return res, (statistics.median(sm) if sm else None), (max(smax) if smax else None), sorted(reasons)
+
+
 if __name__ == "__main__":  # pragma: no cover
     import json
 
-    r = measure()
-    clk = torch.cuda.clock_rate() if hasattr(torch.cuda, "clock_rate") else None
-    print(json.dumps({k: (v if k == "sms" else v / 1e12) for k, v in r.items()}))
+    # about 25 s in all (0.3 to 2.2 s per launch), long enough for the clock samples
+    r, mhz, max_mhz, reasons = sample_clocks(lambda: measure(iters=4096, reps=3))
+    out = {"sms": r["sms"], "sm_mhz_median": mhz, "sm_max_mhz": max_mhz, "reasons": reasons}
+    for k in KINDS.values():
+        out[k + "_tops"] = r[k] / 1e12
+        if mhz:
+            out[k + "_per_sm_clock"] = r[k] / (r["sms"] * mhz * 1e6)
+    print(json.dumps(out))

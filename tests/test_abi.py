@@ -231,3 +231,20 @@ def test_noalloc_status_reader_rejects_a_null_pointer(fmb):
     L = fmb.load_library()
     assert L.fmb_read_noalloc_status(None, None) == 1
     assert "h_status" in L.fmb_last_error().decode()
+
+
+def test_launch_count_follows_the_batch_split(fmb):
+    """Launches per call: prologue + kernel per launch batch; views beyond one
+    batch's capacity add batches; deterministic mode adds the reductions."""
+    s = synth.object_orbit(K=10, n_views=3, W=8, H=6)
+    p = fmb.default_params()
+    assert fmb.fmb_launch_count(p, s.obj_offsets, s.views, backward=False) == 2
+    assert fmb.fmb_launch_count(p, s.obj_offsets, s.views, backward=True) == 2
+    pd = fmb.default_params(deterministic=1)
+    assert fmb.fmb_launch_count(pd, s.obj_offsets, s.views, backward=True, want_pose=True) == 4
+    assert fmb.fmb_launch_count(pd, s.obj_offsets, s.views, backward=True, want_pose=False) == 3
+    big = synth.object_orbit(K=10, n_views=300, W=4, H=4)
+    n = fmb.fmb_launch_count(p, big.obj_offsets, big.views, backward=False)
+    assert n >= 2 and n % 2 == 0
+    p.fwd_ksplit = 2
+    assert fmb.fmb_launch_count(p, s.obj_offsets, s.views, backward=False) == 3

@@ -22,6 +22,14 @@ def test_reference_arm_prints_one_json_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "pairs/s"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    # the same config object as the GPU arm's (both come from bench.workload_config)
+    sys.path.insert(0, ROOT)
+    import bench
+
+    s, _ = bench.scene_and_inputs(workload=bench.DEFAULT_WORKLOAD)
+    want = dict(bench.workload_config(s, bench.WORKLOADS[bench.DEFAULT_WORKLOAD]), parallelism="single GPU")
+    assert d["config"] == json.loads(json.dumps(want))
+    assert d["config"]["pairs_per_step"] == 8 * 1024 * 768 * 4096
 
 
 def test_profile_gate_follows_sources_and_compile_flags(monkeypatch):
