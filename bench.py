@@ -66,10 +66,10 @@ OPS = {  # normals -> (fwd FP32, fwd MUFU, bwd FP32, bwd MUFU), with pose gradie
     True: (56, 4, 110, 4),
     False: (42, 3, 70, 3),
 }
-# Of those, the operations of the compensated (double-float) geometry: the split
-# residual, the low part of the whitened mean and the second projection onto a^perp
-# (docs/opcount.md).  The method's own work per pair is the rest.
-COMPENSATION = {"fwd": 13, "bwd": 13}
+# The algorithmic minimum of the whitened formulation (docs/opcount.md): the
+# executed counts above less the 16 operations of the compensated geometry and the
+# rsqrt guard of the normal.
+ALGO_OPS = {True: (39, 93), False: (26, 54)}  # normals -> (fwd FP32, bwd FP32), with pose gradients
 # Without pose gradients the two-parameter adjoint needs only the lower triangle of
 # sum v abar^T (6 of its 9 accumulations per pair).
 NO_POSE_SAVING = 3
@@ -82,9 +82,9 @@ OPS_AC = {True: (82, 4, 206, 7), False: (67, 3, 146, 5)}
 MUFU_MIX = {True: {"ex2": 2, "rcp": 1, "rsqrt": 1}, False: {"ex2": 2, "rcp": 1}}  # per pair, each pass
 N_SM = 152
 LANES_PER_SM = 128
-# MUFU results per SM and clock, measured by the ALU probe on the GB300
-# (profiles/alu_probe_rates.md): ex2 29, rcp and rsqrt 15.
-MUFU_RATE = {"ex2": 29.0, "rcp": 15.0, "rsqrt": 15.0}
+# MUFU results per SM and clock, measured by the ALU probe on the GB300 at 2070 MHz
+# (profiles/alu_probe_rates.md): ex2 31.8, rcp and rsqrt 16.0.
+MUFU_RATE = {"ex2": 31.8, "rcp": 16.0, "rsqrt": 16.0}
 
 
 def peak_fp32_gops(clock_mhz: float) -> float:
@@ -173,11 +173,18 @@ WORKLOADS = {
 }
 
 
-def scene_and_inputs(seed=0, workload="orbit"):
+def scene_and_inputs(seed=0, workload="orbit", views=None):
+    """The workload's seeded scene and upstream gradients; ``views``: keep only the
+    first that many views (a smaller case of the same kernels, for profiling)."""
     from paper_2308_14737_gb300 import synth
 
     wl = WORKLOADS[workload]
     s = synth.SCENES[wl["scene"]](seed=seed)
+    if views:
+        objs = [(s.means[s.object_slice(o)], s.chol[s.object_slice(o)], s.weights[s.object_slice(o)])
+                for o in range(s.n_objects)]
+        s = synth.make_scene(objs, [{k: v for k, v in vv.items() if k != "pix_offset"} for vv in s.views[:views]],
+                             s.poses, name=s.name + f"_first{views}")
     if wl.get("rays"):
         s = synth.ray_batch(s, wl["rays"], seed=seed)
     rng = np.random.default_rng(seed + 1)
@@ -281,7 +288,7 @@ def measure_workload(args, name, steps, warmup, dev, ws=1, extras=True, cpu=True
 
     wl = WORKLOADS[name]
     nf, want_pose = wl["n_flow"], wl["want_pose"]
-    s, ups = scene_and_inputs(workload=name)
+    s, ups = scene_and_inputs(workload=name, views=getattr(args, "views", None) if name == args.workload else None)
     pairs = s.n_pairs
     T = lambda a: None if a is None else torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     means, chol, weights, poses = T(s.means), T(s.chol), T(s.weights), T(s.poses)
@@ -451,7 +458,9 @@ def measure_workload(args, name, steps, warmup, dev, ws=1, extras=True, cpu=True
     if not ac:
         # the same times against the method's own operations only (the compensated
         # geometry's extra operations left out of the count)
-        cf, cb = f32f - COMPENSATION["fwd"], f32b - COMPENSATION["bwd"]
+        cf, cb = ALGO_OPS[bool(wl["normals"])]
+        if not want_pose:
+            cb -= NO_POSE_SAVING
         roofline["method_ops_only"] = {
             "bwd_fp32": cb, "fwd_fp32": cf,
             "frac": pairs * cb / (bwd_ms * 1e-3) / 1e9 / peak,
@@ -993,6 +1002,8 @@ def main():
     ap.add_argument("--points", action="store_true", help="also time the oriented point export (Sec. 6)")
     ap.add_argument("--attribution", action="store_true",
                     help="also time the loss attribution of the splitting criterion (Sec. 8)")
+    ap.add_argument("--views", type=int, default=None,
+                    help="render only the first N views of the headline workload (a smaller case for profiling)")
     ap.add_argument("--stored", action="store_true",
                     help="also time the stored-intermediate adjoint (always on for --workload recon)")
     args = ap.parse_args()

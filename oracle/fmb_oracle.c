@@ -235,6 +235,18 @@ static void forward_ray(int K, const double* means, const double* chol, const do
   }
 }
 
+/* Thread count of a call: n_threads > 0 as given, otherwise the process default
+ * (recorded before any call changed it, so a single-thread call does not leave
+ * later default calls on one thread). */
+#ifdef _OPENMP
+static int g_default_threads = 0;
+static void use_threads(int n_threads) {
+#pragma omp critical(fmbo_threads)
+  if (g_default_threads == 0) g_default_threads = omp_get_max_threads();
+  omp_set_num_threads(n_threads > 0 ? n_threads : g_default_threads);
+}
+#endif
+
 static int check_args(int K, int W, int H, int n_targets, double fx, double fy, double eta) {
   if (K < 1 || W < 1 || H < 1) return 1;
   if (n_targets < 0 || n_targets > FMBO_MAX_TARGETS) return 1;
@@ -261,7 +273,7 @@ static int forward_impl(int variant, int K, const double* means, const double* c
   const double* R = pose;
   const double* t = pose + 9;
 #ifdef _OPENMP
-  if (n_threads > 0) omp_set_num_threads(n_threads);
+  use_threads(n_threads);
 #else
   (void)n_threads;
 #endif
@@ -561,7 +573,7 @@ static int backward_impl(int variant, int K, const double* means, const double* 
   const double* t = pose + 9;
   int nt = 1;
 #ifdef _OPENMP
-  if (n_threads > 0) omp_set_num_threads(n_threads);
+  use_threads(n_threads);
   nt = omp_get_max_threads();
 #else
   (void)n_threads;
@@ -733,7 +745,7 @@ int fmbo_points(int variant, int K, const double* means, const double* chol, con
   const double* R = pose;
   const double* t = pose + 9;
 #ifdef _OPENMP
-  if (n_threads > 0) omp_set_num_threads(n_threads);
+  use_threads(n_threads);
 #else
   (void)n_threads;
 #endif
@@ -850,6 +862,7 @@ int fmbo_attribution(int variant, int K, const double* means, const double* chol
 /* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
 int fmbo_max_threads(void) {
 #ifdef _OPENMP
+  use_threads(0);
   return omp_get_max_threads();
 #else
   return 1;

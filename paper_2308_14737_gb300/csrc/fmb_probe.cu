@@ -48,10 +48,10 @@ __global__ void __launch_bounds__(256) probe_kernel(float* __restrict__ out, int
     for (int i = 0; i < iters; ++i)
 #pragma unroll
       for (int j = 0; j < 8; ++j) x[j] = ex2_approx(x[j]) - 1.0f;
-  } else if (KIND == 3) {  // rcp.approx
+  } else if (KIND == 3) {  // rcp.approx (plus a constant, so that no two reciprocals cancel)
     for (int i = 0; i < iters; ++i)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) x[j] = rcp_approx(x[j]);
+      for (int j = 0; j < 8; ++j) x[j] = rcp_approx(x[j]) + 0.25f;
   } else {  // rsqrt.approx
     for (int i = 0; i < iters; ++i)
 #pragma unroll

@@ -84,8 +84,8 @@ def sample_clocks(fn, period_ms: int = 100):
 if __name__ == "__main__":  # pragma: no cover
     import json
 
-    # about 25 s in all (0.3 to 2.2 s per launch), long enough for the clock samples
-    r, mhz, max_mhz, reasons = sample_clocks(lambda: measure(iters=4096, reps=3))
+    # about 6 s in all (0.07 to 0.5 s per launch), long enough for the clock samples
+    r, mhz, max_mhz, reasons = sample_clocks(lambda: measure(iters=1 << 20, reps=3))
     out = {"sms": r["sms"], "sm_mhz_median": mhz, "sm_max_mhz": max_mhz, "reasons": reasons}
     for k in KINDS.values():
         out[k + "_tops"] = r[k] / 1e12
