@@ -64,11 +64,11 @@ SUB_STEPS = {"single": 400, "orbit": 400, "ragged": 40, "recon": 30, "largek": 2
 # in docs/opcount.md from the formulas, with and without the normal plane.
 OPS = {  # normals -> (fwd FP32, fwd MUFU, bwd FP32, bwd MUFU), with pose gradients
     True: (56, 4, 110, 4),
-    False: (42, 3, 70, 3),
+    False: (35, 3, 63, 3),  # without normals the second projection of u is skipped (7 operations)
 }
 # The algorithmic minimum of the whitened formulation (docs/opcount.md): the
-# executed counts above less the 16 operations of the compensated geometry and the
-# rsqrt guard of the normal.
+# executed counts above less the operations of the compensated geometry (16 with
+# normals, 9 without) and the rsqrt guard of the normal.
 ALGO_OPS = {True: (39, 93), False: (26, 54)}  # normals -> (fwd FP32, bwd FP32), with pose gradients
 # Without pose gradients the two-parameter adjoint needs only the lower triangle of
 # sum v abar^T (6 of its 9 accumulations per pair).

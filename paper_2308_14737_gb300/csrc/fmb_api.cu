@@ -33,6 +33,8 @@ constexpr int kDefaultRpt = 2;
 constexpr int kMaxGaussPerCta = 256;
 constexpr long long kMaxK = 1 << 22;
 constexpr int kMaxKAlphaCompositing = 256;
+constexpr long long kMaxGaussians = 0x7fffffffll;  // all objects together (32-bit Gaussian offsets)
+constexpr long long kMaxRecords = 1ll << 28;       // sum over views of K (32-bit record offsets, 16 GB)
 
 fmb_status fail(fmb_status s, const std::string& msg) {
   g_err = msg;
@@ -160,6 +162,7 @@ fmb_status validate_scene(const fmb_params* p, int n_objects, const long long* o
       return fail(FMB_ERR_INVALID_ARG, "object " + std::to_string(k) +
                                            " has more than 256 Gaussians (the alpha-compositing limit)");
   }
+  if (offs[n_objects] > kMaxGaussians) return fail(FMB_ERR_INVALID_ARG, "too many Gaussians in all");
   if (n_views < 1) return fail(FMB_ERR_INVALID_ARG, "n_views must be >= 1");
   if (!views) return fail(FMB_ERR_INVALID_ARG, "h_views is NULL");
   return FMB_OK;
@@ -273,11 +276,11 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
       d.pose = v.pose;
       d.tgt0 = n_flow > 0 ? v.flow_target[0] : -1;
       d.tgt1 = n_flow > 1 ? v.flow_target[1] : -1;
-      d.obj = v.object;
       d.K = static_cast<int>(offs[v.object + 1] - offs[v.object]);
       pl.maxK = std::max(pl.maxK, d.K);
-      d.gauss_off = offs[v.object];
-      d.rec_off = rec;
+      d.gauss_off = static_cast<int>(offs[v.object]);
+      if (rec + d.K > kMaxRecords) throw std::runtime_error("too many (view, Gaussian) pairs in one batch");
+      d.rec_off = static_cast<int>(rec);
       d.pix_off = v.pix_offset;
       rec += d.K;
       const long long P = view_entries(v);

@@ -93,11 +93,11 @@ __device__ __forceinline__ void bwd_pair2(BwdAcc2& A, const GaussRec2& gr, const
   PairGeom2 G;
   f2 what, delta;
   if (STORED) {
-    G = pair_geom2_given_t(gr, st, v0, v1, v2, as_f2(q5.x), as_f2(q5.y), as_f2(q6.x));
+    G = pair_geom2_given_t<NORMALS>(gr, st, v0, v1, v2, as_f2(q5.x), as_f2(q5.y), as_f2(q6.x));
     what = ex2_2(add2(se, nlse));
     delta = sd;
   } else {
-    G = pair_geom2(gr, v0, v1, v2, as_f2(q5.x), as_f2(q5.y), as_f2(q6.x));
+    G = pair_geom2<NORMALS>(gr, v0, v1, v2, as_f2(q5.x), as_f2(q5.y), as_f2(q6.x));
     const f2 x = fma2(G.q, K3, gr.l2);  // log2(delta)
     what = ex2_2(fma2(x, B1, fma2(G.t, K2, nlse)));
     delta = ex2_2(x);

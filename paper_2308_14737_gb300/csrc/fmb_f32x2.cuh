@@ -97,9 +97,15 @@ __device__ __forceinline__ GaussRec2 pair_rec(const GaussRec& a, const GaussRec&
 // pair_geom for two lanes (two rays against one Gaussian, or one ray against two
 // Gaussians); same operation sequence as
 // the scalar pair_geom, so each lane's result is bitwise the scalar one.
+// REFINE = false skips the second projection of u onto the complement of a: it
+// only removes the component a dt that the rounding dt of t leaves in u, to which
+// q = u.u is stationary (it changes q by dt^2 a.a, below fp32 resolution), so
+// passes that use u only through q (no normal plane) do not need it; the normal
+// g = L u does.
 struct PairGeom2 {
   f2 a0, a1, a2, ninv, t, u0, u1, u2, q;  // ninv = -1 / a.a
 };
+template <bool REFINE = true>
 __device__ __forceinline__ PairGeom2 pair_geom2(const GaussRec2& g, f2 v0, f2 v1, f2 v2, f2 vl0, f2 vl1, f2 vl2) {
   PairGeom2 G;
   G.a0 = fma2(g.L[3], v2, fma2(g.L[1], v1, mul2(g.L[0], v0)));
@@ -117,10 +123,16 @@ __device__ __forceinline__ PairGeom2 pair_geom2(const GaussRec2& g, f2 v0, f2 v1
   const f2 u0 = fma2(g.L[0], r0, fma2(g.L[1], r1, fma2(g.L[3], r2, g.nbl[0])));
   const f2 u1 = fma2(g.L[2], r1, fma2(g.L[4], r2, g.nbl[1]));
   const f2 u2 = fma2(g.L[5], r2, g.nbl[2]);
-  const f2 nk = mul2(fma2(u2, G.a2, fma2(u1, G.a1, mul2(u0, G.a0))), ninv);
-  G.u0 = fma2(nk, G.a0, u0);
-  G.u1 = fma2(nk, G.a1, u1);
-  G.u2 = fma2(nk, G.a2, u2);
+  if (REFINE) {
+    const f2 nk = mul2(fma2(u2, G.a2, fma2(u1, G.a1, mul2(u0, G.a0))), ninv);
+    G.u0 = fma2(nk, G.a0, u0);
+    G.u1 = fma2(nk, G.a1, u1);
+    G.u2 = fma2(nk, G.a2, u2);
+  } else {
+    G.u0 = u0;
+    G.u1 = u1;
+    G.u2 = u2;
+  }
   G.q = fma2(G.u2, G.u2, fma2(G.u1, G.u1, mul2(G.u0, G.u0)));
   return G;
 }
@@ -129,6 +141,7 @@ __device__ __forceinline__ PairGeom2 pair_geom2(const GaussRec2& g, f2 v0, f2 v1
 // reads the forward's t instead of recomputing it): the same operations after t,
 // so with the forward's t the results are those pair_geom2 would give; q is not
 // formed (the density comes stored too).
+template <bool REFINE = true>
 __device__ __forceinline__ PairGeom2 pair_geom2_given_t(const GaussRec2& g, f2 t, f2 v0, f2 v1, f2 v2, f2 vl0,
                                                         f2 vl1, f2 vl2) {
   PairGeom2 G;
@@ -146,10 +159,16 @@ __device__ __forceinline__ PairGeom2 pair_geom2_given_t(const GaussRec2& g, f2 t
   const f2 u0 = fma2(g.L[0], r0, fma2(g.L[1], r1, fma2(g.L[3], r2, g.nbl[0])));
   const f2 u1 = fma2(g.L[2], r1, fma2(g.L[4], r2, g.nbl[1]));
   const f2 u2 = fma2(g.L[5], r2, g.nbl[2]);
-  const f2 nk = mul2(fma2(u2, G.a2, fma2(u1, G.a1, mul2(u0, G.a0))), ninv);
-  G.u0 = fma2(nk, G.a0, u0);
-  G.u1 = fma2(nk, G.a1, u1);
-  G.u2 = fma2(nk, G.a2, u2);
+  if (REFINE) {
+    const f2 nk = mul2(fma2(u2, G.a2, fma2(u1, G.a1, mul2(u0, G.a0))), ninv);
+    G.u0 = fma2(nk, G.a0, u0);
+    G.u1 = fma2(nk, G.a1, u1);
+    G.u2 = fma2(nk, G.a2, u2);
+  } else {
+    G.u0 = u0;
+    G.u1 = u1;
+    G.u2 = u2;
+  }
   G.q = dup(0.f);
   return G;
 }

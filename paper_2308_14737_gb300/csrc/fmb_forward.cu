@@ -94,7 +94,7 @@ struct RayAcc {
 
 template <bool NORMALS>
 __device__ __forceinline__ void fwd_pair(RayAcc& A, const GaussRec& g, const Consts& k) {
-  const PairGeom G = pair_geom(g.L, g.b, g.mh, g.nbl, A.v0, A.v1, A.v2, A.vl0, A.vl1, A.vl2);
+  const PairGeom G = pair_geom<NORMALS>(g.L, g.b, g.mh, g.nbl, A.v0, A.v1, A.v2, A.vl0, A.vl1, A.vl2);
   const float x = fmaf(G.q, k.K3, g.l2);  // log2(delta)
   A.Sd += ex2_approx(x);
   const float e2 = fmaf(x, k.beta1, G.t * k.K2);
@@ -141,7 +141,7 @@ struct PairOut2 {
 template <bool NORMALS, bool COLOR = false>
 __device__ __forceinline__ PairOut2 fwd_pair2(RayAcc2& A, const GaussRec2& g, f2 K2, f2 K3, f2 beta1, f2 tiny,
                                               float4 col = float4{}) {
-  const PairGeom2 G = pair_geom2(g, A.v0, A.v1, A.v2, A.vl0, A.vl1, A.vl2);
+  const PairGeom2 G = pair_geom2<NORMALS>(g, A.v0, A.v1, A.v2, A.vl0, A.vl1, A.vl2);
   const f2 x = fma2(G.q, K3, g.l2);  // log2(delta)
   const f2 delta = ex2_2(x);
   A.Sd = add2(A.Sd, delta);

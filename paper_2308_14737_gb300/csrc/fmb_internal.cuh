@@ -11,9 +11,17 @@
 namespace fmb {
 
 // Views per kernel launch: the view table travels in the kernel's parameter space
-// (a __grid_constant__ struct), so launches need no host->device copy and can be
-// captured in CUDA graphs.  Larger batches are split into several launches.
-constexpr int kMaxBatchViews = 64;
+// (a __grid_constant__ struct of about 7 KB), so launches need no host->device copy
+// and can be captured in CUDA graphs.  Larger batches are split into several
+// launches.  (256 views, 30 KB, would still fit the 32 KB of kernel parameters of
+// sm_90 and later; measured on the GB300, one launch per pass instead of four made
+// the 256-view ragged batch 0.35 % faster, but the larger parameter block made
+// every launch of a small batch slower: a single 64x64 view's forward + backward
+// calls took 5-10 us more, 15-30 %.)
+#ifndef FMB_MAX_BATCH_VIEWS
+#define FMB_MAX_BATCH_VIEWS 64
+#endif
+constexpr int kMaxBatchViews = FMB_MAX_BATCH_VIEWS;
 
 // Per (view, Gaussian) record written by the prologue, 64 bytes (4 x float4):
 //   [L00 L10 L11 L20 | L21 L22 b0 b1 | b2 mh0 mh1 mh2 | nbl0 nbl1 nbl2 l2]
@@ -47,21 +55,21 @@ struct DevView {
   float fx, fy, cx, cy;
   int pose, tgt0, tgt1;
   int K;           // Gaussians of the view's object
-  int obj;
   int n_tiles;     // ray tiles of this view
   int n_gblocks;   // backward: Gaussian blocks
   int GB, S;       // backward: Gaussians per block, ray subgroups per CTA
-  long long gauss_off;  // first Gaussian of the object in means/chol/weights
-  long long rec_off;    // first record (in records) of this view in the workspace
-  long long pix_off;    // first pixel of this view in the planes
-  long long part_off;   // backward deterministic mode: float offset of the view's first slot
   int slot_floats;      // floats per (tile, gblock) slot in deterministic mode
   int Kp;               // stored-intermediate mode: row length (K rounded up to a multiple of 4)
-  long long pair_off;   // stored-intermediate mode: first float of the view's [P][Kp] block
-  const int* rays;      // ray batch: pixel index of each plane entry, or null (whole image)
   int P;                // plane entries of the view: n_rays, or W * H
   int rt;               // backward: rays per tile of this view (0: the launch's ray tile)
+  int gauss_off;        // first Gaussian of the object in means/chol/weights (< 2^31, checked on the host)
+  int rec_off;          // first record (in records) of this view in the workspace (< 2^28, checked)
+  long long pix_off;    // first pixel of this view in the planes
+  long long part_off;   // backward deterministic mode: float offset of the view's first slot
+  long long pair_off;   // stored-intermediate mode: first float of the view's [P][Kp] block
+  const int* rays;      // ray batch: pixel index of each plane entry, or null (whole image)
 };
+static_assert(sizeof(DevView) == 112, "DevView layout");
 
 // Pixel rendered by plane entry i of a view.
 __device__ __forceinline__ int ray_pixel(const DevView& V, int i) { return V.rays ? __ldg(V.rays + i) : i; }
@@ -77,6 +85,8 @@ struct Batch {
   int order_begin[kMaxBatchViews + 1];  // first item of order_view[j]
   DevView v[kMaxBatchViews];
 };
+// Leaves room below the 32 764-byte kernel-parameter limit for the other arguments.
+static_assert(sizeof(Batch) <= 31 * 1024, "Batch must fit the kernel parameter space");
 
 // Constants folded from the parameters (log2 domain).
 // With x = log2(delta) = K3 q + log2(lambda), the log2 weight of Eq. 7 is
@@ -209,6 +219,7 @@ __device__ __forceinline__ void camera_centre_dd(const float R[9], const float t
 struct PairGeom {
   float a0, a1, a2, inv, t, u0, u1, u2, q;
 };
+template <bool REFINE = true>  // REFINE: the second projection (see pair_geom2)
 __device__ __forceinline__ PairGeom pair_geom(const float L[6], const float b[3], const float mh[3],
                                               const float nbl[3], float v0, float v1, float v2, float vl0,
                                               float vl1, float vl2) {
@@ -227,10 +238,16 @@ __device__ __forceinline__ PairGeom pair_geom(const float L[6], const float b[3]
   float u0 = fmaf(L00, r0, fmaf(L10, r1, fmaf(L20, r2, nbl[0])));
   float u1 = fmaf(L11, r1, fmaf(L21, r2, nbl[1]));
   float u2 = fmaf(L22, r2, nbl[2]);
-  const float k = fmaf(u2, G.a2, fmaf(u1, G.a1, u0 * G.a0)) * G.inv;
-  G.u0 = fmaf(-k, G.a0, u0);
-  G.u1 = fmaf(-k, G.a1, u1);
-  G.u2 = fmaf(-k, G.a2, u2);
+  if (REFINE) {
+    const float k = fmaf(u2, G.a2, fmaf(u1, G.a1, u0 * G.a0)) * G.inv;
+    G.u0 = fmaf(-k, G.a0, u0);
+    G.u1 = fmaf(-k, G.a1, u1);
+    G.u2 = fmaf(-k, G.a2, u2);
+  } else {
+    G.u0 = u0;
+    G.u1 = u1;
+    G.u2 = u2;
+  }
   G.q = fmaf(G.u2, G.u2, fmaf(G.u1, G.u1, G.u0 * G.u0));
   return G;
 }

@@ -273,6 +273,48 @@ def test_orbit_full_size_dense_gradients():
     compare_grads(g, refg)
 
 
+def test_orbit_unmasked_normal_gradient_within_bound():
+    """Gradients on the 16-view orbit with the normal plane's upstream gradient NOT
+    masked by |N| >= 0.05 (only by the paper's object mask, alpha >= 1e-2), against
+    a bound computed per gradient entry.  A pixel p whose per-Gaussian normals nearly
+    cancel contributes c_p = J_p^T Nbar_p with Nbar_p = (I - n n^T) nbar_f / |N_p|:
+    an error dN_p of the forward's blended vector N_p moves n = N/|N| and 1/|N| by at
+    most dN_p/|N_p| each, and (I - n n^T) by 2 dN_p/|N_p|, so c_p moves by at most
+    |c_p| (4 dN_p/|N_p| + e), e = 1e-4 for the per-pair terms.  dN_p is the measured
+    forward error at that pixel (GPU against oracle, both |N| n_f), c_p the oracle's
+    gradient of that pixel alone.  The bound is the masked tolerance, 1e-4 of the
+    tensor's largest entry (it covers every pixel with |N| >= 0.05, as the masked
+    tests show), plus the sum of those terms over the pixels with |N| < 0.05."""
+    s = synth.object_orbit()
+    params = fmb.default_params(n_flow=1)
+    gpu, r, dev = gpu_forward(s, params)
+    ref = oracle.render_scene(s, n_flow=1)
+    ups = masked_upstream(s, ref["alpha"], 1, seed=2)  # object mask only
+    g = gpu_backward(r, dev, ups)
+    refg = oracle.backward_scene(s, ups["g_depth"], ups["g_alpha"], ups["g_normal"], ups["g_flow"], n_flow=1)
+    nn = nnorm_batched(s, ref["saved"])
+    small = np.nonzero((ref["alpha"] >= 1e-2) & (nn < 0.05))[0]
+    bound = {k: np.full(refg[k].shape, 1e-4 * np.max(np.abs(refg[k]))) for k in refg}
+    for vi, v in enumerate(s.views):
+        o, P = v["pix_offset"], v["W"] * v["H"]
+        Ng = plane_view(gpu["normal"], v, 3) * plane_view(gpu["saved"], v, 3)[2]
+        Nr = plane_view(ref["normal"], v, 3) * plane_view(ref["saved"], v, 3)[2]
+        dN = np.linalg.norm(Ng - Nr, axis=0)
+        for p in small[(small >= o) & (small < o + P)] - o:
+            c = oracle_backward_sampled(s, ups, {vj: ([p] if vj == vi else []) for vj in range(len(s.views))}, 1)
+            f = 4.0 * dN[p] / max(nn[o + p], 1e-30) + 1e-4
+            for k in bound:
+                bound[k] += f * np.abs(c[k])
+    report = {}
+    for k in ("means", "chol", "weights", "poses"):
+        err = np.abs(g[k].reshape(refg[k].shape) - refg[k])
+        scale = np.max(np.abs(refg[k]))
+        report[k] = (float(err.max() / scale), float(bound[k].max() / scale))
+        assert np.all(err <= bound[k]), (k, report[k])
+    print(f"unmasked normal-gradient errors (max err / max |g|, max bound / max |g|), {len(small)} pixels with "
+          f"|N| < 0.05: {report}")
+
+
 def test_large_K4096_8x1024x768_sampled():
     _sampled_full_size(synth.large_k(), n_flow=1, n_per_view=48)
 
