@@ -294,7 +294,9 @@ def measure_workload(args, name, steps, warmup, dev, ws=1, extras=True, cpu=True
     means, chol, weights, poses = T(s.means), T(s.chol), T(s.weights), T(s.poses)
     gd, ga, gn, gf = (T(ups[k]) for k in ("g_depth", "g_alpha", "g_normal", "g_flow"))
     ac = args.variant == "ac"
-    params = fmb.default_params(n_flow=nf, want_normals=wl["normals"], variant=1 if ac else 0)
+    # alpha compositing: the forward keeps each ray's depth order for the backward (both arms)
+    params = fmb.default_params(n_flow=nf, want_normals=wl["normals"], variant=1 if ac else 0,
+                                keep_order=1 if ac else 0)
     batched = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), params, device=dev)
     G = means.shape[0]
     grads = dict(means=torch.empty(G, 3, device=dev), chol=torch.empty(G, 6, device=dev),

@@ -102,7 +102,14 @@ typedef struct {
                         tiles fill less than half a wave of the GPU and an object has
                         at least 128 Gaussians), 1 = never, 2..8 = that many splits.
                         Two-parameter model only; ignored with colors or store_pairs. */
-  int reserved;      /* 0 */
+  int keep_order;    /* variant 1 only.  1: the forward also keeps each ray's depth order
+                        of the object's Gaussians (the result of its per-ray sort, Eq. 10)
+                        in the workspace -- 32 M bytes per plane entry, M = 2, 4 or 8 for
+                        a largest object of at most 64, 128 or 256 Gaussians -- and the
+                        backward starts from it instead of sorting again.  The backward
+                        must then be given the workspace of the forward call of the same
+                        batch, unchanged (as with store_pairs).  0 (default): the backward
+                        sorts each ray afresh.  Not with fmb_render_forward_noalloc. */
 } fmb_params;
 
 /* One camera view of one object.  Planes of the view start at pixel `pix_offset`
@@ -157,7 +164,9 @@ typedef struct {
  * are scratch and need not be preserved between calls, except with
  * store_pairs = 1, where the forward leaves the per-pair values there for the
  * backward of the same batch (workspace size then grows by 12 bytes per pair,
- * rounded up: 12 x sum over views of P_v x (K_v rounded up to a multiple of 4)).
+ * rounded up: 12 x sum over views of P_v x (K_v rounded up to a multiple of 4)),
+ * and with keep_order = 1 (variant 1), where it leaves each ray's depth order
+ * there (32 M bytes per plane entry).
  * A Gaussian-split forward (fwd_ksplit, fmb_forward_ksplit) also keeps 32 bytes per
  * ray and split of partial sums there between its two kernels.
  */

@@ -15,8 +15,14 @@ from . import fmb
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "fmb_gb300", "autotune.json")
 
-CANDIDATES = [dict(fwd_rays_per_thread=r, bwd_threads=t, bwd_ray_tile=t * m, use_persistent=p)
-              for r in (2, 4) for t in (128, 160) for m in (2, 3) for p in (0, 1)]
+# Grid launches only: the persistent mode (use_persistent = 1) measured slower than
+# the grid launch on every configuration and tile on the GB300 (orbit 3-19 %, large
+# K 0.05-0.4 %, ragged batch see the design notes): it cannot use the backward's
+# 2-CTA clusters, and each work item costs two CTA barriers and a global atomic
+# round trip, where the hardware starts the next CTA of a grid in a freed slot
+# directly and already takes the cost-ordered items most expensive first.
+CANDIDATES = [dict(fwd_rays_per_thread=r, bwd_threads=t, bwd_ray_tile=t * m, use_persistent=0)
+              for r in (2, 4) for t in (128, 160) for m in (2, 3)]
 
 # Extra candidates for small batches (fewer 256-ray tiles than two waves of the
 # GPU's SMs): short ray tiles and narrow CTAs spread a few thousand rays over more

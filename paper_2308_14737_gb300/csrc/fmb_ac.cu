@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 4 : 5) forward_ac_kernel(
       // a ray batch's consecutive entries are not neighbouring pixels: sort each afresh
       const AcSums a = ac_render_ray<NORMALS, M>(srec, V.K, v, vl, k, lane, t, dl, n, sd, sw, sT, key,
                                                  j > 0 && V.rays == nullptr, crec);
+      if (out.order != nullptr) ac_store_order<M>(out.order + (off + p) * (32 * M), key, lane);
       if (lane == 0) {
         const float iW = a.W > 0.f ? 1.0f / a.W : 0.f;
         const float D = a.WT * iW;
@@ -317,8 +318,10 @@ __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 2 : 3) backward_ac_kernel
       pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
       float t[M], dl[M], n[M][3];
       const float4* crec = color ? s.crec + V.rec_off : nullptr;
+      // the forward's order (keep_order): the refinement then only confirms it
+      if (in.order != nullptr) ac_load_order<M>(in.order + (off + p) * (32 * M), K, lane, key);
       const AcSums a = ac_render_ray<NORMALS, M>(srec, K, v, vl, k, lane, t, dl, n, sd, sw, sT, key,
-                                                 j > 0 && V.rays == nullptr, crec);
+                                                 in.order != nullptr || (j > 0 && V.rays == nullptr), crec);
       const float iW = a.W > 0.f ? 1.0f / a.W : 0.f;
       const float D = a.WT * iW;
       // colour mode: Cbar and the blended colour C = sum w c / W

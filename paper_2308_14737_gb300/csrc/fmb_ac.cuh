@@ -287,6 +287,35 @@ __device__ __forceinline__ AcSums ac_render_ray(const float4* __restrict__ rec, 
   return r;
 }
 
+// keep_order: a ray's depth order as the indices of its sorted Gaussians, 32 M
+// bytes per plane entry (sorting position lane M + m at byte lane M + m; K <= 256
+// so an index fits a byte; positions >= K are unused).  Each lane moves its M bytes
+// with one M-byte access.
+template <int M>
+__device__ __forceinline__ void ac_store_order(unsigned char* row, const unsigned long long (&key)[M], int lane) {
+  unsigned long long w = 0;
+#pragma unroll
+  for (int m = 0; m < M; ++m)
+    if (key[m] != kNoKey) w |= static_cast<unsigned long long>(key[m] & 0xffu) << (8 * m);
+  unsigned char* dst = row + lane * M;
+  if (M == 2) *reinterpret_cast<unsigned short*>(dst) = static_cast<unsigned short>(w);
+  if (M == 4) *reinterpret_cast<unsigned*>(dst) = static_cast<unsigned>(w);
+  if (M == 8) *reinterpret_cast<unsigned long long*>(dst) = w;
+}
+// The stored order as start keys for ac_render_ray's refinement (Gaussian index in
+// the low word; the high word is filled in there from the recomputed depths).
+template <int M>
+__device__ __forceinline__ void ac_load_order(const unsigned char* __restrict__ row, int K, int lane,
+                                              unsigned long long (&key)[M]) {
+  const unsigned char* src = row + lane * M;
+  unsigned long long w = 0;
+  if (M == 2) w = __ldg(reinterpret_cast<const unsigned short*>(src));
+  if (M == 4) w = __ldg(reinterpret_cast<const unsigned*>(src));
+  if (M == 8) w = __ldg(reinterpret_cast<const unsigned long long*>(src));
+#pragma unroll
+  for (int m = 0; m < M; ++m) key[m] = lane * M + m < K ? (w >> (8 * m)) & 0xffu : kNoKey;
+}
+
 // Stages a view's K records into shared memory with one bulk copy; every thread
 // waits (bounded).  Returns false (after recording the timeout) if the copy did
 // not arrive.

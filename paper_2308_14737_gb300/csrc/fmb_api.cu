@@ -124,6 +124,7 @@ struct Plan {
   int ksplit = 1;  // two-parameter forward: Gaussian splits per view (1 = unsplit)
   long long fwd_part_floats = 0;  // split forward: per-ray partial sums
   std::vector<fmb::Batch> fmerge;  // split forward: merge launches (one per forward launch)
+  long long n_entries = 0;         // plane entries of the batch (pixels or rays)
 };
 
 fmb_status validate_scene(const fmb_params* p, int n_objects, const long long* offs, int n_views,
@@ -139,6 +140,9 @@ fmb_status validate_scene(const fmb_params* p, int n_objects, const long long* o
   if (p->use_persistent != 0 && p->use_persistent != 1) return fail(FMB_ERR_INVALID_ARG, "use_persistent must be 0 or 1");
   if (p->store_pairs != 0 && p->store_pairs != 1) return fail(FMB_ERR_INVALID_ARG, "store_pairs must be 0 or 1");
   if (p->colors != 0 && p->colors != 1) return fail(FMB_ERR_INVALID_ARG, "colors must be 0 or 1");
+  if (p->keep_order != 0 && p->keep_order != 1) return fail(FMB_ERR_INVALID_ARG, "keep_order must be 0 or 1");
+  if (p->keep_order && p->variant != 1)
+    return fail(FMB_ERR_INVALID_ARG, "keep_order applies to variant 1 (alpha compositing) only");
   if (p->colors && p->store_pairs) return fail(FMB_ERR_INVALID_ARG, "colors is not available with store_pairs");
   if (p->store_pairs && (p->fwd_rays_per_thread == 1 || p->fwd_rays_per_thread == 4))
     return fail(FMB_ERR_INVALID_ARG, "store_pairs needs fwd_rays_per_thread 0 or 2");
@@ -284,6 +288,7 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
       d.pix_off = v.pix_offset;
       rec += d.K;
       const long long P = view_entries(v);
+      pl.n_entries += P;
       d.rays = v.rays;
       d.P = static_cast<int>(P);
       d.Kp = (d.K + 3) / 4 * 4;  // rows of 16-byte multiples
@@ -372,9 +377,17 @@ size_t fwd_part_offset(const fmb_params* p, const Plan& pl) {
   return bytes;
 }
 
-size_t workspace_needed(const fmb_params* p, const Plan& pl) {
+size_t order_offset(const fmb_params* p, const Plan& pl) {
   return fwd_part_offset(p, pl) + align256(static_cast<size_t>(pl.fwd_part_floats) * sizeof(float));
 }
+
+// keep_order: 32 M bytes (M of the alpha-compositing kernels) per plane entry.
+size_t order_bytes(const fmb_params* p, const Plan& pl) {
+  if (!p->keep_order) return 0;
+  return align256(static_cast<size_t>(pl.n_entries) * 32 * fmb::ac_lanes_per_ray_elements(pl.maxK));
+}
+
+size_t workspace_needed(const fmb_params* p, const Plan& pl) { return order_offset(p, pl) + order_bytes(p, pl); }
 
 fmb::Consts make_consts(const fmb_params* p) {
   const double log2e = 1.4426950408889634;
@@ -509,6 +522,7 @@ fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const lon
       fmb::FwdOut fo{depth, alpha, normal, flow, saved, pairs, pl.pair_stride};
       fo.color = color;
       fo.part = reinterpret_cast<float*>(static_cast<char*>(workspace) + fwd_part_offset(params, pl));
+      if (params->keep_order) fo.order = static_cast<unsigned char*>(workspace) + order_offset(params, pl);
       if (params->variant == 1) {
         fo.pairs = nullptr;
         e = fmb::launch_forward_ac(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.maxK, fo, pl.ac_run,
@@ -579,6 +593,7 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
       in.g_color = g_color;
       out.gcolors = grad_colors;
     }
+    if (params->keep_order) in.order = reinterpret_cast<const unsigned char*>(base + order_offset(params, pl));
 
     fmb::ZeroJob zj{};
     zj.ptr[0] = reinterpret_cast<float*>(status);
@@ -825,6 +840,8 @@ extern "C" fmb_status fmb_render_forward_noalloc(const fmb_params* params, int n
     if (st != FMB_OK) return st;
     if (params->store_pairs)
       return fail(FMB_ERR_INVALID_ARG, "store_pairs needs a workspace (use fmb_render_forward)");
+    if (params->keep_order)
+      return fail(FMB_ERR_INVALID_ARG, "keep_order needs a workspace (use fmb_render_forward)");
     fmb_params unsplit = *params;  // the fixed scratch holds the records only: no Gaussian split
     unsplit.fwd_ksplit = 1;
     params = &unsplit;

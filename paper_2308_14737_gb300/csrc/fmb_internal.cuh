@@ -426,6 +426,7 @@ struct FwdOut {
   long long pair_stride;    // floats per array
   float* color = nullptr;   // colour plane [3][P_v] per view (colour mode)
   float* part = nullptr;    // Gaussian-split forward: per-ray partial sums, 8 floats per (ray, split)
+  unsigned char* order = nullptr;  // alpha compositing, keep_order: [plane entry][32 M] sorted Gaussian indices
 };
 
 cudaError_t launch_zero(const ZeroJob& job, cudaStream_t st);
@@ -450,6 +451,7 @@ struct BwdIn {
   long long pair_stride;   // floats per array
   const float* color = nullptr;    // colour mode: the forward's colour plane
   const float* g_color = nullptr;  // colour mode: its upstream gradient (may be null)
+  const unsigned char* order = nullptr;  // alpha compositing, keep_order: the forward's per-ray depth order
 };
 cudaError_t launch_backward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
                             int n_flow, int ray_tile, int threads, const BwdIn& in, const BwdOut& out,
@@ -461,6 +463,7 @@ int backward_ctas_per_sm(bool normals, int n_flow, int ray_tile, int threads);
 // Alpha-compositing variant (Sec. 3.3): work items are 32-ray tiles, K <= 256 per
 // view (maxK: the batch's largest K).
 int ac_rays_per_item();
+int ac_lanes_per_ray_elements(int maxK);  // M: each lane holds M of the 32 M sort keys of a ray
 int ac_fwd_run(long long total_rays, int sms);  // forward rays per warp for a batch of total_rays
 int ac_fwd_rays_per_item(int run);
 cudaError_t launch_forward_ac(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,

@@ -248,3 +248,23 @@ def test_launch_count_follows_the_batch_split(fmb):
     assert n >= 2 and n % 2 == 0
     p.fwd_ksplit = 2
     assert fmb.fmb_launch_count(p, s.obj_offsets, s.views, backward=False) == 3
+
+
+def test_keep_order_workspace_and_validation(fmb):
+    """keep_order (alpha compositing) adds 32 M bytes per plane entry to the
+    workspace (M = 4 for objects of at most 128 Gaussians), is rejected for the
+    two-parameter model and by the allocation-free forward."""
+    views = [_view(W=10, H=7)]
+    p1 = fmb.default_params(variant=1)
+    pk = fmb.default_params(variant=1, keep_order=1)
+    extra = fmb.fmb_workspace_bytes(pk, [0, 100], views) - fmb.fmb_workspace_bytes(p1, [0, 100], views)
+    assert 70 * 32 * 4 <= extra < 70 * 32 * 4 + 256
+    st, err = _call_fwd(fmb, fmb.default_params(keep_order=1), [0, 5], [_view()])
+    assert st == 1 and "keep_order" in err
+    L = fmb.load_library()
+    f = _Fake()
+    fp = ctypes.c_void_p(f.data_ptr())
+    o = np.asarray([0, 5], dtype=np.int64)
+    st = L.fmb_render_forward_noalloc(ctypes.byref(pk), 1, o.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), fp,
+                                      fp, fp, fp, 1, fp, 1, fmb.make_views([_view()]), fp, fp, fp, fp, fp, fp, None)
+    assert st == 1 and "keep_order" in L.fmb_last_error().decode()
