@@ -98,7 +98,13 @@ def mufu_busy_frac(pairs_per_s: float, clock_mhz: float, normals: bool = True) -
     return pairs_per_s * sm_clocks_per_pair / (N_SM * clock_mhz * 1e6)
 
 
-PROFILE = os.path.join(ROOT, "profiles", "backward_kernel_orbit16x320x240_K100.md")
+# Committed ncu summaries of the backward kernel, per workload.  Each records the
+# DRAM bytes of one captured launch and the factor that scales them to one launch
+# of the workload (the large-K capture is a 3-view case of the same kernel, within
+# the size rule for full ncu captures; its plane traffic grows with the pixels).
+PROFILES = {"orbit": os.path.join(ROOT, "profiles", "backward_kernel_orbit16x320x240_K100.md"),
+            "largek": os.path.join(ROOT, "profiles", "backward_kernel_largek8x1024x768_K4096.md")}
+PROFILE = PROFILES["orbit"]
 
 
 def csrc_sha256() -> str:
@@ -117,26 +123,31 @@ def csrc_sha256() -> str:
     return h.hexdigest()
 
 
-def profiled_traffic(tiles=None):
-    """DRAM bytes (read + write) per launch of the backward kernel from the
-    committed ncu summary, or None if the kernel sources or the launch tiles
-    changed since the capture."""
+def profiled_traffic(tiles=None, workload="orbit"):
+    """DRAM bytes (read + write) per launch of the backward kernel on a workload,
+    from the committed ncu summary (scaled to a full launch by the summary's
+    scale_to_full factor), or None if there is no summary for the workload or the
+    kernel sources or the launch tiles changed since the capture."""
     try:
-        txt = open(PROFILE).read()
-    except OSError:
+        txt = open(PROFILES[workload]).read()
+    except (OSError, KeyError):
         return None
-    vals = dict(line.split(":", 1) for line in txt.splitlines() if line.startswith(("dram_bytes_per_launch",
-                                                                                    "source_sha256", "tiles")))
+    vals = dict(line.split(":", 1) for line in txt.splitlines()
+                if line.startswith(("dram_bytes_per_launch", "source_sha256", "tiles", "scale_to_full")))
     sha = next((v for k, v in vals.items() if k.startswith("source_sha256")), "").strip()
     if not sha or sha.split()[-1] != csrc_sha256():
         return None
-    if tiles is not None:
-        want = " ".join(f"{k}={int(v)}" for k, v in sorted(tiles.items()))
+    if tiles is not None:  # the backward kernel's tiles (the forward's do not change its traffic)
+        want = " ".join(f"{k}={int(v)}" for k, v in sorted(tiles.items())
+                        if k in ("bwd_ray_tile", "bwd_threads", "use_persistent"))
         if vals.get("tiles", "").strip() != want:
             return None
     try:
-        return int(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
+        frac = vals.get("scale_to_full", "1").split("(")[0].strip()  # e.g. "8/3 (pixels)"
+        num, _, den = frac.partition("/")
+        scale = float(num) / (float(den) if den else 1.0)
+        return int(round(int(vals["dram_bytes_per_launch"]) * scale))
+    except (KeyError, ValueError, SyntaxError, TypeError, ZeroDivisionError):
         return None
 
 
@@ -468,9 +479,10 @@ def measure_workload(args, name, steps, warmup, dev, ws=1, extras=True, cpu=True
             "frac": pairs * cb / (bwd_ms * 1e-3) / 1e9 / peak,
             "forward_frac": pairs * cf / (fwd_ms * 1e-3) / 1e9 / peak,
             "step_frac": pairs * (cf + cb) / (ms_step * 1e-3) / 1e9 / peak}
-    # the committed ncu summary covers the two-parameter backward on the orbit workload
-    roofline["traffic"] = (profiled_traffic({k: int(getattr(tuned_params, k)) for k in autotune.TUNED_FIELDS})
-                           if name == "orbit" and not ac else None)
+    # the committed ncu summaries cover the two-parameter backward on the orbit and large-K workloads
+    roofline["traffic"] = (profiled_traffic({k: int(getattr(tuned_params, k)) for k in autotune.TUNED_FIELDS},
+                                            workload=name)
+                           if not ac and not getattr(args, "views", None) else None)
     rec = {
         "workload": name,
         "config": workload_config(s, wl, args.variant),

@@ -112,15 +112,24 @@ def tune(obj_offsets, views, n_poses, params: fmb.FmbParams, means, chol, weight
                                    upstream["g_normal"], upstream["g_flow"], want_pose=want_pose, out=out))
         step()
         torch.cuda.synchronize(device)
+        # short steps (a few hundred microseconds or less) are timed over more
+        # repetitions, so that each timed block lasts about 2 ms and the choice does
+        # not follow the timing noise of a handful of tiny launches
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        torch.cuda.synchronize(device)
+        n_rep = max(reps, min(64, int(2.0 / max(e0.elapsed_time(e1), 1e-3))))
         best_ms = None
         for _ in range(3):  # best of three timed runs: robust to the GPU's other work
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            for _ in range(reps):
+            for _ in range(n_rep):
                 step()
             e1.record()
             torch.cuda.synchronize(device)
-            ms = e0.elapsed_time(e1) / reps
+            ms = e0.elapsed_time(e1) / n_rep
             best_ms = ms if best_ms is None else min(best_ms, ms)
         timings.append(dict(choice=c, ms=best_ms))
         del r

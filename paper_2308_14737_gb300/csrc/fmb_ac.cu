@@ -51,6 +51,7 @@ template <bool NORMALS, int NFLOW, int M>
 __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 4 : 5) forward_ac_kernel(const __grid_constant__ Batch batch, Scene s,
                                                                 Consts k, const float4* __restrict__ records,
                                                                 FwdOut out, int run, int* status, int* counter) {
+  pdl_enter();
   extern __shared__ float4 ac_smem[];  // records [32 M][4 float4] | per warp: sd, sw, sT [32 M floats each]
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_item;
@@ -252,6 +253,7 @@ template <bool NORMALS, int NFLOW, int M>
 __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 2 : 3) backward_ac_kernel(const __grid_constant__ Batch batch, Scene s,
                                                                  Consts k, const float4* __restrict__ records,
                                                                  BwdIn in, BwdOut out, int* status, int* counter) {
+  pdl_enter();
   extern __shared__ float4 ac_smem[];
   constexpr int NPV = 12 * (1 + NFLOW);
   __shared__ float pose_ray[kAcWarps][NPV];
@@ -672,8 +674,7 @@ static cudaError_t launch_fwd_ac_t(const Batch& b, const Scene& s, const Consts&
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kAcThreads, smem);
     grid = std::min(b.n_items, std::max(1, sms) * std::max(1, per));
   }
-  kern<<<grid, kAcThreads, smem, st>>>(b, s, c, records, o, run, status, counter);
-  return cudaGetLastError();
+  return launch_kernel(kern, dim3(grid), dim3(kAcThreads), smem, st, 1, b, s, c, records, o, run, status, counter);
 }
 
 template <bool NORMALS, int NFLOW, int M>
@@ -693,8 +694,7 @@ static cudaError_t launch_bwd_ac_t(const Batch& b, const Scene& s, const Consts&
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kAcThreads, smem);
     grid = std::min(b.n_items, std::max(1, sms) * std::max(1, per));
   }
-  kern<<<grid, kAcThreads, smem, st>>>(b, s, c, records, in, out, status, counter);
-  return cudaGetLastError();
+  return launch_kernel(kern, dim3(grid), dim3(kAcThreads), smem, st, 1, b, s, c, records, in, out, status, counter);
 }
 
 template <int M>

@@ -11,6 +11,7 @@ namespace fmb {
 __global__ void adam_kernel(float* __restrict__ param, const float* __restrict__ grad, float* __restrict__ m,
                             float* __restrict__ v, long long n, long long positive_begin, float lr, float b1,
                             float b2, float eps, const int* __restrict__ step) {
+  pdl_enter();
   const int t = *step + 1;
   const float c1 = 1.0f - powf(b1, static_cast<float>(t));
   const float c2 = 1.0f - powf(b2, static_cast<float>(t));
@@ -30,7 +31,10 @@ __global__ void adam_kernel(float* __restrict__ param, const float* __restrict__
   }
 }
 
-__global__ void increment_kernel(int* step) { *step += 1; }
+__global__ void increment_kernel(int* step) {
+  pdl_enter();
+  *step += 1;
+}
 
 }  // namespace fmb
 
@@ -43,8 +47,9 @@ extern "C" fmb_status fmb_adam_step(const fmb_adam_params* p, float* param, cons
     return FMB_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const long long blocks = (n + 255) / 256;
-  fmb::adam_kernel<<<static_cast<unsigned>(blocks < 4 * 152 ? blocks : 4 * 152), 256, 0, s>>>(
-      param, grad, m, v, n, positive_begin, p->lr, p->beta1, p->beta2, p->eps, step_counter);
-  fmb::increment_kernel<<<1, 1, 0, s>>>(step_counter);
-  return cudaGetLastError() == cudaSuccess ? FMB_OK : FMB_ERR_CUDA;
+  cudaError_t e = fmb::launch_kernel(fmb::adam_kernel, dim3(static_cast<unsigned>(blocks < 4 * 152 ? blocks : 4 * 152)),
+                                     dim3(256), 0, s, 1, param, grad, m, v, n, positive_begin, p->lr, p->beta1,
+                                     p->beta2, p->eps, static_cast<const int*>(step_counter));
+  if (e == cudaSuccess) e = fmb::launch_kernel(fmb::increment_kernel, dim3(1), dim3(1), 0, s, 1, step_counter);
+  return e == cudaSuccess ? FMB_OK : FMB_ERR_CUDA;
 }

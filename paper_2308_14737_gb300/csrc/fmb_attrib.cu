@@ -32,6 +32,7 @@ template <int M>
 __global__ void __launch_bounds__(kAcThreads) attribution_kernel(const __grid_constant__ Batch batch, Scene s,
                                                                  Consts k, const float4* __restrict__ records,
                                                                  const float* __restrict__ loss, float* out) {
+  pdl_enter();
   __shared__ float scratch[kAcWarps][3 * 32 * M];
   __shared__ float sums[kAcWarps][32 * M];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -96,6 +97,7 @@ __global__ void __launch_bounds__(kAtt2MaxThreads) attribution2_kernel(const __g
                                                                        const float* __restrict__ saved,
                                                                        const float* __restrict__ loss, float* out,
                                                                        int ray_tile) {
+  pdl_enter();
   extern __shared__ float4 asm_[];
   __shared__ int wtot[kAtt2MaxThreads / 32];
   int local;
@@ -199,16 +201,17 @@ cudaError_t launch_attribution2(const Batch& b, const Scene& s, const Consts& c,
     cudaError_t e = cudaFuncSetAttribute(attribution2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
-  attribution2_kernel<<<b.n_items, threads, smem, st>>>(b, s, c, records, saved, loss, out, ray_tile);
-  return cudaGetLastError();
+  return launch_kernel(attribution2_kernel, dim3(b.n_items), dim3(threads), smem, st, 1, b, s, c, records, saved, loss,
+                       out, ray_tile);
 }
 
 cudaError_t launch_attribution_ac(const Batch& b, const Scene& s, const Consts& c, const float4* records, int maxK,
                                   const float* loss, float* out, cudaStream_t st) {
   const int M = maxK <= 64 ? 2 : (maxK <= 128 ? 4 : 8);
-  if (M == 2) attribution_kernel<2><<<b.n_items, kAcThreads, 0, st>>>(b, s, c, records, loss, out);
-  else if (M == 4) attribution_kernel<4><<<b.n_items, kAcThreads, 0, st>>>(b, s, c, records, loss, out);
-  else attribution_kernel<8><<<b.n_items, kAcThreads, 0, st>>>(b, s, c, records, loss, out);
+  const dim3 grid(b.n_items), block(kAcThreads);
+  if (M == 2) return launch_kernel(attribution_kernel<2>, grid, block, 0, st, 1, b, s, c, records, loss, out);
+  if (M == 4) return launch_kernel(attribution_kernel<4>, grid, block, 0, st, 1, b, s, c, records, loss, out);
+  return launch_kernel(attribution_kernel<8>, grid, block, 0, st, 1, b, s, c, records, loss, out);
   return cudaGetLastError();
 }
 

@@ -189,6 +189,7 @@ template <bool NORMALS, int NFLOW, bool STORED, bool COLOR = false, bool POSE = 
 __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
     backward_kernel(const __grid_constant__ Batch batch, Scene s, Consts k, const float4* __restrict__ records,
                     BwdIn in, BwdOut out, int ray_tile, int* counter) {
+  pdl_enter();
   extern __shared__ float4 bsm[];
   constexpr int NPV = 12 * (1 + NFLOW);  // pose values reduced per CTA
   __shared__ float pose_ray[kBwdMaxThreads / 32][NPV];  // per-warp sums of the per-ray pose terms
@@ -605,27 +606,14 @@ static cudaError_t launch_bwd_s(const Batch& b, const Scene& s, const Consts& c,
   }
   if constexpr (!STORED && !COLOR) {
     if (counter == nullptr && bwd_cluster_size(b) == 2) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    e = prepare_bwd_t<NORMALS, NFLOW, STORED, COLOR, POSE, 2>(smem);
-    if (e != cudaSuccess) return e;
-    return cudaLaunchKernelEx(&cfg, backward_kernel<NORMALS, NFLOW, STORED, COLOR, POSE, 2>, b, s, c, records, in, out,
-                              ray_tile, counter);
+      e = prepare_bwd_t<NORMALS, NFLOW, STORED, COLOR, POSE, 2>(smem);
+      if (e != cudaSuccess) return e;
+      return launch_kernel(backward_kernel<NORMALS, NFLOW, STORED, COLOR, POSE, 2>, dim3(grid), dim3(threads), smem, st,
+                           2, b, s, c, records, in, out, ray_tile, counter);
     }
   }
-  backward_kernel<NORMALS, NFLOW, STORED, COLOR, POSE><<<grid, threads, smem, st>>>(b, s, c, records, in, out, ray_tile,
-                                                                               counter);
-  return cudaGetLastError();
+  return launch_kernel(backward_kernel<NORMALS, NFLOW, STORED, COLOR, POSE>, dim3(grid), dim3(threads), smem, st, 1, b,
+                       s, c, records, in, out, ray_tile, counter);
 }
 
 template <bool NORMALS, int NFLOW>
@@ -665,6 +653,7 @@ int backward_ctas_per_sm(bool normals, int n_flow, int ray_tile, int threads) {
 // One launch clears the status word and every gradient output before the
 // backward kernels accumulate into them.
 __global__ void zero_kernel(ZeroJob job) {
+  pdl_enter();
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
   long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
   for (int b = 0; b < ZeroJob::kMax; ++b) {
@@ -674,8 +663,7 @@ __global__ void zero_kernel(ZeroJob job) {
 }
 
 cudaError_t launch_zero(const ZeroJob& job, cudaStream_t st) {
-  zero_kernel<<<2 * 152, 256, 0, st>>>(job);
-  return cudaGetLastError();
+  return launch_kernel(zero_kernel, dim3(2 * 152), dim3(256), 0, st, 1, job);
 }
 
 // ------------------------------------------- deterministic second stage
@@ -692,6 +680,7 @@ __device__ __forceinline__ float warp_sum_fixed(float x) {
 __global__ void reduce_gauss_kernel(const __grid_constant__ Batch batch, const float* __restrict__ partials,
                                     float* gmeans, float* gchol, float* gweights, float* gcolors, long long n_gauss,
                                     int nc) {
+  pdl_enter();
   const long long w = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= n_gauss * nc) return;  // whole warps exit together
@@ -723,6 +712,7 @@ __global__ void reduce_gauss_kernel(const __grid_constant__ Batch batch, const f
 // Pose gradients: warp w handles (pose p, component comp), w = p * 12 + comp.
 __global__ void reduce_pose_kernel(const __grid_constant__ Batch batch, const float* __restrict__ partials,
                                    float* gposes, int n_poses, int n_flow, int nc) {
+  pdl_enter();
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= n_poses * 12) return;
@@ -747,13 +737,13 @@ cudaError_t launch_backward_reduce(const Batch& b, int n_flow, long long n_gauss
                                    cudaStream_t st) {
   const int nc = out.gcolors != nullptr ? 13 : 10;
   const long long warps = n_gauss * nc;
-  reduce_gauss_kernel<<<static_cast<unsigned>((warps * 32 + 255) / 256), 256, 0, st>>>(
-      b, out.partials, out.gmeans, out.gchol, out.gweights, out.gcolors, n_gauss, nc);
-  cudaError_t e = cudaGetLastError();
+  const dim3 grid(static_cast<unsigned>((warps * 32 + 255) / 256));
+  const float* partials = out.partials;
+  cudaError_t e = launch_kernel(reduce_gauss_kernel, grid, dim3(256), 0, st, 1, b, partials, out.gmeans, out.gchol,
+                                out.gweights, out.gcolors, n_gauss, nc);
   if (e != cudaSuccess || out.gposes == nullptr) return e;
-  reduce_pose_kernel<<<(n_poses * 12 * 32 + 255) / 256, 256, 0, st>>>(b, out.partials, out.gposes, n_poses, n_flow,
-                                                                       nc);
-  return cudaGetLastError();
+  return launch_kernel(reduce_pose_kernel, dim3((n_poses * 12 * 32 + 255) / 256), dim3(256), 0, st, 1, b, partials,
+                       out.gposes, n_poses, n_flow, nc);
 }
 
 }  // namespace fmb

@@ -28,6 +28,7 @@ constexpr int kChunk = 256;  // records per shared-memory stage (16 KB)
 __global__ void __launch_bounds__(128) prologue_kernel(const __grid_constant__ Batch batch, Scene s, Consts k,
                                                         float4* __restrict__ records, int* status_to_clear,
                                                         int* counter_to_clear, ZeroJob zero) {
+  pdl_enter();
   const DevView& V = batch.v[blockIdx.y];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0 && blockIdx.y == 0) {
@@ -78,9 +79,8 @@ __global__ void __launch_bounds__(128) prologue_kernel(const __grid_constant__ B
 cudaError_t launch_prologue(const Batch& b, const Scene& s, const Consts& c, float4* records, int maxK,
                             int* status_to_clear, int* counter_to_clear, cudaStream_t st, const ZeroJob* zero) {
   dim3 grid((maxK + 127) / 128, b.n_views);
-  prologue_kernel<<<grid, 128, 0, st>>>(b, s, c, records, status_to_clear, counter_to_clear,
-                                        zero != nullptr ? *zero : ZeroJob{});
-  return cudaGetLastError();
+  return launch_kernel(prologue_kernel, grid, dim3(128), 0, st, 1, b, s, c, records, status_to_clear,
+                       counter_to_clear, zero != nullptr ? *zero : ZeroJob{});
 }
 
 // ------------------------------------------------------------------- forward
@@ -278,6 +278,7 @@ template <bool NORMALS, int NFLOW, int RPT, bool STORE, bool COLOR = false>
 __global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_constant__ Batch batch, Scene s,
                                                               Consts k, const float4* __restrict__ records,
                                                               FwdOut out, int* status, int* counter) {
+  pdl_enter();
   extern __shared__ float4 fwd_smem[];  // 1 or 2 stages x kChunk records
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ int s_item;
@@ -522,8 +523,7 @@ static cudaError_t launch_fwd_t(const Batch& b, const Scene& s, const Consts& c,
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     grid = std::min(b.n_items, std::max(1, sms) * fwd_ctas_per_sm_t<NORMALS, NFLOW, RPT>(maxK));
   }
-  kern<<<grid, kFwdThreads, smem, st>>>(b, s, c, records, o, status, counter);
-  return cudaGetLastError();
+  return launch_kernel(kern, dim3(grid), dim3(kFwdThreads), smem, st, 1, b, s, c, records, o, status, counter);
 }
 
 template <bool NORMALS, int NFLOW>
@@ -566,6 +566,7 @@ int forward_merge_rays_per_item() { return kMergeThreads; }
 template <bool NORMALS, int NFLOW>
 __global__ void __launch_bounds__(kMergeThreads) fwd_merge_kernel(const __grid_constant__ Batch batch, Scene s,
                                                                   FwdOut out) {
+  pdl_enter();
   int local;
   const int vi = find_item(batch, blockIdx.x, local);
   const DevView& V = batch.v[vi];
@@ -618,16 +619,15 @@ __global__ void __launch_bounds__(kMergeThreads) fwd_merge_kernel(const __grid_c
 cudaError_t launch_forward_merge(const Batch& b, const Scene& s, bool normals, int n_flow, const FwdOut& o,
                                  cudaStream_t st) {
   if (b.n_items <= 0) return cudaSuccess;
+  const dim3 grid(b.n_items), block(kMergeThreads);
   if (normals) {
-    if (n_flow == 0) fwd_merge_kernel<true, 0><<<b.n_items, kMergeThreads, 0, st>>>(b, s, o);
-    else if (n_flow == 1) fwd_merge_kernel<true, 1><<<b.n_items, kMergeThreads, 0, st>>>(b, s, o);
-    else fwd_merge_kernel<true, 2><<<b.n_items, kMergeThreads, 0, st>>>(b, s, o);
-  } else {
-    if (n_flow == 0) fwd_merge_kernel<false, 0><<<b.n_items, kMergeThreads, 0, st>>>(b, s, o);
-    else if (n_flow == 1) fwd_merge_kernel<false, 1><<<b.n_items, kMergeThreads, 0, st>>>(b, s, o);
-    else fwd_merge_kernel<false, 2><<<b.n_items, kMergeThreads, 0, st>>>(b, s, o);
+    if (n_flow == 0) return launch_kernel(fwd_merge_kernel<true, 0>, grid, block, 0, st, 1, b, s, o);
+    if (n_flow == 1) return launch_kernel(fwd_merge_kernel<true, 1>, grid, block, 0, st, 1, b, s, o);
+    return launch_kernel(fwd_merge_kernel<true, 2>, grid, block, 0, st, 1, b, s, o);
   }
-  return cudaGetLastError();
+  if (n_flow == 0) return launch_kernel(fwd_merge_kernel<false, 0>, grid, block, 0, st, 1, b, s, o);
+  if (n_flow == 1) return launch_kernel(fwd_merge_kernel<false, 1>, grid, block, 0, st, 1, b, s, o);
+  return launch_kernel(fwd_merge_kernel<false, 2>, grid, block, 0, st, 1, b, s, o);
 }
 
 int forward_ctas_per_sm(bool normals, int n_flow, int rpt, int maxK) {

@@ -115,6 +115,21 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   return y;
 }
 
+// Programmatic dependent launch (sm_90 and later).  Every kernel of the library is
+// launched with programmatic stream serialisation (launch_kernel below) and starts
+// with pdl_enter(): it first waits until the grids before it in the stream have
+// completed and their memory is visible (griddepcontrol.wait), so its memory
+// accesses are ordered exactly as without the attribute, and then allows the next
+// kernel of the stream to be launched (griddepcontrol.launch_dependents).  That
+// launch takes effect once every CTA of this grid has started, so the next
+// kernel's CTAs are scheduled into the SMs this grid's last wave leaves idle and
+// wait there, instead of being launched only after this grid has drained.  In a
+// kernel launched without the attribute both instructions do nothing.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -383,6 +398,34 @@ __device__ __forceinline__ void load_pose(const float* poses, int idx, float R[9
 }
 
 // ----------------------------------------------------------- launchers (host)
+// Launches kern<<<grid, block, smem, st>>>(args...) with programmatic stream
+// serialisation (see pdl_enter), as a thread-block cluster of cluster_x CTAs if
+// cluster_x > 1.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                 unsigned cluster_x, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[2];
+  unsigned n = 0;
+  at[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[n].val.programmaticStreamSerializationAllowed = 1;
+  ++n;
+  if (cluster_x > 1) {
+    at[n].id = cudaLaunchAttributeClusterDimension;
+    at[n].val.clusterDim.x = cluster_x;
+    at[n].val.clusterDim.y = 1;
+    at[n].val.clusterDim.z = 1;
+    ++n;
+  }
+  cfg.attrs = at;
+  cfg.numAttrs = n;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 struct Scene {
   const float* means;
   const float* chol;

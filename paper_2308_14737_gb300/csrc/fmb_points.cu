@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kPtsThreads) points_kernel(const __grid_consta
                                                              const float4* __restrict__ records,
                                                              const float* __restrict__ depth,
                                                              const float* __restrict__ saved, PtsOut out) {
+  pdl_enter();
   int tile;
   const int vi = find_item(batch, blockIdx.x, tile);
   const DevView& V = batch.v[vi];
@@ -204,6 +205,7 @@ __global__ void __launch_bounds__(kAcThreads) points_ac_kernel(const __grid_cons
                                                                Consts k, const float4* __restrict__ records,
                                                                const float* __restrict__ depth, PtsOut out,
                                                                int run) {
+  pdl_enter();
   __shared__ float scratch[kAcWarps][3 * 32 * M];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int tile;
@@ -280,13 +282,12 @@ cudaError_t launch_points(const Batch& b, const Scene& s, const Consts& c, const
   if (variant == 1) {
     const int M = maxK <= 64 ? 2 : (maxK <= 128 ? 4 : 8);
     if (ac_run < 1 || ac_run > kAcMaxRun) return cudaErrorInvalidValue;
-    if (M == 2) points_ac_kernel<2><<<b.n_items, kAcThreads, 0, st>>>(b, s, c, records, depth, o, ac_run);
-    else if (M == 4) points_ac_kernel<4><<<b.n_items, kAcThreads, 0, st>>>(b, s, c, records, depth, o, ac_run);
-    else points_ac_kernel<8><<<b.n_items, kAcThreads, 0, st>>>(b, s, c, records, depth, o, ac_run);
-  } else {
-    points_kernel<<<b.n_items, kPtsThreads, 0, st>>>(b, s, c, records, depth, saved, o);
+    const dim3 grid(b.n_items), block(kAcThreads);
+    if (M == 2) return launch_kernel(points_ac_kernel<2>, grid, block, 0, st, 1, b, s, c, records, depth, o, ac_run);
+    if (M == 4) return launch_kernel(points_ac_kernel<4>, grid, block, 0, st, 1, b, s, c, records, depth, o, ac_run);
+    return launch_kernel(points_ac_kernel<8>, grid, block, 0, st, 1, b, s, c, records, depth, o, ac_run);
   }
-  return cudaGetLastError();
+  return launch_kernel(points_kernel, dim3(b.n_items), dim3(kPtsThreads), 0, st, 1, b, s, c, records, depth, saved, o);
 }
 
 }  // namespace fmb
