@@ -725,7 +725,7 @@ def e2e_measure(args, name, s, ups, params, dev):
     overlaps those copies with the neighbouring steps' kernels."""
     import torch
 
-    from paper_2308_14737_gb300 import pipeline
+    from paper_2308_14737_gb300 import fmb, pipeline
 
     want_pose = WORKLOADS[name]["want_pose"]
     pin = lambda a: None if a is None else torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).pin_memory()
@@ -752,8 +752,28 @@ def e2e_measure(args, name, s, ups, params, dev):
     e1.record(cur)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / n
+    # the last step's host results against a plain device-resident call on the same
+    # inputs: planes bitwise, gradients up to the order of fp32 atomic additions
+    d = {k: None if v is None else v.to(dev) for k, v in h_in.items()}
+    r = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), params, device=dev)
+    out = r.forward(d["means"], d["chol"], d["weights"], d["poses"])
+    g = r.backward(d["means"], d["chol"], d["weights"], d["poses"], d["g_depth"], d["g_alpha"], d["g_normal"],
+                   d["g_flow"], want_pose=want_pose)
+    want = dict(depth=out["depth"], alpha=out["alpha"], normal=out["normal"], flow=out["flow"],
+                grad_means=g["means"], grad_chol=g["chol"], grad_weights=g["weights"], grad_poses=g["poses"])
+    got = h_outs[(n - 1) % 2]
+    for k, v in want.items():
+        if v is None:
+            continue
+        a, b = got[k].reshape(-1), v.reshape(-1).cpu()
+        ok = torch.equal(a, b) if not k.startswith("grad") else \
+            bool((a - b).abs().max() <= 1e-5 * float(b.abs().max()) + 1e-30)
+        if not ok:
+            raise RuntimeError(f"host-fed pipeline result {k} differs from the plain call's")
     return {"value": s.n_pairs / (ms * 1e-3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": ms,
+            "parity": "last step's host results vs a plain device call: planes bitwise, gradients within 1e-5 "
+                      "of the largest entry",
             "api": "pipeline.HostPipeline: two device buffer sets; each step's host->device copies, forward + "
                    "backward (CUDA graph) and device->host copies on three streams, overlapped across steps"}
 

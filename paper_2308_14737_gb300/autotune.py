@@ -96,10 +96,10 @@ def tune(obj_offsets, views, n_poses, params: fmb.FmbParams, means, chol, weight
         n_sms = torch.cuda.get_device_properties(torch.device(device)).multi_processor_count
         candidates = CANDIDATES_AC if int(params.variant) == 1 else candidates_for(views, n_sms)
     cands = candidates
-    G = means.shape[0]
+    G = int(np.asarray(obj_offsets)[-1])
     out = dict(means=torch.empty(G, 3, device=device), chol=torch.empty(G, 6, device=device),
                weights=torch.empty(G, device=device),
-               poses=torch.empty(poses.shape[0], 12, device=device) if want_pose else None)
+               poses=torch.empty(int(n_poses), 12, device=device) if want_pose else None)
     timings = []
     for c in cands:
         p = apply(params, c)

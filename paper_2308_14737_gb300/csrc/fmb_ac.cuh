@@ -304,6 +304,9 @@ __device__ __forceinline__ void ac_store_order(unsigned char* row, const unsigne
 }
 // The stored order as start keys for ac_render_ray's refinement (Gaussian index in
 // the low word; the high word is filled in there from the recomputed depths).
+// Indices are masked to the warp's 32 M scratch entries: a no-op for an order a
+// forward of the same batch stored (indices below K <= 32 M), and it keeps the
+// shared-memory reads inside the warp's slice for any other bytes.
 template <int M>
 __device__ __forceinline__ void ac_load_order(const unsigned char* __restrict__ row, int K, int lane,
                                               unsigned long long (&key)[M]) {
@@ -313,7 +316,7 @@ __device__ __forceinline__ void ac_load_order(const unsigned char* __restrict__ 
   if (M == 4) w = __ldg(reinterpret_cast<const unsigned*>(src));
   if (M == 8) w = __ldg(reinterpret_cast<const unsigned long long*>(src));
 #pragma unroll
-  for (int m = 0; m < M; ++m) key[m] = lane * M + m < K ? (w >> (8 * m)) & 0xffu : kNoKey;
+  for (int m = 0; m < M; ++m) key[m] = lane * M + m < K ? (w >> (8 * m)) & (32u * M - 1u) & 0xffu : kNoKey;
 }
 
 // Stages a view's K records into shared memory with one bulk copy; every thread

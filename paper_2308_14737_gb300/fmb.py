@@ -171,6 +171,57 @@ def _check(status):
         raise FmbError(status, load_library().fmb_last_error().decode())
 
 
+# The C ABI takes plain pointers and trusts the caller for every buffer's size, so
+# the binding checks each tensor against the batch layout before the call: G, the
+# Gaussians (the last object offset); P, the plane entries the views address
+# (largest pix_offset + entries); the pose count is the poses tensor's size / 12,
+# whatever its shape (a flattened [12 n_poses] tensor is as good as [n_poses][12]).
+
+def _extent(o, va) -> tuple[int, int]:
+    G = int(o[-1]) if len(o) else 0
+    P = 0
+    for a in va:
+        P = max(P, int(a.pix_offset) + (int(a.n_rays) if a.rays else int(a.W) * int(a.H)))
+    return G, P
+
+
+def _n_poses(poses) -> int:
+    n = int(poses.numel()) if isinstance(poses, torch.Tensor) else 0
+    if n == 0 or n % 12:
+        raise ValueError(f"poses: 12 floats per camera expected, got {n} floats")
+    return n // 12
+
+
+def _need(**sized):
+    """sized: name=(tensor or None, elements the call reads or writes)."""
+    for name, (t, n) in sized.items():
+        if isinstance(t, torch.Tensor) and t.numel() < n:
+            raise ValueError(f"{name}: {t.numel()} elements, the batch needs {n}")
+
+
+# Elements per Gaussian and per plane entry of the named buffers.
+_PER_GAUSSIAN = dict(means=3, chol=6, weights=1, colors=3, grad_means=3, grad_chol=6, grad_weights=1,
+                     grad_colors=3, attribution=1)
+_PER_ENTRY = dict(depth=1, alpha=1, normal=3, color=3, saved=3, g_depth=1, g_alpha=1, g_normal=3, g_color=3,
+                  points=3, normal_tf=3, normal_screen=3, quality=1, ray_loss=1)
+
+
+def _check_scene(o, va, params, means=None, chol=None, weights=None, colors=None, **planes):
+    """Checks the scene tensors and the named per-Gaussian or per-entry buffers
+    (``flow`` and ``g_flow``: 2 n_flow per entry) against the batch layout."""
+    G, P = _extent(o, va)
+    nf = int(params.n_flow)
+    sized = dict(means=(means, 3 * G), chol=(chol, 6 * G), weights=(weights, G), colors=(colors, 3 * G))
+    for k, t in planes.items():
+        if k in ("flow", "g_flow"):
+            sized[k] = (t, 2 * nf * P)
+        elif k in _PER_GAUSSIAN:
+            sized[k] = (t, _PER_GAUSSIAN[k] * G)
+        else:
+            sized[k] = (t, _PER_ENTRY[k] * P)
+    _need(**sized)
+
+
 def fmb_workspace_bytes(params: FmbParams, obj_offsets, views) -> int:
     L = load_library()
     o, op = _offsets(obj_offsets)
@@ -208,8 +259,11 @@ def fmb_render_forward(params, obj_offsets, means, chol, weights, poses, views, 
     L = load_library()
     o, op = _offsets(obj_offsets)
     va = views if isinstance(views, ctypes.Array) else make_views(views)
+    n_poses = _n_poses(poses)
+    _check_scene(o, va, params, means, chol, weights, colors, depth=depth, alpha=alpha, normal=normal, flow=flow,
+                 color=color, saved=saved)
     _check(L.fmb_render_forward(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol), _ptr(weights),
-                                _ptr(colors), int(poses.shape[0]), _ptr(poses), len(va), va, _ptr(depth),
+                                _ptr(colors), n_poses, _ptr(poses), len(va), va, _ptr(depth),
                                 _ptr(alpha), _ptr(normal), _ptr(flow), _ptr(color), _ptr(saved), _ptr(workspace),
                                 workspace.numel(), _stream(stream)))
 
@@ -221,8 +275,11 @@ def fmb_render_forward_noalloc(params, obj_offsets, means, chol, weights, poses,
     L = load_library()
     o, op = _offsets(obj_offsets)
     va = views if isinstance(views, ctypes.Array) else make_views(views)
+    n_poses = _n_poses(poses)
+    _check_scene(o, va, params, means, chol, weights, colors, depth=depth, alpha=alpha, normal=normal, flow=flow,
+                 color=color, saved=saved)
     _check(L.fmb_render_forward_noalloc(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol),
-                                        _ptr(weights), _ptr(colors), int(poses.shape[0]), _ptr(poses), len(va), va,
+                                        _ptr(weights), _ptr(colors), n_poses, _ptr(poses), len(va), va,
                                         _ptr(depth), _ptr(alpha), _ptr(normal), _ptr(flow), _ptr(color), _ptr(saved),
                                         _stream(stream)))
 
@@ -241,8 +298,11 @@ def fmb_render_points(params, obj_offsets, means, chol, weights, poses, views, d
     L = load_library()
     o, op = _offsets(obj_offsets)
     va = views if isinstance(views, ctypes.Array) else make_views(views)
+    n_poses = _n_poses(poses)
+    _check_scene(o, va, params, means, chol, weights, depth=depth, saved=saved, points=points, normal_tf=normal_tf,
+                 normal_screen=normal_screen, quality=quality)
     _check(L.fmb_render_points(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol), _ptr(weights),
-                               int(poses.shape[0]), _ptr(poses), len(va), va, _ptr(depth), _ptr(saved), _ptr(points),
+                               n_poses, _ptr(poses), len(va), va, _ptr(depth), _ptr(saved), _ptr(points),
                                _ptr(normal_tf), _ptr(normal_screen), _ptr(quality), _ptr(workspace),
                                workspace.numel(), _stream(stream)))
 
@@ -252,8 +312,10 @@ def fmb_loss_attribution(params, obj_offsets, means, chol, weights, poses, views
     L = load_library()
     o, op = _offsets(obj_offsets)
     va = views if isinstance(views, ctypes.Array) else make_views(views)
+    n_poses = _n_poses(poses)
+    _check_scene(o, va, params, means, chol, weights, saved=saved, ray_loss=ray_loss, attribution=attribution)
     _check(L.fmb_loss_attribution(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol), _ptr(weights),
-                                  int(poses.shape[0]), _ptr(poses), len(va), va, _ptr(saved), _ptr(ray_loss),
+                                  n_poses, _ptr(poses), len(va), va, _ptr(saved), _ptr(ray_loss),
                                   _ptr(attribution), _ptr(workspace), workspace.numel(), _stream(stream)))
 
 
@@ -263,8 +325,13 @@ def fmb_render_backward(params, obj_offsets, means, chol, weights, poses, views,
     L = load_library()
     o, op = _offsets(obj_offsets)
     va = views if isinstance(views, ctypes.Array) else make_views(views)
+    n_poses = _n_poses(poses)
+    _check_scene(o, va, params, means, chol, weights, colors, depth=depth, normal=normal, color=color, saved=saved,
+                 g_depth=g_depth, g_alpha=g_alpha, g_normal=g_normal, g_flow=g_flow, g_color=g_color,
+                 grad_means=grad_means, grad_chol=grad_chol, grad_weights=grad_weights, grad_colors=grad_colors)
+    _need(grad_poses=(grad_poses, 12 * n_poses))
     _check(L.fmb_render_backward(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol), _ptr(weights),
-                                 _ptr(colors), int(poses.shape[0]), _ptr(poses), len(va), va, _ptr(depth),
+                                 _ptr(colors), n_poses, _ptr(poses), len(va), va, _ptr(depth),
                                  _ptr(normal), _ptr(color), _ptr(saved), _ptr(g_depth), _ptr(g_alpha),
                                  _ptr(g_normal), _ptr(g_flow), _ptr(g_color), _ptr(grad_means), _ptr(grad_chol),
                                  _ptr(grad_weights), _ptr(grad_colors), _ptr(grad_poses), _ptr(workspace),
@@ -310,7 +377,8 @@ class Renderer:
                      for v in self.views]  # kept alive: the views point at them
         self.c_views = make_views(self.views, self.rays)
         self.n_poses = int(n_poses)
-        self.P = int(sum(view_entries(v) for v in self.views))
+        self.P = max(int(v["pix_offset"]) + view_entries(v) for v in self.views) if self.views else 0
+        self.G = int(self.obj_offsets[-1])
         self.device = device
         self.ws = alloc_workspace(fmb_workspace_bytes(self.params, self.obj_offsets, self.c_views), device)
         planes = self.new_planes()
@@ -356,7 +424,7 @@ class Renderer:
         """Sec. 8 loss attribution of the batch's rays (after a forward call of the
         same batch): per Gaussian, the sum of ray_loss times its normalised weight."""
         if out is None:
-            out = torch.empty(means.shape[0], dtype=torch.float32, device=means.device)
+            out = torch.empty(self.G, dtype=torch.float32, device=means.device)
         fmb_loss_attribution(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, self.saved,
                              ray_loss, out, self.ws, stream)
         return out
@@ -365,13 +433,13 @@ class Renderer:
                  out=None, stream=None, colors=None, g_color=None, planes=None):
         """Gradients of the forward call whose planes are ``planes`` (default: the
         renderer's own, i.e. its last forward call into them)."""
-        G = means.shape[0]
+        G = self.G
         pl = planes if planes is not None else dict(depth=self.depth, normal=self.normal, saved=self.saved,
                                                     color=self.color)
         if out is None:
             f32 = dict(dtype=torch.float32, device=means.device)
             out = dict(means=torch.empty(G, 3, **f32), chol=torch.empty(G, 6, **f32), weights=torch.empty(G, **f32),
-                       poses=torch.empty(poses.shape[0], 12, **f32) if want_pose else None)
+                       poses=torch.empty(_n_poses(poses), 12, **f32) if want_pose else None)
             if self.params.colors:
                 out["colors"] = torch.empty(G, 3, **f32)
         fmb_render_backward(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, pl["depth"],

@@ -268,3 +268,65 @@ def test_keep_order_workspace_and_validation(fmb):
     st = L.fmb_render_forward_noalloc(ctypes.byref(pk), 1, o.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), fp,
                                       fp, fp, fp, 1, fp, 1, fmb.make_views([_view()]), fp, fp, fp, fp, fp, fp, None)
     assert st == 1 and "keep_order" in L.fmb_last_error().decode()
+
+
+def _host_call_args(s, fmb, n_flow=1):
+    """Host tensors of the right sizes for fmb_render_forward / backward on scene s
+    (the binding checks sizes before it requires device memory)."""
+    import torch
+
+    G, P = int(s.obj_offsets[-1]), int(s.n_pixels)
+    z = lambda n: torch.zeros(n, dtype=torch.float32)
+    fwd = dict(means=z(3 * G), chol=z(6 * G), weights=z(G), poses=torch.as_tensor(s.poses, dtype=torch.float32),
+               depth=z(P), alpha=z(P), normal=z(3 * P), flow=z(2 * n_flow * P), saved=z(3 * P))
+    bwd = dict(g_depth=z(P), g_alpha=z(P), g_normal=z(3 * P), g_flow=z(2 * n_flow * P), grad_means=z(3 * G),
+               grad_chol=z(6 * G), grad_weights=z(G), grad_poses=z(12 * len(s.poses)))
+    return fwd, bwd
+
+
+def _call_backward(fmb, s, p, f, b):
+    ws = None  # no device: the size checks run before any pointer is taken
+    fmb.fmb_render_backward(p, s.obj_offsets, f["means"], f["chol"], f["weights"], f["poses"], s.views,
+                            f["depth"], f["normal"], f["saved"], b["g_depth"], b["g_alpha"], b["g_normal"],
+                            b["g_flow"], b["grad_means"], b["grad_chol"], b["grad_weights"], b["grad_poses"], ws)
+
+
+@pytest.mark.parametrize("short", ["means", "chol", "weights", "depth", "normal", "saved", "g_depth", "g_alpha",
+                                   "g_normal", "g_flow", "grad_means", "grad_chol", "grad_weights", "grad_poses"])
+def test_binding_rejects_short_buffers(fmb, short):
+    # The C ABI takes plain pointers; the binding checks every tensor's size against
+    # the batch layout (G Gaussians, P plane entries, n_poses = poses' size / 12).
+    s = synth.object_orbit(K=10, n_views=3, W=8, H=6)
+    p = fmb.default_params(n_flow=1)
+    f, b = _host_call_args(s, fmb)
+    d = f if short in f else b
+    d[short] = d[short][:-1]
+    with pytest.raises(ValueError, match=short):
+        _call_backward(fmb, s, p, f, b)
+
+
+def test_binding_pose_count_from_size(fmb):
+    # a flattened [12 n_poses] poses tensor is n_poses cameras (its first dimension
+    # is not the count): it passes the size checks, and so does a grad_poses of
+    # exactly 12 n_poses floats; a size that is not a multiple of 12 is refused
+    s = synth.object_orbit(K=10, n_views=3, W=8, H=6)
+    p = fmb.default_params(n_flow=1)
+    f, b = _host_call_args(s, fmb)
+    f["poses"] = f["poses"].reshape(-1)
+    with pytest.raises(ValueError, match="device tensors expected"):  # past the size checks
+        _call_backward(fmb, s, p, f, b)
+    f["poses"] = f["poses"][:-1]
+    with pytest.raises(ValueError, match="12 floats per camera"):
+        _call_backward(fmb, s, p, f, b)
+
+
+def test_binding_forward_checks_planes(fmb):
+    s = synth.object_orbit(K=10, n_views=3, W=8, H=6)
+    p = fmb.default_params(n_flow=1)
+    f, _ = _host_call_args(s, fmb)
+    for k in ("depth", "alpha", "normal", "flow", "saved"):
+        g = dict(f)
+        g[k] = g[k][:-1]
+        with pytest.raises(ValueError, match=k):
+            fmb.fmb_render_forward(p, s.obj_offsets, g["means"], g["chol"], g["weights"], g["poses"], s.views,
+                                   g["depth"], g["alpha"], g["normal"], g["flow"], g["saved"], None)

@@ -21,11 +21,38 @@ def _lib():
     fmb.load_library()
 
 
-@pytest.mark.parametrize("variant", [0, 1])
-def test_host_pipeline_matches_plain_calls(variant):
-    s = synth.object_orbit(K=60, n_views=4, W=64, H=48)
+def _plain(s, params, st):
+    """Planes and gradients of one plain device-resident forward + backward."""
+    r = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), params)
+    d = {k: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float32, device="cuda") for k, v in st.items()}
+    out = r.forward(d["means"], d["chol"], d["weights"], d["poses"])
+    g = r.backward(d["means"], d["chol"], d["weights"], d["poses"], d["g_depth"], d["g_alpha"], d["g_normal"],
+                   d["g_flow"], want_pose=True)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in
+            dict(depth=out["depth"], alpha=out["alpha"], normal=out["normal"], flow=out["flow"],
+                 grad_means=g["means"], grad_chol=g["chol"], grad_weights=g["weights"],
+                 grad_poses=g["poses"]).items()}
+
+
+def _same(got, want, deterministic, what):
+    for k, b in want.items():
+        a = np.asarray(got[k]).reshape(b.shape)
+        if k.startswith("grad") and not deterministic:
+            # sums of fp32 atomics (order-dependent): equal up to rounding
+            assert np.allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max()), (what, k)
+        else:
+            assert np.array_equal(a, b), (what, k)
+
+
+# variant 1 at K = 100: four keys per lane, so the per-ray sort runs the
+# refinement from the neighbouring ray's (or, with keep_order, the forward's) order
+@pytest.mark.parametrize("variant,keep_order,deterministic,K", [(0, 0, 0, 60), (0, 0, 1, 60), (1, 0, 1, 60),
+                                                                (1, 0, 1, 100), (1, 1, 1, 100), (1, 1, 0, 100)])
+def test_host_pipeline_matches_plain_calls(variant, keep_order, deterministic, K):
+    s = synth.object_orbit(K=K, n_views=4, W=64, H=48)
     n_flow = 1
-    params = fmb.default_params(n_flow=n_flow, variant=variant)
+    params = fmb.default_params(n_flow=n_flow, variant=variant, keep_order=keep_order, deterministic=deterministic)
     P = s.n_pixels
     rng = np.random.default_rng(3)
     steps = []
@@ -36,7 +63,15 @@ def test_host_pipeline_matches_plain_calls(variant):
                           g_alpha=ups[1], g_normal=ups[2].reshape(-1), g_flow=ups[3].reshape(-1)))
     pin = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).pin_memory()
     h_in = [{k: pin(v) for k, v in st.items()} for st in steps]
+    want = [_plain(s, params, st) for st in steps]
+
     pipe = pipeline.HostPipeline(s.obj_offsets, s.views, len(s.poses), params, h_in[0], want_pose=True)
+    # each buffer set's captured graph, replayed on the set-up inputs as they are
+    for j, sl in enumerate(pipe.slots):
+        sl["graph"].replay()
+        torch.cuda.synchronize()
+        _same({k: v.cpu().numpy() for k, v in pipe.outputs(sl).items()}, want[0], deterministic, f"slot {j}")
+
     h_out = [pipe.host_outputs() for _ in steps]
     events = [pipe.submit(h_in[i], h_out[i]) for i in range(2)]
     events[0].synchronize()
@@ -44,20 +79,5 @@ def test_host_pipeline_matches_plain_calls(variant):
         events[i - 2].synchronize()
         events.append(pipe.submit(h_in[i], h_out[i]))
     torch.cuda.synchronize()
-
-    r = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), params)
-    for i, st in enumerate(steps):
-        d = {k: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float32, device="cuda") for k, v in st.items()}
-        out = r.forward(d["means"], d["chol"], d["weights"], d["poses"])
-        g = r.backward(d["means"], d["chol"], d["weights"], d["poses"], d["g_depth"], d["g_alpha"], d["g_normal"],
-                       d["g_flow"], want_pose=True)
-        torch.cuda.synchronize()
-        want = dict(depth=out["depth"], alpha=out["alpha"], normal=out["normal"], flow=out["flow"],
-                    grad_means=g["means"], grad_chol=g["chol"], grad_weights=g["weights"], grad_poses=g["poses"])
-        for k, v in want.items():
-            a, b = h_out[i][k].numpy(), v.cpu().numpy()
-            # the gradients are sums of fp32 atomics (order-dependent): equal up to rounding
-            if k.startswith("grad"):
-                assert np.allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max()), (i, k)
-            else:
-                assert np.array_equal(a, b), (i, k)
+    for i in range(len(steps)):
+        _same({k: v.numpy() for k, v in h_out[i].items()}, want[i], deterministic, f"step {i}")
