@@ -107,9 +107,22 @@ def tune(obj_offsets, views, n_poses, params: fmb.FmbParams, means, chol, weight
             r = fmb.Renderer(obj_offsets, views, n_poses, p, device=device)
         except fmb.FmbError:
             continue
-        step = lambda: (r.forward(means, chol, weights, poses),
-                        r.backward(means, chol, weights, poses, upstream["g_depth"], upstream["g_alpha"],
-                                   upstream["g_normal"], upstream["g_flow"], want_pose=want_pose, out=out))
+        eager = lambda: (r.forward(means, chol, weights, poses),
+                         r.backward(means, chol, weights, poses, upstream["g_depth"], upstream["g_alpha"],
+                                    upstream["g_normal"], upstream["g_flow"], want_pose=want_pose, out=out))
+        # Each candidate is timed as the batched path runs it: forward + backward
+        # captured in one CUDA graph and replayed, so that the host's per-call cost
+        # (which decides eager timings of small batches) does not choose the tiles.
+        side = torch.cuda.Stream(device)
+        side.wait_stream(torch.cuda.current_stream(device))
+        with torch.cuda.stream(side):
+            eager()  # lazy set-up happens outside the capture
+        torch.cuda.current_stream(device).wait_stream(side)
+        torch.cuda.synchronize(device)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            eager()
+        step = graph.replay
         step()
         torch.cuda.synchronize(device)
         # short steps (a few hundred microseconds or less) are timed over more
@@ -132,7 +145,7 @@ def tune(obj_offsets, views, n_poses, params: fmb.FmbParams, means, chol, weight
             ms = e0.elapsed_time(e1) / n_rep
             best_ms = ms if best_ms is None else min(best_ms, ms)
         timings.append(dict(choice=c, ms=best_ms))
-        del r
+        del graph, r
     if not timings:
         raise RuntimeError("no autotune candidate could be run")
     best = min(timings, key=lambda x: x["ms"])

@@ -206,10 +206,11 @@ _PER_ENTRY = dict(depth=1, alpha=1, normal=3, color=3, saved=3, g_depth=1, g_alp
                   points=3, normal_tf=3, normal_screen=3, quality=1, ray_loss=1)
 
 
-def _check_scene(o, va, params, means=None, chol=None, weights=None, colors=None, **planes):
+def _check_scene(o, va, params, means=None, chol=None, weights=None, colors=None, extent=None, **planes):
     """Checks the scene tensors and the named per-Gaussian or per-entry buffers
-    (``flow`` and ``g_flow``: 2 n_flow per entry) against the batch layout."""
-    G, P = _extent(o, va)
+    (``flow`` and ``g_flow``: 2 n_flow per entry) against the batch layout;
+    ``extent``: its (G, P) when the caller has them (else computed from the views)."""
+    G, P = extent if extent is not None else _extent(o, va)
     nf = int(params.n_flow)
     sized = dict(means=(means, 3 * G), chol=(chol, 6 * G), weights=(weights, G), colors=(colors, 3 * G))
     for k, t in planes.items():
@@ -255,13 +256,13 @@ def fmb_launch_count(params: FmbParams, obj_offsets, views, backward: bool, want
 
 
 def fmb_render_forward(params, obj_offsets, means, chol, weights, poses, views, depth, alpha, normal, flow, saved,
-                       workspace, stream=None, colors=None, color=None):
+                       workspace, stream=None, colors=None, color=None, extent=None):
     L = load_library()
     o, op = _offsets(obj_offsets)
     va = views if isinstance(views, ctypes.Array) else make_views(views)
     n_poses = _n_poses(poses)
-    _check_scene(o, va, params, means, chol, weights, colors, depth=depth, alpha=alpha, normal=normal, flow=flow,
-                 color=color, saved=saved)
+    _check_scene(o, va, params, means, chol, weights, colors, extent, depth=depth, alpha=alpha, normal=normal,
+                 flow=flow, color=color, saved=saved)
     _check(L.fmb_render_forward(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol), _ptr(weights),
                                 _ptr(colors), n_poses, _ptr(poses), len(va), va, _ptr(depth),
                                 _ptr(alpha), _ptr(normal), _ptr(flow), _ptr(color), _ptr(saved), _ptr(workspace),
@@ -269,15 +270,15 @@ def fmb_render_forward(params, obj_offsets, means, chol, weights, poses, views, 
 
 
 def fmb_render_forward_noalloc(params, obj_offsets, means, chol, weights, poses, views, depth, alpha, normal, flow,
-                               saved, stream=None, colors=None, color=None):
+                               saved, stream=None, colors=None, color=None, extent=None):
     """fmb_render_forward with the library's fixed scratch instead of a workspace
     (for callers that cannot allocate device memory)."""
     L = load_library()
     o, op = _offsets(obj_offsets)
     va = views if isinstance(views, ctypes.Array) else make_views(views)
     n_poses = _n_poses(poses)
-    _check_scene(o, va, params, means, chol, weights, colors, depth=depth, alpha=alpha, normal=normal, flow=flow,
-                 color=color, saved=saved)
+    _check_scene(o, va, params, means, chol, weights, colors, extent, depth=depth, alpha=alpha, normal=normal,
+                 flow=flow, color=color, saved=saved)
     _check(L.fmb_render_forward_noalloc(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol),
                                         _ptr(weights), _ptr(colors), n_poses, _ptr(poses), len(va), va,
                                         _ptr(depth), _ptr(alpha), _ptr(normal), _ptr(flow), _ptr(color), _ptr(saved),
@@ -294,13 +295,13 @@ def fmb_read_noalloc_status(stream=None) -> int:
 
 
 def fmb_render_points(params, obj_offsets, means, chol, weights, poses, views, depth, saved, points, normal_tf,
-                      normal_screen, quality, workspace, stream=None):
+                      normal_screen, quality, workspace, stream=None, extent=None):
     L = load_library()
     o, op = _offsets(obj_offsets)
     va = views if isinstance(views, ctypes.Array) else make_views(views)
     n_poses = _n_poses(poses)
-    _check_scene(o, va, params, means, chol, weights, depth=depth, saved=saved, points=points, normal_tf=normal_tf,
-                 normal_screen=normal_screen, quality=quality)
+    _check_scene(o, va, params, means, chol, weights, None, extent, depth=depth, saved=saved, points=points,
+                 normal_tf=normal_tf, normal_screen=normal_screen, quality=quality)
     _check(L.fmb_render_points(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol), _ptr(weights),
                                n_poses, _ptr(poses), len(va), va, _ptr(depth), _ptr(saved), _ptr(points),
                                _ptr(normal_tf), _ptr(normal_screen), _ptr(quality), _ptr(workspace),
@@ -308,12 +309,13 @@ def fmb_render_points(params, obj_offsets, means, chol, weights, poses, views, d
 
 
 def fmb_loss_attribution(params, obj_offsets, means, chol, weights, poses, views, saved, ray_loss, attribution,
-                         workspace, stream=None):
+                         workspace, stream=None, extent=None):
     L = load_library()
     o, op = _offsets(obj_offsets)
     va = views if isinstance(views, ctypes.Array) else make_views(views)
     n_poses = _n_poses(poses)
-    _check_scene(o, va, params, means, chol, weights, saved=saved, ray_loss=ray_loss, attribution=attribution)
+    _check_scene(o, va, params, means, chol, weights, None, extent, saved=saved, ray_loss=ray_loss,
+                 attribution=attribution)
     _check(L.fmb_loss_attribution(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol), _ptr(weights),
                                   n_poses, _ptr(poses), len(va), va, _ptr(saved), _ptr(ray_loss),
                                   _ptr(attribution), _ptr(workspace), workspace.numel(), _stream(stream)))
@@ -321,13 +323,13 @@ def fmb_loss_attribution(params, obj_offsets, means, chol, weights, poses, views
 
 def fmb_render_backward(params, obj_offsets, means, chol, weights, poses, views, depth, normal, saved, g_depth,
                         g_alpha, g_normal, g_flow, grad_means, grad_chol, grad_weights, grad_poses, workspace,
-                        stream=None, colors=None, color=None, g_color=None, grad_colors=None):
+                        stream=None, colors=None, color=None, g_color=None, grad_colors=None, extent=None):
     L = load_library()
     o, op = _offsets(obj_offsets)
     va = views if isinstance(views, ctypes.Array) else make_views(views)
     n_poses = _n_poses(poses)
-    _check_scene(o, va, params, means, chol, weights, colors, depth=depth, normal=normal, color=color, saved=saved,
-                 g_depth=g_depth, g_alpha=g_alpha, g_normal=g_normal, g_flow=g_flow, g_color=g_color,
+    _check_scene(o, va, params, means, chol, weights, colors, extent, depth=depth, normal=normal, color=color,
+                 saved=saved, g_depth=g_depth, g_alpha=g_alpha, g_normal=g_normal, g_flow=g_flow, g_color=g_color,
                  grad_means=grad_means, grad_chol=grad_chol, grad_weights=grad_weights, grad_colors=grad_colors)
     _need(grad_poses=(grad_poses, 12 * n_poses))
     _check(L.fmb_render_backward(ctypes.byref(params), len(o) - 1, op, _ptr(means), _ptr(chol), _ptr(weights),
@@ -405,7 +407,7 @@ class Renderer:
                        color=self.color)
         fmb_render_forward(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, out["depth"],
                            out["alpha"], out["normal"], out["flow"], out["saved"], self.ws, stream, colors=colors,
-                           color=out["color"])
+                           color=out["color"], extent=(self.G, self.P))
         return out
 
     def points(self, means, chol, weights, poses, stream=None):
@@ -417,7 +419,7 @@ class Renderer:
                    normal_screen=torch.empty(3 * self.P, **f32), quality=torch.empty(self.P, **f32))
         fmb_render_points(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, self.depth,
                           self.saved, out["points"], out["normal_tf"], out["normal_screen"], out["quality"], self.ws,
-                          stream)
+                          stream, extent=(self.G, self.P))
         return out
 
     def attribution(self, means, chol, weights, poses, ray_loss, out=None, stream=None):
@@ -426,7 +428,7 @@ class Renderer:
         if out is None:
             out = torch.empty(self.G, dtype=torch.float32, device=means.device)
         fmb_loss_attribution(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, self.saved,
-                             ray_loss, out, self.ws, stream)
+                             ray_loss, out, self.ws, stream, extent=(self.G, self.P))
         return out
 
     def backward(self, means, chol, weights, poses, g_depth, g_alpha, g_normal, g_flow, want_pose=True,
@@ -445,7 +447,7 @@ class Renderer:
         fmb_render_backward(self.params, self.obj_offsets, means, chol, weights, poses, self.c_views, pl["depth"],
                             pl["normal"], pl["saved"], g_depth, g_alpha, g_normal, g_flow, out["means"], out["chol"],
                             out["weights"], out["poses"], self.ws, stream, colors=colors, color=pl["color"],
-                            g_color=g_color, grad_colors=out.get("colors"))
+                            g_color=g_color, grad_colors=out.get("colors"), extent=(self.G, self.P))
         return out
 
 
