@@ -739,7 +739,9 @@ def e2e_measure(args, name, s, ups, params, dev):
     for i in range(4):
         pipe.submit(h_in, h_outs[i % 2])
     torch.cuda.synchronize(dev)
-    n = max(args.steps // 4, 5)
+    # at least 20 steps: the pipeline's fill (the first step's inputs in) and drain
+    # (the last step's results out) are paid once per timed run, as in a training loop
+    n = max(args.steps, 20)
     cur = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(cur)
@@ -771,7 +773,7 @@ def e2e_measure(args, name, s, ups, params, dev):
         if not ok:
             raise RuntimeError(f"host-fed pipeline result {k} differs from the plain call's")
     return {"value": s.n_pairs / (ms * 1e-3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": ms,
+            "d2h_bytes_per_step": d2h, "ms_per_step": ms, "steps": n,
             "parity": "last step's host results vs a plain device call: planes bitwise, gradients within 1e-5 "
                       "of the largest entry",
             "api": "pipeline.HostPipeline: two device buffer sets; each step's host->device copies, forward + "
