@@ -288,8 +288,9 @@ def workload_config(s, wl, variant="two-param"):
 
 def measure_workload(args, name, steps, warmup, dev, ws=1, extras=True, cpu=True):
     """Measures one configuration: the batched arm (one call per pass for all
-    views, autotuned tiles, each pass replayed from a CUDA graph) timed per step
-    with CUDA events, the plain arm (one forward and one backward call per view),
+    views, autotuned tiles, the step's two calls replayed from one CUDA graph; each
+    call also from a graph of its own for the forward / backward split) timed per
+    step with CUDA events, the plain arm (one forward and one backward call per view),
     the host-fed end-to-end rate, the roofline fractions and, with ``cpu``, the
     oracle on a bounded sample with the parity of the GPU result there.  Returns a
     dict (rates are this rank's; the caller aggregates over ranks)."""
@@ -353,7 +354,12 @@ def measure_workload(args, name, steps, warmup, dev, ws=1, extras=True, cpu=True
             batched.forward(means, chol, weights, poses)
             batched.backward(means, chol, weights, poses, gd, ga, gn, gf, want_pose=want_pose, out=grads)
     torch.cuda.current_stream(dev).wait_stream(side)
-    graph_f, graph_b = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    # the step (forward and backward) as one graph, as a training loop replays it; each
+    # call in a graph of its own for the forward / backward split
+    graph_s, graph_f, graph_b = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph_s):
+        batched.forward(means, chol, weights, poses)
+        batched.backward(means, chol, weights, poses, gd, ga, gn, gf, want_pose=want_pose, out=grads)
     with torch.cuda.graph(graph_f):
         batched.forward(means, chol, weights, poses)
     with torch.cuda.graph(graph_b):
@@ -415,7 +421,8 @@ def measure_workload(args, name, steps, warmup, dev, ws=1, extras=True, cpu=True
         return tot, fwd, bwd
 
     with ClockSampler(dev.index if dev.index is not None else 0) as clk:
-        t_b, t_f, t_bw = timed(None, steps, warmup, split=True)
+        t_b, _, _ = timed(graph_s.replay, steps, warmup)
+        _, t_f, t_bw = timed(None, steps, warmup, split=True)
     clocks = clk.summary()
     plain_steps = max(steps // 4, 3)
     t_p, _, _ = timed(plain_step, plain_steps, max(warmup, 3))
@@ -497,8 +504,8 @@ def measure_workload(args, name, steps, warmup, dev, ws=1, extras=True, cpu=True
                   "launch": "one forward and one backward call per view, default tiles, no graph"},
         "batched_over_plain": ms_plain / ms_step,
         "frames_per_s": ws * len(s.views) / (ms_step * 1e-3),
-        "launch": {"batched": "one forward and one backward call for all views, autotuned tiles, each pass "
-                              "replayed from a CUDA graph",
+        "launch": {"batched": "one forward and one backward call for all views, autotuned tiles, the step "
+                              "replayed from one CUDA graph (fwd_ms / bwd_ms: each call from a graph of its own)",
                    "tiles": {k: int(getattr(tuned_params, k)) for k in autotune.TUNED_FIELDS},
                    "fwd_ksplit": ksplit, "kernel_launches_per_step": launches},
         "roofline": roofline,
@@ -524,7 +531,7 @@ def measure_workload(args, name, steps, warmup, dev, ws=1, extras=True, cpu=True
         rec["plain_vs_batched_grad_max_rel"] = {
             k: float((psum[k] - grads[k]).abs().max() / grads[k].abs().max()) for k in psum}
         rec["cpu_baseline"] = cpu_baseline(name, s, batched, (means, chol, weights, poses), want_pose, args)
-    del plain, pgrads, graph_f, graph_b, batched, flush
+    del plain, pgrads, graph_s, graph_f, graph_b, batched, flush
     torch.cuda.synchronize(dev)
     torch.cuda.empty_cache()
     return rec

@@ -462,7 +462,11 @@ class FmbRender(torch.autograd.Function):
     renderer's params do not produce are returned as empty tensors.  Pose gradients
     are computed only when ``poses`` requires a gradient.  The backward may run
     more than once (``retain_graph``): each run recomputes from the saved planes.
-    Inside ``torch.cuda.graph`` the planes come from the graph's memory pool."""
+    Inside ``torch.cuda.graph`` the planes come from the graph's memory pool.  With
+    ``keep_order`` (alpha compositing) the depth order lives in the renderer's
+    workspace, which the last forward wrote: an earlier render's backward refines from
+    that order instead of its own, which takes more passes but reaches the same sorted
+    keys (any permutation of a view's Gaussians refines to them)."""
 
     @staticmethod
     def forward(ctx, renderer: Renderer, means, chol, weights, poses, colors=None):

@@ -40,3 +40,5 @@ def test_small_batches_get_short_tile_candidates():
     for c in autotune.SMALL_CANDIDATES:
         assert c["bwd_ray_tile"] % 32 == 0 and 32 <= c["bwd_threads"] <= 160 and c["bwd_threads"] % 32 == 0
         assert c["fwd_rays_per_thread"] in (1, 2, 4)
+        # a Gaussian split runs only with packed (even) rays per thread
+        assert c.get("fwd_ksplit", 0) in (0, 2, 4) and (c.get("fwd_ksplit", 0) == 0 or c["fwd_rays_per_thread"] == 2)

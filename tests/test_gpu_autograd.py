@@ -83,19 +83,26 @@ def test_fmbrender_forward_and_gradients_match_oracle(pose_grad, deterministic):
             torch.testing.assert_close(g1, g2, rtol=0, atol=1e-6 * float(g1.abs().max()))
 
 
-def test_fmbrender_two_renders_alive_in_one_graph():
+@pytest.mark.parametrize("variant,keep_order", [(0, 0), (1, 0), (1, 1)])
+def test_fmbrender_two_renders_alive_in_one_graph(variant, keep_order):
     """Two calls on one renderer keep their own planes: the gradient of a functional
-    of the first render, taken after the second render ran, is the first render's."""
+    of the first render, taken after the second render ran, is the first render's.
+    The second render moves the means, so (alpha compositing) its depth orders differ;
+    with keep_order the first render's backward starts from the second's stored order
+    and must still reach the same gradients bit for bit."""
     s = synth.object_orbit(K=40, n_views=2, W=32, H=24)
-    params = fmb.default_params(n_flow=1, want_normals=1, deterministic=1)
+    params = fmb.default_params(n_flow=1, want_normals=1, deterministic=1, variant=variant, keep_order=keep_order)
     r = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), params)
     means, chol, weights, poses = _leaves(s)
     ref = oracle.render_scene(s, n_flow=1)
     ups = masked_upstream(s, ref["alpha"], 1, seed=9, nnorm_ref=nnorm_batched(s, ref["saved"]))
     alone = torch.autograd.grad(_functional(fmb.render(r, means, chol, weights, poses), ups),
                                 [means, chol, weights, poses])
+    shift = torch.as_tensor(np.random.default_rng(4).normal(0.0, 0.2, s.means.shape).astype(np.float32),
+                            device="cuda")
     pa = fmb.render(r, means, chol, weights, poses)
-    pb = fmb.render(r, means, chol, weights * 1.5, poses)  # overwrites the renderer's workspace records
+    # overwrites the renderer's workspace (records, and with keep_order the depth orders)
+    pb = fmb.render(r, means + shift, chol, weights * 1.5, poses)
     ga = torch.autograd.grad(_functional(pa, ups), [means, chol, weights, poses])
     for x, y in zip(alone, ga):
         assert torch.equal(x, y)
