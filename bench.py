@@ -87,6 +87,22 @@ LANES_PER_SM = 128
 MUFU_RATE = {"ex2": 31.8, "rcp": 16.0, "rsqrt": 16.0}
 
 
+# The paper's runtime-per-ray table (its Table 2): one whole iteration (forward,
+# backward and memory transfers) per ray with 40 Gaussians, JAX on an i5-7267U CPU and
+# a GTX 1080 GPU.  Context only: other hardware, unstated precision.
+PAPER_RUNTIME_PER_RAY = {"weighted blending": {"cpu_us": 4.94, "gpu_ns": 226.6},
+                         "alpha compositing": {"cpu_us": 12.7, "gpu_ns": 377.6}}
+PAPER_RUNTIME_GAUSSIANS = 40
+
+
+def paper_context(variant: str) -> dict:
+    name = "alpha compositing" if variant == "ac" else "weighted blending"
+    ns = PAPER_RUNTIME_PER_RAY[name]["gpu_ns"]
+    return {"what": "Table 2: whole iteration (forward, backward, memory transfers) per ray, 40 Gaussians, JAX; "
+                    "other hardware, context only",
+            "gtx1080_ns_per_ray": ns, "gtx1080_pairs_per_s": PAPER_RUNTIME_GAUSSIANS / (ns * 1e-9), "variant": name}
+
+
 def peak_fp32_gops(clock_mhz: float) -> float:
     """FP32-pipe peak in G lane-operations per second (152 SMs x 128 lanes x clock)."""
     return N_SM * LANES_PER_SM * clock_mhz * 1e6 / 1e9
@@ -604,11 +620,7 @@ def run_gpu(args):
         "fwd_ms": head["fwd_ms"],
         "bwd_ms": head["bwd_ms"],
         "frames_per_s": head["frames_per_s"],
-        "paper_context": {"what": "Table 1: whole iteration (forward, backward, memory transfers) per ray, 40 "
-                                  "Gaussians, JAX; other hardware, context only",
-                          "gtx1080_ns_per_ray": 226.6 if args.variant != "ac" else 377.6,
-                          "gtx1080_pairs_per_s": 40 / ((226.6 if args.variant != "ac" else 377.6) * 1e-9),
-                          "variant": "weighted blending" if args.variant != "ac" else "alpha compositing"},
+        "paper_context": paper_context(args.variant),
         "roofline": head["roofline"],
         "clocks": head["clocks"],
         # the library's own count of its launches per forward + backward call, times the timed steps
