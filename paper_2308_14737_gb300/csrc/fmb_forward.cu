@@ -274,8 +274,19 @@ __host__ __device__ constexpr int fwd_stage_float4() {
   return kChunk * (kRecFloat4 + (COLOR ? 1 : 0));
 }
 
+// Minimum resident CTAs: 7 for the plain two-rays-per-thread kernels with normals and
+// flow, whose default register allocation spills (one flow slot: 28 bytes at 72
+// registers) or stops at 5 CTAs per SM (two flow slots: 96 registers); bounded they
+// take 72 registers with 8 bytes of spill, and 70 with none (orbit forward 0.256 ->
+// 0.252 ms).  0 leaves the others to the compiler: a bound made them slower.
+template <bool NORMALS, int NFLOW, int RPT, bool STORE>
+constexpr int fwd_min_blocks() {
+  return (RPT == 2 && NORMALS && NFLOW > 0 && !STORE) ? 7 : 0;
+}
+
 template <bool NORMALS, int NFLOW, int RPT, bool STORE, bool COLOR = false>
-__global__ void __launch_bounds__(kFwdThreads) forward_kernel(const __grid_constant__ Batch batch, Scene s,
+__global__ void __launch_bounds__(kFwdThreads, COLOR ? 0 : fwd_min_blocks<NORMALS, NFLOW, RPT, STORE>())
+    forward_kernel(const __grid_constant__ Batch batch, Scene s,
                                                               Consts k, const float4* __restrict__ records,
                                                               FwdOut out, int* status, int* counter) {
   pdl_enter();
