@@ -120,7 +120,6 @@ def mufu_busy_frac(pairs_per_s: float, clock_mhz: float, normals: bool = True) -
 # the size rule for full ncu captures; its plane traffic grows with the pixels).
 PROFILES = {"orbit": os.path.join(ROOT, "profiles", "backward_kernel_orbit16x320x240_K100.md"),
             "largek": os.path.join(ROOT, "profiles", "backward_kernel_largek8x1024x768_K4096.md")}
-PROFILE = PROFILES["orbit"]
 
 
 def csrc_sha256() -> str:
