@@ -739,8 +739,12 @@ def e2e_measure(args, name, s, ups, params, dev):
     """Same metric through the public host-fed API (``pipeline.HostPipeline``) with
     pinned host buffers: every step copies its inputs (scene, poses, upstream
     gradient planes) host -> device and its results (depth, alpha, normal, flow
-    planes and all gradients) device -> host inside the timed region; the pipeline
-    overlaps those copies with the neighbouring steps' kernels."""
+    planes and all gradients) device -> host inside the timed region, overlapped with
+    the neighbouring steps' kernels.  Two modes of the API: ``submit`` (any host
+    tensors each step; a launch per copy) and the fixed-buffer graphs
+    (``capture_fixed`` / ``submit_fixed``: each buffer set's copies in and out
+    replayed as graphs, around the render's graph, on the same three streams).  ``value`` is the fixed-buffer mode's; both
+    modes' last steps are checked against a plain device call."""
     import torch
 
     from paper_2308_14737_gb300 import fmb, pipeline
@@ -754,24 +758,40 @@ def e2e_measure(args, name, s, ups, params, dev):
     h_outs = [pipe.host_outputs(), pipe.host_outputs()]
     h2d = sum(h.numel() * 4 for h in h_in.values() if h is not None)
     d2h = sum(o.numel() * 4 for o in h_outs[0].values())
-    for i in range(4):
-        pipe.submit(h_in, h_outs[i % 2])
-    torch.cuda.synchronize(dev)
     # at least 20 steps: the pipeline's fill (the first step's inputs in) and drain
     # (the last step's results out) are paid once per timed run, as in a training loop
     n = max(args.steps, 20)
     cur = torch.cuda.current_stream(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(cur)
-    for st in pipe.streams():
-        st.wait_stream(cur)
-    for i in range(n):
-        pipe.submit(h_in, h_outs[i % 2])
-    for st in pipe.streams():
-        cur.wait_stream(st)
-    e1.record(cur)
-    torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1) / n
+
+    def timed(step, streams):
+        for _ in range(4):
+            step()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        for st in streams:
+            st.wait_stream(cur)
+        for _ in range(n):
+            step()
+        for st in streams:
+            cur.wait_stream(st)
+        e1.record(cur)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / n
+
+    k_call = [0]
+
+    def call_step():
+        pipe.submit(h_in, h_outs[k_call[0] % 2])
+        k_call[0] += 1
+
+    ms_call = timed(call_step, pipe.streams())
+    got_call = {k: v.clone() for k, v in h_outs[(k_call[0] - 1) % 2].items()}
+    h_fixed = [pipe.host_outputs(), pipe.host_outputs()]
+    pipe.capture_fixed(h_in, h_fixed)
+    ms_fixed = timed(pipe.submit_fixed, pipe.streams())
+    got_fixed = h_fixed[(pipe.i_fixed - 1) % 2]
+
     # the last step's host results against a plain device-resident call on the same
     # inputs: planes bitwise, gradients up to the order of fp32 atomic additions
     d = {k: None if v is None else v.to(dev) for k, v in h_in.items()}
@@ -781,21 +801,24 @@ def e2e_measure(args, name, s, ups, params, dev):
                    d["g_flow"], want_pose=want_pose)
     want = dict(depth=out["depth"], alpha=out["alpha"], normal=out["normal"], flow=out["flow"],
                 grad_means=g["means"], grad_chol=g["chol"], grad_weights=g["weights"], grad_poses=g["poses"])
-    got = h_outs[(n - 1) % 2]
-    for k, v in want.items():
-        if v is None:
-            continue
-        a, b = got[k].reshape(-1), v.reshape(-1).cpu()
-        ok = torch.equal(a, b) if not k.startswith("grad") else \
-            bool((a - b).abs().max() <= 1e-5 * float(b.abs().max()) + 1e-30)
-        if not ok:
-            raise RuntimeError(f"host-fed pipeline result {k} differs from the plain call's")
-    return {"value": s.n_pairs / (ms * 1e-3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": ms, "steps": n,
-            "parity": "last step's host results vs a plain device call: planes bitwise, gradients within 1e-5 "
-                      "of the largest entry",
-            "api": "pipeline.HostPipeline: two device buffer sets; each step's host->device copies, forward + "
-                   "backward (CUDA graph) and device->host copies on three streams, overlapped across steps"}
+    for mode, got in (("submit", got_call), ("fixed-buffer", got_fixed)):
+        for k, v in want.items():
+            if v is None:
+                continue
+            a, b = got[k].reshape(-1), v.reshape(-1).cpu()
+            ok = torch.equal(a, b) if not k.startswith("grad") else \
+                bool((a - b).abs().max() <= 1e-5 * float(b.abs().max()) + 1e-30)
+            if not ok:
+                raise RuntimeError(f"host-fed pipeline ({mode}) result {k} differs from the plain call's")
+    return {"value": s.n_pairs / (ms_fixed * 1e-3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": ms_fixed, "steps": n,
+            "per_call_submit": {"value": s.n_pairs / (ms_call * 1e-3), "ms_per_step": ms_call, "steps": n},
+            "parity": "both modes' last step's host results vs a plain device call: planes bitwise, gradients "
+                      "within 1e-5 of the largest entry",
+            "api": "pipeline.HostPipeline, two device buffer sets, three streams (copies in, forward + backward, "
+                   "copies out) overlapped across steps; with fixed pinned host buffers (capture_fixed / "
+                   "submit_fixed) each set's copies in and copies out are CUDA graphs too (three graph launches "
+                   "per step); per_call_submit: submit() with a launch per copy"}
 
 
 def cpu_model() -> str:

@@ -121,3 +121,65 @@ class HostPipeline:
 
     def streams(self):
         return self.s_in, self.s_comp, self.s_out
+
+    # ---------------------------------------------------------------- fixed host buffers
+    # A caller whose host buffers stay the same from step to step (a pinned staging
+    # area that a data loader refills, say) can have each buffer set's copies captured
+    # as CUDA graphs: its inputs' copies in as one graph, its results' copies out as
+    # another.  A step then costs the host three graph launches (copies in, the render
+    # and adjoint, copies out) on the same three streams and with the same ordering as
+    # ``submit``, instead of a launch per copy.  Every replay still performs all of its
+    # copies.
+
+    def capture_fixed(self, h_in: dict, h_outs: list):
+        """Captures, per buffer set j, the copies of ``h_in`` (pinned host tensors
+        named as in ``INPUTS``, shared by both sets) into the set's device inputs and
+        of its results into ``h_outs[j]`` (from ``host_outputs``).  Afterwards
+        ``submit_fixed`` runs the steps, the sets in turn.  The caller refills ``h_in``
+        only after the previous step's ``last_input_event`` and reads ``h_outs[j]``
+        after the event of a step of set j."""
+        if len(h_outs) != len(self.slots):
+            raise ValueError(f"one host output set per buffer set ({len(self.slots)}) expected")
+        for h in list(h_in.values()) + [v for o in h_outs for v in o.values()]:
+            if h is not None and not h.is_pinned():
+                raise ValueError("fixed host buffers must be pinned (page-locked)")
+        if any(sl["graph"] is None for sl in self.slots):
+            raise RuntimeError("capture_fixed needs the pipeline's graphs (use_graphs=True)")
+        torch.cuda.synchronize(self.device)
+        for sl, h_out in zip(self.slots, h_outs):
+            g_in, g_out = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g_in):
+                for k, d in sl["d_in"].items():
+                    if d is not None:
+                        d.copy_(h_in[k].reshape(-1), non_blocking=True)
+            with torch.cuda.graph(g_out):
+                for k, d in self.outputs(sl).items():
+                    h_out[k].copy_(d, non_blocking=True)
+            sl["graph_in"], sl["graph_out"] = g_in, g_out
+        self.i_fixed = 0
+
+    def submit_fixed(self) -> torch.cuda.Event:
+        """Enqueues the next step on the captured host buffers (the buffer sets in
+        turn, ordered as ``submit`` orders them); returns the event after which that
+        step's host outputs are complete."""
+        j = self.i_fixed % len(self.slots)
+        self.i_fixed += 1
+        sl = self.slots[j]
+        with torch.cuda.stream(self.s_in):
+            if sl["used"]:
+                self.s_in.wait_event(sl["ev_comp"])  # the slot's previous step has read its inputs
+            sl["graph_in"].replay()
+            sl["ev_in"].record(self.s_in)
+        with torch.cuda.stream(self.s_comp):
+            self.s_comp.wait_event(sl["ev_in"])
+            if sl["used"]:
+                self.s_comp.wait_event(sl["ev_out"])  # the slot's previous results are out
+            sl["graph"].replay()
+            sl["ev_comp"].record(self.s_comp)
+        with torch.cuda.stream(self.s_out):
+            self.s_out.wait_event(sl["ev_comp"])
+            sl["graph_out"].replay()
+            sl["ev_out"].record(self.s_out)
+        sl["used"] = True
+        self.last_input_event = sl["ev_in"]
+        return sl["ev_out"]

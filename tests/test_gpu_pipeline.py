@@ -81,3 +81,31 @@ def test_host_pipeline_matches_plain_calls(variant, keep_order, deterministic, K
     torch.cuda.synchronize()
     for i in range(len(steps)):
         _same({k: v.numpy() for k, v in h_out[i].items()}, want[i], deterministic, f"step {i}")
+
+
+@pytest.mark.parametrize("variant,keep_order", [(0, 0), (1, 1)])
+def test_fixed_host_buffer_graphs_match_plain_calls(variant, keep_order):
+    """The fixed-buffer mode (each buffer set's copies in, render, adjoint and copies
+    out captured as one graph) gives each step the plain calls' results on the
+    inputs the host buffers held: the buffers are refilled between steps."""
+    s = synth.object_orbit(K=100, n_views=4, W=64, H=48)
+    params = fmb.default_params(n_flow=1, variant=variant, keep_order=keep_order, deterministic=1)
+    P = s.n_pixels
+    rng = np.random.default_rng(11)
+    steps = []
+    for i in range(4):
+        ups = synth.upstream_grads(rng, P, 1)
+        steps.append(dict(means=(s.means + 0.02 * i).astype(np.float32), chol=s.chol, weights=s.weights,
+                          poses=s.poses, g_depth=ups[0], g_alpha=ups[1], g_normal=ups[2].reshape(-1),
+                          g_flow=ups[3].reshape(-1)))
+    want = [_plain(s, params, st) for st in steps]
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).pin_memory()
+    h_in = {k: pin(v) for k, v in steps[0].items()}
+    pipe = pipeline.HostPipeline(s.obj_offsets, s.views, len(s.poses), params, h_in, want_pose=True)
+    h_outs = [pipe.host_outputs(), pipe.host_outputs()]
+    pipe.capture_fixed(h_in, h_outs)
+    for i, st in enumerate(steps):
+        for k, v in st.items():  # refill the fixed host inputs between steps
+            h_in[k].copy_(torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float32).reshape(h_in[k].shape))
+        pipe.submit_fixed().synchronize()
+        _same({k: v.numpy() for k, v in h_outs[i % 2].items()}, want[i], True, f"step {i}")
