@@ -31,6 +31,11 @@
  *   - Invalid arguments are reported before anything is enqueued.  No C++ exception
  *     crosses the ABI.  On a non-OK status, fmb_last_error() returns a message
  *     (thread-local, valid until the next call on the same thread).
+ *   - Every buffer must hold the elements its description states, in terms of G
+ *     (the Gaussians, h_obj_offsets[n_objects]), P_total (the plane entries) and
+ *     n_poses.  The library sees pointers only and cannot check their sizes: a
+ *     short buffer is read or written past its end.  (The Python binding checks
+ *     every tensor's size before it calls.)
  *   - Invalid data that is not checked on the host (lambda <= 0, a singular L, a
  *     flow target point at or behind its camera plane, NaN inputs) gives NaN or Inf
  *     in the affected outputs; it never makes a kernel read or write out of bounds.
