@@ -345,6 +345,8 @@ def fmb_adam_step(adam: FmbAdamParams, param, grad, m, v, positive_begin, step_c
     L = load_library()
     if step_counter.dtype != torch.int32:
         raise ValueError("step_counter must be an int32 device tensor")
+    n = int(param.numel())
+    _need(grad=(grad, n), m=(m, n), v=(v, n), step_counter=(step_counter, 1))
     _check(L.fmb_adam_step(ctypes.byref(adam), _ptr(param), _ptr(grad), _ptr(m), _ptr(v), int(param.numel()),
                            int(positive_begin), ctypes.c_void_p(step_counter.data_ptr()), _stream(stream)))
 

@@ -330,3 +330,16 @@ def test_binding_forward_checks_planes(fmb):
         with pytest.raises(ValueError, match=k):
             fmb.fmb_render_forward(p, s.obj_offsets, g["means"], g["chol"], g["weights"], g["poses"], s.views,
                                    g["depth"], g["alpha"], g["normal"], g["flow"], g["saved"], None)
+
+
+def test_adam_binding_rejects_short_state(fmb):
+    import torch
+
+    adam = fmb.FmbAdamParams(lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8)
+    z = lambda n: torch.zeros(n, dtype=torch.float32)
+    step = torch.zeros(1, dtype=torch.int32)
+    for short in ("grad", "m", "v"):
+        bufs = dict(param=z(10), grad=z(10), m=z(10), v=z(10))
+        bufs[short] = z(9)
+        with pytest.raises(ValueError, match=short):
+            fmb.fmb_adam_step(adam, bufs["param"], bufs["grad"], bufs["m"], bufs["v"], 0, step)

@@ -1,5 +1,5 @@
 """No call writes outside the buffers it is given.  Every output (planes, gradients,
-point export, attribution) is cut out of a larger buffer whose guard zones on both
+point export, attribution, the Adam step's state) is cut out of a larger buffer whose guard zones on both
 sides hold a NaN bit pattern; after forward, backward, point export and loss
 attribution the guards must be unchanged and the results bitwise those of the same
 calls on plainly allocated buffers (deterministic mode).  The inputs are passed
@@ -74,9 +74,9 @@ def test_outputs_stay_inside_their_buffers(variant, keep_order, deterministic):
     # attribution() read)
     ref_planes = r.forward(m, c, w, po)
     ref_grads = r.backward(m, c, w, po, gd, ga, gn, gf, want_pose=True)
-    ref_points = r.points(m, c, w, po) if variant == 0 else None
+    ref_points = r.points(m, c, w, po)
     ray_loss = torch.rand(P, device="cuda")
-    ref_attr = r.attribution(m, c, w, po, ray_loss) if variant == 0 else None
+    ref_attr = r.attribution(m, c, w, po, ray_loss)
     torch.cuda.synchronize()
 
     A = Arena()
@@ -86,13 +86,11 @@ def test_outputs_stay_inside_their_buffers(variant, keep_order, deterministic):
                  poses=A.take(12 * NP).view(NP, 12))
     r.forward(m, c, w, po, out=planes)
     r.backward(m, c, w, po, gd, ga, gn, gf, want_pose=True, out=grads, planes=planes)
-    if variant == 0:
-        pts = dict(points=A.take(3 * P), normal_tf=A.take(3 * P), normal_screen=A.take(3 * P), quality=A.take(P))
-        fmb.fmb_render_points(params, s.obj_offsets, m, c, w, po, r.c_views, planes["depth"], planes["saved"],
-                              pts["points"], pts["normal_tf"], pts["normal_screen"], pts["quality"], r.ws)
-        attr = A.take(G)
-        fmb.fmb_loss_attribution(params, s.obj_offsets, m, c, w, po, r.c_views, planes["saved"], ray_loss, attr,
-                                 r.ws)
+    pts = dict(points=A.take(3 * P), normal_tf=A.take(3 * P), normal_screen=A.take(3 * P), quality=A.take(P))
+    fmb.fmb_render_points(params, s.obj_offsets, m, c, w, po, r.c_views, planes["depth"], planes["saved"],
+                          pts["points"], pts["normal_tf"], pts["normal_screen"], pts["quality"], r.ws)
+    attr = A.take(G)
+    fmb.fmb_loss_attribution(params, s.obj_offsets, m, c, w, po, r.c_views, planes["saved"], ray_loss, attr, r.ws)
     assert A.intact() == []
     assert fmb.fmb_read_device_status(r.ws) == 0
 
@@ -104,7 +102,33 @@ def test_outputs_stay_inside_their_buffers(variant, keep_order, deterministic):
             assert torch.equal(a, b), k
         else:  # fp32 atomics: equal up to the order of the additions
             assert torch.allclose(a, b, rtol=1e-5, atol=1e-6 * float(b.abs().max())), k
-    if variant == 0:
-        for k in ("points", "normal_tf", "normal_screen", "quality"):
-            assert torch.equal(pts[k], ref_points[k]), k
-        assert torch.allclose(attr, ref_attr, rtol=1e-5, atol=1e-6 * float(ref_attr.abs().max()))
+    for k in ("points", "normal_tf", "normal_screen", "quality"):
+        assert torch.equal(pts[k], ref_points[k]), k
+    assert torch.allclose(attr, ref_attr, rtol=1e-5, atol=1e-6 * float(ref_attr.abs().max()))
+
+
+def test_adam_step_stays_inside_its_buffers():
+    n, pos = 3 * 1000 + 37, 3000  # the last 37 entries are updated in log space
+    A = Arena()
+    rng = np.random.default_rng(2)
+    vals = {k: torch.as_tensor(rng.uniform(0.1, 1.0, n).astype(np.float32), device="cuda")
+            for k in ("param", "grad", "m", "v")}
+    ref = {k: v.clone() for k, v in vals.items()}
+    got = {}
+    for k, v in vals.items():
+        got[k] = A.take(n)
+        got[k].copy_(v)
+    step_ref = torch.zeros(1, dtype=torch.int32, device="cuda")
+    step_raw = torch.full((2 * GUARD + 1,), SENTINEL, dtype=torch.int32, device="cuda")
+    step_got = step_raw[GUARD:GUARD + 1]
+    step_got.zero_()
+    adam = fmb.FmbAdamParams(lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8)
+    for _ in range(3):
+        fmb.fmb_adam_step(adam, ref["param"], ref["grad"], ref["m"], ref["v"], pos, step_ref)
+        fmb.fmb_adam_step(adam, got["param"], got["grad"], got["m"], got["v"], pos, step_got)
+    assert A.intact() == []
+    lo, hi = step_raw[:GUARD].cpu().numpy(), step_raw[GUARD + 1:].cpu().numpy()
+    assert (lo == SENTINEL).all() and (hi == SENTINEL).all()
+    assert int(step_got.item()) == 3 and int(step_ref.item()) == 3
+    for k in ("param", "m", "v"):
+        assert torch.equal(got[k], ref[k]), k
