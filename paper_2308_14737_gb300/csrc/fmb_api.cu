@@ -14,6 +14,7 @@
 #include <mutex>
 #include <stdexcept>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "fmb_internal.cuh"
@@ -110,8 +111,12 @@ int choose_bwd_threads(const fmb_view* views, int n_views, const long long* offs
 }
 
 struct Plan {
+  // A call's launches, one batch per launch: up to 64 views per batch, or (`big`: a
+  // two-parameter call with more than 64 views) up to 256 in the *_big lists.
+  bool big = false;
   std::vector<fmb::Batch> fwd;  // forward launches (tiles of rays)
   std::vector<fmb::Batch> bwd;  // backward launches (ray tiles x Gaussian blocks)
+  std::vector<fmb::BigBatch> fwd_big, bwd_big, fmerge_big;
   long long n_records = 0;
   long long part_floats = 0;
   long long pair_stride = 0;  // stored-intermediate mode: floats per per-pair array
@@ -198,8 +203,8 @@ fmb_status validate_views(int n_objects, int n_poses, int n_views, const fmb_vie
   return FMB_OK;
 }
 
-template <class Cost, class Count>
-void order_items(fmb::Batch& b, Cost cost, Count count) {
+template <class B, class Cost, class Count>
+void order_items(B& b, Cost cost, Count count) {
   std::vector<int> idx(b.n_views);
   for (int i = 0; i < b.n_views; ++i) idx[i] = i;
   std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost(b.v[x]) > cost(b.v[y]); });
@@ -213,58 +218,19 @@ void order_items(fmb::Batch& b, Cost cost, Count count) {
   b.n_items = static_cast<int>(acc);
 }
 
-Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_views, const fmb_view* views) {
-  Plan pl;
-  pl.rpt = p->fwd_rays_per_thread > 0 ? p->fwd_rays_per_thread : kDefaultRpt;
-  pl.bwd_threads = p->bwd_threads > 0 ? p->bwd_threads : choose_bwd_threads(views, n_views, offs);
-  // default ray tile: three rays per thread in the per-ray phase (balanced, and long
-  // enough to amortise the per-CTA reductions)
-  pl.ray_tile = p->bwd_ray_tile > 0 ? p->bwd_ray_tile : 3 * pl.bwd_threads;
-  pl.n_gauss = offs[n_objects];
-  const bool ac = p->variant == 1;
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-    cudaGetLastError();  // no device (a host-only size query): plan for 152 SMs
-    sms = 152;
-  }
-  if (ac) {
-    long long total = 0;
-    for (int i = 0; i < n_views; ++i) total += view_entries(views[i]);
-    pl.ac_run = fmb::ac_fwd_run(total, sms);
-  }
-  const int rays_fwd = ac ? fmb::ac_fwd_rays_per_item(pl.ac_run) : fmb::forward_rays_per_cta(pl.rpt);
-  // Gaussian split of the two-parameter forward: when the batch's ray tiles fill
-  // less than half a wave of the GPU (about 6 resident forward CTAs per SM) and the
-  // objects are large (K >= 128, so each CTA's serial Gaussian loop is long), each
-  // tile's Gaussians are spread over up to 4 CTAs.  Measured on the GB300: a
-  // 50 000-ray minibatch at K = 256 (200 tiles) 78.9 -> 66.6 us with 4 splits, while
-  // a single 320x240 view at K = 100 (300 tiles), a 64x64 view at K = 40 and a
-  // 640x480 view at K = 256 (1200 tiles) only lose from splitting.
-  if (!ac && !p->colors && !p->store_pairs && pl.rpt % 2 == 0 && p->fwd_ksplit != 1) {
-    if (p->fwd_ksplit > 1) {
-      pl.ksplit = p->fwd_ksplit;
-    } else {
-      long long tiles = 0;
-      int maxK = 1;
-      for (int i = 0; i < n_views; ++i) {
-        tiles += (view_entries(views[i]) + rays_fwd - 1) / rays_fwd;
-        maxK = std::max(maxK, static_cast<int>(offs[views[i].object + 1] - offs[views[i].object]));
-      }
-      const long long wave = static_cast<long long>(std::max(sms, 1)) * 6;
-      if (tiles > 0 && 2 * tiles < wave && maxK >= 128) {
-        const long long k = (wave + tiles - 1) / tiles;
-        pl.ksplit = static_cast<int>(std::max(1ll, std::min({k, 4ll, static_cast<long long>(maxK / 16)})));
-      }
-    }
-  }
+// The views in batches of up to B::kCapacity, one batch per launch: each view's
+// per-launch record (forward and backward tiling), the running offsets of its
+// records, partial slots and stored pairs, and the batch's work items in cost order.
+template <class B>
+void fill_batches(Plan& pl, const fmb_params* p, const long long* offs, int n_views, const fmb_view* views, bool ac,
+                  int rays_fwd, std::vector<B>& fwd, std::vector<B>& bwd, std::vector<B>& fmerge, long long& rec,
+                  long long& part, long long& pairs) {
   const int n_flow = p->n_flow;
-  long long rec = 0, part = 0, pairs = 0;
-  for (int base = 0; base < n_views; base += fmb::kMaxBatchViews) {
-    const int nb = std::min(fmb::kMaxBatchViews, n_views - base);
-    fmb::Batch bf;
+  for (int base = 0; base < n_views; base += B::kCapacity) {
+    const int nb = std::min(B::kCapacity, n_views - base);
+    B bf;
     std::memset(&bf, 0, sizeof(bf));
-    fmb::Batch bb = bf;
+    B bb = bf;
     bf.n_views = bb.n_views = nb;
     long long ctas_f = 0, ctas_b = 0;
     for (int i = 0; i < nb; ++i) {
@@ -333,7 +299,7 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
                 [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles) * v.n_gblocks; });
     if (pl.ksplit > 1) {
       // the merge: one item per tile of forward_merge_rays_per_item() rays of a view
-      fmb::Batch bm = bf;
+      B bm = bf;
       const int rm = fmb::forward_merge_rays_per_item();
       for (int i = 0; i < nb; ++i) {
         // views left unsplit (fewer Gaussians than splits) were finished by the forward
@@ -342,13 +308,70 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
       }
       order_items(bm, [&](const fmb::DevView& v) { return static_cast<double>(v.S); },
                   [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles); });
-      pl.fmerge.push_back(bm);
+      fmerge.push_back(bm);
     }
     order_items(bb, [&](const fmb::DevView& v) { return static_cast<double>(v.GB); },
                 [](const fmb::DevView& v) { return static_cast<long long>(v.n_tiles) * v.n_gblocks; });
-    pl.fwd.push_back(bf);
-    pl.bwd.push_back(bb);
+    fwd.push_back(bf);
+    bwd.push_back(bb);
   }
+}
+
+// allow_big: the caller launches through the overloads that take 256-view batches
+// (the two-parameter render and adjoint); others always get 64-view batches.
+Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_views, const fmb_view* views,
+               bool allow_big = false) {
+  Plan pl;
+  pl.rpt = p->fwd_rays_per_thread > 0 ? p->fwd_rays_per_thread : kDefaultRpt;
+  pl.bwd_threads = p->bwd_threads > 0 ? p->bwd_threads : choose_bwd_threads(views, n_views, offs);
+  // default ray tile: three rays per thread in the per-ray phase (balanced, and long
+  // enough to amortise the per-CTA reductions)
+  pl.ray_tile = p->bwd_ray_tile > 0 ? p->bwd_ray_tile : 3 * pl.bwd_threads;
+  pl.n_gauss = offs[n_objects];
+  const bool ac = p->variant == 1;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();  // no device (a host-only size query): plan for 152 SMs
+    sms = 152;
+  }
+  if (ac) {
+    long long total = 0;
+    for (int i = 0; i < n_views; ++i) total += view_entries(views[i]);
+    pl.ac_run = fmb::ac_fwd_run(total, sms);
+  }
+  const int rays_fwd = ac ? fmb::ac_fwd_rays_per_item(pl.ac_run) : fmb::forward_rays_per_cta(pl.rpt);
+  // Gaussian split of the two-parameter forward: when the batch's ray tiles fill
+  // less than half a wave of the GPU (about 6 resident forward CTAs per SM) and the
+  // objects are large (K >= 128, so each CTA's serial Gaussian loop is long), each
+  // tile's Gaussians are spread over up to 4 CTAs.  Measured on the GB300: a
+  // 50 000-ray minibatch at K = 256 (200 tiles) 78.9 -> 66.6 us with 4 splits, while
+  // a single 320x240 view at K = 100 (300 tiles), a 64x64 view at K = 40 and a
+  // 640x480 view at K = 256 (1200 tiles) only lose from splitting.
+  if (!ac && !p->colors && !p->store_pairs && pl.rpt % 2 == 0 && p->fwd_ksplit != 1) {
+    if (p->fwd_ksplit > 1) {
+      pl.ksplit = p->fwd_ksplit;
+    } else {
+      long long tiles = 0;
+      int maxK = 1;
+      for (int i = 0; i < n_views; ++i) {
+        tiles += (view_entries(views[i]) + rays_fwd - 1) / rays_fwd;
+        maxK = std::max(maxK, static_cast<int>(offs[views[i].object + 1] - offs[views[i].object]));
+      }
+      const long long wave = static_cast<long long>(std::max(sms, 1)) * 6;
+      if (tiles > 0 && 2 * tiles < wave && maxK >= 128) {
+        const long long k = (wave + tiles - 1) / tiles;
+        pl.ksplit = static_cast<int>(std::max(1ll, std::min({k, 4ll, static_cast<long long>(maxK / 16)})));
+      }
+    }
+  }
+  long long rec = 0, part = 0, pairs = 0;
+  // two-parameter calls with more than 64 views: one launch per pass for up to 256
+  pl.big = allow_big && !ac && n_views > fmb::kMaxBatchViews;
+  if (pl.big)
+    fill_batches(pl, p, offs, n_views, views, ac, rays_fwd, pl.fwd_big, pl.bwd_big, pl.fmerge_big, rec, part, pairs);
+  else
+    fill_batches(pl, p, offs, n_views, views, ac, rays_fwd, pl.fwd, pl.bwd, pl.fmerge, rec, part, pairs);
   pl.n_records = rec;
   pl.part_floats = part;
   pl.pair_stride = (pairs + 63) / 64 * 64;
@@ -449,8 +472,9 @@ int fmb_launch_count(const fmb_params* params, int n_objects, const long long* h
       fail(FMB_ERR_INVALID_ARG, "pass must be 0 (forward) or 1 (backward)");
       return -1;
     }
-    const Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views);
-    const int nb = static_cast<int>(pass == 0 ? pl.fwd.size() : pl.bwd.size());
+    const Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views, true);
+    const int nb = static_cast<int>(pass == 0 ? (pl.big ? pl.fwd_big.size() : pl.fwd.size())
+                                              : (pl.big ? pl.bwd_big.size() : pl.bwd.size()));
     if (pass == 0) return nb * (2 + (params->variant == 0 && pl.ksplit > 1 ? 1 : 0));  // prologue, forward, merge
     if (nb == 0) return 1;  // the zeroing launch
     // prologue and backward per batch; deterministic mode adds the Gaussian (and pose) reductions
@@ -494,7 +518,7 @@ fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const lon
       return fail(FMB_ERR_INVALID_ARG, "colors and color are required when params->colors is set");
     st = validate_views(n_objects, n_poses, n_views, h_views);
     if (st != FMB_OK) return st;
-    Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views);
+    Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views, true);
     st = check_workspace(workspace, workspace_bytes, workspace_needed(params, pl));
     if (st != FMB_OK) return st;
 
@@ -515,27 +539,34 @@ fmb_status fmb_render_forward(const fmb_params* params, int n_objects, const lon
     int* counter = params->use_persistent
                        ? reinterpret_cast<int*>(reinterpret_cast<char*>(status) + kFwdCounterOffset)
                        : nullptr;
-    for (size_t bi = 0; bi < pl.fwd.size(); ++bi) {
-      const fmb::Batch& b = pl.fwd[bi];
-      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, bi == 0 ? status : nullptr, counter, s);
-      if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
-      fmb::FwdOut fo{depth, alpha, normal, flow, saved, pairs, pl.pair_stride};
-      fo.color = color;
-      fo.part = reinterpret_cast<float*>(static_cast<char*>(workspace) + fwd_part_offset(params, pl));
-      if (params->keep_order) fo.order = static_cast<unsigned char*>(workspace) + order_offset(params, pl);
-      if (params->variant == 1) {
-        fo.pairs = nullptr;
-        e = fmb::launch_forward_ac(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.maxK, fo, pl.ac_run,
-                                   status, counter, s);
-      } else {
+    // batches: pl.fwd / pl.fmerge, or their 256-view counterparts
+    auto run = [&](const auto& fwd, const auto& fmerge) -> fmb_status {
+      for (size_t bi = 0; bi < fwd.size(); ++bi) {
+        const auto& b = fwd[bi];
+        e = fmb::launch_prologue(b, sc, c, records, pl.maxK, bi == 0 ? status : nullptr, counter, s);
+        if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
+        fmb::FwdOut fo{depth, alpha, normal, flow, saved, pairs, pl.pair_stride};
+        fo.color = color;
+        fo.part = reinterpret_cast<float*>(static_cast<char*>(workspace) + fwd_part_offset(params, pl));
+        if (params->keep_order) fo.order = static_cast<unsigned char*>(workspace) + order_offset(params, pl);
+        if constexpr (std::is_same_v<std::decay_t<decltype(b)>, fmb::Batch>) {
+          if (params->variant == 1) {  // alpha compositing: 64-view batches only
+            fo.pairs = nullptr;
+            e = fmb::launch_forward_ac(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.maxK, fo,
+                                       pl.ac_run, status, counter, s);
+            if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+            continue;
+          }
+        }
         e = fmb::launch_forward(b, sc, c, records, params->want_normals != 0, params->n_flow, pl.rpt, pl.maxK, fo,
                                 status, counter, s);
         if (e == cudaSuccess && pl.ksplit > 1)
-          e = fmb::launch_forward_merge(pl.fmerge[bi], sc, params->want_normals != 0, params->n_flow, fo, s);
+          e = fmb::launch_forward_merge(fmerge[bi], sc, params->want_normals != 0, params->n_flow, fo, s);
+        if (e != cudaSuccess) return cuda_fail(e, "forward launch");
       }
-      if (e != cudaSuccess) return cuda_fail(e, "forward launch");
-    }
-    return FMB_OK;
+      return FMB_OK;
+    };
+    return pl.big ? run(pl.fwd_big, pl.fmerge_big) : run(pl.fwd, pl.fmerge);
   } catch (const std::exception& e) {
     return fail(FMB_ERR_INVALID_ARG, e.what());
   } catch (...) {
@@ -566,7 +597,7 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
       return fail(FMB_ERR_INVALID_ARG, "colors, color and grad_colors are required when params->colors is set");
     st = validate_views(n_objects, n_poses, n_views, h_views);
     if (st != FMB_OK) return st;
-    Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views);
+    Plan pl = make_plan(params, h_obj_offsets, n_objects, n_views, h_views, true);
     st = check_workspace(workspace, workspace_bytes, workspace_needed(params, pl));
     if (st != FMB_OK) return st;
 
@@ -611,21 +642,33 @@ fmb_status fmb_render_backward(const fmb_params* params, int n_objects, const lo
     cudaError_t e = cudaSuccess;
     int* counter = params->use_persistent ? reinterpret_cast<int*>(base + kBwdCounterOffset) : nullptr;
     bool first = true;  // the first batch's prologue clears the outputs and the status word
-    for (const fmb::Batch& b : pl.bwd) {
-      e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, counter, s, first ? &zj : nullptr);
-      first = false;
-      if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
-      if (params->variant == 1)
-        e = fmb::launch_backward_ac(b, sc, c, records, normals, params->n_flow, pl.maxK, in, out, status, counter, s);
-      else
-        e = fmb::launch_backward(b, sc, c, records, normals, params->n_flow, pl.ray_tile, pl.bwd_threads, in, out,
-                                 counter, s);
-      if (e != cudaSuccess) return cuda_fail(e, "backward launch");
-      if (partials) {
-        e = fmb::launch_backward_reduce(b, params->n_flow, pl.n_gauss, n_poses, out, s);
-        if (e != cudaSuccess) return cuda_fail(e, "reduction launch");
+    // batches: pl.bwd, or its 256-view counterpart
+    auto run = [&](const auto& bwd) -> fmb_status {
+      for (const auto& b : bwd) {
+        e = fmb::launch_prologue(b, sc, c, records, pl.maxK, nullptr, counter, s, first ? &zj : nullptr);
+        first = false;
+        if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
+        bool done = false;
+        if constexpr (std::is_same_v<std::decay_t<decltype(b)>, fmb::Batch>) {
+          if (params->variant == 1) {  // alpha compositing: 64-view batches only
+            e = fmb::launch_backward_ac(b, sc, c, records, normals, params->n_flow, pl.maxK, in, out, status,
+                                        counter, s);
+            done = true;
+          }
+        }
+        if (!done)
+          e = fmb::launch_backward(b, sc, c, records, normals, params->n_flow, pl.ray_tile, pl.bwd_threads, in, out,
+                                   counter, s);
+        if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+        if (partials) {
+          e = fmb::launch_backward_reduce(b, params->n_flow, pl.n_gauss, n_poses, out, s);
+          if (e != cudaSuccess) return cuda_fail(e, "reduction launch");
+        }
       }
-    }
+      return FMB_OK;
+    };
+    st = pl.big ? run(pl.bwd_big) : run(pl.bwd);
+    if (st != FMB_OK) return st;
     if (first) {  // nothing to render: the outputs are still cleared
       e = fmb::launch_zero(zj, s);
       if (e != cudaSuccess) return cuda_fail(e, "zeroing launch");

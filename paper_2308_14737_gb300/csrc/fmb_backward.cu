@@ -185,9 +185,9 @@ __device__ __forceinline__ float warp_sum(float x) {
 
 // CL = 2: launched as clusters of two CTAs, the two Gaussian blocks of one ray tile
 // (grid mode, every view of the batch in two blocks); CL = 1: no cluster.
-template <bool NORMALS, int NFLOW, bool STORED, bool COLOR = false, bool POSE = true, int CL = 1>
+template <bool NORMALS, int NFLOW, bool STORED, bool COLOR = false, bool POSE = true, int CL = 1, class B = Batch>
 __global__ void __launch_bounds__(kBwdMaxThreads, kBwdMinBlocks)
-    backward_kernel(const __grid_constant__ Batch batch, Scene s, Consts k, const float4* __restrict__ records,
+    backward_kernel(const __grid_constant__ B batch, Scene s, Consts k, const float4* __restrict__ records,
                     BwdIn in, BwdOut out, int ray_tile, int* counter) {
   pdl_enter();
   extern __shared__ float4 bsm[];
@@ -553,11 +553,12 @@ static int bwd_smem_bytes(int ray_tile, int threads, bool color = false) {
                   threads * (color ? acc_floats<true>() : kAccFloats) * static_cast<int>(sizeof(float)));
 }
 
-template <bool NORMALS, int NFLOW, bool STORED = false, bool COLOR = false, bool POSE = true, int CL = 1>
+template <bool NORMALS, int NFLOW, bool STORED = false, bool COLOR = false, bool POSE = true, int CL = 1,
+          class B = Batch>
 static cudaError_t prepare_bwd_t(int smem) {
   // Dynamic plus static shared memory above the 48 KB default needs the opt-in.
   if (smem + static_cast<int>(sizeof(float) * (kBwdMaxThreads / 32) * 48) > 48 * 1024)
-    return cudaFuncSetAttribute(backward_kernel<NORMALS, NFLOW, STORED, COLOR, POSE, CL>,
+    return cudaFuncSetAttribute(backward_kernel<NORMALS, NFLOW, STORED, COLOR, POSE, CL, B>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return cudaSuccess;
 }
@@ -576,7 +577,8 @@ static int bwd_ctas_per_sm_t(int ray_tile, int threads) {
 // Cluster size of a grid-mode backward launch: 2 when every view of the batch runs
 // as two Gaussian blocks (then each tile's two items are consecutive and 2-aligned,
 // one cluster), else 1 (no cluster).
-static int bwd_cluster_size(const Batch& b) {
+template <class B>
+static int bwd_cluster_size(const B& b) {
   int C = 0;
   for (int i = 0; i < b.n_views; ++i) {
     const DevView& v = b.v[i];
@@ -590,12 +592,12 @@ static int bwd_cluster_size(const Batch& b) {
   return C;
 }
 
-template <bool NORMALS, int NFLOW, bool STORED, bool COLOR = false, bool POSE = true>
-static cudaError_t launch_bwd_s(const Batch& b, const Scene& s, const Consts& c, const float4* records,
+template <bool NORMALS, int NFLOW, bool STORED, bool COLOR = false, bool POSE = true, class B>
+static cudaError_t launch_bwd_s(const B& b, const Scene& s, const Consts& c, const float4* records,
                                 int ray_tile, int threads, const BwdIn& in, const BwdOut& out, int* counter,
                                 cudaStream_t st) {
   const int smem = bwd_smem_bytes(ray_tile, threads, COLOR);
-  cudaError_t e = prepare_bwd_t<NORMALS, NFLOW, STORED, COLOR, POSE>(smem);
+  cudaError_t e = prepare_bwd_t<NORMALS, NFLOW, STORED, COLOR, POSE, 1, B>(smem);
   if (e != cudaSuccess) return e;
   int grid = b.n_items;
   if (counter) {
@@ -606,18 +608,18 @@ static cudaError_t launch_bwd_s(const Batch& b, const Scene& s, const Consts& c,
   }
   if constexpr (!STORED && !COLOR) {
     if (counter == nullptr && bwd_cluster_size(b) == 2) {
-      e = prepare_bwd_t<NORMALS, NFLOW, STORED, COLOR, POSE, 2>(smem);
+      e = prepare_bwd_t<NORMALS, NFLOW, STORED, COLOR, POSE, 2, B>(smem);
       if (e != cudaSuccess) return e;
-      return launch_kernel(backward_kernel<NORMALS, NFLOW, STORED, COLOR, POSE, 2>, dim3(grid), dim3(threads), smem, st,
-                           2, b, s, c, records, in, out, ray_tile, counter);
+      return launch_kernel(backward_kernel<NORMALS, NFLOW, STORED, COLOR, POSE, 2, B>, dim3(grid), dim3(threads), smem,
+                           st, 2, b, s, c, records, in, out, ray_tile, counter);
     }
   }
-  return launch_kernel(backward_kernel<NORMALS, NFLOW, STORED, COLOR, POSE>, dim3(grid), dim3(threads), smem, st, 1, b,
-                       s, c, records, in, out, ray_tile, counter);
+  return launch_kernel(backward_kernel<NORMALS, NFLOW, STORED, COLOR, POSE, 1, B>, dim3(grid), dim3(threads), smem, st,
+                       1, b, s, c, records, in, out, ray_tile, counter);
 }
 
-template <bool NORMALS, int NFLOW>
-static cudaError_t launch_bwd_t(const Batch& b, const Scene& s, const Consts& c, const float4* records,
+template <bool NORMALS, int NFLOW, class B>
+static cudaError_t launch_bwd_t(const B& b, const Scene& s, const Consts& c, const float4* records,
                                 int ray_tile, int threads, const BwdIn& in, const BwdOut& out, int* counter,
                                 cudaStream_t st) {
   if (in.pairs != nullptr)
@@ -630,9 +632,10 @@ static cudaError_t launch_bwd_t(const Batch& b, const Scene& s, const Consts& c,
   return launch_bwd_s<NORMALS, NFLOW, false>(b, s, c, records, ray_tile, threads, in, out, counter, st);
 }
 
-cudaError_t launch_backward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
-                            int n_flow, int ray_tile, int threads, const BwdIn& in, const BwdOut& out,
-                            int* counter, cudaStream_t st) {
+template <class B>
+static cudaError_t launch_backward_t(const B& b, const Scene& s, const Consts& c, const float4* records,
+                                     bool normals, int n_flow, int ray_tile, int threads, const BwdIn& in,
+                                     const BwdOut& out, int* counter, cudaStream_t st) {
   if (normals) {
     if (n_flow == 0) return launch_bwd_t<true, 0>(b, s, c, records, ray_tile, threads, in, out, counter, st);
     if (n_flow == 1) return launch_bwd_t<true, 1>(b, s, c, records, ray_tile, threads, in, out, counter, st);
@@ -641,6 +644,16 @@ cudaError_t launch_backward(const Batch& b, const Scene& s, const Consts& c, con
   if (n_flow == 0) return launch_bwd_t<false, 0>(b, s, c, records, ray_tile, threads, in, out, counter, st);
   if (n_flow == 1) return launch_bwd_t<false, 1>(b, s, c, records, ray_tile, threads, in, out, counter, st);
   return launch_bwd_t<false, 2>(b, s, c, records, ray_tile, threads, in, out, counter, st);
+}
+cudaError_t launch_backward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
+                            int n_flow, int ray_tile, int threads, const BwdIn& in, const BwdOut& out,
+                            int* counter, cudaStream_t st) {
+  return launch_backward_t(b, s, c, records, normals, n_flow, ray_tile, threads, in, out, counter, st);
+}
+cudaError_t launch_backward(const BigBatch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
+                            int n_flow, int ray_tile, int threads, const BwdIn& in, const BwdOut& out,
+                            int* counter, cudaStream_t st) {
+  return launch_backward_t(b, s, c, records, normals, n_flow, ray_tile, threads, in, out, counter, st);
 }
 
 int backward_ctas_per_sm(bool normals, int n_flow, int ray_tile, int threads) {
@@ -677,7 +690,8 @@ __device__ __forceinline__ float warp_sum_fixed(float x) {
 
 // Gaussian gradients: warp w handles (Gaussian g, component comp), w = g * nc + comp
 // (nc = 10, or 13 with colours: means 3, chol 6, weight 1, colour 3).
-__global__ void reduce_gauss_kernel(const __grid_constant__ Batch batch, const float* __restrict__ partials,
+template <class B>
+__global__ void reduce_gauss_kernel(const __grid_constant__ B batch, const float* __restrict__ partials,
                                     float* gmeans, float* gchol, float* gweights, float* gcolors, long long n_gauss,
                                     int nc) {
   pdl_enter();
@@ -710,7 +724,8 @@ __global__ void reduce_gauss_kernel(const __grid_constant__ Batch batch, const f
 }
 
 // Pose gradients: warp w handles (pose p, component comp), w = p * 12 + comp.
-__global__ void reduce_pose_kernel(const __grid_constant__ Batch batch, const float* __restrict__ partials,
+template <class B>
+__global__ void reduce_pose_kernel(const __grid_constant__ B batch, const float* __restrict__ partials,
                                    float* gposes, int n_poses, int n_flow, int nc) {
   pdl_enter();
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -733,17 +748,26 @@ __global__ void reduce_pose_kernel(const __grid_constant__ Batch batch, const fl
   if (lane == 0) gposes[12 * static_cast<long long>(p) + comp] += acc;
 }
 
-cudaError_t launch_backward_reduce(const Batch& b, int n_flow, long long n_gauss, int n_poses, const BwdOut& out,
-                                   cudaStream_t st) {
+template <class B>
+static cudaError_t launch_backward_reduce_t(const B& b, int n_flow, long long n_gauss, int n_poses,
+                                            const BwdOut& out, cudaStream_t st) {
   const int nc = out.gcolors != nullptr ? 13 : 10;
   const long long warps = n_gauss * nc;
   const dim3 grid(static_cast<unsigned>((warps * 32 + 255) / 256));
   const float* partials = out.partials;
-  cudaError_t e = launch_kernel(reduce_gauss_kernel, grid, dim3(256), 0, st, 1, b, partials, out.gmeans, out.gchol,
-                                out.gweights, out.gcolors, n_gauss, nc);
+  cudaError_t e = launch_kernel(reduce_gauss_kernel<B>, grid, dim3(256), 0, st, 1, b, partials, out.gmeans,
+                                out.gchol, out.gweights, out.gcolors, n_gauss, nc);
   if (e != cudaSuccess || out.gposes == nullptr) return e;
-  return launch_kernel(reduce_pose_kernel, dim3((n_poses * 12 * 32 + 255) / 256), dim3(256), 0, st, 1, b, partials,
-                       out.gposes, n_poses, n_flow, nc);
+  return launch_kernel(reduce_pose_kernel<B>, dim3((n_poses * 12 * 32 + 255) / 256), dim3(256), 0, st, 1, b,
+                       partials, out.gposes, n_poses, n_flow, nc);
+}
+cudaError_t launch_backward_reduce(const Batch& b, int n_flow, long long n_gauss, int n_poses, const BwdOut& out,
+                                   cudaStream_t st) {
+  return launch_backward_reduce_t(b, n_flow, n_gauss, n_poses, out, st);
+}
+cudaError_t launch_backward_reduce(const BigBatch& b, int n_flow, long long n_gauss, int n_poses, const BwdOut& out,
+                                   cudaStream_t st) {
+  return launch_backward_reduce_t(b, n_flow, n_gauss, n_poses, out, st);
 }
 
 }  // namespace fmb

@@ -25,7 +25,8 @@ constexpr int kChunk = 256;  // records per shared-memory stage (16 KB)
 // accuracy relative to its own size.  The same launch clears the arrays of `zero`
 // (the backward's gradient outputs and status word, which its kernels then
 // accumulate into), grid-stride over all its threads.
-__global__ void __launch_bounds__(128) prologue_kernel(const __grid_constant__ Batch batch, Scene s, Consts k,
+template <class B>
+__global__ void __launch_bounds__(128) prologue_kernel(const __grid_constant__ B batch, Scene s, Consts k,
                                                         float4* __restrict__ records, int* status_to_clear,
                                                         int* counter_to_clear, ZeroJob zero) {
   pdl_enter();
@@ -76,11 +77,21 @@ __global__ void __launch_bounds__(128) prologue_kernel(const __grid_constant__ B
   (void)k;
 }
 
+template <class B>
+static cudaError_t launch_prologue_t(const B& b, const Scene& s, const Consts& c, float4* records, int maxK,
+                                     int* status_to_clear, int* counter_to_clear, cudaStream_t st,
+                                     const ZeroJob* zero) {
+  dim3 grid((maxK + 127) / 128, b.n_views);
+  return launch_kernel(prologue_kernel<B>, grid, dim3(128), 0, st, 1, b, s, c, records, status_to_clear,
+                       counter_to_clear, zero != nullptr ? *zero : ZeroJob{});
+}
 cudaError_t launch_prologue(const Batch& b, const Scene& s, const Consts& c, float4* records, int maxK,
                             int* status_to_clear, int* counter_to_clear, cudaStream_t st, const ZeroJob* zero) {
-  dim3 grid((maxK + 127) / 128, b.n_views);
-  return launch_kernel(prologue_kernel, grid, dim3(128), 0, st, 1, b, s, c, records, status_to_clear,
-                       counter_to_clear, zero != nullptr ? *zero : ZeroJob{});
+  return launch_prologue_t(b, s, c, records, maxK, status_to_clear, counter_to_clear, st, zero);
+}
+cudaError_t launch_prologue(const BigBatch& b, const Scene& s, const Consts& c, float4* records, int maxK,
+                            int* status_to_clear, int* counter_to_clear, cudaStream_t st, const ZeroJob* zero) {
+  return launch_prologue_t(b, s, c, records, maxK, status_to_clear, counter_to_clear, st, zero);
 }
 
 // ------------------------------------------------------------------- forward
@@ -284,9 +295,9 @@ constexpr int fwd_min_blocks() {
   return (RPT == 2 && NORMALS && NFLOW > 0 && !STORE) ? 7 : 0;
 }
 
-template <bool NORMALS, int NFLOW, int RPT, bool STORE, bool COLOR = false>
+template <bool NORMALS, int NFLOW, int RPT, bool STORE, bool COLOR = false, class B = Batch>
 __global__ void __launch_bounds__(kFwdThreads, COLOR ? 0 : fwd_min_blocks<NORMALS, NFLOW, RPT, STORE>())
-    forward_kernel(const __grid_constant__ Batch batch, Scene s,
+    forward_kernel(const __grid_constant__ B batch, Scene s,
                                                               Consts k, const float4* __restrict__ records,
                                                               FwdOut out, int* status, int* counter) {
   pdl_enter();
@@ -518,10 +529,10 @@ static int fwd_ctas_per_sm_t(int maxK) {
   return n > 0 ? n : 1;
 }
 
-template <bool NORMALS, int NFLOW, int RPT, bool STORE = false, bool COLOR = false>
-static cudaError_t launch_fwd_t(const Batch& b, const Scene& s, const Consts& c, const float4* records,
+template <bool NORMALS, int NFLOW, int RPT, bool STORE = false, bool COLOR = false, class B>
+static cudaError_t launch_fwd_t(const B& b, const Scene& s, const Consts& c, const float4* records,
                                 const FwdOut& o, int maxK, int* status, int* counter, cudaStream_t st) {
-  auto kern = forward_kernel<NORMALS, NFLOW, RPT, STORE, COLOR>;
+  auto kern = forward_kernel<NORMALS, NFLOW, RPT, STORE, COLOR, B>;
   const int smem = fwd_smem_bytes(maxK, COLOR);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -537,8 +548,8 @@ static cudaError_t launch_fwd_t(const Batch& b, const Scene& s, const Consts& c,
   return launch_kernel(kern, dim3(grid), dim3(kFwdThreads), smem, st, 1, b, s, c, records, o, status, counter);
 }
 
-template <bool NORMALS, int NFLOW>
-static cudaError_t launch_fwd_r(int rpt, const Batch& b, const Scene& s, const Consts& c, const float4* records,
+template <bool NORMALS, int NFLOW, class B>
+static cudaError_t launch_fwd_r(int rpt, const B& b, const Scene& s, const Consts& c, const float4* records,
                                 const FwdOut& o, int maxK, int* status, int* counter, cudaStream_t st) {
   if (o.pairs != nullptr)  // stored-intermediate mode: two rays per thread only
     return launch_fwd_t<NORMALS, NFLOW, 2, true>(b, s, c, records, o, maxK, status, counter, st);
@@ -551,9 +562,10 @@ static cudaError_t launch_fwd_r(int rpt, const Batch& b, const Scene& s, const C
   }
 }
 
-cudaError_t launch_forward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
-                           int n_flow, int rpt, int maxK, const FwdOut& o, int* status, int* counter,
-                           cudaStream_t st) {
+template <class B>
+static cudaError_t launch_forward_t(const B& b, const Scene& s, const Consts& c, const float4* records,
+                                    bool normals, int n_flow, int rpt, int maxK, const FwdOut& o, int* status,
+                                    int* counter, cudaStream_t st) {
   if (normals) {
     if (n_flow == 0) return launch_fwd_r<true, 0>(rpt, b, s, c, records, o, maxK, status, counter, st);
     if (n_flow == 1) return launch_fwd_r<true, 1>(rpt, b, s, c, records, o, maxK, status, counter, st);
@@ -562,6 +574,16 @@ cudaError_t launch_forward(const Batch& b, const Scene& s, const Consts& c, cons
   if (n_flow == 0) return launch_fwd_r<false, 0>(rpt, b, s, c, records, o, maxK, status, counter, st);
   if (n_flow == 1) return launch_fwd_r<false, 1>(rpt, b, s, c, records, o, maxK, status, counter, st);
   return launch_fwd_r<false, 2>(rpt, b, s, c, records, o, maxK, status, counter, st);
+}
+cudaError_t launch_forward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
+                           int n_flow, int rpt, int maxK, const FwdOut& o, int* status, int* counter,
+                           cudaStream_t st) {
+  return launch_forward_t(b, s, c, records, normals, n_flow, rpt, maxK, o, status, counter, st);
+}
+cudaError_t launch_forward(const BigBatch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
+                           int n_flow, int rpt, int maxK, const FwdOut& o, int* status, int* counter,
+                           cudaStream_t st) {
+  return launch_forward_t(b, s, c, records, normals, n_flow, rpt, maxK, o, status, counter, st);
 }
 
 int forward_rays_per_cta(int rpt) { return kFwdThreads * rpt; }
@@ -574,8 +596,8 @@ int forward_rays_per_cta(int rpt) { return kFwdThreads * rpt; }
 constexpr int kMergeThreads = 128;
 int forward_merge_rays_per_item() { return kMergeThreads; }
 
-template <bool NORMALS, int NFLOW>
-__global__ void __launch_bounds__(kMergeThreads) fwd_merge_kernel(const __grid_constant__ Batch batch, Scene s,
+template <bool NORMALS, int NFLOW, class B>
+__global__ void __launch_bounds__(kMergeThreads) fwd_merge_kernel(const __grid_constant__ B batch, Scene s,
                                                                   FwdOut out) {
   pdl_enter();
   int local;
@@ -627,18 +649,27 @@ __global__ void __launch_bounds__(kMergeThreads) fwd_merge_kernel(const __grid_c
   write_ray_outputs<NORMALS, NFLOW>(V, R, o, Rj, tj, has_t, a, pxy, p, out);
 }
 
-cudaError_t launch_forward_merge(const Batch& b, const Scene& s, bool normals, int n_flow, const FwdOut& o,
-                                 cudaStream_t st) {
+template <class B>
+static cudaError_t launch_forward_merge_t(const B& b, const Scene& s, bool normals, int n_flow, const FwdOut& o,
+                                          cudaStream_t st) {
   if (b.n_items <= 0) return cudaSuccess;
   const dim3 grid(b.n_items), block(kMergeThreads);
   if (normals) {
-    if (n_flow == 0) return launch_kernel(fwd_merge_kernel<true, 0>, grid, block, 0, st, 1, b, s, o);
-    if (n_flow == 1) return launch_kernel(fwd_merge_kernel<true, 1>, grid, block, 0, st, 1, b, s, o);
-    return launch_kernel(fwd_merge_kernel<true, 2>, grid, block, 0, st, 1, b, s, o);
+    if (n_flow == 0) return launch_kernel(fwd_merge_kernel<true, 0, B>, grid, block, 0, st, 1, b, s, o);
+    if (n_flow == 1) return launch_kernel(fwd_merge_kernel<true, 1, B>, grid, block, 0, st, 1, b, s, o);
+    return launch_kernel(fwd_merge_kernel<true, 2, B>, grid, block, 0, st, 1, b, s, o);
   }
-  if (n_flow == 0) return launch_kernel(fwd_merge_kernel<false, 0>, grid, block, 0, st, 1, b, s, o);
-  if (n_flow == 1) return launch_kernel(fwd_merge_kernel<false, 1>, grid, block, 0, st, 1, b, s, o);
-  return launch_kernel(fwd_merge_kernel<false, 2>, grid, block, 0, st, 1, b, s, o);
+  if (n_flow == 0) return launch_kernel(fwd_merge_kernel<false, 0, B>, grid, block, 0, st, 1, b, s, o);
+  if (n_flow == 1) return launch_kernel(fwd_merge_kernel<false, 1, B>, grid, block, 0, st, 1, b, s, o);
+  return launch_kernel(fwd_merge_kernel<false, 2, B>, grid, block, 0, st, 1, b, s, o);
+}
+cudaError_t launch_forward_merge(const Batch& b, const Scene& s, bool normals, int n_flow, const FwdOut& o,
+                                 cudaStream_t st) {
+  return launch_forward_merge_t(b, s, normals, n_flow, o, st);
+}
+cudaError_t launch_forward_merge(const BigBatch& b, const Scene& s, bool normals, int n_flow, const FwdOut& o,
+                                 cudaStream_t st) {
+  return launch_forward_merge_t(b, s, normals, n_flow, o, st);
 }
 
 int forward_ctas_per_sm(bool normals, int n_flow, int rpt, int maxK) {

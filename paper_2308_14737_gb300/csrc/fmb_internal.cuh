@@ -10,18 +10,21 @@
 
 namespace fmb {
 
-// Views per kernel launch: the view table travels in the kernel's parameter space
-// (a __grid_constant__ struct of about 7 KB), so launches need no host->device copy
-// and can be captured in CUDA graphs.  Larger batches are split into several
-// launches.  (256 views, 30 KB, would still fit the 32 KB of kernel parameters of
-// sm_90 and later; measured on the GB300, one launch per pass instead of four made
-// the 256-view ragged batch 0.35 % faster, but the larger parameter block made
-// every launch of a small batch slower: a single 64x64 view's forward + backward
-// calls took 5-10 us more, 15-30 %.)
+// Views per kernel launch.  The view table travels as a kernel parameter (a
+// __grid_constant__ struct), so launches need no host->device copy and can be
+// captured in CUDA graphs.  Two table sizes: up to 64 views (about 7 KB) for most
+// calls, and up to 256 views (30 KB, within the 32 KB of kernel parameters of sm_90
+// and later) for the two-parameter render and adjoint kernels of a call with more
+// than 64 views, which then run as one launch per pass.  A graph launch costs the
+// same with either block (measured on the GB300: 1.12-1.16 us per launch from 256
+// bytes to 30 KB); an eager launch does not, since the host marshals the block each
+// time (per-view calls of a single 64x64 view were 6 % slower with the 30 KB table),
+// hence the small table wherever it suffices.
 #ifndef FMB_MAX_BATCH_VIEWS
 #define FMB_MAX_BATCH_VIEWS 64
 #endif
 constexpr int kMaxBatchViews = FMB_MAX_BATCH_VIEWS;
+constexpr int kMaxBigBatchViews = 256;
 
 // Per (view, Gaussian) record written by the prologue, 64 bytes (4 x float4):
 //   [L00 L10 L11 L20 | L21 L22 b0 b1 | b2 mh0 mh1 mh2 | nbl0 nbl1 nbl2 l2]
@@ -78,15 +81,19 @@ __device__ __forceinline__ int ray_pixel(const DevView& V, int i) { return V.ray
 // Gaussian block) are numbered view by view in `order_view` order -- the views
 // sorted by decreasing cost per item -- so both the hardware's block dispatch and
 // the persistent work queue take the most expensive items first.
-struct Batch {
+template <int CAP>
+struct BatchT {
+  static constexpr int kCapacity = CAP;
   int n_views;
   int n_items;
-  int order_view[kMaxBatchViews];       // views by decreasing cost per item
-  int order_begin[kMaxBatchViews + 1];  // first item of order_view[j]
-  DevView v[kMaxBatchViews];
+  int order_view[CAP];       // views by decreasing cost per item
+  int order_begin[CAP + 1];  // first item of order_view[j]
+  DevView v[CAP];
 };
+using Batch = BatchT<kMaxBatchViews>;
+using BigBatch = BatchT<kMaxBigBatchViews>;
 // Leaves room below the 32 764-byte kernel-parameter limit for the other arguments.
-static_assert(sizeof(Batch) <= 31 * 1024, "Batch must fit the kernel parameter space");
+static_assert(sizeof(BigBatch) <= 31 * 1024, "a batch table must fit the kernel parameter space");
 
 // Constants folded from the parameters (log2 domain).
 // With x = log2(delta) = K3 q + log2(lambda), the log2 weight of Eq. 7 is
@@ -282,7 +289,8 @@ __device__ __forceinline__ GaussRec unpack_rec(const float4& r0, const float4& r
 }
 
 // View and view-local index of work item `item`.
-__device__ __forceinline__ int find_item(const Batch& batch, int item, int& local) {
+template <class B>
+__device__ __forceinline__ int find_item(const B& batch, int item, int& local) {
   int lo = 0, hi = batch.n_views - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
@@ -447,16 +455,24 @@ struct ZeroJob {
 cudaError_t launch_prologue(const Batch& b, const Scene& s, const Consts& c, float4* records, int maxK,
                             int* status_to_clear, int* counter_to_clear, cudaStream_t st,
                             const ZeroJob* zero = nullptr);
+cudaError_t launch_prologue(const BigBatch& b, const Scene& s, const Consts& c, float4* records, int maxK,
+                            int* status_to_clear, int* counter_to_clear, cudaStream_t st,
+                            const ZeroJob* zero = nullptr);
 // counter: persistent mode's work counter (zeroed before the launch), or null for
 // one CTA per work item.
 struct FwdOut;
 cudaError_t launch_forward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
                            int n_flow, int rpt, int maxK, const FwdOut& o, int* status, int* counter,
                            cudaStream_t st);
+cudaError_t launch_forward(const BigBatch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
+                           int n_flow, int rpt, int maxK, const FwdOut& o, int* status, int* counter,
+                           cudaStream_t st);
 // Gaussian-split forward: the merge of the splits' partial sums (o.part) into the
 // planes; work items of forward_merge_rays_per_item() rays, the split count in DevView::S.
 int forward_merge_rays_per_item();
 cudaError_t launch_forward_merge(const Batch& b, const Scene& s, bool normals, int n_flow, const FwdOut& o,
+                                 cudaStream_t st);
+cudaError_t launch_forward_merge(const BigBatch& b, const Scene& s, bool normals, int n_flow, const FwdOut& o,
                                  cudaStream_t st);
 
 struct FwdOut {
@@ -499,6 +515,9 @@ struct BwdIn {
 cudaError_t launch_backward(const Batch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
                             int n_flow, int ray_tile, int threads, const BwdIn& in, const BwdOut& out,
                             int* counter, cudaStream_t st);
+cudaError_t launch_backward(const BigBatch& b, const Scene& s, const Consts& c, const float4* records, bool normals,
+                            int n_flow, int ray_tile, int threads, const BwdIn& in, const BwdOut& out,
+                            int* counter, cudaStream_t st);
 // Resident CTAs per SM of the render kernels for this configuration (persistent
 // grid sizing).
 int forward_ctas_per_sm(bool normals, int n_flow, int rpt, int maxK);
@@ -534,6 +553,8 @@ int attribution_rays_per_item();
 cudaError_t launch_attribution_ac(const Batch& b, const Scene& s, const Consts& c, const float4* records, int maxK,
                                   const float* loss, float* out, cudaStream_t st);
 cudaError_t launch_backward_reduce(const Batch& b, int n_flow, long long n_gauss, int n_poses,
+                                   const BwdOut& out, cudaStream_t st);
+cudaError_t launch_backward_reduce(const BigBatch& b, int n_flow, long long n_gauss, int n_poses,
                                    const BwdOut& out, cudaStream_t st);
 
 }  // namespace fmb

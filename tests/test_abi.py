@@ -235,7 +235,8 @@ def test_noalloc_status_reader_rejects_a_null_pointer(fmb):
 
 def test_launch_count_follows_the_batch_split(fmb):
     """Launches per call: prologue + kernel per launch batch; views beyond one
-    batch's capacity add batches; deterministic mode adds the reductions."""
+    batch's capacity (64 views, or 256 for the two-parameter render and adjoint of a
+    call with more than 64) add batches; deterministic mode adds the reductions."""
     s = synth.object_orbit(K=10, n_views=3, W=8, H=6)
     p = fmb.default_params()
     assert fmb.fmb_launch_count(p, s.obj_offsets, s.views, backward=False) == 2
@@ -243,9 +244,15 @@ def test_launch_count_follows_the_batch_split(fmb):
     pd = fmb.default_params(deterministic=1)
     assert fmb.fmb_launch_count(pd, s.obj_offsets, s.views, backward=True, want_pose=True) == 4
     assert fmb.fmb_launch_count(pd, s.obj_offsets, s.views, backward=True, want_pose=False) == 3
-    big = synth.object_orbit(K=10, n_views=300, W=4, H=4)
-    n = fmb.fmb_launch_count(p, big.obj_offsets, big.views, backward=False)
-    assert n >= 2 and n % 2 == 0
+    # the two-parameter render and adjoint take up to 256 views per launch once a call
+    # has more than 64; alpha compositing keeps 64 per launch
+    for n_views, batches in ((64, 1), (65, 1), (200, 1), (256, 1), (300, 2)):
+        many = synth.object_orbit(K=10, n_views=n_views, W=4, H=4)
+        assert fmb.fmb_launch_count(p, many.obj_offsets, many.views, backward=False) == 2 * batches, n_views
+        assert fmb.fmb_launch_count(p, many.obj_offsets, many.views, backward=True) == 2 * batches, n_views
+        pa = fmb.default_params(variant=1)
+        ac_batches = (n_views + 63) // 64
+        assert fmb.fmb_launch_count(pa, many.obj_offsets, many.views, backward=False) == 2 * ac_batches, n_views
     p.fwd_ksplit = 2
     assert fmb.fmb_launch_count(p, s.obj_offsets, s.views, backward=False) == 3
 
