@@ -83,12 +83,14 @@ def test_gaussian_split_forward(ksplit):
 
 def test_gaussian_split_forward_ray_batch_and_auto():
     """The automatic choice against the unsplit forward (a 6000-ray minibatch at
-    K = 256 is split, a single 64x64 view at K = 40 is not): the same planes up to the
-    rounding of the merge."""
+    K = 256 is split, also over 80 views in one 256-view launch; a single 64x64 view
+    at K = 40 is not): the same planes up to the rounding of the merge."""
     from paper_2308_14737_gb300 import synth as sy
 
+    # the 80-view batch runs its render in one 256-view launch (and the merge with it)
+    big = sy.ray_batch(sy.reconstruction(n_views=80, K=256, W=80, H=60), 8000, seed=3)
     for scene, nf, nrm in ((sy.ray_batch(sy.reconstruction(n_views=20, K=256, W=160, H=120), 6000, seed=2), 2, 0),
-                           (sy.single_view(), 0, 1)):
+                           (big, 2, 0), (sy.single_view(), 0, 1)):
         outs = []
         for ks in (1, 0):
             params = fmb.default_params(n_flow=nf, want_normals=nrm, fwd_ksplit=ks)
@@ -96,6 +98,8 @@ def test_gaussian_split_forward_ray_batch_and_auto():
             outs.append(gpu)
             if ks == 0:
                 assert fmb.fmb_forward_ksplit(params, scene.obj_offsets, r.c_views) == (4 if nf == 2 else 1)
+            if scene is big:  # prologue, forward (and merge) as one launch each for the 80 views
+                assert fmb.fmb_launch_count(params, scene.obj_offsets, r.c_views, backward=False) == 2 + (ks == 0)
         for k in ("depth", "alpha"):
             assert np.allclose(outs[0][k], outs[1][k], rtol=1e-5, atol=1e-6), k
         sv0, sv1 = outs[0]["saved"], outs[1]["saved"]
@@ -211,6 +215,19 @@ def test_cluster_backward(deterministic):
         _, _, g2 = _full_check(s, n_flow=1, deterministic=True, bwd_threads=128, bwd_ray_tile=384)
         for k in g2:
             assert np.array_equal(res[0][k], g2[k]), k
+
+
+@pytest.mark.parametrize("deterministic", [False, True])
+def test_more_than_64_views_in_one_launch(deterministic):
+    """A two-parameter call with more than 64 views runs each pass as one launch over a
+    256-view table: 70 orbit views at K = 100 and 128 backward threads (two Gaussian
+    blocks, so grid mode launches 2-CTA clusters), in atomic and deterministic mode,
+    against the oracle."""
+    s = synth.object_orbit(K=100, n_views=70, W=24, H=16)
+    p = fmb.default_params(n_flow=1, deterministic=int(deterministic), bwd_threads=128, bwd_ray_tile=384)
+    assert fmb.fmb_launch_count(p, s.obj_offsets, s.views, backward=False) == 2
+    assert fmb.fmb_launch_count(p, s.obj_offsets, s.views, backward=True, want_pose=True) == (4 if deterministic else 2)
+    _full_check(s, n_flow=1, deterministic=deterministic, bwd_threads=128, bwd_ray_tile=384)
 
 
 def test_permutation_invariance():
