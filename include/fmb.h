@@ -309,6 +309,7 @@ int fmb_forward_ksplit(const fmb_params* params, int n_objects, const long long*
  * like fmb_workspace_bytes; -1 on invalid input (message in fmb_last_error).  The
  * paper has no counterpart: this reports a launch decision of this
  * implementation (the batch is split into launches of at most a fixed number of
+ * views: 64, or 256 for a two-parameter forward or backward of more than 64
  * views; a Gaussian-split forward adds a merge; deterministic mode adds the
  * second-stage reductions). */
 int fmb_launch_count(const fmb_params* params, int n_objects, const long long* h_obj_offsets, int n_views,
