@@ -58,6 +58,21 @@ def gpu_backward(r, dev, ups, want_pose=True):
     return {k: (v.cpu().numpy().astype(np.float64) if v is not None else None) for k, v in g.items()}
 
 
+def many_small_views(n_views, seed=11):
+    """n_views tiny views (3x7 to 9x5) of three objects (K = 5, 60, 130), each with its
+    own sphere pose and forward flow to the next view's pose."""
+    rng = np.random.default_rng(seed)
+    objs = [synth.random_gaussians(rng, K, "cholesky") for K in (5, 60, 130)]
+    sizes = [(3, 7), (8, 6), (9, 5), (4, 4)]
+    poses = [synth.look_at_pose(p) for p in synth.sphere_positions(rng, n_views)]
+    views = []
+    for i in range(n_views):
+        W, H = sizes[i % len(sizes)]
+        views.append(dict(W=W, H=H, fx=float(2 * max(W, H)), fy=float(2 * max(W, H)), cx=W / 2, cy=H / 2,
+                          object=(i * 7) % 3, pose=i, flow_target=((i + 1) % n_views, -1)))
+    return synth.make_scene(objs, views, poses)
+
+
 def view_slices(scene, n_flow):
     for v in scene.views:
         o, P = v["pix_offset"], synth.view_entries(v)

@@ -13,7 +13,7 @@ import torch
 import oracle
 from paper_2308_14737_gb300 import fmb, synth
 
-from gpu_util import compare_forward, compare_grads, masked_upstream, nnorm_batched
+from gpu_util import compare_forward, compare_grads, many_small_views, masked_upstream, nnorm_batched
 
 pytestmark = pytest.mark.gpu
 
@@ -81,6 +81,27 @@ def test_fmbrender_forward_and_gradients_match_oracle(pose_grad, deterministic):
             assert torch.equal(g1, g2), k
         else:
             torch.testing.assert_close(g1, g2, rtol=0, atol=1e-6 * float(g1.abs().max()))
+
+
+def test_fmbrender_over_300_views():
+    """A renderer over 300 views of three objects (its passes run as two launches of
+    at most 256 views): planes and autograd gradients, pose gradients included,
+    against the oracle."""
+    s = many_small_views(300)
+    params = fmb.default_params(n_flow=1, want_normals=1, deterministic=1)
+    r = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), params)
+    means, chol, weights, poses = _leaves(s)
+    planes = fmb.render(r, means, chol, weights, poses)
+    own = r.forward(means.detach(), chol.detach(), weights.detach(), poses.detach())  # for the saved plane
+    ref = oracle.render_scene(s, n_flow=1)
+    gpu = dict(depth=_np(planes[0]), alpha=_np(planes[1]), normal=_np(planes[2]), flow=_np(planes[3]),
+               saved=_np(own["saved"]))
+    compare_forward(s, gpu, ref, 1, True)
+    ups = masked_upstream(s, ref["alpha"], 1, seed=6, nnorm_ref=nnorm_batched(s, ref["saved"]))
+    keys = ("means", "chol", "weights", "poses")
+    grads = torch.autograd.grad(_functional(planes, ups), [means, chol, weights, poses])
+    refg = oracle.backward_scene(s, ups["g_depth"], ups["g_alpha"], ups["g_normal"], ups["g_flow"], n_flow=1)
+    compare_grads({k: _np(g) for k, g in zip(keys, grads)}, refg, keys=keys)
 
 
 @pytest.mark.parametrize("variant,keep_order", [(0, 0), (1, 0), (1, 1)])

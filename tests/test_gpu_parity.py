@@ -15,7 +15,7 @@ from paper_2308_14737_gb300 import fmb, synth
 from gpu_util import (ac_order_ambiguous, compare_forward, compare_grads, dev_scene, gpu_backward, gpu_forward,
                       masked_upstream,
                       plane_view, points_tolerances,
-                      nnorm_batched,
+                      nnorm_batched, many_small_views,
                       oracle_backward_sampled, oracle_forward_sampled, pixel_mask_from, sample_pixels)
 
 pytestmark = pytest.mark.gpu
@@ -228,6 +228,24 @@ def test_more_than_64_views_in_one_launch(deterministic):
     assert fmb.fmb_launch_count(p, s.obj_offsets, s.views, backward=False) == 2
     assert fmb.fmb_launch_count(p, s.obj_offsets, s.views, backward=True, want_pose=True) == (4 if deterministic else 2)
     _full_check(s, n_flow=1, deterministic=deterministic, bwd_threads=128, bwd_ray_tile=384)
+
+
+@pytest.mark.parametrize("deterministic", [False, True])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_more_than_256_views_in_one_call(variant, deterministic):
+    """300 views of three objects in one call: the two-parameter passes run as two
+    launches (256 + 44 views; this small batch also takes the automatic Gaussian split
+    of the forward, so each forward launch has its merge), alpha compositing as five of
+    at most 64; forward planes and gradients against the oracle in atomic and
+    deterministic mode."""
+    s = many_small_views(300)
+    p = fmb.default_params(n_flow=1, variant=variant, deterministic=int(deterministic))
+    batches = 2 if variant == 0 else 5
+    merge = variant == 0 and fmb.fmb_forward_ksplit(p, s.obj_offsets, s.views) > 1
+    assert fmb.fmb_launch_count(p, s.obj_offsets, s.views, backward=False) == (3 if merge else 2) * batches
+    if not deterministic:
+        assert fmb.fmb_launch_count(p, s.obj_offsets, s.views, backward=True, want_pose=True) == 2 * batches
+    _full_check(s, n_flow=1, deterministic=deterministic, variant=variant)
 
 
 def test_permutation_invariance():
