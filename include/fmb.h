@@ -115,6 +115,14 @@ typedef struct {
                         must then be given the workspace of the forward call of the same
                         batch, unchanged (as with store_pairs).  0 (default): the backward
                         sorts each ray afresh.  Not with fmb_render_forward_noalloc. */
+  int bwd_gblocks;   /* two-parameter backward: Gaussian blocks per object (each block is a
+                        CTA per ray tile; more blocks spread a small batch over more SMs, at
+                        the price of one set of per-ray records per block).  0 = automatic
+                        (the fewest blocks of at most min(2 bwd_threads, 256) Gaussians, or
+                        up to three more where they fill the threads better), 1..64 = at
+                        least that many (at most one per Gaussian).  A tile hint like
+                        bwd_ray_tile: the gradients are the same up to the rounding of their
+                        sums.  Ignored by alpha compositing and the loss attribution. */
 } fmb_params;
 
 /* One camera view of one object.  Planes of the view start at pixel `pix_offset`

@@ -26,14 +26,20 @@ CANDIDATES = [dict(fwd_rays_per_thread=r, bwd_threads=t, bwd_ray_tile=t * m, use
 
 # Extra candidates for small batches (fewer 256-ray tiles than two waves of the
 # GPU's SMs): short ray tiles and narrow CTAs spread a few thousand rays over more
-# SMs, at the price of more per-tile overhead; and the forward's Gaussian split
+# SMs, at the price of more per-tile overhead; the forward's Gaussian split
 # (fwd_ksplit, two rays per thread), which shortens each thread's serial walk over
-# the Gaussians at the price of the merge launch.
+# the Gaussians at the price of the merge launch; and more Gaussian blocks per ray
+# tile in the backward (bwd_gblocks), which does the same for the adjoint at the
+# price of one set of per-ray records per block (50 000-ray minibatch at K = 256:
+# backward 0.0606 -> 0.0571 ms with 4 blocks at 256-ray tiles; one 64x64 view at
+# K = 40: 0.0167 -> 0.0146 ms with 2).
 SMALL_BWD_TILES = ((64, 64), (64, 128), (128, 128))
 SMALL_CANDIDATES = [dict(fwd_rays_per_thread=r, bwd_threads=t, bwd_ray_tile=m, use_persistent=0)
                     for r in (1, 2) for t, m in SMALL_BWD_TILES] + \
                    [dict(fwd_rays_per_thread=2, fwd_ksplit=s, bwd_threads=t, bwd_ray_tile=m, use_persistent=0)
-                    for s in (2, 4) for t, m in SMALL_BWD_TILES]
+                    for s in (2, 4) for t, m in SMALL_BWD_TILES] + \
+                   [dict(fwd_rays_per_thread=r, bwd_threads=128, bwd_ray_tile=m, bwd_gblocks=g, use_persistent=0)
+                    for r in (1, 2) for m in (128, 256) for g in (2, 4)]
 
 
 def candidates_for(views, n_sms: int) -> list:
@@ -46,7 +52,7 @@ def candidates_for(views, n_sms: int) -> list:
 # The alpha-compositing variant has fixed 32-ray tiles: only the launch mode is tuned.
 CANDIDATES_AC = [dict(use_persistent=p) for p in (0, 1)]
 
-TUNED_FIELDS = ("fwd_rays_per_thread", "bwd_threads", "bwd_ray_tile", "use_persistent", "fwd_ksplit")
+TUNED_FIELDS = ("fwd_rays_per_thread", "bwd_threads", "bwd_ray_tile", "use_persistent", "fwd_ksplit", "bwd_gblocks")
 
 
 def layout_key(obj_offsets, views, params: fmb.FmbParams, want_pose: bool) -> str:

@@ -8,6 +8,7 @@
 //   [.., ..)            backward partials (deterministic mode only)
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <exception>
@@ -22,6 +23,10 @@
 namespace fmb {
 int forward_rays_per_cta(int rpt);
 }
+
+// The Python binding mirrors these layouts field by field (ctypes structures).
+static_assert(sizeof(fmb_params) == 68 && offsetof(fmb_params, bwd_gblocks) == 64, "fmb_params layout");
+static_assert(sizeof(fmb_view) == 64 && offsetof(fmb_view, pix_offset) == 40, "fmb_view layout");
 
 namespace {
 
@@ -69,7 +74,9 @@ static double bwd_lane_fill(int K, int T, int n) {
 // better: the modelled cost per ray is K / fill (pair work) plus 5 per block (the
 // per-ray records each block builds), e.g. K = 200 at T = 160 runs as two blocks of
 // 100 (3 subgroups of 50 threads) instead of one of 200 (one subgroup of 100).
-BwdBlocking bwd_blocking(int K, int T) {
+// min_blocks > 0 (the bwd_gblocks hint) raises the count to at least that many,
+// for batches too small to fill the GPU with one block per ray tile.
+BwdBlocking bwd_blocking(int K, int T, int min_blocks = 0) {
   const int gbmax = std::min(2 * T, kMaxGaussPerCta);
   const int n_min = (K + gbmax - 1) / gbmax;
   int best_n = n_min;
@@ -84,6 +91,11 @@ BwdBlocking bwd_blocking(int K, int T) {
   BwdBlocking b;
   b.n_gb = best_n;
   b.GB = (K + b.n_gb - 1) / b.n_gb;
+  if (min_blocks > best_n) {
+    // blocks of ceil(K / n) Gaussians, none of them empty
+    b.GB = (K + std::min(min_blocks, K) - 1) / std::min(min_blocks, K);
+    b.n_gb = (K + b.GB - 1) / b.GB;
+  }
   b.S = std::max(1, T / ((b.GB + 1) / 2));
   return b;
 }
@@ -91,7 +103,7 @@ BwdBlocking bwd_blocking(int K, int T) {
 // Threads per backward CTA: the candidate with the lowest modelled cost over the
 // batch (each view's rays x (K / lane fill + 5 per Gaussian block), as in
 // bwd_blocking).
-int choose_bwd_threads(const fmb_view* views, int n_views, const long long* offs) {
+int choose_bwd_threads(const fmb_view* views, int n_views, const long long* offs, int min_blocks) {
   const int cand[] = {128, 160};
   int best = 160;
   double best_cost = -1.0;
@@ -99,7 +111,7 @@ int choose_bwd_threads(const fmb_view* views, int n_views, const long long* offs
     double cost = 0.0;
     for (int i = 0; i < n_views; ++i) {
       const int K = static_cast<int>(offs[views[i].object + 1] - offs[views[i].object]);
-      const BwdBlocking b = bwd_blocking(K, T);
+      const BwdBlocking b = bwd_blocking(K, T, min_blocks);
       cost += static_cast<double>(view_entries(views[i])) * (K / bwd_lane_fill(K, T, b.n_gb) + 5.0 * b.n_gb);
     }
     if (best_cost < 0.0 || cost < best_cost - 1e-9 || (std::fabs(cost - best_cost) <= 1e-9 && T > best)) {
@@ -160,6 +172,8 @@ fmb_status validate_scene(const fmb_params* p, int n_objects, const long long* o
     return fail(FMB_ERR_INVALID_ARG, "bwd_ray_tile must be in [32, 1024] (0 = default)");
   if (p->bwd_threads != 0 && (p->bwd_threads < 32 || p->bwd_threads > 160 || (p->bwd_threads % 32) != 0))
     return fail(FMB_ERR_INVALID_ARG, "bwd_threads must be a multiple of 32 in [32, 160] (0 = default)");
+  if (p->bwd_gblocks < 0 || p->bwd_gblocks > 64)
+    return fail(FMB_ERR_INVALID_ARG, "bwd_gblocks must be in [0, 64] (0 = automatic)");
   if (n_objects < 1) return fail(FMB_ERR_INVALID_ARG, "n_objects must be >= 1");
   if (!offs) return fail(FMB_ERR_INVALID_ARG, "h_obj_offsets is NULL");
   if (offs[0] != 0) return fail(FMB_ERR_INVALID_ARG, "h_obj_offsets[0] must be 0");
@@ -276,7 +290,7 @@ void fill_batches(Plan& pl, const fmb_params* p, const long long* offs, int n_vi
       bf.v[i] = df;
       // backward
       fmb::DevView db = d;
-      BwdBlocking bk = bwd_blocking(d.K, pl.bwd_threads);
+      BwdBlocking bk = bwd_blocking(d.K, pl.bwd_threads, p->bwd_gblocks);
       if (ac) bk = BwdBlocking{1, d.K, 1};  // one 32-ray tile x all K Gaussians per item
       const int tile_b = ac ? fmb::ac_rays_per_item() : pl.ray_tile;
       db.n_tiles = static_cast<int>((P + tile_b - 1) / tile_b);
@@ -323,7 +337,7 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
                bool allow_big = false) {
   Plan pl;
   pl.rpt = p->fwd_rays_per_thread > 0 ? p->fwd_rays_per_thread : kDefaultRpt;
-  pl.bwd_threads = p->bwd_threads > 0 ? p->bwd_threads : choose_bwd_threads(views, n_views, offs);
+  pl.bwd_threads = p->bwd_threads > 0 ? p->bwd_threads : choose_bwd_threads(views, n_views, offs, p->bwd_gblocks);
   // default ray tile: three rays per thread in the per-ray phase (balanced, and long
   // enough to amortise the per-CTA reductions)
   pl.ray_tile = p->bwd_ray_tile > 0 ? p->bwd_ray_tile : 3 * pl.bwd_threads;

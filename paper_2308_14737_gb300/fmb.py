@@ -32,7 +32,8 @@ class FmbParams(ctypes.Structure):
                 ("deterministic", ctypes.c_int), ("use_persistent", ctypes.c_int),
                 ("fwd_rays_per_thread", ctypes.c_int), ("fwd_threads", ctypes.c_int),
                 ("bwd_ray_tile", ctypes.c_int), ("bwd_threads", ctypes.c_int), ("store_pairs", ctypes.c_int),
-                ("colors", ctypes.c_int), ("fwd_ksplit", ctypes.c_int), ("keep_order", ctypes.c_int)]
+                ("colors", ctypes.c_int), ("fwd_ksplit", ctypes.c_int), ("keep_order", ctypes.c_int),
+                ("bwd_gblocks", ctypes.c_int)]
 
 
 class FmbView(ctypes.Structure):

@@ -43,8 +43,9 @@ def test_struct_layouts(fmb):
     assert ctypes.sizeof(fmb.FmbView) == 64
     assert fmb.FmbView.pix_offset.offset == 40
     assert fmb.FmbView.rays.offset == 48 and fmb.FmbView.n_rays.offset == 56
-    assert ctypes.sizeof(fmb.FmbParams) == 64
+    assert ctypes.sizeof(fmb.FmbParams) == 68
     assert fmb.FmbParams.store_pairs.offset == 48 and fmb.FmbParams.colors.offset == 52
+    assert fmb.FmbParams.keep_order.offset == 60 and fmb.FmbParams.bwd_gblocks.offset == 64
 
 
 def test_default_params_and_version(fmb):
@@ -134,11 +135,24 @@ def test_forward_rejects_bad_params(fmb):
                       ("fwd_rays_per_thread", 3, "fwd_rays_per_thread"), ("bwd_threads", 100, "bwd_threads"),
                       ("bwd_threads", 192, "bwd_threads"), ("bwd_ray_tile", 16, "bwd_ray_tile"),
                       ("store_pairs", 2, "store_pairs"), ("fwd_ksplit", 9, "fwd_ksplit"),
-                      ("fwd_ksplit", -1, "fwd_ksplit")]:
+                      ("fwd_ksplit", -1, "fwd_ksplit"), ("bwd_gblocks", 65, "bwd_gblocks"),
+                      ("bwd_gblocks", -1, "bwd_gblocks")]:
         p = fmb.default_params()
         setattr(p, k, v)
         st, err = _call_fwd(fmb, p, [0, 5], [_view()])
         assert st == 1 and msg in err, (k, err)
+
+
+def test_gaussian_block_hint_sizes_the_partials(fmb):
+    """bwd_gblocks raises the backward's Gaussian blocks per ray tile: in
+    deterministic mode each (tile, block) has a partial slot in the workspace, so the
+    workspace grows with the block count; 0 and 1 keep the automatic blocking."""
+    s = synth.object_orbit(K=40, n_views=2, W=16, H=16)
+    sizes = {}
+    for g in (0, 1, 2, 4, 64):
+        p = fmb.default_params(deterministic=1, bwd_threads=128, bwd_ray_tile=128, bwd_gblocks=g)
+        sizes[g] = fmb.fmb_workspace_bytes(p, s.obj_offsets, s.views)
+    assert sizes[0] == sizes[1] < sizes[2] < sizes[4] < sizes[64]
 
 
 def test_stored_pairs_needs_two_rays_per_thread_and_a_workspace(fmb):

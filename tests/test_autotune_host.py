@@ -42,3 +42,9 @@ def test_small_batches_get_short_tile_candidates():
         assert c["fwd_rays_per_thread"] in (1, 2, 4)
         # a Gaussian split runs only with packed (even) rays per thread
         assert c.get("fwd_ksplit", 0) in (0, 2, 4) and (c.get("fwd_ksplit", 0) == 0 or c["fwd_rays_per_thread"] == 2)
+        assert 0 <= c.get("bwd_gblocks", 0) <= 64
+    # the Gaussian-block hint is among the small-batch candidates, and a tuned field
+    assert {c.get("bwd_gblocks", 0) for c in autotune.SMALL_CANDIDATES} == {0, 2, 4}
+    assert "bwd_gblocks" in autotune.TUNED_FIELDS
+    p = autotune.apply(fmb.default_params(), dict(bwd_gblocks=4, bwd_threads=128))
+    assert p.bwd_gblocks == 4 and p.bwd_threads == 128

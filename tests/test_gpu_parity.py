@@ -189,6 +189,27 @@ def test_backward_tilings(ray_tile, threads):
     _full_check(s, n_flow=1, bwd_ray_tile=ray_tile, bwd_threads=threads)
 
 
+@pytest.mark.parametrize("gblocks,deterministic", [(2, False), (4, True), (8, False), (64, True)])
+def test_backward_gaussian_block_hint(gblocks, deterministic):
+    """bwd_gblocks raises each object's Gaussian blocks to at least that many (K = 37
+    in 2, 4, 8 blocks; K = 5 in one block per Gaussian, 128 ray subgroups of one
+    thread; two uniform blocks run as 2-CTA clusters), in a ragged two-object batch
+    and in a ray minibatch, against the oracle."""
+    rng = np.random.default_rng(21)
+    objs = [synth.random_gaussians(rng, K, "cholesky") for K in (37, 5)]
+    poses = [synth.look_at_pose(p) for p in synth.sphere_positions(rng, 4)]
+    views = [dict(W=W, H=H, fx=float(W), fy=float(W), cx=W / 2, cy=H / 2, object=o, pose=i,
+                  flow_target=((i + 1) % 4, -1)) for i, (W, H, o) in enumerate(((40, 30, 0), (17, 9, 1), (33, 33, 0),
+                                                                                (8, 8, 1)))]
+    s = synth.make_scene(objs, views, poses)
+    _full_check(s, n_flow=1, deterministic=deterministic, bwd_gblocks=gblocks, bwd_threads=128, bwd_ray_tile=128)
+    _full_check(synth.object_orbit(K=60, n_views=3, W=32, H=24), n_flow=1, deterministic=deterministic,
+                bwd_gblocks=gblocks, bwd_threads=128, bwd_ray_tile=256)
+    mb = synth.ray_batch(synth.reconstruction(n_views=6, K=64, W=40, H=30), 900, seed=4)
+    _full_check(mb, n_flow=2, normals=False, deterministic=deterministic, bwd_gblocks=gblocks, bwd_threads=128,
+                bwd_ray_tile=256)
+
+
 def test_gaussian_blocks_over_128():
     """K = 300 splits into several Gaussian blocks per CTA; K = 129 leaves a block
     with one Gaussian."""
