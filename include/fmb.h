@@ -103,7 +103,7 @@ typedef struct {
                         a share of every object's Gaussians into per-ray partial sums (32
                         bytes per ray and split, in the workspace), which a second kernel
                         merges (the max-shifted sums of Eq. 3 combine exactly) and turns
-                        into the planes.  0 = automatic (up to 4 splits when the ray
+                        into the planes.  0 = automatic (up to 6 splits when the ray
                         tiles fill less than half a wave of the GPU and an object has
                         at least 128 Gaussians), 1 = never, 2..8 = that many splits.
                         Two-parameter model only; ignored with colors or store_pairs. */

@@ -358,10 +358,11 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
   // Gaussian split of the two-parameter forward: when the batch's ray tiles fill
   // less than half a wave of the GPU (about 6 resident forward CTAs per SM) and the
   // objects are large (K >= 128, so each CTA's serial Gaussian loop is long), each
-  // tile's Gaussians are spread over up to 4 CTAs.  Measured on the GB300: a
-  // 50 000-ray minibatch at K = 256 (200 tiles) 78.9 -> 66.6 us with 4 splits, while
-  // a single 320x240 view at K = 100 (300 tiles), a 64x64 view at K = 40 and a
-  // 640x480 view at K = 256 (1200 tiles) only lose from splitting.
+  // tile's Gaussians are spread over enough CTAs for about 1.25 waves, at most 6.
+  // Measured on the GB300: a 50 000-ray minibatch at K = 256 (200 tiles) 78.9 us
+  // unsplit, 45.3 / 43.3 / 42.5 / 42.4 / 45.3 us with 4 / 5 / 6 / 7 / 8 splits,
+  // while a single 320x240 view at K = 100 (300 tiles), a 64x64 view at K = 40 and
+  // a 640x480 view at K = 256 (1200 tiles) only lose from splitting.
   if (!ac && !p->colors && !p->store_pairs && pl.rpt % 2 == 0 && p->fwd_ksplit != 1) {
     if (p->fwd_ksplit > 1) {
       pl.ksplit = p->fwd_ksplit;
@@ -374,8 +375,8 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
       }
       const long long wave = static_cast<long long>(std::max(sms, 1)) * 6;
       if (tiles > 0 && 2 * tiles < wave && maxK >= 128) {
-        const long long k = (wave + tiles - 1) / tiles;
-        pl.ksplit = static_cast<int>(std::max(1ll, std::min({k, 4ll, static_cast<long long>(maxK / 16)})));
+        const long long k = (wave + wave / 4 + tiles - 1) / tiles;
+        pl.ksplit = static_cast<int>(std::max(1ll, std::min({k, 6ll, static_cast<long long>(maxK / 16)})));
       }
     }
   }

@@ -97,7 +97,7 @@ def test_gaussian_split_forward_ray_batch_and_auto():
             gpu, r, dev = gpu_forward(scene, params)
             outs.append(gpu)
             if ks == 0:
-                assert fmb.fmb_forward_ksplit(params, scene.obj_offsets, r.c_views) == (4 if nf == 2 else 1)
+                assert fmb.fmb_forward_ksplit(params, scene.obj_offsets, r.c_views) == (6 if nf == 2 else 1)
             if scene is big:  # prologue, forward (and merge) as one launch each for the 80 views
                 assert fmb.fmb_launch_count(params, scene.obj_offsets, r.c_views, backward=False) == 2 + (ks == 0)
         for k in ("depth", "alpha"):
