@@ -75,8 +75,11 @@ static double bwd_lane_fill(int K, int T, int n) {
 // per-ray records each block builds), e.g. K = 200 at T = 160 runs as two blocks of
 // 100 (3 subgroups of 50 threads) instead of one of 200 (one subgroup of 100).
 // min_blocks > 0 (the bwd_gblocks hint) raises the count to at least that many,
-// for batches too small to fill the GPU with one block per ray tile.
-BwdBlocking bwd_blocking(int K, int T, int min_blocks = 0) {
+// for batches too small to fill the GPU with one block per ray tile.  even_blocks
+// (the stored-intermediate adjoint, which reads a thread's two Gaussians' stored
+// values with one 8-byte load) rounds the block size up to an even count, so that
+// every block starts at an even Gaussian index.
+BwdBlocking bwd_blocking(int K, int T, int min_blocks = 0, bool even_blocks = false) {
   const int gbmax = std::min(2 * T, kMaxGaussPerCta);
   const int n_min = (K + gbmax - 1) / gbmax;
   int best_n = n_min;
@@ -96,6 +99,10 @@ BwdBlocking bwd_blocking(int K, int T, int min_blocks = 0) {
     b.GB = (K + std::min(min_blocks, K) - 1) / std::min(min_blocks, K);
     b.n_gb = (K + b.GB - 1) / b.GB;
   }
+  if (even_blocks && b.n_gb > 1 && (b.GB & 1)) {
+    b.GB += 1;  // at most min(2T, 256) still: that bound is even
+    b.n_gb = (K + b.GB - 1) / b.GB;
+  }
   b.S = std::max(1, T / ((b.GB + 1) / 2));
   return b;
 }
@@ -103,7 +110,7 @@ BwdBlocking bwd_blocking(int K, int T, int min_blocks = 0) {
 // Threads per backward CTA: the candidate with the lowest modelled cost over the
 // batch (each view's rays x (K / lane fill + 5 per Gaussian block), as in
 // bwd_blocking).
-int choose_bwd_threads(const fmb_view* views, int n_views, const long long* offs, int min_blocks) {
+int choose_bwd_threads(const fmb_view* views, int n_views, const long long* offs, int min_blocks, bool even_blocks) {
   const int cand[] = {128, 160};
   int best = 160;
   double best_cost = -1.0;
@@ -111,7 +118,7 @@ int choose_bwd_threads(const fmb_view* views, int n_views, const long long* offs
     double cost = 0.0;
     for (int i = 0; i < n_views; ++i) {
       const int K = static_cast<int>(offs[views[i].object + 1] - offs[views[i].object]);
-      const BwdBlocking b = bwd_blocking(K, T, min_blocks);
+      const BwdBlocking b = bwd_blocking(K, T, min_blocks, even_blocks);
       cost += static_cast<double>(view_entries(views[i])) * (K / bwd_lane_fill(K, T, b.n_gb) + 5.0 * b.n_gb);
     }
     if (best_cost < 0.0 || cost < best_cost - 1e-9 || (std::fabs(cost - best_cost) <= 1e-9 && T > best)) {
@@ -290,7 +297,7 @@ void fill_batches(Plan& pl, const fmb_params* p, const long long* offs, int n_vi
       bf.v[i] = df;
       // backward
       fmb::DevView db = d;
-      BwdBlocking bk = bwd_blocking(d.K, pl.bwd_threads, p->bwd_gblocks);
+      BwdBlocking bk = bwd_blocking(d.K, pl.bwd_threads, p->bwd_gblocks, p->store_pairs != 0);
       if (ac) bk = BwdBlocking{1, d.K, 1};  // one 32-ray tile x all K Gaussians per item
       const int tile_b = ac ? fmb::ac_rays_per_item() : pl.ray_tile;
       db.n_tiles = static_cast<int>((P + tile_b - 1) / tile_b);
@@ -337,7 +344,7 @@ Plan make_plan(const fmb_params* p, const long long* offs, int n_objects, int n_
                bool allow_big = false) {
   Plan pl;
   pl.rpt = p->fwd_rays_per_thread > 0 ? p->fwd_rays_per_thread : kDefaultRpt;
-  pl.bwd_threads = p->bwd_threads > 0 ? p->bwd_threads : choose_bwd_threads(views, n_views, offs, p->bwd_gblocks);
+  pl.bwd_threads = p->bwd_threads > 0 ? p->bwd_threads : choose_bwd_threads(views, n_views, offs, p->bwd_gblocks, p->store_pairs != 0);
   // default ray tile: three rays per thread in the per-ray phase (balanced, and long
   // enough to amortise the per-CTA reductions)
   pl.ray_tile = p->bwd_ray_tile > 0 ? p->bwd_ray_tile : 3 * pl.bwd_threads;

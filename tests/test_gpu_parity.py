@@ -423,6 +423,12 @@ def test_stored_intermediate_adjoint(deterministic):
         _, _, gr = _full_check(scene, n_flow=nf, deterministic=deterministic, normals=(nf == 1))
         for k in gs:
             np.testing.assert_allclose(gs[k], gr[k], rtol=0, atol=2e-5 * np.abs(gr[k]).max())
+    # Gaussian blocks that would start at an odd index (K = 37 in 8 blocks of 5, or 2 of
+    # 19) are rounded up to even sizes in this mode, whose loads take two Gaussians
+    s37 = synth.object_orbit(K=37, n_views=2, W=24, H=20)
+    for g in (2, 8):
+        _full_check(s37, n_flow=1, store_pairs=1, deterministic=deterministic, bwd_gblocks=g, bwd_threads=128,
+                    bwd_ray_tile=128)
 
 
 def test_stored_intermediate_adjoint_full_size_sampled():
