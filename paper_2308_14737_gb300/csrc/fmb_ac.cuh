@@ -15,6 +15,11 @@ constexpr int kAcThreads = 32 * kAcWarps;
 constexpr int kAcRays = 32;          // rays per backward / export work item (8 per warp)
 constexpr int kAcMaxRun = 32;        // longest forward run of neighbouring rays per warp
 constexpr int kAcRayRec = 7;         // backward per-ray record, float4s (values duplicated)
+// Gaussian records staged in shared memory every 5 float4s (80 bytes) instead of 4:
+// lane l reads record 32 m + l, and with a 64-byte stride the 16-byte loads of
+// eight neighbouring lanes fall into two of the eight 16-byte bank groups (a
+// four-way conflict per quarter warp); with 80 bytes they fall into all eight.
+constexpr int kAcRecStride = 5;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr unsigned long long kNoKey = ~0ull;
@@ -154,7 +159,9 @@ struct AcSums {
   float WC0 = 0.f, WC1 = 0.f, WC2 = 0.f;  // colour mode: sum w c
 };
 
-template <bool NORMALS, int M>
+// rec: the records, RS float4s apart (kAcRecStride in shared memory, kRecFloat4 in
+// global memory).
+template <bool NORMALS, int M, int RS = kAcRecStride>
 __device__ __forceinline__ AcSums ac_render_ray(const float4* __restrict__ rec, int K, const float v[3],
                                                 const float vl[3], const Consts& k, int lane, float (&t)[M],
                                                 float (&dl)[M], float (&n)[M][3], float* sd, float* sw, float* sT,
@@ -173,8 +180,7 @@ __device__ __forceinline__ AcSums ac_render_ray(const float4* __restrict__ rec, 
     n[m][0] = n[m][1] = n[m][2] = 0.f;
     key[m] = kNoKey;
     if (e < K) {
-      const GaussRec g = unpack_rec(rec[kRecFloat4 * e], rec[kRecFloat4 * e + 1], rec[kRecFloat4 * e + 2],
-                                    rec[kRecFloat4 * e + 3]);
+      const GaussRec g = unpack_rec(rec[RS * e], rec[RS * e + 1], rec[RS * e + 2], rec[RS * e + 3]);
       const PairGeom G = pair_geom(g.L, g.b, g.mh, g.nbl, v[0], v[1], v[2], vl[0], vl[1], vl[2]);
       t[m] = G.t;
       dl[m] = ex2_approx(fmaf(G.q, k.K3, g.l2));  // delta (Eq. 4)
@@ -319,18 +325,12 @@ __device__ __forceinline__ void ac_load_order(const unsigned char* __restrict__ 
   for (int m = 0; m < M; ++m) key[m] = lane * M + m < K ? (w >> (8 * m)) & (32u * M - 1u) & 0xffu : kNoKey;
 }
 
-// Stages a view's K records into shared memory with one bulk copy; every thread
-// waits (bounded).  Returns false (after recording the timeout) if the copy did
-// not arrive.
-__device__ __forceinline__ bool ac_stage_records(float4* dst, const float4* src, int K, uint64_t* bar,
-                                                 unsigned& uses, int* status) {
-  if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(bar, static_cast<uint32_t>(K) * kRecBytes);
-    bulk_g2s(dst, src, static_cast<uint32_t>(K) * kRecBytes, bar);
-  }
-  const bool ok = mbar_wait_bounded(bar, uses & 1u, status);
-  ++uses;
-  return !__syncthreads_or(!ok);
+// Stages a view's K records into shared memory, kAcRecStride float4s apart, by
+// the whole CTA (coalesced 16-byte loads), and makes them visible to all threads.
+__device__ __forceinline__ void ac_stage_records(float4* dst, const float4* __restrict__ src, int K) {
+  for (int i = threadIdx.x; i < kRecFloat4 * K; i += blockDim.x)
+    dst[kAcRecStride * (i / kRecFloat4) + i % kRecFloat4] = __ldg(src + i);
+  __syncthreads();
 }
 
 }  // namespace fmb

@@ -64,8 +64,8 @@ __global__ void __launch_bounds__(kAcThreads) attribution_kernel(const __grid_co
     pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
     float t[M], dl[M], n[M][3];
     float* sd = scratch[warp];
-    const AcSums a = ac_render_ray<false, M>(rec, Kb, v, vl, k, lane, t, dl, n, sd, sd + 32 * M, sd + 64 * M,
-                                             key, have_order && V.rays == nullptr);
+    const AcSums a = ac_render_ray<false, M, kRecFloat4>(rec, Kb, v, vl, k, lane, t, dl, n, sd, sd + 32 * M,
+                                                         sd + 64 * M, key, have_order && V.rays == nullptr);
     have_order = true;
     const float c = a.W > 0.f ? Lj / a.W : 0.f;
 #pragma unroll

@@ -230,8 +230,8 @@ __global__ void __launch_bounds__(kAcThreads) points_ac_kernel(const __grid_cons
     float vc[3], v[3], vl[3], pxy[2];
     pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
     float t[M], dl[M], n[M][3];
-    const AcSums a = ac_render_ray<false, M>(rec, V.K, v, vl, k, lane, t, dl, n, sd, sw, sT, key,
-                                             j > 0 && V.rays == nullptr);
+    const AcSums a = ac_render_ray<false, M, kRecFloat4>(rec, V.K, v, vl, k, lane, t, dl, n, sd, sw, sT, key,
+                                                         j > 0 && V.rays == nullptr);
     const float D = depth[off + p];
     const float iW = a.W > 0.f ? 1.0f / a.W : 0.f;
     float qmax = 0.f, N[3] = {0.f, 0.f, 0.f};
