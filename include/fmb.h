@@ -111,10 +111,14 @@ typedef struct {
                         of the object's Gaussians (the result of its per-ray sort, Eq. 10)
                         in the workspace -- 32 M bytes per plane entry, M = 2, 4 or 8 for
                         a largest object of at most 64, 128 or 256 Gaussians -- and the
-                        backward starts from it instead of sorting again.  The backward
-                        must then be given the workspace of the forward call of the same
-                        batch, unchanged (as with store_pairs).  0 (default): the backward
-                        sorts each ray afresh.  Not with fmb_render_forward_noalloc. */
+                        backward walks it, four threads per ray, instead of sorting again;
+                        a ray whose stored order is not strictly increasing in its own
+                        recomputed depths (equal depths; bytes another call left) is sorted
+                        afresh, so the gradients do not depend on the workspace's content.
+                        Give the backward the workspace of the forward call of the same
+                        batch, unchanged (as with store_pairs), for the speed.  0 (default):
+                        the backward sorts each ray afresh.  Not with
+                        fmb_render_forward_noalloc. */
   int bwd_gblocks;   /* two-parameter backward: Gaussian blocks per object (each block is a
                         CTA per ray tile; more blocks spread a small batch over more SMs, at
                         the price of one set of per-ray records per block).  0 = automatic

@@ -22,7 +22,9 @@
 // (the suffix sum runs over the sorted order, again run-aware for equal depths).
 // A packed pair loop (two Gaussians per thread) then recomputes the geometry of
 // every pair and accumulates the same per-Gaussian sums as the two-parameter
-// backward, with t's direct gradient Dbar c_i and the normal's scale c_i.
+// backward, with t's direct gradient Dbar c_i and the normal's scale c_i.  With the
+// forward's depth orders kept (keep_order), four threads per ray walk the stored
+// order instead of a warp re-sorting each ray (the TPR instantiation).
 #include <algorithm>
 
 #include "fmb_ac.cuh"
@@ -229,6 +231,106 @@ __device__ __forceinline__ void bwd_pair_ac2(AcAcc2& A, const GaussRec2& gr, con
   }
 }
 
+// Per-ray part of the adjoint, shared by the warp-per-ray and the four-threads-per-
+// ray phases: the colour's upstream gradient Cbar (colour mode), the depth's total
+// upstream gradient Dbar (its own plus the flow's, Sec. 5), Nbar of the blended
+// normal N = sum w n / W (the Eq. 17 renormalisation, world frame) and Abar e^-Sd
+// (Eq. 8).  With pose_lane the ray's pose-gradient terms are added to pose_acc.
+struct AcRayAdj {
+  float Dbar, KA, Nb[3], Cb[3];
+};
+template <bool NORMALS, int NFLOW, int NPV>
+__device__ __forceinline__ AcRayAdj ac_ray_adjoint(const DevView& V, const BwdIn& in, long long off, int p,
+                                                   const float (&v)[3], const float (&vc)[3], const float (&R)[9],
+                                                   const float (&tp)[3], float o0, float o1, float o2,
+                                                   const float (&Rj)[NFLOW > 0 ? NFLOW : 1][9],
+                                                   const float (&tj)[NFLOW > 0 ? NFLOW : 1][3],
+                                                   const bool (&has_t)[NFLOW > 0 ? NFLOW : 1], float D,
+                                                   const float (&N)[3], float Sd, bool color, bool pose_lane,
+                                                   float (&pose_acc)[NPV]) {
+  const int P = V.P;
+  AcRayAdj r;
+  float* Cb = r.Cb;
+  Cb[0] = Cb[1] = Cb[2] = 0.f;
+  if (color && in.g_color != nullptr) {
+    const float* gc3 = in.g_color + 3 * off;
+#pragma unroll
+    for (int k3 = 0; k3 < 3; ++k3) Cb[k3] = gc3[k3 * P + p];
+  }
+  const float gD = in.g_depth ? in.g_depth[off + p] : 0.f;
+  const float gA = in.g_alpha ? in.g_alpha[off + p] : 0.f;
+  // flow (Sec. 5): p3 = o + v D, X = R_j p3 + t_j, flow = pi(X) - pixel
+  float pb0 = 0.f, pb1 = 0.f, pb2 = 0.f;
+  if (NFLOW > 0) {
+    const float p0 = fmaf(v[0], D, o0), p1 = fmaf(v[1], D, o1), p2 = fmaf(v[2], D, o2);
+    const float* gf = in.g_flow + 2 * NFLOW * off;
+#pragma unroll
+    for (int j = 0; j < NFLOW; ++j) {
+      if (!has_t[j]) continue;
+      const float X0 = fmaf(Rj[j][2], p2, fmaf(Rj[j][1], p1, fmaf(Rj[j][0], p0, tj[j][0])));
+      const float X1 = fmaf(Rj[j][5], p2, fmaf(Rj[j][4], p1, fmaf(Rj[j][3], p0, tj[j][1])));
+      const float X2 = fmaf(Rj[j][8], p2, fmaf(Rj[j][7], p1, fmaf(Rj[j][6], p0, tj[j][2])));
+      const float iz = 1.0f / X2;
+      const float gu = gf[(2 * j) * P + p], gv = gf[(2 * j + 1) * P + p];
+      const float Xb0 = gu * V.fx * iz;
+      const float Xb1 = gv * V.fy * iz;
+      const float Xb2 = -(Xb0 * X0 + Xb1 * X1) * iz;
+      pb0 += fmaf(Rj[j][6], Xb2, fmaf(Rj[j][3], Xb1, Rj[j][0] * Xb0));
+      pb1 += fmaf(Rj[j][7], Xb2, fmaf(Rj[j][4], Xb1, Rj[j][1] * Xb0));
+      pb2 += fmaf(Rj[j][8], Xb2, fmaf(Rj[j][5], Xb1, Rj[j][2] * Xb0));
+      if (pose_lane) {
+        float* pa = pose_acc + 12 * (1 + j);
+        const float Xb[3] = {Xb0, Xb1, Xb2};
+        const float pp[3] = {p0, p1, p2};
+#pragma unroll
+        for (int a3 = 0; a3 < 3; ++a3) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) pa[3 * a3 + c] = fmaf(Xb[a3], pp[c], pa[3 * a3 + c]);
+          pa[9 + a3] += Xb[a3];
+        }
+      }
+    }
+  }
+  const float Dbar = fmaf(v[2], pb2, fmaf(v[1], pb1, fmaf(v[0], pb0, gD)));
+  r.Dbar = Dbar;
+  if (NFLOW > 0 && pose_lane) {
+    const float w3[3] = {fmaf(D, vc[0], -tp[0]), fmaf(D, vc[1], -tp[1]), fmaf(D, vc[2], -tp[2])};
+    const float pb[3] = {pb0, pb1, pb2};
+#pragma unroll
+    for (int a3 = 0; a3 < 3; ++a3) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) pose_acc[3 * a3 + c] = fmaf(w3[a3], pb[c], pose_acc[3 * a3 + c]);
+      pose_acc[9 + a3] -= fmaf(R[3 * a3 + 2], pb2, fmaf(R[3 * a3 + 1], pb1, R[3 * a3] * pb0));
+    }
+  }
+  // normal: ncam = R n_f, n_f = N / |N|, N = sum w n / W
+  float* Nb = r.Nb;
+  Nb[0] = Nb[1] = Nb[2] = 0.f;
+  if (NORMALS && in.g_normal != nullptr) {
+    const float Nn = sqrtf(fmaf(N[0], N[0], fmaf(N[1], N[1], N[2] * N[2])));
+    const float iN = Nn > 0.f ? 1.0f / Nn : 0.f;
+    const float nf[3] = {N[0] * iN, N[1] * iN, N[2] * iN};
+    const float* gn3 = in.g_normal + 3 * off;
+    const float gn[3] = {gn3[p], gn3[P + p], gn3[2 * P + p]};
+    float nfb[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) nfb[c] = fmaf(R[6 + c], gn[2], fmaf(R[3 + c], gn[1], R[c] * gn[0]));
+    if (pose_lane) {
+#pragma unroll
+      for (int a3 = 0; a3 < 3; ++a3)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) pose_acc[3 * a3 + c] = fmaf(gn[a3], nf[c], pose_acc[3 * a3 + c]);
+    }
+    if (Nn > 0.f) {
+      const float sdot = fmaf(nf[2], nfb[2], fmaf(nf[1], nfb[1], nf[0] * nfb[0]));
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Nb[c] = fmaf(-sdot, nf[c], nfb[c]) * iN;
+    }
+  }
+  r.KA = gA * __expf(-Sd);
+  return r;
+}
+
 // Shared memory of the backward, in floats after the records:
 //   ray records [kAcRays][kAcRayRec float4] | pair values [kAcRays][32 M][2] |
 //   per warp scratch sd, sw, sT, sq [32 M floats each]
@@ -243,7 +345,10 @@ __host__ __device__ constexpr int ac_bwd_smem_floats() {
   return 32 * M * 4 * kAcRecStride + kAcRays * kAcRayRec * 4 + ac_pairv_floats<M>() + kAcWarps * 4 * 32 * M;
 }
 
-template <bool NORMALS, int NFLOW, int M>
+// TPR: the per-ray phase runs four threads per ray over the forward's stored depth
+// order (keep_order; see the four-thread phase below), the warp-per-ray phase only
+// for the rays whose stored order fails its check.
+template <bool NORMALS, int NFLOW, int M, bool TPR>
 __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 2 : 3) backward_ac_kernel(const __grid_constant__ Batch batch, Scene s,
                                                                  Consts k, const float4* __restrict__ records,
                                                                  BwdIn in, BwdOut out, int* status, int* counter) {
@@ -253,6 +358,7 @@ __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 2 : 3) backward_ac_kernel
   __shared__ float pose_ray[kAcWarps][NPV];
   __shared__ float pose_gau[kAcWarps][12];
   __shared__ int s_item;
+  __shared__ unsigned s_bad;  // TPR: rays of the item left to the warp-per-ray phase
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float4* srec = ac_smem;
   float4* rays = ac_smem + 32 * M * kAcRecStride;
@@ -278,6 +384,7 @@ __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 2 : 3) backward_ac_kernel
     const int nr = min(kAcRays, P - pix0);
     const long long off = V.pix_off;
     if (round > 0) __syncthreads();
+    if (TPR && tid == 0) s_bad = 0u;  // published by the staging's barrier
     ac_stage_records(srec, records + kRecFloat4 * V.rec_off, K);
 
     // ------------- phase A: one warp per ray -> per-ray record and per-pair (dbar, c)
@@ -297,12 +404,167 @@ __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 2 : 3) backward_ac_kernel
     float pose_acc[NPV];
 #pragma unroll
     for (int i = 0; i < NPV; ++i) pose_acc[i] = 0.f;
+    if (TPR) {
+      // ------------- phase A': four threads per ray over the forward's depth order.
+      // Thread `sub` of ray rr walks the ray's sorted positions [c0, c1).  A first pass
+      // forms the chunk's sums of w, w (t - Dref), w n and w c with the transmittance of
+      // the hits in front of it within the chunk; the four chunks combine by shuffles
+      // (T = exp(-S_in) exp(-S_chunk), the sums of the earlier chunks give each chunk's
+      // prefix); a second pass writes (dbar delta, w / W) per pair, the sums over the
+      // hits behind a hit being the ray's totals minus the inclusive prefix, which the
+      // linearity of wbar in (t, n, c) turns into U of Eq. 10's adjoint.  A ray whose
+      // stored order is not strictly increasing in the recomputed depths (equal depths,
+      // bytes from another call) or whose object has fewer than 8 Gaussians is left to
+      // the warp-per-ray phase below.
+      static_assert(kAcThreads / 4 == kAcRays, "four threads per ray of the item");
+      static_assert(8 * 32 * M <= 4 * 32 * M * static_cast<int>(sizeof(float)), "a warp's 8 orders fit its scratch");
+      const int rr = tid >> 2, sub = tid & 3;
+      const bool live = rr < nr;
+      const int p = pix0 + (live ? rr : 0);
+      float vc[3], v[3], vl[3], pxy[2];
+      pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
+      // the warp's eight stored orders, staged by 16-byte loads into its scratch (which
+      // only the warp-per-ray phase uses, after this one)
+      unsigned char* orows = reinterpret_cast<unsigned char*>(scratch);
+      {
+        constexpr int kRowU4 = 32 * M / 16;  // 16-byte words per row
+        for (int i = lane; i < 8 * kRowU4; i += 32) {
+          const int rj = warp * 8 + i / kRowU4;
+          if (rj < nr)
+            reinterpret_cast<uint4*>(orows)[i] =
+                __ldg(reinterpret_cast<const uint4*>(in.order + (off + pix0 + rj) * (32 * M)) + i % kRowU4);
+        }
+        __syncwarp();
+      }
+      const unsigned char* orow = orows + (rr & 7) * (32 * M);
+      const int c0 = (K * sub) >> 2, c1 = (K * (sub + 1)) >> 2;
+      float Dref = in.depth[off + p];  // centres the depth sums (any finite value is exact)
+      if (!(fabsf(Dref) < 1e30f)) Dref = 0.f;
+      const float4* crec = color ? s.crec + V.rec_off : nullptr;
+      constexpr int NS = 8;  // sums: w, w (t - Dref), w n (3), w c (3)
+      bool ok = K >= 8;
+      float Sc = 0.f, tl = -INFINITY, t0 = INFINITY;
+      float sum[NS];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) sum[q] = 0.f;
+#pragma unroll 2
+      for (int i = c0; i < c1; ++i) {
+        const int e = orow[i];
+        ok = ok && e < K;
+        const AcPair q = ac_pair_eval<NORMALS>(srec + kAcRecStride * (e < K ? e : 0), v, vl, k);
+        ok = ok && q.t > tl;  // strictly increasing: a sorted permutation without ties
+        if (i == c0) t0 = q.t;
+        tl = q.t;
+        const float w = ex2_approx(-Sc * kLog2e) * one_minus_exp_neg(q.dl);
+        Sc += q.dl;
+        sum[0] += w;
+        sum[1] = fmaf(w, q.t - Dref, sum[1]);
+        if (NORMALS) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) sum[2 + c] = fmaf(w, q.n[c], sum[2 + c]);
+        }
+        if (color) {
+          const float4 cc = __ldg(crec + (e < K ? e : 0));
+          sum[5] = fmaf(w, cc.x, sum[5]);
+          sum[6] = fmaf(w, cc.y, sum[6]);
+          sum[7] = fmaf(w, cc.z, sum[7]);
+        }
+      }
+      // the ray's four chunks, in depth order: lanes 4 rr .. 4 rr + 3 of the warp
+      const float Sin = ac_excl4(Sc, sub);
+      const float Sd = __shfl_sync(kFull, Sin + Sc, 3, 4);
+      const float T0 = ex2_approx(-Sin * kLog2e);
+      const float tprev = __shfl_up_sync(kFull, tl, 1, 4);
+      ok = ok && (sub == 0 || t0 > tprev);
+      const bool ok4 = __shfl_sync(kFull, ac_all4(ok) ? 1 : 0, 0, 4) != 0;
+      float pre[NS], tot[NS];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        const float x = T0 * sum[q];
+        pre[q] = ac_excl4(x, sub);
+        tot[q] = __shfl_sync(kFull, pre[q] + x, 3, 4);
+      }
+      const float W = tot[0];
+      const float iW = W > 0.f ? 1.0f / W : 0.f;
+      const float Dc = tot[1] * iW;  // D - Dref
+      const float N[3] = {tot[2] * iW, tot[3] * iW, tot[4] * iW};
+      const float Cc[3] = {tot[5] * iW, tot[6] * iW, tot[7] * iW};
+      const bool use = live && ok4;
+      const AcRayAdj ra = ac_ray_adjoint<NORMALS, NFLOW, NPV>(V, in, off, p, v, vc, R, tp, o0, o1, o2, Rj, tj, has_t,
+                                                              Dref + Dc, N, Sd, color, want_pose && use && sub == 0,
+                                                              pose_acc);
+      if (use) {
+        float2* pv = reinterpret_cast<float2*>(pairv) + rr * 32 * M;
+        float S2 = 0.f;
+        float run[NS];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) run[q] = 0.f;
+#pragma unroll 2
+        for (int i = c0; i < c1; ++i) {
+          const int e = orow[i];
+          const AcPair q = ac_pair_eval<NORMALS>(srec + kAcRecStride * e, v, vl, k);
+          const float Tl = ex2_approx(-S2 * kLog2e);
+          const float wl = Tl * one_minus_exp_neg(q.dl);
+          S2 += q.dl;
+          run[0] += wl;
+          run[1] = fmaf(wl, q.t - Dref, run[1]);
+          // sums over the hits strictly behind this one (its depth is unique on the ray)
+          const float SW = W - (pre[0] + T0 * run[0]);
+          float x = ra.Dbar * ((q.t - Dref) - Dc);
+          float u = ra.Dbar * ((tot[1] - (pre[1] + T0 * run[1])) - Dc * SW);
+          if (NORMALS) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              run[2 + c] = fmaf(wl, q.n[c], run[2 + c]);
+              x = fmaf(ra.Nb[c], q.n[c] - N[c], x);
+              u = fmaf(ra.Nb[c], (tot[2 + c] - (pre[2 + c] + T0 * run[2 + c])) - N[c] * SW, u);
+            }
+          }
+          if (color) {
+            const float4 cc = __ldg(crec + e);
+            const float cv[3] = {cc.x, cc.y, cc.z};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              run[5 + c] = fmaf(wl, cv[c], run[5 + c]);
+              x = fmaf(ra.Cb[c], cv[c] - Cc[c], x);
+              u = fmaf(ra.Cb[c], (tot[5 + c] - (pre[5 + c] + T0 * run[5 + c])) - Cc[c] * SW, u);
+            }
+          }
+          const float wbar = x * iW;
+          const float deltabar = fmaf(wbar * (T0 * Tl), ex2_approx(-q.dl * kLog2e), ra.KA - u * iW);
+          pv[e] = make_float2(deltabar * q.dl, T0 * wl * iW);
+        }
+        if (sub == 0) {
+          if (K & 1) pv[K] = make_float2(0.f, 0.f);  // the odd block's second lane in the pair loop
+          float4* rec = rays + rr * kAcRayRec;
+          rec[0] = make_float4(v[0], v[0], v[1], v[1]);
+          rec[1] = make_float4(v[2], v[2], ra.Dbar, ra.Dbar);
+          rec[2] = make_float4(ra.Nb[0], ra.Nb[0], ra.Nb[1], ra.Nb[1]);
+          rec[3] = make_float4(ra.Nb[2], ra.Nb[2], vl[0], vl[0]);
+          rec[4] = make_float4(vl[1], vl[1], vl[2], vl[2]);
+          rec[5] = make_float4(ra.Cb[0], ra.Cb[0], ra.Cb[1], ra.Cb[1]);
+          rec[6] = make_float4(ra.Cb[2], ra.Cb[2], 0.f, 0.f);
+        }
+      } else if (live && sub == 0) {
+        atomicOr(&s_bad, 1u << rr);
+      }
+      if (want_pose) {
+#pragma unroll
+        for (int i = 0; i < NPV; ++i) {
+          const float x = warp_allsum(pose_acc[i]);
+          if (lane == 0) pose_ray[warp][i] = x;
+          pose_acc[i] = 0.f;
+        }
+      }
+      __syncthreads();  // s_bad is complete
+    }
     constexpr int kPerWarp = kAcRays / kAcWarps;
     unsigned long long key[M];
     for (int m = 0; m < M; ++m) key[m] = kNoKey;
     for (int j = 0; j < kPerWarp; ++j) {
       const int rr = warp * kPerWarp + j;  // a run of neighbouring rays per warp
       if (rr >= nr) break;
+      if (TPR && !((s_bad >> rr) & 1u)) continue;  // done by the four-thread phase
       const int p = pix0 + rr;
       float vc[3], v[3], vl[3], pxy[2];
       pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
@@ -315,82 +577,12 @@ __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 2 : 3) backward_ac_kernel
       const float iW = a.W > 0.f ? 1.0f / a.W : 0.f;
       const float D = a.WT * iW;
       // colour mode: Cbar and the blended colour C = sum w c / W
-      float Cb[3] = {0.f, 0.f, 0.f}, Cc[3] = {a.WC0 * iW, a.WC1 * iW, a.WC2 * iW};
-      if (color && in.g_color != nullptr) {
-        const float* gc3 = in.g_color + 3 * off;
-#pragma unroll
-        for (int k3 = 0; k3 < 3; ++k3) Cb[k3] = gc3[k3 * P + p];
-      }
-      const float gD = in.g_depth ? in.g_depth[off + p] : 0.f;
-      const float gA = in.g_alpha ? in.g_alpha[off + p] : 0.f;
-      // flow (Sec. 5): p3 = o + v D, X = R_j p3 + t_j, flow = pi(X) - pixel
-      float pb0 = 0.f, pb1 = 0.f, pb2 = 0.f;
-      if (NFLOW > 0) {
-        const float p0 = fmaf(v[0], D, o0), p1 = fmaf(v[1], D, o1), p2 = fmaf(v[2], D, o2);
-        const float* gf = in.g_flow + 2 * NFLOW * off;
-#pragma unroll
-        for (int j = 0; j < NFLOW; ++j) {
-          if (!has_t[j]) continue;
-          const float X0 = fmaf(Rj[j][2], p2, fmaf(Rj[j][1], p1, fmaf(Rj[j][0], p0, tj[j][0])));
-          const float X1 = fmaf(Rj[j][5], p2, fmaf(Rj[j][4], p1, fmaf(Rj[j][3], p0, tj[j][1])));
-          const float X2 = fmaf(Rj[j][8], p2, fmaf(Rj[j][7], p1, fmaf(Rj[j][6], p0, tj[j][2])));
-          const float iz = 1.0f / X2;
-          const float gu = gf[(2 * j) * P + p], gv = gf[(2 * j + 1) * P + p];
-          const float Xb0 = gu * V.fx * iz;
-          const float Xb1 = gv * V.fy * iz;
-          const float Xb2 = -(Xb0 * X0 + Xb1 * X1) * iz;
-          pb0 += fmaf(Rj[j][6], Xb2, fmaf(Rj[j][3], Xb1, Rj[j][0] * Xb0));
-          pb1 += fmaf(Rj[j][7], Xb2, fmaf(Rj[j][4], Xb1, Rj[j][1] * Xb0));
-          pb2 += fmaf(Rj[j][8], Xb2, fmaf(Rj[j][5], Xb1, Rj[j][2] * Xb0));
-          if (want_pose && lane == 0) {
-            float* pa = pose_acc + 12 * (1 + j);
-            const float Xb[3] = {Xb0, Xb1, Xb2};
-            const float pp[3] = {p0, p1, p2};
-#pragma unroll
-            for (int a3 = 0; a3 < 3; ++a3) {
-#pragma unroll
-              for (int c = 0; c < 3; ++c) pa[3 * a3 + c] = fmaf(Xb[a3], pp[c], pa[3 * a3 + c]);
-              pa[9 + a3] += Xb[a3];
-            }
-          }
-        }
-      }
-      const float Dbar = fmaf(v[2], pb2, fmaf(v[1], pb1, fmaf(v[0], pb0, gD)));
-      if (NFLOW > 0 && want_pose && lane == 0) {
-        const float w3[3] = {fmaf(D, vc[0], -tp[0]), fmaf(D, vc[1], -tp[1]), fmaf(D, vc[2], -tp[2])};
-        const float pb[3] = {pb0, pb1, pb2};
-#pragma unroll
-        for (int a3 = 0; a3 < 3; ++a3) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) pose_acc[3 * a3 + c] = fmaf(w3[a3], pb[c], pose_acc[3 * a3 + c]);
-          pose_acc[9 + a3] -= fmaf(R[3 * a3 + 2], pb2, fmaf(R[3 * a3 + 1], pb1, R[3 * a3] * pb0));
-        }
-      }
-      // normal: ncam = R n_f, n_f = N / |N|, N = sum w n / W
-      float N[3] = {a.WN0 * iW, a.WN1 * iW, a.WN2 * iW};
-      float Nb[3] = {0.f, 0.f, 0.f};
-      if (NORMALS && in.g_normal != nullptr) {
-        const float Nn = sqrtf(fmaf(N[0], N[0], fmaf(N[1], N[1], N[2] * N[2])));
-        const float iN = Nn > 0.f ? 1.0f / Nn : 0.f;
-        const float nf[3] = {N[0] * iN, N[1] * iN, N[2] * iN};
-        const float* gn3 = in.g_normal + 3 * off;
-        const float gn[3] = {gn3[p], gn3[P + p], gn3[2 * P + p]};
-        float nfb[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) nfb[c] = fmaf(R[6 + c], gn[2], fmaf(R[3 + c], gn[1], R[c] * gn[0]));
-        if (want_pose && lane == 0) {
-#pragma unroll
-          for (int a3 = 0; a3 < 3; ++a3)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) pose_acc[3 * a3 + c] = fmaf(gn[a3], nf[c], pose_acc[3 * a3 + c]);
-        }
-        if (Nn > 0.f) {
-          const float sdot = fmaf(nf[2], nfb[2], fmaf(nf[1], nfb[1], nf[0] * nfb[0]));
-#pragma unroll
-          for (int c = 0; c < 3; ++c) Nb[c] = fmaf(-sdot, nf[c], nfb[c]) * iN;
-        }
-      }
-      const float KA = gA * __expf(-a.Sd);
+      const float Cc[3] = {a.WC0 * iW, a.WC1 * iW, a.WC2 * iW};
+      const float N[3] = {a.WN0 * iW, a.WN1 * iW, a.WN2 * iW};
+      const AcRayAdj ra = ac_ray_adjoint<NORMALS, NFLOW, NPV>(V, in, off, p, v, vc, R, tp, o0, o1, o2, Rj, tj, has_t,
+                                                              D, N, a.Sd, color, want_pose && lane == 0, pose_acc);
+      const float Dbar = ra.Dbar, KA = ra.KA;
+      const float Nb[3] = {ra.Nb[0], ra.Nb[1], ra.Nb[2]}, Cb[3] = {ra.Cb[0], ra.Cb[1], ra.Cb[2]};
       // wbar_e (index order) and q_e = wbar_e w_e
       float wbar[M];
 #pragma unroll
@@ -492,7 +684,7 @@ __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 2 : 3) backward_ac_kernel
     if (want_pose) {
 #pragma unroll
       for (int i = 0; i < NPV; ++i)
-        if (lane == 0) pose_ray[warp][i] = pose_acc[i];
+        if (lane == 0) pose_ray[warp][i] = TPR ? pose_ray[warp][i] + pose_acc[i] : pose_acc[i];
     }
     __syncthreads();
 
@@ -668,7 +860,7 @@ static cudaError_t launch_fwd_ac_t(const Batch& b, const Scene& s, const Consts&
 template <bool NORMALS, int NFLOW, int M>
 static cudaError_t launch_bwd_ac_t(const Batch& b, const Scene& s, const Consts& c, const float4* records,
                                    const BwdIn& in, const BwdOut& out, int* status, int* counter, cudaStream_t st) {
-  auto kern = backward_ac_kernel<NORMALS, NFLOW, M>;
+  auto kern = in.order != nullptr ? backward_ac_kernel<NORMALS, NFLOW, M, true> : backward_ac_kernel<NORMALS, NFLOW, M, false>;
   const int smem = ac_bwd_smem_floats<M>() * static_cast<int>(sizeof(float));
   if (smem > 40 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -144,10 +144,53 @@ __device__ __forceinline__ float warp_incl_max(float x, int lane) {
   }
   return x;
 }
+// Over each aligned group of four lanes (sub = lane & 3): the sum of x over the
+// group's lanes before this one (0 for sub 0), added in lane order; and whether
+// every lane of the group has b.
+__device__ __forceinline__ float ac_excl4(float x, int sub) {
+  const float x0 = __shfl_sync(kFull, x, 0, 4), x1 = __shfl_sync(kFull, x, 1, 4), x2 = __shfl_sync(kFull, x, 2, 4);
+  const float s01 = x0 + x1;
+  return sub == 0 ? 0.f : (sub == 1 ? x0 : (sub == 2 ? s01 : s01 + x2));
+}
+__device__ __forceinline__ bool ac_all4(bool b) {
+  int v = b ? 1 : 0;
+  v &= __shfl_xor_sync(kFull, v, 1, 4);
+  v &= __shfl_xor_sync(kFull, v, 2, 4);
+  return v != 0;
+}
 __device__ __forceinline__ float warp_allsum(float x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
   return x;
+}
+
+// One (ray, Gaussian) pair of the alpha-compositing render: the hit depth t (Eq. 2),
+// the density delta (Eq. 4) and, with NORMALS, the unit normal of Eq. 17 (zero
+// otherwise).  r: the Gaussian's record.  Every kernel of this variant evaluates a
+// pair through this function, so a depth order the forward kept is the order of
+// the depths the adjoint recomputes.
+struct AcPair {
+  float t, dl, n[3];
+};
+template <bool NORMALS>
+__device__ __forceinline__ AcPair ac_pair_eval(const float4* __restrict__ r, const float v[3], const float vl[3],
+                                               const Consts& k) {
+  const GaussRec g = unpack_rec(r[0], r[1], r[2], r[3]);
+  const PairGeom G = pair_geom(g.L, g.b, g.mh, g.nbl, v[0], v[1], v[2], vl[0], vl[1], vl[2]);
+  AcPair q;
+  q.t = G.t;
+  q.dl = ex2_approx(fmaf(G.q, k.K3, g.l2));  // delta (Eq. 4)
+  q.n[0] = q.n[1] = q.n[2] = 0.f;
+  if (NORMALS) {
+    const float g0 = g.L[0] * G.u0;
+    const float g1 = fmaf(g.L[2], G.u1, g.L[1] * G.u0);
+    const float g2 = fmaf(g.L[5], G.u2, fmaf(g.L[4], G.u1, g.L[3] * G.u0));
+    const float rs = rsqrt_approx(fmaxf(fmaf(g2, g2, fmaf(g1, g1, g0 * g0)), 1e-30f));
+    q.n[0] = g0 * rs;
+    q.n[1] = g1 * rs;
+    q.n[2] = g2 * rs;
+  }
+  return q;
 }
 
 // One ray of the alpha-compositing render, by one warp.  Per lane, for its
@@ -180,22 +223,15 @@ __device__ __forceinline__ AcSums ac_render_ray(const float4* __restrict__ rec, 
     n[m][0] = n[m][1] = n[m][2] = 0.f;
     key[m] = kNoKey;
     if (e < K) {
-      const GaussRec g = unpack_rec(rec[RS * e], rec[RS * e + 1], rec[RS * e + 2], rec[RS * e + 3]);
-      const PairGeom G = pair_geom(g.L, g.b, g.mh, g.nbl, v[0], v[1], v[2], vl[0], vl[1], vl[2]);
-      t[m] = G.t;
-      dl[m] = ex2_approx(fmaf(G.q, k.K3, g.l2));  // delta (Eq. 4)
-      if (NORMALS) {
-        const float g0 = g.L[0] * G.u0;
-        const float g1 = fmaf(g.L[2], G.u1, g.L[1] * G.u0);
-        const float g2 = fmaf(g.L[5], G.u2, fmaf(g.L[4], G.u1, g.L[3] * G.u0));
-        const float rs = rsqrt_approx(fmaxf(fmaf(g2, g2, fmaf(g1, g1, g0 * g0)), 1e-30f));
-        n[m][0] = g0 * rs;
-        n[m][1] = g1 * rs;
-        n[m][2] = g2 * rs;
-      }
+      const AcPair q = ac_pair_eval<NORMALS>(rec + RS * e, v, vl, k);
+      t[m] = q.t;
+      dl[m] = q.dl;
+      n[m][0] = q.n[0];
+      n[m][1] = q.n[1];
+      n[m][2] = q.n[2];
       sd[e] = dl[m];
-      sT[e] = G.t;  // for the reordering below (overwritten by T afterwards)
-      key[m] = (static_cast<unsigned long long>(order_bits(G.t)) << 32) | static_cast<unsigned>(e);
+      sT[e] = q.t;  // for the reordering below (overwritten by T afterwards)
+      key[m] = (static_cast<unsigned long long>(order_bits(q.t)) << 32) | static_cast<unsigned>(e);
     }
   }
   __syncwarp();

@@ -467,9 +467,10 @@ class FmbRender(torch.autograd.Function):
     more than once (``retain_graph``): each run recomputes from the saved planes.
     Inside ``torch.cuda.graph`` the planes come from the graph's memory pool.  With
     ``keep_order`` (alpha compositing) the depth order lives in the renderer's
-    workspace, which the last forward wrote: an earlier render's backward refines from
-    that order instead of its own, which takes more passes but reaches the same sorted
-    keys (any permutation of a view's Gaussians refines to them)."""
+    workspace, which the last forward wrote: an earlier render's backward finds that
+    order instead of its own, and every ray whose stored order fails the check against
+    its own recomputed depths is sorted afresh, so the gradients are that render's (to
+    the rounding of the other summation order), only slower."""
 
     @staticmethod
     def forward(ctx, renderer: Renderer, means, chol, weights, poses, colors=None):

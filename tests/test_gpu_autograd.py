@@ -109,8 +109,10 @@ def test_fmbrender_two_renders_alive_in_one_graph(variant, keep_order):
     """Two calls on one renderer keep their own planes: the gradient of a functional
     of the first render, taken after the second render ran, is the first render's.
     The second render moves the means, so (alpha compositing) its depth orders differ;
-    with keep_order the first render's backward starts from the second's stored order
-    and must still reach the same gradients bit for bit."""
+    with keep_order the first render's backward finds the second's stored orders in
+    the workspace, sorts the rays whose order fails its check afresh and reaches the
+    same gradients up to the rounding of the other summation order (bit for bit
+    otherwise)."""
     s = synth.object_orbit(K=40, n_views=2, W=32, H=24)
     params = fmb.default_params(n_flow=1, want_normals=1, deterministic=1, variant=variant, keep_order=keep_order)
     r = fmb.Renderer(s.obj_offsets, s.views, len(s.poses), params)
@@ -126,7 +128,12 @@ def test_fmbrender_two_renders_alive_in_one_graph(variant, keep_order):
     pb = fmb.render(r, means + shift, chol, weights * 1.5, poses)
     ga = torch.autograd.grad(_functional(pa, ups), [means, chol, weights, poses])
     for x, y in zip(alone, ga):
-        assert torch.equal(x, y)
+        if keep_order:
+            # (the upstream here is not masked at near-equal depths, where the
+            # gradient is ill-conditioned: the parity tolerance, 1e-4 of the largest)
+            assert float((x - y).abs().max()) <= 1e-4 * float(x.abs().max())
+        else:
+            assert torch.equal(x, y)
     assert not torch.equal(pa[0], pb[0])
 
 
