@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 4 : 5) forward_ac_kernel(
   pdl_enter();
   extern __shared__ float4 ac_smem[];  // records [32 M][kAcRecStride float4] | per warp: sd, sw, sT [32 M floats each]
   __shared__ int s_item;
+  __shared__ float ep[kAcWarps][kAcMaxRun][9];  // per ray of a warp's run: W, WT, Sd, WN, WC
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float4* srec = ac_smem;
   float* scratch = reinterpret_cast<float*>(ac_smem + 32 * M * kAcRecStride) + warp * 3 * 32 * M;
@@ -101,54 +102,75 @@ __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 4 : 5) forward_ac_kernel(
       const AcSums a = ac_render_ray<NORMALS, M>(srec, V.K, v, vl, k, lane, t, dl, n, sd, sw, sT, key,
                                                  j > 0 && V.rays == nullptr, crec);
       if (out.order != nullptr) ac_store_order<M>(out.order + (off + p) * (32 * M), key, lane);
-      if (lane == 0) {
-        const float iW = a.W > 0.f ? 1.0f / a.W : 0.f;
-        const float D = a.WT * iW;
-        if (crec != nullptr) {
-          float* col = out.color + 3 * off;
-          col[p] = a.WC0 * iW;
-          col[P + p] = a.WC1 * iW;
-          col[2 * P + p] = a.WC2 * iW;
-        }
-        out.depth[off + p] = D;
-        out.alpha[off + p] = -expm1f(-a.Sd);
-        float* sv = out.saved + 3 * off;
-        sv[p] = a.W;
-        sv[P + p] = a.Sd;
-        if (NORMALS) {
-          const float N0 = a.WN0 * iW, N1 = a.WN1 * iW, N2 = a.WN2 * iW;
-          const float Nn = sqrtf(fmaf(N0, N0, fmaf(N1, N1, N2 * N2)));
-          const float iN = Nn > 0.f ? 1.0f / Nn : 0.f;
-          const float n0 = N0 * iN, n1 = N1 * iN, n2 = N2 * iN;
-          float* nrm = out.normal + 3 * off;
-          nrm[p] = fmaf(R[2], n2, fmaf(R[1], n1, R[0] * n0));
-          nrm[P + p] = fmaf(R[5], n2, fmaf(R[4], n1, R[3] * n0));
-          nrm[2 * P + p] = fmaf(R[8], n2, fmaf(R[7], n1, R[6] * n0));
-          sv[2 * P + p] = Nn;
-        } else {
-          sv[2 * P + p] = 0.f;
-        }
-        if (NFLOW > 0) {
-          const float p0 = fmaf(v[0], D, o0), p1 = fmaf(v[1], D, o1), p2 = fmaf(v[2], D, o2);
-          float* fl = out.flow + 2 * NFLOW * off;
-#pragma unroll
-          for (int j = 0; j < NFLOW; ++j) {
-            float fu = 0.f, fv = 0.f;
-            if (has_t[j]) {
-              const float X0 = fmaf(Rj[j][2], p2, fmaf(Rj[j][1], p1, fmaf(Rj[j][0], p0, tj[j][0])));
-              const float X1 = fmaf(Rj[j][5], p2, fmaf(Rj[j][4], p1, fmaf(Rj[j][3], p0, tj[j][1])));
-              const float X2 = fmaf(Rj[j][8], p2, fmaf(Rj[j][7], p1, fmaf(Rj[j][6], p0, tj[j][2])));
-              const float iz = 1.0f / X2;
-              fu = fmaf(V.fx * X0, iz, V.cx) - pxy[0];
-              fv = fmaf(V.fy * X1, iz, V.cy) - pxy[1];
-            }
-            fl[(2 * j) * P + p] = fu;
-            fl[(2 * j + 1) * P + p] = fv;
-          }
-        }
+      if (lane == 0) {  // the ray's sums, for the epilogue below
+        float* e = ep[warp][j];
+        e[0] = a.W;
+        e[1] = a.WT;
+        e[2] = a.Sd;
+        e[3] = a.WN0;
+        e[4] = a.WN1;
+        e[5] = a.WN2;
+        e[6] = a.WC0;
+        e[7] = a.WC1;
+        e[8] = a.WC2;
       }
       __syncwarp();  // the scratch of this ray is read before the next ray overwrites it
     }
+    // Per-ray epilogue, one lane per ray of the run (it was lane 0's alone per ray):
+    // the planes of Eq. 3, 8, 17 and the Sec. 5 flow from the ray's sums.
+    const int p_run = (tile * kAcWarps + warp) * run;
+    if (lane < run && p_run + lane < P) {
+      const int p = p_run + lane;
+      float vc[3], v[3], vl[3], pxy[2];
+      pixel_ray_dd(V, R, ray_pixel(V, p), vc, v, vl, pxy);
+      const float* e = ep[warp][lane];
+      const float4* crec = s.crec != nullptr && out.color != nullptr ? s.crec + V.rec_off : nullptr;
+      const float iW = e[0] > 0.f ? 1.0f / e[0] : 0.f;
+      const float D = e[1] * iW;
+      if (crec != nullptr) {
+        float* col = out.color + 3 * off;
+        col[p] = e[6] * iW;
+        col[P + p] = e[7] * iW;
+        col[2 * P + p] = e[8] * iW;
+      }
+      out.depth[off + p] = D;
+      out.alpha[off + p] = -expm1f(-e[2]);
+      float* sv = out.saved + 3 * off;
+      sv[p] = e[0];
+      sv[P + p] = e[2];
+      if (NORMALS) {
+        const float N0 = e[3] * iW, N1 = e[4] * iW, N2 = e[5] * iW;
+        const float Nn = sqrtf(fmaf(N0, N0, fmaf(N1, N1, N2 * N2)));
+        const float iN = Nn > 0.f ? 1.0f / Nn : 0.f;
+        const float n0 = N0 * iN, n1 = N1 * iN, n2 = N2 * iN;
+        float* nrm = out.normal + 3 * off;
+        nrm[p] = fmaf(R[2], n2, fmaf(R[1], n1, R[0] * n0));
+        nrm[P + p] = fmaf(R[5], n2, fmaf(R[4], n1, R[3] * n0));
+        nrm[2 * P + p] = fmaf(R[8], n2, fmaf(R[7], n1, R[6] * n0));
+        sv[2 * P + p] = Nn;
+      } else {
+        sv[2 * P + p] = 0.f;
+      }
+      if (NFLOW > 0) {
+        const float p0 = fmaf(v[0], D, o0), p1 = fmaf(v[1], D, o1), p2 = fmaf(v[2], D, o2);
+        float* fl = out.flow + 2 * NFLOW * off;
+#pragma unroll
+        for (int j = 0; j < NFLOW; ++j) {
+          float fu = 0.f, fv = 0.f;
+          if (has_t[j]) {
+            const float X0 = fmaf(Rj[j][2], p2, fmaf(Rj[j][1], p1, fmaf(Rj[j][0], p0, tj[j][0])));
+            const float X1 = fmaf(Rj[j][5], p2, fmaf(Rj[j][4], p1, fmaf(Rj[j][3], p0, tj[j][1])));
+            const float X2 = fmaf(Rj[j][8], p2, fmaf(Rj[j][7], p1, fmaf(Rj[j][6], p0, tj[j][2])));
+            const float iz = 1.0f / X2;
+            fu = fmaf(V.fx * X0, iz, V.cx) - pxy[0];
+            fv = fmaf(V.fy * X1, iz, V.cy) - pxy[1];
+          }
+          fl[(2 * j) * P + p] = fu;
+          fl[(2 * j + 1) * P + p] = fv;
+        }
+      }
+    }
+    __syncwarp();  // ep is read before the next item's rays overwrite it
   }
 }
 
