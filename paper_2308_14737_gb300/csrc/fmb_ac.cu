@@ -369,9 +369,12 @@ __host__ __device__ constexpr int ac_bwd_smem_floats() {
 
 // TPR: the per-ray phase runs four threads per ray over the forward's stored depth
 // order (keep_order; see the four-thread phase below), the warp-per-ray phase only
-// for the rays whose stored order fails its check.
+// for the rays whose stored order fails its check.  Register budget: 3 CTAs per SM
+// (4 with TPR, whose phase spills 24-60 bytes at 128 registers and runs 1.2 %
+// faster on the orbit; the re-sorting phase spills 148-164 bytes there and is 9 %
+// slower), 2 for M = 8.
 template <bool NORMALS, int NFLOW, int M, bool TPR>
-__global__ void __launch_bounds__(kAcThreads, M >= 8 ? 2 : 3) backward_ac_kernel(const __grid_constant__ Batch batch, Scene s,
+__global__ void __launch_bounds__(kAcThreads, M >= 8 ? 2 : (TPR ? 4 : 3)) backward_ac_kernel(const __grid_constant__ Batch batch, Scene s,
                                                                  Consts k, const float4* __restrict__ records,
                                                                  BwdIn in, BwdOut out, int* status, int* counter) {
   pdl_enter();
