@@ -766,6 +766,14 @@ __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 2 : (TPR ? 4 : 3)) backwa
     float pose_g[12];
 #pragma unroll
     for (int i = 0; i < 12; ++i) pose_g[i] = 0.f;
+    // Atomic mode: the item's gradient values go to shared memory (the per-warp
+    // scratch, dead after the pair loop) in the outputs' layout, and the CTA then adds
+    // them with consecutive threads on consecutive floats: a Gaussian-per-thread
+    // pattern (stride 3 or 6 floats) touched about 4.5 times as many 32-byte sectors,
+    // and thousands of items add into the same few kilobytes of one object's
+    // gradients (one L2 slice was 80 % busy with them on the orbit).
+    float* cg = pairv + ac_pairv_floats<M>();  // 13 K floats: [3K means | 6K chol | K weights | 3K colours]
+    static_assert(13 * 32 * M <= kAcWarps * 4 * 32 * M, "the staged gradients fit the scratch");
     for (int gi = tid; gi < K; gi += kAcThreads) {
       float acc[22];
 #pragma unroll
@@ -811,15 +819,15 @@ __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 2 : (TPR ? 4 : 3)) backwa
           pose_g[9 + a3] += fmaf(R[3 * a3 + 2], gm[2], fmaf(R[3 * a3 + 1], gm[1], R[3 * a3] * gm[0]));
         }
       }
-      if (slot == nullptr) {
-        atomicAdd(out.gmeans + 3 * gg + 0, gm[0]);
-        atomicAdd(out.gmeans + 3 * gg + 1, gm[1]);
-        atomicAdd(out.gmeans + 3 * gg + 2, gm[2]);
+      if (slot == nullptr) {  // staged in the outputs' layout for the coalesced atomics below
+        cg[3 * gi + 0] = gm[0];
+        cg[3 * gi + 1] = gm[1];
+        cg[3 * gi + 2] = gm[2];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) atomicAdd(out.gchol + 6 * gg + i, gL[i]);
-        atomicAdd(out.gweights + gg, glam);
+        for (int i = 0; i < 6; ++i) cg[3 * K + 6 * gi + i] = gL[i];
+        cg[9 * K + gi] = glam;
         if (color)
-          for (int k3 = 0; k3 < 3; ++k3) atomicAdd(out.gcolors + 3 * gg + k3, acc[19 + k3]);
+          for (int k3 = 0; k3 < 3; ++k3) cg[10 * K + 3 * gi + k3] = acc[19 + k3];
       } else {
         float* d = slot + NC * gi;
         d[0] = gm[0];
@@ -831,6 +839,16 @@ __global__ void __launch_bounds__(kAcThreads, M >= 8 ? 2 : (TPR ? 4 : 3)) backwa
         if (color)
           for (int k3 = 0; k3 < 3; ++k3) d[10 + k3] = acc[19 + k3];
       }
+    }
+
+    if (slot == nullptr) {
+      __syncthreads();
+      const long long g0 = V.gauss_off;
+      for (int i = tid; i < 3 * K; i += kAcThreads) atomicAdd(out.gmeans + 3 * g0 + i, cg[i]);
+      for (int i = tid; i < 6 * K; i += kAcThreads) atomicAdd(out.gchol + 6 * g0 + i, cg[3 * K + i]);
+      for (int i = tid; i < K; i += kAcThreads) atomicAdd(out.gweights + g0 + i, cg[9 * K + i]);
+      if (color)
+        for (int i = tid; i < 3 * K; i += kAcThreads) atomicAdd(out.gcolors + 3 * g0 + i, cg[10 * K + i]);
     }
 
     // ------------- phase D: pose gradient of this CTA
