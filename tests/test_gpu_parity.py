@@ -654,6 +654,9 @@ def test_ray_batch_parity(variant):
     if variant == 0:
         _full_check(s, n_flow=1, use_persistent=1)
         _full_check(s, n_flow=1, store_pairs=1)
+    else:  # the adjoint walking the forward's stored orders, four threads per ray
+        _full_check(s, n_flow=1, variant=1, keep_order=1)
+        _full_check(s, n_flow=1, variant=1, keep_order=1, deterministic=True, use_persistent=1)
 
 
 def test_ray_batch_matches_full_render():
