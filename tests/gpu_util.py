@@ -2,7 +2,9 @@
 oracle on the same seeded scene, and the tolerances they are compared with.
 
 Tolerances (FP32 GPU vs FP64 oracle):
-* depth, alpha, saved sum-delta: |d| <= 1e-4 + 1e-5 |ref| (depth units), depth and
+* depth, alpha, saved sum-delta and the saved log2 normaliser: |d| <= 1e-4 + 1e-5 |ref|
+  (depth units; log2 units for the normaliser, whose exponents reach several hundred
+  at grazing rays, where the relative term carries the fp32 rounding), depth and
   the other geometric planes only where the oracle's alpha >= 1e-2.  The paper's
   own losses weight depth and flow by the object mask (Sec. 4), and on rays that
   miss every Gaussian the fp32 rounding of the whitened residual (about
@@ -164,7 +166,7 @@ def compare_forward(scene, gpu, ref, n_flow, want_normals, pixels_per_view=None,
             assert np.all(el <= tol(rs[0])), f"view {vi}: W err {el.max()}"
         else:
             el = np.abs(gs[0] - rs[0] * LOG2E)[mask]
-            assert np.all(el <= 1e-3 + 1e-5 * np.abs(rs[0][mask] * LOG2E)), f"view {vi}: lse err {el.max()}"
+            assert np.all(el <= tol(rs[0][mask] * LOG2E)), f"view {vi}: lse err {el.max()}"
         stats["alpha"] = max(stats["alpha"], float(ea.max()))
         stats["depth"] = max(stats["depth"], float(ed.max()) if ed.size else 0.0)
         stats["sdelta"] = max(stats["sdelta"], float(es.max()))
