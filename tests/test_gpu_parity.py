@@ -489,6 +489,11 @@ def test_alpha_compositing_keep_order(deterministic):
         _, _, g0 = _full_check(scene, n_flow=nf, variant=1, deterministic=deterministic)
         for k in gk:
             np.testing.assert_allclose(gk[k], g0[k], rtol=0, atol=1e-5 * np.abs(g0[k]).max())
+    # without the normal plane, two flow slots, with and without pose gradients
+    scene = synth.reconstruction(n_views=3, K=37, W=40, H=30)
+    for want_pose in (True, False):
+        _full_check(scene, n_flow=2, normals=False, want_pose=want_pose, variant=1, keep_order=1,
+                    deterministic=deterministic)
 
 
 @pytest.mark.parametrize("deterministic", [False, True])
