@@ -77,7 +77,9 @@ NO_POSE_SAVING = 3
 # transmittance and weight arithmetic (prefix sums, T = e^-S, 1 - e^-delta by its
 # series), and in the backward a re-render, the per-pair weight adjoint and the
 # packed pair loop; the per-ray 64-bit sort network (integer compares and
-# shuffles) is extra and not counted.
+# shuffles) is extra and not counted.  The backward count has one re-render: the
+# keep_order adjoint evaluates each pair twice in its per-ray phase (about 60 FP32
+# operations more), so its fraction against this count is a lower bound.
 OPS_AC = {True: (82, 4, 206, 7), False: (67, 3, 146, 5)}
 MUFU_MIX = {True: {"ex2": 2, "rcp": 1, "rsqrt": 1}, False: {"ex2": 2, "rcp": 1}}  # per pair, each pass
 N_SM = 152
