@@ -166,9 +166,10 @@ __device__ __forceinline__ float warp_allsum(float x) {
 
 // One (ray, Gaussian) pair of the alpha-compositing render: the hit depth t (Eq. 2),
 // the density delta (Eq. 4) and, with NORMALS, the unit normal of Eq. 17 (zero
-// otherwise).  r: the Gaussian's record.  Every kernel of this variant evaluates a
-// pair through this function, so a depth order the forward kept is the order of
-// the depths the adjoint recomputes.
+// otherwise).  r: the Gaussian's record.  The forward's per-ray sort and the
+// adjoint's per-ray phases (the warp re-render and the four-thread walk) all take a
+// pair's depth from this function, so a depth order the forward kept is the order
+// of the depths the adjoint recomputes.
 struct AcPair {
   float t, dl, n[3];
 };
