@@ -113,9 +113,10 @@ typedef struct {
                         a largest object of at most 64, 128 or 256 Gaussians -- and the
                         backward walks it, four threads per ray, instead of sorting again;
                         a ray whose stored order is not strictly increasing in its own
-                        recomputed depths (equal depths; bytes another call left) is sorted
-                        afresh, so the gradients do not depend on the workspace's content.
-                        Give the backward the workspace of the forward call of the same
+                        recomputed depths (equal depths; bytes another call left), and every
+                        ray of an object of fewer than 8 Gaussians, is sorted afresh, so the
+                        gradients do not depend on the workspace's content beyond the
+                        rounding of the two summation orders.  Give the backward the workspace of the forward call of the same
                         batch, unchanged (as with store_pairs), for the speed.  0 (default):
                         the backward sorts each ray afresh.  Not with
                         fmb_render_forward_noalloc. */
